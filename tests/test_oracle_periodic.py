@@ -1,0 +1,121 @@
+"""Pins for the oracle's periodizing scheme and Bragg extraction (Secs. 2.1-2.4, Remarks 2.2-2.3)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import qp_dense as qd
+from paper_1301_1247_gb300 import inputs
+
+OMEGA, D = 10.0, 1.0
+OPTS = dict(m=150, h=0.4, c=2.0, w=2.0)
+
+
+def _golden():
+    vals = {}
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_claims.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()[:2]
+                vals[k] = v
+    return vals
+
+
+def _star(n):
+    return inputs.star(0.3, 0.3, 5).sample(n)
+
+
+def test_wall_residual_quasi_periodicity():
+    """The solved field, summed directly at real points of the walls, satisfies
+    u|_L - alpha^{-1} u|_R = 0 and the same for u_x (Eqs. f, fn).  This checks B, C~ and Q
+    together without using their Fourier-space derivation."""
+    x, y, dx, dy = _star(400)
+    th = -math.pi / 5
+    s = qd.dense_solve(x, y, dx, dy, OMEGA, D, th, qd.Options(**OPTS))
+    bd = qd.boundary(x, y, dx, dy)
+    ct = qd.contour(OPTS["m"], OPTS["h"], OPTS["c"], OPTS["w"])
+    yy = np.linspace(-1.0, 1.0, 41)
+    for der in (None, "x"):
+        el, xl = qd.eval_rows(np.full_like(yy, -0.5), yy, bd, ct, OMEGA, D, s.alpha, 1, der)
+        er, xr = qd.eval_rows(np.full_like(yy, 0.5), yy, bd, ct, OMEGA, D, s.alpha, 1, der)
+        ul = el @ s.eta + xl @ s.xi
+        ur = er @ s.eta + xr @ s.xi
+        assert np.max(np.abs(ul - ur / s.alpha)) < 1e-11 * np.max(np.abs(ul))
+
+
+def test_flux_conservation_and_sixth_order_convergence():
+    """Lossless Dirichlet grating: outgoing flux equals incoming flux, up to the
+    discretization error, which falls at the KR6 rate as N doubles."""
+    th = -math.pi / 5
+    errs = []
+    for n in (256, 512):
+        x, y, dx, dy = _star(n)
+        errs.append(qd.dense_solve(x, y, dx, dy, OMEGA, D, th, qd.Options(**OPTS)).flux_error)
+    assert errs[1] < 1e-6
+    assert errs[0] / errs[1] > 40
+
+
+def test_paper_star_accuracy_order_of_magnitude():
+    """Sec. 6.1: for f(t) = 0.35 + 0.105 cos 3t at omega = 10, N = 512 'already has accuracy
+    1e-8'.  The oracle's flux error at N = 1024 is below that figure and at N = 512 within
+    two orders of magnitude of it (the paper gives no precise error definition)."""
+    g = _golden()
+    r0, a3 = float(g["star_f_r0"]), float(g["star_f_a3"])
+    obs = inputs.RadialObstacle(r0, ((3, a3 / r0, 0.0),))
+    th = float(g["star_theta_over_pi"]) * math.pi
+    claim = float(g["star_accuracy_n512"])
+    e512 = qd.dense_solve(*obs.sample(512), float(g["star_omega"]), D, th, qd.Options(**OPTS)).flux_error
+    assert e512 < 100 * claim
+    e1024 = qd.dense_solve(*obs.sample(1024), float(g["star_omega"]), D, th, qd.Options(**OPTS)).flux_error
+    assert e1024 < claim
+
+
+def test_neighbour_images_p0_equals_p1():
+    """With P = 0 and P = 1 the continuum problem is the same; with enough contour nodes the
+    Bragg amplitudes agree.  A wrong image index in C~ breaks this (reading of Sec. 2.4)."""
+    x, y, dx, dy = _star(300)
+    th = -math.pi / 5
+    s1 = qd.dense_solve(x, y, dx, dy, OMEGA, D, th, qd.Options(**OPTS, p=1))
+    s0 = qd.dense_solve(x, y, dx, dy, OMEGA, D, th, qd.Options(m=1000, h=0.4, c=2.0, w=2.0, p=0))
+    v1, v0 = qd.bragg_vector(s1), qd.bragg_vector(s0)
+    assert np.linalg.norm(v1 - v0) / np.linalg.norm(v1) < 1e-11
+
+
+def test_woods_anomaly_shifted_contour():
+    """Sec. 6.2 uses theta = -arccos(1 - 2 pi/omega), a Wood's anomaly: k_1 = 0.  On the
+    standard contour the flux balance fails; moving the crossing point and adding the one
+    Rayleigh-Bloch unknown and row restores it (Sec. 2.4)."""
+    th = -math.acos(1.0 - 2.0 * math.pi / OMEGA)
+    assert abs(qd.k_n(OMEGA, qd.kappa_n(OMEGA, D, th, 1))) < 1e-6
+    x, y, dx, dy = _star(600)
+    bad = qd.dense_solve(x, y, dx, dy, OMEGA, D, th, qd.Options(**OPTS))
+    good = qd.dense_solve(x, y, dx, dy, OMEGA, D, th, qd.Options(**OPTS, t0=2.3))
+    assert list(good.wood_modes) == [1]
+    assert bad.flux_error > 1e-5
+    assert good.flux_error < 1e-6
+    # next to the anomaly the two contours describe the same solution
+    th2 = th + 0.3
+    a = qd.dense_solve(x, y, dx, dy, OMEGA, D, th2, qd.Options(**OPTS))
+    b = qd.dense_solve(x, y, dx, dy, OMEGA, D, th2, qd.Options(**OPTS, t0=2.3))
+    va, vb = qd.bragg_vector(a), qd.bragg_vector(b)
+    assert np.linalg.norm(va - vb) / np.linalg.norm(va) < 1e-9
+
+
+def test_mirror_symmetry_normal_incidence():
+    """An obstacle symmetric under x -> -x at normal incidence (alpha = 1) scatters
+    symmetrically: c_n = c_{-n}, d_n = d_{-n}."""
+    obs = inputs.star(0.3, 0.25, 4)
+    x, y, dx, dy = obs.sample(320)
+    s = qd.dense_solve(x, y, dx, dy, OMEGA, D, -math.pi / 2, qd.Options(**OPTS))
+    assert list(s.orders) == list(-s.orders[::-1])
+    assert np.allclose(s.c, s.c[::-1], atol=1e-12, rtol=0)
+    assert np.allclose(s.d, s.d[::-1], atol=1e-12, rtol=0)
+
+
+def test_bloch_sharing_count():
+    """Remark 3.1: about omega d / pi angles share one Bloch phase (within +-1)."""
+    for omega in (10.0, 30.0, 60.0):
+        step = 2 * math.pi / (omega * D)
+        q = int(math.floor(2.0 / step))  # values c + m step inside (-1, 1)
+        assert abs(q - omega * D / math.pi) <= 1.0
