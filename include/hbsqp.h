@@ -1,0 +1,185 @@
+/*
+ * hbsqp: fast direct solver for quasi-periodic Dirichlet scattering from a
+ * grating of obstacles (Gillman & Barnett, "A fast direct solver for
+ * quasi-periodic scattering problems"), GB300 (sm_103a) CUDA library.
+ *
+ * C ABI.  All complex numbers are complex128 stored as interleaved (re, im)
+ * pairs of doubles.  Matrices are column-major.  Device pointers are plain
+ * CUDA global-memory addresses; `stream` is a cudaStream_t passed as void*
+ * (NULL = legacy default stream).  Every call returns an hbs_status;
+ * hbs_last_error() gives a human-readable message for the last failure on
+ * the calling thread.  Nothing here falls back to the CPU: a call that
+ * cannot run its kernels fails with HBS_ERR_CUDA.
+ */
+#ifndef HBSQP_H
+#define HBSQP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hbs_status {
+  HBS_OK = 0,
+  HBS_ERR_INVALID_ARG = 1, /* bad size, pointer, angle or geometry */
+  HBS_ERR_OOM = 2,         /* device allocation failed */
+  HBS_ERR_CUDA = 3,        /* a CUDA call or kernel launch failed */
+  HBS_ERR_RANK = 4,        /* a skeleton rank exceeded the supported maximum */
+  HBS_WARN_ILLCOND = 5,    /* a Schur system was numerically singular (guided mode, Remark 2.1) */
+  HBS_ERR_TIMEOUT = 6,     /* a bounded device wait gave up */
+  HBS_ERR_IO = 7,          /* file could not be read or written */
+  HBS_ERR_INTERNAL = 8
+} hbs_status;
+
+typedef struct hbs_handle hbs_handle; /* compressed inverse of A + periodizer precompute */
+typedef struct hbs_result hbs_result; /* Bragg amplitudes of a batch of incident angles */
+
+/*
+ * Obstacle boundary sampled by the N-point periodic trapezoid rule (Sec. 2.3):
+ * nodes z(t_j) = (x_j, y_j) and derivatives z'(t_j) = (dx_j, dy_j) at
+ * t_j = 2 pi j / N, counter-clockwise, with the obstacle inside the unit
+ * cell |x| < d/2 (Sec. 2.1).  The arrays are copied at build time; the
+ * caller keeps ownership.
+ */
+typedef struct hbs_geometry {
+  int64_t n;
+  double d;
+  const double* x;
+  const double* y;
+  const double* dx;
+  const double* dy;
+  int on_device; /* 0: host pointers, 1: device pointers */
+} hbs_geometry;
+
+#define HBS_PRECISION_FP64 0
+
+typedef struct hbs_options {
+  int leaf_size;        /* maximum points per leaf of the binary tree (default 64) */
+  int n_proxy_min;      /* minimum proxy points on each node's proxy circle (default 64) */
+  double proxy_rho;     /* node proxy circle radius / node radius (default 1.5) */
+  double nb_radius;     /* neighbour proxy circle radius, Sec. 3.2 (0: automatic) */
+  int nb_proxies;       /* neighbour proxy points (0: automatic) */
+  int m;                /* Sommerfeld nodes per wall density type (0: automatic) */
+  double contour_h;     /* trapezoid spacing in Re k (0: automatic) */
+  double contour_c;     /* contour height c in k = t - i c tanh((t - t0)/w) (0: 2) */
+  double contour_w;     /* contour width w (0: 2) */
+  double contour_k;     /* truncation |Re k - t0| <= K (0: automatic) */
+  double wood_shift;    /* crossing point t0 of the second contour (0: automatic, < 0: none) */
+  int n_bragg_samples;  /* samples per line for the Bragg DFT (0: automatic) */
+  double y0;            /* Bragg sampling height (0: max |y| + d/4) */
+  int precision;        /* HBS_PRECISION_FP64 */
+} hbs_options;
+
+typedef struct hbs_info_t {
+  int64_t n;             /* boundary nodes */
+  int levels;            /* tree levels below the root */
+  int max_rank;          /* largest skeleton size over all nodes */
+  int nb_rank;           /* neighbour interaction rank l (Sec. 3.2) */
+  int m;                 /* Sommerfeld nodes per density type */
+  int n_contours;        /* 1, or 2 when a Wood's-anomaly contour is precomputed */
+  size_t device_bytes;   /* device memory held by the handle */
+  double build_seconds;  /* wall time of hbs_build */
+  double factor_bytes;   /* bytes of the compressed inverse (E, F*, G over all nodes) */
+  double apply_flops_per_rhs; /* real flops of one A^{-1} apply per right-hand side */
+  double contour_h, contour_c, contour_w; /* Sommerfeld contour actually used */
+  double wood_t0;        /* crossing point of the second contour (0 if none) */
+  int n_bragg_samples;   /* S */
+  double y0;             /* Bragg sampling height */
+  double nb_radius;      /* neighbour proxy circle radius */
+  int nb_proxies;        /* neighbour proxy points */
+} hbs_info_t;
+
+/* Fill `opts` with the defaults listed above. */
+void hbs_default_options(hbs_options* opts);
+
+/*
+ * Pre-computation (Sec. 6, first step): HBS compression and inversion of the
+ * isolated-obstacle matrix A = I/2 + D - i w S (Sec. 4), the neighbour-image
+ * factors A_{+-1} = L R (Sec. 3.2) and the angle-independent products with
+ * the periodizing blocks (Secs. 2.2-2.4).  `tol` is the relative ID
+ * tolerance.  On success *out owns device memory until hbs_free.
+ * Errors: INVALID_ARG (n < 64, d <= 0, omega <= 0, tol outside (0, 1),
+ * obstacle touching a wall), OOM, CUDA, RANK.
+ */
+hbs_status hbs_build(const hbs_geometry* geom, double omega, double tol, const hbs_options* opts,
+                     void* stream, hbs_handle** out);
+
+/*
+ * Block solve (Sec. 3 and Sec. 6, second step) for incident angles
+ * theta[0..n_theta) in (-pi, 0) (host array).  Angles are grouped by Bloch
+ * phase alpha = exp(i w d cos theta) (Remark 3.1) and each group is solved
+ * with one multi-right-hand-side apply of the compressed inverse.  Returns
+ * a result holding Bragg amplitudes for every angle.  Errors: INVALID_ARG,
+ * OOM, CUDA; WARN_ILLCOND when a Schur system was singular to working
+ * precision (the result is still produced).
+ */
+hbs_status hbs_solve(hbs_handle* h, const double* theta, int64_t n_theta, void* stream,
+                     hbs_result** out);
+
+/*
+ * Same result as hbs_solve, computed the way the paper counts it: for each
+ * Bloch phase the compressed inverse is applied to q + 2M + 2Pl vectors
+ * (Remark 3.2) instead of using the angle-independent precompute.  This is
+ * the plain FP64 per-angle path used as a reference.
+ */
+hbs_status hbs_solve_plain(hbs_handle* h, const double* theta, int64_t n_theta, void* stream,
+                           hbs_result** out);
+
+/*
+ * Bragg amplitudes of angle i of a result (Remarks 2.2, 2.3): propagating
+ * orders n_min..n_max (|kappa_n| <= w), upward c_n and downward d_n as in
+ * Eqs. (rbu), (rbd), and the flux error |sum_n (k_n/k_0)(|c_n|^2 +
+ * |d_n + delta_n0 e^{i k_0 y0}|^2) - 1|.  c and d are caller-allocated host
+ * arrays of 2 (n_max - n_min + 1) doubles, or NULL to query the orders only.
+ */
+hbs_status hbs_bragg_amplitudes(const hbs_result* r, int64_t i, int* n_min, int* n_max, double* c,
+                                double* d, double* flux_err);
+
+/* Extra per-angle facts of a result: Wood's-anomaly modes added (count) and the
+ * contour crossing point used. */
+hbs_status hbs_result_angle_info(const hbs_result* r, int64_t i, int* n_wood, double* t0);
+
+/* Sizes and timings of a built handle. */
+hbs_status hbs_info(const hbs_handle* h, hbs_info_t* info);
+
+/*
+ * x = A^{-1} b with the compressed inverse (Sec. 4, telescoping apply),
+ * for nrhs columns at once.  b and x are device arrays of N x nrhs complex128,
+ * column-major with leading dimension N; they may not alias.
+ */
+hbs_status hbs_apply_inverse(const hbs_handle* h, const void* b, void* x, int64_t nrhs,
+                             void* stream);
+
+/*
+ * Kernel block fill, the building block of every matrix in the method
+ * (Sec. 2.3 entry formula): out[r + nr c] = entry(rows[r], cols[c]) for
+ * device index arrays rows (nr) and cols (nc) into the boundary nodes of a
+ * device geometry.  kind 0: A_ij (with I/2 and Kapur-Rokhlin weights);
+ * kind 1: image block A_s with the source obstacle shifted by shift_x.
+ * out is device complex128, nr x nc column-major.
+ */
+hbs_status hbs_kernel_block(const hbs_geometry* geom, double omega, int kind, double shift_x,
+                            const int64_t* rows, int64_t nr, const int64_t* cols, int64_t nc,
+                            void* out, void* stream);
+
+/*
+ * Interpolative decomposition (Def. 3.1) by column-pivoted QR of a device
+ * matrix Mt = M^T (m x n, column-major, overwritten): M ~ P M(J, :).
+ * On return *rank = l, perm[0..n) (device int32) lists J = perm[0..l) first,
+ * and T (device, l x (n - l) column-major, capacity min(m,n) x n) holds
+ * R11^{-1} R12 so that P(perm[l + j], :) = T(:, j)^T.
+ */
+hbs_status hbs_row_id(void* mt, int64_t m, int64_t n, double tol, int* rank, int* perm, void* t,
+                      void* stream);
+
+void hbs_free(hbs_handle* h);
+void hbs_result_free(hbs_result* r);
+const char* hbs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HBSQP_H */

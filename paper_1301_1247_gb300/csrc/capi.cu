@@ -1,0 +1,273 @@
+// C ABI of the library (include/hbsqp.h): argument checks, handle lifetime, error codes.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "dense_kernels.cuh"
+#include "qp_kernels.cuh"
+
+namespace hbs {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+size_t Handle::device_bytes() const {
+  size_t b = x.bytes() + y.bytes() + nx.bytes() + ny.bytes() + w.bytes() + Groot.bytes();
+  for (const auto& lv : levels)
+    b += lv.idx.bytes() + lv.perm.bytes() + lv.T.bytes() + lv.E.bytes() + lv.F.bytes() + lv.G.bytes() +
+         lv.Dhat.bytes() + lv.cx.bytes() + lv.cy.bytes() + lv.rad.bytes();
+  b += nb_skel.bytes() + Pnb.bytes() + Rm.bytes() + Rp.bytes() + Esamp.bytes() + W.bytes();
+  for (const auto& c : contours)
+    b += c.dk.bytes() + c.dwk.bytes() + c.CL.bytes() + c.CR.bytes() + c.SL.bytes() + c.SR.bytes() + c.Zd.bytes();
+  return b;
+}
+
+template <typename F>
+static hbs_status guarded(F&& f) {
+  try {
+    f();
+    return HBS_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return HBS_ERR_OOM;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return HBS_ERR_INTERNAL;
+  }
+}
+
+__global__ void k_kernel_block(DevGeom g, int kind, double shift_x, const int64_t* rows, int64_t nr,
+                               const int64_t* cols, int64_t nc, cplx* out) {
+  const int64_t tot = nr * nc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = rows[e % nr], c = cols[e / nr];
+    out[e] = kind == 0 ? a_entry(g, r, c) : a_image_entry(g, r, c, shift_x);
+  }
+}
+
+// Copy the caller's geometry into device SoA arrays and derive normals and weights.
+static void load_geometry(Handle& h, const hbs_geometry* geom, cudaStream_t s) {
+  const int64_t N = geom->n;
+  h.N = N;
+  h.d = geom->d;
+  h.x.alloc(N); h.y.alloc(N); h.nx.alloc(N); h.ny.alloc(N); h.w.alloc(N);
+  DevBuf<double> dx(N), dy(N);
+  const cudaMemcpyKind kind = geom->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  HBS_CUDA(cudaMemcpyAsync(h.x.get(), geom->x, N * sizeof(double), kind, s));
+  HBS_CUDA(cudaMemcpyAsync(h.y.get(), geom->y, N * sizeof(double), kind, s));
+  HBS_CUDA(cudaMemcpyAsync(dx.get(), geom->dx, N * sizeof(double), kind, s));
+  HBS_CUDA(cudaMemcpyAsync(dy.get(), geom->dy, N * sizeof(double), kind, s));
+  k_geom<<<grid_1d(N), 256, 0, s>>>(dx.get(), dy.get(), h.nx.get(), h.ny.get(), h.w.get(), N);
+  HBS_LAUNCH_CHECK("k_geom");
+  h.hx = h.x.download(s);
+  h.hy = h.y.download(s);
+}
+
+static DevGeom geom_view(const hbs_geometry* geom, double omega, DevBuf<double>& nx, DevBuf<double>& ny,
+                         DevBuf<double>& w, cudaStream_t s) {
+  const int64_t N = geom->n;
+  nx.alloc(N); ny.alloc(N); w.alloc(N);
+  k_geom<<<grid_1d(N), 256, 0, s>>>(geom->dx, geom->dy, nx.get(), ny.get(), w.get(), N);
+  HBS_LAUNCH_CHECK("k_geom");
+  DevGeom g;
+  g.x = geom->x; g.y = geom->y; g.nx = nx.get(); g.ny = ny.get(); g.w = w.get(); g.n = N; g.omega = omega;
+  return g;
+}
+
+}  // namespace hbs
+
+using namespace hbs;
+
+extern "C" {
+
+void hbs_default_options(hbs_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->leaf_size = 64;
+  o->n_proxy_min = 64;
+  o->proxy_rho = 1.5;
+  o->precision = HBS_PRECISION_FP64;
+}
+
+hbs_status hbs_build(const hbs_geometry* geom, double omega, double tol, const hbs_options* opts, void* stream,
+                     hbs_handle** out) {
+  if (!out) { set_last_error("out is NULL"); return HBS_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (!geom || !geom->x || !geom->y || !geom->dx || !geom->dy) {
+    set_last_error("geometry arrays are NULL");
+    return HBS_ERR_INVALID_ARG;
+  }
+  if (geom->n < 64 || !(geom->d > 0) || !(omega > 0) || !(tol > 0 && tol < 1)) {
+    set_last_error("need n >= 64, d > 0, omega > 0, 0 < tol < 1");
+    return HBS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  hbs_handle* hh = new (std::nothrow) hbs_handle();
+  if (!hh) { set_last_error("host allocation failed"); return HBS_ERR_OOM; }
+  hbs_status st = guarded([&] {
+    Handle& h = hh->h;
+    auto t0 = std::chrono::steady_clock::now();
+    hbs_default_options(&h.opts);
+    if (opts) h.opts = *opts;
+    if (h.opts.leaf_size < 8) h.opts.leaf_size = 64;
+    if (h.opts.n_proxy_min < 8) h.opts.n_proxy_min = 64;
+    if (!(h.opts.proxy_rho > 1.0)) h.opts.proxy_rho = 1.5;
+    if (h.opts.precision != HBS_PRECISION_FP64) throw Error(HBS_ERR_INVALID_ARG, "unsupported precision mode");
+    h.omega = omega;
+    h.tol = tol;
+    load_geometry(h, geom, s);
+    for (int64_t i = 0; i < h.N; ++i)
+      if (!(std::fabs(h.hx[i]) < 0.5 * h.d)) throw Error(HBS_ERR_INVALID_ARG, "obstacle touches a unit-cell wall");
+    build_hbs(h, s);
+    build_periodizer(h, s);
+    HBS_CUDA(cudaStreamSynchronize(s));
+    h.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  });
+  if (st != HBS_OK) {
+    delete hh;
+    return st;
+  }
+  *out = hh;
+  return HBS_OK;
+}
+
+static hbs_status solve_common(hbs_handle* h, const double* theta, int64_t n_theta, void* stream, hbs_result** out,
+                               bool plain) {
+  if (!h || !out || (n_theta > 0 && !theta) || n_theta < 0) {
+    set_last_error("bad arguments to hbs_solve");
+    return HBS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  hbs_result* r = new (std::nothrow) hbs_result();
+  if (!r) { set_last_error("host allocation failed"); return HBS_ERR_OOM; }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  hbs_status st = guarded([&] {
+    solve_angles(h->h, theta, n_theta, plain, r->r, s);
+    HBS_CUDA(cudaStreamSynchronize(s));
+  });
+  if (st != HBS_OK) { delete r; return st; }
+  *out = r;
+  if (r->r.illcond) {
+    set_last_error("a Schur system was singular to working precision");
+    return HBS_WARN_ILLCOND;
+  }
+  return HBS_OK;
+}
+
+hbs_status hbs_solve(hbs_handle* h, const double* theta, int64_t n_theta, void* stream, hbs_result** out) {
+  return solve_common(h, theta, n_theta, stream, out, false);
+}
+
+hbs_status hbs_solve_plain(hbs_handle* h, const double* theta, int64_t n_theta, void* stream, hbs_result** out) {
+  return solve_common(h, theta, n_theta, stream, out, true);
+}
+
+hbs_status hbs_bragg_amplitudes(const hbs_result* r, int64_t i, int* n_min, int* n_max, double* c, double* d,
+                                double* flux_err) {
+  if (!r || i < 0 || i >= (int64_t)r->r.angles.size()) {
+    set_last_error("bad result or angle index");
+    return HBS_ERR_INVALID_ARG;
+  }
+  const AngleResult& a = r->r.angles[i];
+  if (n_min) *n_min = a.n_min;
+  if (n_max) *n_max = a.n_max;
+  if (flux_err) *flux_err = a.flux_err;
+  for (size_t o = 0; o < a.c.size(); ++o) {
+    if (c) { c[2 * o] = a.c[o].real(); c[2 * o + 1] = a.c[o].imag(); }
+    if (d) { d[2 * o] = a.d[o].real(); d[2 * o + 1] = a.d[o].imag(); }
+  }
+  return HBS_OK;
+}
+
+hbs_status hbs_result_angle_info(const hbs_result* r, int64_t i, int* n_wood, double* t0) {
+  if (!r || i < 0 || i >= (int64_t)r->r.angles.size()) {
+    set_last_error("bad result or angle index");
+    return HBS_ERR_INVALID_ARG;
+  }
+  if (n_wood) *n_wood = r->r.angles[i].n_wood;
+  if (t0) *t0 = r->r.angles[i].t0;
+  return HBS_OK;
+}
+
+hbs_status hbs_info(const hbs_handle* hh, hbs_info_t* info) {
+  if (!hh || !info) { set_last_error("NULL argument"); return HBS_ERR_INVALID_ARG; }
+  const Handle& h = hh->h;
+  info->n = h.N;
+  info->levels = h.L;
+  info->max_rank = h.max_rank;
+  info->nb_rank = h.nb_rank;
+  info->m = h.M;
+  info->n_contours = (int)h.contours.size();
+  info->device_bytes = h.device_bytes();
+  info->build_seconds = h.build_seconds;
+  info->factor_bytes = h.factor_bytes;
+  info->apply_flops_per_rhs = h.apply_flops;
+  info->contour_h = h.ch;
+  info->contour_c = h.cc;
+  info->contour_w = h.cw;
+  info->wood_t0 = h.contours.size() > 1 ? h.contours[1].t0 : 0.0;
+  info->n_bragg_samples = h.S;
+  info->y0 = h.y0;
+  info->nb_radius = h.nb_R;
+  info->nb_proxies = h.nb_np;
+  return HBS_OK;
+}
+
+hbs_status hbs_apply_inverse(const hbs_handle* hh, const void* b, void* x, int64_t nrhs, void* stream) {
+  if (!hh || !b || !x || nrhs < 0) { set_last_error("bad arguments to hbs_apply_inverse"); return HBS_ERR_INVALID_ARG; }
+  if (b == x) { set_last_error("b and x must not alias"); return HBS_ERR_INVALID_ARG; }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return guarded([&] {
+    hh->h.apply_inverse(static_cast<const cplx*>(b), static_cast<cplx*>(x), nrhs, s);
+    HBS_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+hbs_status hbs_kernel_block(const hbs_geometry* geom, double omega, int kind, double shift_x, const int64_t* rows,
+                            int64_t nr, const int64_t* cols, int64_t nc, void* out, void* stream) {
+  if (!geom || !geom->on_device || !rows || !cols || !out || nr < 0 || nc < 0 || (kind != 0 && kind != 1) ||
+      geom->n < 13) {
+    set_last_error("bad arguments to hbs_kernel_block (geometry must be on the device)");
+    return HBS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return guarded([&] {
+    DevBuf<double> nx, ny, w;
+    DevGeom g = geom_view(geom, omega, nx, ny, w, s);
+    if (nr * nc > 0) {
+      k_kernel_block<<<grid_1d(nr * nc), 256, 0, s>>>(g, kind, shift_x, rows, nr, cols, nc, static_cast<cplx*>(out));
+      HBS_LAUNCH_CHECK("k_kernel_block");
+    }
+    HBS_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+hbs_status hbs_row_id(void* mt, int64_t m, int64_t n, double tol, int* rank, int* perm, void* t, void* stream) {
+  if (!mt || !rank || !perm || !t || m <= 0 || n <= 0 || !(tol > 0)) {
+    set_last_error("bad arguments to hbs_row_id");
+    return HBS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return guarded([&] {
+    if (n <= 4096) {
+      std::vector<CpqrJob> jobs(1);
+      jobs[0] = {0, 0, 0, (int)m, (int)n, 0};
+      auto r = batched_id(jobs, static_cast<cplx*>(mt), static_cast<cplx*>(t), perm, tol, s);
+      *rank = r[0];
+    } else {
+      *rank = big_row_id(static_cast<cplx*>(mt), m, n, tol, perm, static_cast<cplx*>(t),
+                         (int)std::min<int64_t>(m, n), s);
+    }
+    HBS_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+void hbs_free(hbs_handle* h) { delete h; }
+void hbs_result_free(hbs_result* r) { delete r; }
+const char* hbs_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,287 @@
+// Batched small dense complex FP64 kernels used by the HBS build (Sec. 4):
+// column-pivoted QR for the interpolative decomposition (Def. 3.1) and
+// Gauss-Jordan inversion with partial pivoting for the per-node blocks.
+// One CTA works on one matrix; matrices live in global memory (L2-resident).
+#pragma once
+
+#include "common.cuh"
+
+namespace hbs {
+
+// Descriptor of one matrix of a batch.
+struct CpqrJob {
+  int64_t mt_off;  // offset (in cplx) of Mt (m x n, ld = m)
+  int64_t t_off;   // offset of T output (k x (n - k), ld = k; capacity min(m,n) * n)
+  int64_t perm_off;  // offset of perm output (n ints)
+  int m, n;
+  int job;         // index into the rank output array
+};
+
+struct InvJob {
+  int64_t a_off;   // matrix (n x n, ld = n), inverted in place
+  int64_t piv_off; // int scratch (n)
+  int n;
+  int job;
+};
+
+// Block-wide reduction helpers (NT threads, NT multiple of 32).
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) red[0] = t;
+  }
+  __syncthreads();
+  t = red[0];
+  __syncthreads();
+  return t;
+}
+
+// Returns (max value, lowest index attaining it) over the block.
+template <int NT>
+__device__ __forceinline__ void block_argmax(double v, int idx, double* redv, int* redi, double* outv,
+                                             int* outi) {
+  for (int o = 16; o > 0; o >>= 1) {
+    double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (v2 > v || (v2 == v && i2 < idx)) { v = v2; idx = i2; }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) { redv[warp] = v; redi[warp] = idx; }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < NT / 32 ? redv[threadIdx.x] : -1.0;
+    int ti = threadIdx.x < NT / 32 ? redi[threadIdx.x] : 0x7fffffff;
+    for (int o = 16; o > 0; o >>= 1) {
+      double t2 = __shfl_xor_sync(0xffffffffu, t, o);
+      int i2 = __shfl_xor_sync(0xffffffffu, ti, o);
+      if (t2 > t || (t2 == t && i2 < ti)) { t = t2; ti = i2; }
+    }
+    if (threadIdx.x == 0) { redv[0] = t; redi[0] = ti; }
+  }
+  __syncthreads();
+  *outv = redv[0];
+  *outi = redi[0];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Column-pivoted Householder QR of Mt (m x n) with rank revealed at
+// |R_ss| <= tol |R_00| (the interpolative decomposition of Def. 3.1 applied to
+// the rows of M = Mt^T).  Column norms are downdated after each reflection
+// and recomputed when cancellation has removed more than 7/8 of their digits
+// (relative to the norm at the last recomputation).
+// Dynamic shared memory: 2 n doubles + n ints.
+// ---------------------------------------------------------------------------
+template <int NT>
+__global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, cplx* pool, cplx* tpool, int* permpool,
+                                             int* rank_out, double tol, int kmax) {
+  extern __shared__ double smem[];
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  __shared__ cplx sh_v0;
+  __shared__ double sh_tau;
+
+  const CpqrJob jb = jobs[blockIdx.x];
+  const int m = jb.m, n = jb.n;
+  cplx* A = pool + jb.mt_off;
+  double* nrm = smem;          // current squared norms of the trailing parts
+  double* nrm_ref = smem + n;  // reference norms for the cancellation test
+  int* perm = reinterpret_cast<int*>(smem + 2 * n);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = NT / 32;
+
+  // initial column norms (one warp per column)
+  for (int j = warp; j < n; j += NW) {
+    double s = 0.0;
+    const cplx* col = A + (int64_t)j * m;
+    for (int i = lane; i < m; i += 32) s += cabs2(col[i]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) { nrm[j] = s; nrm_ref[j] = s; }
+  }
+  for (int j = tid; j < n; j += NT) perm[j] = j;
+  __syncthreads();
+
+  const int kcap = min(min(m, n), kmax);
+  double r00 = 0.0;
+  int rank = 0;
+  for (int s = 0; s < kcap; ++s) {
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int j = s + tid; j < n; j += NT) {
+      double v = nrm[j];
+      if (v > best || (v == best && j < bi)) { best = v; bi = j; }
+    }
+    double pv;
+    int p;
+    block_argmax<NT>(best, bi, redv, redi, &pv, &p);
+    if (s == 0) r00 = sqrt(pv);
+    if (!(r00 > 0.0) || sqrt(pv) <= tol * r00) break;
+    // swap columns s and p
+    if (p != s) {
+      cplx* cs = A + (int64_t)s * m;
+      cplx* cp = A + (int64_t)p * m;
+      for (int i = tid; i < m; i += NT) { cplx t = cs[i]; cs[i] = cp[i]; cp[i] = t; }
+      if (tid == 0) {
+        double t = nrm[s]; nrm[s] = nrm[p]; nrm[p] = t;
+        t = nrm_ref[s]; nrm_ref[s] = nrm_ref[p]; nrm_ref[p] = t;
+        int ti = perm[s]; perm[s] = perm[p]; perm[p] = ti;
+      }
+    }
+    __syncthreads();
+    // Householder reflector for x = A[s:m, s]
+    cplx* cs = A + (int64_t)s * m;
+    double sig = 0.0;
+    for (int i = s + 1 + tid; i < m; i += NT) sig += cabs2(cs[i]);
+    sig = block_sum<NT>(sig, redv);
+    if (tid == 0) {
+      cplx x0 = cs[s];
+      double ax0 = cabs1(x0);
+      double xn = sqrt(ax0 * ax0 + sig);
+      cplx ph = ax0 > 0.0 ? cmk(x0.x / ax0, x0.y / ax0) : cmk(1.0, 0.0);
+      cplx beta = cmk(-ph.x * xn, -ph.y * xn);
+      cplx v0 = csub(x0, beta);
+      double vv = cabs2(v0) + sig;
+      sh_v0 = v0;
+      sh_tau = vv > 0.0 ? 2.0 / vv : 0.0;
+      cs[s] = beta;  // R_ss
+    }
+    __syncthreads();
+    const cplx v0 = sh_v0;
+    const double tau = sh_tau;
+    // apply H = I - tau v v^H to columns s+1..n-1 (one warp per column)
+    for (int j = s + 1 + warp; j < n; j += NW) {
+      cplx* cj = A + (int64_t)j * m;
+      cplx w = cmk(0.0, 0.0);
+      for (int i = s + 1 + lane; i < m; i += 32) w = cfma(cconj(cs[i]), cj[i], w);
+      for (int o = 16; o > 0; o >>= 1) {
+        w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
+        w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
+      }
+      w = cfma(cconj(v0), cj[s], w);
+      w = cscale(w, tau);
+      if (lane == 0) cj[s] = csub(cj[s], cmul(v0, w));
+      for (int i = s + 1 + lane; i < m; i += 32) cj[i] = csub(cj[i], cmul(cs[i], w));
+      __syncwarp();
+      // norm downdate, recomputation on cancellation
+      if (lane == 0) {
+        double t = nrm[j] - cabs2(cj[s]);
+        nrm[j] = t;
+      }
+      __syncwarp();
+      if (nrm[j] <= 0.0078125 * nrm_ref[j]) {
+        double t = 0.0;
+        for (int i = s + 1 + lane; i < m; i += 32) t += cabs2(cj[i]);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) { nrm[j] = t; nrm_ref[j] = t; }
+      }
+    }
+    __syncthreads();
+    rank = s + 1;
+  }
+  // T = R11^{-1} R12, one warp per column of R12
+  const int k = rank;
+  cplx* T = tpool + jb.t_off;
+  for (int c = warp; c < n - k; c += NW) {
+    const cplx* r12 = A + (int64_t)(k + c) * m;
+    cplx* tc = T + (int64_t)c * k;
+    for (int i = k - 1; i >= 0; --i) {
+      cplx acc = cmk(0.0, 0.0);
+      for (int l = i + 1 + lane; l < k; l += 32) acc = cfma(A[(int64_t)l * m + i], tc[l], acc);
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (lane == 0) tc[i] = cdiv(csub(r12[i], acc), A[(int64_t)i * m + i]);
+      __syncwarp();
+    }
+  }
+  int* po = permpool + jb.perm_off;
+  for (int j = tid; j < n; j += NT) po[j] = perm[j];
+  if (tid == 0) rank_out[jb.job] = k;
+}
+
+// ---------------------------------------------------------------------------
+// In-place inverse of an n x n matrix by Gauss-Jordan elimination with
+// partial (row) pivoting; column interchanges are undone at the end.
+// rank_out[job] receives 0 on success, or 1 if a zero pivot was met.
+// ---------------------------------------------------------------------------
+template <int NT>
+__global__ void __launch_bounds__(NT) k_gj_inverse(const InvJob* jobs, cplx* pool, int* ipool, int* flag_out) {
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  __shared__ cplx sh_piv;
+  const InvJob jb = jobs[blockIdx.x];
+  const int n = jb.n;
+  cplx* A = pool + jb.a_off;
+  int* piv = ipool + jb.piv_off;
+  const int tid = threadIdx.x;
+  int bad = 0;
+  for (int c = 0; c < n; ++c) {
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = c + tid; i < n; i += NT) {
+      double v = cabs2(A[(int64_t)c * n + i]);
+      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+    }
+    double pv;
+    int p;
+    block_argmax<NT>(best, bi, redv, redi, &pv, &p);
+    if (tid == 0) piv[c] = p;
+    if (!(pv > 0.0)) { bad = 1; p = c; }
+    if (p != c) {
+      for (int j = tid; j < n; j += NT) {
+        cplx t = A[(int64_t)j * n + c];
+        A[(int64_t)j * n + c] = A[(int64_t)j * n + p];
+        A[(int64_t)j * n + p] = t;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      cplx d = A[(int64_t)c * n + c];
+      sh_piv = (cabs2(d) > 0.0) ? cdiv(cmk(1.0, 0.0), d) : cmk(0.0, 0.0);
+    }
+    __syncthreads();
+    const cplx ip = sh_piv;
+    // scale pivot row: A[c, :] *= 1/d, with A[c,c] := 1/d
+    for (int j = tid; j < n; j += NT) {
+      if (j == c) A[(int64_t)c * n + c] = ip;
+      else A[(int64_t)j * n + c] = cmul(A[(int64_t)j * n + c], ip);
+    }
+    __syncthreads();
+    // eliminate: for rows i != c: A[i, j] -= A[i, c] * A[c, j]  (j != c); A[i, c] = -A[i, c] / d
+    for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
+      int i = (int)(e % n), j = (int)(e / n);
+      if (i == c || j == c) continue;
+      A[(int64_t)j * n + i] = csub(A[(int64_t)j * n + i], cmul(A[(int64_t)c * n + i], A[(int64_t)j * n + c]));
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += NT) {
+      if (i != c) A[(int64_t)c * n + i] = cmul(cmk(-A[(int64_t)c * n + i].x, -A[(int64_t)c * n + i].y), ip);
+    }
+    __syncthreads();
+  }
+  // undo the row interchanges as column interchanges, in reverse order
+  for (int c = n - 1; c >= 0; --c) {
+    int p = piv[c];
+    if (p != c) {
+      for (int i = tid; i < n; i += NT) {
+        cplx t = A[(int64_t)c * n + i];
+        A[(int64_t)c * n + i] = A[(int64_t)p * n + i];
+        A[(int64_t)p * n + i] = t;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) flag_out[jb.job] = bad;
+}
+
+}  // namespace hbs

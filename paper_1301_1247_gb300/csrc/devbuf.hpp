@@ -1,0 +1,84 @@
+// Device buffers, status codes and error plumbing shared by the library's host code.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/hbsqp.h"
+
+namespace hbs {
+
+struct Error : public std::runtime_error {
+  hbs_status code;
+  Error(hbs_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+inline void cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(e == cudaErrorMemoryAllocation ? HBS_ERR_OOM : HBS_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+#define HBS_CUDA(call) ::hbs::cuda_check((call), #call)
+#define HBS_LAUNCH_CHECK(name) ::hbs::cuda_check(cudaGetLastError(), name)
+
+// Owning device allocation (cudaMalloc / cudaFree).
+template <typename T>
+class DevBuf {
+ public:
+  DevBuf() = default;
+  explicit DevBuf(size_t n) { alloc(n); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p_(o.p_), n_(o.n_) { o.p_ = nullptr; o.n_ = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p_ = o.p_; n_ = o.n_; o.p_ = nullptr; o.n_ = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t n) {
+    release();
+    if (n == 0) return;
+    void* p = nullptr;
+    HBS_CUDA(cudaMalloc(&p, n * sizeof(T)));
+    p_ = static_cast<T*>(p);
+    n_ = n;
+  }
+  void release() {
+    if (p_) cudaFree(p_);
+    p_ = nullptr;
+    n_ = 0;
+  }
+  T* get() const { return p_; }
+  size_t size() const { return n_; }
+  size_t bytes() const { return n_ * sizeof(T); }
+  void upload(const std::vector<T>& h, cudaStream_t s) {
+    if (h.size() > n_) alloc(h.size());
+    if (!h.empty())
+      HBS_CUDA(cudaMemcpyAsync(p_, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+  std::vector<T> download(cudaStream_t s, size_t count = SIZE_MAX) const {
+    size_t c = count == SIZE_MAX ? n_ : count;
+    std::vector<T> h(c);
+    if (c) {
+      HBS_CUDA(cudaMemcpyAsync(h.data(), p_, c * sizeof(T), cudaMemcpyDeviceToHost, s));
+      HBS_CUDA(cudaStreamSynchronize(s));
+    }
+    return h;
+  }
+
+ private:
+  T* p_ = nullptr;
+  size_t n_ = 0;
+};
+
+void set_last_error(const std::string& msg);
+
+}  // namespace hbs

@@ -1,0 +1,107 @@
+// Internal state of a built solver (opaque hbs_handle) and of a batch result.
+#pragma once
+
+#include <complex>
+#include <vector>
+
+#include "common.cuh"
+#include "devbuf.hpp"
+
+namespace hbs {
+
+// One level of the binary tree (Sec. 4): node-wise index sets I_tau, skeletons,
+// interpolation matrices and the Woodbury factors E, F*, G of Eqs. (def_muE..def_muG).
+struct Level {
+  int l = 0;
+  int first = 0;   // heap index of the first node on this level
+  int count = 0;   // number of nodes (2^l)
+  std::vector<int> n, k;        // |I_tau|, skeleton size |J_tau|
+  std::vector<int64_t> off;     // row offset of node tau in the level's index / vector arrays
+  int64_t ntot = 0;
+  DevBuf<int64_t> idx;          // global boundary indices of I_tau, concatenated
+  DevBuf<int> perm;             // pivot order per node (first k = skeleton positions)
+  std::vector<int64_t> t_off;   // T = R11^{-1} R12 (k x (n - k)) per node
+  DevBuf<cplx> T;
+  std::vector<int64_t> e_off, f_off, g_off, dh_off;
+  DevBuf<cplx> E, F, G, Dhat;   // E: n x k, F: F* (k x n), G: n x n, Dhat: k x k
+  DevBuf<double> cx, cy, rad;   // enclosing circle of the node's original points
+  std::vector<double> h_rad;
+};
+
+// Periodizer blocks on one Sommerfeld contour (Secs. 2.2-2.4).
+struct ContourData {
+  double t0 = 0.0;
+  std::vector<std::complex<double>> k, wk;  // nodes and weights (host)
+  DevBuf<cplx> dk, dwk;
+  // Columns of W = A^{-1} [B_L | B_R] live in the handle's W buffer at col_off.
+  int64_t col_off = 0;
+  // Rows: C_L (2M x N) and C_R (2M x N)
+  DevBuf<cplx> CL, CR;
+  // Wall contributions to the Bragg samples (4 S x 2M for the L and R walls)
+  DevBuf<cplx> SL, SR;
+  // small products: rows [R_-1; R_1; C_L; C_R; E_-1; E_0; E_1] times columns [W_P | W_BL | W_BR]
+  DevBuf<cplx> Zd;  // column-major (zr x zc)
+  int zr = 0, zc = 0;
+};
+
+struct Handle {
+  int64_t N = 0;
+  double d = 1.0, omega = 0.0, tol = 0.0;
+  hbs_options opts{};
+  int L = 0;
+  DevBuf<double> x, y, nx, ny, w;
+  std::vector<double> hx, hy, hnx, hny, hw;  // host copies (for host-side planning only)
+  std::vector<Level> levels;                  // index = level (0 = root)
+  int nroot = 0;
+  DevBuf<cplx> Groot;                         // inverse of the root block
+  int max_rank = 0;
+
+  // neighbour images (Sec. 3.2): A_{+-1} ~ P_nb R_{+-1}
+  int nb_rank = 0;
+  double nb_R = 0.0;
+  int nb_np = 0;
+  DevBuf<int64_t> nb_skel;     // J (l)
+  DevBuf<cplx> Pnb;            // N x l
+  DevBuf<cplx> Rm, Rp;         // A_{-1}(J,:), A_{+1}(J,:)  (l x N)
+
+  // Bragg sampling
+  int S = 0;
+  double y0 = 0.0;
+  DevBuf<cplx> Esamp;          // 3 images x (4 S x N): rows u(+y0), u(-y0), u_y(+y0), u_y(-y0)
+
+  int M = 0;
+  double ch = 0.0, cc = 2.0, cw = 2.0, cK = 0.0;
+  std::vector<ContourData> contours;
+  DevBuf<cplx> W;              // N x (l + 4 M * n_contours)
+  int64_t wcols = 0;
+
+  double build_seconds = 0.0;
+  size_t device_bytes() const;
+  double factor_bytes = 0.0;
+  double apply_flops = 0.0;
+
+  // scratch for applies
+  void apply_inverse(const cplx* b, cplx* x, int64_t nrhs, cudaStream_t s) const;
+};
+
+struct AngleResult {
+  int n_min = 0, n_max = -1;
+  std::vector<std::complex<double>> c, d;
+  double flux_err = 0.0;
+  int n_wood = 0;
+  double t0 = 0.0;
+};
+
+struct Result {
+  std::vector<AngleResult> angles;
+  bool illcond = false;
+};
+
+}  // namespace hbs
+
+struct hbs_handle {
+  hbs::Handle h;
+};
+struct hbs_result {
+  hbs::Result r;
+};

@@ -1,0 +1,612 @@
+// HBS compression and inversion of the isolated-obstacle matrix A (Sec. 4) and the
+// telescoping apply of its compressed inverse.
+//
+// Tree: a balanced binary tree over contiguous index ranges; level l has 2^l nodes,
+// node j of level l owns the boundary nodes [j N / 2^l, (j+1) N / 2^l).  Leaves are
+// at level L with at most `leaf_size` points.
+//
+// Compression (leaf to root).  For each node tau with index set I_tau (all points of a
+// leaf; the union of the children's skeletons above), one joint interpolative
+// decomposition (Def. 3.1) of
+//     [ A(I_tau, near) | proxy sources -> I_tau | A(near, I_tau)^T | I_tau -> proxy field ]
+// picks skeleton rows J_tau and P_tau with A(I_tau, far) ~ P_tau A(J_tau, far) and
+// A(far, I_tau) ~ A(far, J_tau) P_tau^T.  "near" are the active points of the other
+// nodes of the level inside the proxy circle (radius rho r_tau, concentric with the node);
+// everything outside is represented by the proxy points on that circle (the potential
+// theory argument of Sec. 3.2 applied per node).  This gives the block-separable form
+// of Eq. (yy2) with U = P, V* = P^T and off-diagonal skeleton blocks A(J_sigma, J_tau).
+//
+// Inversion (Eqs. woodbury, def_muhD..def_muG), per node:
+//     D_tau = A(I_tau, I_tau)                          (leaf)
+//     D_tau = [[Dhat_a, A(J_a, J_b)], [A(J_b, J_a), Dhat_b]]   (children a, b)
+//     Dhat = (P^T D^{-1} P)^{-1},  E = D^{-1} P Dhat,  F* = Dhat P^T D^{-1},
+//     G = D^{-1} - D^{-1} P Dhat P^T D^{-1},
+// and the root block [[Dhat_a, A(J_a,J_b)], [A(J_b,J_a), Dhat_b]] is inverted densely.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <numeric>
+
+#include "dense_kernels.cuh"
+#include "handle.hpp"
+#include "zgemm.cuh"
+
+namespace hbs {
+
+__global__ void k_geom(const double* dx, const double* dy, double* nx, double* ny, double* w, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double sp = sqrt(dx[i] * dx[i] + dy[i] * dy[i]);
+  nx[i] = dy[i] / sp;
+  ny[i] = -dx[i] / sp;
+  w[i] = (2.0 * HBS_PI / (double)n) * sp;
+}
+
+__device__ __forceinline__ int64_t node_lo(int64_t j, int l, int64_t N) { return (j * N) >> l; }
+
+// Enclosing circle of the original points of each node on level l: centre of the
+// bounding box, radius = largest distance from it.
+__global__ void k_node_circles(const double* x, const double* y, int64_t N, int l, double* cx, double* cy,
+                               double* rad) {
+  __shared__ double red[32];
+  const int64_t j = blockIdx.x;
+  const int64_t lo = node_lo(j, l, N), hi = node_lo(j + 1, l, N);
+  double mnx = 1e300, mxx = -1e300, mny = 1e300, mxy = -1e300;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    mnx = fmin(mnx, x[i]); mxx = fmax(mxx, x[i]);
+    mny = fmin(mny, y[i]); mxy = fmax(mxy, y[i]);
+  }
+  double v[4] = {-mnx, mxx, -mny, mxy};
+  for (int q = 0; q < 4; ++q) {
+    double t = v[q];
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double r = -1e300;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
+      red[31] = r;
+    }
+    __syncthreads();
+    v[q] = red[31];
+  }
+  const double ccx = 0.5 * (v[1] - v[0]), ccy = 0.5 * (v[3] - v[2]);
+  double r2 = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    double ddx = x[i] - ccx, ddy = y[i] - ccy;
+    r2 = fmax(r2, ddx * ddx + ddy * ddy);
+  }
+  for (int o = 16; o > 0; o >>= 1) r2 = fmax(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
+    cx[j] = ccx;
+    cy[j] = ccy;
+    rad[j] = sqrt(r);
+  }
+}
+
+// Near lists: active points of other nodes of the level inside node tau's proxy circle.
+// One block per node scans the level's active points in order, so the list order is
+// deterministic.  With `out` == nullptr only the count is produced.
+__global__ void k_near(const double* x, const double* y, const int64_t* idx, int64_t ntot, const int64_t* off,
+                       const int* nn, const double* cx, const double* cy, const double* rad, double rho,
+                       int64_t* count, const int64_t* out_off, int64_t* out) {
+  __shared__ int wsum[32];
+  __shared__ int64_t base;
+  const int tau = blockIdx.x;
+  const int64_t own_lo = off[tau], own_hi = off[tau] + nn[tau];
+  const double R = rho * rad[tau], R2 = R * R, ccx = cx[tau], ccy = cy[tau];
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t p0 = 0; p0 < ntot; p0 += blockDim.x) {
+    int64_t p = p0 + threadIdx.x;
+    bool f = false;
+    int64_t g = 0;
+    if (p < ntot && (p < own_lo || p >= own_hi)) {
+      g = idx[p];
+      double ddx = x[g] - ccx, ddy = y[g] - ccy;
+      f = ddx * ddx + ddy * ddy < R2;
+    }
+    unsigned b = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wsum[warp] = __popc(b);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) before += wsum[w];
+      total += wsum[w];
+    }
+    if (f && out) out[out_off[tau] + base + before + __popc(b & ((1u << lane) - 1u))] = g;
+    __syncthreads();
+    if (threadIdx.x == 0) base += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) count[tau] = base;
+}
+
+struct YJob {
+  int64_t mt_off;    // into the Y pool
+  int64_t idx_off;   // into level idx
+  int64_t near_off;  // into near list
+  int n, nn, np;
+  double cx, cy, R, wp;
+};
+
+// Fill Mt = Y^T (m x n, m = 2 nn + 3 np): columns are the node's points.
+__global__ void k_fill_y(DevGeom g, const YJob* jobs, const int64_t* idx, const int64_t* near, cplx* pool) {
+  const YJob jb = jobs[blockIdx.y];
+  const int m = 2 * jb.nn + 3 * jb.np;
+  const int64_t tot = (int64_t)m * jb.n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % m), c = (int)(e / m);
+    const int64_t gj = idx[jb.idx_off + c];
+    cplx v;
+    if (r < jb.nn) {
+      v = a_entry(g, near[jb.near_off + r], gj);
+    } else if (r < 2 * jb.nn) {
+      v = a_entry(g, gj, near[jb.near_off + r - jb.nn]);
+    } else {
+      int q = r - 2 * jb.nn;
+      int kind = q / jb.np;
+      int p = q - kind * jb.np;
+      double th = 2.0 * HBS_PI * (double)p / (double)jb.np;
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      double px = jb.cx + jb.R * cs, py = jb.cy + jb.R * sn;
+      if (kind < 2) {
+        cplx gg, dg;
+        proxy_kernels(g.x[gj], g.y[gj], px, py, cs, sn, g.omega, &gg, &dg);
+        v = kind == 0 ? cscale(gg, g.omega * jb.wp) : cscale(dg, jb.wp);
+      } else {
+        v = cscale(combined_kernel(px, py, g.x[gj], g.y[gj], g.nx[gj], g.ny[gj], g.omega), g.w[gj]);
+      }
+    }
+    pool[jb.mt_off + e] = v;
+  }
+}
+
+struct DJob {
+  int64_t d_off;      // into D pool (n x n)
+  int64_t idx_off;    // level idx offset of the node
+  int n, k0;          // node size; first child's skeleton size (0 for leaves)
+  int leaf;
+  const cplx* dh0;    // children's Dhat (k0 x k0, k1 x k1)
+  const cplx* dh1;
+};
+
+__global__ void k_fill_d(DevGeom g, const DJob* jobs, const int64_t* idx, cplx* pool) {
+  const DJob jb = jobs[blockIdx.y];
+  const int n = jb.n;
+  const int64_t tot = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % n), c = (int)(e / n);
+    cplx v;
+    if (jb.leaf) {
+      v = a_entry(g, idx[jb.idx_off + r], idx[jb.idx_off + c]);
+    } else {
+      const int k0 = jb.k0, k1 = n - k0;
+      const bool r0 = r < k0, c0 = c < k0;
+      if (r0 && c0) v = jb.dh0[(int64_t)c * k0 + r];
+      else if (!r0 && !c0) v = jb.dh1[(int64_t)(c - k0) * k1 + (r - k0)];
+      else v = a_entry(g, idx[jb.idx_off + r], idx[jb.idx_off + c]);
+    }
+    pool[jb.d_off + e] = v;
+  }
+}
+
+struct PJob {
+  const cplx* in;   // input matrix
+  cplx* out;
+  const int* perm;  // n entries
+  const cplx* T;    // k x (n - k), ld = k
+  int n, k;
+  int other;        // the other dimension (rows of In for right-P, columns for left-P^T)
+  int ld_in, ld_out;
+};
+
+// out = In * P  (In: other x n, out: other x k):  out[:, i] = In[:, perm[i]] + sum_j T[i, j] In[:, perm[k + j]]
+__global__ void k_right_p(const PJob* jobs) {
+  const PJob jb = jobs[blockIdx.y];
+  const int64_t tot = (int64_t)jb.other * jb.k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % jb.other), i = (int)(e / jb.other);
+    cplx acc = jb.in[(int64_t)jb.perm[i] * jb.ld_in + r];
+    for (int j = 0; j < jb.n - jb.k; ++j)
+      acc = cfma(jb.T[(int64_t)j * jb.k + i], jb.in[(int64_t)jb.perm[jb.k + j] * jb.ld_in + r], acc);
+    jb.out[(int64_t)i * jb.ld_out + r] = acc;
+  }
+}
+
+// out = P^T * In  (In: n x other, out: k x other): out[i, :] = In[perm[i], :] + sum_j T[i, j] In[perm[k+j], :]
+__global__ void k_left_pt(const PJob* jobs) {
+  const PJob jb = jobs[blockIdx.y];
+  const int64_t tot = (int64_t)jb.other * jb.k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % jb.k), c = (int)(e / jb.k);
+    const cplx* col = jb.in + (int64_t)c * jb.ld_in;
+    cplx acc = col[jb.perm[i]];
+    for (int j = 0; j < jb.n - jb.k; ++j) acc = cfma(jb.T[(int64_t)j * jb.k + i], col[jb.perm[jb.k + j]], acc);
+    jb.out[(int64_t)c * jb.ld_out + i] = acc;
+  }
+}
+
+// Parent index sets from the children's skeletons: idx_p = [idx_a(perm_a[0..k_a)), idx_b(perm_b[0..k_b))].
+struct GatherJob {
+  int64_t src_off, dst_off;
+  int k;
+};
+__global__ void k_gather_skel(const GatherJob* jobs, const int64_t* src_idx, const int* src_perm, int64_t* dst_idx) {
+  const GatherJob jb = jobs[blockIdx.y];
+  for (int i = threadIdx.x; i < jb.k; i += blockDim.x)
+    dst_idx[jb.dst_off + i] = src_idx[jb.src_off + src_perm[jb.src_off + i]];
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+
+static void launch_gemms(std::vector<GemmJob>& jobs, cudaStream_t s) {
+  if (jobs.empty()) return;
+  int64_t tiles = gemm_plan(jobs.data(), (int)jobs.size());
+  if (tiles == 0) return;
+  DevBuf<GemmJob> dj(jobs.size());
+  HBS_CUDA(cudaMemcpyAsync(dj.get(), jobs.data(), jobs.size() * sizeof(GemmJob), cudaMemcpyHostToDevice, s));
+  k_zgemm_batched<<<(unsigned)tiles, 256, 0, s>>>(dj.get(), (int)jobs.size());
+  HBS_LAUNCH_CHECK("k_zgemm_batched");
+  HBS_CUDA(cudaStreamSynchronize(s));  // job table is freed on return
+}
+
+void run_gemms(std::vector<GemmJob>& jobs, cudaStream_t s) { launch_gemms(jobs, s); }
+
+template <typename J>
+static DevBuf<J> upload_jobs(const std::vector<J>& v, cudaStream_t s) {
+  DevBuf<J> d(v.size());
+  if (!v.empty())
+    HBS_CUDA(cudaMemcpyAsync(d.get(), v.data(), v.size() * sizeof(J), cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+static inline int grid_for(int64_t tot, int nt, int cap = 4096) {
+  int64_t b = (tot + nt - 1) / nt;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+DevGeom Handle_geom(const Handle& h) {
+  DevGeom g;
+  g.x = h.x.get(); g.y = h.y.get(); g.nx = h.nx.get(); g.ny = h.ny.get(); g.w = h.w.get();
+  g.n = h.N; g.omega = h.omega;
+  return g;
+}
+
+// Batched CPQR-ID of the matrices described by `jobs` (in `pool`).  Returns ranks.
+std::vector<int> batched_id(std::vector<CpqrJob>& jobs, cplx* pool, cplx* tpool, int* permpool, double tol,
+                            cudaStream_t s) {
+  std::vector<int> ranks(jobs.size(), 0);
+  if (jobs.empty()) return ranks;
+  int maxn = 0;
+  for (auto& j : jobs) maxn = std::max(maxn, j.n);
+  DevBuf<CpqrJob> dj = upload_jobs(jobs, s);
+  DevBuf<int> dr(jobs.size());
+  size_t sm = (size_t)maxn * (2 * sizeof(double) + sizeof(int));
+  if (sm > 48 * 1024) HBS_CUDA(cudaFuncSetAttribute(k_cpqr<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_cpqr<256><<<(unsigned)jobs.size(), 256, sm, s>>>(dj.get(), pool, tpool, permpool, dr.get(), tol, 1 << 30);
+  HBS_LAUNCH_CHECK("k_cpqr");
+  ranks = dr.download(s);
+  return ranks;
+}
+
+// Batched in-place inverses; throws on a singular block.
+void batched_inverse(std::vector<InvJob>& jobs, cplx* pool, cudaStream_t s, const char* what) {
+  if (jobs.empty()) return;
+  int64_t piv = 0;
+  for (auto& j : jobs) { j.piv_off = piv; piv += j.n; }
+  DevBuf<int> dpiv(std::max<int64_t>(piv, 1));
+  DevBuf<InvJob> dj = upload_jobs(jobs, s);
+  DevBuf<int> flags(jobs.size());
+  k_gj_inverse<256><<<(unsigned)jobs.size(), 256, 0, s>>>(dj.get(), pool, dpiv.get(), flags.get());
+  HBS_LAUNCH_CHECK("k_gj_inverse");
+  auto f = flags.download(s);
+  for (int v : f)
+    if (v) throw Error(HBS_WARN_ILLCOND, std::string("singular block in ") + what);
+}
+
+void build_hbs(Handle& h, cudaStream_t s) {
+  const int64_t N = h.N;
+  const DevGeom g = Handle_geom(h);
+  const double rho = h.opts.proxy_rho;
+  int L = 0;
+  while ((N >> L) > h.opts.leaf_size || ((N + (1LL << L) - 1) >> L) > h.opts.leaf_size) ++L;
+  if (L < 1) L = 1;
+  h.L = L;
+  h.levels.clear();
+  h.levels.resize(L + 1);
+  h.max_rank = 0;
+  h.factor_bytes = 0.0;
+  h.apply_flops = 0.0;
+
+  for (int l = L; l >= 0; --l) {
+    Level& lv = h.levels[l];
+    lv.l = l;
+    lv.count = 1 << l;
+    lv.first = (1 << l) - 1;
+    lv.n.assign(lv.count, 0);
+    lv.off.assign(lv.count, 0);
+    // ---- index sets
+    if (l == L) {
+      for (int j = 0; j < lv.count; ++j) {
+        int64_t lo = ((int64_t)j * N) >> l, hi = ((int64_t)(j + 1) * N) >> l;
+        lv.n[j] = (int)(hi - lo);
+        lv.off[j] = lo;
+      }
+      lv.ntot = N;
+      std::vector<int64_t> hidx(N);
+      std::iota(hidx.begin(), hidx.end(), 0);
+      lv.idx.upload(hidx, s);
+    } else {
+      Level& ch = h.levels[l + 1];
+      int64_t o = 0;
+      std::vector<GatherJob> gj;
+      for (int j = 0; j < lv.count; ++j) {
+        int a = 2 * j, b = 2 * j + 1;
+        lv.off[j] = o;
+        lv.n[j] = ch.k[a] + ch.k[b];
+        gj.push_back({ch.off[a], o, ch.k[a]});
+        gj.push_back({ch.off[b], o + ch.k[a], ch.k[b]});
+        o += lv.n[j];
+      }
+      lv.ntot = o;
+      lv.idx.alloc(std::max<int64_t>(o, 1));
+      DevBuf<GatherJob> dg = upload_jobs(gj, s);
+      k_gather_skel<<<dim3(1, (unsigned)gj.size()), 128, 0, s>>>(dg.get(), ch.idx.get(), ch.perm.get(), lv.idx.get());
+      HBS_LAUNCH_CHECK("k_gather_skel");
+      HBS_CUDA(cudaStreamSynchronize(s));
+    }
+    DevBuf<int> dn;
+    DevBuf<int64_t> doff;
+    {
+      std::vector<int> nn(lv.n.begin(), lv.n.end());
+      dn.upload(nn, s);
+      doff.upload(lv.off, s);
+    }
+
+    if (l == 0) {
+      // ---- root: dense inverse of [[Dhat_a, A(J_a,J_b)], [A(J_b,J_a), Dhat_b]]
+      Level& ch = h.levels[1];
+      h.nroot = lv.n[0];
+      h.Groot.alloc((size_t)h.nroot * h.nroot);
+      std::vector<DJob> dj(1);
+      dj[0] = {0, 0, h.nroot, ch.k[0], 0, ch.Dhat.get() + ch.dh_off[0], ch.Dhat.get() + ch.dh_off[1]};
+      DevBuf<DJob> ddj = upload_jobs(dj, s);
+      k_fill_d<<<dim3(grid_for((int64_t)h.nroot * h.nroot, 256), 1), 256, 0, s>>>(g, ddj.get(), lv.idx.get(), h.Groot.get());
+      HBS_LAUNCH_CHECK("k_fill_d root");
+      std::vector<InvJob> ij(1);
+      ij[0] = {0, 0, h.nroot, 0};
+      batched_inverse(ij, h.Groot.get(), s, "root block");
+      h.factor_bytes += 16.0 * h.nroot * h.nroot;
+      h.apply_flops += 8.0 * h.nroot * h.nroot;
+      lv.k.assign(1, 0);
+      break;
+    }
+
+    // ---- node circles
+    lv.cx.alloc(lv.count); lv.cy.alloc(lv.count); lv.rad.alloc(lv.count);
+    k_node_circles<<<lv.count, 128, 0, s>>>(h.x.get(), h.y.get(), N, l, lv.cx.get(), lv.cy.get(), lv.rad.get());
+    HBS_LAUNCH_CHECK("k_node_circles");
+    lv.h_rad = lv.rad.download(s);
+    std::vector<double> hcx = lv.cx.download(s), hcy = lv.cy.download(s);
+
+    // ---- near lists
+    DevBuf<int64_t> cnt(lv.count);
+    k_near<<<lv.count, 256, 0, s>>>(h.x.get(), h.y.get(), lv.idx.get(), lv.ntot, doff.get(), dn.get(), lv.cx.get(),
+                                    lv.cy.get(), lv.rad.get(), rho, cnt.get(), nullptr, nullptr);
+    HBS_LAUNCH_CHECK("k_near count");
+    std::vector<int64_t> hc = cnt.download(s);
+    std::vector<int64_t> noff(lv.count, 0);
+    int64_t ntot_near = 0;
+    for (int j = 0; j < lv.count; ++j) { noff[j] = ntot_near; ntot_near += hc[j]; }
+    DevBuf<int64_t> dnoff;
+    dnoff.upload(noff, s);
+    DevBuf<int64_t> near(std::max<int64_t>(ntot_near, 1));
+    k_near<<<lv.count, 256, 0, s>>>(h.x.get(), h.y.get(), lv.idx.get(), lv.ntot, doff.get(), dn.get(), lv.cx.get(),
+                                    lv.cy.get(), lv.rad.get(), rho, cnt.get(), dnoff.get(), near.get());
+    HBS_LAUNCH_CHECK("k_near fill");
+
+    // ---- ID matrices
+    std::vector<YJob> yj(lv.count);
+    int64_t ypool = 0;
+    for (int j = 0; j < lv.count; ++j) {
+      double R = rho * lv.h_rad[j];
+      int np = (int)(2.0 * std::ceil(h.omega * R) + 40.0);
+      np = std::max(np, h.opts.n_proxy_min);
+      np = (np + 7) / 8 * 8;
+      yj[j] = {ypool, lv.off[j], noff[j], lv.n[j], (int)hc[j], np, hcx[j], hcy[j], R, 2.0 * HBS_PI * R / np};
+      ypool += (int64_t)(2 * hc[j] + 3 * np) * lv.n[j];
+    }
+    DevBuf<cplx> Y(std::max<int64_t>(ypool, 1));
+    {
+      DevBuf<YJob> dyj = upload_jobs(yj, s);
+      k_fill_y<<<dim3(64, lv.count), 256, 0, s>>>(g, dyj.get(), lv.idx.get(), near.get(), Y.get());
+      HBS_LAUNCH_CHECK("k_fill_y");
+      std::vector<CpqrJob> cj(lv.count);
+      lv.t_off.assign(lv.count, 0);
+      int64_t tpool = 0;
+      for (int j = 0; j < lv.count; ++j) {
+        int m = 2 * (int)hc[j] + 3 * yj[j].np;
+        cj[j] = {yj[j].mt_off, tpool, lv.off[j], m, lv.n[j], j};
+        lv.t_off[j] = tpool;
+        tpool += (int64_t)std::min(m, lv.n[j]) * lv.n[j];
+      }
+      lv.T.alloc(std::max<int64_t>(tpool, 1));
+      lv.perm.alloc(std::max<int64_t>(lv.ntot, 1));
+      lv.k = batched_id(cj, Y.get(), lv.T.get(), lv.perm.get(), h.tol, s);
+    }
+    Y.release();
+    for (int j = 0; j < lv.count; ++j) h.max_rank = std::max(h.max_rank, lv.k[j]);
+
+    // ---- D blocks and their inverses
+    std::vector<int64_t> d_off(lv.count);
+    int64_t dpool = 0;
+    for (int j = 0; j < lv.count; ++j) { d_off[j] = dpool; dpool += (int64_t)lv.n[j] * lv.n[j]; }
+    DevBuf<cplx> Dinv(std::max<int64_t>(dpool, 1));
+    {
+      std::vector<DJob> dj(lv.count);
+      for (int j = 0; j < lv.count; ++j) {
+        if (l == L) {
+          dj[j] = {d_off[j], lv.off[j], lv.n[j], 0, 1, nullptr, nullptr};
+        } else {
+          Level& ch = h.levels[l + 1];
+          dj[j] = {d_off[j], lv.off[j], lv.n[j], ch.k[2 * j], 0, ch.Dhat.get() + ch.dh_off[2 * j],
+                   ch.Dhat.get() + ch.dh_off[2 * j + 1]};
+        }
+      }
+      DevBuf<DJob> ddj = upload_jobs(dj, s);
+      k_fill_d<<<dim3(64, lv.count), 256, 0, s>>>(g, ddj.get(), lv.idx.get(), Dinv.get());
+      HBS_LAUNCH_CHECK("k_fill_d");
+      std::vector<InvJob> ij(lv.count);
+      for (int j = 0; j < lv.count; ++j) ij[j] = {d_off[j], 0, lv.n[j], j};
+      batched_inverse(ij, Dinv.get(), s, "leaf/level block");
+    }
+    // X = D^{-1} P (n x k), Yt = P^T D^{-1} (k x n), S = P^T X (k x k)
+    lv.e_off.assign(lv.count, 0); lv.f_off.assign(lv.count, 0); lv.g_off.assign(lv.count, 0); lv.dh_off.assign(lv.count, 0);
+    int64_t eo = 0, go = 0, dho = 0;
+    for (int j = 0; j < lv.count; ++j) {
+      lv.e_off[j] = eo; lv.f_off[j] = eo; eo += (int64_t)lv.n[j] * lv.k[j];
+      lv.g_off[j] = go; go += (int64_t)lv.n[j] * lv.n[j];
+      lv.dh_off[j] = dho; dho += (int64_t)lv.k[j] * lv.k[j];
+    }
+    DevBuf<cplx> X(std::max<int64_t>(eo, 1)), Yp(std::max<int64_t>(eo, 1)), S(std::max<int64_t>(dho, 1));
+    {
+      std::vector<PJob> rp(lv.count), lp(lv.count);
+      for (int j = 0; j < lv.count; ++j) {
+        const int n = lv.n[j], k = lv.k[j];
+        const int* pm = lv.perm.get() + lv.off[j];
+        const cplx* T = lv.T.get() + lv.t_off[j];
+        rp[j] = {Dinv.get() + d_off[j], X.get() + lv.e_off[j], pm, T, n, k, n, n, n};
+        lp[j] = {Dinv.get() + d_off[j], Yp.get() + lv.f_off[j], pm, T, n, k, n, n, k};
+      }
+      DevBuf<PJob> drp = upload_jobs(rp, s), dlp = upload_jobs(lp, s);
+      k_right_p<<<dim3(32, lv.count), 256, 0, s>>>(drp.get());
+      HBS_LAUNCH_CHECK("k_right_p");
+      k_left_pt<<<dim3(32, lv.count), 256, 0, s>>>(dlp.get());
+      HBS_LAUNCH_CHECK("k_left_pt");
+      for (int j = 0; j < lv.count; ++j) {
+        const int n = lv.n[j], k = lv.k[j];
+        lp[j] = {X.get() + lv.e_off[j], S.get() + lv.dh_off[j], lv.perm.get() + lv.off[j], lv.T.get() + lv.t_off[j],
+                 n, k, k, n, k};
+      }
+      DevBuf<PJob> dlp2 = upload_jobs(lp, s);
+      k_left_pt<<<dim3(32, lv.count), 256, 0, s>>>(dlp2.get());
+      HBS_LAUNCH_CHECK("k_left_pt S");
+      HBS_CUDA(cudaStreamSynchronize(s));
+    }
+    // Dhat = S^{-1}
+    {
+      std::vector<InvJob> ij;
+      for (int j = 0; j < lv.count; ++j)
+        if (lv.k[j] > 0) ij.push_back({lv.dh_off[j], 0, lv.k[j], j});
+      batched_inverse(ij, S.get(), s, "skeleton block P^T D^-1 P");
+    }
+    lv.Dhat = std::move(S);
+    lv.E.alloc(std::max<int64_t>(eo, 1));
+    lv.F.alloc(std::max<int64_t>(eo, 1));
+    lv.G = std::move(Dinv);
+    lv.g_off = d_off;
+    {
+      std::vector<GemmJob> gj;
+      for (int j = 0; j < lv.count; ++j) {
+        const int n = lv.n[j], k = lv.k[j];
+        if (k == 0) continue;
+        // E = X Dhat  (n x k)
+        gj.push_back({X.get() + lv.e_off[j], lv.Dhat.get() + lv.dh_off[j], lv.E.get() + lv.e_off[j], n, k, k, n, k, n,
+                      cmk(1, 0), cmk(0, 0), 0, 0, 0});
+        // F* = Dhat Yt  (k x n)
+        gj.push_back({lv.Dhat.get() + lv.dh_off[j], Yp.get() + lv.f_off[j], lv.F.get() + lv.f_off[j], k, n, k, k, k, k,
+                      cmk(1, 0), cmk(0, 0), 0, 0, 0});
+      }
+      launch_gemms(gj, s);
+      gj.clear();
+      for (int j = 0; j < lv.count; ++j) {
+        const int n = lv.n[j], k = lv.k[j];
+        if (k == 0) continue;
+        // G = D^{-1} - E Yt
+        gj.push_back({lv.E.get() + lv.e_off[j], Yp.get() + lv.f_off[j], lv.G.get() + lv.g_off[j], n, n, k, n, k, n,
+                      cmk(-1, 0), cmk(1, 0), 0, 0, 0});
+      }
+      launch_gemms(gj, s);
+    }
+    for (int j = 0; j < lv.count; ++j) {
+      const double n = lv.n[j], k = lv.k[j];
+      h.factor_bytes += 16.0 * (2 * n * k + n * n);
+      h.apply_flops += 8.0 * (2 * n * k + n * n);
+    }
+  }
+}
+
+// x = A^{-1} b through the telescoping factorization (Sec. 4): upward b^_tau = F*_tau b_tau,
+// root solve, downward x_tau = E_tau x^_tau + G_tau b_tau.
+void Handle::apply_inverse(const cplx* b, cplx* xout, int64_t nrhs, cudaStream_t s) const {
+  if (nrhs <= 0) return;
+  const int Lv = L;
+  // level vectors: up[l] holds b_tau for all nodes of level l (ntot x nrhs, ld = ntot)
+  std::vector<DevBuf<cplx>> up(Lv + 1), dn(Lv + 1);
+  for (int l = 0; l < Lv; ++l) {
+    up[l].alloc(std::max<int64_t>(levels[l].ntot * nrhs, 1));
+    dn[l].alloc(std::max<int64_t>(levels[l].ntot * nrhs, 1));
+  }
+  auto upptr = [&](int l) -> const cplx* { return l == Lv ? b : up[l].get(); };
+  for (int l = Lv; l >= 1; --l) {
+    const Level& lv = levels[l];
+    const Level& pa = levels[l - 1];
+    std::vector<GemmJob> gj;
+    for (int j = 0; j < lv.count; ++j) {
+      const int n = lv.n[j], k = lv.k[j];
+      if (k == 0) continue;
+      const int parent = j >> 1;
+      const int64_t prow = pa.off[parent] + ((j & 1) ? levels[l].k[j - 1] : 0);
+      gj.push_back({lv.F.get() + lv.f_off[j], upptr(l) + lv.off[j], up[l - 1].get() + prow, k, (int)nrhs, n, k,
+                    (int)lv.ntot, (int)pa.ntot, cmk(1, 0), cmk(0, 0), 0, 0, 0});
+    }
+    run_gemms(gj, s);
+  }
+  {
+    std::vector<GemmJob> gj(1);
+    gj[0] = {Groot.get(), up[0].get(), dn[0].get(), nroot, (int)nrhs, nroot, nroot, nroot, nroot, cmk(1, 0), cmk(0, 0),
+             0, 0, 0};
+    run_gemms(gj, s);
+  }
+  for (int l = 1; l <= Lv; ++l) {
+    const Level& lv = levels[l];
+    const Level& pa = levels[l - 1];
+    cplx* outp = l == Lv ? xout : dn[l].get();
+    std::vector<GemmJob> gj;
+    for (int j = 0; j < lv.count; ++j) {
+      const int n = lv.n[j], k = lv.k[j];
+      const int parent = j >> 1;
+      const int64_t prow = pa.off[parent] + ((j & 1) ? levels[l].k[j - 1] : 0);
+      // x_tau = G b_tau
+      gj.push_back({lv.G.get() + lv.g_off[j], upptr(l) + lv.off[j], outp + lv.off[j], n, (int)nrhs, n, n,
+                    (int)lv.ntot, (int)lv.ntot, cmk(1, 0), cmk(0, 0), 0, 0, 0});
+    }
+    run_gemms(gj, s);
+    gj.clear();
+    for (int j = 0; j < lv.count; ++j) {
+      const int n = lv.n[j], k = lv.k[j];
+      if (k == 0) continue;
+      const int parent = j >> 1;
+      const int64_t prow = pa.off[parent] + ((j & 1) ? levels[l].k[j - 1] : 0);
+      // x_tau += E x^_tau
+      gj.push_back({lv.E.get() + lv.e_off[j], dn[l - 1].get() + prow, outp + lv.off[j], n, (int)nrhs, k, n,
+                    (int)pa.ntot, (int)lv.ntot, cmk(1, 0), cmk(1, 0), 0, 0, 0});
+    }
+    run_gemms(gj, s);
+  }
+}
+
+}  // namespace hbs

@@ -1,0 +1,372 @@
+// Periodizing blocks and neighbour images on the device (Secs. 2.2-2.4, 3.2):
+// Sommerfeld-contour wall potentials B_L, B_R (Eqs. Sh, Dh, B), Fourier wall rows
+// C_L, C_R (operators S^, D^, D*^, T^ and Eq. C with the image reading of Sec. 2.4),
+// Bragg sampling rows (Remarks 2.2, 2.3), the neighbour interpolative decomposition
+// (Sec. 3.2) as a multi-CTA column-pivoted QR over all N boundary points.
+#include "dense_kernels.cuh"
+#include "handle.hpp"
+#include "qp_kernels.cuh"
+
+namespace hbs {
+
+__device__ __forceinline__ cplx sqrt_branch(double omega, cplx k) {
+  // sqrt(omega - k) * sqrt(omega + k), principal roots (cuts on the real axis beyond +-omega)
+  return cmul(csqrt_principal(cmk(omega - k.x, -k.y)), csqrt_principal(cmk(omega + k.x, k.y)));
+}
+
+// B_L and B_R columns (N x 2M each) for one contour, written into W (ld = N) at
+// columns [col_bl, col_bl + 2M) and [col_br, col_br + 2M).  Optionally combined as
+// B_L + alpha B_R into col_bl only (alpha_only != 0).
+__global__ void k_fill_b(DevGeom g, const cplx* k, const cplx* wk, int M, double d, cplx* W, int64_t ldw,
+                         int64_t col_bl, int64_t col_br, int combine, cplx alpha) {
+  const int64_t tot = g.n * (int64_t)M;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % g.n;
+    const int m = (int)(e / g.n);
+    const cplx km = k[m], w = wk[m];
+    const cplx s = sqrt_branch(g.omega, km);
+    const double xi = g.x[i], yi = g.y[i];
+    // e^{i k y} e^{i s |x - x0|} for x0 = -d/2 (L) and x0 = d/2 (R)
+    cplx eky = cexp(cmk(-km.y * yi, km.x * yi));
+    double al = xi + 0.5 * d, ar = 0.5 * d - xi;
+    cplx el = cmul(eky, cexp(cmk(-s.y * al, s.x * al)));
+    cplx er = cmul(eky, cexp(cmk(-s.y * ar, s.x * ar)));
+    cplx is2 = cdiv(cmk(0.0, 0.5), s);  // i / (2 s)
+    cplx sl = cmul(cmul(el, is2), w), dl = cmul(cscale(el, 0.5), w);
+    cplx sr = cmul(cmul(er, is2), w), dr = cmul(cscale(er, -0.5), w);
+    if (combine) {
+      W[(col_bl + m) * ldw + i] = cadd(sl, cmul(alpha, sr));
+      W[(col_bl + M + m) * ldw + i] = cadd(dl, cmul(alpha, dr));
+    } else {
+      W[(col_bl + m) * ldw + i] = sl;
+      W[(col_bl + M + m) * ldw + i] = dl;
+      W[(col_br + m) * ldw + i] = sr;
+      W[(col_br + M + m) * ldw + i] = dr;
+    }
+  }
+}
+
+// Fourier wall rows (2M x N, ld = ldc) for sources shifted by shift_x, wall at x0:
+// f-row = D^ - i w S^, fn-row = T^ - i w D*^, times the source weights.
+__global__ void k_fill_c(DevGeom g, const cplx* k, int M, double shift_x, double x0, cplx* C, int64_t ldc) {
+  const int64_t tot = g.n * (int64_t)M;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e % M);
+    const int64_t j = e / M;
+    const cplx km = k[m];
+    const cplx s = sqrt_branch(g.omega, km);
+    const double sx = g.x[j] + shift_x, sy = g.y[j], nx = g.nx[j], ny = g.ny[j];
+    const double sg = sx - x0 > 0.0 ? 1.0 : -1.0;
+    const double ax = fabs(sx - x0);
+    // base = e^{-i k y} e^{i s |x - x0|} / (4 pi)
+    cplx base = cmul(cexp(cmk(km.y * sy, -km.x * sy)), cexp(cmk(-s.y * ax, s.x * ax)));
+    base = cscale(base, 1.0 / (4.0 * HBS_PI));
+    cplx s_hat = cdiv(cmul(cmk(0.0, 1.0), base), s);
+    cplx kos = cdiv(km, s);
+    cplx d_hat = cmul(base, cadd(cmk(-sg * nx, 0.0), cscale(kos, ny)));
+    cplx dstar_hat = cscale(base, sg);
+    cplx t_hat = cmul(cmul(cmk(0.0, 1.0), base), csub(cscale(s, nx), cscale(km, sg * ny)));
+    const cplx iw = cmk(0.0, g.omega);
+    cplx f = csub(d_hat, cmul(iw, s_hat));
+    cplx fn = csub(t_hat, cmul(iw, dstar_hat));
+    const double w = g.w[j];
+    C[j * ldc + m] = cscale(f, w);
+    C[j * ldc + M + m] = cscale(fn, w);
+  }
+}
+
+// Bragg sampling rows for one image shift: rows (4S) = [u(x_s, +y0) | u(x_s, -y0) |
+// u_y(x_s, +y0) | u_y(x_s, -y0)], columns = boundary nodes; entry = kernel * weight.
+__global__ void k_fill_samples(DevGeom g, int S, double d, double y0, double shift_x, cplx* E, int64_t lde) {
+  const int64_t tot = g.n * (int64_t)(4 * S);
+  const double omega = g.omega;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % (4 * S));
+    const int64_t j = e / (4 * S);
+    const int s = r % S, kind = r / S;  // 0: u(+y0), 1: u(-y0), 2: u_y(+y0), 3: u_y(-y0)
+    const double tx = -0.5 * d + (s + 0.5) * d / S;
+    const double ty = (kind == 0 || kind == 2) ? y0 : -y0;
+    const double sx = g.x[j] + shift_x, sy = g.y[j], nx = g.nx[j], ny = g.ny[j];
+    cplx v;
+    if (kind < 2) {
+      v = combined_kernel(tx, ty, sx, sy, nx, ny, omega);
+    } else {
+      // target y-derivative of dG/dn_y - i w G (see the oracle's derivation):
+      // f' = -(i w/4) H1, f'' = -(i w^2/4)(H0 - H1/(w r)), g = f'/r, g' = (f'' - f'/r)/r
+      double ddx = tx - sx, ddy = ty - sy;
+      double r = sqrt(ddx * ddx + ddy * ddy);
+      double z = omega * r;
+      cplx h0, h1;
+      hankel01(z, &h0, &h1);
+      cplx f1 = cmul(cmk(0.0, -0.25 * omega), h1);
+      cplx f2 = cmul(cmk(0.0, -0.25 * omega * omega), csub(h0, cscale(h1, 1.0 / z)));
+      cplx gg = cscale(f1, 1.0 / r);
+      cplx gp = cscale(csub(f2, cscale(f1, 1.0 / r)), 1.0 / r);
+      double dn = ddx * nx + ddy * ny;
+      cplx t1 = cscale(gp, -(ddy / r) * dn);
+      cplx t2 = cscale(gg, -ny);
+      cplx t3 = cmul(cmk(0.0, -omega * ddy), gg);
+      v = cadd(cadd(t1, t2), t3);
+    }
+    E[j * lde + r] = cscale(v, g.w[j]);
+  }
+}
+
+// Wall-potential contributions to the Bragg samples for one contour:
+// SL, SR (4S x 2M), columns [mu (M) | nu (M)], same row layout as k_fill_samples.
+__global__ void k_fill_wall_samples(const cplx* k, const cplx* wk, int M, int S, double d, double y0, double omega,
+                                    cplx* SL, cplx* SR) {
+  const int64_t tot = (int64_t)(4 * S) * M;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % (4 * S));
+    const int m = (int)(e / (4 * S));
+    const int s = r % S, kind = r / S;
+    const double tx = -0.5 * d + (s + 0.5) * d / S;
+    const double ty = (kind == 0 || kind == 2) ? y0 : -y0;
+    const cplx km = k[m], w = wk[m];
+    const cplx sq = sqrt_branch(omega, km);
+    cplx eky = cexp(cmk(-km.y * ty, km.x * ty));
+    double al = tx + 0.5 * d, ar = 0.5 * d - tx;
+    cplx el = cmul(eky, cexp(cmk(-sq.y * al, sq.x * al)));
+    cplx er = cmul(eky, cexp(cmk(-sq.y * ar, sq.x * ar)));
+    cplx is2 = cdiv(cmk(0.0, 0.5), sq);
+    cplx sl = cmul(el, is2), dl = cscale(el, 0.5);
+    cplx sr = cmul(er, is2), dr = cscale(er, -0.5);
+    if (kind >= 2) {
+      cplx ik = cmk(-km.y, km.x);
+      sl = cmul(ik, sl); dl = cmul(ik, dl); sr = cmul(ik, sr); dr = cmul(ik, dr);
+    }
+    const int64_t ld = 4 * S;
+    SL[(int64_t)m * ld + r] = cmul(sl, w);
+    SL[(int64_t)(M + m) * ld + r] = cmul(dl, w);
+    SR[(int64_t)m * ld + r] = cmul(sr, w);
+    SR[(int64_t)(M + m) * ld + r] = cmul(dr, w);
+  }
+}
+
+// Neighbour interaction matrix, transposed: Mt (m x N, ld = m).  Rows: image -1 near
+// points (A_{-1}(i, near)), image +1 near points, then proxy single- and double-layer
+// sources on the neighbour circle (centre cx, cy; radius R; np points; weight wp).
+__global__ void k_fill_nb(DevGeom g, const int64_t* near_m, int nm, const int64_t* near_p, int npn, double d, double cx,
+                          double cy, double R, int np, double wp, cplx* Mt) {
+  const int m = nm + npn + 2 * np;
+  const int64_t tot = (int64_t)m * g.n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % m);
+    const int64_t i = e / m;
+    cplx v;
+    if (r < nm) {
+      v = a_image_entry(g, i, near_m[r], -d);
+    } else if (r < nm + npn) {
+      v = a_image_entry(g, i, near_p[r - nm], d);
+    } else {
+      int q = r - nm - npn;
+      int kind = q / np, p = q - kind * np;
+      double sn, cs;
+      sincos(2.0 * HBS_PI * (double)p / (double)np, &sn, &cs);
+      cplx gg, dg;
+      proxy_kernels(g.x[i], g.y[i], cx + R * cs, cy + R * sn, cs, sn, g.omega, &gg, &dg);
+      v = kind == 0 ? cscale(gg, g.omega * wp) : cscale(dg, wp);
+    }
+    Mt[i * (int64_t)m + r] = v;
+  }
+}
+
+// Rows J of the image blocks: Rm = A_{-1}(J, :), Rp = A_{+1}(J, :) (l x N, ld = l).
+__global__ void k_fill_r(DevGeom g, const int64_t* J, int l, double d, cplx* Rm, cplx* Rp) {
+  const int64_t tot = (int64_t)l * g.n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % l);
+    const int64_t j = e / l;
+    Rm[e] = a_image_entry(g, J[r], j, -d);
+    Rp[e] = a_image_entry(g, J[r], j, d);
+  }
+}
+
+// P (N x l, ld = N) from the ID: P[perm[i], i] = 1, P[perm[l + j], i] = T[i, j].
+__global__ void k_build_p(const int* perm, const cplx* T, int64_t N, int l, cplx* P) {
+  const int64_t tot = N * (int64_t)l;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / N);
+    const int64_t row = e % N;  // position in pivot order
+    const int64_t g = perm[row];
+    cplx v = row < l ? cmk(row == i ? 1.0 : 0.0, 0.0) : T[(row - l) * (int64_t)l + i];
+    P[(int64_t)i * N + g] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Multi-CTA column-pivoted QR for one large matrix (m x n, n large).  The host runs
+// one step per pivot: k_bq_pivot (one block) picks the pivot, swaps it into place and
+// forms the reflector; k_bq_update (grid over columns) applies it and downdates norms.
+// State lives in BigQrState on the device.
+// ---------------------------------------------------------------------------
+__global__ void k_bq_norms(const cplx* A, int64_t m, int64_t n, double* nrm, double* nref, int* perm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = warp; j < n; j += nwarps) {
+    double s = 0.0;
+    for (int64_t i = lane; i < m; i += 32) s += cabs2(A[j * m + i]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) { nrm[j] = s; nref[j] = s; perm[j] = (int)j; }
+  }
+}
+
+// partial argmax over columns [s, n): per-block result into partial arrays
+__global__ void k_bq_argmax(const double* nrm, int64_t s, int64_t n, const BigQrState* st, double* pv, int* pi) {
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  double best = -1.0;
+  int bi = 0x7fffffff;
+  if (!st->done) {
+    for (int64_t j = s + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+      double v = nrm[j];
+      if (v > best || (v == best && (int)j < bi)) { best = v; bi = (int)j; }
+    }
+  }
+  double v;
+  int i;
+  block_argmax<256>(best, bi, redv, redi, &v, &i);
+  if (threadIdx.x == 0) { pv[blockIdx.x] = v; pi[blockIdx.x] = i; }
+}
+
+__global__ void k_bq_pivot(cplx* A, int64_t m, int64_t s, double* nrm, double* nref, int* perm, const double* pv,
+                           const int* pi, int nparts, BigQrState* st, double tol) {
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  if (st->done) return;
+  double best = -1.0;
+  int bi = 0x7fffffff;
+  for (int q = threadIdx.x; q < nparts; q += blockDim.x) {
+    if (pv[q] > best || (pv[q] == best && pi[q] < bi)) { best = pv[q]; bi = pi[q]; }
+  }
+  double v;
+  int p;
+  block_argmax<256>(best, bi, redv, redi, &v, &p);
+  if (s == 0 && threadIdx.x == 0) st->r00 = sqrt(v);
+  __syncthreads();
+  const double r00 = st->r00;
+  if (!(r00 > 0.0) || sqrt(v) <= tol * r00 || s >= m) {
+    if (threadIdx.x == 0) { st->done = 1; st->rank = (int)s; }
+    return;
+  }
+  if (p != s) {
+    cplx* cs = A + s * m;
+    cplx* cp = A + (int64_t)p * m;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) { cplx t = cs[i]; cs[i] = cp[i]; cp[i] = t; }
+    if (threadIdx.x == 0) {
+      double t = nrm[s]; nrm[s] = nrm[p]; nrm[p] = t;
+      t = nref[s]; nref[s] = nref[p]; nref[p] = t;
+      int ti = perm[s]; perm[s] = perm[p]; perm[p] = ti;
+    }
+  }
+  __syncthreads();
+  cplx* cs = A + s * m;
+  double sig = 0.0;
+  for (int64_t i = s + 1 + threadIdx.x; i < m; i += blockDim.x) sig += cabs2(cs[i]);
+  sig = block_sum<256>(sig, redv);
+  if (threadIdx.x == 0) {
+    cplx x0 = cs[s];
+    double ax0 = cabs1(x0);
+    double xn = sqrt(ax0 * ax0 + sig);
+    cplx ph = ax0 > 0.0 ? cmk(x0.x / ax0, x0.y / ax0) : cmk(1.0, 0.0);
+    cplx beta = cmk(-ph.x * xn, -ph.y * xn);
+    cplx v0 = csub(x0, beta);
+    double vv = cabs2(v0) + sig;
+    st->v0 = v0;
+    st->tau = vv > 0.0 ? 2.0 / vv : 0.0;
+    cs[s] = beta;
+    st->rank = (int)(s + 1);
+  }
+}
+
+__global__ void k_bq_update(cplx* A, int64_t m, int64_t n, int64_t s, double* nrm, double* nref, const BigQrState* st) {
+  if (st->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const cplx v0 = st->v0;
+  const double tau = st->tau;
+  const cplx* cs = A + s * m;
+  for (int64_t j = s + 1 + warp; j < n; j += nwarps) {
+    cplx* cj = A + j * m;
+    cplx w = cmk(0.0, 0.0);
+    for (int64_t i = s + 1 + lane; i < m; i += 32) w = cfma(cconj(cs[i]), cj[i], w);
+    for (int o = 16; o > 0; o >>= 1) {
+      w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
+      w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
+    }
+    w = cfma(cconj(v0), cj[s], w);
+    w = cscale(w, tau);
+    cplx top = csub(cj[s], cmul(v0, w));
+    for (int64_t i = s + 1 + lane; i < m; i += 32) cj[i] = csub(cj[i], cmul(cs[i], w));
+    double t = nrm[j] - cabs2(top);
+    if (t <= 0.0078125 * nref[j]) {
+      double q = 0.0;
+      for (int64_t i = s + 1 + lane; i < m; i += 32) q += cabs2(cj[i]);
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      t = q;
+      if (lane == 0) nref[j] = q;
+    }
+    if (lane == 0) { cj[s] = top; nrm[j] = t; }
+  }
+}
+
+// T = R11^{-1} R12 for the big QR: one warp per column of R12.
+__global__ void k_bq_tsolve(const cplx* A, int64_t m, int64_t n, int k, cplx* T) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp; c < n - k; c += nwarps) {
+    const cplx* r12 = A + (k + c) * m;
+    cplx* tc = T + c * (int64_t)k;
+    for (int i = k - 1; i >= 0; --i) {
+      cplx acc = cmk(0.0, 0.0);
+      for (int l = i + 1 + lane; l < k; l += 32) acc = cfma(A[(int64_t)l * m + i], tc[l], acc);
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (lane == 0) tc[i] = cdiv(csub(r12[i], acc), A[(int64_t)i * m + i]);
+      __syncwarp();
+    }
+  }
+}
+
+int big_row_id(cplx* Mt, int64_t m, int64_t n, double tol, int* perm, cplx* T, int max_rank, cudaStream_t s) {
+  DevBuf<double> nrm(n), nref(n);
+  DevBuf<BigQrState> st(1);
+  HBS_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(BigQrState), s));
+  const int nparts = 296;
+  DevBuf<double> pv(nparts);
+  DevBuf<int> pi(nparts);
+  k_bq_norms<<<1184, 256, 0, s>>>(Mt, m, n, nrm.get(), nref.get(), perm);
+  HBS_LAUNCH_CHECK("k_bq_norms");
+  const int64_t kcap = std::min<int64_t>(std::min<int64_t>(m, n), max_rank);
+  BigQrState hs{};
+  for (int64_t step = 0; step < kcap; ++step) {
+    k_bq_argmax<<<nparts, 256, 0, s>>>(nrm.get(), step, n, st.get(), pv.get(), pi.get());
+    k_bq_pivot<<<1, 256, 0, s>>>(Mt, m, step, nrm.get(), nref.get(), perm, pv.get(), pi.get(), nparts, st.get(), tol);
+    k_bq_update<<<1184, 256, 0, s>>>(Mt, m, n, step, nrm.get(), nref.get(), st.get());
+    if ((step & 15) == 15) {
+      HBS_LAUNCH_CHECK("big qr step");
+      HBS_CUDA(cudaMemcpyAsync(&hs, st.get(), sizeof(BigQrState), cudaMemcpyDeviceToHost, s));
+      HBS_CUDA(cudaStreamSynchronize(s));
+      if (hs.done) break;
+    }
+  }
+  HBS_LAUNCH_CHECK("big qr");
+  HBS_CUDA(cudaMemcpyAsync(&hs, st.get(), sizeof(BigQrState), cudaMemcpyDeviceToHost, s));
+  HBS_CUDA(cudaStreamSynchronize(s));
+  const int k = hs.rank;
+  if (!hs.done && k >= max_rank && k < std::min<int64_t>(m, n))
+    throw Error(HBS_ERR_RANK, "neighbour interaction rank exceeds the supported maximum");
+  if (k > 0 && n > k) {
+    k_bq_tsolve<<<1184, 256, 0, s>>>(Mt, m, n, k, T);
+    HBS_LAUNCH_CHECK("k_bq_tsolve");
+  }
+  return k;
+}
+
+}  // namespace hbs

@@ -1,0 +1,52 @@
+// Declarations shared between the library's translation units.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+#include "handle.hpp"
+#include "zgemm.cuh"
+
+namespace hbs {
+
+struct BigQrState {
+  int done;
+  int rank;
+  double r00;
+  cplx v0;
+  double tau;
+};
+
+// hbs_build.cu
+void build_hbs(Handle& h, cudaStream_t s);
+DevGeom Handle_geom(const Handle& h);
+void run_gemms(std::vector<GemmJob>& jobs, cudaStream_t s);
+std::vector<int> batched_id(std::vector<CpqrJob>& jobs, cplx* pool, cplx* tpool, int* permpool, double tol,
+                            cudaStream_t s);
+__global__ void k_geom(const double* dx, const double* dy, double* nx, double* ny, double* w, int64_t n);
+
+// qp_kernels.cu
+__global__ void k_fill_b(DevGeom g, const cplx* k, const cplx* wk, int M, double d, cplx* W, int64_t ldw,
+                         int64_t col_bl, int64_t col_br, int combine, cplx alpha);
+__global__ void k_fill_c(DevGeom g, const cplx* k, int M, double shift_x, double x0, cplx* C, int64_t ldc);
+__global__ void k_fill_samples(DevGeom g, int S, double d, double y0, double shift_x, cplx* E, int64_t lde);
+__global__ void k_fill_wall_samples(const cplx* k, const cplx* wk, int M, int S, double d, double y0, double omega,
+                                    cplx* SL, cplx* SR);
+__global__ void k_fill_nb(DevGeom g, const int64_t* near_m, int nm, const int64_t* near_p, int npn, double d,
+                          double cx, double cy, double R, int np, double wp, cplx* Mt);
+__global__ void k_fill_r(DevGeom g, const int64_t* J, int l, double d, cplx* Rm, cplx* Rp);
+__global__ void k_build_p(const int* perm, const cplx* T, int64_t N, int l, cplx* P);
+int big_row_id(cplx* Mt, int64_t m, int64_t n, double tol, int* perm, cplx* T, int max_rank, cudaStream_t s);
+
+// qp_solve.cu
+void build_periodizer(Handle& h, cudaStream_t s);
+void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, Result& out, cudaStream_t s);
+
+inline int grid_1d(int64_t tot, int nt = 256, int cap = 8192) {
+  int64_t b = (tot + nt - 1) / nt;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+}  // namespace hbs

@@ -1,0 +1,849 @@
+// Periodizer precompute and the per-Bloch-phase block solve (Secs. 2.2-2.4, 3).
+//
+// With the neighbour factors A_{+-1} ~ P R_{+-1} (Sec. 3.2), Eq. (block2) becomes the
+// extended system
+//     [ A   L   B   PW ] [eta ]   [b]        L = [alpha^{-1} P | alpha P],  R = [R_{-1}; R_1]
+//     [ R  -I   0   0  ] [zeta] = [0]        B = B_L + alpha B_R
+//     [ C~  0   Q   0  ] [xi  ]   [0]        C~ = alpha C_L - alpha^{-2} C_R  (P = 1)
+//     [ Wr  0   Wx  Wa ] [a   ]   [0]        Wood's rows/columns (Sec. 2.4)
+// Eliminating eta = A^{-1}(b - L zeta - B xi - PW a) leaves a Schur system in
+// (zeta, xi, a) of size 2l + 2M + n_wood (Eqs. blocksolve and inv).  Every product it
+// needs is "a row functional of A^{-1} times a column": rows R, C_L, C_R and the Bragg
+// sampling rows E; columns P, B_L, B_R (angle independent, applied once at build:
+// W = A^{-1}[P | B_L | B_R], Z = Rows W) and the right-hand sides b, PW (per Bloch phase:
+// X = A^{-1}[b | PW], Proj = Rows X).  The plain path applies A^{-1} to L and B(alpha)
+// for every Bloch phase instead, q + 2M + 2l applies (Remark 3.2).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <map>
+
+#include "dense_kernels.cuh"
+#include "qp_kernels.cuh"
+
+namespace hbs {
+
+using zc = std::complex<double>;
+
+static inline cplx to_c(zc v) { return cmk(v.real(), v.imag()); }
+
+// ---------------------------------------------------------------------------
+// Periodizer precompute
+// ---------------------------------------------------------------------------
+
+static void contour_nodes(ContourData& c, int M, double h, double cc, double cw, double t0) {
+  c.t0 = t0;
+  c.k.resize(M);
+  c.wk.resize(M);
+  for (int m = 0; m < M; ++m) {
+    double t = t0 + (m - 0.5 * (M - 1)) * h;
+    double u = (t - t0) / cw;
+    double ch = std::cosh(u);
+    c.k[m] = zc(t, -cc * std::tanh(u));
+    c.wk[m] = zc(h, -h * (cc / cw) / (ch * ch));
+  }
+  std::vector<cplx> kk(M), ww(M);
+  for (int m = 0; m < M; ++m) { kk[m] = to_c(c.k[m]); ww[m] = to_c(c.wk[m]); }
+  c.dk.upload(kk, 0);
+  c.dwk.upload(ww, 0);
+}
+
+// Pole-free crossing point for angles at or near a Wood's anomaly: half the smallest
+// positive k_n that occurs at an exact anomaly, k = sqrt(w^2 - (w - 2 pi j / d)^2).
+static double auto_wood_shift(double omega, double d) {
+  double best = 1e300;
+  for (int j = 1; 2.0 * M_PI * j / d < 2.0 * omega; ++j) {
+    double kap = omega - 2.0 * M_PI * j / d;
+    double v = omega * omega - kap * kap;
+    if (v > 1e-12) best = std::min(best, std::sqrt(v));
+  }
+  if (best > 1e299) best = omega;
+  return 0.5 * best;
+}
+
+void build_periodizer(Handle& h, cudaStream_t s) {
+  const int64_t N = h.N;
+  const DevGeom g = Handle_geom(h);
+  const double d = h.d, omega = h.omega;
+
+  // ---- geometry extents (host planning)
+  double cx = 0, cy = 0;
+  {
+    double mnx = 1e300, mxx = -1e300, mny = 1e300, mxy = -1e300;
+    for (int64_t i = 0; i < N; ++i) {
+      mnx = std::min(mnx, h.hx[i]); mxx = std::max(mxx, h.hx[i]);
+      mny = std::min(mny, h.hy[i]); mxy = std::max(mxy, h.hy[i]);
+    }
+    cx = 0.5 * (mnx + mxx);
+    cy = 0.5 * (mny + mxy);
+  }
+  double rmax = 0.0, ymax = 0.0, xmax = 0.0;
+  for (int64_t i = 0; i < N; ++i) {
+    rmax = std::max(rmax, std::hypot(h.hx[i] - cx, h.hy[i] - cy));
+    ymax = std::max(ymax, std::fabs(h.hy[i]));
+    xmax = std::max(xmax, std::fabs(h.hx[i]));
+  }
+  double rsrc = 1e300;
+  for (int64_t i = 0; i < N; ++i) {
+    rsrc = std::min(rsrc, std::hypot(h.hx[i] - d - cx, h.hy[i] - cy));
+    rsrc = std::min(rsrc, std::hypot(h.hx[i] + d - cx, h.hy[i] - cy));
+  }
+
+  // ---- neighbour proxy circle and near points (Sec. 3.2)
+  double R = h.opts.nb_radius;
+  if (!(R > 0.0)) R = rsrc > 1.05 * rmax ? 0.5 * (rmax + rsrc) : 1.1 * rmax;
+  std::vector<int64_t> near_m, near_p;
+  double rfar = 1e300;
+  for (int64_t i = 0; i < N; ++i) {
+    double dm = std::hypot(h.hx[i] - d - cx, h.hy[i] - cy);
+    double dp = std::hypot(h.hx[i] + d - cx, h.hy[i] - cy);
+    if (dm < R) near_m.push_back(i); else rfar = std::min(rfar, dm);
+    if (dp < R) near_p.push_back(i); else rfar = std::min(rfar, dp);
+  }
+  int np = h.opts.nb_proxies;
+  if (np <= 0) {
+    double q = std::max(rmax / R, R / rfar);
+    q = std::min(q, 0.97);
+    np = (int)(2.0 * (std::ceil(omega * R) + std::ceil(std::log(1e-16) / std::log(q))));
+    np = std::max(64, std::min(np, 2048));
+    np = (np + 7) / 8 * 8;
+  }
+  const double wp = 2.0 * M_PI * R / np;
+  h.nb_R = R;
+  h.nb_np = np;
+  {
+    const int nm = (int)near_m.size(), npn = (int)near_p.size();
+    const int64_t m = nm + npn + 2 * np;
+    DevBuf<int64_t> dnm, dnp;
+    dnm.upload(near_m, s);
+    dnp.upload(near_p, s);
+    DevBuf<cplx> Mt(m * N);
+    k_fill_nb<<<grid_1d(m * N), 256, 0, s>>>(g, dnm.get(), nm, dnp.get(), npn, d, cx, cy, R, np, wp, Mt.get());
+    HBS_LAUNCH_CHECK("k_fill_nb");
+    DevBuf<int> perm(N);
+    const int kcap = (int)std::min<int64_t>(m, 4096);
+    DevBuf<cplx> T((size_t)kcap * N);
+    int l = big_row_id(Mt.get(), m, N, h.tol, perm.get(), T.get(), kcap, s);
+    h.nb_rank = l;
+    std::vector<int> hperm = perm.download(s, l);
+    std::vector<int64_t> J(hperm.begin(), hperm.end());
+    h.nb_skel.upload(J, s);
+    h.Rm.alloc(std::max<int64_t>((int64_t)l * N, 1));
+    h.Rp.alloc(std::max<int64_t>((int64_t)l * N, 1));
+    if (l > 0) {
+      k_fill_r<<<grid_1d((int64_t)l * N), 256, 0, s>>>(g, h.nb_skel.get(), l, d, h.Rm.get(), h.Rp.get());
+      HBS_LAUNCH_CHECK("k_fill_r");
+    }
+    h.Pnb.alloc(std::max<int64_t>((int64_t)l * N, 1));
+    if (l > 0) {
+      k_build_p<<<grid_1d((int64_t)l * N), 256, 0, s>>>(perm.get(), T.get(), N, l, h.Pnb.get());
+      HBS_LAUNCH_CHECK("k_build_p");
+    }
+    HBS_CUDA(cudaStreamSynchronize(s));
+  }
+  const int l = h.nb_rank;
+
+  // ---- Sommerfeld contours (Sec. 2.3)
+  h.cc = h.opts.contour_c > 0 ? h.opts.contour_c : 2.0;
+  h.cw = h.opts.contour_w > 0 ? h.opts.contour_w : 2.0;
+  h.ch = h.opts.contour_h > 0 ? h.opts.contour_h : 0.4;
+  double shift = h.opts.wood_shift;
+  if (shift == 0.0) shift = auto_wood_shift(omega, d);
+  {
+    const double dB = 0.5 * d - xmax, dC = 1.5 * d - xmax;
+    const double smin = 37.0 / (dB + dC);
+    double K = h.opts.contour_k > 0 ? h.opts.contour_k : std::sqrt(omega * omega + smin * smin) + 2.0 * h.cw;
+    if (shift > 0) K += shift;
+    h.cK = K;
+  }
+  h.M = h.opts.m > 0 ? h.opts.m : (int)std::ceil(2.0 * h.cK / h.ch);
+  const int M = h.M;
+  const int nc = shift > 0 ? 2 : 1;
+  h.contours.clear();
+  h.contours.resize(nc);
+  for (int c = 0; c < nc; ++c) contour_nodes(h.contours[c], M, h.ch, h.cc, h.cw, c == 0 ? 0.0 : shift);
+
+  // ---- Bragg sampling rows (Remarks 2.2, 2.3)
+  h.S = h.opts.n_bragg_samples > 0 ? h.opts.n_bragg_samples
+                                   : std::max(32, 2 * (int)std::ceil(omega * d / (2.0 * M_PI)) + 44);
+  h.y0 = h.opts.y0 > 0 ? h.opts.y0 : ymax + 0.25 * d;
+  const int S = h.S;
+  h.Esamp.alloc((size_t)12 * S * N);
+  for (int jj = 0; jj < 3; ++jj) {
+    k_fill_samples<<<grid_1d((int64_t)4 * S * N), 256, 0, s>>>(g, S, d, h.y0, (jj - 1) * d, h.Esamp.get() + 4 * S * jj,
+                                                                 12 * S);
+    HBS_LAUNCH_CHECK("k_fill_samples");
+  }
+
+  // ---- W = A^{-1} [P | B_L^c | B_R^c ...]
+  h.wcols = l + (int64_t)4 * M * nc;
+  h.W.alloc((size_t)N * h.wcols);
+  if (l > 0) HBS_CUDA(cudaMemcpyAsync(h.W.get(), h.Pnb.get(), sizeof(cplx) * N * l, cudaMemcpyDeviceToDevice, s));
+  for (int c = 0; c < nc; ++c) {
+    ContourData& cd = h.contours[c];
+    cd.col_off = l + (int64_t)4 * M * c;
+    k_fill_b<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), cd.dwk.get(), M, d, h.W.get(), N, cd.col_off,
+                                                      cd.col_off + 2 * M, 0, cmk(0, 0));
+    HBS_LAUNCH_CHECK("k_fill_b");
+    cd.CL.alloc((size_t)2 * M * N);
+    cd.CR.alloc((size_t)2 * M * N);
+    k_fill_c<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), M, d, -0.5 * d, cd.CL.get(), 2 * M);
+    k_fill_c<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), M, -d, 0.5 * d, cd.CR.get(), 2 * M);
+    HBS_LAUNCH_CHECK("k_fill_c");
+    cd.SL.alloc((size_t)4 * S * 2 * M);
+    cd.SR.alloc((size_t)4 * S * 2 * M);
+    k_fill_wall_samples<<<grid_1d((int64_t)4 * S * M), 256, 0, s>>>(cd.dk.get(), cd.dwk.get(), M, S, d, h.y0, omega,
+                                                                     cd.SL.get(), cd.SR.get());
+    HBS_LAUNCH_CHECK("k_fill_wall_samples");
+  }
+  {
+    const int64_t chunk = 256;
+    DevBuf<cplx> tmp((size_t)N * chunk);
+    for (int64_t c0 = 0; c0 < h.wcols; c0 += chunk) {
+      int64_t nq = std::min(chunk, h.wcols - c0);
+      HBS_CUDA(cudaMemcpyAsync(tmp.get(), h.W.get() + c0 * N, sizeof(cplx) * N * nq, cudaMemcpyDeviceToDevice, s));
+      h.apply_inverse(tmp.get(), h.W.get() + c0 * N, nq, s);
+    }
+  }
+  // ---- Z_c = Rows_c W_c
+  const int zr = 2 * l + 4 * M + 12 * S, zcn = l + 4 * M;
+  for (int c = 0; c < nc; ++c) {
+    ContourData& cd = h.contours[c];
+    cd.zr = zr;
+    cd.zc = zcn;
+    cd.Zd.alloc((size_t)zr * zcn);
+    std::vector<GemmJob> gj;
+    struct Blk { const cplx* A; int rows; int lda; int row0; };
+    Blk rows[5] = {{h.Rm.get(), l, l, 0}, {h.Rp.get(), l, l, l}, {cd.CL.get(), 2 * M, 2 * M, 2 * l},
+                   {cd.CR.get(), 2 * M, 2 * M, 2 * l + 2 * M}, {h.Esamp.get(), 12 * S, 12 * S, 2 * l + 4 * M}};
+    struct CBlk { const cplx* B; int cols; int col0; };
+    CBlk cols[2] = {{h.W.get(), l, 0}, {h.W.get() + cd.col_off * N, 4 * M, l}};
+    for (auto& rb : rows)
+      for (auto& cbk : cols) {
+        if (rb.rows == 0 || cbk.cols == 0) continue;
+        gj.push_back({rb.A, cbk.B, cd.Zd.get() + (int64_t)cbk.col0 * zr + rb.row0, rb.rows, cbk.cols, (int)N, rb.lda,
+                      (int)N, zr, cmk(1, 0), cmk(0, 0), 0, 0, 0});
+      }
+    run_gemms(gj, s);
+  }
+  HBS_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------------------
+// Per-Bloch-phase solve
+// ---------------------------------------------------------------------------
+
+struct GroupJob {
+  cplx alpha;
+  int q, nw;                 // angles, Wood's modes
+  int rhs_col;               // first column of this group in X / Proj (b's then PW)
+  int contour;               // 0 standard, 1 shifted
+  const cplx* zp;            // fast path: Z (zr x zc) of the contour
+  const cplx* zl;            // plain path: Rows A^{-1} L (zr x 2l), else null
+  const cplx* zb;            // plain path: Rows A^{-1} B(alpha) (zr x 2M), else null
+  const cplx* sl;            // wall sample rows SL, SR (4S x 2M)
+  const cplx* sr;
+  const cplx* ck;            // contour nodes (M)
+  double wkap[4];            // kappa_n of Wood's modes
+  cplx wkn[4];               // k_n of Wood's modes
+  int64_t s_off, r_off;      // offsets of S (nS x nS) and rhs (nS x q) in the pools
+  int64_t piv_off;
+};
+
+struct Dims {
+  int l, M, S, zr;
+  double d, omega;
+  int64_t ldproj;  // leading dimension of Proj (= zr)
+};
+
+// Value of (Rows A^{-1} [column C of the Schur unknowns]) at Rows row r.
+__device__ __forceinline__ cplx rows_ainv(const Dims& D, const GroupJob& G, const cplx* proj, int r, int C) {
+  const int l = D.l, M = D.M, zr = D.zr;
+  if (C < 2 * l) {
+    if (G.zl) return G.zl[(int64_t)C * zr + r];
+    const int c = C < l ? C : C - l;
+    cplx v = G.zp[(int64_t)c * zr + r];
+    cplx f = C < l ? cdiv(cmk(1, 0), G.alpha) : G.alpha;
+    return cmul(f, v);
+  }
+  if (C < 2 * l + 2 * M) {
+    const int c = C - 2 * l;
+    if (G.zb) return G.zb[(int64_t)c * zr + r];
+    cplx v = G.zp[(int64_t)(l + c) * zr + r];
+    cplx w = G.zp[(int64_t)(l + 2 * M + c) * zr + r];
+    return cfma(G.alpha, w, v);
+  }
+  const int t = C - 2 * l - 2 * M;
+  return proj[(int64_t)(G.rhs_col + G.q + t) * D.ldproj + r];
+}
+
+// Sampling-row weight psi for Wood's row t at sample row s in [0, 4S): i k_n F_n on
+// u(-y0), F_n on u_y(-y0), F_n = e^{-i kappa_n x_s} / S.
+__device__ __forceinline__ cplx wood_psi(const Dims& D, const GroupJob& G, int t, int s) {
+  const int S = D.S;
+  const int kind = s / S, ss = s % S;
+  if (kind != 1 && kind != 3) return cmk(0, 0);
+  const double xs = -0.5 * D.d + (ss + 0.5) * D.d / S;
+  double sn, cs;
+  sincos(-G.wkap[t] * xs, &sn, &cs);
+  cplx f = cmk(cs / S, sn / S);
+  if (kind == 3) return f;
+  return cmul(cmul(cmk(0, 1), G.wkn[t]), f);
+}
+
+// Schur row functional applied to (Rows A^{-1} column C): row block zeta, xi or Wood's.
+__device__ cplx row_functional(const Dims& D, const GroupJob& G, const cplx* proj, int Rw, int C) {
+  const int l = D.l, M = D.M, S = D.S;
+  if (Rw < 2 * l) return rows_ainv(D, G, proj, Rw, C);
+  if (Rw < 2 * l + 2 * M) {
+    const int r = Rw - 2 * l;
+    cplx a = rows_ainv(D, G, proj, 2 * l + r, C);
+    cplx b = rows_ainv(D, G, proj, 2 * l + 2 * M + r, C);
+    cplx a2 = cmul(G.alpha, G.alpha);
+    return csub(cmul(G.alpha, a), cdiv(b, a2));
+  }
+  const int t = Rw - 2 * l - 2 * M;
+  cplx acc = cmk(0, 0);
+  cplx aj = cdiv(cmk(1, 0), G.alpha);
+  for (int jj = 0; jj < 3; ++jj) {
+    cplx part = cmk(0, 0);
+    for (int sidx = S; sidx < 4 * S; ++sidx) {
+      cplx p = wood_psi(D, G, t, sidx);
+      if (p.x == 0.0 && p.y == 0.0) continue;
+      part = cfma(p, rows_ainv(D, G, proj, 2 * l + 4 * M + 4 * S * jj + sidx, C), part);
+    }
+    acc = cfma(aj, part, acc);
+    aj = cmul(aj, G.alpha);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ cplx plane_wave_at(double kap, cplx kn, double x, double y, bool dy) {
+  // e^{i kappa x} e^{i k y}, k complex
+  cplx e = cexp(cmk(-kn.y * y, kap * x + kn.x * y));
+  if (dy) e = cmul(cmul(cmk(0, 1), kn), e);
+  return e;
+}
+
+__device__ __forceinline__ cplx sample_point_pw(const Dims& D, const GroupJob& G, int t, int r, double y0) {
+  const int S = D.S;
+  const int kind = r / S, ss = r % S;
+  const double xs = -0.5 * D.d + (ss + 0.5) * D.d / S;
+  const double ys = (kind == 0 || kind == 2) ? y0 : -y0;
+  return plane_wave_at(G.wkap[t], G.wkn[t], xs, ys, kind >= 2);
+}
+
+// Assemble S (nS x nS) and the right-hand sides (nS x q) of every group.
+__global__ void k_assemble(Dims D, const GroupJob* groups, const cplx* proj, double y0, cplx* Spool, cplx* Rpool) {
+  const GroupJob G = groups[blockIdx.y];
+  const int l = D.l, M = D.M, S = D.S;
+  const int nS = 2 * l + 2 * M + G.nw;
+  const int64_t tot = (int64_t)nS * (nS + G.q);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int Rw = (int)(e % nS);
+    const int C = (int)(e / nS);
+    if (C >= nS) {
+      // right-hand side: -(row functional of Rows X_b)
+      const int i = C - nS;
+      cplx v;
+      if (Rw < 2 * l) {
+        v = proj[(int64_t)(G.rhs_col + i) * D.ldproj + Rw];
+      } else if (Rw < 2 * l + 2 * M) {
+        const int r = Rw - 2 * l;
+        cplx a = proj[(int64_t)(G.rhs_col + i) * D.ldproj + 2 * l + r];
+        cplx b = proj[(int64_t)(G.rhs_col + i) * D.ldproj + 2 * l + 2 * M + r];
+        v = csub(cmul(G.alpha, a), cdiv(b, cmul(G.alpha, G.alpha)));
+      } else {
+        const int t = Rw - 2 * l - 2 * M;
+        v = cmk(0, 0);
+        cplx aj = cdiv(cmk(1, 0), G.alpha);
+        for (int jj = 0; jj < 3; ++jj) {
+          cplx part = cmk(0, 0);
+          for (int sidx = S; sidx < 4 * S; ++sidx) {
+            cplx p = wood_psi(D, G, t, sidx);
+            if (p.x == 0.0 && p.y == 0.0) continue;
+            part = cfma(p, proj[(int64_t)(G.rhs_col + i) * D.ldproj + 2 * l + 4 * M + 4 * S * jj + sidx], part);
+          }
+          v = cfma(aj, part, v);
+          aj = cmul(aj, G.alpha);
+        }
+      }
+      Rpool[G.r_off + (int64_t)i * nS + Rw] = cmk(-v.x, -v.y);
+      continue;
+    }
+    cplx v = row_functional(D, G, proj, Rw, C);
+    v = cmk(-v.x, -v.y);
+    if (Rw < 2 * l) {
+      if (C == Rw) v.x -= 1.0;
+    } else if (Rw < 2 * l + 2 * M) {
+      const int r = Rw - 2 * l;
+      if (C >= 2 * l && C < 2 * l + 2 * M) {
+        const int c = C - 2 * l;
+        const int m = r % M, cm = c % M;
+        if (m == cm) {
+          // Q(alpha) entries (rows [f; fn], columns [mu; nu]) at contour node m
+          cplx km = G.ck[m];
+          cplx sq = cmul(csqrt_principal(cmk(D.omega - km.x, -km.y)), csqrt_principal(cmk(D.omega + km.x, km.y)));
+          cplx ee = cexp(cmk(-sq.y * D.d, sq.x * D.d));
+          cplx ia = cdiv(cmk(1, 0), G.alpha);
+          cplx ap = cadd(G.alpha, ia), am = csub(G.alpha, ia);
+          cplx q;
+          const bool frow = r < M, mucol = c < M;
+          if (frow && mucol) q = cdiv(cmul(cmul(ee, cmk(0, 1)), am), cscale(sq, 2.0));
+          else if (frow && !mucol) q = csub(cmk(1, 0), cscale(cmul(ee, ap), 0.5));
+          else if (!frow && mucol) q = cadd(cmk(-1, 0), cscale(cmul(ee, ap), 0.5));
+          else q = cscale(cmul(cmul(ee, cmk(0, 1)), cmul(sq, am)), 0.5);
+          v = cadd(v, q);
+        }
+      }
+    } else {
+      const int t = Rw - 2 * l - 2 * M;
+      if (C >= 2 * l && C < 2 * l + 2 * M) {
+        // psi^T Wall(alpha) column
+        const int c = C - 2 * l;
+        cplx acc = cmk(0, 0);
+        for (int sidx = S; sidx < 4 * S; ++sidx) {
+          cplx p = wood_psi(D, G, t, sidx);
+          if (p.x == 0.0 && p.y == 0.0) continue;
+          cplx wv = cfma(G.alpha, G.sr[(int64_t)c * 4 * S + sidx], G.sl[(int64_t)c * 4 * S + sidx]);
+          acc = cfma(p, wv, acc);
+        }
+        v = cadd(v, acc);
+      } else if (C >= 2 * l + 2 * M) {
+        const int t2 = C - 2 * l - 2 * M;
+        cplx acc = cmk(0, 0);
+        for (int sidx = S; sidx < 4 * S; ++sidx) {
+          cplx p = wood_psi(D, G, t, sidx);
+          if (p.x == 0.0 && p.y == 0.0) continue;
+          acc = cfma(p, sample_point_pw(D, G, t2, sidx, y0), acc);
+        }
+        v = cadd(v, acc);
+      }
+    }
+    Spool[G.s_off + (int64_t)C * nS + Rw] = v;
+  }
+}
+
+// Batched dense solve S U = Rhs (Gaussian elimination with partial pivoting on the
+// augmented matrix), one CTA per group.  illcond[g] = 1 if a pivot fell below
+// 1e-14 times the largest pivot.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_schur_solve(Dims D, const GroupJob* groups, cplx* Spool, cplx* Rpool,
+                                                    int* illcond) {
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  __shared__ cplx sh_ip;
+  const GroupJob G = groups[blockIdx.x];
+  const int n = 2 * D.l + 2 * D.M + G.nw, q = G.q;
+  cplx* A = Spool + G.s_off;
+  cplx* B = Rpool + G.r_off;
+  const int tid = threadIdx.x;
+  double pmax = 0.0, pmin = 1e300;
+  for (int c = 0; c < n; ++c) {
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = c + tid; i < n; i += NT) {
+      double v = cabs2(A[(int64_t)c * n + i]);
+      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+    }
+    double pv;
+    int p;
+    block_argmax<NT>(best, bi, redv, redi, &pv, &p);
+    pmax = fmax(pmax, pv);
+    pmin = fmin(pmin, pv);
+    if (p != c) {
+      for (int j = tid; j < n; j += NT) {
+        cplx t = A[(int64_t)j * n + c]; A[(int64_t)j * n + c] = A[(int64_t)j * n + p]; A[(int64_t)j * n + p] = t;
+      }
+      for (int j = tid; j < q; j += NT) {
+        cplx t = B[(int64_t)j * n + c]; B[(int64_t)j * n + c] = B[(int64_t)j * n + p]; B[(int64_t)j * n + p] = t;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      cplx dv = A[(int64_t)c * n + c];
+      sh_ip = cabs2(dv) > 0.0 ? cdiv(cmk(1, 0), dv) : cmk(0, 0);
+    }
+    __syncthreads();
+    const cplx ip = sh_ip;
+    // multipliers l_ic = A[i,c]/A[c,c] stored in place
+    for (int i = c + 1 + tid; i < n; i += NT) A[(int64_t)c * n + i] = cmul(A[(int64_t)c * n + i], ip);
+    __syncthreads();
+    const int rows = n - c - 1;
+    const int64_t tot = (int64_t)rows * (n - c - 1 + q);
+    for (int64_t e = tid; e < tot; e += NT) {
+      const int i = c + 1 + (int)(e % rows);
+      const int j = (int)(e / rows);
+      const cplx li = A[(int64_t)c * n + i];
+      if (j < n - c - 1) {
+        const int jj = c + 1 + j;
+        A[(int64_t)jj * n + i] = csub(A[(int64_t)jj * n + i], cmul(li, A[(int64_t)jj * n + c]));
+      } else {
+        const int jj = j - (n - c - 1);
+        B[(int64_t)jj * n + i] = csub(B[(int64_t)jj * n + i], cmul(li, B[(int64_t)jj * n + c]));
+      }
+    }
+    __syncthreads();
+  }
+  // back substitution, one RHS per warp
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int j = warp; j < q; j += NT / 32) {
+    cplx* b = B + (int64_t)j * n;
+    for (int i = n - 1; i >= 0; --i) {
+      cplx acc = cmk(0, 0);
+      for (int t = i + 1 + lane; t < n; t += 32) acc = cfma(A[(int64_t)t * n + i], b[t], acc);
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (lane == 0) b[i] = cdiv(csub(b[i], acc), A[(int64_t)i * n + i]);
+      __syncwarp();
+    }
+  }
+  if (tid == 0) illcond[blockIdx.x] = (pmin <= 1e-28 * pmax) ? 1 : 0;
+}
+
+struct AngleJob {
+  int group;
+  int col;            // index of this angle within its group
+  double kappa;       // kappa^i = w cos(theta)
+  double k0;          // w |sin theta|
+  int n_min, n_max;
+  int64_t out_off;    // into c/d output arrays
+};
+
+// Bragg amplitudes and flux per angle: samples of u at +-y0 from
+// sum_j alpha^j E_j eta + Wall(alpha) xi + PW a, with
+// E_j eta = Proj[E_j, b] - (Rows A^{-1} [L B PW]) [zeta; xi; a], then the DFT.
+__global__ void k_bragg(Dims D, const GroupJob* groups, const AngleJob* angles, const cplx* proj, const cplx* Rpool,
+                        double y0, cplx* cout, cplx* dout, double* flux) {
+  extern __shared__ cplx samp[];  // 2S
+  const AngleJob A = angles[blockIdx.x];
+  const GroupJob G = groups[A.group];
+  const int l = D.l, M = D.M, S = D.S;
+  const int nS = 2 * l + 2 * M + G.nw;
+  const cplx* u = Rpool + G.r_off + (int64_t)A.col * nS;
+  for (int r = threadIdx.x; r < 2 * S; r += blockDim.x) {
+    cplx acc = cmk(0, 0);
+    cplx aj = cdiv(cmk(1, 0), G.alpha);
+    for (int jj = 0; jj < 3; ++jj) {
+      const int row = 2 * l + 4 * M + 4 * S * jj + r;
+      cplx part = proj[(int64_t)(G.rhs_col + A.col) * D.ldproj + row];
+      for (int C = 0; C < nS; ++C) part = csub(part, cmul(rows_ainv(D, G, proj, row, C), u[C]));
+      acc = cfma(aj, part, acc);
+      aj = cmul(aj, G.alpha);
+    }
+    for (int c = 0; c < 2 * M; ++c) {
+      cplx wv = cfma(G.alpha, G.sr[(int64_t)c * 4 * S + r], G.sl[(int64_t)c * 4 * S + r]);
+      acc = cfma(wv, u[2 * l + c], acc);
+    }
+    for (int t = 0; t < G.nw; ++t) acc = cfma(sample_point_pw(D, G, t, r, y0), u[2 * l + 2 * M + t], acc);
+    samp[r] = acc;
+  }
+  __syncthreads();
+  __shared__ double fl[32];
+  const int no = A.n_max - A.n_min + 1;
+  double fsum = 0.0;
+  for (int o = threadIdx.x; o < no; o += blockDim.x) {
+    const int n = A.n_min + o;
+    const double kap = A.kappa + 2.0 * HBS_PI * n / D.d;
+    cplx cn = cmk(0, 0), dn = cmk(0, 0);
+    for (int s = 0; s < S; ++s) {
+      const double xs = -0.5 * D.d + (s + 0.5) * D.d / S;
+      double sn, cs;
+      sincos(-kap * xs, &sn, &cs);
+      cplx e = cmk(cs / S, sn / S);
+      cn = cfma(e, samp[s], cn);
+      dn = cfma(e, samp[S + s], dn);
+    }
+    cout[A.out_off + o] = cn;
+    dout[A.out_off + o] = dn;
+    const double kn2 = D.omega * D.omega - kap * kap;
+    const double kn = kn2 > 0 ? sqrt(kn2) : 0.0;
+    cplx dd = dn;
+    if (n == 0) {
+      double sn, cs;
+      sincos(A.k0 * y0, &sn, &cs);
+      dd = cadd(dd, cmk(cs, sn));
+    }
+    fsum += (kn / A.k0) * (cabs2(cn) + cabs2(dd));
+  }
+  for (int o = 16; o > 0; o >>= 1) fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
+  if ((threadIdx.x & 31) == 0) fl[threadIdx.x >> 5] = fsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += fl[w];
+    flux[blockIdx.x] = fabs(t - 1.0);
+  }
+}
+
+// Right-hand sides: column c of X gets -e^{i(kappa x + ky y)} (incident data b = -u^i)
+// or a Wood's plane wave e^{i(kappa_n x + k_n y)}.
+struct RhsCol {
+  double kap;
+  cplx ky;
+  double sign;
+};
+__global__ void k_fill_rhs(DevGeom g, const RhsCol* cols, int ncol, cplx* X) {
+  const int64_t tot = g.n * (int64_t)ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % g.n;
+    const int c = (int)(e / g.n);
+    const RhsCol rc = cols[c];
+    cplx v = cexp(cmk(-rc.ky.y * g.y[i], rc.kap * g.x[i] + rc.ky.x * g.y[i]));
+    X[e] = cscale(v, rc.sign);
+  }
+}
+
+// columns c0.. of X: s * P (P: N x l)
+__global__ void k_scaled_copy(const cplx* src, int64_t n, cplx f, cplx* dst) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = cmul(f, src[e]);
+}
+
+static zc kn_of(double omega, double kap) {
+  double v = omega * omega - kap * kap;
+  return v >= 0 ? zc(std::sqrt(v), 0.0) : zc(0.0, std::sqrt(-v));
+}
+
+void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, Result& out, cudaStream_t s) {
+  const double omega = h.omega, d = h.d;
+  const int l = h.nb_rank, M = h.M, S = h.S;
+  const int zr = 2 * l + 4 * M + 12 * S;
+  const DevGeom g = Handle_geom(h);
+  out.angles.assign(n_theta, AngleResult());
+  out.illcond = false;
+  if (n_theta == 0) return;
+  for (int64_t i = 0; i < n_theta; ++i)
+    if (!(theta[i] > -M_PI && theta[i] < 0.0)) throw Error(HBS_ERR_INVALID_ARG, "incident angle outside (-pi, 0)");
+
+  // ---- group angles by Bloch phase (Remark 3.1)
+  std::vector<int64_t> order(n_theta);
+  std::vector<double> key(n_theta);
+  for (int64_t i = 0; i < n_theta; ++i) {
+    double ph = std::fmod(omega * d * std::cos(theta[i]), 2.0 * M_PI);
+    if (ph < 0) ph += 2.0 * M_PI;
+    key[i] = ph;
+    order[i] = i;
+  }
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return key[a] < key[b]; });
+  std::vector<std::vector<int64_t>> groups;
+  for (int64_t t = 0; t < n_theta; ++t) {
+    int64_t i = order[t];
+    if (!groups.empty()) {
+      double k0 = key[groups.back()[0]];
+      double dk = std::fabs(key[i] - k0);
+      dk = std::min(dk, 2.0 * M_PI - dk);
+      if (dk < 1e-9) { groups.back().push_back(i); continue; }
+    }
+    groups.push_back({i});
+  }
+  // wrap-around merge (phase near 0 and near 2 pi)
+  if (groups.size() > 1) {
+    double a = key[groups.front()[0]], b = key[groups.back()[0]];
+    if (std::fabs(a + 2.0 * M_PI - b) < 1e-9) {
+      for (auto i : groups.back()) groups.front().push_back(i);
+      groups.pop_back();
+    }
+  }
+
+  // ---- process groups in batches
+  const int nc = (int)h.contours.size();
+  const int64_t max_cols = plain ? 1024 : 512;
+  size_t gi = 0;
+  while (gi < groups.size()) {
+    std::vector<GroupJob> gjobs;
+    std::vector<AngleJob> ajobs;
+    std::vector<RhsCol> rcols;
+    std::vector<std::vector<int64_t>*> gmembers;
+    int64_t cols = 0;
+    while (gi < groups.size()) {
+      auto& mem = groups[gi];
+      const int q = (int)mem.size();
+      const double th0 = theta[mem[0]];
+      const double kap_i = omega * std::cos(th0);
+      // poles +-k_n: choose the contour whose crossing is farther from them
+      std::vector<std::pair<int, zc>> modes;
+      const int nlo = (int)std::floor((-omega - kap_i) * d / (2 * M_PI)) - 4;
+      const int nhi = (int)std::ceil((omega - kap_i) * d / (2 * M_PI)) + 4;
+      double dist0 = 1e300, dist1 = 1e300;
+      const double t1 = nc > 1 ? h.contours[1].t0 : 0.0;
+      for (int n = nlo; n <= nhi; ++n) {
+        zc kn = kn_of(omega, kap_i + 2 * M_PI * n / d);
+        modes.push_back({n, kn});
+        dist0 = std::min(dist0, std::abs(kn));
+        dist1 = std::min(dist1, std::min(std::abs(kn - t1), std::abs(-kn - t1)));
+      }
+      const int c = (nc > 1 && dist1 > dist0) ? 1 : 0;
+      GroupJob G{};
+      std::vector<std::pair<double, zc>> wood;
+      if (c == 1) {
+        const double height = h.cc * std::tanh(t1 / h.cw);
+        for (auto& md : modes) {
+          zc kn = md.second;
+          bool flip = (kn.imag() == 0.0) ? (kn.real() >= 0.0 && kn.real() < t1) : (kn.real() == 0.0 && kn.imag() < height);
+          if (flip) wood.push_back({kap_i + 2 * M_PI * md.first / d, kn});
+        }
+      }
+      if (wood.size() > 4) throw Error(HBS_ERR_INTERNAL, "more than four Wood's modes flipped");
+      const int nw = (int)wood.size();
+      const int need = q + nw + (plain ? 2 * l + 2 * M : 0);
+      if (!gjobs.empty() && cols + need > max_cols) break;
+      G.alpha = to_c(std::exp(zc(0.0, omega * d * std::cos(th0))));
+      G.q = q;
+      G.nw = nw;
+      G.rhs_col = (int)cols;
+      G.contour = c;
+      G.zp = h.contours[c].Zd.get();
+      G.sl = h.contours[c].SL.get();
+      G.sr = h.contours[c].SR.get();
+      G.ck = h.contours[c].dk.get();
+      for (int t = 0; t < nw; ++t) { G.wkap[t] = wood[t].first; G.wkn[t] = to_c(wood[t].second); }
+      for (int a = 0; a < q; ++a) {
+        const double th = theta[mem[a]];
+        rcols.push_back({omega * std::cos(th), cmk(omega * std::sin(th), 0.0), -1.0});
+      }
+      for (int t = 0; t < nw; ++t) rcols.push_back({wood[t].first, to_c(wood[t].second), 1.0});
+      cols += q + nw;
+      if (plain) cols += 2 * l + 2 * M;
+      gjobs.push_back(G);
+      gmembers.push_back(&mem);
+      ++gi;
+    }
+    const int ng = (int)gjobs.size();
+    const int64_t N = h.N;
+    // ---- right-hand sides, applies
+    DevBuf<cplx> RHS((size_t)N * cols), X((size_t)N * cols);
+    {
+      // b and PW columns are packed per group at rhs_col; in the plain path the
+      // L and B(alpha) columns follow each group's q + nw columns.
+      int64_t pos = 0;
+      size_t rc = 0;
+      for (int gg = 0; gg < ng; ++gg) {
+        GroupJob& G = gjobs[gg];
+        G.rhs_col = (int)pos;
+        DevBuf<RhsCol> dr;
+        dr.upload(std::vector<RhsCol>(rcols.begin() + rc, rcols.begin() + rc + G.q + G.nw), s);
+        rc += G.q + G.nw;
+        k_fill_rhs<<<grid_1d(N * (G.q + G.nw)), 256, 0, s>>>(g, dr.get(), G.q + G.nw, RHS.get() + pos * N);
+        HBS_LAUNCH_CHECK("k_fill_rhs");
+        HBS_CUDA(cudaStreamSynchronize(s));
+        pos += G.q + G.nw;
+        if (plain) {
+          // L = [alpha^{-1} P | alpha P], B(alpha) = B_L + alpha B_R
+          const cplx ia = cdiv(cmk(1, 0), G.alpha);
+          if (l > 0) {
+            k_scaled_copy<<<grid_1d(N * l), 256, 0, s>>>(h.Pnb.get(), N * (int64_t)l, ia, RHS.get() + pos * N);
+            k_scaled_copy<<<grid_1d(N * l), 256, 0, s>>>(h.Pnb.get(), N * (int64_t)l, G.alpha, RHS.get() + (pos + l) * N);
+          }
+          const ContourData& cd = h.contours[G.contour];
+          k_fill_b<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), cd.dwk.get(), M, d, RHS.get(), N, pos + 2 * l,
+                                                            0, 1, G.alpha);
+          HBS_LAUNCH_CHECK("plain fills");
+          pos += 2 * l + 2 * M;
+        }
+      }
+    }
+    h.apply_inverse(RHS.get(), X.get(), cols, s);
+    RHS.release();
+    // ---- Proj = Rows X
+    DevBuf<cplx> Proj((size_t)zr * cols);
+    {
+      std::vector<GemmJob> gj;
+      for (int gg = 0; gg < ng; ++gg) {
+        const GroupJob& G = gjobs[gg];
+        const ContourData& cd = h.contours[G.contour];
+        const int gcols = G.q + G.nw + (plain ? 2 * l + 2 * M : 0);
+        struct Blk { const cplx* A; int rows; int lda; int row0; };
+        Blk rows[5] = {{h.Rm.get(), l, l, 0}, {h.Rp.get(), l, l, l}, {cd.CL.get(), 2 * M, 2 * M, 2 * l},
+                       {cd.CR.get(), 2 * M, 2 * M, 2 * l + 2 * M}, {h.Esamp.get(), 12 * S, 12 * S, 2 * l + 4 * M}};
+        for (auto& rb : rows) {
+          if (rb.rows == 0) continue;
+          gj.push_back({rb.A, X.get() + (int64_t)G.rhs_col * N, Proj.get() + (int64_t)G.rhs_col * zr + rb.row0, rb.rows,
+                        gcols, (int)N, rb.lda, (int)N, zr, cmk(1, 0), cmk(0, 0), 0, 0, 0});
+        }
+      }
+      run_gemms(gj, s);
+    }
+    X.release();
+    // plain path: point zl / zb at the per-group products
+    for (int gg = 0; gg < ng; ++gg) {
+      GroupJob& G = gjobs[gg];
+      if (plain) {
+        G.zl = Proj.get() + (int64_t)(G.rhs_col + G.q + G.nw) * zr;
+        G.zb = Proj.get() + (int64_t)(G.rhs_col + G.q + G.nw + 2 * l) * zr;
+      }
+    }
+    // ---- Schur systems
+    int64_t so = 0, ro = 0;
+    for (auto& G : gjobs) {
+      const int nS = 2 * l + 2 * M + G.nw;
+      G.s_off = so; so += (int64_t)nS * nS;
+      G.r_off = ro; ro += (int64_t)nS * G.q;
+    }
+    DevBuf<cplx> Sp(so), Rp(ro);
+    DevBuf<GroupJob> dg;
+    dg.upload(gjobs, s);
+    Dims D{l, M, S, zr, d, omega, zr};
+    k_assemble<<<dim3(64, ng), 256, 0, s>>>(D, dg.get(), Proj.get(), h.y0, Sp.get(), Rp.get());
+    HBS_LAUNCH_CHECK("k_assemble");
+    DevBuf<int> ill(ng);
+    k_schur_solve<256><<<ng, 256, 0, s>>>(D, dg.get(), Sp.get(), Rp.get(), ill.get());
+    HBS_LAUNCH_CHECK("k_schur_solve");
+    // ---- Bragg amplitudes
+    int64_t oo = 0;
+    for (int gg = 0; gg < ng; ++gg) {
+      const auto& mem = *gmembers[gg];
+      for (int a = 0; a < gjobs[gg].q; ++a) {
+        const double th = theta[mem[a]];
+        const double kap = omega * std::cos(th);
+        AngleJob aj;
+        aj.group = gg;
+        aj.col = a;
+        aj.kappa = kap;
+        aj.k0 = omega * std::fabs(std::sin(th));
+        aj.n_min = (int)std::ceil((-omega - kap) * d / (2 * M_PI));
+        aj.n_max = (int)std::floor((omega - kap) * d / (2 * M_PI));
+        aj.out_off = oo;
+        oo += aj.n_max - aj.n_min + 1;
+        ajobs.push_back(aj);
+      }
+    }
+    DevBuf<AngleJob> da;
+    da.upload(ajobs, s);
+    DevBuf<cplx> cbuf(std::max<int64_t>(oo, 1)), dbuf(std::max<int64_t>(oo, 1));
+    DevBuf<double> fbuf(ajobs.size());
+    k_bragg<<<(unsigned)ajobs.size(), 128, 2 * S * sizeof(cplx), s>>>(D, dg.get(), da.get(), Proj.get(), Rp.get(), h.y0,
+                                                                      cbuf.get(), dbuf.get(), fbuf.get());
+    HBS_LAUNCH_CHECK("k_bragg");
+    auto hc = cbuf.download(s), hd = dbuf.download(s);
+    auto hf = fbuf.download(s);
+    auto hill = ill.download(s);
+    for (int v : hill)
+      if (v) out.illcond = true;
+    size_t ai = 0;
+    for (int gg = 0; gg < ng; ++gg) {
+      const auto& mem = *gmembers[gg];
+      for (int a = 0; a < gjobs[gg].q; ++a, ++ai) {
+        const AngleJob& aj = ajobs[ai];
+        AngleResult& r = out.angles[mem[a]];
+        r.n_min = aj.n_min;
+        r.n_max = aj.n_max;
+        const int no = aj.n_max - aj.n_min + 1;
+        r.c.resize(no);
+        r.d.resize(no);
+        for (int o = 0; o < no; ++o) {
+          r.c[o] = zc(hc[aj.out_off + o].x, hc[aj.out_off + o].y);
+          r.d[o] = zc(hd[aj.out_off + o].x, hd[aj.out_off + o].y);
+        }
+        r.flux_err = hf[ai];
+        r.n_wood = gjobs[gg].nw;
+        r.t0 = h.contours[gjobs[gg].contour].t0;
+      }
+    }
+  }
+}
+
+}  // namespace hbs

@@ -1,0 +1,219 @@
+"""Thin ctypes binding of libhbsqp.so (include/hbsqp.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy arrays,
+torch CUDA tensors and integers into the plain pointers and sizes of the C ABI.
+Loading fails loudly if the library has not been built (there is no CPU path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhbsqp.so")
+
+HBS_OK = 0
+HBS_WARN_ILLCOND = 5
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "RANK", 5: "WARN_ILLCOND",
+                6: "TIMEOUT", 7: "IO", 8: "INTERNAL"}
+
+# Every entry point declared in include/hbsqp.h.
+EXPORTED = ("hbs_default_options", "hbs_build", "hbs_solve", "hbs_solve_plain", "hbs_bragg_amplitudes",
+            "hbs_result_angle_info", "hbs_info", "hbs_apply_inverse", "hbs_kernel_block", "hbs_row_id",
+            "hbs_free", "hbs_result_free", "hbs_last_error")
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_double), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("dx", ctypes.c_void_p), ("dy", ctypes.c_void_p), ("on_device", ctypes.c_int)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int), ("n_proxy_min", ctypes.c_int), ("proxy_rho", ctypes.c_double),
+                ("nb_radius", ctypes.c_double), ("nb_proxies", ctypes.c_int), ("m", ctypes.c_int),
+                ("contour_h", ctypes.c_double), ("contour_c", ctypes.c_double), ("contour_w", ctypes.c_double),
+                ("contour_k", ctypes.c_double), ("wood_shift", ctypes.c_double),
+                ("n_bragg_samples", ctypes.c_int), ("y0", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("levels", ctypes.c_int), ("max_rank", ctypes.c_int),
+                ("nb_rank", ctypes.c_int), ("m", ctypes.c_int), ("n_contours", ctypes.c_int),
+                ("device_bytes", ctypes.c_size_t), ("build_seconds", ctypes.c_double),
+                ("factor_bytes", ctypes.c_double), ("apply_flops_per_rhs", ctypes.c_double),
+                ("contour_h", ctypes.c_double), ("contour_c", ctypes.c_double), ("contour_w", ctypes.c_double),
+                ("wood_t0", ctypes.c_double), ("n_bragg_samples", ctypes.c_int), ("y0", ctypes.c_double),
+                ("nb_radius", ctypes.c_double), ("nb_proxies", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libhbsqp.so (raises if it is missing: build it with paper_1301_1247_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run `python -m paper_1301_1247_gb300.build` first")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, dbl, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    L.hbs_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.hbs_default_options.restype = None
+    L.hbs_build.argtypes = [ctypes.POINTER(Geometry), dbl, dbl, ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]
+    L.hbs_solve.argtypes = [vp, ctypes.POINTER(dbl), i64, vp, ctypes.POINTER(vp)]
+    L.hbs_solve_plain.argtypes = [vp, ctypes.POINTER(dbl), i64, vp, ctypes.POINTER(vp)]
+    L.hbs_bragg_amplitudes.argtypes = [vp, i64, ctypes.POINTER(ci), ctypes.POINTER(ci), vp, vp,
+                                       ctypes.POINTER(dbl)]
+    L.hbs_result_angle_info.argtypes = [vp, i64, ctypes.POINTER(ci), ctypes.POINTER(dbl)]
+    L.hbs_info.argtypes = [vp, ctypes.POINTER(Info)]
+    L.hbs_apply_inverse.argtypes = [vp, vp, vp, i64, vp]
+    L.hbs_kernel_block.argtypes = [ctypes.POINTER(Geometry), dbl, ci, dbl, vp, i64, vp, i64, vp, vp]
+    L.hbs_row_id.argtypes = [vp, i64, i64, dbl, ctypes.POINTER(ci), vp, vp, vp]
+    L.hbs_free.argtypes = [vp]
+    L.hbs_free.restype = None
+    L.hbs_result_free.argtypes = [vp]
+    L.hbs_result_free.restype = None
+    L.hbs_last_error.argtypes = []
+    L.hbs_last_error.restype = ctypes.c_char_p
+    for name in ("hbs_build", "hbs_solve", "hbs_solve_plain", "hbs_bragg_amplitudes", "hbs_result_angle_info",
+                 "hbs_info", "hbs_apply_inverse", "hbs_kernel_block", "hbs_row_id"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class HbsError(RuntimeError):
+    def __init__(self, status, where):
+        msg = lib().hbs_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st, where, allow_warn=False):
+    if st == HBS_OK or (allow_warn and st == HBS_WARN_ILLCOND):
+        return st
+    raise HbsError(st, where)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(a):
+    """Device pointer of a torch tensor, or host pointer of a contiguous numpy array."""
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"] and not a.flags["F_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    return ctypes.c_void_p(int(a))
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().hbs_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Result:
+    def __init__(self, ptr, n):
+        self._p = ptr
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "_p", None):
+            lib().hbs_result_free(self._p)
+            self._p = None
+
+    def bragg(self, i):
+        """(orders, c_n, d_n, flux_error) of angle i."""
+        nmin, nmax = ctypes.c_int(), ctypes.c_int()
+        _check(lib().hbs_bragg_amplitudes(self._p, i, ctypes.byref(nmin), ctypes.byref(nmax), None, None, None),
+               "hbs_bragg_amplitudes")
+        no = nmax.value - nmin.value + 1
+        c = np.zeros(no, dtype=np.complex128)
+        d = np.zeros(no, dtype=np.complex128)
+        fe = ctypes.c_double()
+        _check(lib().hbs_bragg_amplitudes(self._p, i, ctypes.byref(nmin), ctypes.byref(nmax),
+                                          c.ctypes.data_as(ctypes.c_void_p), d.ctypes.data_as(ctypes.c_void_p),
+                                          ctypes.byref(fe)), "hbs_bragg_amplitudes")
+        return np.arange(nmin.value, nmax.value + 1), c, d, fe.value
+
+    def angle_info(self, i):
+        nw, t0 = ctypes.c_int(), ctypes.c_double()
+        _check(lib().hbs_result_angle_info(self._p, i, ctypes.byref(nw), ctypes.byref(t0)), "hbs_result_angle_info")
+        return nw.value, t0.value
+
+
+class Handle:
+    """A built solver (hbs_build)."""
+
+    def __init__(self, x, y, dx, dy, d, omega, tol, opts: Options | None = None, stream=None):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, dx, dy)]
+        self._keep = arrs
+        g = Geometry(len(arrs[0]), float(d), *[a.ctypes.data for a in arrs], 0)
+        out = ctypes.c_void_p()
+        st = lib().hbs_build(ctypes.byref(g), float(omega), float(tol),
+                             ctypes.byref(opts) if opts is not None else None, _stream(stream), ctypes.byref(out))
+        _check(st, "hbs_build")
+        self._p = out
+        self.n = len(arrs[0])
+
+    def __del__(self):
+        if getattr(self, "_p", None):
+            lib().hbs_free(self._p)
+            self._p = None
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(lib().hbs_info(self._p, ctypes.byref(inf)), "hbs_info")
+        return inf.as_dict()
+
+    def _solve(self, fn, thetas, stream):
+        th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).ravel())
+        out = ctypes.c_void_p()
+        st = fn(self._p, th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(th), _stream(stream),
+                ctypes.byref(out))
+        _check(st, fn.__name__, allow_warn=True)
+        r = Result(out, len(th))
+        r.status = st
+        return r
+
+    def solve(self, thetas, stream=None) -> Result:
+        return self._solve(lib().hbs_solve, thetas, stream)
+
+    def solve_plain(self, thetas, stream=None) -> Result:
+        return self._solve(lib().hbs_solve_plain, thetas, stream)
+
+    def apply_inverse(self, b, x, nrhs, stream=None):
+        """x = A^{-1} b for device complex128 tensors (N x nrhs, column-major, i.e. torch shape (nrhs, N))."""
+        _check(lib().hbs_apply_inverse(self._p, _ptr(b), _ptr(x), int(nrhs), _stream(stream)), "hbs_apply_inverse")
+
+
+def kernel_block(x, y, dx, dy, omega, kind, shift_x, rows, cols, out, stream=None):
+    """Device-side fill of Nystrom entries (kind 0: A with I/2 and KR6; kind 1: image shifted by shift_x)."""
+    g = Geometry(int(x.numel()), 1.0, _ptr(x).value, _ptr(y).value, _ptr(dx).value, _ptr(dy).value, 1)
+    _check(lib().hbs_kernel_block(ctypes.byref(g), float(omega), int(kind), float(shift_x), _ptr(rows),
+                                  int(rows.numel()), _ptr(cols), int(cols.numel()), _ptr(out), _stream(stream)),
+           "hbs_kernel_block")
+
+
+def row_id(mt, m, n, tol, perm, t, stream=None) -> int:
+    """Interpolative decomposition of M = Mt^T (device, m x n column-major, overwritten)."""
+    rank = ctypes.c_int()
+    _check(lib().hbs_row_id(_ptr(mt), int(m), int(n), float(tol), ctypes.byref(rank), _ptr(perm), _ptr(t),
+                            _stream(stream)), "hbs_row_id")
+    return rank.value

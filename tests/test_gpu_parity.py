@@ -1,0 +1,155 @@
+"""Parity of the CUDA path (through the C ABI) with the dense FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import interp, qp_dense as qd
+from paper_1301_1247_gb300 import inputs
+
+from gpu_util import dev, relerr, require_lib
+
+pytestmark = pytest.mark.gpu
+
+
+def _geom(obs, n):
+    return obs.sample(n)
+
+
+@pytest.mark.parametrize("case", [("star", 400, 10.0), ("wiggly", 3001, 60.0)])
+def test_kernel_block_entries(case):
+    """Nystrom entries (A with I/2 and KR6 weights; neighbour images) element by element."""
+    import torch
+    hbs = require_lib()
+    name, n, omega = case
+    obs = inputs.star(0.3, 0.3, 5) if name == "star" else inputs.wiggly(3, 0.3, 60, 0.05)
+    x, y, dx, dy = obs.sample(n)
+    bd = qd.boundary(x, y, dx, dy)
+    rng = np.random.default_rng(1)
+    rows = np.unique(np.concatenate([rng.integers(0, n, 40), [0, 1, 2, n - 1, n // 2]]))
+    cols = np.unique(np.concatenate([rng.integers(0, n, 50), [0, 1, 3, 5, 6, 7, n - 1, n - 6, n // 2 + 1]]))
+    ref = qd.matrix_a(bd, omega)[np.ix_(rows, cols)]
+    gx, gy, gdx, gdy = (dev(a) for a in (x, y, dx, dy))
+    out = torch.zeros((len(cols), len(rows)), dtype=torch.complex128, device="cuda")
+    hbs.kernel_block(gx, gy, gdx, gdy, omega, 0, 0.0, dev(rows.astype(np.int64)), dev(cols.astype(np.int64)), out)
+    got = out.cpu().numpy().T
+    scale = np.abs(ref).max()
+    assert np.max(np.abs(got - ref)) <= 1e-13 * scale
+    big = np.abs(ref) > 1e-3 * scale
+    assert np.max(np.abs(got - ref)[big] / np.abs(ref)[big]) < 1e-12
+    for shift in (-1.0, 1.0):
+        refi = qd.matrix_a_image(bd, omega, 1.0, int(shift))[np.ix_(rows, cols)]
+        hbs.kernel_block(gx, gy, gdx, gdy, omega, 1, shift, dev(rows.astype(np.int64)), dev(cols.astype(np.int64)), out)
+        got = out.cpu().numpy().T
+        assert np.max(np.abs(got - refi)) <= 1e-13 * np.abs(refi).max()
+
+
+@pytest.mark.parametrize("shape", [(300, 40), (150, 64), (37, 90)])
+def test_row_id_matches_oracle(shape):
+    """CPQR interpolative decomposition (Def. 3.1): same rank and skeleton as the oracle's
+    LAPACK-pivoted QR on a kernel block, and the same reconstruction accuracy."""
+    import torch
+    hbs = require_lib()
+    m_cols, n_rows = shape
+    omega = 20.0
+    x, y, dx, dy = inputs.star(0.3, 0.3, 5).sample(600)
+    bd = qd.boundary(x, y, dx, dy)
+    rows = np.arange(0, n_rows)
+    cols = np.arange(200, 200 + m_cols)
+    blk = qd.combined(bd.x[rows, None], bd.y[rows, None], bd.x[None, cols], bd.y[None, cols],
+                      bd.nx[None, cols], bd.ny[None, cols], omega) * bd.w[None, cols]
+    tol = 1e-12
+    j_ref, p_ref, k_ref = interp.row_id(blk, tol)
+    # device column-major Mt (m x n) with m = cols, n = rows: blk (n x m) row-major == Mt column-major
+    mt = dev(np.ascontiguousarray(blk))
+    perm = torch.zeros(n_rows, dtype=torch.int32, device="cuda")
+    t = torch.zeros(min(m_cols, n_rows) * n_rows, dtype=torch.complex128, device="cuda")
+    k = hbs.row_id(mt, m_cols, n_rows, tol, perm, t)
+    assert abs(k - k_ref) <= 1
+    pm = perm.cpu().numpy()
+    tt = t.cpu().numpy()[: k * (n_rows - k)].reshape((n_rows - k, k)).T if k < n_rows else np.zeros((k, 0))
+    p = np.zeros((n_rows, k), dtype=np.complex128)
+    p[pm[:k], :] = np.eye(k)
+    p[pm[k:], :] = tt.T
+    err = np.linalg.norm(blk - p @ blk[pm[:k], :]) / np.linalg.norm(blk)
+    err_ref = np.linalg.norm(blk - p_ref @ blk[j_ref, :]) / np.linalg.norm(blk)
+    assert err < max(10 * err_ref, 1e-12)
+    if k == k_ref:
+        assert set(pm[:k]) == set(j_ref)
+
+
+@pytest.mark.parametrize("case", [("star", 400, 10.0), ("wiggly", 1501, 30.0)])
+def test_apply_inverse_matches_dense_inverse(case):
+    """Compressed A^{-1} (Sec. 4) applied to random vectors vs a dense LU solve of the oracle's A."""
+    import torch
+    hbs = require_lib()
+    name, n, omega = case
+    obs = inputs.star(0.3, 0.3, 5) if name == "star" else inputs.wiggly(0, 0.35, 20, 0.03)
+    x, y, dx, dy = obs.sample(n)
+    h = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12, hbs.default_options(leaf_size=32))
+    rng = np.random.default_rng(2)
+    b = rng.standard_normal((5, n)) + 1j * rng.standard_normal((5, n))
+    xb = torch.zeros((5, n), dtype=torch.complex128, device="cuda")
+    h.apply_inverse(dev(b), xb, 5)
+    got = xb.cpu().numpy()
+    a = qd.matrix_a(qd.boundary(x, y, dx, dy), omega)
+    ref = np.linalg.solve(a, b.T).T
+    assert relerr(got, ref) < 1e-10
+
+
+def _oracle_opts(info):
+    return dict(m=info["m"], h=info["contour_h"], c=info["contour_c"], w=info["contour_w"],
+                n_samples=info["n_bragg_samples"], y0=info["y0"])
+
+
+def test_solve_matches_oracle_star():
+    """Bragg amplitudes of the full block solve (Secs. 2-4) vs the dense oracle, several angles."""
+    hbs = require_lib()
+    x, y, dx, dy = inputs.star(0.3, 0.3, 5).sample(400)
+    omega = 10.0
+    h = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12)
+    info = h.info()
+    thetas = np.array([-math.pi / 5, -0.4, -1.0, -2.5, -math.pi / 2])
+    res = h.solve(thetas)
+    for i, th in enumerate(thetas):
+        nw, t0 = res.angle_info(i)
+        sol = qd.dense_solve(x, y, dx, dy, omega, 1.0, th, qd.Options(**_oracle_opts(info), t0=t0))
+        orders, c, d, fe = res.bragg(i)
+        assert list(orders) == list(sol.orders)
+        assert nw == len(sol.wood_modes)
+        assert relerr(np.concatenate([c, d]), qd.bragg_vector(sol)) < 1e-10
+        assert abs(fe - sol.flux_error) < 1e-9
+
+
+def test_woods_anomaly_matches_oracle():
+    """At the Wood's anomaly of Sec. 6.2 the library switches to the shifted contour and adds
+    one Rayleigh-Bloch unknown; the oracle with the same contour agrees."""
+    hbs = require_lib()
+    x, y, dx, dy = inputs.star(0.3, 0.3, 5).sample(400)
+    omega = 10.0
+    h = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12)
+    info = h.info()
+    th = -math.acos(1.0 - 2.0 * math.pi / omega)
+    res = h.solve([th])
+    nw, t0 = res.angle_info(0)
+    assert nw == 1 and t0 > 0
+    sol = qd.dense_solve(x, y, dx, dy, omega, 1.0, th, qd.Options(**_oracle_opts(info), t0=t0))
+    orders, c, d, fe = res.bragg(0)
+    assert relerr(np.concatenate([c, d]), qd.bragg_vector(sol)) < 1e-10
+    assert fe < 1e-5
+
+
+def test_plain_path_matches_precomputed_path():
+    """The paper's per-Bloch-phase path (q + 2M + 2l applies) and the precomputed path agree."""
+    hbs = require_lib()
+    obs = inputs.wiggly(0, 0.35, 20, 0.03)
+    x, y, dx, dy = obs.sample(2000)
+    omega = 30.0
+    h = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12)
+    thetas = inputs.bloch_grouped_angles(5, omega, 1.0, 2, 3).ravel()
+    a = h.solve(thetas)
+    b = h.solve_plain(thetas)
+    for i in range(len(thetas)):
+        _, c1, d1, _ = a.bragg(i)
+        _, c2, d2, _ = b.bragg(i)
+        assert relerr(np.concatenate([c1, d1]), np.concatenate([c2, d2])) < 1e-11

@@ -1,0 +1,58 @@
+"""The C-ABI library builds, loads and exports every entry point its header declares (CPU only)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _ensure_built():
+    from paper_1301_1247_gb300 import build, hbs
+    if not os.path.exists(hbs.LIB_PATH):
+        build.build()
+    return hbs.LIB_PATH
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hbsqp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hbs_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_bound_names():
+    from paper_1301_1247_gb300 import hbs
+    assert sorted(hbs.EXPORTED) == _declared()
+
+
+def test_library_exports_all_declared_symbols():
+    path = _ensure_built()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (hbs_[a-z_]+)\b", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_reports_defaults():
+    _ensure_built()
+    from paper_1301_1247_gb300 import hbs
+    L = hbs.lib()
+    for name in _declared():
+        assert hasattr(L, name)
+    o = hbs.default_options()
+    assert o.leaf_size == 64 and o.proxy_rho == 1.5 and o.precision == 0
+    assert L.hbs_last_error() is not None
+
+
+def test_argument_errors_need_no_gpu():
+    """Invalid arguments are rejected on the host before any CUDA call."""
+    _ensure_built()
+    from paper_1301_1247_gb300 import hbs
+    L = hbs.lib()
+    out = ctypes.c_void_p()
+    g = hbs.Geometry(10, 1.0, None, None, None, None, 0)
+    assert L.hbs_build(ctypes.byref(g), 10.0, 1e-12, None, None, ctypes.byref(out)) == 1
+    assert L.hbs_solve(None, None, 0, None, ctypes.byref(out)) == 1
+    assert L.hbs_apply_inverse(None, None, None, 1, None) == 1
