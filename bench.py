@@ -1,0 +1,313 @@
+"""Benchmark: HBS build seconds + incident angles per second at N = 100 000.
+
+Workload (default): the complicated obstacle, r0 = 0.3 with 60 seeded Fourier modes of
+amplitude <= 0.05, omega = 60, d = 1, N = 100 000 boundary nodes, 1000 incident angles
+in 100 groups of 10 that share a Bloch phase.  One step = the whole hot path:
+hbs_build (HBS compression and inversion, neighbour factors, periodizer precompute)
+followed by hbs_solve of all 1000 angles (Bragg amplitudes + flux errors).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` = angles solved per second of whole-step time (build
+included) with the geometry resident on the device; `e2e` = the same through the C ABI
+with host arrays (host-to-device copies and the read-back of the amplitudes inside the
+timed region).  Under torchrun every rank solves its own copy of the workload on its GPU
+(independent problems, no collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1301_1247_gb300 import inputs  # noqa: E402
+
+METRIC = "HBS build s + incident angles/s at N=1e5, err <=1e-10 vs FP64 plain path"
+UNIT = "angles/s"
+# FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def workload(name):
+    if name == "complicated_n100k":
+        w = inputs.workload_complicated_n100k()
+    elif name == "wiggly_n10k":
+        w = inputs.workload_wiggly_n10k()
+    elif name == "star_n400":
+        w = inputs.workload_star_n400()
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    w["name"] = name
+    return w
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda() else "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def _cuda():
+    import torch
+    return torch.cuda.is_available()
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if _cuda() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_1301_1247_gb300 import hbs
+
+    torch.cuda.set_device(local)
+    w = workload(args.workload)
+    obs, omega, d, n = w["obstacle"], w["omega"], w["d"], w["N"]
+    thetas = np.asarray(w["thetas"], dtype=np.float64).ravel()
+    x, y, dx, dy = obs.sample(n)
+    gx, gy, gdx, gdy = (torch.from_numpy(a).cuda() for a in (x, y, dx, dy))
+    hx, hy, hdx, hdy = (torch.from_numpy(a).pin_memory() for a in (x, y, dx, dy))
+    hth = torch.from_numpy(thetas).pin_memory()
+    stream = torch.cuda.current_stream()
+    tol = 1e-12
+
+    def step(device_inputs: bool):
+        if device_inputs:
+            h = hbs.Handle(gx, gy, gdx, gdy, d, omega, tol, stream=stream)
+        else:
+            h = hbs.Handle(hx.numpy(), hy.numpy(), hdx.numpy(), hdy.numpy(), d, omega, tol, stream=stream)
+        r = h.solve(hth.numpy(), stream=stream)
+        amps = [r.bragg(i) for i in range(len(thetas))]
+        return h, r, amps
+
+    info = None
+    for _ in range(args.warmup):
+        h, r, amps = step(True)
+        info = h.info()
+        del h, r
+    torch.cuda.synchronize()
+
+    # ---- device-resident inputs: value + roofline
+    hbs.profile_reset()
+    hbs.profile_enable(True)
+    l0 = hbs.launch_count()
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            h, r, amps = step(True)
+            if info is None:
+                info = h.info()
+            del h, r
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    launches = hbs.launch_count() - l0
+    hbs.profile_enable(False)
+    prof = hbs.profile_get()
+    ms = e0.elapsed_time(e1)
+    clocks = clk.summary()
+    ms_max = max_over_ranks(ms, ws)
+
+    # ---- end to end: host inputs, copies and read-back inside the timed region
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        h, r, amps = step(False)
+        del h, r
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(max(e2.elapsed_time(e3), 1e3 * (time.perf_counter() - t0)), ws)
+    flux = [a[3] for a in amps]
+
+    n_ang = len(thetas)
+    value = ws * n_ang * args.steps / (ms_max / 1e3)
+    kern = {k: v for k, v in prof.items() if not k.startswith("phase:")}
+    phases = {k[6:]: round(v["ms"] / args.steps, 2) for k, v in prof.items() if k.startswith("phase:")}
+    top = max(kern.items(), key=lambda kv: kv[1]["ms"])
+    tname, tv = top
+    achieved = tv["flops"] / (tv["ms"] / 1e3) / 1e12 if tv["ms"] > 0 else 0.0
+    shares = {k: round(v["ms"] / sum(x["ms"] for x in kern.values()), 4) for k, v in
+              sorted(kern.items(), key=lambda kv: -kv[1]["ms"])[:8]}
+    h2d = 4 * n * 8 + n_ang * 8
+    n_orders = sum(len(a[1]) for a in amps)
+    d2h = n_orders * 2 * 16 + n_ang * 8
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)", "data": "synthetic",
+        "config": {"workload": w["name"], "N": n, "omega": omega, "d": d, "angles": n_ang,
+                   "bloch_groups": int(np.asarray(w["thetas"]).shape[0]) if np.asarray(w["thetas"]).ndim == 2 else None,
+                   "tol": tol, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (factor + precompute %.1f GB resident)" % (info["device_bytes"] / 1e9),
+                   "build_s": round(info["build_seconds"], 3), "max_rank": info["max_rank"],
+                   "nb_rank": info["nb_rank"], "M": info["m"], "levels": info["levels"],
+                   "phases_ms_per_step": phases, "max_flux_error": float(max(flux))},
+        "e2e": {"value": round(ws * n_ang * args.steps / (e2e_ms / 1e3), 3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "kernel": tname, "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                     "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                     "peak_note": "FP64 from unit counts x clock (152 SM x 2 DFMA/clk x 2.07 GHz); "
+                                  "no FP64 figure in MEASURED_PEAKS.json",
+                     "kernel_time_shares": shares},
+        "clocks": clocks,
+    }
+    return out
+
+
+def oracle_sample(w, n_sample):
+    """Dense oracle on the same obstacle family at a bounded N; returns (fill+solve seconds, parts)."""
+    from oracle import qp_dense as qd
+    obs, omega, d = w["obstacle"], w["omega"], w["d"]
+    th = float(np.asarray(w["thetas"]).ravel()[0])
+    x, y, dx, dy = obs.sample(n_sample)
+    t0 = time.perf_counter()
+    qd.dense_solve(x, y, dx, dy, omega, d, th, qd.Options(m=120, h=0.4, c=2.0, w=2.0))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(w, n_sample):
+    secs = oracle_sample(w, n_sample)
+    n = w["N"]
+    scale = (n / n_sample) ** 3
+    per_angle = secs * scale
+    cores = os.cpu_count()
+    return {"value": 1.0 / per_angle, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"dense FP64 fill + LAPACK solve of one angle at N={n_sample} (same obstacle, omega="
+                      f"{w['omega']}, M=120) took {secs:.2f} s; extrapolated to N={n} by (N/{n_sample})^3 "
+                      f"(LU-dominated), i.e. {per_angle:.3g} s per angle"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    w = workload(args.workload)
+    n_sample = 1500 if w["N"] > 1500 else w["N"]
+    for _ in range(args.warmup):
+        oracle_sample(w, n_sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample(w, n_sample)
+    secs = (time.perf_counter() - t0) / args.steps
+    n = w["N"]
+    value = 1.0 / (secs * (n / n_sample) ** 3)
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (complex128)", "data": "synthetic",
+            "config": {"workload": w["name"], "N": n, "omega": w["omega"], "sample_N": n_sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"one angle, dense oracle at N={n_sample}, extrapolated by (N/{n_sample})^3"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="complicated_n100k")
+    ap.add_argument("--cpu-sample-n", type=int, default=2000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    out = run_ours(args, ws, rank, local)
+    if rank == 0:
+        if ws == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(workload(args.workload), args.cpu_sample_n)
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

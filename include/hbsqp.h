@@ -174,6 +174,26 @@ hbs_status hbs_kernel_block(const hbs_geometry* geom, double omega, int kind, do
 hbs_status hbs_row_id(void* mt, int64_t m, int64_t n, double tol, int* rank, int* perm, void* t,
                       void* stream);
 
+/*
+ * Profiling.  hbs_launch_count() is the number of kernels this library has
+ * launched since it was loaded.  With hbs_profile_enable(1) every launch is also
+ * bracketed by CUDA events on its stream; hbs_profile_get copies up to `max`
+ * per-kernel records (launches, summed device milliseconds, summed algorithmic
+ * flops and bytes; entries named "phase:..." are host wall time of build and
+ * solve phases) and returns the number of records.  hbs_profile_reset clears them.
+ */
+typedef struct hbs_kernel_stat {
+  char name[48];
+  int64_t launches;
+  double ms;
+  double flops;
+  double bytes;
+} hbs_kernel_stat;
+void hbs_profile_enable(int on);
+void hbs_profile_reset(void);
+int hbs_profile_get(hbs_kernel_stat* out, int max);
+int64_t hbs_launch_count(void);
+
 void hbs_free(hbs_handle* h);
 void hbs_result_free(hbs_result* r);
 const char* hbs_last_error(void);

@@ -5,6 +5,8 @@
 #include <string>
 
 #include "dense_kernels.cuh"
+#include "profile.hpp"
+#include "profile.hpp"
 #include "qp_kernels.cuh"
 
 namespace hbs {
@@ -61,7 +63,10 @@ static void load_geometry(Handle& h, const hbs_geometry* geom, cudaStream_t s) {
   HBS_CUDA(cudaMemcpyAsync(h.y.get(), geom->y, N * sizeof(double), kind, s));
   HBS_CUDA(cudaMemcpyAsync(dx.get(), geom->dx, N * sizeof(double), kind, s));
   HBS_CUDA(cudaMemcpyAsync(dy.get(), geom->dy, N * sizeof(double), kind, s));
-  k_geom<<<grid_1d(N), 256, 0, s>>>(dx.get(), dy.get(), h.nx.get(), h.ny.get(), h.w.get(), N);
+  {
+    prof::KScope _ks("k_geom", s);
+    k_geom<<<grid_1d(N), 256, 0, s>>>(dx.get(), dy.get(), h.nx.get(), h.ny.get(), h.w.get(), N);
+  }
   HBS_LAUNCH_CHECK("k_geom");
   h.hx = h.x.download(s);
   h.hy = h.y.download(s);
@@ -71,7 +76,10 @@ static DevGeom geom_view(const hbs_geometry* geom, double omega, DevBuf<double>&
                          DevBuf<double>& w, cudaStream_t s) {
   const int64_t N = geom->n;
   nx.alloc(N); ny.alloc(N); w.alloc(N);
-  k_geom<<<grid_1d(N), 256, 0, s>>>(geom->dx, geom->dy, nx.get(), ny.get(), w.get(), N);
+  {
+    prof::KScope _ks("k_geom", s);
+    k_geom<<<grid_1d(N), 256, 0, s>>>(geom->dx, geom->dy, nx.get(), ny.get(), w.get(), N);
+  }
   HBS_LAUNCH_CHECK("k_geom");
   DevGeom g;
   g.x = geom->x; g.y = geom->y; g.nx = nx.get(); g.ny = ny.get(); g.w = w.get(); g.n = N; g.omega = omega;
@@ -122,7 +130,10 @@ hbs_status hbs_build(const hbs_geometry* geom, double omega, double tol, const h
     load_geometry(h, geom, s);
     for (int64_t i = 0; i < h.N; ++i)
       if (!(std::fabs(h.hx[i]) < 0.5 * h.d)) throw Error(HBS_ERR_INVALID_ARG, "obstacle touches a unit-cell wall");
-    build_hbs(h, s);
+    {
+      prof::Phase ph("build:hbs_compress_invert", s);
+      build_hbs(h, s);
+    }
     build_periodizer(h, s);
     HBS_CUDA(cudaStreamSynchronize(s));
     h.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -239,7 +250,10 @@ hbs_status hbs_kernel_block(const hbs_geometry* geom, double omega, int kind, do
     DevBuf<double> nx, ny, w;
     DevGeom g = geom_view(geom, omega, nx, ny, w, s);
     if (nr * nc > 0) {
-      k_kernel_block<<<grid_1d(nr * nc), 256, 0, s>>>(g, kind, shift_x, rows, nr, cols, nc, static_cast<cplx*>(out));
+      {
+        prof::KScope _ks("k_kernel_block", s);
+        k_kernel_block<<<grid_1d(nr * nc), 256, 0, s>>>(g, kind, shift_x, rows, nr, cols, nc, static_cast<cplx*>(out));
+      }
       HBS_LAUNCH_CHECK("k_kernel_block");
     }
     HBS_CUDA(cudaStreamSynchronize(s));

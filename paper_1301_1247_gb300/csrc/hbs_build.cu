@@ -28,6 +28,7 @@
 #include <numeric>
 
 #include "dense_kernels.cuh"
+#include "profile.hpp"
 #include "handle.hpp"
 #include "zgemm.cuh"
 
@@ -256,7 +257,16 @@ static void launch_gemms(std::vector<GemmJob>& jobs, cudaStream_t s) {
   if (tiles == 0) return;
   DevBuf<GemmJob> dj(jobs.size());
   HBS_CUDA(cudaMemcpyAsync(dj.get(), jobs.data(), jobs.size() * sizeof(GemmJob), cudaMemcpyHostToDevice, s));
-  k_zgemm_batched<<<(unsigned)tiles, 256, 0, s>>>(dj.get(), (int)jobs.size());
+  double fl = 0.0, by = 0.0;
+  for (const auto& j : jobs) {
+    fl += 8.0 * j.m * (double)j.n * j.k;
+    by += 16.0 * ((double)j.m * j.k + (double)j.k * j.n + (double)j.m * j.n *
+                  ((j.beta.x != 0.0 || j.beta.y != 0.0) ? 2.0 : 1.0));
+  }
+  {
+    prof::KScope _ks("k_zgemm_batched", s, fl, by);
+    k_zgemm_batched<<<(unsigned)tiles, 256, 0, s>>>(dj.get(), (int)jobs.size());
+  }
   HBS_LAUNCH_CHECK("k_zgemm_batched");
   HBS_CUDA(cudaStreamSynchronize(s));  // job table is freed on return
 }
@@ -296,9 +306,18 @@ std::vector<int> batched_id(std::vector<CpqrJob>& jobs, cplx* pool, cplx* tpool,
   DevBuf<int> dr(jobs.size());
   size_t sm = (size_t)maxn * (2 * sizeof(double) + sizeof(int));
   if (sm > 48 * 1024) HBS_CUDA(cudaFuncSetAttribute(k_cpqr<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_cpqr<256><<<(unsigned)jobs.size(), 256, sm, s>>>(dj.get(), pool, tpool, permpool, dr.get(), tol, 1 << 30);
+  {
+    prof::KScope _ks("k_cpqr", s);
+    k_cpqr<256><<<(unsigned)jobs.size(), 256, sm, s>>>(dj.get(), pool, tpool, permpool, dr.get(), tol, 1 << 30);
+  }
   HBS_LAUNCH_CHECK("k_cpqr");
   ranks = dr.download(s);
+  double fl = 0.0;
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    const double m = jobs[i].m, n = jobs[i].n, k = ranks[i];
+    fl += 4.0 * (4.0 * m * n * k - 2.0 * (m + n) * k * k + 4.0 / 3.0 * k * k * k) + 4.0 * k * k * (n - k);
+  }
+  prof::add_work("k_cpqr", fl, 0.0);
   return ranks;
 }
 
@@ -310,7 +329,12 @@ void batched_inverse(std::vector<InvJob>& jobs, cplx* pool, cudaStream_t s, cons
   DevBuf<int> dpiv(std::max<int64_t>(piv, 1));
   DevBuf<InvJob> dj = upload_jobs(jobs, s);
   DevBuf<int> flags(jobs.size());
-  k_gj_inverse<256><<<(unsigned)jobs.size(), 256, 0, s>>>(dj.get(), pool, dpiv.get(), flags.get());
+  double fl = 0.0;
+  for (auto& j : jobs) fl += 8.0 * (double)j.n * j.n * j.n;
+  {
+    prof::KScope _ks("k_gj_inverse", s, fl, 0.0);
+    k_gj_inverse<256><<<(unsigned)jobs.size(), 256, 0, s>>>(dj.get(), pool, dpiv.get(), flags.get());
+  }
   HBS_LAUNCH_CHECK("k_gj_inverse");
   auto f = flags.download(s);
   for (int v : f)
@@ -364,7 +388,10 @@ void build_hbs(Handle& h, cudaStream_t s) {
       lv.ntot = o;
       lv.idx.alloc(std::max<int64_t>(o, 1));
       DevBuf<GatherJob> dg = upload_jobs(gj, s);
-      k_gather_skel<<<dim3(1, (unsigned)gj.size()), 128, 0, s>>>(dg.get(), ch.idx.get(), ch.perm.get(), lv.idx.get());
+      {
+        prof::KScope _ks("k_gather_skel", s);
+        k_gather_skel<<<dim3(1, (unsigned)gj.size()), 128, 0, s>>>(dg.get(), ch.idx.get(), ch.perm.get(), lv.idx.get());
+      }
       HBS_LAUNCH_CHECK("k_gather_skel");
       HBS_CUDA(cudaStreamSynchronize(s));
     }
@@ -384,7 +411,10 @@ void build_hbs(Handle& h, cudaStream_t s) {
       std::vector<DJob> dj(1);
       dj[0] = {0, 0, h.nroot, ch.k[0], 0, ch.Dhat.get() + ch.dh_off[0], ch.Dhat.get() + ch.dh_off[1]};
       DevBuf<DJob> ddj = upload_jobs(dj, s);
-      k_fill_d<<<dim3(grid_for((int64_t)h.nroot * h.nroot, 256), 1), 256, 0, s>>>(g, ddj.get(), lv.idx.get(), h.Groot.get());
+      {
+        prof::KScope _ks("k_fill_d", s);
+        k_fill_d<<<dim3(grid_for((int64_t)h.nroot * h.nroot, 256), 1), 256, 0, s>>>(g, ddj.get(), lv.idx.get(), h.Groot.get());
+      }
       HBS_LAUNCH_CHECK("k_fill_d root");
       std::vector<InvJob> ij(1);
       ij[0] = {0, 0, h.nroot, 0};
@@ -397,15 +427,21 @@ void build_hbs(Handle& h, cudaStream_t s) {
 
     // ---- node circles
     lv.cx.alloc(lv.count); lv.cy.alloc(lv.count); lv.rad.alloc(lv.count);
-    k_node_circles<<<lv.count, 128, 0, s>>>(h.x.get(), h.y.get(), N, l, lv.cx.get(), lv.cy.get(), lv.rad.get());
+    {
+      prof::KScope _ks("k_node_circles", s);
+      k_node_circles<<<lv.count, 128, 0, s>>>(h.x.get(), h.y.get(), N, l, lv.cx.get(), lv.cy.get(), lv.rad.get());
+    }
     HBS_LAUNCH_CHECK("k_node_circles");
     lv.h_rad = lv.rad.download(s);
     std::vector<double> hcx = lv.cx.download(s), hcy = lv.cy.download(s);
 
     // ---- near lists
     DevBuf<int64_t> cnt(lv.count);
-    k_near<<<lv.count, 256, 0, s>>>(h.x.get(), h.y.get(), lv.idx.get(), lv.ntot, doff.get(), dn.get(), lv.cx.get(),
-                                    lv.cy.get(), lv.rad.get(), rho, cnt.get(), nullptr, nullptr);
+    {
+      prof::KScope _ks("k_near", s);
+      k_near<<<lv.count, 256, 0, s>>>(h.x.get(), h.y.get(), lv.idx.get(), lv.ntot, doff.get(), dn.get(), lv.cx.get(),
+                                      lv.cy.get(), lv.rad.get(), rho, cnt.get(), nullptr, nullptr);
+    }
     HBS_LAUNCH_CHECK("k_near count");
     std::vector<int64_t> hc = cnt.download(s);
     std::vector<int64_t> noff(lv.count, 0);
@@ -414,8 +450,11 @@ void build_hbs(Handle& h, cudaStream_t s) {
     DevBuf<int64_t> dnoff;
     dnoff.upload(noff, s);
     DevBuf<int64_t> near(std::max<int64_t>(ntot_near, 1));
-    k_near<<<lv.count, 256, 0, s>>>(h.x.get(), h.y.get(), lv.idx.get(), lv.ntot, doff.get(), dn.get(), lv.cx.get(),
-                                    lv.cy.get(), lv.rad.get(), rho, cnt.get(), dnoff.get(), near.get());
+    {
+      prof::KScope _ks("k_near", s);
+      k_near<<<lv.count, 256, 0, s>>>(h.x.get(), h.y.get(), lv.idx.get(), lv.ntot, doff.get(), dn.get(), lv.cx.get(),
+                                      lv.cy.get(), lv.rad.get(), rho, cnt.get(), dnoff.get(), near.get());
+    }
     HBS_LAUNCH_CHECK("k_near fill");
 
     // ---- ID matrices
@@ -432,7 +471,10 @@ void build_hbs(Handle& h, cudaStream_t s) {
     DevBuf<cplx> Y(std::max<int64_t>(ypool, 1));
     {
       DevBuf<YJob> dyj = upload_jobs(yj, s);
-      k_fill_y<<<dim3(64, lv.count), 256, 0, s>>>(g, dyj.get(), lv.idx.get(), near.get(), Y.get());
+      {
+        prof::KScope _ks("k_fill_y", s);
+        k_fill_y<<<dim3(64, lv.count), 256, 0, s>>>(g, dyj.get(), lv.idx.get(), near.get(), Y.get());
+      }
       HBS_LAUNCH_CHECK("k_fill_y");
       std::vector<CpqrJob> cj(lv.count);
       lv.t_off.assign(lv.count, 0);
@@ -467,7 +509,10 @@ void build_hbs(Handle& h, cudaStream_t s) {
         }
       }
       DevBuf<DJob> ddj = upload_jobs(dj, s);
-      k_fill_d<<<dim3(64, lv.count), 256, 0, s>>>(g, ddj.get(), lv.idx.get(), Dinv.get());
+      {
+        prof::KScope _ks("k_fill_d", s);
+        k_fill_d<<<dim3(64, lv.count), 256, 0, s>>>(g, ddj.get(), lv.idx.get(), Dinv.get());
+      }
       HBS_LAUNCH_CHECK("k_fill_d");
       std::vector<InvJob> ij(lv.count);
       for (int j = 0; j < lv.count; ++j) ij[j] = {d_off[j], 0, lv.n[j], j};
@@ -492,9 +537,15 @@ void build_hbs(Handle& h, cudaStream_t s) {
         lp[j] = {Dinv.get() + d_off[j], Yp.get() + lv.f_off[j], pm, T, n, k, n, n, k};
       }
       DevBuf<PJob> drp = upload_jobs(rp, s), dlp = upload_jobs(lp, s);
-      k_right_p<<<dim3(32, lv.count), 256, 0, s>>>(drp.get());
+      {
+        prof::KScope _ks("k_right_p", s);
+        k_right_p<<<dim3(32, lv.count), 256, 0, s>>>(drp.get());
+      }
       HBS_LAUNCH_CHECK("k_right_p");
-      k_left_pt<<<dim3(32, lv.count), 256, 0, s>>>(dlp.get());
+      {
+        prof::KScope _ks("k_left_pt", s);
+        k_left_pt<<<dim3(32, lv.count), 256, 0, s>>>(dlp.get());
+      }
       HBS_LAUNCH_CHECK("k_left_pt");
       for (int j = 0; j < lv.count; ++j) {
         const int n = lv.n[j], k = lv.k[j];
@@ -502,7 +553,10 @@ void build_hbs(Handle& h, cudaStream_t s) {
                  n, k, k, n, k};
       }
       DevBuf<PJob> dlp2 = upload_jobs(lp, s);
-      k_left_pt<<<dim3(32, lv.count), 256, 0, s>>>(dlp2.get());
+      {
+        prof::KScope _ks("k_left_pt", s);
+        k_left_pt<<<dim3(32, lv.count), 256, 0, s>>>(dlp2.get());
+      }
       HBS_LAUNCH_CHECK("k_left_pt S");
       HBS_CUDA(cudaStreamSynchronize(s));
     }

@@ -4,6 +4,7 @@
 // Bragg sampling rows (Remarks 2.2, 2.3), the neighbour interpolative decomposition
 // (Sec. 3.2) as a multi-CTA column-pivoted QR over all N boundary points.
 #include "dense_kernels.cuh"
+#include "profile.hpp"
 #include "handle.hpp"
 #include "qp_kernels.cuh"
 
@@ -341,14 +342,27 @@ int big_row_id(cplx* Mt, int64_t m, int64_t n, double tol, int* perm, cplx* T, i
   const int nparts = 296;
   DevBuf<double> pv(nparts);
   DevBuf<int> pi(nparts);
-  k_bq_norms<<<1184, 256, 0, s>>>(Mt, m, n, nrm.get(), nref.get(), perm);
+  {
+    prof::KScope _ks("k_bq_norms", s);
+    k_bq_norms<<<1184, 256, 0, s>>>(Mt, m, n, nrm.get(), nref.get(), perm);
+  }
   HBS_LAUNCH_CHECK("k_bq_norms");
   const int64_t kcap = std::min<int64_t>(std::min<int64_t>(m, n), max_rank);
   BigQrState hs{};
   for (int64_t step = 0; step < kcap; ++step) {
-    k_bq_argmax<<<nparts, 256, 0, s>>>(nrm.get(), step, n, st.get(), pv.get(), pi.get());
-    k_bq_pivot<<<1, 256, 0, s>>>(Mt, m, step, nrm.get(), nref.get(), perm, pv.get(), pi.get(), nparts, st.get(), tol);
-    k_bq_update<<<1184, 256, 0, s>>>(Mt, m, n, step, nrm.get(), nref.get(), st.get());
+    {
+      prof::KScope _ks("k_bq_argmax", s);
+      k_bq_argmax<<<nparts, 256, 0, s>>>(nrm.get(), step, n, st.get(), pv.get(), pi.get());
+    }
+    {
+      prof::KScope _ks("k_bq_pivot", s);
+      k_bq_pivot<<<1, 256, 0, s>>>(Mt, m, step, nrm.get(), nref.get(), perm, pv.get(), pi.get(), nparts, st.get(), tol);
+    }
+    {
+      prof::KScope _ks("k_bq_update", s, 16.0 * (double)(m - step) * (double)(n - step),
+                       32.0 * (double)(m - step) * (double)(n - step));
+      k_bq_update<<<1184, 256, 0, s>>>(Mt, m, n, step, nrm.get(), nref.get(), st.get());
+    }
     if ((step & 15) == 15) {
       HBS_LAUNCH_CHECK("big qr step");
       HBS_CUDA(cudaMemcpyAsync(&hs, st.get(), sizeof(BigQrState), cudaMemcpyDeviceToHost, s));
@@ -363,7 +377,10 @@ int big_row_id(cplx* Mt, int64_t m, int64_t n, double tol, int* perm, cplx* T, i
   if (!hs.done && k >= max_rank && k < std::min<int64_t>(m, n))
     throw Error(HBS_ERR_RANK, "neighbour interaction rank exceeds the supported maximum");
   if (k > 0 && n > k) {
-    k_bq_tsolve<<<1184, 256, 0, s>>>(Mt, m, n, k, T);
+    {
+      prof::KScope _ks("k_bq_tsolve", s);
+      k_bq_tsolve<<<1184, 256, 0, s>>>(Mt, m, n, k, T);
+    }
     HBS_LAUNCH_CHECK("k_bq_tsolve");
   }
   return k;

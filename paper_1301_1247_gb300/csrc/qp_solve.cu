@@ -20,6 +20,7 @@
 #include <map>
 
 #include "dense_kernels.cuh"
+#include "profile.hpp"
 #include "qp_kernels.cuh"
 
 namespace hbs {
@@ -90,6 +91,8 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     rsrc = std::min(rsrc, std::hypot(h.hx[i] + d - cx, h.hy[i] - cy));
   }
 
+  prof::PhaseSeq ph(s);
+  ph.next("build:neighbour_id");
   // ---- neighbour proxy circle and near points (Sec. 3.2)
   double R = h.opts.nb_radius;
   if (!(R > 0.0)) R = rsrc > 1.05 * rmax ? 0.5 * (rmax + rsrc) : 1.1 * rmax;
@@ -119,7 +122,10 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     dnm.upload(near_m, s);
     dnp.upload(near_p, s);
     DevBuf<cplx> Mt(m * N);
-    k_fill_nb<<<grid_1d(m * N), 256, 0, s>>>(g, dnm.get(), nm, dnp.get(), npn, d, cx, cy, R, np, wp, Mt.get());
+    {
+      prof::KScope _ks("k_fill_nb", s);
+      k_fill_nb<<<grid_1d(m * N), 256, 0, s>>>(g, dnm.get(), nm, dnp.get(), npn, d, cx, cy, R, np, wp, Mt.get());
+    }
     HBS_LAUNCH_CHECK("k_fill_nb");
     DevBuf<int> perm(N);
     const int kcap = (int)std::min<int64_t>(m, 4096);
@@ -132,17 +138,24 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     h.Rm.alloc(std::max<int64_t>((int64_t)l * N, 1));
     h.Rp.alloc(std::max<int64_t>((int64_t)l * N, 1));
     if (l > 0) {
-      k_fill_r<<<grid_1d((int64_t)l * N), 256, 0, s>>>(g, h.nb_skel.get(), l, d, h.Rm.get(), h.Rp.get());
+      {
+        prof::KScope _ks("k_fill_r", s);
+        k_fill_r<<<grid_1d((int64_t)l * N), 256, 0, s>>>(g, h.nb_skel.get(), l, d, h.Rm.get(), h.Rp.get());
+      }
       HBS_LAUNCH_CHECK("k_fill_r");
     }
     h.Pnb.alloc(std::max<int64_t>((int64_t)l * N, 1));
     if (l > 0) {
-      k_build_p<<<grid_1d((int64_t)l * N), 256, 0, s>>>(perm.get(), T.get(), N, l, h.Pnb.get());
+      {
+        prof::KScope _ks("k_build_p", s);
+        k_build_p<<<grid_1d((int64_t)l * N), 256, 0, s>>>(perm.get(), T.get(), N, l, h.Pnb.get());
+      }
       HBS_LAUNCH_CHECK("k_build_p");
     }
     HBS_CUDA(cudaStreamSynchronize(s));
   }
   const int l = h.nb_rank;
+  ph.next("build:periodizer_fill");
 
   // ---- Sommerfeld contours (Sec. 2.3)
   h.cc = h.opts.contour_c > 0 ? h.opts.contour_c : 2.0;
@@ -171,8 +184,11 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   const int S = h.S;
   h.Esamp.alloc((size_t)12 * S * N);
   for (int jj = 0; jj < 3; ++jj) {
-    k_fill_samples<<<grid_1d((int64_t)4 * S * N), 256, 0, s>>>(g, S, d, h.y0, (jj - 1) * d, h.Esamp.get() + 4 * S * jj,
-                                                                 12 * S);
+    {
+      prof::KScope _ks("k_fill_samples", s);
+      k_fill_samples<<<grid_1d((int64_t)4 * S * N), 256, 0, s>>>(g, S, d, h.y0, (jj - 1) * d, h.Esamp.get() + 4 * S * jj,
+                                                                   12 * S);
+    }
     HBS_LAUNCH_CHECK("k_fill_samples");
   }
 
@@ -183,20 +199,33 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   for (int c = 0; c < nc; ++c) {
     ContourData& cd = h.contours[c];
     cd.col_off = l + (int64_t)4 * M * c;
-    k_fill_b<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), cd.dwk.get(), M, d, h.W.get(), N, cd.col_off,
-                                                      cd.col_off + 2 * M, 0, cmk(0, 0));
+    {
+      prof::KScope _ks("k_fill_b", s);
+      k_fill_b<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), cd.dwk.get(), M, d, h.W.get(), N, cd.col_off,
+                                                        cd.col_off + 2 * M, 0, cmk(0, 0));
+    }
     HBS_LAUNCH_CHECK("k_fill_b");
     cd.CL.alloc((size_t)2 * M * N);
     cd.CR.alloc((size_t)2 * M * N);
-    k_fill_c<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), M, d, -0.5 * d, cd.CL.get(), 2 * M);
-    k_fill_c<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), M, -d, 0.5 * d, cd.CR.get(), 2 * M);
+    {
+      prof::KScope _ks("k_fill_c", s);
+      k_fill_c<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), M, d, -0.5 * d, cd.CL.get(), 2 * M);
+    }
+    {
+      prof::KScope _ks("k_fill_c", s);
+      k_fill_c<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), M, -d, 0.5 * d, cd.CR.get(), 2 * M);
+    }
     HBS_LAUNCH_CHECK("k_fill_c");
     cd.SL.alloc((size_t)4 * S * 2 * M);
     cd.SR.alloc((size_t)4 * S * 2 * M);
-    k_fill_wall_samples<<<grid_1d((int64_t)4 * S * M), 256, 0, s>>>(cd.dk.get(), cd.dwk.get(), M, S, d, h.y0, omega,
-                                                                     cd.SL.get(), cd.SR.get());
+    {
+      prof::KScope _ks("k_fill_wall_samples", s);
+      k_fill_wall_samples<<<grid_1d((int64_t)4 * S * M), 256, 0, s>>>(cd.dk.get(), cd.dwk.get(), M, S, d, h.y0, omega,
+                                                                       cd.SL.get(), cd.SR.get());
+    }
     HBS_LAUNCH_CHECK("k_fill_wall_samples");
   }
+  ph.next("build:W_apply");
   {
     const int64_t chunk = 256;
     DevBuf<cplx> tmp((size_t)N * chunk);
@@ -207,6 +236,7 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     }
   }
   // ---- Z_c = Rows_c W_c
+  ph.next("build:Z_products");
   const int zr = 2 * l + 4 * M + 12 * S, zcn = l + 4 * M;
   for (int c = 0; c < nc; ++c) {
     ContourData& cd = h.contours[c];
@@ -714,6 +744,8 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
     }
     const int ng = (int)gjobs.size();
     const int64_t N = h.N;
+    prof::PhaseSeq ph(s);
+    ph.next("solve:rhs_apply");
     // ---- right-hand sides, applies
     DevBuf<cplx> RHS((size_t)N * cols), X((size_t)N * cols);
     {
@@ -727,7 +759,10 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
         DevBuf<RhsCol> dr;
         dr.upload(std::vector<RhsCol>(rcols.begin() + rc, rcols.begin() + rc + G.q + G.nw), s);
         rc += G.q + G.nw;
-        k_fill_rhs<<<grid_1d(N * (G.q + G.nw)), 256, 0, s>>>(g, dr.get(), G.q + G.nw, RHS.get() + pos * N);
+        {
+          prof::KScope _ks("k_fill_rhs", s);
+          k_fill_rhs<<<grid_1d(N * (G.q + G.nw)), 256, 0, s>>>(g, dr.get(), G.q + G.nw, RHS.get() + pos * N);
+        }
         HBS_LAUNCH_CHECK("k_fill_rhs");
         HBS_CUDA(cudaStreamSynchronize(s));
         pos += G.q + G.nw;
@@ -735,12 +770,21 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
           // L = [alpha^{-1} P | alpha P], B(alpha) = B_L + alpha B_R
           const cplx ia = cdiv(cmk(1, 0), G.alpha);
           if (l > 0) {
-            k_scaled_copy<<<grid_1d(N * l), 256, 0, s>>>(h.Pnb.get(), N * (int64_t)l, ia, RHS.get() + pos * N);
-            k_scaled_copy<<<grid_1d(N * l), 256, 0, s>>>(h.Pnb.get(), N * (int64_t)l, G.alpha, RHS.get() + (pos + l) * N);
+            {
+              prof::KScope _ks("k_scaled_copy", s);
+              k_scaled_copy<<<grid_1d(N * l), 256, 0, s>>>(h.Pnb.get(), N * (int64_t)l, ia, RHS.get() + pos * N);
+            }
+            {
+              prof::KScope _ks("k_scaled_copy", s);
+              k_scaled_copy<<<grid_1d(N * l), 256, 0, s>>>(h.Pnb.get(), N * (int64_t)l, G.alpha, RHS.get() + (pos + l) * N);
+            }
           }
           const ContourData& cd = h.contours[G.contour];
-          k_fill_b<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), cd.dwk.get(), M, d, RHS.get(), N, pos + 2 * l,
-                                                            0, 1, G.alpha);
+          {
+            prof::KScope _ks("k_fill_b", s);
+            k_fill_b<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), cd.dwk.get(), M, d, RHS.get(), N, pos + 2 * l,
+                                                              0, 1, G.alpha);
+          }
           HBS_LAUNCH_CHECK("plain fills");
           pos += 2 * l + 2 * M;
         }
@@ -749,6 +793,7 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
     h.apply_inverse(RHS.get(), X.get(), cols, s);
     RHS.release();
     // ---- Proj = Rows X
+    ph.next("solve:projections");
     DevBuf<cplx> Proj((size_t)zr * cols);
     {
       std::vector<GemmJob> gj;
@@ -777,6 +822,7 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
       }
     }
     // ---- Schur systems
+    ph.next("solve:schur");
     int64_t so = 0, ro = 0;
     for (auto& G : gjobs) {
       const int nS = 2 * l + 2 * M + G.nw;
@@ -787,12 +833,24 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
     DevBuf<GroupJob> dg;
     dg.upload(gjobs, s);
     Dims D{l, M, S, zr, d, omega, zr};
-    k_assemble<<<dim3(64, ng), 256, 0, s>>>(D, dg.get(), Proj.get(), h.y0, Sp.get(), Rp.get());
+    {
+      prof::KScope _ks("k_assemble", s);
+      k_assemble<<<dim3(64, ng), 256, 0, s>>>(D, dg.get(), Proj.get(), h.y0, Sp.get(), Rp.get());
+    }
     HBS_LAUNCH_CHECK("k_assemble");
     DevBuf<int> ill(ng);
-    k_schur_solve<256><<<ng, 256, 0, s>>>(D, dg.get(), Sp.get(), Rp.get(), ill.get());
+    double sfl = 0.0;
+    for (auto& G : gjobs) {
+      const double n = 2.0 * l + 2.0 * M + G.nw;
+      sfl += 8.0 / 3.0 * n * n * n + 8.0 * n * n * G.q;
+    }
+    {
+      prof::KScope _ks("k_schur_solve", s, sfl, 0.0);
+      k_schur_solve<256><<<ng, 256, 0, s>>>(D, dg.get(), Sp.get(), Rp.get(), ill.get());
+    }
     HBS_LAUNCH_CHECK("k_schur_solve");
     // ---- Bragg amplitudes
+    ph.next("solve:bragg");
     int64_t oo = 0;
     for (int gg = 0; gg < ng; ++gg) {
       const auto& mem = *gmembers[gg];
@@ -815,8 +873,11 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
     da.upload(ajobs, s);
     DevBuf<cplx> cbuf(std::max<int64_t>(oo, 1)), dbuf(std::max<int64_t>(oo, 1));
     DevBuf<double> fbuf(ajobs.size());
-    k_bragg<<<(unsigned)ajobs.size(), 128, 2 * S * sizeof(cplx), s>>>(D, dg.get(), da.get(), Proj.get(), Rp.get(), h.y0,
-                                                                      cbuf.get(), dbuf.get(), fbuf.get());
+    {
+      prof::KScope _ks("k_bragg", s);
+      k_bragg<<<(unsigned)ajobs.size(), 128, 2 * S * sizeof(cplx), s>>>(D, dg.get(), da.get(), Proj.get(), Rp.get(), h.y0,
+                                                                        cbuf.get(), dbuf.get(), fbuf.get());
+    }
     HBS_LAUNCH_CHECK("k_bragg");
     auto hc = cbuf.download(s), hd = dbuf.download(s);
     auto hf = fbuf.download(s);

@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "RANK", 5: "W
 # Every entry point declared in include/hbsqp.h.
 EXPORTED = ("hbs_default_options", "hbs_build", "hbs_solve", "hbs_solve_plain", "hbs_bragg_amplitudes",
             "hbs_result_angle_info", "hbs_info", "hbs_apply_inverse", "hbs_kernel_block", "hbs_row_id",
+            "hbs_profile_enable", "hbs_profile_reset", "hbs_profile_get", "hbs_launch_count",
             "hbs_free", "hbs_result_free", "hbs_last_error")
 
 
@@ -51,6 +52,11 @@ class Info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -75,6 +81,14 @@ def lib():
     L.hbs_apply_inverse.argtypes = [vp, vp, vp, i64, vp]
     L.hbs_kernel_block.argtypes = [ctypes.POINTER(Geometry), dbl, ci, dbl, vp, i64, vp, i64, vp, vp]
     L.hbs_row_id.argtypes = [vp, i64, i64, dbl, ctypes.POINTER(ci), vp, vp, vp]
+    L.hbs_profile_enable.argtypes = [ci]
+    L.hbs_profile_enable.restype = None
+    L.hbs_profile_reset.argtypes = []
+    L.hbs_profile_reset.restype = None
+    L.hbs_profile_get.argtypes = [ctypes.POINTER(KernelStat), ci]
+    L.hbs_profile_get.restype = ci
+    L.hbs_launch_count.argtypes = []
+    L.hbs_launch_count.restype = i64
     L.hbs_free.argtypes = [vp]
     L.hbs_free.restype = None
     L.hbs_result_free.argtypes = [vp]
@@ -162,15 +176,23 @@ class Handle:
     """A built solver (hbs_build)."""
 
     def __init__(self, x, y, dx, dy, d, omega, tol, opts: Options | None = None, stream=None):
-        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, dx, dy)]
-        self._keep = arrs
-        g = Geometry(len(arrs[0]), float(d), *[a.ctypes.data for a in arrs], 0)
+        """Geometry arrays are host numpy arrays, or float64 CUDA tensors (device-resident input)."""
+        if hasattr(x, "data_ptr"):
+            arrs = [x, y, dx, dy]
+            self._keep = arrs
+            g = Geometry(int(x.numel()), float(d), *[a.data_ptr() for a in arrs], 1)
+            n = int(x.numel())
+        else:
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, dx, dy)]
+            self._keep = arrs
+            g = Geometry(len(arrs[0]), float(d), *[a.ctypes.data for a in arrs], 0)
+            n = len(arrs[0])
         out = ctypes.c_void_p()
         st = lib().hbs_build(ctypes.byref(g), float(omega), float(tol),
                              ctypes.byref(opts) if opts is not None else None, _stream(stream), ctypes.byref(out))
         _check(st, "hbs_build")
         self._p = out
-        self.n = len(arrs[0])
+        self.n = n
 
     def __del__(self):
         if getattr(self, "_p", None):
@@ -217,3 +239,24 @@ def row_id(mt, m, n, tol, perm, t, stream=None) -> int:
     _check(lib().hbs_row_id(_ptr(mt), int(m), int(n), float(tol), ctypes.byref(rank), _ptr(perm), _ptr(t),
                             _stream(stream)), "hbs_row_id")
     return rank.value
+
+
+def profile_enable(on: bool = True):
+    lib().hbs_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    lib().hbs_profile_reset()
+
+
+def profile_get() -> dict:
+    """Per-kernel records {name: dict(launches, ms, flops, bytes)} (host phases are 'phase:...')."""
+    n = lib().hbs_profile_get(None, 0)
+    arr = (KernelStat * max(n, 1))()
+    n = lib().hbs_profile_get(arr, n)
+    return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms, flops=arr[i].flops,
+                                        bytes=arr[i].bytes) for i in range(n)}
+
+
+def launch_count() -> int:
+    return int(lib().hbs_launch_count())
