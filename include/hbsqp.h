@@ -194,6 +194,28 @@ void hbs_profile_reset(void);
 int hbs_profile_get(hbs_kernel_stat* out, int max);
 int64_t hbs_launch_count(void);
 
+/*
+ * Allocation-free interpolative decomposition.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory during the
+ * call (a fixed, pre-reserved memory budget; code that cannot wait for cudaMalloc /
+ * cudaFree, which synchronize the device; a foreign allocator in charge of memory).
+ *
+ * Same inputs, outputs and result as hbs_row_id, computed by the multi-CTA pivoted
+ * QR, but its working arrays live in one fixed device array that the library
+ * reserves on every GPU that loads it (about 4 MiB, kept until the process exits).
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ *  - n may not exceed HBS_ROW_ID_STATIC_MAX_N columns; larger n returns
+ *    HBS_ERR_INVALID_ARG.
+ *  - The first call on a device looks up the array's device address (with that
+ *    device current); make that first call before any CUDA graph capture.
+ *  - All calls share the one array and it keeps the last call's contents: two
+ *    calls that overlap on the GPU (different streams, or different host threads)
+ *    race and give wrong results.  Serialise them.
+ */
+#define HBS_ROW_ID_STATIC_MAX_N 262144
+hbs_status hbs_row_id_static(void* mt, int64_t m, int64_t n, double tol, int* rank, int* perm,
+                             void* t, void* stream);
+
 void hbs_free(hbs_handle* h);
 void hbs_result_free(hbs_result* r);
 const char* hbs_last_error(void);

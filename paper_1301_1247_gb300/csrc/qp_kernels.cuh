@@ -37,6 +37,13 @@ __global__ void k_fill_nb(DevGeom g, const int64_t* near_m, int nm, const int64_
 __global__ void k_fill_r(DevGeom g, const int64_t* J, int l, double d, cplx* Rm, cplx* Rp);
 __global__ void k_build_p(const int* perm, const cplx* T, int64_t N, int l, cplx* P);
 int big_row_id(cplx* Mt, int64_t m, int64_t n, double tol, int* perm, cplx* T, int max_rank, cudaStream_t s);
+__global__ void k_bq_norms(const cplx* A, int64_t m, int64_t n, double* nrm, double* nref, int* perm);
+__global__ void k_bq_argmax(const double* nrm, int64_t s, int64_t n, const BigQrState* st, double* pv, int* pi);
+__global__ void k_bq_pivot(cplx* A, int64_t m, int64_t s, double* nrm, double* nref, int* perm, const double* pv,
+                           const int* pi, int nparts, BigQrState* st, double tol);
+__global__ void k_bq_update(cplx* A, int64_t m, int64_t n, int64_t s, double* nrm, double* nref,
+                            const BigQrState* st);
+__global__ void k_bq_tsolve(const cplx* A, int64_t m, int64_t n, int k, cplx* T);
 
 // qp_solve.cu
 void build_periodizer(Handle& h, cudaStream_t s);

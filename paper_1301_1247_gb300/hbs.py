@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "RANK", 5: "W
 # Every entry point declared in include/hbsqp.h.
 EXPORTED = ("hbs_default_options", "hbs_build", "hbs_solve", "hbs_solve_plain", "hbs_bragg_amplitudes",
             "hbs_result_angle_info", "hbs_info", "hbs_apply_inverse", "hbs_kernel_block", "hbs_row_id",
+            "hbs_row_id_static",
             "hbs_profile_enable", "hbs_profile_reset", "hbs_profile_get", "hbs_launch_count",
             "hbs_free", "hbs_result_free", "hbs_last_error")
 
@@ -81,6 +82,7 @@ def lib():
     L.hbs_apply_inverse.argtypes = [vp, vp, vp, i64, vp]
     L.hbs_kernel_block.argtypes = [ctypes.POINTER(Geometry), dbl, ci, dbl, vp, i64, vp, i64, vp, vp]
     L.hbs_row_id.argtypes = [vp, i64, i64, dbl, ctypes.POINTER(ci), vp, vp, vp]
+    L.hbs_row_id_static.argtypes = [vp, i64, i64, dbl, ctypes.POINTER(ci), vp, vp, vp]
     L.hbs_profile_enable.argtypes = [ci]
     L.hbs_profile_enable.restype = None
     L.hbs_profile_reset.argtypes = []
@@ -96,7 +98,7 @@ def lib():
     L.hbs_last_error.argtypes = []
     L.hbs_last_error.restype = ctypes.c_char_p
     for name in ("hbs_build", "hbs_solve", "hbs_solve_plain", "hbs_bragg_amplitudes", "hbs_result_angle_info",
-                 "hbs_info", "hbs_apply_inverse", "hbs_kernel_block", "hbs_row_id"):
+                 "hbs_info", "hbs_apply_inverse", "hbs_kernel_block", "hbs_row_id", "hbs_row_id_static"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -238,6 +240,19 @@ def row_id(mt, m, n, tol, perm, t, stream=None) -> int:
     rank = ctypes.c_int()
     _check(lib().hbs_row_id(_ptr(mt), int(m), int(n), float(tol), ctypes.byref(rank), _ptr(perm), _ptr(t),
                             _stream(stream)), "hbs_row_id")
+    return rank.value
+
+
+ROW_ID_STATIC_MAX_N = 262144
+
+
+def row_id_static(mt, m, n, tol, perm, t, stream=None) -> int:
+    """hbs_row_id_static: the same decomposition as row_id with no device allocation during the
+    call (its working arrays sit in a fixed array the library reserves per GPU); n is limited
+    to ROW_ID_STATIC_MAX_N and overlapping calls must not run concurrently."""
+    rank = ctypes.c_int()
+    _check(lib().hbs_row_id_static(_ptr(mt), int(m), int(n), float(tol), ctypes.byref(rank), _ptr(perm), _ptr(t),
+                                   _stream(stream)), "hbs_row_id_static")
     return rank.value
 
 
