@@ -89,6 +89,9 @@ typedef struct hbs_info_t {
   double y0;             /* Bragg sampling height */
   double nb_radius;      /* neighbour proxy circle radius */
   int nb_proxies;        /* neighbour proxy points */
+  int pid_col_rank;      /* skeleton columns kept of the wall blocks B_L, B_R (all contours) */
+  int pid_row_rank;      /* skeleton rows kept of C_L, C_R and of the Bragg sampling rows */
+  double pid_residual;   /* relative error of those decompositions on an independent point sample */
 } hbs_info_t;
 
 /* Fill `opts` with the defaults listed above. */

@@ -19,7 +19,8 @@ size_t Handle::device_bytes() const {
   for (const auto& lv : levels)
     b += lv.idx.bytes() + lv.perm.bytes() + lv.T.bytes() + lv.E.bytes() + lv.F.bytes() + lv.G.bytes() +
          lv.Dhat.bytes() + lv.cx.bytes() + lv.cy.bytes() + lv.rad.bytes();
-  b += nb_skel.bytes() + Pnb.bytes() + Rm.bytes() + Rp.bytes() + Esamp.bytes() + W.bytes();
+  b += nb_skel.bytes() + Pnb.bytes() + Rm.bytes() + Rp.bytes() + Esamp.bytes() + W.bytes() + TY.bytes() + TC.bytes() +
+       TE.bytes() + Rsel.bytes();
   for (const auto& c : contours)
     b += c.dk.bytes() + c.dwk.bytes() + c.CL.bytes() + c.CR.bytes() + c.SL.bytes() + c.SR.bytes() + c.Zd.bytes();
   return b;
@@ -225,6 +226,9 @@ hbs_status hbs_info(const hbs_handle* hh, hbs_info_t* info) {
   info->y0 = h.y0;
   info->nb_radius = h.nb_R;
   info->nb_proxies = h.nb_np;
+  info->pid_col_rank = h.rB;
+  info->pid_row_rank = h.rC + h.rE;
+  info->pid_residual = h.pid_residual;
   return HBS_OK;
 }
 

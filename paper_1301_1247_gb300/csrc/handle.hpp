@@ -42,6 +42,8 @@ struct ContourData {
   // small products: rows [R_-1; R_1; C_L; C_R; E_-1; E_0; E_1] times columns [W_P | W_BL | W_BR]
   DevBuf<cplx> Zd;  // column-major (zr x zc)
   int zr = 0, zc = 0;
+  // Recipes that expand compressed rows (Rsel) / columns (W) to this contour's rows / columns.
+  DevBuf<int2> row_recipe, col_recipe;
 };
 
 struct Handle {
@@ -72,8 +74,14 @@ struct Handle {
   int M = 0;
   double ch = 0.0, cc = 2.0, cw = 2.0, cK = 0.0;
   std::vector<ContourData> contours;
-  DevBuf<cplx> W;              // N x (l + 4 M * n_contours)
+  DevBuf<cplx> W;              // N x (l + rB): A^{-1} [P | skeleton columns of B]
   int64_t wcols = 0;
+  // Interpolative decompositions of the periodizer blocks over all contours:
+  //   columns Y = [B_L^0 | B_R^0 | ...] ~ Y(:, JY) [I | TY],  rows C = [C_L^0; C_R^0; ...] and E
+  //   ~ rows IC / IE expanded by TC / TE.  Rsel = [R_-1; R_1; C(IC, :); E(IE, :)] (rsel x N).
+  int rB = 0, rC = 0, rE = 0, rsel = 0;
+  DevBuf<cplx> TY, TC, TE, Rsel;
+  double pid_residual = 0.0;
 
   double build_seconds = 0.0;
   size_t device_bytes() const;

@@ -387,3 +387,120 @@ int big_row_id(cplx* Mt, int64_t m, int64_t n, double tol, int* perm, cplx* T, i
 }
 
 }  // namespace hbs
+
+namespace hbs {
+
+// ---------------------------------------------------------------------------
+// Compression of the periodizer blocks by interpolative decompositions computed on a
+// subsample of the boundary points (their columns and rows are smooth functions of the
+// boundary point, so the decomposition found on a fine subsample holds on all N points;
+// a second, disjoint subsample checks it).
+// ---------------------------------------------------------------------------
+
+// out[i + c ldo] = src[sub[i] + c lds]: rows `sub` of src (all ncol columns).
+__global__ void k_gather_subrows(const cplx* src, int64_t lds, const int64_t* sub, int ns, int ncol, cplx* out,
+                                 int64_t ldo) {
+  const int64_t tot = (int64_t)ns * ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % ns);
+    const int64_t c = e / ns;
+    out[i + c * ldo] = src[sub[i] + c * lds];
+  }
+}
+
+// out[i + (col0 + r) ldo] = src[r + sub[i] lds] for r < nrows: columns `sub` of src, transposed.
+__global__ void k_gather_subcols_t(const cplx* src, int64_t lds, int nrows, const int64_t* sub, int ns, cplx* out,
+                                   int64_t ldo, int col0) {
+  const int64_t tot = (int64_t)ns * nrows;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % ns);
+    const int r = (int)(e / ns);
+    out[i + (int64_t)(col0 + r) * ldo] = src[r + sub[i] * lds];
+  }
+}
+
+// out[t + j ldo] = refs[t].base[j refs[t].ld]: selected rows of several matrices, stacked.
+__global__ void k_gather_rowrefs(const RowRef* refs, int nsel, int64_t ncol, cplx* out, int64_t ldo) {
+  const int64_t tot = (int64_t)nsel * ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int t = (int)(e % nsel);
+    const int64_t j = e / nsel;
+    out[t + j * ldo] = refs[t].base[j * refs[t].ld];
+  }
+}
+
+// Row expansion by recipe: out[o, c] = in[idx, c] (kind 0), or
+// sum_i T1[i, idx] in[off1 + i, c] (kind 1), or sum_i T2[i, idx] in[off2 + i, c] (kind 2).
+__global__ void k_expand_rows(const cplx* in, int64_t ldi, int ncol, const int2* recipe, int nout, const cplx* T1,
+                              int r1, int off1, const cplx* T2, int r2, int off2, cplx* out, int64_t ldo) {
+  const int64_t tot = (int64_t)nout * ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int o = (int)(e % nout);
+    const int64_t c = e / nout;
+    const int2 rc = recipe[o];
+    const cplx* col = in + c * ldi;
+    cplx v;
+    if (rc.x == 0) {
+      v = col[rc.y];
+    } else {
+      const cplx* T = rc.x == 1 ? T1 : T2;
+      const int r = rc.x == 1 ? r1 : r2, off = rc.x == 1 ? off1 : off2;
+      const cplx* tc = T + (int64_t)rc.y * r;
+      v = cmk(0, 0);
+      for (int i = 0; i < r; ++i) v = cfma(tc[i], col[off + i], v);
+    }
+    out[o + c * ldo] = v;
+  }
+}
+
+// Column expansion by recipe: out[:, o] = in[:, idx] (kind 0), or sum_i T[i, idx] in[:, col(i)]
+// with col(i) = skel ? skel[i] : off + i (kind 1).
+__global__ void k_expand_cols(const cplx* in, int64_t ldi, int nrow, const int2* recipe, int nout, const cplx* T, int r,
+                              int off, const int* skel, cplx* out, int64_t ldo) {
+  const int64_t tot = (int64_t)nrow * nout;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int rw = (int)(e % nrow);
+    const int o = (int)(e / nrow);
+    const int2 rc = recipe[o];
+    cplx v;
+    if (rc.x == 0) {
+      v = in[rw + (int64_t)rc.y * ldi];
+    } else {
+      const cplx* tc = T + (int64_t)rc.y * r;
+      v = cmk(0, 0);
+      for (int i = 0; i < r; ++i) {
+        const int cc = skel ? skel[i] : off + i;
+        v = cfma(tc[i], in[rw + (int64_t)cc * ldi], v);
+      }
+    }
+    out[rw + (int64_t)o * ldo] = v;
+  }
+}
+
+// acc[0] += |a - b|^2, acc[1] += |b|^2 over an nrow x ncol block.
+__global__ void k_diff_norm2(const cplx* a, int64_t lda, const cplx* b, int64_t ldb, int nrow, int ncol, double* acc) {
+  __shared__ double red[2][32];
+  double s0 = 0.0, s1 = 0.0;
+  const int64_t tot = (int64_t)nrow * ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int rw = (int)(e % nrow);
+    const int64_t c = e / nrow;
+    const cplx x = a[rw + c * lda], y = b[rw + c * ldb];
+    s0 += cabs2(csub(x, y));
+    s1 += cabs2(y);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = s0; red[1][threadIdx.x >> 5] = s1; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t0 += red[0][w]; t1 += red[1][w]; }
+    atomicAdd(&acc[0], t0);
+    atomicAdd(&acc[1], t1);
+  }
+}
+
+}  // namespace hbs

@@ -45,6 +45,21 @@ __global__ void k_bq_update(cplx* A, int64_t m, int64_t n, int64_t s, double* nr
                             const BigQrState* st);
 __global__ void k_bq_tsolve(const cplx* A, int64_t m, int64_t n, int k, cplx* T);
 
+struct RowRef {
+  const cplx* base;  // first element of the row
+  int64_t ld;        // stride between consecutive columns
+};
+__global__ void k_gather_subrows(const cplx* src, int64_t lds, const int64_t* sub, int ns, int ncol, cplx* out,
+                                 int64_t ldo);
+__global__ void k_gather_subcols_t(const cplx* src, int64_t lds, int nrows, const int64_t* sub, int ns, cplx* out,
+                                   int64_t ldo, int col0);
+__global__ void k_gather_rowrefs(const RowRef* refs, int nsel, int64_t ncol, cplx* out, int64_t ldo);
+__global__ void k_expand_rows(const cplx* in, int64_t ldi, int ncol, const int2* recipe, int nout, const cplx* T1,
+                              int r1, int off1, const cplx* T2, int r2, int off2, cplx* out, int64_t ldo);
+__global__ void k_expand_cols(const cplx* in, int64_t ldi, int nrow, const int2* recipe, int nout, const cplx* T, int r,
+                              int off, const int* skel, cplx* out, int64_t ldo);
+__global__ void k_diff_norm2(const cplx* a, int64_t lda, const cplx* b, int64_t ldb, int nrow, int ncol, double* acc);
+
 // qp_solve.cu
 void build_periodizer(Handle& h, cudaStream_t s);
 void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, Result& out, cudaStream_t s);

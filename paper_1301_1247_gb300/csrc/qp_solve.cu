@@ -192,16 +192,15 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     HBS_LAUNCH_CHECK("k_fill_samples");
   }
 
-  // ---- W = A^{-1} [P | B_L^c | B_R^c ...]
-  h.wcols = l + (int64_t)4 * M * nc;
-  h.W.alloc((size_t)N * h.wcols);
-  if (l > 0) HBS_CUDA(cudaMemcpyAsync(h.W.get(), h.Pnb.get(), sizeof(cplx) * N * l, cudaMemcpyDeviceToDevice, s));
+  // ---- periodizer fills: Y = [B_L^c | B_R^c ...] (N x 4M nc), C_L^c, C_R^c, wall samples
+  const int ny = 4 * M * nc;
+  DevBuf<cplx> Yfull((size_t)N * ny);
   for (int c = 0; c < nc; ++c) {
     ContourData& cd = h.contours[c];
-    cd.col_off = l + (int64_t)4 * M * c;
+    cd.col_off = (int64_t)4 * M * c;
     {
       prof::KScope _ks("k_fill_b", s);
-      k_fill_b<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), cd.dwk.get(), M, d, h.W.get(), N, cd.col_off,
+      k_fill_b<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), cd.dwk.get(), M, d, Yfull.get(), N, cd.col_off,
                                                         cd.col_off + 2 * M, 0, cmk(0, 0));
     }
     HBS_LAUNCH_CHECK("k_fill_b");
@@ -225,37 +224,169 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     }
     HBS_LAUNCH_CHECK("k_fill_wall_samples");
   }
+
+  // ---- interpolative decompositions of the periodizer blocks on a subsample of points
+  ph.next("build:periodizer_id");
+  const int ns = (int)std::min<int64_t>(N, 8192);
+  std::vector<int64_t> hsub(ns), hsub2(ns);
+  for (int i = 0; i < ns; ++i) {
+    hsub[i] = (int64_t)((double)i * N / ns);
+    hsub2[i] = std::min<int64_t>(N - 1, (int64_t)(((double)i + 0.5) * N / ns));
+  }
+  DevBuf<int64_t> dsub, dsub2;
+  dsub.upload(hsub, s);
+  dsub2.upload(hsub2, s);
+  const double ptol = std::min(0.1 * h.tol, 1e-13);
+  const int nce = 12 * S;
+  // IDs: returns rank, fills perm (host), T (device), and the check residual on the second subsample.
+  auto subsample_id = [&](auto&& gather, int ncols, std::vector<int>& hperm, DevBuf<cplx>& Tout) -> int {
+    DevBuf<cplx> A((size_t)ns * ncols), A2((size_t)ns * ncols);
+    gather(dsub.get(), A.get());
+    gather(dsub2.get(), A2.get());
+    DevBuf<int> perm(ncols);
+    DevBuf<cplx> T((size_t)std::min(ns, ncols) * ncols);
+    int r = big_row_id(A.get(), ns, ncols, ptol, perm.get(), T.get(), std::min(ns, ncols), s);
+    hperm = perm.download(s);
+    Tout.alloc(std::max<int64_t>((int64_t)r * (ncols - r), 1));
+    if ((int64_t)r * (ncols - r) > 0)
+      HBS_CUDA(cudaMemcpyAsync(Tout.get(), T.get(), sizeof(cplx) * r * (ncols - r), cudaMemcpyDeviceToDevice, s));
+    // check on the second subsample: columns rebuilt from the skeleton columns
+    std::vector<int2> rec(ncols);
+    std::vector<int> inv(ncols);
+    for (int p = 0; p < ncols; ++p) inv[hperm[p]] = p;
+    for (int a = 0; a < ncols; ++a) rec[a] = inv[a] < r ? make_int2(0, a) : make_int2(1, inv[a] - r);
+    DevBuf<int2> drec;
+    drec.upload(rec, s);
+    DevBuf<int> dperm;
+    dperm.upload(hperm, s);
+    DevBuf<cplx> B2((size_t)ns * ncols);
+    {
+      prof::KScope _ks("k_expand_cols", s);
+      k_expand_cols<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(A2.get(), ns, ns, drec.get(), ncols, Tout.get(), r, 0,
+                                                                  dperm.get(), B2.get(), ns);
+    }
+    DevBuf<double> acc(2);
+    HBS_CUDA(cudaMemsetAsync(acc.get(), 0, 2 * sizeof(double), s));
+    {
+      prof::KScope _ks("k_diff_norm2", s);
+      k_diff_norm2<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(B2.get(), ns, A2.get(), ns, ns, ncols, acc.get());
+    }
+    auto ha = acc.download(s);
+    const double res = ha[1] > 0 ? std::sqrt(ha[0] / ha[1]) : 0.0;
+    h.pid_residual = std::max(h.pid_residual, res);
+    return r;
+  };
+  h.pid_residual = 0.0;
+  std::vector<int> permY, permC, permE;
+  h.rB = subsample_id([&](const int64_t* sub, cplx* out) {
+    prof::KScope _ks("k_gather_subrows", s);
+    k_gather_subrows<<<grid_1d((int64_t)ns * ny), 256, 0, s>>>(Yfull.get(), N, sub, ns, ny, out, ns);
+  }, ny, permY, h.TY);
+  h.rC = subsample_id([&](const int64_t* sub, cplx* out) {
+    for (int c = 0; c < nc; ++c) {
+      prof::KScope _ks("k_gather_subcols_t", s);
+      k_gather_subcols_t<<<grid_1d((int64_t)ns * 2 * M), 256, 0, s>>>(h.contours[c].CL.get(), 2 * M, 2 * M, sub, ns, out,
+                                                                        ns, 4 * M * c);
+      k_gather_subcols_t<<<grid_1d((int64_t)ns * 2 * M), 256, 0, s>>>(h.contours[c].CR.get(), 2 * M, 2 * M, sub, ns, out,
+                                                                        ns, 4 * M * c + 2 * M);
+    }
+  }, ny, permC, h.TC);
+  h.rE = subsample_id([&](const int64_t* sub, cplx* out) {
+    prof::KScope _ks("k_gather_subcols_t", s);
+    k_gather_subcols_t<<<grid_1d((int64_t)ns * nce), 256, 0, s>>>(h.Esamp.get(), nce, nce, sub, ns, out, ns, 0);
+  }, nce, permE, h.TE);
+  HBS_LAUNCH_CHECK("periodizer ids");
+
+  // ---- W = A^{-1} [P | Y(:, JY)]
   ph.next("build:W_apply");
+  const int rB = h.rB, rC = h.rC, rE = h.rE;
+  h.wcols = l + rB;
+  h.W.alloc((size_t)N * h.wcols);
   {
+    DevBuf<cplx> Wsrc((size_t)N * h.wcols);
+    if (l > 0) HBS_CUDA(cudaMemcpyAsync(Wsrc.get(), h.Pnb.get(), sizeof(cplx) * N * l, cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < rB; ++i)
+      HBS_CUDA(cudaMemcpyAsync(Wsrc.get() + (int64_t)(l + i) * N, Yfull.get() + (int64_t)permY[i] * N,
+                               sizeof(cplx) * N, cudaMemcpyDeviceToDevice, s));
+    Yfull.release();
     const int64_t chunk = 256;
-    DevBuf<cplx> tmp((size_t)N * chunk);
     for (int64_t c0 = 0; c0 < h.wcols; c0 += chunk) {
       int64_t nq = std::min(chunk, h.wcols - c0);
-      HBS_CUDA(cudaMemcpyAsync(tmp.get(), h.W.get() + c0 * N, sizeof(cplx) * N * nq, cudaMemcpyDeviceToDevice, s));
-      h.apply_inverse(tmp.get(), h.W.get() + c0 * N, nq, s);
+      h.apply_inverse(Wsrc.get() + c0 * N, h.W.get() + c0 * N, nq, s);
     }
   }
-  // ---- Z_c = Rows_c W_c
+
+  // ---- Rsel = [R_-1; R_1; C(IC, :); E(IE, :)] and Z = Rsel W
   ph.next("build:Z_products");
+  h.rsel = 2 * l + rC + rE;
+  {
+    std::vector<RowRef> refs;
+    for (int i = 0; i < l; ++i) refs.push_back({h.Rm.get() + i, l});
+    for (int i = 0; i < l; ++i) refs.push_back({h.Rp.get() + i, l});
+    for (int i = 0; i < rC; ++i) {
+      const int a = permC[i], c = a / (4 * M), rr = a % (4 * M);
+      const cplx* base = rr < 2 * M ? h.contours[c].CL.get() + rr : h.contours[c].CR.get() + (rr - 2 * M);
+      refs.push_back({base, 2 * M});
+    }
+    for (int i = 0; i < rE; ++i) refs.push_back({h.Esamp.get() + permE[i], nce});
+    DevBuf<RowRef> drefs;
+    drefs.upload(refs, s);
+    h.Rsel.alloc((size_t)h.rsel * N);
+    {
+      prof::KScope _ks("k_gather_rowrefs", s);
+      k_gather_rowrefs<<<grid_1d((int64_t)h.rsel * N), 256, 0, s>>>(drefs.get(), h.rsel, N, h.Rsel.get(), h.rsel);
+    }
+    HBS_CUDA(cudaStreamSynchronize(s));
+  }
+  DevBuf<cplx> Zc((size_t)h.rsel * h.wcols);
+  {
+    std::vector<GemmJob> gj(1);
+    gj[0] = {h.Rsel.get(), h.W.get(), Zc.get(), h.rsel, (int)h.wcols, (int)N, h.rsel, (int)N, h.rsel, cmk(1, 0),
+             cmk(0, 0), 0, 0, 0};
+    run_gemms(gj, s);
+  }
+  // expand to each contour's rows [R; C_L^c; C_R^c; E] and columns [P | B_L^c | B_R^c]
+  std::vector<int> invC(ny), invE(nce), invY(ny);
+  for (int p = 0; p < ny; ++p) invC[permC[p]] = p;
+  for (int p = 0; p < nce; ++p) invE[permE[p]] = p;
+  for (int p = 0; p < ny; ++p) invY[permY[p]] = p;
   const int zr = 2 * l + 4 * M + 12 * S, zcn = l + 4 * M;
   for (int c = 0; c < nc; ++c) {
     ContourData& cd = h.contours[c];
     cd.zr = zr;
     cd.zc = zcn;
+    std::vector<int2> rrec(zr), crec(zcn);
+    for (int o = 0; o < 2 * l; ++o) rrec[o] = make_int2(0, o);
+    for (int j = 0; j < 4 * M; ++j) {
+      const int p = invC[4 * M * c + j];
+      rrec[2 * l + j] = p < rC ? make_int2(0, 2 * l + p) : make_int2(1, p - rC);
+    }
+    for (int e = 0; e < nce; ++e) {
+      const int p = invE[e];
+      rrec[2 * l + 4 * M + e] = p < rE ? make_int2(0, 2 * l + rC + p) : make_int2(2, p - rE);
+    }
+    for (int j = 0; j < l; ++j) crec[j] = make_int2(0, j);
+    for (int j = 0; j < 4 * M; ++j) {
+      const int p = invY[4 * M * c + j];
+      crec[l + j] = p < rB ? make_int2(0, l + p) : make_int2(1, p - rB);
+    }
+    cd.row_recipe.upload(rrec, s);
+    cd.col_recipe.upload(crec, s);
+    DevBuf<cplx> Zr((size_t)zr * h.wcols);
+    {
+      prof::KScope _ks("k_expand_rows", s);
+      k_expand_rows<<<grid_1d((int64_t)zr * h.wcols), 256, 0, s>>>(Zc.get(), h.rsel, (int)h.wcols, cd.row_recipe.get(),
+                                                                  zr, h.TC.get(), rC, 2 * l, h.TE.get(), rE,
+                                                                  2 * l + rC, Zr.get(), zr);
+    }
     cd.Zd.alloc((size_t)zr * zcn);
-    std::vector<GemmJob> gj;
-    struct Blk { const cplx* A; int rows; int lda; int row0; };
-    Blk rows[5] = {{h.Rm.get(), l, l, 0}, {h.Rp.get(), l, l, l}, {cd.CL.get(), 2 * M, 2 * M, 2 * l},
-                   {cd.CR.get(), 2 * M, 2 * M, 2 * l + 2 * M}, {h.Esamp.get(), 12 * S, 12 * S, 2 * l + 4 * M}};
-    struct CBlk { const cplx* B; int cols; int col0; };
-    CBlk cols[2] = {{h.W.get(), l, 0}, {h.W.get() + cd.col_off * N, 4 * M, l}};
-    for (auto& rb : rows)
-      for (auto& cbk : cols) {
-        if (rb.rows == 0 || cbk.cols == 0) continue;
-        gj.push_back({rb.A, cbk.B, cd.Zd.get() + (int64_t)cbk.col0 * zr + rb.row0, rb.rows, cbk.cols, (int)N, rb.lda,
-                      (int)N, zr, cmk(1, 0), cmk(0, 0), 0, 0, 0});
-      }
-    run_gemms(gj, s);
+    {
+      prof::KScope _ks("k_expand_cols", s);
+      k_expand_cols<<<grid_1d((int64_t)zr * zcn), 256, 0, s>>>(Zr.get(), zr, zr, cd.col_recipe.get(), zcn, h.TY.get(),
+                                                                rB, l, nullptr, cd.Zd.get(), zr);
+    }
+    HBS_LAUNCH_CHECK("Z expansion");
+    HBS_CUDA(cudaStreamSynchronize(s));
   }
   HBS_CUDA(cudaStreamSynchronize(s));
 }
@@ -795,7 +926,25 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
     // ---- Proj = Rows X
     ph.next("solve:projections");
     DevBuf<cplx> Proj((size_t)zr * cols);
-    {
+    if (!plain) {
+      // compressed rows (Rsel, rsel x N) once for all columns, then each group's contour rows
+      DevBuf<cplx> Psel((size_t)h.rsel * cols);
+      std::vector<GemmJob> gj(1);
+      gj[0] = {h.Rsel.get(), X.get(), Psel.get(), h.rsel, (int)cols, (int)N, h.rsel, (int)N, h.rsel, cmk(1, 0),
+               cmk(0, 0), 0, 0, 0};
+      run_gemms(gj, s);
+      for (int gg = 0; gg < ng; ++gg) {
+        const GroupJob& G = gjobs[gg];
+        const ContourData& cd = h.contours[G.contour];
+        const int gcols = G.q + G.nw;
+        prof::KScope _ks("k_expand_rows", s);
+        k_expand_rows<<<grid_1d((int64_t)zr * gcols), 256, 0, s>>>(
+            Psel.get() + (int64_t)G.rhs_col * h.rsel, h.rsel, gcols, cd.row_recipe.get(), zr, h.TC.get(), h.rC,
+            2 * l, h.TE.get(), h.rE, 2 * l + h.rC, Proj.get() + (int64_t)G.rhs_col * zr, zr);
+      }
+      HBS_LAUNCH_CHECK("projection expansion");
+      HBS_CUDA(cudaStreamSynchronize(s));
+    } else {
       std::vector<GemmJob> gj;
       for (int gg = 0; gg < ng; ++gg) {
         const GroupJob& G = gjobs[gg];

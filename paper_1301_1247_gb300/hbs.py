@@ -47,7 +47,8 @@ class Info(ctypes.Structure):
                 ("factor_bytes", ctypes.c_double), ("apply_flops_per_rhs", ctypes.c_double),
                 ("contour_h", ctypes.c_double), ("contour_c", ctypes.c_double), ("contour_w", ctypes.c_double),
                 ("wood_t0", ctypes.c_double), ("n_bragg_samples", ctypes.c_int), ("y0", ctypes.c_double),
-                ("nb_radius", ctypes.c_double), ("nb_proxies", ctypes.c_int)]
+                ("nb_radius", ctypes.c_double), ("nb_proxies", ctypes.c_int), ("pid_col_rank", ctypes.c_int),
+                ("pid_row_rank", ctypes.c_int), ("pid_residual", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -147,6 +147,8 @@ def test_plain_path_matches_precomputed_path():
     omega = 30.0
     h = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12)
     thetas = inputs.bloch_grouped_angles(5, omega, 1.0, 2, 3).ravel()
+    info = h.info()
+    assert 0 < info["pid_col_rank"] < 8 * info["m"] and info["pid_residual"] < 1e-11
     a = h.solve(thetas)
     b = h.solve_plain(thetas)
     for i in range(len(thetas)):
