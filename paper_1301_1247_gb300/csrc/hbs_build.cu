@@ -30,6 +30,7 @@
 #include "dense_kernels.cuh"
 #include "profile.hpp"
 #include "handle.hpp"
+#include "qp_kernels.cuh"
 #include "zgemm.cuh"
 
 namespace hbs {
@@ -295,23 +296,53 @@ DevGeom Handle_geom(const Handle& h) {
   return g;
 }
 
+// Work above which one matrix is decomposed by the multi-CTA kernels instead of one CTA.
+static bool big_cpqr(const CpqrJob& j) { return (double)j.m * j.n * std::min(j.m, j.n) > 4e6; }
+static bool big_inverse(int n) { return n > 128; }
+
 // Batched CPQR-ID of the matrices described by `jobs` (in `pool`).  Returns ranks.
+// Small matrices go to one launch with one CTA each; large ones (the top tree levels,
+// where a level has few nodes) run one after another on all SMs (big_row_id).
 std::vector<int> batched_id(std::vector<CpqrJob>& jobs, cplx* pool, cplx* tpool, int* permpool, double tol,
                             cudaStream_t s) {
   std::vector<int> ranks(jobs.size(), 0);
   if (jobs.empty()) return ranks;
-  int maxn = 0;
-  for (auto& j : jobs) maxn = std::max(maxn, j.n);
-  DevBuf<CpqrJob> dj = upload_jobs(jobs, s);
-  DevBuf<int> dr(jobs.size());
-  size_t sm = (size_t)maxn * (2 * sizeof(double) + sizeof(int));
-  if (sm > 48 * 1024) HBS_CUDA(cudaFuncSetAttribute(k_cpqr<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  {
-    prof::KScope _ks("k_cpqr", s);
-    k_cpqr<256><<<(unsigned)jobs.size(), 256, sm, s>>>(dj.get(), pool, tpool, permpool, dr.get(), tol, 1 << 30);
+  std::vector<CpqrJob> small;
+  std::vector<size_t> small_idx, big_idx;
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    if (big_cpqr(jobs[i])) {
+      big_idx.push_back(i);
+    } else {
+      small_idx.push_back(i);
+      small.push_back(jobs[i]);
+      small.back().job = (int)(small.size() - 1);
+    }
   }
-  HBS_LAUNCH_CHECK("k_cpqr");
-  ranks = dr.download(s);
+  if (!small.empty()) {
+    int maxn = 0;
+    for (auto& j : small) maxn = std::max(maxn, j.n);
+    DevBuf<CpqrJob> dj = upload_jobs(small, s);
+    DevBuf<int> dr(small.size());
+    size_t sm = (size_t)maxn * (2 * sizeof(double) + sizeof(int));
+    if (sm > 48 * 1024)
+      HBS_CUDA(cudaFuncSetAttribute(k_cpqr<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    {
+      prof::KScope _ks("k_cpqr", s);
+      k_cpqr<256><<<(unsigned)small.size(), 256, sm, s>>>(dj.get(), pool, tpool, permpool, dr.get(), tol, 1 << 30);
+    }
+    HBS_LAUNCH_CHECK("k_cpqr");
+    auto r = dr.download(s);
+    for (size_t t = 0; t < small.size(); ++t) ranks[small_idx[t]] = r[t];
+  }
+  if (!big_idx.empty()) {
+    std::vector<BigQrJobSpec> specs;
+    for (size_t i : big_idx) {
+      const CpqrJob& j = jobs[i];
+      specs.push_back({pool + j.mt_off, j.m, j.n, permpool + j.perm_off, tpool + j.t_off});
+    }
+    auto r = big_row_id_batched(specs, tol, s);
+    for (size_t t = 0; t < big_idx.size(); ++t) ranks[big_idx[t]] = r[t];
+  }
   double fl = 0.0;
   for (size_t i = 0; i < jobs.size(); ++i) {
     const double m = jobs[i].m, n = jobs[i].n, k = ranks[i];
@@ -321,9 +352,79 @@ std::vector<int> batched_id(std::vector<CpqrJob>& jobs, cplx* pool, cplx* tpool,
   return ranks;
 }
 
+// Multi-CTA Gauss-Jordan inverses of several large matrices in place (host-stepped over
+// columns; every matrix of the batch advances in the same launches).
+static void big_inverse_batched(std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, const char* what) {
+  const int nj = (int)mats.size();
+  if (nj == 0) return;
+  int nmax = 0;
+  int64_t ptot = 0;
+  for (auto& m : mats) { nmax = std::max(nmax, m.second); ptot += m.second; }
+  DevBuf<int> piv(ptot);
+  DevBuf<BigGjState> st(nj);
+  HBS_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(BigGjState) * nj, s));
+  std::vector<BigGjJob> jobs(nj);
+  int64_t o = 0;
+  double fl = 0.0;
+  for (int j = 0; j < nj; ++j) {
+    jobs[j] = {mats[j].first, mats[j].second, piv.get() + o, st.get() + j};
+    o += mats[j].second;
+    fl += 8.0 * (double)mats[j].second * mats[j].second;
+  }
+  DevBuf<BigGjJob> dj;
+  dj.upload(jobs, s);
+  const int eg = std::max(8, grid_1d((int64_t)nmax * nmax, 256, 2048) / nj);
+  for (int c = 0; c < nmax; ++c) {
+    {
+      prof::KScope _ks("k_bgjb_pivot", s);
+      k_bgjb_pivot<256><<<dim3(1, nj), 256, 0, s>>>(dj.get(), c);
+    }
+    {
+      prof::KScope _ks("k_bgjb_elim", s, fl, 0.0);
+      k_bgjb_elim<<<dim3(eg, nj), 256, 0, s>>>(dj.get(), c);
+    }
+    {
+      prof::KScope _ks("k_bgjb_colc", s);
+      k_bgjb_colc<<<dim3((nmax + 255) / 256, nj), 256, 0, s>>>(dj.get(), c);
+    }
+  }
+  HBS_LAUNCH_CHECK("batched big inverse");
+  std::vector<int> hp = piv.download(s);
+  std::vector<BigGjState> hs(nj);
+  HBS_CUDA(cudaMemcpyAsync(hs.data(), st.get(), sizeof(BigGjState) * nj, cudaMemcpyDeviceToHost, s));
+  HBS_CUDA(cudaStreamSynchronize(s));
+  o = 0;
+  for (int j = 0; j < nj; ++j) {
+    const int n = mats[j].second;
+    if (hs[j].singular) throw Error(HBS_WARN_ILLCOND, std::string("singular block in ") + what);
+    // undo the row interchanges: column swaps (c, piv[c]) in reverse order
+    std::vector<int> src(n);
+    for (int q = 0; q < n; ++q) src[q] = q;
+    for (int c = n - 1; c >= 0; --c) std::swap(src[c], src[hp[o + c]]);
+    o += n;
+    DevBuf<int> dsrc;
+    dsrc.upload(src, s);
+    DevBuf<cplx> tmp((size_t)n * n);
+    {
+      prof::KScope _ks("k_permute_cols", s);
+      k_permute_cols<<<grid_1d((int64_t)n * n), 256, 0, s>>>(mats[j].first, n, dsrc.get(), tmp.get());
+    }
+    HBS_CUDA(cudaMemcpyAsync(mats[j].first, tmp.get(), sizeof(cplx) * n * n, cudaMemcpyDeviceToDevice, s));
+    HBS_CUDA(cudaStreamSynchronize(s));
+  }
+}
+
 // Batched in-place inverses; throws on a singular block.
-void batched_inverse(std::vector<InvJob>& jobs, cplx* pool, cudaStream_t s, const char* what) {
+void batched_inverse(std::vector<InvJob>& jobs_in, cplx* pool, cudaStream_t s, const char* what) {
+  std::vector<InvJob> jobs;
+  std::vector<std::pair<cplx*, int>> big;
+  for (auto& j : jobs_in) {
+    if (big_inverse(j.n)) big.push_back({pool + j.a_off, j.n});
+    else jobs.push_back(j);
+  }
+  big_inverse_batched(big, s, what);
   if (jobs.empty()) return;
+  for (size_t i = 0; i < jobs.size(); ++i) jobs[i].job = (int)i;
   int64_t piv = 0;
   for (auto& j : jobs) { j.piv_off = piv; piv += j.n; }
   DevBuf<int> dpiv(std::max<int64_t>(piv, 1));
@@ -355,7 +456,13 @@ void build_hbs(Handle& h, cudaStream_t s) {
   h.factor_bytes = 0.0;
   h.apply_flops = 0.0;
 
+  static const char* kLevelNames[] = {
+      "build:level_00", "build:level_01", "build:level_02", "build:level_03", "build:level_04", "build:level_05",
+      "build:level_06", "build:level_07", "build:level_08", "build:level_09", "build:level_10", "build:level_11",
+      "build:level_12", "build:level_13", "build:level_14", "build:level_15", "build:level_16", "build:level_17",
+      "build:level_18", "build:level_19", "build:level_20", "build:level_21", "build:level_22", "build:level_23"};
   for (int l = L; l >= 0; --l) {
+    prof::Phase ph_level(kLevelNames[std::min(l, 23)], s);
     Level& lv = h.levels[l];
     lv.l = l;
     lv.count = 1 << l;

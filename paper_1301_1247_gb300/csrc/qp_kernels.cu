@@ -504,3 +504,220 @@ __global__ void k_diff_norm2(const cplx* a, int64_t lda, const cplx* b, int64_t 
 }
 
 }  // namespace hbs
+
+namespace hbs {
+
+// ---------------------------------------------------------------------------
+// Batched multi-CTA column-pivoted QR: the same steps as k_bq_* for several matrices at
+// once (blockIdx.y = matrix), so a tree level with a few dozen large nodes advances all
+// of them with one launch per kernel and step.
+// ---------------------------------------------------------------------------
+__global__ void k_bqb_norms(const BigQrJob* jobs) {
+  const BigQrJob jb = jobs[blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = warp; j < jb.n; j += nwarps) {
+    double s = 0.0;
+    for (int64_t i = lane; i < jb.m; i += 32) s += cabs2(jb.A[j * jb.m + i]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) { jb.nrm[j] = s; jb.nref[j] = s; jb.perm[j] = (int)j; }
+  }
+}
+
+__global__ void k_bqb_argmax(const BigQrJob* jobs, int64_t s) {
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  const BigQrJob jb = jobs[blockIdx.y];
+  double best = -1.0;
+  int bi = 0x7fffffff;
+  if (!jb.st->done) {
+    for (int64_t j = s + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < jb.n; j += (int64_t)gridDim.x * blockDim.x) {
+      double v = jb.nrm[j];
+      if (v > best || (v == best && (int)j < bi)) { best = v; bi = (int)j; }
+    }
+  }
+  double v;
+  int i;
+  block_argmax<256>(best, bi, redv, redi, &v, &i);
+  if (threadIdx.x == 0) { jb.pv[blockIdx.x] = v; jb.pi[blockIdx.x] = i; }
+}
+
+__global__ void k_bqb_pivot(const BigQrJob* jobs, int64_t s, int nparts, double tol) {
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  const BigQrJob jb = jobs[blockIdx.y];
+  BigQrState* st = jb.st;
+  if (st->done) return;
+  const int64_t m = jb.m;
+  if (s >= jb.n || s >= m) {
+    if (threadIdx.x == 0) { st->done = 1; st->rank = (int)s; }
+    return;
+  }
+  double best = -1.0;
+  int bi = 0x7fffffff;
+  for (int q = threadIdx.x; q < nparts; q += blockDim.x) {
+    if (jb.pv[q] > best || (jb.pv[q] == best && jb.pi[q] < bi)) { best = jb.pv[q]; bi = jb.pi[q]; }
+  }
+  double v;
+  int p;
+  block_argmax<256>(best, bi, redv, redi, &v, &p);
+  if (s == 0 && threadIdx.x == 0) st->r00 = sqrt(v);
+  __syncthreads();
+  const double r00 = st->r00;
+  if (!(r00 > 0.0) || sqrt(v) <= tol * r00) {
+    if (threadIdx.x == 0) { st->done = 1; st->rank = (int)s; }
+    return;
+  }
+  cplx* A = jb.A;
+  if (p != s) {
+    cplx* cs = A + s * m;
+    cplx* cp = A + (int64_t)p * m;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) { cplx t = cs[i]; cs[i] = cp[i]; cp[i] = t; }
+    if (threadIdx.x == 0) {
+      double t = jb.nrm[s]; jb.nrm[s] = jb.nrm[p]; jb.nrm[p] = t;
+      t = jb.nref[s]; jb.nref[s] = jb.nref[p]; jb.nref[p] = t;
+      int ti = jb.perm[s]; jb.perm[s] = jb.perm[p]; jb.perm[p] = ti;
+    }
+  }
+  __syncthreads();
+  cplx* cs = A + s * m;
+  double sig = 0.0;
+  for (int64_t i = s + 1 + threadIdx.x; i < m; i += blockDim.x) sig += cabs2(cs[i]);
+  sig = block_sum<256>(sig, redv);
+  if (threadIdx.x == 0) {
+    cplx x0 = cs[s];
+    double ax0 = cabs1(x0);
+    double xn = sqrt(ax0 * ax0 + sig);
+    cplx ph = ax0 > 0.0 ? cmk(x0.x / ax0, x0.y / ax0) : cmk(1.0, 0.0);
+    cplx beta = cmk(-ph.x * xn, -ph.y * xn);
+    cplx v0 = csub(x0, beta);
+    double vv = cabs2(v0) + sig;
+    st->v0 = v0;
+    st->tau = vv > 0.0 ? 2.0 / vv : 0.0;
+    cs[s] = beta;
+    st->rank = (int)(s + 1);
+  }
+}
+
+__global__ void k_bqb_update(const BigQrJob* jobs, int64_t s) {
+  const BigQrJob jb = jobs[blockIdx.y];
+  const BigQrState* st = jb.st;
+  if (st->done) return;
+  const int64_t m = jb.m, n = jb.n;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const cplx v0 = st->v0;
+  const double tau = st->tau;
+  cplx* A = jb.A;
+  const cplx* cs = A + s * m;
+  for (int64_t j = s + 1 + warp; j < n; j += nwarps) {
+    cplx* cj = A + j * m;
+    cplx w = cmk(0.0, 0.0);
+    for (int64_t i = s + 1 + lane; i < m; i += 32) w = cfma(cconj(cs[i]), cj[i], w);
+    for (int o = 16; o > 0; o >>= 1) {
+      w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
+      w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
+    }
+    w = cfma(cconj(v0), cj[s], w);
+    w = cscale(w, tau);
+    cplx top = csub(cj[s], cmul(v0, w));
+    for (int64_t i = s + 1 + lane; i < m; i += 32) cj[i] = csub(cj[i], cmul(cs[i], w));
+    double t = jb.nrm[j] - cabs2(top);
+    if (t <= 0.0078125 * jb.nref[j]) {
+      double q = 0.0;
+      for (int64_t i = s + 1 + lane; i < m; i += 32) q += cabs2(cj[i]);
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      t = q;
+      if (lane == 0) jb.nref[j] = q;
+    }
+    if (lane == 0) { cj[s] = top; jb.nrm[j] = t; }
+  }
+}
+
+__global__ void k_bqb_tsolve(const BigQrJob* jobs) {
+  const BigQrJob jb = jobs[blockIdx.y];
+  const int k = jb.st->rank;
+  const int64_t m = jb.m, n = jb.n;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const cplx* A = jb.A;
+  for (int64_t c = warp; c < n - k; c += nwarps) {
+    const cplx* r12 = A + (k + c) * m;
+    cplx* tc = jb.T + c * (int64_t)k;
+    for (int i = k - 1; i >= 0; --i) {
+      cplx acc = cmk(0.0, 0.0);
+      for (int l = i + 1 + lane; l < k; l += 32) acc = cfma(A[(int64_t)l * m + i], tc[l], acc);
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (lane == 0) tc[i] = cdiv(csub(r12[i], acc), A[(int64_t)i * m + i]);
+      __syncwarp();
+    }
+  }
+}
+
+std::vector<int> big_row_id_batched(std::vector<BigQrJobSpec>& specs, double tol, cudaStream_t s) {
+  const int nj = (int)specs.size();
+  std::vector<int> ranks(nj, 0);
+  if (nj == 0) return ranks;
+  const int nparts = std::max(8, 296 / nj);
+  const int ublocks = std::max(8, 1184 / nj);
+  int64_t ntot = 0, kmax = 0;
+  for (auto& sp : specs) { ntot += sp.n; kmax = std::max<int64_t>(kmax, std::min<int64_t>(sp.m, sp.n)); }
+  DevBuf<double> nrm(ntot), nref(ntot), pv((size_t)nparts * nj);
+  DevBuf<int> pi((size_t)nparts * nj);
+  DevBuf<BigQrState> st(nj);
+  HBS_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(BigQrState) * nj, s));
+  std::vector<BigQrJob> jobs(nj);
+  int64_t o = 0;
+  for (int j = 0; j < nj; ++j) {
+    jobs[j] = {specs[j].A, specs[j].m, specs[j].n, specs[j].perm, specs[j].T, nrm.get() + o, nref.get() + o,
+               pv.get() + (int64_t)nparts * j, pi.get() + (int64_t)nparts * j, st.get() + j};
+    o += specs[j].n;
+  }
+  DevBuf<BigQrJob> dj;
+  dj.upload(jobs, s);
+  {
+    prof::KScope _ks("k_bqb_norms", s);
+    k_bqb_norms<<<dim3(ublocks, nj), 256, 0, s>>>(dj.get());
+  }
+  std::vector<BigQrState> hs(nj);
+  for (int64_t step = 0; step < kmax; ++step) {
+    {
+      prof::KScope _ks("k_bqb_argmax", s);
+      k_bqb_argmax<<<dim3(nparts, nj), 256, 0, s>>>(dj.get(), step);
+    }
+    {
+      prof::KScope _ks("k_bqb_pivot", s);
+      k_bqb_pivot<<<dim3(1, nj), 256, 0, s>>>(dj.get(), step, nparts, tol);
+    }
+    {
+      prof::KScope _ks("k_bqb_update", s);
+      k_bqb_update<<<dim3(ublocks, nj), 256, 0, s>>>(dj.get(), step);
+    }
+    if ((step & 15) == 15) {
+      HBS_LAUNCH_CHECK("batched big qr step");
+      HBS_CUDA(cudaMemcpyAsync(hs.data(), st.get(), sizeof(BigQrState) * nj, cudaMemcpyDeviceToHost, s));
+      HBS_CUDA(cudaStreamSynchronize(s));
+      bool all = true;
+      for (auto& x : hs) all = all && x.done;
+      if (all) break;
+    }
+  }
+  HBS_LAUNCH_CHECK("batched big qr");
+  {
+    prof::KScope _ks("k_bqb_tsolve", s);
+    k_bqb_tsolve<<<dim3(ublocks, nj), 256, 0, s>>>(dj.get());
+  }
+  HBS_LAUNCH_CHECK("k_bqb_tsolve");
+  HBS_CUDA(cudaMemcpyAsync(hs.data(), st.get(), sizeof(BigQrState) * nj, cudaMemcpyDeviceToHost, s));
+  HBS_CUDA(cudaStreamSynchronize(s));
+  for (int j = 0; j < nj; ++j) ranks[j] = hs[j].rank;
+  return ranks;
+}
+
+}  // namespace hbs

@@ -17,6 +17,26 @@ struct BigQrState {
   double tau;
 };
 
+struct BigQrJob {
+  cplx* A;
+  int64_t m, n;
+  int* perm;
+  cplx* T;
+  double* nrm;
+  double* nref;
+  double* pv;
+  int* pi;
+  BigQrState* st;
+};
+struct BigQrJobSpec {
+  cplx* A;     // m x n, column-major, overwritten
+  int64_t m, n;
+  int* perm;   // n
+  cplx* T;     // output k x (n - k)
+};
+// Column-pivoted QR / ID of several large matrices at once on all SMs; returns the ranks.
+std::vector<int> big_row_id_batched(std::vector<BigQrJobSpec>& specs, double tol, cudaStream_t s);
+
 // hbs_build.cu
 void build_hbs(Handle& h, cudaStream_t s);
 DevGeom Handle_geom(const Handle& h);
