@@ -44,6 +44,9 @@ struct ContourData {
   int zr = 0, zc = 0;
   // Recipes that expand compressed rows (Rsel) / columns (W) to this contour's rows / columns.
   DevBuf<int2> row_recipe, col_recipe;
+  // Dense interpolation matrices: C_L = UL C_sel, C_R = UR C_sel (2M x rC);
+  // B_L = Y_sel VL^T, B_R = Y_sel VR^T (VL, VR: 2M x rB).
+  DevBuf<cplx> UL, UR, VL, VR;
 };
 
 struct Handle {
@@ -81,6 +84,9 @@ struct Handle {
   //   ~ rows IC / IE expanded by TC / TE.  Rsel = [R_-1; R_1; C(IC, :); E(IE, :)] (rsel x N).
   int rB = 0, rC = 0, rE = 0, rsel = 0;
   DevBuf<cplx> TY, TC, TE, Rsel;
+  DevBuf<cplx> Zc;             // Rsel A^{-1} [P | Y_sel]  (rsel x (l + rB))
+  DevBuf<cplx> PE;             // Bragg rows from their skeleton rows (12 S x rE)
+  DevBuf<cplx> EZ;             // PE Zc[E rows]  (12 S x (l + rB))
   double pid_residual = 0.0;
 
   double build_seconds = 0.0;

@@ -27,6 +27,8 @@ namespace hbs {
 
 using zc = std::complex<double>;
 
+__global__ void k_dense_from_recipe(const int2* rec, int nout, int tkind, const cplx* T, int r, int off, cplx* out);
+
 static inline cplx to_c(zc v) { return cmk(v.real(), v.imag()); }
 
 // ---------------------------------------------------------------------------
@@ -345,7 +347,7 @@ void build_periodizer(Handle& h, cudaStream_t s) {
              cmk(0, 0), 0, 0, 0};
     run_gemms(gj, s);
   }
-  // expand to each contour's rows [R; C_L^c; C_R^c; E] and columns [P | B_L^c | B_R^c]
+  // interpolation matrices of the reduced Schur systems
   std::vector<int> invC(ny), invE(nce), invY(ny);
   for (int p = 0; p < ny; ++p) invC[permC[p]] = p;
   for (int p = 0; p < nce; ++p) invE[permE[p]] = p;
@@ -372,22 +374,38 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     }
     cd.row_recipe.upload(rrec, s);
     cd.col_recipe.upload(crec, s);
-    DevBuf<cplx> Zr((size_t)zr * h.wcols);
+    cd.UL.alloc((size_t)2 * M * std::max(rC, 1));
+    cd.UR.alloc((size_t)2 * M * std::max(rC, 1));
+    cd.VL.alloc((size_t)2 * M * std::max(rB, 1));
+    cd.VR.alloc((size_t)2 * M * std::max(rB, 1));
     {
-      prof::KScope _ks("k_expand_rows", s);
-      k_expand_rows<<<grid_1d((int64_t)zr * h.wcols), 256, 0, s>>>(Zc.get(), h.rsel, (int)h.wcols, cd.row_recipe.get(),
-                                                                  zr, h.TC.get(), rC, 2 * l, h.TE.get(), rE,
-                                                                  2 * l + rC, Zr.get(), zr);
+      prof::KScope _ks("k_dense_from_recipe", s);
+      k_dense_from_recipe<<<grid_1d((int64_t)2 * M * rC), 256, 0, s>>>(cd.row_recipe.get() + 2 * l, 2 * M, 1,
+                                                                        h.TC.get(), rC, 2 * l, cd.UL.get());
+      k_dense_from_recipe<<<grid_1d((int64_t)2 * M * rC), 256, 0, s>>>(cd.row_recipe.get() + 2 * l + 2 * M, 2 * M, 1,
+                                                                        h.TC.get(), rC, 2 * l, cd.UR.get());
+      k_dense_from_recipe<<<grid_1d((int64_t)2 * M * rB), 256, 0, s>>>(cd.col_recipe.get() + l, 2 * M, 1, h.TY.get(),
+                                                                        rB, l, cd.VL.get());
+      k_dense_from_recipe<<<grid_1d((int64_t)2 * M * rB), 256, 0, s>>>(cd.col_recipe.get() + l + 2 * M, 2 * M, 1,
+                                                                        h.TY.get(), rB, l, cd.VR.get());
     }
-    cd.Zd.alloc((size_t)zr * zcn);
-    {
-      prof::KScope _ks("k_expand_cols", s);
-      k_expand_cols<<<grid_1d((int64_t)zr * zcn), 256, 0, s>>>(Zr.get(), zr, zr, cd.col_recipe.get(), zcn, h.TY.get(),
-                                                                rB, l, nullptr, cd.Zd.get(), zr);
+    HBS_LAUNCH_CHECK("interpolation matrices");
+    if (c == 0) {
+      h.PE.alloc((size_t)nce * std::max(rE, 1));
+      {
+        prof::KScope _ks("k_dense_from_recipe", s);
+        k_dense_from_recipe<<<grid_1d((int64_t)nce * rE), 256, 0, s>>>(cd.row_recipe.get() + 2 * l + 4 * M, nce, 2,
+                                                                        h.TE.get(), rE, 2 * l + rC, h.PE.get());
+      }
+      h.EZ.alloc((size_t)nce * h.wcols);
+      std::vector<GemmJob> gj(1);
+      gj[0] = {h.PE.get(), Zc.get() + 2 * l + rC, h.EZ.get(), nce, (int)h.wcols, rE, nce, h.rsel, nce, cmk(1, 0),
+               cmk(0, 0), 0, 0, 0};
+      run_gemms(gj, s);
     }
-    HBS_LAUNCH_CHECK("Z expansion");
     HBS_CUDA(cudaStreamSynchronize(s));
   }
+  h.Zc = std::move(Zc);
   HBS_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -410,6 +428,17 @@ struct GroupJob {
   cplx wkn[4];               // k_n of Wood's modes
   int64_t s_off, r_off;      // offsets of S (nS x nS) and rhs (nS x q) in the pools
   int64_t piv_off;
+  int nsys;                  // size of the Schur system solved for this group
+  // reduced path (compressed periodizer): per-group work arrays
+  const cplx* ul;            // U_L, U_R (2M x rC): C_L, C_R rows from the skeleton rows
+  const cplx* ur;
+  const cplx* vl;            // V_L, V_R (2M x rB): B_L, B_R columns from the skeleton columns
+  const cplx* vr;
+  cplx* vt;                  // (V_L + alpha V_R)^T  (rB x 2M)
+  cplx* qu;                  // Q^{-1} (alpha U_L - alpha^{-2} U_R)  (2M x rC)
+  cplx* hm;                  // H = Vt QU  (rB x rC)
+  cplx* hc;                  // H [Zc(C rows) | Psel(C rows)]  (rB x (l + rB + q + nw))
+  cplx* wd;                  // Wood's: psi^T Wall(alpha) (2M) then w = that QU (rC), per mode
 };
 
 struct Dims {
@@ -596,7 +625,7 @@ __global__ void __launch_bounds__(NT) k_schur_solve(Dims D, const GroupJob* grou
   __shared__ int redi[32];
   __shared__ cplx sh_ip;
   const GroupJob G = groups[blockIdx.x];
-  const int n = 2 * D.l + 2 * D.M + G.nw, q = G.q;
+  const int n = G.nsys, q = G.q;
   cplx* A = Spool + G.s_off;
   cplx* B = Rpool + G.r_off;
   const int tid = threadIdx.x;
@@ -764,6 +793,411 @@ __global__ void k_scaled_copy(const cplx* src, int64_t n, cplx f, cplx* dst) {
     dst[e] = cmul(f, src[e]);
 }
 
+// ---------------------------------------------------------------------------
+// Reduced Schur systems (precomputed path).  With the compressed periodizer,
+// C~ = U(alpha) C_sel and B = Y_sel V(alpha)^T with U = alpha U_L - alpha^{-2} U_R and
+// V = V_L + alpha V_R (interpolation matrices of the IDs).  The wall rows then read
+// Q xi = U gamma with gamma = C_sel A^{-1} (L zeta + Y_sel beta + PW a - b) and beta = V^T xi,
+// so xi = Q^{-1} U gamma (Q is 2 x 2 block diagonal) and beta = H gamma, H = V^T Q^{-1} U.
+// The unknowns become (zeta, beta, a): 2l + rB + n_wood instead of 2l + 2M + n_wood.
+// ---------------------------------------------------------------------------
+
+// Dense interpolation matrix (nout x r) from a recipe: row j = e_{rec.y - off} (kind 0)
+// or T[:, rec.y]^T (kind tkind); other kinds give zero rows.
+__global__ void k_dense_from_recipe(const int2* rec, int nout, int tkind, const cplx* T, int r, int off, cplx* out) {
+  const int64_t tot = (int64_t)nout * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e % nout), i = (int)(e / nout);
+    const int2 rc = rec[j];
+    cplx v = cmk(0, 0);
+    if (rc.x == 0) v = cmk(i == rc.y - off ? 1.0 : 0.0, 0.0);
+    else if (rc.x == tkind) v = T[i + (int64_t)rc.y * r];
+    out[j + (int64_t)i * nout] = v;
+  }
+}
+
+struct RedDims {
+  int l, M, S, rB, rC, rsel;
+  double d, omega;
+};
+
+__device__ __forceinline__ void q_node(double omega, double d, cplx alpha, cplx km, cplx* qff, cplx* qfn, cplx* qnf,
+                                       cplx* qnn) {
+  // Q at one contour node: rows [f; fn], columns [mu; nu] (derived from (urep), (f), (fn))
+  cplx sq = cmul(csqrt_principal(cmk(omega - km.x, -km.y)), csqrt_principal(cmk(omega + km.x, km.y)));
+  cplx ee = cexp(cmk(-sq.y * d, sq.x * d));
+  cplx ia = cdiv(cmk(1, 0), alpha);
+  cplx ap = cadd(alpha, ia), am = csub(alpha, ia);
+  *qff = cdiv(cmul(cmul(ee, cmk(0, 1)), am), cscale(sq, 2.0));
+  *qfn = csub(cmk(1, 0), cscale(cmul(ee, ap), 0.5));
+  *qnf = cadd(cmk(-1, 0), cscale(cmul(ee, ap), 0.5));
+  *qnn = cscale(cmul(cmul(ee, cmk(0, 1)), cmul(sq, am)), 0.5);
+}
+
+// Per group: vt = (V_L + alpha V_R)^T and qu = Q^{-1} (alpha U_L - alpha^{-2} U_R).
+__global__ void k_red_prep(RedDims D, const GroupJob* groups) {
+  const GroupJob G = groups[blockIdx.y];
+  const int M = D.M, M2 = 2 * D.M;
+  const int64_t nv = (int64_t)D.rB * M2, nq = (int64_t)M * D.rC;
+  const cplx ia2 = cdiv(cmk(1, 0), cmul(G.alpha, G.alpha));
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nv + nq; e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < nv) {
+      const int i = (int)(e % D.rB), mm = (int)(e / D.rB);
+      G.vt[i + (int64_t)mm * D.rB] = cfma(G.alpha, G.vr[mm + (int64_t)i * M2], G.vl[mm + (int64_t)i * M2]);
+    } else {
+      const int64_t q = e - nv;
+      const int m = (int)(q % M), c = (int)(q / M);
+      cplx qff, qfn, qnf, qnn;
+      q_node(D.omega, D.d, G.alpha, G.ck[m], &qff, &qfn, &qnf, &qnn);
+      const cplx det = csub(cmul(qff, qnn), cmul(qfn, qnf));
+      const int64_t o = (int64_t)c * M2;
+      cplx uf = csub(cmul(G.alpha, G.ul[m + o]), cmul(ia2, G.ur[m + o]));
+      cplx un = csub(cmul(G.alpha, G.ul[M + m + o]), cmul(ia2, G.ur[M + m + o]));
+      G.qu[m + o] = cdiv(csub(cmul(qnn, uf), cmul(qfn, un)), det);
+      G.qu[M + m + o] = cdiv(csub(cmul(qff, un), cmul(qnf, uf)), det);
+    }
+  }
+}
+
+// Wood's rows of one group: wd[t] = [psi_t^T Wall(alpha) (2M) | that times qu (rC)].
+__global__ void k_red_wood(RedDims D, const GroupJob* groups, Dims DD) {
+  const GroupJob G = groups[blockIdx.x];
+  if (G.nw == 0) return;
+  const int M2 = 2 * D.M, S4 = 4 * D.S;
+  for (int t = 0; t < G.nw; ++t) {
+    cplx* w = G.wd + (int64_t)t * (M2 + D.rC);
+    for (int mm = threadIdx.x; mm < M2; mm += blockDim.x) {
+      cplx acc = cmk(0, 0);
+      for (int sidx = D.S; sidx < S4; ++sidx) {
+        cplx p = wood_psi(DD, G, t, sidx);
+        if (p.x == 0.0 && p.y == 0.0) continue;
+        acc = cfma(p, cfma(G.alpha, G.sr[(int64_t)mm * S4 + sidx], G.sl[(int64_t)mm * S4 + sidx]), acc);
+      }
+      w[mm] = acc;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < D.rC; c += blockDim.x) {
+      cplx acc = cmk(0, 0);
+      for (int mm = 0; mm < M2; ++mm) acc = cfma(w[mm], G.qu[mm + (int64_t)c * M2], acc);
+      w[M2 + c] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// phi_t . X: Wood's sampling functional over the three images' E rows (ld 12S column X).
+__device__ __forceinline__ cplx wood_phi(const Dims& DD, const GroupJob& G, int t, const cplx* X) {
+  const int S = DD.S;
+  cplx acc = cmk(0, 0);
+  cplx aj = cdiv(cmk(1, 0), G.alpha);
+  for (int jj = 0; jj < 3; ++jj) {
+    cplx part = cmk(0, 0);
+    for (int sidx = S; sidx < 4 * S; ++sidx) {
+      cplx p = wood_psi(DD, G, t, sidx);
+      if (p.x == 0.0 && p.y == 0.0) continue;
+      part = cfma(p, X[4 * S * jj + sidx], part);
+    }
+    acc = cfma(aj, part, acc);
+    aj = cmul(aj, G.alpha);
+  }
+  return acc;
+}
+
+__global__ void k_red_assemble(RedDims D, Dims DD, const GroupJob* groups, const cplx* Zc, const cplx* Psel,
+                               const cplx* EZ, const cplx* EP, double y0, cplx* Spool, cplx* Rpool) {
+  const GroupJob G = groups[blockIdx.y];
+  const int l = D.l, rB = D.rB, rC = D.rC, rsel = D.rsel, S12 = 12 * D.S;
+  const int n = G.nsys, M2 = 2 * D.M;
+  const cplx ia = cdiv(cmk(1, 0), G.alpha);
+  const int64_t tot = (int64_t)n * (n + G.q);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % n);
+    const int C = (int)(e / n);
+    // column description
+    int kind, idx;  // 0 zeta (base col idx, factor f), 1 beta (idx), 2 Wood (idx), 3 rhs (idx)
+    cplx f = cmk(1, 0);
+    if (C >= n) { kind = 3; idx = C - n; }
+    else if (C < 2 * l) { kind = 0; idx = C < l ? C : C - l; f = C < l ? ia : G.alpha; }
+    else if (C < 2 * l + rB) { kind = 1; idx = C - 2 * l; }
+    else { kind = 2; idx = C - 2 * l - rB; }
+    // Zc / Psel column for this unknown
+    const int zcol = kind == 0 ? idx : (kind == 1 ? l + idx : -1);
+    const int pcol = kind == 2 ? G.rhs_col + G.q + idx : (kind == 3 ? G.rhs_col + idx : -1);
+    cplx v;
+    if (r < 2 * l) {
+      if (zcol >= 0) v = cmul(f, Zc[r + (int64_t)zcol * rsel]);
+      else v = Psel[r + (int64_t)pcol * rsel];
+      v = cmk(-v.x, -v.y);
+      if (kind == 0 && C == r) v.x -= 1.0;
+    } else if (r < 2 * l + rB) {
+      const int ii = r - 2 * l;
+      const int hcol = kind == 0 ? idx : (kind == 1 ? l + idx : (kind == 2 ? l + rB + G.q + idx : l + rB + idx));
+      v = cmul(f, G.hc[ii + (int64_t)hcol * rB]);
+      v = cmk(-v.x, -v.y);
+      if (kind == 1 && idx == ii) v.x += 1.0;
+    } else {
+      const int tw = r - 2 * l - rB;
+      const cplx* w = G.wd + (int64_t)tw * (M2 + rC) + M2;
+      const cplx* X = zcol >= 0 ? EZ + (int64_t)zcol * S12 : EP + (int64_t)pcol * S12;
+      cplx ph = wood_phi(DD, G, tw, X);
+      cplx wz = cmk(0, 0);
+      if (zcol >= 0)
+        for (int c = 0; c < rC; ++c) wz = cfma(w[c], Zc[2 * l + c + (int64_t)zcol * rsel], wz);
+      else
+        for (int c = 0; c < rC; ++c) wz = cfma(w[c], Psel[2 * l + c + (int64_t)pcol * rsel], wz);
+      v = cmul(f, csub(wz, ph));
+      if (kind == 2) {
+        cplx acc = cmk(0, 0);
+        for (int sidx = D.S; sidx < 4 * D.S; ++sidx) {
+          cplx p = wood_psi(DD, G, tw, sidx);
+          if (p.x == 0.0 && p.y == 0.0) continue;
+          acc = cfma(p, sample_point_pw(DD, G, idx, sidx, y0), acc);
+        }
+        v = cadd(v, acc);
+      }
+    }
+    if (kind == 3) Rpool[G.r_off + (int64_t)idx * n + r] = v;
+    else Spool[G.s_off + (int64_t)C * n + r] = v;
+  }
+}
+
+// Bragg amplitudes from the reduced solution: gamma, xi = Q^{-1} U gamma, samples, DFT.
+__global__ void k_red_bragg(RedDims D, Dims DD, const GroupJob* groups, const AngleJob* angles, const cplx* Zc,
+                            const cplx* Psel, const cplx* EZ, const cplx* EP, const cplx* Rpool, double y0,
+                            cplx* cout, cplx* dout, double* flux) {
+  extern __shared__ cplx sh[];
+  const AngleJob A = angles[blockIdx.x];
+  const GroupJob G = groups[A.group];
+  const int l = D.l, rB = D.rB, rC = D.rC, rsel = D.rsel, S = D.S, S4 = 4 * D.S, S12 = 12 * D.S, M2 = 2 * D.M;
+  const int n = G.nsys;
+  cplx* gam = sh;
+  cplx* xi = sh + rC;
+  cplx* samp = sh + rC + M2;
+  const cplx* u = Rpool + G.r_off + (int64_t)A.col * n;
+  const cplx ia = cdiv(cmk(1, 0), G.alpha);
+  for (int c = threadIdx.x; c < rC; c += blockDim.x) {
+    const int row = 2 * l + c;
+    cplx acc = cmk(0, 0);
+    for (int j = 0; j < 2 * l; ++j) {
+      const cplx f = j < l ? ia : G.alpha;
+      acc = cfma(cmul(f, Zc[row + (int64_t)(j < l ? j : j - l) * rsel]), u[j], acc);
+    }
+    for (int k = 0; k < rB; ++k) acc = cfma(Zc[row + (int64_t)(l + k) * rsel], u[2 * l + k], acc);
+    for (int t = 0; t < G.nw; ++t) acc = cfma(Psel[row + (int64_t)(G.rhs_col + G.q + t) * rsel], u[2 * l + rB + t], acc);
+    gam[c] = csub(acc, Psel[row + (int64_t)(G.rhs_col + A.col) * rsel]);
+  }
+  __syncthreads();
+  for (int mm = threadIdx.x; mm < M2; mm += blockDim.x) {
+    cplx acc = cmk(0, 0);
+    for (int c = 0; c < rC; ++c) acc = cfma(G.qu[mm + (int64_t)c * M2], gam[c], acc);
+    xi[mm] = acc;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < 2 * S; r += blockDim.x) {
+    cplx acc = cmk(0, 0);
+    cplx aj = ia;
+    for (int jj = 0; jj < 3; ++jj) {
+      const int row = S4 * jj + r;
+      cplx part = EP[row + (int64_t)(G.rhs_col + A.col) * S12];
+      for (int j = 0; j < 2 * l; ++j) {
+        const cplx f = j < l ? ia : G.alpha;
+        part = csub(part, cmul(cmul(f, EZ[row + (int64_t)(j < l ? j : j - l) * S12]), u[j]));
+      }
+      for (int k = 0; k < rB; ++k) part = csub(part, cmul(EZ[row + (int64_t)(l + k) * S12], u[2 * l + k]));
+      for (int t = 0; t < G.nw; ++t)
+        part = csub(part, cmul(EP[row + (int64_t)(G.rhs_col + G.q + t) * S12], u[2 * l + rB + t]));
+      acc = cfma(aj, part, acc);
+      aj = cmul(aj, G.alpha);
+    }
+    for (int mm = 0; mm < M2; ++mm) {
+      cplx wv = cfma(G.alpha, G.sr[(int64_t)mm * S4 + r], G.sl[(int64_t)mm * S4 + r]);
+      acc = cfma(wv, xi[mm], acc);
+    }
+    for (int t = 0; t < G.nw; ++t) acc = cfma(sample_point_pw(DD, G, t, r, y0), u[2 * l + rB + t], acc);
+    samp[r] = acc;
+  }
+  __syncthreads();
+  __shared__ double fl[32];
+  const int no = A.n_max - A.n_min + 1;
+  double fsum = 0.0;
+  for (int o = threadIdx.x; o < no; o += blockDim.x) {
+    const int nn = A.n_min + o;
+    const double kap = A.kappa + 2.0 * HBS_PI * nn / D.d;
+    cplx cn = cmk(0, 0), dn = cmk(0, 0);
+    for (int si = 0; si < S; ++si) {
+      const double xs = -0.5 * D.d + (si + 0.5) * D.d / S;
+      double sn, cs;
+      sincos(-kap * xs, &sn, &cs);
+      cplx ev = cmk(cs / S, sn / S);
+      cn = cfma(ev, samp[si], cn);
+      dn = cfma(ev, samp[S + si], dn);
+    }
+    cout[A.out_off + o] = cn;
+    dout[A.out_off + o] = dn;
+    const double kn2 = D.omega * D.omega - kap * kap;
+    const double kn = kn2 > 0 ? sqrt(kn2) : 0.0;
+    cplx dd = dn;
+    if (nn == 0) {
+      double sn, cs;
+      sincos(A.k0 * y0, &sn, &cs);
+      dd = cadd(dd, cmk(cs, sn));
+    }
+    fsum += (kn / A.k0) * (cabs2(cn) + cabs2(dd));
+  }
+  for (int o = 16; o > 0; o >>= 1) fsum += __shfl_xor_sync(0xffffffffu, fsum, o);
+  if ((threadIdx.x & 31) == 0) fl[threadIdx.x >> 5] = fsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += fl[w];
+    flux[blockIdx.x] = fabs(t - 1.0);
+  }
+}
+
+static AngleJob make_angle_job(double omega, double d, double th, int group, int col, int64_t* oo) {
+  const double kap = omega * std::cos(th);
+  AngleJob aj;
+  aj.group = group;
+  aj.col = col;
+  aj.kappa = kap;
+  aj.k0 = omega * std::fabs(std::sin(th));
+  aj.n_min = (int)std::ceil((-omega - kap) * d / (2 * M_PI));
+  aj.n_max = (int)std::floor((omega - kap) * d / (2 * M_PI));
+  aj.out_off = *oo;
+  *oo += aj.n_max - aj.n_min + 1;
+  return aj;
+}
+
+// One batch of Bloch-phase groups on the precomputed, compressed path.
+static void reduced_batch(Handle& h, std::vector<GroupJob>& gjobs, std::vector<std::vector<int64_t>*>& gmembers,
+                          const double* theta, const cplx* Psel, int64_t cols, Result& out, cudaStream_t s) {
+  const int l = h.nb_rank, M = h.M, S = h.S, rB = h.rB, rC = h.rC, rE = h.rE, rsel = h.rsel;
+  const int M2 = 2 * M, S12 = 12 * S;
+  const int ng = (int)gjobs.size();
+  prof::PhaseSeq ph(s);
+  ph.next("solve:schur");
+  // E rows of the projections, expanded: EP = P_E Psel[E rows]
+  DevBuf<cplx> EP((size_t)S12 * cols);
+  {
+    std::vector<GemmJob> gj(1);
+    gj[0] = {h.PE.get(), Psel + 2 * l + rC, EP.get(), S12, (int)cols, rE, S12, rsel, S12, cmk(1, 0), cmk(0, 0), 0, 0, 0};
+    run_gemms(gj, s);
+  }
+  // per-group work arrays
+  int64_t nvt = 0, nqu = 0, nhm = 0, nhc = 0, nwd = 0, so = 0, ro = 0;
+  for (auto& G : gjobs) {
+    G.nsys = 2 * l + rB + G.nw;
+    nvt += (int64_t)rB * M2;
+    nqu += (int64_t)M2 * rC;
+    nhm += (int64_t)rB * rC;
+    nhc += (int64_t)rB * (l + rB + G.q + G.nw);
+    nwd += (int64_t)G.nw * (M2 + rC);
+    G.s_off = so; so += (int64_t)G.nsys * G.nsys;
+    G.r_off = ro; ro += (int64_t)G.nsys * G.q;
+  }
+  DevBuf<cplx> vt(std::max<int64_t>(nvt, 1)), qu(std::max<int64_t>(nqu, 1)), hm(std::max<int64_t>(nhm, 1)),
+      hc(std::max<int64_t>(nhc, 1)), wd(std::max<int64_t>(nwd, 1)), Sp(std::max<int64_t>(so, 1)),
+      Rp(std::max<int64_t>(ro, 1));
+  {
+    int64_t a = 0, b = 0, c = 0, d2 = 0, e = 0;
+    for (auto& G : gjobs) {
+      const ContourData& cd = h.contours[G.contour];
+      G.ul = cd.UL.get(); G.ur = cd.UR.get(); G.vl = cd.VL.get(); G.vr = cd.VR.get();
+      G.vt = vt.get() + a; a += (int64_t)rB * M2;
+      G.qu = qu.get() + b; b += (int64_t)M2 * rC;
+      G.hm = hm.get() + c; c += (int64_t)rB * rC;
+      G.hc = hc.get() + d2; d2 += (int64_t)rB * (l + rB + G.q + G.nw);
+      G.wd = wd.get() + e; e += (int64_t)G.nw * (M2 + rC);
+    }
+  }
+  DevBuf<GroupJob> dg;
+  dg.upload(gjobs, s);
+  RedDims R{l, M, S, rB, rC, rsel, h.d, h.omega};
+  Dims DD{l, M, S, 0, h.d, h.omega, 0};
+  {
+    prof::KScope _ks("k_red_prep", s);
+    k_red_prep<<<dim3(64, ng), 256, 0, s>>>(R, dg.get());
+  }
+  HBS_LAUNCH_CHECK("k_red_prep");
+  {
+    std::vector<GemmJob> gj;
+    for (auto& G : gjobs)
+      gj.push_back({G.vt, G.qu, G.hm, rB, rC, M2, rB, M2, rB, cmk(1, 0), cmk(0, 0), 0, 0, 0});
+    run_gemms(gj, s);
+    gj.clear();
+    for (auto& G : gjobs) {
+      gj.push_back({G.hm, h.Zc.get() + 2 * l, G.hc, rB, l + rB, rC, rB, rsel, rB, cmk(1, 0), cmk(0, 0), 0, 0, 0});
+      gj.push_back({G.hm, Psel + 2 * l + (int64_t)G.rhs_col * rsel, G.hc + (int64_t)(l + rB) * rB, rB, G.q + G.nw, rC,
+                    rB, rsel, rB, cmk(1, 0), cmk(0, 0), 0, 0, 0});
+    }
+    run_gemms(gj, s);
+  }
+  {
+    prof::KScope _ks("k_red_wood", s);
+    k_red_wood<<<ng, 256, 0, s>>>(R, dg.get(), DD);
+  }
+  {
+    prof::KScope _ks("k_red_assemble", s);
+    k_red_assemble<<<dim3(64, ng), 256, 0, s>>>(R, DD, dg.get(), h.Zc.get(), Psel, h.EZ.get(), EP.get(), h.y0,
+                                                 Sp.get(), Rp.get());
+  }
+  HBS_LAUNCH_CHECK("k_red_assemble");
+  DevBuf<int> ill(ng);
+  {
+    double sfl = 0.0;
+    for (auto& G : gjobs) {
+      const double n = G.nsys;
+      sfl += 8.0 / 3.0 * n * n * n + 8.0 * n * n * G.q;
+    }
+    prof::KScope _ks("k_schur_solve", s, sfl, 0.0);
+    k_schur_solve<256><<<ng, 256, 0, s>>>(DD, dg.get(), Sp.get(), Rp.get(), ill.get());
+  }
+  HBS_LAUNCH_CHECK("k_schur_solve");
+  ph.next("solve:bragg");
+  std::vector<AngleJob> ajobs;
+  int64_t oo = 0;
+  for (int gg = 0; gg < ng; ++gg) {
+    const auto& mem = *gmembers[gg];
+    for (int a = 0; a < gjobs[gg].q; ++a) ajobs.push_back(make_angle_job(h.omega, h.d, theta[mem[a]], gg, a, &oo));
+  }
+  DevBuf<AngleJob> da;
+  da.upload(ajobs, s);
+  DevBuf<cplx> cbuf(std::max<int64_t>(oo, 1)), dbuf(std::max<int64_t>(oo, 1));
+  DevBuf<double> fbuf(ajobs.size());
+  {
+    prof::KScope _ks("k_red_bragg", s);
+    const size_t shm = (size_t)(rC + M2 + 2 * S) * sizeof(cplx);
+    k_red_bragg<<<(unsigned)ajobs.size(), 128, shm, s>>>(R, DD, dg.get(), da.get(), h.Zc.get(), Psel, h.EZ.get(),
+                                                         EP.get(), Rp.get(), h.y0, cbuf.get(), dbuf.get(), fbuf.get());
+  }
+  HBS_LAUNCH_CHECK("k_red_bragg");
+  auto hcv = cbuf.download(s), hdv = dbuf.download(s);
+  auto hf = fbuf.download(s);
+  auto hill = ill.download(s);
+  for (int v : hill)
+    if (v) out.illcond = true;
+  size_t ai = 0;
+  for (int gg = 0; gg < ng; ++gg) {
+    const auto& mem = *gmembers[gg];
+    for (int a = 0; a < gjobs[gg].q; ++a, ++ai) {
+      const AngleJob& aj = ajobs[ai];
+      AngleResult& r = out.angles[mem[a]];
+      r.n_min = aj.n_min;
+      r.n_max = aj.n_max;
+      const int no = aj.n_max - aj.n_min + 1;
+      r.c.resize(no);
+      r.d.resize(no);
+      for (int o = 0; o < no; ++o) {
+        r.c[o] = zc(hcv[aj.out_off + o].x, hcv[aj.out_off + o].y);
+        r.d[o] = zc(hdv[aj.out_off + o].x, hdv[aj.out_off + o].y);
+      }
+      r.flux_err = hf[ai];
+      r.n_wood = gjobs[gg].nw;
+      r.t0 = h.contours[gjobs[gg].contour].t0;
+    }
+  }
+}
+
 static zc kn_of(double omega, double kap) {
   double v = omega * omega - kap * kap;
   return v >= 0 ? zc(std::sqrt(v), 0.0) : zc(0.0, std::sqrt(-v));
@@ -927,23 +1361,17 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
     ph.next("solve:projections");
     DevBuf<cplx> Proj((size_t)zr * cols);
     if (!plain) {
-      // compressed rows (Rsel, rsel x N) once for all columns, then each group's contour rows
+      // compressed rows (Rsel, rsel x N) once for all columns; the reduced Schur systems
+      // work on them directly (no expansion to the full wall rows)
+      Proj.release();
       DevBuf<cplx> Psel((size_t)h.rsel * cols);
       std::vector<GemmJob> gj(1);
       gj[0] = {h.Rsel.get(), X.get(), Psel.get(), h.rsel, (int)cols, (int)N, h.rsel, (int)N, h.rsel, cmk(1, 0),
                cmk(0, 0), 0, 0, 0};
       run_gemms(gj, s);
-      for (int gg = 0; gg < ng; ++gg) {
-        const GroupJob& G = gjobs[gg];
-        const ContourData& cd = h.contours[G.contour];
-        const int gcols = G.q + G.nw;
-        prof::KScope _ks("k_expand_rows", s);
-        k_expand_rows<<<grid_1d((int64_t)zr * gcols), 256, 0, s>>>(
-            Psel.get() + (int64_t)G.rhs_col * h.rsel, h.rsel, gcols, cd.row_recipe.get(), zr, h.TC.get(), h.rC,
-            2 * l, h.TE.get(), h.rE, 2 * l + h.rC, Proj.get() + (int64_t)G.rhs_col * zr, zr);
-      }
-      HBS_LAUNCH_CHECK("projection expansion");
-      HBS_CUDA(cudaStreamSynchronize(s));
+      X.release();
+      reduced_batch(h, gjobs, gmembers, theta, Psel.get(), cols, out, s);
+      continue;
     } else {
       std::vector<GemmJob> gj;
       for (int gg = 0; gg < ng; ++gg) {
@@ -975,6 +1403,7 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
     int64_t so = 0, ro = 0;
     for (auto& G : gjobs) {
       const int nS = 2 * l + 2 * M + G.nw;
+      G.nsys = nS;
       G.s_off = so; so += (int64_t)nS * nS;
       G.r_off = ro; ro += (int64_t)nS * G.q;
     }
