@@ -139,10 +139,14 @@ struct YJob {
   double cx, cy, R, wp;
 };
 
-// Fill Mt = Y^T (m x n, m = 2 nn + 3 np): columns are the node's points.
+// Fill Mt = Y^T (m x n, m = 2 nn + 2 np): columns are the node's points.  Proxy rows: the
+// combined layer dG/dn_p - i w G of proxy sources acting on the node (outside -> in; no
+// Fourier mode of the disk is missed since H_m' - i H_m never vanishes on the real axis),
+// then the node's field at the proxy points (in -> out; the exterior Dirichlet data
+// determine a radiating field).
 __global__ void k_fill_y(DevGeom g, const YJob* jobs, const int64_t* idx, const int64_t* near, cplx* pool) {
   const YJob jb = jobs[blockIdx.y];
-  const int m = 2 * jb.nn + 3 * jb.np;
+  const int m = 2 * jb.nn + 2 * jb.np;
   const int64_t tot = (int64_t)m * jb.n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(e % m), c = (int)(e / m);
@@ -160,10 +164,10 @@ __global__ void k_fill_y(DevGeom g, const YJob* jobs, const int64_t* idx, const 
       double sn, cs;
       sincos(th, &sn, &cs);
       double px = jb.cx + jb.R * cs, py = jb.cy + jb.R * sn;
-      if (kind < 2) {
+      if (kind == 0) {
         cplx gg, dg;
         proxy_kernels(g.x[gj], g.y[gj], px, py, cs, sn, g.omega, &gg, &dg);
-        v = kind == 0 ? cscale(gg, g.omega * jb.wp) : cscale(dg, jb.wp);
+        v = cscale(cadd(dg, cmul(cmk(0.0, -g.omega), gg)), jb.wp);
       } else {
         v = cscale(combined_kernel(px, py, g.x[gj], g.y[gj], g.nx[gj], g.ny[gj], g.omega), g.w[gj]);
       }
@@ -573,7 +577,7 @@ void build_hbs(Handle& h, cudaStream_t s) {
       np = std::max(np, h.opts.n_proxy_min);
       np = (np + 7) / 8 * 8;
       yj[j] = {ypool, lv.off[j], noff[j], lv.n[j], (int)hc[j], np, hcx[j], hcy[j], R, 2.0 * HBS_PI * R / np};
-      ypool += (int64_t)(2 * hc[j] + 3 * np) * lv.n[j];
+      ypool += (int64_t)(2 * hc[j] + 2 * np) * lv.n[j];
     }
     DevBuf<cplx> Y(std::max<int64_t>(ypool, 1));
     {
@@ -587,7 +591,7 @@ void build_hbs(Handle& h, cudaStream_t s) {
       lv.t_off.assign(lv.count, 0);
       int64_t tpool = 0;
       for (int j = 0; j < lv.count; ++j) {
-        int m = 2 * (int)hc[j] + 3 * yj[j].np;
+        int m = 2 * (int)hc[j] + 2 * yj[j].np;
         cj[j] = {yj[j].mt_off, tpool, lv.off[j], m, lv.n[j], j};
         lv.t_off[j] = tpool;
         tpool += (int64_t)std::min(m, lv.n[j]) * lv.n[j];

@@ -146,11 +146,11 @@ __global__ void k_fill_wall_samples(const cplx* k, const cplx* wk, int M, int S,
 }
 
 // Neighbour interaction matrix, transposed: Mt (m x N, ld = m).  Rows: image -1 near
-// points (A_{-1}(i, near)), image +1 near points, then proxy single- and double-layer
-// sources on the neighbour circle (centre cx, cy; radius R; np points; weight wp).
+// points (A_{-1}(i, near)), image +1 near points, then combined-layer (dG/dn - i w G)
+// proxy sources on the neighbour circle (centre cx, cy; radius R; np points; weight wp).
 __global__ void k_fill_nb(DevGeom g, const int64_t* near_m, int nm, const int64_t* near_p, int npn, double d, double cx,
                           double cy, double R, int np, double wp, cplx* Mt) {
-  const int m = nm + npn + 2 * np;
+  const int m = nm + npn + np;
   const int64_t tot = (int64_t)m * g.n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(e % m);
@@ -161,13 +161,12 @@ __global__ void k_fill_nb(DevGeom g, const int64_t* near_m, int nm, const int64_
     } else if (r < nm + npn) {
       v = a_image_entry(g, i, near_p[r - nm], d);
     } else {
-      int q = r - nm - npn;
-      int kind = q / np, p = q - kind * np;
+      const int p = r - nm - npn;
       double sn, cs;
       sincos(2.0 * HBS_PI * (double)p / (double)np, &sn, &cs);
       cplx gg, dg;
       proxy_kernels(g.x[i], g.y[i], cx + R * cs, cy + R * sn, cs, sn, g.omega, &gg, &dg);
-      v = kind == 0 ? cscale(gg, g.omega * wp) : cscale(dg, wp);
+      v = cscale(cadd(dg, cmul(cmk(0.0, -g.omega), gg)), wp);
     }
     Mt[i * (int64_t)m + r] = v;
   }

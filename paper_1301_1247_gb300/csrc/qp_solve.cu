@@ -119,7 +119,7 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   h.nb_np = np;
   {
     const int nm = (int)near_m.size(), npn = (int)near_p.size();
-    const int64_t m = nm + npn + 2 * np;
+    const int64_t m = nm + npn + np;
     DevBuf<int64_t> dnm, dnp;
     dnm.upload(near_m, s);
     dnp.upload(near_p, s);
