@@ -720,3 +720,108 @@ std::vector<int> big_row_id_batched(std::vector<BigQrJobSpec>& specs, double tol
 }
 
 }  // namespace hbs
+
+namespace hbs {
+
+// ---------------------------------------------------------------------------
+// Entry-wise periodizer fills on index lists, so that the precomputed path only
+// evaluates the subsample used by the interpolative decompositions and the skeleton
+// rows / columns it keeps.
+// ---------------------------------------------------------------------------
+
+// Column `col` of Y = [B_L^0 | B_R^0 | B_L^1 | B_R^1] at boundary node i (each block [mu | nu]).
+__device__ __forceinline__ cplx b_entry(const DevGeom& g, const ContourPtrs& cp, int M, double d, int64_t i, int col) {
+  const int c = col / (4 * M), rem = col % (4 * M);
+  const int side = rem / (2 * M), kind = (rem % (2 * M)) / M, m = rem % M;
+  const cplx km = cp.k[c][m], w = cp.wk[c][m];
+  const cplx s = sqrt_branch(g.omega, km);
+  const double xi = g.x[i], yi = g.y[i];
+  const double a = side == 0 ? xi + 0.5 * d : 0.5 * d - xi;
+  cplx e = cmul(cexp(cmk(-km.y * yi, km.x * yi)), cexp(cmk(-s.y * a, s.x * a)));
+  if (kind == 0) return cmul(cmul(e, cdiv(cmk(0.0, 0.5), s)), w);
+  return cmul(cscale(e, side == 0 ? 0.5 : -0.5), w);
+}
+
+// Row `a` of C = [C_L^0; C_R^0; C_L^1; C_R^1] (each block [f; fn] rows) at boundary node j.
+__device__ __forceinline__ cplx c_entry(const DevGeom& g, const ContourPtrs& cp, int M, double d, int a, int64_t j) {
+  const int c = a / (4 * M), rem = a % (4 * M);
+  const int side = rem / (2 * M), kind = (rem % (2 * M)) / M, m = rem % M;
+  const double shift_x = side == 0 ? d : -d, x0 = side == 0 ? -0.5 * d : 0.5 * d;
+  const cplx km = cp.k[c][m];
+  const cplx s = sqrt_branch(g.omega, km);
+  const double sx = g.x[j] + shift_x, sy = g.y[j], nx = g.nx[j], ny = g.ny[j];
+  const double sg = sx - x0 > 0.0 ? 1.0 : -1.0;
+  const double ax = fabs(sx - x0);
+  cplx base = cmul(cexp(cmk(km.y * sy, -km.x * sy)), cexp(cmk(-s.y * ax, s.x * ax)));
+  base = cscale(base, g.w[j] / (4.0 * HBS_PI));
+  const cplx iw = cmk(0.0, g.omega);
+  if (kind == 0) {
+    cplx s_hat = cdiv(cmul(cmk(0.0, 1.0), base), s);
+    cplx d_hat = cmul(base, cadd(cmk(-sg * nx, 0.0), cscale(cdiv(km, s), ny)));
+    return csub(d_hat, cmul(iw, s_hat));
+  }
+  cplx dstar_hat = cscale(base, sg);
+  cplx t_hat = cmul(cmul(cmk(0.0, 1.0), base), csub(cscale(s, nx), cscale(km, sg * ny)));
+  return csub(t_hat, cmul(iw, dstar_hat));
+}
+
+// Row `r` of the Bragg sampling rows E (3 images x [u(+y0) | u(-y0) | u_y(+y0) | u_y(-y0)]).
+__device__ __forceinline__ cplx e_entry(const DevGeom& g, int S, double d, double y0, int r, int64_t j) {
+  const int jj = r / (4 * S), rr = r % (4 * S);
+  const int s = rr % S, kind = rr / S;
+  const double tx = -0.5 * d + (s + 0.5) * d / S;
+  const double ty = (kind == 0 || kind == 2) ? y0 : -y0;
+  const double sx = g.x[j] + (jj - 1) * d, sy = g.y[j], nx = g.nx[j], ny = g.ny[j];
+  const double omega = g.omega;
+  cplx v;
+  if (kind < 2) {
+    v = combined_kernel(tx, ty, sx, sy, nx, ny, omega);
+  } else {
+    double ddx = tx - sx, ddy = ty - sy;
+    double rr2 = sqrt(ddx * ddx + ddy * ddy);
+    double z = omega * rr2;
+    cplx h0, h1;
+    hankel01(z, &h0, &h1);
+    cplx f1 = cmul(cmk(0.0, -0.25 * omega), h1);
+    cplx f2 = cmul(cmk(0.0, -0.25 * omega * omega), csub(h0, cscale(h1, 1.0 / z)));
+    cplx gg = cscale(f1, 1.0 / rr2);
+    cplx gp = cscale(csub(f2, cscale(f1, 1.0 / rr2)), 1.0 / rr2);
+    double dn = ddx * nx + ddy * ny;
+    v = cadd(cadd(cscale(gp, -(ddy / rr2) * dn), cscale(gg, -ny)), cmul(cmk(0.0, -omega * ddy), gg));
+  }
+  return cscale(v, g.w[j]);
+}
+
+// out[i + c ld] = entry at (pts[i], c) for kinds 0 (B columns), 1 (C rows), 2 (E rows),
+// all `nfam` members of the family; used for the subsampled decompositions.
+__global__ void k_fill_family_sub(DevGeom g, ContourPtrs cp, int M, double d, int S, double y0, int family,
+                                  const int64_t* pts, int np, int nfam, cplx* out, int64_t ld) {
+  const int64_t tot = (int64_t)np * nfam;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % np), c = (int)(e / np);
+    const int64_t p = pts[i];
+    cplx v = family == 0 ? b_entry(g, cp, M, d, p, c) : (family == 1 ? c_entry(g, cp, M, d, c, p)
+                                                                    : e_entry(g, S, d, y0, c, p));
+    out[i + (int64_t)c * ld] = v;
+  }
+}
+
+// Selected members over all N nodes.  B columns: out[i + t ld] (N x nsel);
+// C / E rows: out[t + i ld] (nsel x N, e.g. rows of Rsel).
+__global__ void k_fill_family_sel(DevGeom g, ContourPtrs cp, int M, double d, int S, double y0, int family,
+                                  const int* sel, int nsel, cplx* out, int64_t ld) {
+  const int64_t tot = g.n * (int64_t)nsel;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    if (family == 0) {
+      const int64_t i = e % g.n;
+      const int t = (int)(e / g.n);
+      out[i + (int64_t)t * ld] = b_entry(g, cp, M, d, i, sel[t]);
+    } else {
+      const int t = (int)(e % nsel);
+      const int64_t i = e / nsel;
+      out[t + i * ld] = family == 1 ? c_entry(g, cp, M, d, sel[t], i) : e_entry(g, S, d, y0, sel[t], i);
+    }
+  }
+}
+
+}  // namespace hbs

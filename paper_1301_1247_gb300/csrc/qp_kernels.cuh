@@ -65,6 +65,15 @@ __global__ void k_bq_update(cplx* A, int64_t m, int64_t n, int64_t s, double* nr
                             const BigQrState* st);
 __global__ void k_bq_tsolve(const cplx* A, int64_t m, int64_t n, int k, cplx* T);
 
+struct ContourPtrs {
+  const cplx* k[2];   // contour nodes of contour 0 and (if present) 1
+  const cplx* wk[2];  // their weights
+};
+__global__ void k_fill_family_sub(DevGeom g, ContourPtrs cp, int M, double d, int S, double y0, int family,
+                                  const int64_t* pts, int np, int nfam, cplx* out, int64_t ld);
+__global__ void k_fill_family_sel(DevGeom g, ContourPtrs cp, int M, double d, int S, double y0, int family,
+                                  const int* sel, int nsel, cplx* out, int64_t ld);
+
 struct RowRef {
   const cplx* base;  // first element of the row
   int64_t ld;        // stride between consecutive columns

@@ -184,39 +184,16 @@ void build_periodizer(Handle& h, cudaStream_t s) {
                                    : std::max(32, 2 * (int)std::ceil(omega * d / (2.0 * M_PI)) + 44);
   h.y0 = h.opts.y0 > 0 ? h.opts.y0 : ymax + 0.25 * d;
   const int S = h.S;
-  h.Esamp.alloc((size_t)12 * S * N);
-  for (int jj = 0; jj < 3; ++jj) {
-    {
-      prof::KScope _ks("k_fill_samples", s);
-      k_fill_samples<<<grid_1d((int64_t)4 * S * N), 256, 0, s>>>(g, S, d, h.y0, (jj - 1) * d, h.Esamp.get() + 4 * S * jj,
-                                                                   12 * S);
-    }
-    HBS_LAUNCH_CHECK("k_fill_samples");
-  }
+  // (the full sampling rows E and wall rows C are only formed for the plain path, on demand)
 
-  // ---- periodizer fills: Y = [B_L^c | B_R^c ...] (N x 4M nc), C_L^c, C_R^c, wall samples
+  // ---- contours' wall-sample rows (small: 4S x 2M each)
   const int ny = 4 * M * nc;
-  DevBuf<cplx> Yfull((size_t)N * ny);
+  ContourPtrs cp{};
   for (int c = 0; c < nc; ++c) {
     ContourData& cd = h.contours[c];
     cd.col_off = (int64_t)4 * M * c;
-    {
-      prof::KScope _ks("k_fill_b", s);
-      k_fill_b<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), cd.dwk.get(), M, d, Yfull.get(), N, cd.col_off,
-                                                        cd.col_off + 2 * M, 0, cmk(0, 0));
-    }
-    HBS_LAUNCH_CHECK("k_fill_b");
-    cd.CL.alloc((size_t)2 * M * N);
-    cd.CR.alloc((size_t)2 * M * N);
-    {
-      prof::KScope _ks("k_fill_c", s);
-      k_fill_c<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), M, d, -0.5 * d, cd.CL.get(), 2 * M);
-    }
-    {
-      prof::KScope _ks("k_fill_c", s);
-      k_fill_c<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), M, -d, 0.5 * d, cd.CR.get(), 2 * M);
-    }
-    HBS_LAUNCH_CHECK("k_fill_c");
+    cp.k[c] = cd.dk.get();
+    cp.wk[c] = cd.dwk.get();
     cd.SL.alloc((size_t)4 * S * 2 * M);
     cd.SR.alloc((size_t)4 * S * 2 * M);
     {
@@ -227,7 +204,11 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     HBS_LAUNCH_CHECK("k_fill_wall_samples");
   }
 
-  // ---- interpolative decompositions of the periodizer blocks on a subsample of points
+  // ---- interpolative decompositions of the periodizer blocks on a subsample of points:
+  // family 0 = columns of Y = [B_L^c | B_R^c ...], 1 = rows of C = [C_L^c; C_R^c ...],
+  // 2 = the Bragg sampling rows E.  Their members are smooth functions of the boundary
+  // node, so an ID found on a fine subsample holds on all N nodes; a disjoint second
+  // subsample checks that.
   ph.next("build:periodizer_id");
   const int ns = (int)std::min<int64_t>(N, 8192);
   std::vector<int64_t> hsub(ns), hsub2(ns);
@@ -241,10 +222,16 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   const double ptol = std::min(0.1 * h.tol, 1e-13);
   const int nce = 12 * S;
   // IDs: returns rank, fills perm (host), T (device), and the check residual on the second subsample.
-  auto subsample_id = [&](auto&& gather, int ncols, std::vector<int>& hperm, DevBuf<cplx>& Tout) -> int {
+  auto subsample_id = [&](int family, int ncols, std::vector<int>& hperm, DevBuf<cplx>& Tout) -> int {
     DevBuf<cplx> A((size_t)ns * ncols), A2((size_t)ns * ncols);
-    gather(dsub.get(), A.get());
-    gather(dsub2.get(), A2.get());
+    {
+      prof::KScope _ks("k_fill_family_sub", s);
+      k_fill_family_sub<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(g, cp, M, d, S, h.y0, family, dsub.get(), ns,
+                                                                      ncols, A.get(), ns);
+      k_fill_family_sub<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(g, cp, M, d, S, h.y0, family, dsub2.get(), ns,
+                                                                      ncols, A2.get(), ns);
+    }
+    HBS_LAUNCH_CHECK("k_fill_family_sub");
     DevBuf<int> perm(ncols);
     DevBuf<cplx> T((size_t)std::min(ns, ncols) * ncols);
     int r = big_row_id(A.get(), ns, ncols, ptol, perm.get(), T.get(), std::min(ns, ncols), s);
@@ -252,7 +239,7 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     Tout.alloc(std::max<int64_t>((int64_t)r * (ncols - r), 1));
     if ((int64_t)r * (ncols - r) > 0)
       HBS_CUDA(cudaMemcpyAsync(Tout.get(), T.get(), sizeof(cplx) * r * (ncols - r), cudaMemcpyDeviceToDevice, s));
-    // check on the second subsample: columns rebuilt from the skeleton columns
+    // check on the second subsample: members rebuilt from the skeleton members
     std::vector<int2> rec(ncols);
     std::vector<int> inv(ncols);
     for (int p = 0; p < ncols; ++p) inv[hperm[p]] = p;
@@ -280,23 +267,9 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   };
   h.pid_residual = 0.0;
   std::vector<int> permY, permC, permE;
-  h.rB = subsample_id([&](const int64_t* sub, cplx* out) {
-    prof::KScope _ks("k_gather_subrows", s);
-    k_gather_subrows<<<grid_1d((int64_t)ns * ny), 256, 0, s>>>(Yfull.get(), N, sub, ns, ny, out, ns);
-  }, ny, permY, h.TY);
-  h.rC = subsample_id([&](const int64_t* sub, cplx* out) {
-    for (int c = 0; c < nc; ++c) {
-      prof::KScope _ks("k_gather_subcols_t", s);
-      k_gather_subcols_t<<<grid_1d((int64_t)ns * 2 * M), 256, 0, s>>>(h.contours[c].CL.get(), 2 * M, 2 * M, sub, ns, out,
-                                                                        ns, 4 * M * c);
-      k_gather_subcols_t<<<grid_1d((int64_t)ns * 2 * M), 256, 0, s>>>(h.contours[c].CR.get(), 2 * M, 2 * M, sub, ns, out,
-                                                                        ns, 4 * M * c + 2 * M);
-    }
-  }, ny, permC, h.TC);
-  h.rE = subsample_id([&](const int64_t* sub, cplx* out) {
-    prof::KScope _ks("k_gather_subcols_t", s);
-    k_gather_subcols_t<<<grid_1d((int64_t)ns * nce), 256, 0, s>>>(h.Esamp.get(), nce, nce, sub, ns, out, ns, 0);
-  }, nce, permE, h.TE);
+  h.rB = subsample_id(0, ny, permY, h.TY);
+  h.rC = subsample_id(1, ny, permC, h.TC);
+  h.rE = subsample_id(2, nce, permE, h.TE);
   HBS_LAUNCH_CHECK("periodizer ids");
 
   // ---- W = A^{-1} [P | Y(:, JY)]
@@ -307,10 +280,14 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   {
     DevBuf<cplx> Wsrc((size_t)N * h.wcols);
     if (l > 0) HBS_CUDA(cudaMemcpyAsync(Wsrc.get(), h.Pnb.get(), sizeof(cplx) * N * l, cudaMemcpyDeviceToDevice, s));
-    for (int i = 0; i < rB; ++i)
-      HBS_CUDA(cudaMemcpyAsync(Wsrc.get() + (int64_t)(l + i) * N, Yfull.get() + (int64_t)permY[i] * N,
-                               sizeof(cplx) * N, cudaMemcpyDeviceToDevice, s));
-    Yfull.release();
+    if (rB > 0) {
+      DevBuf<int> jy;
+      jy.upload(std::vector<int>(permY.begin(), permY.begin() + rB), s);
+      prof::KScope _ks("k_fill_family_sel", s);
+      k_fill_family_sel<<<grid_1d(N * (int64_t)rB), 256, 0, s>>>(g, cp, M, d, S, h.y0, 0, jy.get(), rB,
+                                                                  Wsrc.get() + (int64_t)l * N, N);
+      HBS_CUDA(cudaStreamSynchronize(s));
+    }
     const int64_t chunk = 256;
     for (int64_t c0 = 0; c0 < h.wcols; c0 += chunk) {
       int64_t nq = std::min(chunk, h.wcols - c0);
@@ -322,22 +299,29 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   ph.next("build:Z_products");
   h.rsel = 2 * l + rC + rE;
   {
+    h.Rsel.alloc((size_t)h.rsel * N);
     std::vector<RowRef> refs;
     for (int i = 0; i < l; ++i) refs.push_back({h.Rm.get() + i, l});
     for (int i = 0; i < l; ++i) refs.push_back({h.Rp.get() + i, l});
-    for (int i = 0; i < rC; ++i) {
-      const int a = permC[i], c = a / (4 * M), rr = a % (4 * M);
-      const cplx* base = rr < 2 * M ? h.contours[c].CL.get() + rr : h.contours[c].CR.get() + (rr - 2 * M);
-      refs.push_back({base, 2 * M});
-    }
-    for (int i = 0; i < rE; ++i) refs.push_back({h.Esamp.get() + permE[i], nce});
     DevBuf<RowRef> drefs;
     drefs.upload(refs, s);
-    h.Rsel.alloc((size_t)h.rsel * N);
-    {
+    if (l > 0) {
       prof::KScope _ks("k_gather_rowrefs", s);
-      k_gather_rowrefs<<<grid_1d((int64_t)h.rsel * N), 256, 0, s>>>(drefs.get(), h.rsel, N, h.Rsel.get(), h.rsel);
+      k_gather_rowrefs<<<grid_1d((int64_t)2 * l * N), 256, 0, s>>>(drefs.get(), 2 * l, N, h.Rsel.get(), h.rsel);
     }
+    DevBuf<int> ic, ie;
+    ic.upload(std::vector<int>(permC.begin(), permC.begin() + rC), s);
+    ie.upload(std::vector<int>(permE.begin(), permE.begin() + rE), s);
+    {
+      prof::KScope _ks("k_fill_family_sel", s);
+      if (rC > 0)
+        k_fill_family_sel<<<grid_1d(N * (int64_t)rC), 256, 0, s>>>(g, cp, M, d, S, h.y0, 1, ic.get(), rC,
+                                                                    h.Rsel.get() + 2 * l, h.rsel);
+      if (rE > 0)
+        k_fill_family_sel<<<grid_1d(N * (int64_t)rE), 256, 0, s>>>(g, cp, M, d, S, h.y0, 2, ie.get(), rE,
+                                                                    h.Rsel.get() + 2 * l + rC, h.rsel);
+    }
+    HBS_LAUNCH_CHECK("Rsel fills");
     HBS_CUDA(cudaStreamSynchronize(s));
   }
   DevBuf<cplx> Zc((size_t)h.rsel * h.wcols);
@@ -1203,7 +1187,34 @@ static zc kn_of(double omega, double kap) {
   return v >= 0 ? zc(std::sqrt(v), 0.0) : zc(0.0, std::sqrt(-v));
 }
 
+// Full wall rows C_L^c, C_R^c and Bragg sampling rows E, used only by the plain path.
+static void ensure_full_rows(Handle& h, cudaStream_t s) {
+  const int64_t N = h.N;
+  const int M = h.M, S = h.S;
+  const DevGeom g = Handle_geom(h);
+  if (!h.Esamp.get()) {
+    h.Esamp.alloc((size_t)12 * S * N);
+    for (int jj = 0; jj < 3; ++jj) {
+      prof::KScope _ks("k_fill_samples", s);
+      k_fill_samples<<<grid_1d((int64_t)4 * S * N), 256, 0, s>>>(g, S, h.d, h.y0, (jj - 1) * h.d,
+                                                                   h.Esamp.get() + 4 * S * jj, 12 * S);
+    }
+    HBS_LAUNCH_CHECK("k_fill_samples");
+  }
+  for (auto& cd : h.contours) {
+    if (cd.CL.get()) continue;
+    cd.CL.alloc((size_t)2 * M * N);
+    cd.CR.alloc((size_t)2 * M * N);
+    prof::KScope _ks("k_fill_c", s);
+    k_fill_c<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), M, h.d, -0.5 * h.d, cd.CL.get(), 2 * M);
+    k_fill_c<<<grid_1d(N * (int64_t)M), 256, 0, s>>>(g, cd.dk.get(), M, -h.d, 0.5 * h.d, cd.CR.get(), 2 * M);
+  }
+  HBS_LAUNCH_CHECK("k_fill_c");
+  HBS_CUDA(cudaStreamSynchronize(s));
+}
+
 void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, Result& out, cudaStream_t s) {
+  if (plain) ensure_full_rows(h, s);
   const double omega = h.omega, d = h.d;
   const int l = h.nb_rank, M = h.M, S = h.S;
   const int zr = 2 * l + 4 * M + 12 * S;
