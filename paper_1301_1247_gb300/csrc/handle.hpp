@@ -77,13 +77,13 @@ struct Handle {
   int M = 0;
   double ch = 0.0, cc = 2.0, cw = 2.0, cK = 0.0;
   std::vector<ContourData> contours;
-  DevBuf<cplx> W;              // N x (l + rB): A^{-1} [P | skeleton columns of B]
-  int64_t wcols = 0;
+  int64_t wcols = 0;           // l + rB: columns [P | skeleton columns of B]
   // Interpolative decompositions of the periodizer blocks over all contours:
   //   columns Y = [B_L^0 | B_R^0 | ...] ~ Y(:, JY) [I | TY],  rows C = [C_L^0; C_R^0; ...] and E
   //   ~ rows IC / IE expanded by TC / TE.  Rsel = [R_-1; R_1; C(IC, :); E(IE, :)] (rsel x N).
   int rB = 0, rC = 0, rE = 0, rsel = 0;
   DevBuf<cplx> TY, TC, TE, Rsel;
+  DevBuf<cplx> VT;             // (Rsel A^{-1})^T = A^{-T} Rsel^T  (N x rsel)
   DevBuf<cplx> Zc;             // Rsel A^{-1} [P | Y_sel]  (rsel x (l + rB))
   DevBuf<cplx> PE;             // Bragg rows from their skeleton rows (12 S x rE)
   DevBuf<cplx> EZ;             // PE Zc[E rows]  (12 S x (l + rB))
@@ -96,6 +96,7 @@ struct Handle {
 
   // scratch for applies
   void apply_inverse(const cplx* b, cplx* x, int64_t nrhs, cudaStream_t s) const;
+  void apply_inverse_transpose(const cplx* b, cplx* x, int64_t nrhs, cudaStream_t s) const;
 };
 
 struct AngleResult {

@@ -716,9 +716,12 @@ void build_hbs(Handle& h, cudaStream_t s) {
 
 // x = A^{-1} b through the telescoping factorization (Sec. 4): upward b^_tau = F*_tau b_tau,
 // root solve, downward x_tau = E_tau x^_tau + G_tau b_tau.
-void Handle::apply_inverse(const cplx* b, cplx* xout, int64_t nrhs, cudaStream_t s) const {
+// x = A^{-1} b (trans = false) or x = A^{-T} b (trans = true, the factors transposed:
+// A^{-T} = F*^T (M~ + Dhat)^{-T} E^T + G^T, applied with the same telescoping sweep).
+static void apply_impl(const Handle& H, const cplx* b, cplx* xout, int64_t nrhs, cudaStream_t s, bool trans) {
   if (nrhs <= 0) return;
-  const int Lv = L;
+  const int Lv = H.L;
+  const auto& levels = H.levels;
   // level vectors: up[l] holds b_tau for all nodes of level l (ntot x nrhs, ld = ntot)
   std::vector<DevBuf<cplx>> up(Lv + 1), dn(Lv + 1);
   for (int l = 0; l < Lv; ++l) {
@@ -726,6 +729,7 @@ void Handle::apply_inverse(const cplx* b, cplx* xout, int64_t nrhs, cudaStream_t
     dn[l].alloc(std::max<int64_t>(levels[l].ntot * nrhs, 1));
   }
   auto upptr = [&](int l) -> const cplx* { return l == Lv ? b : up[l].get(); };
+  const int ta = trans ? 1 : 0;
   for (int l = Lv; l >= 1; --l) {
     const Level& lv = levels[l];
     const Level& pa = levels[l - 1];
@@ -735,15 +739,18 @@ void Handle::apply_inverse(const cplx* b, cplx* xout, int64_t nrhs, cudaStream_t
       if (k == 0) continue;
       const int parent = j >> 1;
       const int64_t prow = pa.off[parent] + ((j & 1) ? levels[l].k[j - 1] : 0);
-      gj.push_back({lv.F.get() + lv.f_off[j], upptr(l) + lv.off[j], up[l - 1].get() + prow, k, (int)nrhs, n, k,
-                    (int)lv.ntot, (int)pa.ntot, cmk(1, 0), cmk(0, 0), 0, 0, 0});
+      // upward: F* (k x n), or E^T with E stored n x k
+      const cplx* Aop = trans ? lv.E.get() + lv.e_off[j] : lv.F.get() + lv.f_off[j];
+      const int lda = trans ? n : k;
+      gj.push_back({Aop, upptr(l) + lv.off[j], up[l - 1].get() + prow, k, (int)nrhs, n, lda, (int)lv.ntot,
+                    (int)pa.ntot, cmk(1, 0), cmk(0, 0), 0, 0, 0, ta});
     }
     run_gemms(gj, s);
   }
   {
     std::vector<GemmJob> gj(1);
-    gj[0] = {Groot.get(), up[0].get(), dn[0].get(), nroot, (int)nrhs, nroot, nroot, nroot, nroot, cmk(1, 0), cmk(0, 0),
-             0, 0, 0};
+    gj[0] = {H.Groot.get(), up[0].get(), dn[0].get(), H.nroot, (int)nrhs, H.nroot, H.nroot, H.nroot, H.nroot,
+             cmk(1, 0), cmk(0, 0), 0, 0, 0, ta};
     run_gemms(gj, s);
   }
   for (int l = 1; l <= Lv; ++l) {
@@ -752,12 +759,10 @@ void Handle::apply_inverse(const cplx* b, cplx* xout, int64_t nrhs, cudaStream_t
     cplx* outp = l == Lv ? xout : dn[l].get();
     std::vector<GemmJob> gj;
     for (int j = 0; j < lv.count; ++j) {
-      const int n = lv.n[j], k = lv.k[j];
-      const int parent = j >> 1;
-      const int64_t prow = pa.off[parent] + ((j & 1) ? levels[l].k[j - 1] : 0);
-      // x_tau = G b_tau
+      const int n = lv.n[j];
+      // x_tau = G b_tau  (or G^T b_tau)
       gj.push_back({lv.G.get() + lv.g_off[j], upptr(l) + lv.off[j], outp + lv.off[j], n, (int)nrhs, n, n,
-                    (int)lv.ntot, (int)lv.ntot, cmk(1, 0), cmk(0, 0), 0, 0, 0});
+                    (int)lv.ntot, (int)lv.ntot, cmk(1, 0), cmk(0, 0), 0, 0, 0, ta});
     }
     run_gemms(gj, s);
     gj.clear();
@@ -766,12 +771,22 @@ void Handle::apply_inverse(const cplx* b, cplx* xout, int64_t nrhs, cudaStream_t
       if (k == 0) continue;
       const int parent = j >> 1;
       const int64_t prow = pa.off[parent] + ((j & 1) ? levels[l].k[j - 1] : 0);
-      // x_tau += E x^_tau
-      gj.push_back({lv.E.get() + lv.e_off[j], dn[l - 1].get() + prow, outp + lv.off[j], n, (int)nrhs, k, n,
-                    (int)pa.ntot, (int)lv.ntot, cmk(1, 0), cmk(1, 0), 0, 0, 0});
+      // x_tau += E x^_tau  (or F*^T x^_tau with F* stored k x n)
+      const cplx* Aop = trans ? lv.F.get() + lv.f_off[j] : lv.E.get() + lv.e_off[j];
+      const int lda = trans ? k : n;
+      gj.push_back({Aop, dn[l - 1].get() + prow, outp + lv.off[j], n, (int)nrhs, k, lda, (int)pa.ntot, (int)lv.ntot,
+                    cmk(1, 0), cmk(1, 0), 0, 0, 0, ta});
     }
     run_gemms(gj, s);
   }
+}
+
+void Handle::apply_inverse(const cplx* b, cplx* xout, int64_t nrhs, cudaStream_t s) const {
+  apply_impl(*this, b, xout, nrhs, s, false);
+}
+
+void Handle::apply_inverse_transpose(const cplx* b, cplx* xout, int64_t nrhs, cudaStream_t s) const {
+  apply_impl(*this, b, xout, nrhs, s, true);
 }
 
 }  // namespace hbs

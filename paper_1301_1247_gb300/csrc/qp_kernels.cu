@@ -825,3 +825,16 @@ __global__ void k_fill_family_sel(DevGeom g, ContourPtrs cp, int M, double d, in
 }
 
 }  // namespace hbs
+
+namespace hbs {
+
+// out (cols x rows, column-major) = in^T for in (rows x cols, column-major).
+__global__ void k_transpose(const cplx* in, int64_t rows, int64_t cols, cplx* out) {
+  const int64_t tot = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e % cols, r = e / cols;
+    out[c + r * cols] = in[r + c * rows];
+  }
+}
+
+}  // namespace hbs

@@ -272,31 +272,25 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   h.rE = subsample_id(2, nce, permE, h.TE);
   HBS_LAUNCH_CHECK("periodizer ids");
 
-  // ---- W = A^{-1} [P | Y(:, JY)]
-  ph.next("build:W_apply");
+  // ---- source columns [P | Y(:, JY)] (not applied: Z is formed as V [P | Y_sel])
+  ph.next("build:skeleton_columns");
   const int rB = h.rB, rC = h.rC, rE = h.rE;
   h.wcols = l + rB;
-  h.W.alloc((size_t)N * h.wcols);
+  DevBuf<cplx> Csrc((size_t)N * h.wcols);
   {
-    DevBuf<cplx> Wsrc((size_t)N * h.wcols);
-    if (l > 0) HBS_CUDA(cudaMemcpyAsync(Wsrc.get(), h.Pnb.get(), sizeof(cplx) * N * l, cudaMemcpyDeviceToDevice, s));
+    if (l > 0) HBS_CUDA(cudaMemcpyAsync(Csrc.get(), h.Pnb.get(), sizeof(cplx) * N * l, cudaMemcpyDeviceToDevice, s));
     if (rB > 0) {
       DevBuf<int> jy;
       jy.upload(std::vector<int>(permY.begin(), permY.begin() + rB), s);
       prof::KScope _ks("k_fill_family_sel", s);
       k_fill_family_sel<<<grid_1d(N * (int64_t)rB), 256, 0, s>>>(g, cp, M, d, S, h.y0, 0, jy.get(), rB,
-                                                                  Wsrc.get() + (int64_t)l * N, N);
+                                                                  Csrc.get() + (int64_t)l * N, N);
       HBS_CUDA(cudaStreamSynchronize(s));
-    }
-    const int64_t chunk = 256;
-    for (int64_t c0 = 0; c0 < h.wcols; c0 += chunk) {
-      int64_t nq = std::min(chunk, h.wcols - c0);
-      h.apply_inverse(Wsrc.get() + c0 * N, h.W.get() + c0 * N, nq, s);
     }
   }
 
   // ---- Rsel = [R_-1; R_1; C(IC, :); E(IE, :)] and Z = Rsel W
-  ph.next("build:Z_products");
+  ph.next("build:R_rows");
   h.rsel = 2 * l + rC + rE;
   {
     h.Rsel.alloc((size_t)h.rsel * N);
@@ -324,13 +318,31 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     HBS_LAUNCH_CHECK("Rsel fills");
     HBS_CUDA(cudaStreamSynchronize(s));
   }
+  // ---- V^T = A^{-T} Rsel^T (one transposed apply of the compressed inverse)
+  ph.next("build:V_apply");
+  h.VT.alloc((size_t)N * h.rsel);
+  {
+    DevBuf<cplx> RT((size_t)N * h.rsel);
+    {
+      prof::KScope _ks("k_transpose", s);
+      k_transpose<<<grid_1d((int64_t)N * h.rsel), 256, 0, s>>>(h.Rsel.get(), h.rsel, N, RT.get());
+    }
+    HBS_LAUNCH_CHECK("k_transpose");
+    const int64_t chunk = 256;
+    for (int64_t c0 = 0; c0 < h.rsel; c0 += chunk) {
+      int64_t nq = std::min<int64_t>(chunk, h.rsel - c0);
+      h.apply_inverse_transpose(RT.get() + c0 * N, h.VT.get() + c0 * N, nq, s);
+    }
+  }
+  ph.next("build:Z_products");
   DevBuf<cplx> Zc((size_t)h.rsel * h.wcols);
   {
     std::vector<GemmJob> gj(1);
-    gj[0] = {h.Rsel.get(), h.W.get(), Zc.get(), h.rsel, (int)h.wcols, (int)N, h.rsel, (int)N, h.rsel, cmk(1, 0),
-             cmk(0, 0), 0, 0, 0};
+    gj[0] = {h.VT.get(), Csrc.get(), Zc.get(), h.rsel, (int)h.wcols, (int)N, (int)N, (int)N, h.rsel, cmk(1, 0),
+             cmk(0, 0), 0, 0, 0, 1};
     run_gemms(gj, s);
   }
+  Csrc.release();
   // interpolation matrices of the reduced Schur systems
   std::vector<int> invC(ny), invE(nce), invY(ny);
   for (int p = 0; p < ny; ++p) invC[permC[p]] = p;
@@ -1366,24 +1378,28 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
         }
       }
     }
+    if (!plain) {
+      // Precomputed path: Rsel A^{-1} [b | PW] = V [b | PW] with V^T = A^{-T} Rsel^T formed at
+      // build, so the right-hand sides need no apply of A^{-1}; the reduced Schur systems
+      // work on these compressed projections directly.
+      X.release();
+      ph.next("solve:projections");
+      DevBuf<cplx> Psel((size_t)h.rsel * cols);
+      std::vector<GemmJob> gj(1);
+      gj[0] = {h.VT.get(), RHS.get(), Psel.get(), h.rsel, (int)cols, (int)N, (int)N, (int)N, h.rsel, cmk(1, 0),
+               cmk(0, 0), 0, 0, 0, 1};
+      run_gemms(gj, s);
+      RHS.release();
+      ph.close();
+      reduced_batch(h, gjobs, gmembers, theta, Psel.get(), cols, out, s);
+      continue;
+    }
     h.apply_inverse(RHS.get(), X.get(), cols, s);
     RHS.release();
     // ---- Proj = Rows X
     ph.next("solve:projections");
     DevBuf<cplx> Proj((size_t)zr * cols);
-    if (!plain) {
-      // compressed rows (Rsel, rsel x N) once for all columns; the reduced Schur systems
-      // work on them directly (no expansion to the full wall rows)
-      Proj.release();
-      DevBuf<cplx> Psel((size_t)h.rsel * cols);
-      std::vector<GemmJob> gj(1);
-      gj[0] = {h.Rsel.get(), X.get(), Psel.get(), h.rsel, (int)cols, (int)N, h.rsel, (int)N, h.rsel, cmk(1, 0),
-               cmk(0, 0), 0, 0, 0};
-      run_gemms(gj, s);
-      X.release();
-      reduced_batch(h, gjobs, gmembers, theta, Psel.get(), cols, out, s);
-      continue;
-    } else {
+    {
       std::vector<GemmJob> gj;
       for (int gg = 0; gg < ng; ++gg) {
         const GroupJob& G = gjobs[gg];

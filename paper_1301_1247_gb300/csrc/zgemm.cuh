@@ -17,6 +17,7 @@ struct GemmJob {
   cplx alpha, beta;
   int tiles_m, tiles_n;  // ceil(m / BM), ceil(n / BN)
   int tile_base;         // prefix sum of tiles over earlier jobs
+  int transA;            // 1: op(A) = A^T (A stored k x m, column-major, leading dimension lda)
 };
 
 constexpr int GBM = 32, GBN = 32, GBK = 8;
@@ -46,9 +47,15 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched(const GemmJob* job
   for (int k0 = 0; k0 < K; k0 += GBK) {
     // load A tile (GBM x GBK): 256 threads, one element each
     {
-      int r = tid & 31, kk = tid >> 5;
-      int gr = row0 + r, gk = k0 + kk;
-      As[kk][r] = (gr < m && gk < K) ? jb.A[(int64_t)gk * jb.lda + gr] : cmk(0.0, 0.0);
+      if (jb.transA) {
+        int r = tid >> 3, kk = tid & 7;
+        int gr = row0 + r, gk = k0 + kk;
+        As[kk][r] = (gr < m && gk < K) ? jb.A[(int64_t)gr * jb.lda + gk] : cmk(0.0, 0.0);
+      } else {
+        int r = tid & 31, kk = tid >> 5;
+        int gr = row0 + r, gk = k0 + kk;
+        As[kk][r] = (gr < m && gk < K) ? jb.A[(int64_t)gk * jb.lda + gr] : cmk(0.0, 0.0);
+      }
       int c = tid >> 3, kb = tid & 7;
       int gc = col0 + c, gkb = k0 + kb;
       Bs[kb][c] = (gc < n && gkb < K) ? jb.B[(int64_t)gc * jb.ldb + gkb] : cmk(0.0, 0.0);
