@@ -19,7 +19,7 @@ size_t Handle::device_bytes() const {
   for (const auto& lv : levels)
     b += lv.idx.bytes() + lv.perm.bytes() + lv.T.bytes() + lv.E.bytes() + lv.F.bytes() + lv.G.bytes() +
          lv.Dhat.bytes() + lv.cx.bytes() + lv.cy.bytes() + lv.rad.bytes();
-  b += nb_skel.bytes() + Pnb.bytes() + Rm.bytes() + Rp.bytes() + Esamp.bytes() + VT.bytes() + Zc.bytes() + EZ.bytes() + PE.bytes() + TY.bytes() + TC.bytes() +
+  b += nb_skel.bytes() + Pnb.bytes() + Rm.bytes() + Rp.bytes() + Esamp.bytes() + VT.bytes() + Pdir.bytes() + Zc.bytes() + EZ.bytes() + PE.bytes() + TY.bytes() + TC.bytes() +
        TE.bytes() + Rsel.bytes();
   for (const auto& c : contours)
     b += c.dk.bytes() + c.dwk.bytes() + c.CL.bytes() + c.CR.bytes() + c.SL.bytes() + c.SR.bytes() + c.Zd.bytes();

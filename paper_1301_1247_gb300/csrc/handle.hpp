@@ -87,6 +87,13 @@ struct Handle {
   DevBuf<cplx> Zc;             // Rsel A^{-1} [P | Y_sel]  (rsel x (l + rB))
   DevBuf<cplx> PE;             // Bragg rows from their skeleton rows (12 S x rE)
   DevBuf<cplx> EZ;             // PE Zc[E rows]  (12 S x (l + rB))
+  // V applied to unit plane waves e^{i w (x - c).(cos phi_k, sin phi_k)} at K equispaced
+  // directions phi_k = 2 pi k / K (rsel x K); V b(theta) for any incidence angle follows by
+  // trigonometric interpolation in theta (the plane wave's Jacobi-Anger expansion is
+  // band-limited to |m| <= w max|x - c| + O((w r)^{1/3}) + O(log 1/eps)).
+  DevBuf<cplx> Pdir;
+  int Kdir = 0;
+  double dir_cx = 0.0, dir_cy = 0.0;
   double pid_residual = 0.0;
 
   double build_seconds = 0.0;

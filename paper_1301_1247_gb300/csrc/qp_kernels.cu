@@ -838,3 +838,19 @@ __global__ void k_transpose(const cplx* in, int64_t rows, int64_t cols, cplx* ou
 }
 
 }  // namespace hbs
+
+namespace hbs {
+
+// out[i + k N] = exp(i w ((x_i - cx) cos phi_k + (y_i - cy) sin phi_k)), phi_k = 2 pi k / K.
+__global__ void k_fill_dirs(DevGeom g, double cx, double cy, int K, cplx* out) {
+  const int64_t tot = g.n * (int64_t)K;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % g.n;
+    const int k = (int)(e / g.n);
+    double sn, cs;
+    sincospi(2.0 * (double)k / (double)K, &sn, &cs);
+    out[e] = cexp_i(g.omega * ((g.x[i] - cx) * cs + (g.y[i] - cy) * sn));
+  }
+}
+
+}  // namespace hbs

@@ -87,6 +87,7 @@ __global__ void k_expand_rows(const cplx* in, int64_t ldi, int ncol, const int2*
                               int r1, int off1, const cplx* T2, int r2, int off2, cplx* out, int64_t ldo);
 __global__ void k_expand_cols(const cplx* in, int64_t ldi, int nrow, const int2* recipe, int nout, const cplx* T, int r,
                               int off, const int* skel, cplx* out, int64_t ldo);
+__global__ void k_fill_dirs(DevGeom g, double cx, double cy, int K, cplx* out);
 __global__ void k_transpose(const cplx* in, int64_t rows, int64_t cols, cplx* out);
 __global__ void k_diff_norm2(const cplx* a, int64_t lda, const cplx* b, int64_t ldb, int nrow, int ncol, double* acc);
 

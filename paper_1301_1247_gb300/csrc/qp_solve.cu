@@ -402,6 +402,30 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     HBS_CUDA(cudaStreamSynchronize(s));
   }
   h.Zc = std::move(Zc);
+
+  // ---- V on plane waves in K equispaced incidence directions (interpolated per angle)
+  ph.next("build:direction_samples");
+  {
+    double rdir = 0.0;
+    for (int64_t i = 0; i < N; ++i) rdir = std::max(rdir, std::hypot(h.hx[i] - cx, h.hy[i] - cy));
+    const double wr = omega * rdir;
+    int K = 2 * (int)std::ceil(wr + 10.0 * std::cbrt(wr) + 30.0);
+    K = (K + 31) / 32 * 32;
+    h.Kdir = K;
+    h.dir_cx = cx;
+    h.dir_cy = cy;
+    DevBuf<cplx> src((size_t)N * K);
+    {
+      prof::KScope _ks("k_fill_dirs", s);
+      k_fill_dirs<<<grid_1d(N * (int64_t)K), 256, 0, s>>>(g, cx, cy, K, src.get());
+    }
+    HBS_LAUNCH_CHECK("k_fill_dirs");
+    h.Pdir.alloc((size_t)h.rsel * K);
+    std::vector<GemmJob> gj(1);
+    gj[0] = {h.VT.get(), src.get(), h.Pdir.get(), h.rsel, K, (int)N, (int)N, (int)N, h.rsel, cmk(1, 0), cmk(0, 0), 0, 0,
+             0, 1};
+    run_gemms(gj, s);
+  }
   HBS_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -1333,6 +1357,76 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
     const int ng = (int)gjobs.size();
     const int64_t N = h.N;
     prof::PhaseSeq ph(s);
+    if (!plain) {
+      // Precomputed path: Rsel A^{-1} [b | PW] = V [b | PW] with V^T = A^{-T} Rsel^T formed at
+      // build.  Incident-field columns and propagating Wood's plane waves come from V on
+      // plane waves in K equispaced directions by trigonometric interpolation in the
+      // direction angle: V e^{i k.x} = e^{i k.c} sum_k P_k D_K(psi - phi_k), D_K the
+      // interpolation kernel of K equispaced points.  Evanescent Wood's columns (complex
+      // k_n) are formed directly.  The reduced Schur systems work on these projections.
+      ph.next("solve:projections");
+      int64_t pos = 0;
+      for (auto& G : gjobs) { G.rhs_col = (int)pos; pos += G.q + G.nw; }
+      const int K = h.Kdir;
+      DevBuf<cplx> Psel((size_t)h.rsel * cols);
+      std::vector<cplx> hint((size_t)K * cols, cmk(0, 0));
+      std::vector<RhsCol> evan;
+      std::vector<int64_t> evan_col;
+      size_t rc = 0;
+      auto interp_col = [&](int64_t col, double psi, zc phase) {
+        cplx* dst = hint.data() + (size_t)col * K;
+        for (int k = 0; k < K; ++k) {
+          const double t = psi - 2.0 * M_PI * k / K;
+          const double sh = std::sin(0.5 * t);
+          double dk;
+          if (std::fabs(sh) < 1e-12) dk = 1.0;
+          else dk = (std::sin(0.5 * (K - 1) * t) / sh + std::cos(0.5 * K * t)) / K;
+          dst[k] = cmk(phase.real() * dk, phase.imag() * dk);
+        }
+      };
+      for (int gg = 0; gg < ng; ++gg) {
+        const GroupJob& G = gjobs[gg];
+        for (int a2 = 0; a2 < G.q + G.nw; ++a2, ++rc) {
+          const RhsCol& r = rcols[rc];
+          const int64_t col = G.rhs_col + a2;
+          if (r.ky.y == 0.0) {
+            const double psi = std::atan2(r.ky.x, r.kap);
+            const zc phase = r.sign * std::exp(zc(0.0, r.kap * h.dir_cx + r.ky.x * h.dir_cy));
+            interp_col(col, psi, phase);
+          } else {
+            evan.push_back(r);
+            evan_col.push_back(col);
+          }
+        }
+      }
+      DevBuf<cplx> dint;
+      dint.upload(hint, s);
+      std::vector<GemmJob> gj(1);
+      gj[0] = {h.Pdir.get(), dint.get(), Psel.get(), h.rsel, (int)cols, K, h.rsel, K, h.rsel, cmk(1, 0), cmk(0, 0), 0,
+               0, 0, 0};
+      run_gemms(gj, s);
+      if (!evan.empty()) {
+        const int ne = (int)evan.size();
+        DevBuf<cplx> RHSe((size_t)N * ne), Pe((size_t)h.rsel * ne);
+        DevBuf<RhsCol> dr;
+        dr.upload(evan, s);
+        {
+          prof::KScope _ks("k_fill_rhs", s);
+          k_fill_rhs<<<grid_1d(N * ne), 256, 0, s>>>(g, dr.get(), ne, RHSe.get());
+        }
+        HBS_LAUNCH_CHECK("k_fill_rhs");
+        gj[0] = {h.VT.get(), RHSe.get(), Pe.get(), h.rsel, ne, (int)N, (int)N, (int)N, h.rsel, cmk(1, 0), cmk(0, 0), 0,
+                 0, 0, 1};
+        run_gemms(gj, s);
+        for (int e = 0; e < ne; ++e)
+          HBS_CUDA(cudaMemcpyAsync(Psel.get() + evan_col[e] * h.rsel, Pe.get() + (int64_t)e * h.rsel,
+                                   sizeof(cplx) * h.rsel, cudaMemcpyDeviceToDevice, s));
+        HBS_CUDA(cudaStreamSynchronize(s));
+      }
+      ph.close();
+      reduced_batch(h, gjobs, gmembers, theta, Psel.get(), cols, out, s);
+      continue;
+    }
     ph.next("solve:rhs_apply");
     // ---- right-hand sides, applies
     DevBuf<cplx> RHS((size_t)N * cols), X((size_t)N * cols);
@@ -1378,22 +1472,7 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
         }
       }
     }
-    if (!plain) {
-      // Precomputed path: Rsel A^{-1} [b | PW] = V [b | PW] with V^T = A^{-T} Rsel^T formed at
-      // build, so the right-hand sides need no apply of A^{-1}; the reduced Schur systems
-      // work on these compressed projections directly.
-      X.release();
-      ph.next("solve:projections");
-      DevBuf<cplx> Psel((size_t)h.rsel * cols);
-      std::vector<GemmJob> gj(1);
-      gj[0] = {h.VT.get(), RHS.get(), Psel.get(), h.rsel, (int)cols, (int)N, (int)N, (int)N, h.rsel, cmk(1, 0),
-               cmk(0, 0), 0, 0, 0, 1};
-      run_gemms(gj, s);
-      RHS.release();
-      ph.close();
-      reduced_batch(h, gjobs, gmembers, theta, Psel.get(), cols, out, s);
-      continue;
-    }
+
     h.apply_inverse(RHS.get(), X.get(), cols, s);
     RHS.release();
     // ---- Proj = Rows X
