@@ -54,6 +54,12 @@ typedef struct hbs_geometry {
 } hbs_geometry;
 
 #define HBS_PRECISION_FP64 0
+/* Dense products (the telescoping applies, the level products E, F*, G and the
+ * periodizer projections) in double-float arithmetic: each FP64 operand is split into
+ * two floats and multiplied and accumulated error-free on the FP32 pipes (about 48
+ * significant bits, relative error near 1e-14 per product).  Kernel evaluations, the
+ * interpolative decompositions, the inversions and the Schur solves stay in FP64. */
+#define HBS_PRECISION_DOUBLE_FLOAT 1
 
 typedef struct hbs_options {
   int leaf_size;        /* maximum points per leaf of the binary tree (default 64) */
@@ -69,7 +75,7 @@ typedef struct hbs_options {
   double wood_shift;    /* crossing point t0 of the second contour (0: automatic, < 0: none) */
   int n_bragg_samples;  /* samples per line for the Bragg DFT (0: automatic) */
   double y0;            /* Bragg sampling height (0: max |y| + d/4) */
-  int precision;        /* HBS_PRECISION_FP64 */
+  int precision;        /* HBS_PRECISION_FP64 (default) or HBS_PRECISION_DOUBLE_FLOAT */
 } hbs_options;
 
 typedef struct hbs_info_t {

@@ -1,5 +1,6 @@
 // C ABI of the library (include/hbsqp.h): argument checks, handle lifetime, error codes.
 #include <chrono>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -13,6 +14,32 @@ namespace hbs {
 
 static thread_local std::string g_last_error;
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+bool& gemm_double_float() {
+  static thread_local bool df = false;
+  return df;
+}
+
+cudaStream_t& current_stream() {
+  static thread_local cudaStream_t s = nullptr;
+  return s;
+}
+
+// Keep freed memory in the device's default pool (the library frees and reallocates
+// work arrays at every level and batch); the pool belongs to this process's context.
+void init_memory_pool() {
+  static std::once_flag once[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return; }
+  std::call_once(once[dev], [dev] {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  });
+}
 
 size_t Handle::device_bytes() const {
   size_t b = x.bytes() + y.bytes() + nx.bytes() + ny.bytes() + w.bytes() + Groot.bytes();
@@ -115,6 +142,7 @@ hbs_status hbs_build(const hbs_geometry* geom, double omega, double tol, const h
     return HBS_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScope scope(s);
   hbs_handle* hh = new (std::nothrow) hbs_handle();
   if (!hh) { set_last_error("host allocation failed"); return HBS_ERR_OOM; }
   hbs_status st = guarded([&] {
@@ -125,7 +153,9 @@ hbs_status hbs_build(const hbs_geometry* geom, double omega, double tol, const h
     if (h.opts.leaf_size < 8) h.opts.leaf_size = 64;
     if (h.opts.n_proxy_min < 8) h.opts.n_proxy_min = 64;
     if (!(h.opts.proxy_rho > 1.0)) h.opts.proxy_rho = 1.5;
-    if (h.opts.precision != HBS_PRECISION_FP64) throw Error(HBS_ERR_INVALID_ARG, "unsupported precision mode");
+    if (h.opts.precision != HBS_PRECISION_FP64 && h.opts.precision != HBS_PRECISION_DOUBLE_FLOAT)
+      throw Error(HBS_ERR_INVALID_ARG, "unsupported precision mode");
+    GemmModeScope gm(h.opts.precision == HBS_PRECISION_DOUBLE_FLOAT);
     h.omega = omega;
     h.tol = tol;
     load_geometry(h, geom, s);
@@ -157,7 +187,9 @@ static hbs_status solve_common(hbs_handle* h, const double* theta, int64_t n_the
   hbs_result* r = new (std::nothrow) hbs_result();
   if (!r) { set_last_error("host allocation failed"); return HBS_ERR_OOM; }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScope scope(s);
   hbs_status st = guarded([&] {
+    GemmModeScope gm(h->h.opts.precision == HBS_PRECISION_DOUBLE_FLOAT && !plain);
     solve_angles(h->h, theta, n_theta, plain, r->r, s);
     HBS_CUDA(cudaStreamSynchronize(s));
   });
@@ -236,7 +268,9 @@ hbs_status hbs_apply_inverse(const hbs_handle* hh, const void* b, void* x, int64
   if (!hh || !b || !x || nrhs < 0) { set_last_error("bad arguments to hbs_apply_inverse"); return HBS_ERR_INVALID_ARG; }
   if (b == x) { set_last_error("b and x must not alias"); return HBS_ERR_INVALID_ARG; }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScope scope(s);
   return guarded([&] {
+    GemmModeScope gm(hh->h.opts.precision == HBS_PRECISION_DOUBLE_FLOAT);
     hh->h.apply_inverse(static_cast<const cplx*>(b), static_cast<cplx*>(x), nrhs, s);
     HBS_CUDA(cudaStreamSynchronize(s));
   });
@@ -250,6 +284,7 @@ hbs_status hbs_kernel_block(const hbs_geometry* geom, double omega, int kind, do
     return HBS_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScope scope(s);
   return guarded([&] {
     DevBuf<double> nx, ny, w;
     DevGeom g = geom_view(geom, omega, nx, ny, w, s);
@@ -270,6 +305,7 @@ hbs_status hbs_row_id(void* mt, int64_t m, int64_t n, double tol, int* rank, int
     return HBS_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScope scope(s);
   return guarded([&] {
     if (n <= 4096) {
       std::vector<CpqrJob> jobs(1);
@@ -284,7 +320,15 @@ hbs_status hbs_row_id(void* mt, int64_t m, int64_t n, double tol, int* rank, int
   });
 }
 
-void hbs_free(hbs_handle* h) { delete h; }
+void hbs_free(hbs_handle* h) {
+  if (!h) return;
+  // the handle's buffers are freed in stream order on the legacy stream; finish all work first
+  cudaDeviceSynchronize();
+  StreamScope scope(nullptr);
+  delete h;
+  cudaDeviceSynchronize();
+  cudaGetLastError();
+}
 void hbs_result_free(hbs_result* r) { delete r; }
 const char* hbs_last_error(void) { return g_last_error.c_str(); }
 

@@ -29,7 +29,10 @@ inline void cuda_check(cudaError_t e, const char* what) {
 #define HBS_CUDA(call) ::hbs::cuda_check((call), #call)
 #define HBS_LAUNCH_CHECK(name) ::hbs::cuda_check(cudaGetLastError(), name)
 
-// Owning device allocation (cudaMalloc / cudaFree).
+cudaStream_t& current_stream();
+
+// Owning device allocation (stream-ordered cudaMallocAsync / cudaFreeAsync on the
+// library's current stream).
 template <typename T>
 class DevBuf {
  public:
@@ -47,12 +50,12 @@ class DevBuf {
     release();
     if (n == 0) return;
     void* p = nullptr;
-    HBS_CUDA(cudaMalloc(&p, n * sizeof(T)));
+    HBS_CUDA(cudaMallocAsync(&p, n * sizeof(T), current_stream()));
     p_ = static_cast<T*>(p);
     n_ = n;
   }
   void release() {
-    if (p_) cudaFree(p_);
+    if (p_) cudaFreeAsync(p_, current_stream());
     p_ = nullptr;
     n_ = 0;
   }
@@ -80,5 +83,30 @@ class DevBuf {
 };
 
 void set_last_error(const std::string& msg);
+
+// Stream on which the library allocates and frees device memory.  Every C entry point
+// that works on a stream installs it for its duration (StreamScope); allocations are
+// stream ordered (cudaMallocAsync / cudaFreeAsync from the device's memory pool), so
+// freeing a buffer does not synchronize the device and memory is reused in stream order.
+cudaStream_t& current_stream();
+void init_memory_pool();
+
+// Arithmetic of the library's batched GEMMs on this thread: FP64 (false) or double-float
+// (true), set for the duration of a call from the handle's precision option.
+bool& gemm_double_float();
+struct GemmModeScope {
+  bool prev;
+  explicit GemmModeScope(bool df) : prev(gemm_double_float()) { gemm_double_float() = df; }
+  ~GemmModeScope() { gemm_double_float() = prev; }
+};
+
+struct StreamScope {
+  cudaStream_t prev;
+  explicit StreamScope(cudaStream_t s) : prev(current_stream()) {
+    init_memory_pool();
+    current_stream() = s;
+  }
+  ~StreamScope() { current_stream() = prev; }
+};
 
 }  // namespace hbs

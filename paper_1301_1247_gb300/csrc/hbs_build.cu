@@ -256,24 +256,99 @@ __global__ void k_gather_skel(const GatherJob* jobs, const int64_t* src_idx, con
 // host orchestration
 // ---------------------------------------------------------------------------
 
-static void launch_gemms(std::vector<GemmJob>& jobs, cudaStream_t s) {
-  if (jobs.empty()) return;
-  int64_t tiles = gemm_plan(jobs.data(), (int)jobs.size());
-  if (tiles == 0) return;
-  DevBuf<GemmJob> dj(jobs.size());
-  HBS_CUDA(cudaMemcpyAsync(dj.get(), jobs.data(), jobs.size() * sizeof(GemmJob), cudaMemcpyHostToDevice, s));
+// C = beta C + sum of the split-K partial products W_s (fixed order: deterministic).
+struct SplitRed {
+  cplx* C;
+  const cplx* W;
+  int m, n, ldc, splits;
+  cplx beta;
+};
+__global__ void k_splitk_reduce(const SplitRed* reds, int nred) {
+  const SplitRed r = reds[blockIdx.y];
+  const int64_t tot = (int64_t)r.m * r.n, mn = tot;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % r.m);
+    const int64_t j = e / r.m;
+    cplx acc = cmk(0.0, 0.0);
+    for (int sidx = 0; sidx < r.splits; ++sidx) acc = cadd(acc, r.W[sidx * mn + e]);
+    cplx* c = r.C + j * r.ldc + i;
+    if (r.beta.x != 0.0 || r.beta.y != 0.0) acc = cfma(r.beta, *c, acc);
+    *c = acc;
+  }
+}
+
+// Batched GEMMs.  Jobs with a long inner dimension and few output tiles (tall-skinny
+// products over all N boundary nodes) are split along K so that every SM gets work; the
+// partial products are summed in a fixed order by k_splitk_reduce.
+static void launch_gemms(std::vector<GemmJob>& jobs_in, cudaStream_t s) {
+  if (jobs_in.empty()) return;
   double fl = 0.0, by = 0.0;
-  for (const auto& j : jobs) {
+  for (const auto& j : jobs_in) {
     fl += 8.0 * j.m * (double)j.n * j.k;
     by += 16.0 * ((double)j.m * j.k + (double)j.k * j.n + (double)j.m * j.n *
                   ((j.beta.x != 0.0 || j.beta.y != 0.0) ? 2.0 : 1.0));
   }
-  {
-    prof::KScope _ks("k_zgemm_batched", s, fl, by);
-    k_zgemm_batched<<<(unsigned)tiles, 256, 0, s>>>(dj.get(), (int)jobs.size());
+  std::vector<GemmJob> jobs;
+  std::vector<SplitRed> reds;
+  std::vector<size_t> red_ws_off;
+  int64_t ws = 0;
+  for (const auto& j : jobs_in) {
+    const int64_t tiles = (int64_t)((j.m + GBM - 1) / GBM) * ((j.n + GBN - 1) / GBN);
+    int splits = 1;
+    if (j.k >= 8192 && tiles > 0 && tiles < 304) {
+      splits = (int)std::min<int64_t>((j.k + 4095) / 4096, std::max<int64_t>(1, 1216 / tiles));
+    }
+    if (splits <= 1) {
+      jobs.push_back(j);
+      continue;
+    }
+    int chunk = (j.k + splits - 1) / splits;
+    chunk = (chunk + GBK - 1) / GBK * GBK;
+    splits = (j.k + chunk - 1) / chunk;
+    SplitRed r{j.C, nullptr, j.m, j.n, j.ldc, splits, j.beta};
+    reds.push_back(r);
+    red_ws_off.push_back((size_t)ws);
+    for (int sidx = 0; sidx < splits; ++sidx) {
+      const int k0 = sidx * chunk, kl = std::min(chunk, j.k - k0);
+      GemmJob sj = j;
+      sj.A = j.transA ? j.A + k0 : j.A + (int64_t)k0 * j.lda;
+      sj.B = j.B + k0;
+      sj.k = kl;
+      sj.C = nullptr;  // set below (workspace)
+      sj.ldc = j.m;
+      sj.beta = cmk(0.0, 0.0);
+      sj.tile_base = (int)(ws + (int64_t)sidx * j.m * j.n);  // temporary: workspace offset
+      jobs.push_back(sj);
+    }
+    ws += (int64_t)splits * j.m * j.n;
+  }
+  DevBuf<cplx> W(std::max<int64_t>(ws, 1));
+  for (auto& j : jobs)
+    if (j.C == nullptr) j.C = W.get() + j.tile_base;
+  for (size_t r = 0; r < reds.size(); ++r) reds[r].W = W.get() + red_ws_off[r];
+  int64_t tiles = gemm_plan(jobs.data(), (int)jobs.size());
+  if (tiles > 0) {
+    DevBuf<GemmJob> dj(jobs.size());
+    HBS_CUDA(cudaMemcpyAsync(dj.get(), jobs.data(), jobs.size() * sizeof(GemmJob), cudaMemcpyHostToDevice, s));
+    if (gemm_double_float()) {
+      prof::KScope _ks("k_zgemm_batched_df", s, fl, by);
+      k_zgemm_batched_df<<<(unsigned)tiles, 256, 0, s>>>(dj.get(), (int)jobs.size());
+    } else {
+      prof::KScope _ks("k_zgemm_batched", s, fl, by);
+      k_zgemm_batched<<<(unsigned)tiles, 256, 0, s>>>(dj.get(), (int)jobs.size());
+    }
   }
   HBS_LAUNCH_CHECK("k_zgemm_batched");
-  HBS_CUDA(cudaStreamSynchronize(s));  // job table is freed on return
+  if (!reds.empty()) {
+    DevBuf<SplitRed> dr(reds.size());
+    HBS_CUDA(cudaMemcpyAsync(dr.get(), reds.data(), reds.size() * sizeof(SplitRed), cudaMemcpyHostToDevice, s));
+    int64_t mx = 0;
+    for (auto& r : reds) mx = std::max<int64_t>(mx, (int64_t)r.m * r.n);
+    prof::KScope _ks("k_splitk_reduce", s);
+    k_splitk_reduce<<<dim3(grid_1d(mx, 256, 1024), (unsigned)reds.size()), 256, 0, s>>>(dr.get(), (int)reds.size());
+    HBS_LAUNCH_CHECK("k_splitk_reduce");
+  }
+  // job tables and the workspace are freed in stream order (cudaFreeAsync) after the kernels
 }
 
 void run_gemms(std::vector<GemmJob>& jobs, cudaStream_t s) { launch_gemms(jobs, s); }

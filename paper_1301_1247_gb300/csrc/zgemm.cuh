@@ -87,6 +87,134 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched(const GemmJob* job
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float variant.  FP64 operands are split on load into float pairs (hi, lo),
+// hi = fl32(x), lo = fl32(x - hi), and every multiply-add is carried out in double-float
+// arithmetic on the FP32 pipes (error-free product via fmaf, error-free sum via two-sum,
+// about 48 significant bits).  GB300 issues FP32 FMAs at 64x its FP64 rate, so the
+// double-float product is several times faster than DFMA while keeping relative
+// errors near 2^-48 per operation; results are written back in FP64.
+// ---------------------------------------------------------------------------
+struct df2 {
+  float h, l;
+};
+__device__ __forceinline__ df2 df_split(double x) {
+  df2 r;
+  r.h = __double2float_rn(x);
+  r.l = __double2float_rn(x - (double)r.h);
+  return r;
+}
+// acc += x * y   (double-float, lazy low part; renormalised by df_norm)
+// (explicit _rn intrinsics: the compiler may not contract these into FMAs, which would
+// break the error-free transformations)
+__device__ __forceinline__ void df_mac(float xh, float xl, float yh, float yl, float& ah, float& al) {
+  const float p = __fmul_rn(xh, yh);
+  float e = fmaf(xh, yh, -p);
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  const float sum = __fadd_rn(ah, p);
+  const float v = __fsub_rn(sum, ah);
+  const float t = __fadd_rn(__fsub_rn(ah, __fsub_rn(sum, v)), __fsub_rn(p, v));
+  al = __fadd_rn(al, __fadd_rn(t, e));
+  ah = sum;
+}
+__device__ __forceinline__ void df_norm(float& ah, float& al) {
+  const float sum = __fadd_rn(ah, al);
+  al = __fsub_rn(al, __fsub_rn(sum, ah));
+  ah = sum;
+}
+
+struct dfc {
+  float rh, rl, ih, il;
+};
+
+static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* jobs, int njobs) {
+  __shared__ dfc As[GBK][GBM + 1];
+  __shared__ dfc Bs[GBK][GBN + 1];
+  int t = blockIdx.x;
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_base <= t) lo = mid; else hi = mid - 1;
+  }
+  const GemmJob& jb = jobs[lo];
+  t -= jb.tile_base;
+  const int tm = t % jb.tiles_m, tn = t / jb.tiles_m;
+  const int row0 = tm * GBM, col0 = tn * GBN;
+  const int tid = threadIdx.x;
+  const int tr = tid & 15, tc = tid >> 4;
+  dfc acc[2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) acc[a][b] = {0.f, 0.f, 0.f, 0.f};
+  const int m = jb.m, n = jb.n, K = jb.k;
+  auto to_dfc = [](cplx v) {
+    df2 re = df_split(v.x), im = df_split(v.y);
+    dfc r;
+    r.rh = re.h; r.rl = re.l; r.ih = im.h; r.il = im.l;
+    return r;
+  };
+  for (int k0 = 0; k0 < K; k0 += GBK) {
+    {
+      cplx av;
+      int r, kk;
+      if (jb.transA) {
+        r = tid >> 3; kk = tid & 7;
+        int gr = row0 + r, gk = k0 + kk;
+        av = (gr < m && gk < K) ? jb.A[(int64_t)gr * jb.lda + gk] : cmk(0.0, 0.0);
+      } else {
+        r = tid & 31; kk = tid >> 5;
+        int gr = row0 + r, gk = k0 + kk;
+        av = (gr < m && gk < K) ? jb.A[(int64_t)gk * jb.lda + gr] : cmk(0.0, 0.0);
+      }
+      As[kk][r] = to_dfc(av);
+      int c = tid >> 3, kb = tid & 7;
+      int gc = col0 + c, gkb = k0 + kb;
+      Bs[kb][c] = to_dfc((gc < n && gkb < K) ? jb.B[(int64_t)gc * jb.ldb + gkb] : cmk(0.0, 0.0));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      const dfc a[2] = {As[kk][tr], As[kk][tr + 16]};
+      const dfc b[2] = {Bs[kk][tc], Bs[kk][tc + 16]};
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+          dfc& c = acc[x][y];
+          // re += ar br - ai bi ; im += ar bi + ai br
+          df_mac(a[x].rh, a[x].rl, b[y].rh, b[y].rl, c.rh, c.rl);
+          df_mac(-a[x].ih, -a[x].il, b[y].ih, b[y].il, c.rh, c.rl);
+          df_mac(a[x].rh, a[x].rl, b[y].ih, b[y].il, c.ih, c.il);
+          df_mac(a[x].ih, a[x].il, b[y].rh, b[y].rl, c.ih, c.il);
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+      for (int y = 0; y < 2; ++y) {
+        df_norm(acc[x][y].rh, acc[x][y].rl);
+        df_norm(acc[x][y].ih, acc[x][y].il);
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int gr = row0 + tr + 16 * a, gc = col0 + tc + 16 * b;
+      if (gr < m && gc < n) {
+        cplx* c = jb.C + (int64_t)gc * jb.ldc + gr;
+        const dfc& q = acc[a][b];
+        cplx v = cmul(jb.alpha, cmk((double)q.rh + (double)q.rl, (double)q.ih + (double)q.il));
+        if (jb.beta.x != 0.0 || jb.beta.y != 0.0) v = cfma(jb.beta, *c, v);
+        *c = v;
+      }
+    }
+  }
+}
+
 // Host helper: fill tile bookkeeping and return the total tile count.
 inline int64_t gemm_plan(GemmJob* jobs, int njobs) {
   int64_t tot = 0;

@@ -155,3 +155,32 @@ def test_plain_path_matches_precomputed_path():
         _, c1, d1, _ = a.bragg(i)
         _, c2, d2, _ = b.bragg(i)
         assert relerr(np.concatenate([c1, d1]), np.concatenate([c2, d2])) < 1e-11
+
+
+def test_double_float_products_match_oracle_and_fp64():
+    """HBS_PRECISION_DOUBLE_FLOAT (dense products in double-float arithmetic) stays within the
+    FP64 bar: Bragg amplitudes vs the dense oracle, and vs the all-FP64 plain path."""
+    hbs = require_lib()
+    x, y, dx, dy = inputs.star(0.3, 0.3, 5).sample(400)
+    omega = 10.0
+    h = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12, hbs.default_options(precision=1))
+    info = h.info()
+    thetas = np.array([-math.pi / 5, -1.0, -2.5])
+    res = h.solve(thetas)
+    for i, th in enumerate(thetas):
+        nw, t0 = res.angle_info(i)
+        sol = qd.dense_solve(x, y, dx, dy, omega, 1.0, th, qd.Options(**_oracle_opts(info), t0=t0))
+        _, c, d, _ = res.bragg(i)
+        assert relerr(np.concatenate([c, d]), qd.bragg_vector(sol)) < 1e-10
+    obs = inputs.wiggly(0, 0.35, 20, 0.03)
+    x, y, dx, dy = obs.sample(3000)
+    omega = 30.0
+    hdf = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12, hbs.default_options(precision=1))
+    h64 = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12)
+    thetas = inputs.bloch_grouped_angles(9, omega, 1.0, 3, 4).ravel()
+    a = hdf.solve(thetas)
+    b = h64.solve_plain(thetas)
+    for i in range(len(thetas)):
+        _, c1, d1, _ = a.bragg(i)
+        _, c2, d2, _ = b.bragg(i)
+        assert relerr(np.concatenate([c1, d1]), np.concatenate([c2, d2])) < 1e-10
