@@ -108,9 +108,11 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   }
   int np = h.opts.nb_proxies;
   if (np <= 0) {
-    double q = std::max(rmax / R, R / rfar);
-    q = std::min(q, 0.97);
-    np = (int)(2.0 * (std::ceil(omega * R) + std::ceil(std::log(1e-16) / std::log(q))));
+    // The fields of image sources beyond r_far restricted to the obstacle (radius r_max)
+    // have Fourier-Bessel modes decaying like (r_max / r_far)^|m| past |m| ~ w R; the
+    // proxy circle must span modes up to that cut-off (an ID needs the span only).
+    double q = std::min(rmax / rfar, 0.97);
+    np = (int)(2.0 * (std::ceil(omega * R) + std::ceil(std::log(1e-16) / std::log(q)) + 8));
     np = std::max(64, std::min(np, 2048));
     np = (np + 7) / 8 * 8;
   }
