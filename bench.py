@@ -150,11 +150,14 @@ def run_ours(args, ws, rank, local):
     stream = torch.cuda.current_stream()
     tol = 1e-12
 
+    prec = 1 if args.precision == "df" else 0
+    opts = hbs.default_options(precision=prec)
+
     def step(device_inputs: bool):
         if device_inputs:
-            h = hbs.Handle(gx, gy, gdx, gdy, d, omega, tol, stream=stream)
+            h = hbs.Handle(gx, gy, gdx, gdy, d, omega, tol, opts, stream=stream)
         else:
-            h = hbs.Handle(hx.numpy(), hy.numpy(), hdx.numpy(), hdy.numpy(), d, omega, tol, stream=stream)
+            h = hbs.Handle(hx.numpy(), hy.numpy(), hdx.numpy(), hdy.numpy(), d, omega, tol, opts, stream=stream)
         r = h.solve(hth.numpy(), stream=stream)
         amps = [r.bragg(i) for i in range(len(thetas))]
         return h, r, amps
@@ -205,6 +208,24 @@ def run_ours(args, ws, rank, local):
     e2e_ms = max_over_ranks(max(e2.elapsed_time(e3), 1e3 * (time.perf_counter() - t0)), ws)
     flux = [a[3] for a in amps]
 
+    # accuracy check (outside the timed region): one Bloch group against the all-FP64 plain
+    # per-phase path (q + 2M + 2l applies of an FP64-built compressed inverse)
+    err = None
+    if not args.no_check:
+        th2 = np.asarray(w["thetas"])
+        gsel = th2[0] if th2.ndim == 2 else thetas[: min(10, len(thetas))]
+        idx = [int(np.flatnonzero(thetas == t)[0]) for t in gsel]
+        h64 = hbs.Handle(x, y, dx, dy, d, omega, tol)
+        ref = h64.solve_plain(gsel)
+        errs = []
+        for i, k in enumerate(idx):
+            _, c1, d1, _ = amps[k]
+            _, c2, d2, _ = ref.bragg(i)
+            a, b = np.concatenate([c1, d1]), np.concatenate([c2, d2])
+            errs.append(float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+        err = max(errs)
+        del h64, ref
+
     n_ang = len(thetas)
     value = ws * n_ang * args.steps / (ms_max / 1e3)
     kern = {k: v for k, v in prof.items() if not k.startswith("phase:")}
@@ -220,14 +241,19 @@ def run_ours(args, ws, rank, local):
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (complex128); dense products in double-float (2xFP32)" if prec else "f64 (complex128)",
+        "data": "synthetic", "err_vs_fp64_plain_path": err,
         "config": {"workload": w["name"], "N": n, "omega": omega, "d": d, "angles": n_ang,
                    "bloch_groups": int(np.asarray(w["thetas"]).shape[0]) if np.asarray(w["thetas"]).ndim == 2 else None,
                    "tol": tol, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (factor + precompute %.1f GB resident)" % (info["device_bytes"] / 1e9),
                    "build_s": round(info["build_seconds"], 3), "max_rank": info["max_rank"],
                    "nb_rank": info["nb_rank"], "M": info["m"], "levels": info["levels"],
-                   "phases_ms_per_step": phases, "max_flux_error": float(max(flux))},
+                   "phases_ms_per_step": phases, "max_flux_error": float(max(flux)),
+                   "solve_angles_per_s": round(n_ang / (phases.get("solve:projections", 0) / 1e3 +
+                                                       phases.get("solve:schur", 0) / 1e3 +
+                                                       phases.get("solve:bragg", 0) / 1e3 + 1e-9), 1)},
         "e2e": {"value": round(ws * n_ang * args.steps / (e2e_ms / 1e3), 3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
@@ -295,6 +321,8 @@ def main():
     ap.add_argument("--workload", default="complicated_n100k")
     ap.add_argument("--cpu-sample-n", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true", help="skip the FP64 plain-path accuracy check")
+    ap.add_argument("--precision", choices=["fp64", "df"], default="df")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":

@@ -476,3 +476,21 @@ def bragg(bd, ct, omega, d, theta, alpha, eta, xi, wood, wc, y0, n_samples, p=1)
 def bragg_vector(sol: Solution) -> np.ndarray:
     """All propagating amplitudes (c_n then d_n) as one vector, for relative-error checks."""
     return np.concatenate([sol.c, sol.d])
+
+
+def a_rows(bd: Boundary, omega: float, rows) -> np.ndarray:
+    """Selected rows of A (Sec. 2.3), each evaluated directly: delta/2 + (2 pi/N) R_{|n-m|} K w."""
+    rows = np.asarray(rows, dtype=np.int64)
+    n = bd.n
+    idx = np.arange(n)
+    out = np.zeros((len(rows), n), dtype=np.complex128)
+    rw_all = kr6.weights(n)
+    for t, i in enumerate(rows):
+        dist = np.abs(idx - i)
+        dist = np.minimum(dist, n - dist)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            k = combined(bd.x[i], bd.y[i], bd.x, bd.y, bd.nx, bd.ny, omega)
+        k[i] = 0.0
+        out[t] = rw_all[dist] * k * bd.w
+        out[t, i] += 0.5
+    return out

@@ -100,3 +100,11 @@ def test_target_gradient_matches_finite_differences():
     fy = (qd.combined(tx, ty + e, sx, sy, snx, sny, omega) - qd.combined(tx, ty - e, sx, sy, snx, sny, omega)) / (2 * e)
     assert np.allclose(gx, fx, rtol=1e-7, atol=1e-7)
     assert np.allclose(gy, fy, rtol=1e-7, atol=1e-7)
+
+
+def test_a_rows_are_rows_of_a():
+    """The row-by-row evaluation used at full size reproduces rows of the dense A."""
+    x, y, dx, dy = inputs.star(0.3, 0.3, 5).sample(200)
+    bd = qd.boundary(x, y, dx, dy)
+    rows = [0, 1, 7, 100, 199]
+    assert np.allclose(qd.a_rows(bd, 10.0, rows), qd.matrix_a(bd, 10.0)[rows], rtol=0, atol=1e-15)
