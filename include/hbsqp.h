@@ -98,6 +98,7 @@ typedef struct hbs_info_t {
   int pid_col_rank;      /* skeleton columns kept of the wall blocks B_L, B_R (all contours) */
   int pid_row_rank;      /* skeleton rows kept of C_L, C_R and of the Bragg sampling rows */
   double pid_residual;   /* relative error of those decompositions on an independent point sample */
+  double nb_residual;    /* relative error of the neighbour ID (Sec. 3.2) on nodes between its candidates */
 } hbs_info_t;
 
 /* Fill `opts` with the defaults listed above. */
@@ -152,6 +153,27 @@ hbs_status hbs_result_angle_info(const hbs_result* r, int64_t i, int* n_wood, do
 
 /* Sizes and timings of a built handle. */
 hbs_status hbs_info(const hbs_handle* h, hbs_info_t* info);
+
+/*
+ * Persistence of a built handle.  The pre-computation (Sec. 6, first step) depends
+ * only on the geometry, w and the options, and the block solves (second step) reuse
+ * it for any number of angles, so a process may write it once and later processes
+ * read it instead of rebuilding.
+ *
+ * hbs_save writes every factor, skeleton, interpolation matrix and precomputed product
+ * of `h` to `path` (native byte order, a private binary format with a version tag) and
+ * returns when the file is complete.  It copies device data to the host through
+ * `stream`.  Errors: HBS_ERR_INVALID_ARG (NULL argument), HBS_ERR_IO (cannot open or
+ * write the file), HBS_ERR_CUDA.
+ *
+ * hbs_load reads such a file into a new handle on the current device (allocations and
+ * copies on `stream`); the handle is owned by the caller (hbs_free) and solves exactly
+ * like the one that was saved.  The file's tag is checked before any device memory is
+ * touched.  Errors: HBS_ERR_INVALID_ARG, HBS_ERR_IO (missing, foreign, truncated or
+ * corrupt file), HBS_ERR_OOM, HBS_ERR_CUDA.  On error *out is NULL.
+ */
+hbs_status hbs_save(const hbs_handle* h, const char* path, void* stream);
+hbs_status hbs_load(const char* path, void* stream, hbs_handle** out);
 
 /*
  * x = A^{-1} b with the compressed inverse (Sec. 4, telescoping apply),

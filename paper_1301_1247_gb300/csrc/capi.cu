@@ -261,6 +261,7 @@ hbs_status hbs_info(const hbs_handle* hh, hbs_info_t* info) {
   info->pid_col_rank = h.rB;
   info->pid_row_rank = h.rC + h.rE;
   info->pid_residual = h.pid_residual;
+  info->nb_residual = h.nb_residual;
   return HBS_OK;
 }
 
@@ -318,6 +319,33 @@ hbs_status hbs_row_id(void* mt, int64_t m, int64_t n, double tol, int* rank, int
     }
     HBS_CUDA(cudaStreamSynchronize(s));
   });
+}
+
+hbs_status hbs_save(const hbs_handle* h, const char* path, void* stream) {
+  if (!h || !path) {
+    set_last_error("bad arguments to hbs_save");
+    return HBS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScope scope(s);
+  return guarded([&] { save_handle(const_cast<hbs_handle*>(h)->h, path, s); });
+}
+
+hbs_status hbs_load(const char* path, void* stream, hbs_handle** out) {
+  if (!out) { set_last_error("out is NULL"); return HBS_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (!path) { set_last_error("path is NULL"); return HBS_ERR_INVALID_ARG; }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScope scope(s);
+  hbs_handle* hh = new (std::nothrow) hbs_handle();
+  if (!hh) { set_last_error("host allocation failed"); return HBS_ERR_OOM; }
+  hbs_status st = guarded([&] { load_handle(hh->h, path, s); });
+  if (st != HBS_OK) {
+    delete hh;
+    return st;
+  }
+  *out = hh;
+  return HBS_OK;
 }
 
 void hbs_free(hbs_handle* h) {

@@ -61,7 +61,8 @@ __device__ __forceinline__ cplx csqrt_principal(cplx z) {
 // Hankel functions of the first kind, orders 0 and 1, real argument z > 0.
 //
 // z < 17.5: Miller's backward recurrence J_{n-1} = (2n/z) J_n - J_{n+1} from a
-//   start index n0 = floor(z) + 26 with the normalisation J_0 + 2 sum J_{2k} = 1,
+//   fixed start index n0 = 44 (at least z + 26 for every z < 17.5) with the
+//   normalisation J_0 + 2 sum J_{2k} = 1,
 //   then Neumann's series
 //     Y_0 = (2/pi) [ (ln(z/2) + gamma) J_0 - 2 sum_{k>=1} (-1)^k J_{2k} / k ],
 //   and Y_1 = -Y_0' from differentiating it term by term with
@@ -75,31 +76,31 @@ __device__ __forceinline__ cplx csqrt_principal(cplx z) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void hankel01(double z, cplx* h0, cplx* h1) {
   if (z < 17.5) {
-    int n0 = (int)z + 26;
-    if (n0 & 1) n0++;
+    // The loop is unrolled, so the coefficients 1/k and 4n/(n^2-1) are literals and all
+    // lanes of a warp step through the same n.
+    constexpr int n0 = 44;
     double jp1 = 0.0, jn = 1e-30;  // J_{n+1}, J_n at n = n0
     const double tz = 2.0 / z;
-    // accumulators (J_n for current n is added when n is visited)
     double norm = 0.0, sy0 = 0.0, sy1 = 0.0, j1 = 0.0;
+#pragma unroll
     for (int n = n0; n >= 1; --n) {
-      // visit J_n
       if ((n & 1) == 0) {
-        int k = n >> 1;
+        const int k = n >> 1;
         norm += 2.0 * jn;
-        sy0 += ((k & 1) ? -jn : jn) / (double)k;
+        sy0 += ((k & 1) ? -jn : jn) * (1.0 / (double)k);
       } else if (n >= 3) {
-        int e = (n + 1) >> 1;
-        double cm = 4.0 * (double)n / ((double)n * n - 1.0);
+        const int e = (n + 1) >> 1;
+        const double cm = 4.0 * (double)n / ((double)n * n - 1.0);
         sy1 += (e & 1) ? -cm * jn : cm * jn;
       } else {
         j1 = jn;
       }
-      double jm1 = (double)n * tz * jn - jp1;
+      const double jm1 = (double)n * tz * jn - jp1;
       jp1 = jn;
       jn = jm1;
       if (fabs(jn) > 1e200) {
-        const double s = 1e-200;
-        jn *= s; jp1 *= s; norm *= s; sy0 *= s; sy1 *= s; j1 *= s;
+        const double sc = 1e-200;
+        jn *= sc; jp1 *= sc; norm *= sc; sy0 *= sc; sy1 *= sc; j1 *= sc;
       }
     }
     double j0 = jn;
@@ -112,16 +113,17 @@ __device__ __forceinline__ void hankel01(double z, cplx* h0, cplx* h1) {
     *h0 = cmk(j0, y0);
     *h1 = cmk(j1, y1);
   } else {
+    // unrolled: the ratios (4 nu^2 - (2k-1)^2) / (8k) are literals
     const double iz = 1.0 / z;
-    // sum_k i^k a_k / z^k for nu = 0 and nu = 1
     double a0 = 1.0, a1 = 1.0, p = 1.0;
     double s0r = 1.0, s0i = 0.0, s1r = 1.0, s1i = 0.0;
+#pragma unroll
     for (int k = 1; k < 48; ++k) {
-      double q = (double)(2 * k - 1);
+      const double q = (double)(2 * k - 1);
       a0 *= (0.0 - q * q) / (8.0 * k);
       a1 *= (4.0 - q * q) / (8.0 * k);
       p *= iz;
-      double t0 = a0 * p, t1 = a1 * p;
+      const double t0 = a0 * p, t1 = a1 * p;
       switch (k & 3) {
         case 0: s0r += t0; s1r += t1; break;
         case 1: s0i += t0; s1i += t1; break;
@@ -139,6 +141,12 @@ __device__ __forceinline__ void hankel01(double z, cplx* h0, cplx* h1) {
     *h0 = cmul(e0, cmk(s0r, s0i));
     *h1 = cmul(e1, cmk(s1r, s1i));
   }
+}
+
+// i c H1 + (w/4) H0: the combined-field kernel once the geometric factor
+// c = (w/4) ((x - y).n_y) / r is known.
+__device__ __forceinline__ cplx combined_from(double c, cplx h0, cplx h1, double omega) {
+  return cmk(-c * h1.y + 0.25 * omega * h0.x, c * h1.x + 0.25 * omega * h0.y);
 }
 
 // Combined-field kernel dG/dn_y - i w G at target (tx, ty), source (sx, sy) with unit

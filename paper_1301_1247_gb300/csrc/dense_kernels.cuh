@@ -284,162 +284,4 @@ __global__ void __launch_bounds__(NT) k_gj_inverse(const InvJob* jobs, cplx* poo
   if (tid == 0) flag_out[jb.job] = bad;
 }
 
-// ---------------------------------------------------------------------------
-// Multi-CTA Gauss-Jordan inverse for one large matrix: the host runs one column per
-// step; k_bgj_pivot (one block) pivots and scales the pivot row, k_bgj_elim updates
-// every other entry, k_bgj_colc finishes the pivot column.  The row interchanges are
-// undone afterwards as one column permutation (k_permute_cols).
-// ---------------------------------------------------------------------------
-struct BigGjState {
-  cplx ip;     // 1 / pivot of the current step
-  int singular;
-};
-
-template <int NT>
-__global__ void __launch_bounds__(NT) k_bgj_pivot(cplx* A, int n, int c, int* piv, BigGjState* st) {
-  __shared__ double redv[32];
-  __shared__ int redi[32];
-  __shared__ cplx sh_ip;
-  double best = -1.0;
-  int bi = 0x7fffffff;
-  for (int i = c + threadIdx.x; i < n; i += NT) {
-    double v = cabs2(A[(int64_t)c * n + i]);
-    if (v > best || (v == best && i < bi)) { best = v; bi = i; }
-  }
-  double pv;
-  int p;
-  block_argmax<NT>(best, bi, redv, redi, &pv, &p);
-  if (!(pv > 0.0)) p = c;
-  if (threadIdx.x == 0) {
-    piv[c] = p;
-    if (!(pv > 0.0)) st->singular = 1;
-  }
-  if (p != c) {
-    for (int j = threadIdx.x; j < n; j += NT) {
-      cplx t = A[(int64_t)j * n + c];
-      A[(int64_t)j * n + c] = A[(int64_t)j * n + p];
-      A[(int64_t)j * n + p] = t;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    cplx dv = A[(int64_t)c * n + c];
-    sh_ip = cabs2(dv) > 0.0 ? cdiv(cmk(1.0, 0.0), dv) : cmk(0.0, 0.0);
-    st->ip = sh_ip;
-  }
-  __syncthreads();
-  const cplx ip = sh_ip;
-  for (int j = threadIdx.x; j < n; j += NT) {
-    if (j == c) A[(int64_t)c * n + c] = ip;
-    else A[(int64_t)j * n + c] = cmul(A[(int64_t)j * n + c], ip);
-  }
-}
-
-// A[i, j] -= A[i, c] A[c, j] for i != c, j != c.
-static __global__ void k_bgj_elim(cplx* A, int n, int c) {
-  const int64_t tot = (int64_t)n * n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % n), j = (int)(e / n);
-    if (i == c || j == c) continue;
-    A[(int64_t)j * n + i] = csub(A[(int64_t)j * n + i], cmul(A[(int64_t)c * n + i], A[(int64_t)j * n + c]));
-  }
-}
-
-// A[i, c] = -A[i, c] / pivot for i != c.
-static __global__ void k_bgj_colc(cplx* A, int n, int c, const BigGjState* st) {
-  const cplx ip = st->ip;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (i == c) continue;
-    cplx v = A[(int64_t)c * n + i];
-    A[(int64_t)c * n + i] = cmul(cmk(-v.x, -v.y), ip);
-  }
-}
-
-// out[:, j] = A[:, src[j]]
-static __global__ void k_permute_cols(const cplx* A, int n, const int* src, cplx* out) {
-  const int64_t tot = (int64_t)n * n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % n), j = (int)(e / n);
-    out[e] = A[(int64_t)src[j] * n + i];
-  }
-}
-
-// Batched multi-CTA Gauss-Jordan (blockIdx.y = matrix): same steps as k_bgj_*.
-struct BigGjJob {
-  cplx* A;
-  int n;
-  int* piv;
-  BigGjState* st;
-};
-
-template <int NT>
-__global__ void __launch_bounds__(NT) k_bgjb_pivot(const BigGjJob* jobs, int c) {
-  __shared__ double redv[32];
-  __shared__ int redi[32];
-  __shared__ cplx sh_ip;
-  const BigGjJob jb = jobs[blockIdx.y];
-  const int n = jb.n;
-  if (c >= n) return;
-  cplx* A = jb.A;
-  double best = -1.0;
-  int bi = 0x7fffffff;
-  for (int i = c + threadIdx.x; i < n; i += NT) {
-    double v = cabs2(A[(int64_t)c * n + i]);
-    if (v > best || (v == best && i < bi)) { best = v; bi = i; }
-  }
-  double pv;
-  int p;
-  block_argmax<NT>(best, bi, redv, redi, &pv, &p);
-  if (!(pv > 0.0)) p = c;
-  if (threadIdx.x == 0) {
-    jb.piv[c] = p;
-    if (!(pv > 0.0)) jb.st->singular = 1;
-  }
-  if (p != c) {
-    for (int j = threadIdx.x; j < n; j += NT) {
-      cplx t = A[(int64_t)j * n + c];
-      A[(int64_t)j * n + c] = A[(int64_t)j * n + p];
-      A[(int64_t)j * n + p] = t;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    cplx dv = A[(int64_t)c * n + c];
-    sh_ip = cabs2(dv) > 0.0 ? cdiv(cmk(1.0, 0.0), dv) : cmk(0.0, 0.0);
-    jb.st->ip = sh_ip;
-  }
-  __syncthreads();
-  const cplx ip = sh_ip;
-  for (int j = threadIdx.x; j < n; j += NT) {
-    if (j == c) A[(int64_t)c * n + c] = ip;
-    else A[(int64_t)j * n + c] = cmul(A[(int64_t)j * n + c], ip);
-  }
-}
-
-static __global__ void k_bgjb_elim(const BigGjJob* jobs, int c) {
-  const BigGjJob jb = jobs[blockIdx.y];
-  const int n = jb.n;
-  if (c >= n) return;
-  cplx* A = jb.A;
-  const int64_t tot = (int64_t)n * n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % n), j = (int)(e / n);
-    if (i == c || j == c) continue;
-    A[(int64_t)j * n + i] = csub(A[(int64_t)j * n + i], cmul(A[(int64_t)c * n + i], A[(int64_t)j * n + c]));
-  }
-}
-
-static __global__ void k_bgjb_colc(const BigGjJob* jobs, int c) {
-  const BigGjJob jb = jobs[blockIdx.y];
-  const int n = jb.n;
-  if (c >= n) return;
-  cplx* A = jb.A;
-  const cplx ip = jb.st->ip;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (i == c) continue;
-    cplx v = A[(int64_t)c * n + i];
-    A[(int64_t)c * n + i] = cmul(cmk(-v.x, -v.y), ip);
-  }
-}
-
 }  // namespace hbs

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <complex>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -95,13 +96,17 @@ struct Handle {
   int Kdir = 0;
   double dir_cx = 0.0, dir_cy = 0.0;
   double pid_residual = 0.0;
+  double nb_residual = 0.0;     // neighbour ID error on nodes between the candidates
 
   double build_seconds = 0.0;
   size_t device_bytes() const;
   double factor_bytes = 0.0;
   double apply_flops = 0.0;
 
-  // scratch for applies
+  // Guards the dense rows that the plain path forms on first use, so that concurrent
+  // solves on one handle stay safe.
+  std::mutex lazy_mu;
+
   void apply_inverse(const cplx* b, cplx* x, int64_t nrhs, cudaStream_t s) const;
   void apply_inverse_transpose(const cplx* b, cplx* x, int64_t nrhs, cudaStream_t s) const;
 };

@@ -144,35 +144,54 @@ struct YJob {
 // Fourier mode of the disk is missed since H_m' - i H_m never vanishes on the real axis),
 // then the node's field at the proxy points (in -> out; the exterior Dirichlet data
 // determine a radiating field).
+// Entries come in pairs that share one Hankel evaluation: A(near_r, j) and A(j, near_r)
+// (rows r and nn + r), and the combined-layer proxy row and the field-at-proxy column of
+// proxy p (rows 2nn + p and 2nn + np + p) -- each pair has a single distance |x - y|.
 __global__ void k_fill_y(DevGeom g, const YJob* jobs, const int64_t* idx, const int64_t* near, cplx* pool) {
   const YJob jb = jobs[blockIdx.y];
   const int m = 2 * jb.nn + 2 * jb.np;
-  const int64_t tot = (int64_t)m * jb.n;
+  const int half = jb.nn + jb.np;
+  const int64_t tot = (int64_t)half * jb.n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e % m), c = (int)(e / m);
+    const int r = (int)(e % half), c = (int)(e / half);
     const int64_t gj = idx[jb.idx_off + c];
-    cplx v;
+    cplx* col = pool + jb.mt_off + (int64_t)c * m;
+    const double xj = g.x[gj], yj = g.y[gj];
     if (r < jb.nn) {
-      v = a_entry(g, near[jb.near_off + r], gj);
-    } else if (r < 2 * jb.nn) {
-      v = a_entry(g, gj, near[jb.near_off + r - jb.nn]);
+      const int64_t gi = near[jb.near_off + r];
+      cplx v1, v2;
+      if (gi == gj) {
+        v1 = v2 = cmk(0.5, 0.0);
+      } else {
+        const double dx = g.x[gi] - xj, dy = g.y[gi] - yj;
+        const double rr = sqrt(dx * dx + dy * dy);
+        cplx h0, h1;
+        hankel01(g.omega * rr, &h0, &h1);
+        const double q = 0.25 * g.omega / rr;
+        const double kw = kr6_weight(gi, gj, g.n);
+        // A(gi, gj): target gi, source gj;  A(gj, gi): target gj, source gi
+        v1 = cscale(combined_from(q * (dx * g.nx[gj] + dy * g.ny[gj]), h0, h1, g.omega), kw * g.w[gj]);
+        v2 = cscale(combined_from(-q * (dx * g.nx[gi] + dy * g.ny[gi]), h0, h1, g.omega), kw * g.w[gi]);
+      }
+      col[r] = v1;
+      col[jb.nn + r] = v2;
     } else {
-      int q = r - 2 * jb.nn;
-      int kind = q / jb.np;
-      int p = q - kind * jb.np;
-      double th = 2.0 * HBS_PI * (double)p / (double)jb.np;
+      const int p = r - jb.nn;
+      const double th = 2.0 * HBS_PI * (double)p / (double)jb.np;
       double sn, cs;
       sincos(th, &sn, &cs);
-      double px = jb.cx + jb.R * cs, py = jb.cy + jb.R * sn;
-      if (kind == 0) {
-        cplx gg, dg;
-        proxy_kernels(g.x[gj], g.y[gj], px, py, cs, sn, g.omega, &gg, &dg);
-        v = cscale(cadd(dg, cmul(cmk(0.0, -g.omega), gg)), jb.wp);
-      } else {
-        v = cscale(combined_kernel(px, py, g.x[gj], g.y[gj], g.nx[gj], g.ny[gj], g.omega), g.w[gj]);
-      }
+      const double px = jb.cx + jb.R * cs, py = jb.cy + jb.R * sn;
+      const double dx = xj - px, dy = yj - py;
+      const double rr = sqrt(dx * dx + dy * dy);
+      cplx h0, h1;
+      hankel01(g.omega * rr, &h0, &h1);
+      const double q = 0.25 * g.omega / rr;
+      // combined-layer source at the proxy (normal = radial direction), target node j
+      col[2 * jb.nn + p] = cscale(combined_from(q * (dx * cs + dy * sn), h0, h1, g.omega), jb.wp);
+      // field at the proxy of the node's source j
+      col[2 * jb.nn + jb.np + p] =
+          cscale(combined_from(-q * (dx * g.nx[gj] + dy * g.ny[gj]), h0, h1, g.omega), g.w[gj]);
     }
-    pool[jb.mt_off + e] = v;
   }
 }
 
@@ -381,15 +400,20 @@ static bool big_inverse(int n) { return n > 128; }
 
 // Batched CPQR-ID of the matrices described by `jobs` (in `pool`).  Returns ranks.
 // Small matrices go to one launch with one CTA each; large ones (the top tree levels,
-// where a level has few nodes) run one after another on all SMs (big_row_id).
+// where a level has few nodes) share one persistent launch on all SMs (pqr.cu).
 std::vector<int> batched_id(std::vector<CpqrJob>& jobs, cplx* pool, cplx* tpool, int* permpool, double tol,
                             cudaStream_t s) {
   std::vector<int> ranks(jobs.size(), 0);
   if (jobs.empty()) return ranks;
   std::vector<CpqrJob> small;
   std::vector<size_t> small_idx, big_idx;
+  // The persistent multi-CTA QR pays off while a level has fewer large nodes than SMs;
+  // with more, one CTA per node keeps every SM busy.
+  size_t nbig = 0;
+  for (const auto& j : jobs) nbig += big_cpqr(j) ? 1 : 0;
+  const bool use_big = nbig > 0 && nbig <= 128;
   for (size_t i = 0; i < jobs.size(); ++i) {
-    if (big_cpqr(jobs[i])) {
+    if (use_big && big_cpqr(jobs[i])) {
       big_idx.push_back(i);
     } else {
       small_idx.push_back(i);
@@ -431,77 +455,20 @@ std::vector<int> batched_id(std::vector<CpqrJob>& jobs, cplx* pool, cplx* tpool,
   return ranks;
 }
 
-// Multi-CTA Gauss-Jordan inverses of several large matrices in place (host-stepped over
-// columns; every matrix of the batch advances in the same launches).
-static void big_inverse_batched(std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, const char* what) {
-  const int nj = (int)mats.size();
-  if (nj == 0) return;
-  int nmax = 0;
-  int64_t ptot = 0;
-  for (auto& m : mats) { nmax = std::max(nmax, m.second); ptot += m.second; }
-  DevBuf<int> piv(ptot);
-  DevBuf<BigGjState> st(nj);
-  HBS_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(BigGjState) * nj, s));
-  std::vector<BigGjJob> jobs(nj);
-  int64_t o = 0;
-  double fl = 0.0;
-  for (int j = 0; j < nj; ++j) {
-    jobs[j] = {mats[j].first, mats[j].second, piv.get() + o, st.get() + j};
-    o += mats[j].second;
-    fl += 8.0 * (double)mats[j].second * mats[j].second;
-  }
-  DevBuf<BigGjJob> dj;
-  dj.upload(jobs, s);
-  const int eg = std::max(8, grid_1d((int64_t)nmax * nmax, 256, 2048) / nj);
-  for (int c = 0; c < nmax; ++c) {
-    {
-      prof::KScope _ks("k_bgjb_pivot", s);
-      k_bgjb_pivot<256><<<dim3(1, nj), 256, 0, s>>>(dj.get(), c);
-    }
-    {
-      prof::KScope _ks("k_bgjb_elim", s, fl, 0.0);
-      k_bgjb_elim<<<dim3(eg, nj), 256, 0, s>>>(dj.get(), c);
-    }
-    {
-      prof::KScope _ks("k_bgjb_colc", s);
-      k_bgjb_colc<<<dim3((nmax + 255) / 256, nj), 256, 0, s>>>(dj.get(), c);
-    }
-  }
-  HBS_LAUNCH_CHECK("batched big inverse");
-  std::vector<int> hp = piv.download(s);
-  std::vector<BigGjState> hs(nj);
-  HBS_CUDA(cudaMemcpyAsync(hs.data(), st.get(), sizeof(BigGjState) * nj, cudaMemcpyDeviceToHost, s));
-  HBS_CUDA(cudaStreamSynchronize(s));
-  o = 0;
-  for (int j = 0; j < nj; ++j) {
-    const int n = mats[j].second;
-    if (hs[j].singular) throw Error(HBS_WARN_ILLCOND, std::string("singular block in ") + what);
-    // undo the row interchanges: column swaps (c, piv[c]) in reverse order
-    std::vector<int> src(n);
-    for (int q = 0; q < n; ++q) src[q] = q;
-    for (int c = n - 1; c >= 0; --c) std::swap(src[c], src[hp[o + c]]);
-    o += n;
-    DevBuf<int> dsrc;
-    dsrc.upload(src, s);
-    DevBuf<cplx> tmp((size_t)n * n);
-    {
-      prof::KScope _ks("k_permute_cols", s);
-      k_permute_cols<<<grid_1d((int64_t)n * n), 256, 0, s>>>(mats[j].first, n, dsrc.get(), tmp.get());
-    }
-    HBS_CUDA(cudaMemcpyAsync(mats[j].first, tmp.get(), sizeof(cplx) * n * n, cudaMemcpyDeviceToDevice, s));
-    HBS_CUDA(cudaStreamSynchronize(s));
-  }
-}
-
 // Batched in-place inverses; throws on a singular block.
 void batched_inverse(std::vector<InvJob>& jobs_in, cplx* pool, cudaStream_t s, const char* what) {
   std::vector<InvJob> jobs;
   std::vector<std::pair<cplx*, int>> big;
+  // The persistent multi-CTA Gauss-Jordan (pgj.cu) pays off while a level has fewer
+  // large blocks than SMs; with more, one CTA per block keeps every SM busy.
+  size_t nbig = 0;
+  for (const auto& j : jobs_in) nbig += big_inverse(j.n) ? 1 : 0;
+  const bool use_big = nbig > 0 && nbig <= 128;
   for (auto& j : jobs_in) {
-    if (big_inverse(j.n)) big.push_back({pool + j.a_off, j.n});
+    if (use_big && big_inverse(j.n)) big.push_back({pool + j.a_off, j.n});
     else jobs.push_back(j);
   }
-  big_inverse_batched(big, s, what);
+  pgj_run(big, s, what);
   if (jobs.empty()) return;
   for (size_t i = 0; i < jobs.size(); ++i) jobs[i].job = (int)i;
   int64_t piv = 0;

@@ -1,0 +1,246 @@
+// Persistent Gauss-Jordan inversion with partial pivoting for the large per-node blocks
+// of the HBS inversion (the D_tau of Eqs. def_muhD..def_muG at the top tree levels).
+// One cooperative launch runs every column step of every matrix in a batch, with one
+// grid barrier per step.
+//
+// Step c of a matrix: every CTA of the matrix copies column c into shared memory, finds
+// the pivot row p (largest modulus among rows >= c, lowest index on ties; the same in
+// every CTA) and 1/pivot.  Each warp owns a fixed set of columns j != c and applies the
+// row interchange (c, p), the scaling of row c and the elimination to them.  Column c
+// itself must stay untouched until every CTA has read it, so its owner writes its final
+// values (1/pivot in row c, -A(i,c)/pivot elsewhere) at the start of step c+1, from the
+// copy kept in shared memory, before applying step c+1 to it.  The row interchanges
+// are undone at the end as one column permutation (k_pgj_unpivot).
+#include <algorithm>
+
+#include "dense_kernels.cuh"
+#include "gridsync.cuh"
+#include "profile.hpp"
+#include "qp_kernels.cuh"
+
+namespace hbs {
+
+namespace {
+
+constexpr int kNT = 256;
+constexpr int kNW = kNT / 32;
+
+struct PgjJob {
+  cplx* A;   // n x n, ld n, inverted in place
+  int n;
+  int b0, nb;
+  int* piv;  // n
+  int* singular;
+  cplx* tmp;  // n x n scratch for the final column permutation
+};
+
+// Column c after step c (rows swapped): 1/d at row c, -u_i/d elsewhere.
+__device__ __forceinline__ cplx final_pivot_col(const cplx* u, int i, int c, cplx ip) {
+  if (i == c) return ip;
+  const cplx v = u[i];
+  return cmul(cmk(-v.x, -v.y), ip);
+}
+
+// smem: 2 x nmax pivot columns (ping-pong over the step parity), rows already swapped.
+__global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nmax, GridSync* gs) {
+  extern __shared__ cplx su[];
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  __shared__ cplx s_ip[2];
+  int jid = 0;
+  while (jid + 1 < nj && jobs[jid + 1].b0 <= (int)blockIdx.x) ++jid;
+  const PgjJob jb = jobs[jid];
+  const int n = jb.n;
+  const int lb = (int)blockIdx.x - jb.b0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gw = lb * kNW + warp, nw = jb.nb * kNW;
+  cplx* A = jb.A;
+  int steps = 0;
+  for (int q = 0; q < nj; ++q) steps = max(steps, jobs[q].n);
+  for (int c = 0; c < steps; ++c) {
+    if (c < n) {
+      const int par = c & 1;
+      cplx* u = su + (size_t)par * nmax;
+      const cplx* up = su + (size_t)(1 - par) * nmax;
+      const cplx* colc = A + (int64_t)c * n;
+      double best = -1.0;
+      int bi = 0x7fffffff;
+      for (int i = tid; i < n; i += kNT) {
+        const cplx v = colc[i];
+        u[i] = v;
+        if (i >= c) {
+          const double a = cabs2(v);
+          if (a > best || (a == best && i < bi)) { best = a; bi = i; }
+        }
+      }
+      double pmax;
+      int p;
+      block_argmax<kNT>(best, bi, redv, redi, &pmax, &p);  // also publishes u to the CTA
+      if (!(pmax > 0.0)) p = c;
+      if (tid == 0) {
+        if (p != c) {
+          const cplx t = u[c];
+          u[c] = u[p];
+          u[p] = t;
+        }
+        const cplx d = u[c];
+        s_ip[par] = cabs2(d) > 0.0 ? cdiv(cmk(1.0, 0.0), d) : cmk(0.0, 0.0);
+        if (lb == 0) {
+          jb.piv[c] = p;
+          if (!(pmax > 0.0)) *jb.singular = 1;
+        }
+      }
+      __syncthreads();
+      const cplx ip = s_ip[par];
+      for (int j = gw; j < n; j += nw) {
+        cplx* aj = A + (int64_t)j * n;
+        if (j == c) continue;  // finalized at the next step (or after the last one)
+        if (j == c - 1) {
+          // deferred: the final values of column c-1 from step c-1
+          const cplx ipp = s_ip[1 - par];
+          for (int i = lane; i < n; i += 32) aj[i] = final_pivot_col(up, i, c - 1, ipp);
+          __syncwarp();
+        }
+        const cplx ac = aj[p], ap = aj[c];  // rows c and p after the interchange
+        const cplx r = cmul(ac, ip);
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+          if (i == c) continue;
+          const cplx x = (i == p) ? ap : aj[i];
+          aj[i] = csub(x, cmul(u[i], r));
+        }
+        if (lane == 0) aj[c] = r;
+      }
+    }
+    if (grid_sync_sum(gs, 0) < 0) return;
+  }
+  // the last pivot column of this matrix
+  if (n > 0) {
+    const int c = n - 1;
+    const int own = c % nw;
+    if (own == gw) {
+      const cplx* u = su + (size_t)(c & 1) * nmax;
+      const cplx ip = s_ip[c & 1];
+      cplx* ac = A + (int64_t)c * n;
+      for (int i = lane; i < n; i += 32) ac[i] = final_pivot_col(u, i, c, ip);
+    }
+  }
+}
+
+// tmp(:, j) = A(:, src[j]) where src undoes the row interchanges (column swaps
+// (c, piv[c]) in reverse order); then A = tmp (k_pgj_copy).
+__global__ void __launch_bounds__(kNT) k_pgj_unpivot(const PgjJob* jobs, int nmax) {
+  extern __shared__ int src[];
+  const PgjJob jb = jobs[blockIdx.y];
+  const int n = jb.n;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < n; ++q) src[q] = q;
+    for (int c = n - 1; c >= 0; --c) {
+      const int p = jb.piv[c];
+      const int t = src[c];
+      src[c] = src[p];
+      src[p] = t;
+    }
+  }
+  __syncthreads();
+  const int64_t tot = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)kNT + threadIdx.x; e < tot; e += (int64_t)gridDim.x * kNT) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    jb.tmp[e] = jb.A[(int64_t)src[j] * n + i];
+  }
+}
+
+__global__ void k_pgj_copy(const PgjJob* jobs) {
+  const PgjJob jb = jobs[blockIdx.y];
+  const int64_t tot = (int64_t)jb.n * jb.n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x)
+    jb.A[e] = jb.tmp[e];
+}
+
+}  // namespace
+
+static int pgj_grid(size_t smem) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    HBS_CUDA(cudaGetDevice(&dev));
+    HBS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  if (smem > 48 * 1024)
+    HBS_CUDA(cudaFuncSetAttribute(k_pgj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pgj, kNT, smem));
+  if (per_sm < 1) throw Error(HBS_ERR_CUDA, "persistent Gauss-Jordan kernel does not fit on an SM");
+  return sms * std::min(per_sm, 2);
+}
+
+// In-place inverses of the matrices (pointer, n) in one persistent launch; throws
+// HBS_WARN_ILLCOND on a singular block.
+void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, const char* what) {
+  const int nj = (int)mats.size();
+  if (nj == 0) return;
+  int nmax = 0;
+  double work = 0.0, fl = 0.0;
+  int64_t ptot = 0, atot = 0;
+  for (const auto& m : mats) {
+    nmax = std::max(nmax, m.second);
+    work += (double)m.second * m.second;
+    fl += 8.0 * (double)m.second * m.second * m.second;
+    ptot += m.second;
+    atot += (int64_t)m.second * m.second;
+  }
+  const size_t smem = 2 * (size_t)nmax * sizeof(cplx);
+  const int G = pgj_grid(smem);
+  if (nj > G) throw Error(HBS_ERR_INTERNAL, "persistent Gauss-Jordan batch larger than the grid");
+  std::vector<int> nb(nj, 1);
+  const int left = G - nj;
+  for (int j = 0; j < nj; ++j)
+    nb[j] += (int)std::floor((double)left * mats[j].second * mats[j].second / work);
+  int used = 0;
+  for (int v : nb) used += v;
+  for (int j = 0; used < G; j = (j + 1) % nj, ++used) ++nb[j];
+  DevBuf<int> piv(ptot), sing(nj);
+  DevBuf<cplx> tmp(atot);
+  DevBuf<GridSync> gs(1);
+  HBS_CUDA(cudaMemsetAsync(sing.get(), 0, sizeof(int) * nj, s));
+  HBS_CUDA(cudaMemsetAsync(gs.get(), 0, sizeof(GridSync), s));
+  std::vector<PgjJob> jobs(nj);
+  int64_t po = 0, ao = 0;
+  int b0 = 0;
+  for (int j = 0; j < nj; ++j) {
+    jobs[j] = {mats[j].first, mats[j].second, b0, nb[j], piv.get() + po, sing.get() + j, tmp.get() + ao};
+    po += mats[j].second;
+    ao += (int64_t)mats[j].second * mats[j].second;
+    b0 += nb[j];
+  }
+  DevBuf<PgjJob> dj;
+  dj.upload(jobs, s);
+  {
+    const PgjJob* a0 = dj.get();
+    int a1 = nj, a2 = nmax;
+    GridSync* a3 = gs.get();
+    void* args[] = {&a0, &a1, &a2, &a3};
+    prof::KScope _ks("k_pgj", s, fl, 0.0);
+    HBS_CUDA(cudaLaunchCooperativeKernel((const void*)k_pgj, dim3(G), dim3(kNT), args, smem, s));
+  }
+  HBS_LAUNCH_CHECK("k_pgj");
+  {
+    prof::KScope _ks("k_pgj_unpivot", s);
+    const size_t sm = (size_t)nmax * sizeof(int);
+    if (sm > 48 * 1024)
+      HBS_CUDA(cudaFuncSetAttribute(k_pgj_unpivot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_pgj_unpivot<<<dim3(std::max(1, 1216 / nj), nj), kNT, sm, s>>>(dj.get(), nmax);
+    k_pgj_copy<<<dim3(std::max(1, 1216 / nj), nj), 256, 0, s>>>(dj.get());
+  }
+  HBS_LAUNCH_CHECK("k_pgj_unpivot");
+  std::vector<int> hs(nj);
+  GridSync hg{};
+  HBS_CUDA(cudaMemcpyAsync(hs.data(), sing.get(), sizeof(int) * nj, cudaMemcpyDeviceToHost, s));
+  HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+  HBS_CUDA(cudaStreamSynchronize(s));
+  if (hg.timed_out) throw Error(HBS_ERR_TIMEOUT, "persistent Gauss-Jordan: a grid barrier wait gave up");
+  for (int j = 0; j < nj; ++j)
+    if (hs[j]) throw Error(HBS_WARN_ILLCOND, std::string("singular block in ") + what);
+}
+
+}  // namespace hbs

@@ -1,0 +1,544 @@
+// Persistent column-pivoted Householder QR for interpolative decompositions (Def. 3.1)
+// of large matrices: one cooperative launch runs every pivot step of every matrix in a
+// batch, with one grid barrier per step, instead of three launches per step.
+//
+// Step s of a matrix (m x n, column-major, columns = the members to choose from):
+//   * every CTA of the matrix reduces the per-CTA partial maxima of the column norms
+//     left by step s-1 and finds the pivot column p (largest remaining norm, lowest index
+//     on ties) - the same reduction in every CTA, so all agree bit for bit;
+//   * every CTA forms the reflector of column p (rows s..m-1) in shared memory;
+//   * each active column j != p is owned by one warp (m <= 320) or one CTA and is
+//     updated in registers, its norm downdated (recomputed on cancellation), and the
+//     CTA's partial maximum for step s+1 recorded.
+// Columns are never swapped: pivot p of step s stays where it is, its rows < s hold
+// R(:, s) and its rows > s the reflector tail; the diagonal beta_s, the reflector head
+// v0_s and tau_s go to per-step arrays.  The row ID's permutation is the one the
+// column-swapping algorithm would produce, and T = R11^{-1} R12 follows from one
+// triangular solve per column.
+#include <algorithm>
+#include <cstdio>
+
+#include "dense_kernels.cuh"
+#include "gridsync.cuh"
+#include "profile.hpp"
+#include "qp_kernels.cuh"
+
+namespace hbs {
+
+namespace {
+
+constexpr int kNT = 256;
+constexpr int kNW = kNT / 32;
+constexpr int kWarpRows = 320;  // warp-per-column mode up to this many rows
+constexpr int kReg = 10;        // rows per lane held in registers (warp mode)
+constexpr int kRegB = 8;        // rows per thread held in registers (CTA mode)
+
+struct PqrJob {
+  cplx* A;
+  int64_t m, n;
+  int kcap;
+  int b0, nb;  // CTA range of this matrix
+  double* nrm;
+  double* nref;
+  int* piv;
+  cplx* beta;
+  cplx* v0;
+  double* tau;
+  PqrState* st;
+  int* perm;
+  cplx* T;
+  cplx* r11r;  // k x k row-major copy of R11 (scratch for the triangular solves)
+  int* pos;    // n: position of each column in perm (scratch)
+};
+
+__device__ __forceinline__ bool better(double v, int i, double bv, int bi) {
+  return v > bv || (v == bv && i < bi);
+}
+
+template <int NT>
+__device__ __forceinline__ cplx block_sum_c(cplx v, double* red) {
+  double a = block_sum<NT>(v.x, red);
+  double b = block_sum<NT>(v.y, red);
+  return cmk(a, b);
+}
+
+__device__ __forceinline__ cplx warp_sum_c(cplx w) {
+  for (int o = 16; o > 0; o >>= 1) {
+    w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
+    w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
+  }
+  return w;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// x = R^{-1} b for upper-triangular R (k x k, row-major), one warp; x is written to
+// global memory row by row (x may alias b: b[i] is read before x[i] is written).
+__device__ __forceinline__ void tsolve_row_major(const cplx* R, int k, const cplx* b, cplx* x, int lane) {
+  for (int i = k - 1; i >= 0; --i) {
+    const cplx* ri = R + (int64_t)i * k;
+    cplx acc = cmk(0.0, 0.0);
+    for (int l = i + 1 + lane; l < k; l += 32) acc = cfma(ri[l], x[l], acc);
+    acc = warp_sum_c(acc);
+    if (lane == 0) x[i] = cdiv(csub(b[i], acc), ri[i]);
+    __syncwarp();
+  }
+}
+
+// One Householder update of column j at step s (warp mode: 32 lanes own one column).
+__device__ __forceinline__ double update_col_warp(cplx* aj, const cplx* vt, int64_t m, int64_t s, cplx v0, double tau,
+                                                  double nj, double* nref_j, int lane) {
+  cplx r[kReg];
+  cplx w = cmk(0.0, 0.0);
+#pragma unroll
+  for (int q = 0; q < kReg; ++q) {
+    const int64_t i = s + 1 + lane + 32 * q;
+    if (i < m) {
+      r[q] = aj[i];
+      w = cfma(cconj(vt[i - s - 1]), r[q], w);
+    }
+  }
+  w = warp_sum_c(w);
+  const cplx ajs = aj[s];
+  w = cscale(cfma(cconj(v0), ajs, w), tau);
+  const cplx top = csub(ajs, cmul(v0, w));
+  double q2 = 0.0;
+#pragma unroll
+  for (int q = 0; q < kReg; ++q) {
+    const int64_t i = s + 1 + lane + 32 * q;
+    if (i < m) {
+      r[q] = csub(r[q], cmul(vt[i - s - 1], w));
+      aj[i] = r[q];
+      q2 += cabs2(r[q]);
+    }
+  }
+  double t = nj - cabs2(top);
+  if (t <= 0.0078125 * *nref_j) {
+    t = warp_sum(q2);
+    if (lane == 0) *nref_j = t;
+  }
+  __syncwarp();
+  if (lane == 0) aj[s] = top;
+  return t;
+}
+
+// The same update with one CTA per column (rows beyond NT * kRegB are streamed).
+__device__ __forceinline__ double update_col_block(cplx* aj, const cplx* vt, int64_t m, int64_t s, cplx v0, double tau,
+                                                   double nj, double* nref_j, double* red) {
+  const int tid = threadIdx.x;
+  cplx r[kRegB];
+  cplx w = cmk(0.0, 0.0);
+#pragma unroll
+  for (int q = 0; q < kRegB; ++q) {
+    const int64_t i = s + 1 + tid + (int64_t)kNT * q;
+    if (i < m) {
+      r[q] = aj[i];
+      w = cfma(cconj(vt[i - s - 1]), r[q], w);
+    }
+  }
+  for (int64_t i = s + 1 + tid + (int64_t)kNT * kRegB; i < m; i += kNT) w = cfma(cconj(vt[i - s - 1]), aj[i], w);
+  w = block_sum_c<kNT>(w, red);
+  const cplx ajs = aj[s];
+  w = cscale(cfma(cconj(v0), ajs, w), tau);
+  const cplx top = csub(ajs, cmul(v0, w));
+  double q2 = 0.0;
+#pragma unroll
+  for (int q = 0; q < kRegB; ++q) {
+    const int64_t i = s + 1 + tid + (int64_t)kNT * q;
+    if (i < m) {
+      r[q] = csub(r[q], cmul(vt[i - s - 1], w));
+      aj[i] = r[q];
+      q2 += cabs2(r[q]);
+    }
+  }
+  for (int64_t i = s + 1 + tid + (int64_t)kNT * kRegB; i < m; i += kNT) {
+    const cplx x = csub(aj[i], cmul(vt[i - s - 1], w));
+    aj[i] = x;
+    q2 += cabs2(x);
+  }
+  double t = nj - cabs2(top);
+  if (t <= 0.0078125 * *nref_j) {  // uniform over the CTA
+    t = block_sum<kNT>(q2, red);
+    if (tid == 0) *nref_j = t;
+  }
+  __syncthreads();
+  if (tid == 0) aj[s] = top;
+  return t;
+}
+
+// pv / pi: 2 x gridDim.x partial maxima (parity of the step).
+__global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, double* pv, int* pi, GridSync* gs, double tol,
+                                             int vcap) {
+  extern __shared__ cplx sv[];
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  int jid = 0;
+  while (jid + 1 < nj && jobs[jid + 1].b0 <= (int)blockIdx.x) ++jid;
+  const PqrJob jb = jobs[jid];
+  const int G = gridDim.x;
+  const int lb = (int)blockIdx.x - jb.b0;
+  const int64_t m = jb.m, n = jb.n;
+  const bool wmode = m <= kWarpRows;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t gw = (int64_t)lb * kNW + warp, nw = (int64_t)jb.nb * kNW;
+  cplx* A = jb.A;
+
+  // column norms and the first partial maxima (parity 0)
+  {
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    if (wmode) {
+      for (int64_t j = gw; j < n; j += nw) {
+        double s2 = 0.0;
+        for (int64_t i = lane; i < m; i += 32) s2 += cabs2(A[j * m + i]);
+        s2 = warp_sum(s2);
+        if (lane == 0) { jb.nrm[j] = s2; jb.nref[j] = s2; }
+        if (better(s2, (int)j, best, bi)) { best = s2; bi = (int)j; }
+      }
+    } else {
+      for (int64_t j = lb; j < n; j += jb.nb) {
+        double s2 = 0.0;
+        for (int64_t i = tid; i < m; i += kNT) s2 += cabs2(A[j * m + i]);
+        s2 = block_sum<kNT>(s2, redv);
+        if (tid == 0) { jb.nrm[j] = s2; jb.nref[j] = s2; }
+        if (better(s2, (int)j, best, bi)) { best = s2; bi = (int)j; }
+      }
+    }
+    double v;
+    int ix;
+    block_argmax<kNT>(best, bi, redv, redi, &v, &ix);
+    if (tid == 0) { pv[blockIdx.x] = v; pi[blockIdx.x] = ix; }
+  }
+  if (grid_sync_sum(gs, 0) < 0) return;
+
+  double r00 = 0.0;
+  bool done = false;
+  for (int64_t s = 0;; ++s) {
+    const int par = (int)(s & 1);
+    int p = -1;
+    double pvmax = -1.0;
+    if (!done) {
+      double best = -1.0;
+      int bi = 0x7fffffff;
+      for (int q = tid; q < jb.nb; q += kNT) {
+        const double v = pv[par * G + jb.b0 + q];
+        const int ix = pi[par * G + jb.b0 + q];
+        if (better(v, ix, best, bi)) { best = v; bi = ix; }
+      }
+      block_argmax<kNT>(best, bi, redv, redi, &pvmax, &p);
+      if (s == 0) r00 = sqrt(fmax(pvmax, 0.0));
+      const bool tol_met = !(r00 > 0.0) || !(pvmax >= 0.0) || sqrt(pvmax) <= tol * r00;
+      if (tol_met || s >= jb.kcap || s >= m || s >= n || p < 0 || p >= n) {
+        done = true;
+        if (lb == 0 && tid == 0) {
+          jb.st->rank = (int)s;
+          jb.st->capped = (!tol_met && s >= jb.kcap && s < m && s < n) ? 1 : 0;
+          jb.st->r00 = r00;
+        }
+      }
+    }
+    if (!done) {
+      const cplx* ap = A + (int64_t)p * m;
+      const cplx x0 = ap[s];
+      const bool staged = (m - s - 1) <= vcap;
+      double sig = 0.0;
+      for (int64_t i = s + 1 + tid; i < m; i += kNT) {
+        const cplx x = ap[i];
+        sig += cabs2(x);
+        if (staged) sv[i - s - 1] = x;
+      }
+      sig = block_sum<kNT>(sig, redv);  // also publishes sv to the CTA
+      const double ax0 = cabs1(x0);
+      const double xn = sqrt(ax0 * ax0 + sig);
+      const cplx ph = ax0 > 0.0 ? cmk(x0.x / ax0, x0.y / ax0) : cmk(1.0, 0.0);
+      const cplx beta = cmk(-ph.x * xn, -ph.y * xn);
+      const cplx v0 = csub(x0, beta);
+      const double vv = cabs2(v0) + sig;
+      const double tau = vv > 0.0 ? 2.0 / vv : 0.0;
+      if (lb == 0 && tid == 0) {
+        jb.piv[s] = p;
+        jb.beta[s] = beta;
+        jb.v0[s] = v0;
+        jb.tau[s] = tau;
+      }
+      const cplx* vt = staged ? sv : ap + s + 1;
+      double best = -1.0;
+      int bi = 0x7fffffff;
+      if (wmode) {
+        for (int64_t j = gw; j < n; j += nw) {
+          const double nj = jb.nrm[j];
+          if (nj < 0.0) continue;  // an earlier pivot
+          if (j == p) {
+            if (lane == 0) jb.nrm[j] = -1.0;
+            continue;
+          }
+          const double t = update_col_warp(A + j * m, vt, m, s, v0, tau, nj, jb.nref + j, lane);
+          if (lane == 0) jb.nrm[j] = t;
+          if (better(t, (int)j, best, bi)) { best = t; bi = (int)j; }
+        }
+      } else {
+        for (int64_t j = lb; j < n; j += jb.nb) {
+          const double nj = jb.nrm[j];
+          if (nj < 0.0) continue;
+          if (j == p) {
+            if (tid == 0) jb.nrm[j] = -1.0;
+            continue;
+          }
+          const double t = update_col_block(A + j * m, vt, m, s, v0, tau, nj, jb.nref + j, redv);
+          if (tid == 0) jb.nrm[j] = t;
+          if (better(t, (int)j, best, bi)) { best = t; bi = (int)j; }
+        }
+      }
+      double v;
+      int ix;
+      block_argmax<kNT>(best, bi, redv, redi, &v, &ix);
+      if (tid == 0) { pv[(1 - par) * G + blockIdx.x] = v; pi[(1 - par) * G + blockIdx.x] = ix; }
+    }
+    const long long act = grid_sync_sum(gs, (lb == 0 && !done) ? 1 : 0);
+    if (act <= 0) break;  // all matrices finished (0) or a wait gave up (-1)
+  }
+}
+
+// Per matrix (blockIdx.y): the permutation (CTA 0) and R11 as a row-major k x k array
+// (all CTAs).  The permutation is the one a column-swapping QR produces (pivot s swapped
+// into position s at step s): perm[0..k) = piv, and the other columns in the order those
+// swaps leave them.
+__global__ void __launch_bounds__(kNT) k_pqr_finish(const PqrJob* jobs) {
+  const PqrJob jb = jobs[blockIdx.y];
+  const int k = jb.st->rank;
+  const int64_t m = jb.m, n = jb.n;
+  if (blockIdx.x == 0) {
+    for (int64_t i = threadIdx.x; i < n; i += kNT) {
+      jb.perm[i] = (int)i;
+      jb.pos[i] = (int)i;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < k; ++s) {
+        const int p = jb.piv[s], ps = jb.pos[p];
+        if (ps != s) {
+          const int cs = jb.perm[s];
+          jb.perm[s] = p;
+          jb.perm[ps] = cs;
+          jb.pos[cs] = ps;
+          jb.pos[p] = s;
+        }
+      }
+    }
+  }
+  const int64_t tot = (int64_t)k * k;
+  for (int64_t e = blockIdx.x * (int64_t)kNT + threadIdx.x; e < tot; e += (int64_t)gridDim.x * kNT) {
+    const int i = (int)(e / k), l = (int)(e % k);
+    cplx v = cmk(0.0, 0.0);
+    if (l == i) v = jb.beta[i];
+    else if (l > i) v = jb.A[(int64_t)jb.piv[l] * m + i];
+    jb.r11r[e] = v;
+  }
+}
+
+// Per matrix: T(:, c) = R11^{-1} R12(:, c), R12(:, c) = rows 0..k-1 of physical column
+// perm[k + c].  One warp per column.
+__global__ void __launch_bounds__(kNT) k_pqr_tsolve(const PqrJob* jobs) {
+  const PqrJob jb = jobs[blockIdx.y];
+  const int k = jb.st->rank;
+  const int64_t nc = jb.n - k;
+  if (k <= 0 || nc <= 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)kNT + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kNT) >> 5;
+  for (int64_t c = warp; c < nc; c += nwarps) {
+    const cplx* b = jb.A + (int64_t)jb.perm[k + c] * jb.m;
+    cplx* tc = jb.T + c * (int64_t)k;
+    tsolve_row_major(jb.r11r, k, b, tc, lane);
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_tsolve_cols(const cplx* R, int k, const cplx* B, int64_t ldb, int64_t ncols,
+                                                     cplx* X, int64_t ldx) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp; c < ncols; c += nwarps) tsolve_row_major(R, k, B + c * ldb, X + c * ldx, lane);
+}
+
+// Column j of conj(Q1) (Q1 = first k columns of H_0 ... H_{k-1}):  q = H_0 ... H_j e_j.
+// One CTA per column; q lives in the output column.
+__global__ void __launch_bounds__(kNT) k_form_qc(const cplx* A, int64_t m, const int* piv, const cplx* v0,
+                                                 const double* tau, int k, cplx* Qc) {
+  __shared__ double red[32];
+  const int j = blockIdx.x;
+  if (j >= k) return;
+  cplx* q = Qc + (int64_t)j * m;
+  for (int64_t i = threadIdx.x; i < m; i += kNT) q[i] = cmk(i == j ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  for (int s = j; s >= 0; --s) {
+    const cplx* ap = A + (int64_t)piv[s] * m;
+    const cplx h0 = v0[s];
+    cplx w = cmk(0.0, 0.0);
+    if (threadIdx.x == 0) w = cmul(cconj(h0), q[s]);
+    for (int64_t i = s + 1 + threadIdx.x; i < m; i += kNT) w = cfma(cconj(ap[i]), q[i], w);
+    w = block_sum_c<kNT>(w, red);
+    w = cscale(w, tau[s]);
+    if (threadIdx.x == 0) q[s] = csub(q[s], cmul(h0, w));
+    for (int64_t i = s + 1 + threadIdx.x; i < m; i += kNT) q[i] = csub(q[i], cmul(ap[i], w));
+    __syncthreads();
+  }
+  for (int64_t i = threadIdx.x; i < m; i += kNT) q[i] = cconj(q[i]);
+}
+
+// R11 (k x k, row-major) from the factored matrix.
+__global__ void k_r11_rows(const cplx* A, int64_t m, const int* piv, const cplx* beta, int k, cplx* R) {
+  const int64_t tot = (int64_t)k * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / k), l = (int)(e % k);
+    cplx v = cmk(0.0, 0.0);
+    if (l == i) v = beta[i];
+    else if (l > i) v = A[(int64_t)piv[l] * m + i];
+    R[e] = v;
+  }
+}
+
+// out[r + c ldo] = src[r + idx[c] lds]: columns idx of src.
+__global__ void k_gather_cols(const cplx* src, int64_t lds, int64_t rows, const int64_t* idx, int64_t ncols, cplx* out,
+                              int64_t ldo) {
+  const int64_t tot = rows * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % rows, c = e / rows;
+    out[r + c * ldo] = src[r + idx[c] * lds];
+  }
+}
+
+// X(:, idx[c]) = e_c for c < k (X: k x ncols, ld k).
+__global__ void k_set_unit_cols(cplx* X, int k, const int64_t* idx) {
+  const int64_t tot = (int64_t)k * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % k), c = (int)(e / k);
+    X[r + idx[c] * (int64_t)k] = cmk(r == c ? 1.0 : 0.0, 0.0);
+  }
+}
+
+static int pqr_grid(size_t smem) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    HBS_CUDA(cudaGetDevice(&dev));
+    HBS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  if (smem > 48 * 1024)
+    HBS_CUDA(cudaFuncSetAttribute(k_pqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pqr, kNT, smem));
+  if (per_sm < 1) throw Error(HBS_ERR_CUDA, "persistent QR kernel does not fit on an SM");
+  return sms * std::min(per_sm, 2);
+}
+
+void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrOut& out) {
+  const int nj = (int)specs.size();
+  out.rank.assign(nj, 0);
+  out.koff.assign(nj + 1, 0);
+  if (nj == 0) return;
+  int64_t mmax = 0, ntot = 0;
+  double work = 0.0;
+  for (int j = 0; j < nj; ++j) {
+    const auto& sp = specs[j];
+    mmax = std::max(mmax, sp.m);
+    ntot += sp.n;
+    out.koff[j + 1] = out.koff[j] + std::max(1, sp.kcap);
+    work += (double)sp.m * sp.n;
+  }
+  const int vcap = (int)std::min<int64_t>(mmax, 6144);
+  const size_t smem = (size_t)vcap * sizeof(cplx);
+  const int G = pqr_grid(smem);
+  if (nj > G) throw Error(HBS_ERR_INTERNAL, "persistent QR batch larger than the grid");
+  // CTAs per matrix in proportion to its size, at least one each.
+  std::vector<int> nb(nj, 1);
+  int left = G - nj;
+  for (int j = 0; j < nj; ++j) {
+    const int extra = (int)std::floor((double)left * specs[j].m * specs[j].n / work);
+    nb[j] += extra;
+  }
+  int used = 0;
+  for (int v : nb) used += v;
+  for (int j = 0; used < G; j = (j + 1) % nj, ++used) ++nb[j];
+  const int64_t ktot = out.koff[nj];
+  int64_t r11tot = 0;
+  std::vector<int64_t> r11off(nj);
+  for (int j = 0; j < nj; ++j) {
+    r11off[j] = r11tot;
+    const int64_t kk = std::min<int64_t>(specs[j].kcap, std::min(specs[j].m, specs[j].n));
+    r11tot += kk * kk;
+  }
+  DevBuf<double> nrm(ntot), nref(ntot), pv(2 * (size_t)G);
+  DevBuf<int> pi(2 * (size_t)G), pos(ntot);
+  out.piv.alloc(ktot);
+  out.beta.alloc(ktot);
+  out.v0.alloc(ktot);
+  out.tau.alloc(ktot);
+  DevBuf<PqrState> st(nj);
+  DevBuf<GridSync> gs(1);
+  DevBuf<cplx> r11(std::max<int64_t>(r11tot, 1));
+  HBS_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(PqrState) * nj, s));
+  HBS_CUDA(cudaMemsetAsync(gs.get(), 0, sizeof(GridSync), s));
+  std::vector<PqrJob> jobs(nj);
+  int64_t o = 0;
+  int b0 = 0;
+  for (int j = 0; j < nj; ++j) {
+    const auto& sp = specs[j];
+    jobs[j] = {sp.A, sp.m, sp.n, sp.kcap, b0, nb[j], nrm.get() + o, nref.get() + o,
+               out.piv.get() + out.koff[j], out.beta.get() + out.koff[j], out.v0.get() + out.koff[j],
+               out.tau.get() + out.koff[j], st.get() + j, sp.perm, sp.T, r11.get() + r11off[j], pos.get() + o};
+    o += sp.n;
+    b0 += nb[j];
+  }
+  DevBuf<PqrJob> dj;
+  dj.upload(jobs, s);
+  {
+    const PqrJob* a0 = dj.get();
+    int a1 = nj;
+    double* a2 = pv.get();
+    int* a3 = pi.get();
+    GridSync* a4 = gs.get();
+    double a5 = tol;
+    int a6 = vcap;
+    void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};
+    prof::KScope _ks("k_pqr", s);
+    HBS_CUDA(cudaLaunchCooperativeKernel((const void*)k_pqr, dim3(G), dim3(kNT), args, smem, s));
+  }
+  HBS_LAUNCH_CHECK("k_pqr");
+  int64_t nmax = 0;
+  for (const auto& sp : specs) nmax = std::max(nmax, sp.n);
+  {
+    prof::KScope _ks("k_pqr_finish", s);
+    k_pqr_finish<<<dim3(8, nj), kNT, 0, s>>>(dj.get());
+  }
+  {
+    prof::KScope _ks("k_pqr_tsolve", s);
+    const int bx = (int)std::max<int64_t>(1, std::min<int64_t>(1216 / nj + 1, (nmax + kNW - 1) / kNW));
+    k_pqr_tsolve<<<dim3(bx, nj), kNT, 0, s>>>(dj.get());
+  }
+  HBS_LAUNCH_CHECK("k_pqr_finish");
+  std::vector<PqrState> hs(nj);
+  GridSync hg{};
+  HBS_CUDA(cudaMemcpyAsync(hs.data(), st.get(), sizeof(PqrState) * nj, cudaMemcpyDeviceToHost, s));
+  HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+  HBS_CUDA(cudaStreamSynchronize(s));
+  if (hg.timed_out) throw Error(HBS_ERR_TIMEOUT, "persistent QR: a grid barrier wait gave up");
+  for (int j = 0; j < nj; ++j) {
+    out.rank[j] = hs[j].rank;
+    if (hs[j].capped) throw Error(HBS_ERR_RANK, "interpolative decomposition rank exceeds the supported maximum");
+  }
+  // account the factorization's flops (16 m n per step on the active columns)
+  double fl = 0.0;
+  for (int j = 0; j < nj; ++j) {
+    const double m = (double)specs[j].m, n = (double)specs[j].n, k = out.rank[j];
+    fl += 16.0 * k * (m * n - 0.5 * (m + n) * k + k * k / 3.0);
+  }
+  prof::add_work("k_pqr", fl, 0.0);
+}
+
+}  // namespace hbs

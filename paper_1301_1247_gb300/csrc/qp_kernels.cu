@@ -183,18 +183,6 @@ __global__ void k_fill_r(DevGeom g, const int64_t* J, int l, double d, cplx* Rm,
   }
 }
 
-// P (N x l, ld = N) from the ID: P[perm[i], i] = 1, P[perm[l + j], i] = T[i, j].
-__global__ void k_build_p(const int* perm, const cplx* T, int64_t N, int l, cplx* P) {
-  const int64_t tot = N * (int64_t)l;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / N);
-    const int64_t row = e % N;  // position in pivot order
-    const int64_t g = perm[row];
-    cplx v = row < l ? cmk(row == i ? 1.0 : 0.0, 0.0) : T[(row - l) * (int64_t)l + i];
-    P[(int64_t)i * N + g] = v;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Multi-CTA column-pivoted QR for one large matrix (m x n, n large).  The host runs
 // one step per pivot: k_bq_pivot (one block) picks the pivot, swaps it into place and
@@ -335,54 +323,11 @@ __global__ void k_bq_tsolve(const cplx* A, int64_t m, int64_t n, int k, cplx* T)
 }
 
 int big_row_id(cplx* Mt, int64_t m, int64_t n, double tol, int* perm, cplx* T, int max_rank, cudaStream_t s) {
-  DevBuf<double> nrm(n), nref(n);
-  DevBuf<BigQrState> st(1);
-  HBS_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(BigQrState), s));
-  const int nparts = 296;
-  DevBuf<double> pv(nparts);
-  DevBuf<int> pi(nparts);
-  {
-    prof::KScope _ks("k_bq_norms", s);
-    k_bq_norms<<<1184, 256, 0, s>>>(Mt, m, n, nrm.get(), nref.get(), perm);
-  }
-  HBS_LAUNCH_CHECK("k_bq_norms");
-  const int64_t kcap = std::min<int64_t>(std::min<int64_t>(m, n), max_rank);
-  BigQrState hs{};
-  for (int64_t step = 0; step < kcap; ++step) {
-    {
-      prof::KScope _ks("k_bq_argmax", s);
-      k_bq_argmax<<<nparts, 256, 0, s>>>(nrm.get(), step, n, st.get(), pv.get(), pi.get());
-    }
-    {
-      prof::KScope _ks("k_bq_pivot", s);
-      k_bq_pivot<<<1, 256, 0, s>>>(Mt, m, step, nrm.get(), nref.get(), perm, pv.get(), pi.get(), nparts, st.get(), tol);
-    }
-    {
-      prof::KScope _ks("k_bq_update", s, 16.0 * (double)(m - step) * (double)(n - step),
-                       32.0 * (double)(m - step) * (double)(n - step));
-      k_bq_update<<<1184, 256, 0, s>>>(Mt, m, n, step, nrm.get(), nref.get(), st.get());
-    }
-    if ((step & 15) == 15) {
-      HBS_LAUNCH_CHECK("big qr step");
-      HBS_CUDA(cudaMemcpyAsync(&hs, st.get(), sizeof(BigQrState), cudaMemcpyDeviceToHost, s));
-      HBS_CUDA(cudaStreamSynchronize(s));
-      if (hs.done) break;
-    }
-  }
-  HBS_LAUNCH_CHECK("big qr");
-  HBS_CUDA(cudaMemcpyAsync(&hs, st.get(), sizeof(BigQrState), cudaMemcpyDeviceToHost, s));
-  HBS_CUDA(cudaStreamSynchronize(s));
-  const int k = hs.rank;
-  if (!hs.done && k >= max_rank && k < std::min<int64_t>(m, n))
-    throw Error(HBS_ERR_RANK, "neighbour interaction rank exceeds the supported maximum");
-  if (k > 0 && n > k) {
-    {
-      prof::KScope _ks("k_bq_tsolve", s);
-      k_bq_tsolve<<<1184, 256, 0, s>>>(Mt, m, n, k, T);
-    }
-    HBS_LAUNCH_CHECK("k_bq_tsolve");
-  }
-  return k;
+  const int kcap = (int)std::min<int64_t>(std::min<int64_t>(m, n), max_rank);
+  std::vector<PqrSpec> sp{{Mt, m, n, kcap, perm, T}};
+  PqrOut out;
+  pqr_run(sp, tol, s, out);
+  return out.rank[0];
 }
 
 }  // namespace hbs
@@ -506,217 +451,14 @@ __global__ void k_diff_norm2(const cplx* a, int64_t lda, const cplx* b, int64_t 
 
 namespace hbs {
 
-// ---------------------------------------------------------------------------
-// Batched multi-CTA column-pivoted QR: the same steps as k_bq_* for several matrices at
-// once (blockIdx.y = matrix), so a tree level with a few dozen large nodes advances all
-// of them with one launch per kernel and step.
-// ---------------------------------------------------------------------------
-__global__ void k_bqb_norms(const BigQrJob* jobs) {
-  const BigQrJob jb = jobs[blockIdx.y];
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = warp; j < jb.n; j += nwarps) {
-    double s = 0.0;
-    for (int64_t i = lane; i < jb.m; i += 32) s += cabs2(jb.A[j * jb.m + i]);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) { jb.nrm[j] = s; jb.nref[j] = s; jb.perm[j] = (int)j; }
-  }
-}
-
-__global__ void k_bqb_argmax(const BigQrJob* jobs, int64_t s) {
-  __shared__ double redv[32];
-  __shared__ int redi[32];
-  const BigQrJob jb = jobs[blockIdx.y];
-  double best = -1.0;
-  int bi = 0x7fffffff;
-  if (!jb.st->done) {
-    for (int64_t j = s + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < jb.n; j += (int64_t)gridDim.x * blockDim.x) {
-      double v = jb.nrm[j];
-      if (v > best || (v == best && (int)j < bi)) { best = v; bi = (int)j; }
-    }
-  }
-  double v;
-  int i;
-  block_argmax<256>(best, bi, redv, redi, &v, &i);
-  if (threadIdx.x == 0) { jb.pv[blockIdx.x] = v; jb.pi[blockIdx.x] = i; }
-}
-
-__global__ void k_bqb_pivot(const BigQrJob* jobs, int64_t s, int nparts, double tol) {
-  __shared__ double redv[32];
-  __shared__ int redi[32];
-  const BigQrJob jb = jobs[blockIdx.y];
-  BigQrState* st = jb.st;
-  if (st->done) return;
-  const int64_t m = jb.m;
-  if (s >= jb.n || s >= m) {
-    if (threadIdx.x == 0) { st->done = 1; st->rank = (int)s; }
-    return;
-  }
-  double best = -1.0;
-  int bi = 0x7fffffff;
-  for (int q = threadIdx.x; q < nparts; q += blockDim.x) {
-    if (jb.pv[q] > best || (jb.pv[q] == best && jb.pi[q] < bi)) { best = jb.pv[q]; bi = jb.pi[q]; }
-  }
-  double v;
-  int p;
-  block_argmax<256>(best, bi, redv, redi, &v, &p);
-  if (s == 0 && threadIdx.x == 0) st->r00 = sqrt(v);
-  __syncthreads();
-  const double r00 = st->r00;
-  if (!(r00 > 0.0) || sqrt(v) <= tol * r00) {
-    if (threadIdx.x == 0) { st->done = 1; st->rank = (int)s; }
-    return;
-  }
-  cplx* A = jb.A;
-  if (p != s) {
-    cplx* cs = A + s * m;
-    cplx* cp = A + (int64_t)p * m;
-    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) { cplx t = cs[i]; cs[i] = cp[i]; cp[i] = t; }
-    if (threadIdx.x == 0) {
-      double t = jb.nrm[s]; jb.nrm[s] = jb.nrm[p]; jb.nrm[p] = t;
-      t = jb.nref[s]; jb.nref[s] = jb.nref[p]; jb.nref[p] = t;
-      int ti = jb.perm[s]; jb.perm[s] = jb.perm[p]; jb.perm[p] = ti;
-    }
-  }
-  __syncthreads();
-  cplx* cs = A + s * m;
-  double sig = 0.0;
-  for (int64_t i = s + 1 + threadIdx.x; i < m; i += blockDim.x) sig += cabs2(cs[i]);
-  sig = block_sum<256>(sig, redv);
-  if (threadIdx.x == 0) {
-    cplx x0 = cs[s];
-    double ax0 = cabs1(x0);
-    double xn = sqrt(ax0 * ax0 + sig);
-    cplx ph = ax0 > 0.0 ? cmk(x0.x / ax0, x0.y / ax0) : cmk(1.0, 0.0);
-    cplx beta = cmk(-ph.x * xn, -ph.y * xn);
-    cplx v0 = csub(x0, beta);
-    double vv = cabs2(v0) + sig;
-    st->v0 = v0;
-    st->tau = vv > 0.0 ? 2.0 / vv : 0.0;
-    cs[s] = beta;
-    st->rank = (int)(s + 1);
-  }
-}
-
-__global__ void k_bqb_update(const BigQrJob* jobs, int64_t s) {
-  const BigQrJob jb = jobs[blockIdx.y];
-  const BigQrState* st = jb.st;
-  if (st->done) return;
-  const int64_t m = jb.m, n = jb.n;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const cplx v0 = st->v0;
-  const double tau = st->tau;
-  cplx* A = jb.A;
-  const cplx* cs = A + s * m;
-  for (int64_t j = s + 1 + warp; j < n; j += nwarps) {
-    cplx* cj = A + j * m;
-    cplx w = cmk(0.0, 0.0);
-    for (int64_t i = s + 1 + lane; i < m; i += 32) w = cfma(cconj(cs[i]), cj[i], w);
-    for (int o = 16; o > 0; o >>= 1) {
-      w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
-      w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
-    }
-    w = cfma(cconj(v0), cj[s], w);
-    w = cscale(w, tau);
-    cplx top = csub(cj[s], cmul(v0, w));
-    for (int64_t i = s + 1 + lane; i < m; i += 32) cj[i] = csub(cj[i], cmul(cs[i], w));
-    double t = jb.nrm[j] - cabs2(top);
-    if (t <= 0.0078125 * jb.nref[j]) {
-      double q = 0.0;
-      for (int64_t i = s + 1 + lane; i < m; i += 32) q += cabs2(cj[i]);
-      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-      t = q;
-      if (lane == 0) jb.nref[j] = q;
-    }
-    if (lane == 0) { cj[s] = top; jb.nrm[j] = t; }
-  }
-}
-
-__global__ void k_bqb_tsolve(const BigQrJob* jobs) {
-  const BigQrJob jb = jobs[blockIdx.y];
-  const int k = jb.st->rank;
-  const int64_t m = jb.m, n = jb.n;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const cplx* A = jb.A;
-  for (int64_t c = warp; c < n - k; c += nwarps) {
-    const cplx* r12 = A + (k + c) * m;
-    cplx* tc = jb.T + c * (int64_t)k;
-    for (int i = k - 1; i >= 0; --i) {
-      cplx acc = cmk(0.0, 0.0);
-      for (int l = i + 1 + lane; l < k; l += 32) acc = cfma(A[(int64_t)l * m + i], tc[l], acc);
-      for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-      }
-      if (lane == 0) tc[i] = cdiv(csub(r12[i], acc), A[(int64_t)i * m + i]);
-      __syncwarp();
-    }
-  }
-}
-
+// Column-pivoted QR / ID of several large matrices (the top tree levels) in one
+// persistent launch (pqr.cu).
 std::vector<int> big_row_id_batched(std::vector<BigQrJobSpec>& specs, double tol, cudaStream_t s) {
-  const int nj = (int)specs.size();
-  std::vector<int> ranks(nj, 0);
-  if (nj == 0) return ranks;
-  const int nparts = std::max(8, 296 / nj);
-  const int ublocks = std::max(8, 1184 / nj);
-  int64_t ntot = 0, kmax = 0;
-  for (auto& sp : specs) { ntot += sp.n; kmax = std::max<int64_t>(kmax, std::min<int64_t>(sp.m, sp.n)); }
-  DevBuf<double> nrm(ntot), nref(ntot), pv((size_t)nparts * nj);
-  DevBuf<int> pi((size_t)nparts * nj);
-  DevBuf<BigQrState> st(nj);
-  HBS_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(BigQrState) * nj, s));
-  std::vector<BigQrJob> jobs(nj);
-  int64_t o = 0;
-  for (int j = 0; j < nj; ++j) {
-    jobs[j] = {specs[j].A, specs[j].m, specs[j].n, specs[j].perm, specs[j].T, nrm.get() + o, nref.get() + o,
-               pv.get() + (int64_t)nparts * j, pi.get() + (int64_t)nparts * j, st.get() + j};
-    o += specs[j].n;
-  }
-  DevBuf<BigQrJob> dj;
-  dj.upload(jobs, s);
-  {
-    prof::KScope _ks("k_bqb_norms", s);
-    k_bqb_norms<<<dim3(ublocks, nj), 256, 0, s>>>(dj.get());
-  }
-  std::vector<BigQrState> hs(nj);
-  for (int64_t step = 0; step < kmax; ++step) {
-    {
-      prof::KScope _ks("k_bqb_argmax", s);
-      k_bqb_argmax<<<dim3(nparts, nj), 256, 0, s>>>(dj.get(), step);
-    }
-    {
-      prof::KScope _ks("k_bqb_pivot", s);
-      k_bqb_pivot<<<dim3(1, nj), 256, 0, s>>>(dj.get(), step, nparts, tol);
-    }
-    {
-      prof::KScope _ks("k_bqb_update", s);
-      k_bqb_update<<<dim3(ublocks, nj), 256, 0, s>>>(dj.get(), step);
-    }
-    if ((step & 15) == 15) {
-      HBS_LAUNCH_CHECK("batched big qr step");
-      HBS_CUDA(cudaMemcpyAsync(hs.data(), st.get(), sizeof(BigQrState) * nj, cudaMemcpyDeviceToHost, s));
-      HBS_CUDA(cudaStreamSynchronize(s));
-      bool all = true;
-      for (auto& x : hs) all = all && x.done;
-      if (all) break;
-    }
-  }
-  HBS_LAUNCH_CHECK("batched big qr");
-  {
-    prof::KScope _ks("k_bqb_tsolve", s);
-    k_bqb_tsolve<<<dim3(ublocks, nj), 256, 0, s>>>(dj.get());
-  }
-  HBS_LAUNCH_CHECK("k_bqb_tsolve");
-  HBS_CUDA(cudaMemcpyAsync(hs.data(), st.get(), sizeof(BigQrState) * nj, cudaMemcpyDeviceToHost, s));
-  HBS_CUDA(cudaStreamSynchronize(s));
-  for (int j = 0; j < nj; ++j) ranks[j] = hs[j].rank;
-  return ranks;
+  std::vector<PqrSpec> sp;
+  for (auto& j : specs) sp.push_back({j.A, j.m, j.n, (int)std::min(j.m, j.n), j.perm, j.T});
+  PqrOut out;
+  pqr_run(sp, tol, s, out);
+  return out.rank;
 }
 
 }  // namespace hbs

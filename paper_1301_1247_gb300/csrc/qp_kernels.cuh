@@ -17,17 +17,6 @@ struct BigQrState {
   double tau;
 };
 
-struct BigQrJob {
-  cplx* A;
-  int64_t m, n;
-  int* perm;
-  cplx* T;
-  double* nrm;
-  double* nref;
-  double* pv;
-  int* pi;
-  BigQrState* st;
-};
 struct BigQrJobSpec {
   cplx* A;     // m x n, column-major, overwritten
   int64_t m, n;
@@ -36,6 +25,47 @@ struct BigQrJobSpec {
 };
 // Column-pivoted QR / ID of several large matrices at once on all SMs; returns the ranks.
 std::vector<int> big_row_id_batched(std::vector<BigQrJobSpec>& specs, double tol, cudaStream_t s);
+
+// pqr.cu: persistent column-pivoted QR (one cooperative launch for all steps of a batch).
+struct PqrState {
+  int rank;
+  int capped;  // stopped at kcap before reaching the tolerance
+  double r00;
+};
+struct PqrSpec {
+  cplx* A;       // m x n, column-major (ld m), overwritten by the factorization
+  int64_t m, n;
+  int kcap;      // largest rank allowed
+  int* perm;     // out: n entries, skeleton columns first
+  cplx* T;       // out: k x (n - k), ld k (capacity min(m, n, kcap) x n)
+};
+// Per-step data of the factorizations, concatenated (matrix j at koff[j]): pivot column,
+// R diagonal, reflector head and tau; the reflector tail of step s sits in rows s+1..m-1
+// of column piv[s] of the factored matrix.
+struct PqrOut {
+  std::vector<int> rank;
+  std::vector<int64_t> koff;
+  DevBuf<int> piv;
+  DevBuf<cplx> beta, v0;
+  DevBuf<double> tau;
+};
+void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrOut& out);
+// pgj.cu: in-place inverses of several large matrices (pointer, n) in one persistent
+// launch; throws HBS_WARN_ILLCOND on a singular block.
+void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, const char* what);
+// X(:, c) = R^{-1} B(:, c) for upper-triangular R (k x k, row-major); X may alias B.
+__global__ void k_tsolve_cols(const cplx* R, int k, const cplx* B, int64_t ldb, int64_t ncols, cplx* X, int64_t ldx);
+// Columns of conj(Q1), Q1 = the first k columns of the factorization's Q (m x k, ld m).
+__global__ void k_form_qc(const cplx* A, int64_t m, const int* piv, const cplx* v0, const double* tau, int k,
+                          cplx* Qc);
+__global__ void k_r11_rows(const cplx* A, int64_t m, const int* piv, const cplx* beta, int k, cplx* R);
+__global__ void k_gather_cols(const cplx* src, int64_t lds, int64_t rows, const int64_t* idx, int64_t ncols, cplx* out,
+                              int64_t ldo);
+__global__ void k_set_unit_cols(cplx* X, int k, const int64_t* idx);
+
+// persist.cu: the handle to / from a file (HBS_ERR_IO on any file problem)
+void save_handle(Handle& h, const char* path, cudaStream_t s);
+void load_handle(Handle& h, const char* path, cudaStream_t s);
 
 // hbs_build.cu
 void build_hbs(Handle& h, cudaStream_t s);
@@ -55,7 +85,6 @@ __global__ void k_fill_wall_samples(const cplx* k, const cplx* wk, int M, int S,
 __global__ void k_fill_nb(DevGeom g, const int64_t* near_m, int nm, const int64_t* near_p, int npn, double d,
                           double cx, double cy, double R, int np, double wp, cplx* Mt);
 __global__ void k_fill_r(DevGeom g, const int64_t* J, int l, double d, cplx* Rm, cplx* Rp);
-__global__ void k_build_p(const int* perm, const cplx* T, int64_t N, int l, cplx* P);
 int big_row_id(cplx* Mt, int64_t m, int64_t n, double tol, int* perm, cplx* T, int max_rank, cudaStream_t s);
 __global__ void k_bq_norms(const cplx* A, int64_t m, int64_t n, double* nrm, double* nref, int* perm);
 __global__ void k_bq_argmax(const double* nrm, int64_t s, int64_t n, const BigQrState* st, double* pv, int* pi);

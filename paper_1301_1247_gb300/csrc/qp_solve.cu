@@ -131,30 +131,96 @@ void build_periodizer(Handle& h, cudaStream_t s) {
       k_fill_nb<<<grid_1d(m * N), 256, 0, s>>>(g, dnm.get(), nm, dnp.get(), npn, d, cx, cy, R, np, wp, Mt.get());
     }
     HBS_LAUNCH_CHECK("k_fill_nb");
-    DevBuf<int> perm(N);
-    const int kcap = (int)std::min<int64_t>(m, 4096);
-    DevBuf<cplx> T((size_t)kcap * N);
-    int l = big_row_id(Mt.get(), m, N, h.tol, perm.get(), T.get(), kcap, s);
+    // Row ID of the neighbour interactions (Def. 3.1).  The skeleton is chosen by a
+    // column-pivoted QR among candidate boundary nodes (every stride-th node): their
+    // columns of Mt are smooth functions of the node, so candidates far finer than the
+    // wavelength lose nothing.  Every node's interpolation coefficients then follow by
+    // least squares against the skeleton columns, t_i = R11^{-1} Q1^H Mt(:, i), which for
+    // the candidates is exactly T = R11^{-1} R12 of the QR.
+    const int64_t stride = std::max<int64_t>(1, (N + 16383) / 16384);
+    const int64_t nc = (N + stride - 1) / stride;
+    DevBuf<cplx> Mc((size_t)m * nc);
+    HBS_CUDA(cudaMemcpy2DAsync(Mc.get(), sizeof(cplx) * m, Mt.get(), sizeof(cplx) * m * stride, sizeof(cplx) * m, nc,
+                               cudaMemcpyDeviceToDevice, s));
+    const int kcap = (int)std::min<int64_t>(std::min<int64_t>(m, nc), 4096);
+    DevBuf<int> cperm(nc);
+    DevBuf<cplx> cT((size_t)kcap * nc);
+    PqrOut qr;
+    {
+      std::vector<PqrSpec> sp{{Mc.get(), m, nc, kcap, cperm.get(), cT.get()}};
+      pqr_run(sp, h.tol, s, qr);
+    }
+    const int l = qr.rank[0];
     h.nb_rank = l;
-    std::vector<int> hperm = perm.download(s, l);
-    std::vector<int64_t> J(hperm.begin(), hperm.end());
+    std::vector<int> hpiv = qr.piv.download(s, l);
+    std::vector<int64_t> J(l);
+    for (int i = 0; i < l; ++i) J[i] = (int64_t)hpiv[i] * stride;
     h.nb_skel.upload(J, s);
     h.Rm.alloc(std::max<int64_t>((int64_t)l * N, 1));
     h.Rp.alloc(std::max<int64_t>((int64_t)l * N, 1));
+    h.Pnb.alloc(std::max<int64_t>((int64_t)l * N, 1));
+    h.nb_residual = 0.0;
     if (l > 0) {
       {
         prof::KScope _ks("k_fill_r", s);
         k_fill_r<<<grid_1d((int64_t)l * N), 256, 0, s>>>(g, h.nb_skel.get(), l, d, h.Rm.get(), h.Rp.get());
       }
       HBS_LAUNCH_CHECK("k_fill_r");
-    }
-    h.Pnb.alloc(std::max<int64_t>((int64_t)l * N, 1));
-    if (l > 0) {
+      DevBuf<cplx> Qc((size_t)m * l), R11((size_t)l * l), Tall((size_t)l * N);
       {
-        prof::KScope _ks("k_build_p", s);
-        k_build_p<<<grid_1d((int64_t)l * N), 256, 0, s>>>(perm.get(), T.get(), N, l, h.Pnb.get());
+        prof::KScope _ks("k_form_qc", s);
+        k_form_qc<<<l, 256, 0, s>>>(Mc.get(), m, qr.piv.get(), qr.v0.get(), qr.tau.get(), l, Qc.get());
       }
-      HBS_LAUNCH_CHECK("k_build_p");
+      {
+        prof::KScope _ks("k_r11_rows", s);
+        k_r11_rows<<<grid_1d((int64_t)l * l), 256, 0, s>>>(Mc.get(), m, qr.piv.get(), qr.beta.get(), l, R11.get());
+      }
+      HBS_LAUNCH_CHECK("neighbour Q1 / R11");
+      // Tall = Q1^H Mt (l x N), then R11^{-1} in place; skeleton nodes get unit columns.
+      std::vector<GemmJob> gj(1);
+      gj[0] = GemmJob{Qc.get(), Mt.get(), Tall.get(), l, (int)N, (int)m, (int)m, (int)m, l,
+                      cmk(1.0, 0.0), cmk(0.0, 0.0), 0, 0, 0, 1};
+      run_gemms(gj, s);
+      {
+        prof::KScope _ks("k_tsolve_cols", s);
+        k_tsolve_cols<<<grid_1d(N * 32, 256, 4096), 256, 0, s>>>(R11.get(), l, Tall.get(), l, N, Tall.get(), l);
+      }
+      {
+        prof::KScope _ks("k_set_unit_cols", s);
+        k_set_unit_cols<<<grid_1d((int64_t)l * l), 256, 0, s>>>(Tall.get(), l, h.nb_skel.get());
+      }
+      {
+        prof::KScope _ks("k_transpose", s);
+        k_transpose<<<grid_1d((int64_t)l * N), 256, 0, s>>>(Tall.get(), l, N, h.Pnb.get());
+      }
+      HBS_LAUNCH_CHECK("neighbour interpolation");
+      // Check on nodes half-way between candidates: |Mt(:, i) - Mt(:, J) t_i| / |Mt(:, i)|.
+      if (stride > 1) {
+        const int64_t nchk = std::min<int64_t>(nc - 1, 4096);
+        std::vector<int64_t> chk(nchk);
+        for (int64_t c = 0; c < nchk; ++c) chk[c] = std::min<int64_t>(N - 1, ((c * (nc - 1)) / nchk) * stride + stride / 2);
+        DevBuf<int64_t> dchk;
+        dchk.upload(chk, s);
+        DevBuf<cplx> G((size_t)m * l), Ms((size_t)m * nchk), Ts((size_t)l * nchk), Rec((size_t)m * nchk);
+        {
+          prof::KScope _ks("k_gather_cols", s);
+          k_gather_cols<<<grid_1d((int64_t)m * l), 256, 0, s>>>(Mt.get(), m, m, h.nb_skel.get(), l, G.get(), m);
+          k_gather_cols<<<grid_1d(m * nchk), 256, 0, s>>>(Mt.get(), m, m, dchk.get(), nchk, Ms.get(), m);
+          k_gather_cols<<<grid_1d((int64_t)l * nchk), 256, 0, s>>>(Tall.get(), l, l, dchk.get(), nchk, Ts.get(), l);
+        }
+        std::vector<GemmJob> cj(1);
+        cj[0] = GemmJob{G.get(), Ts.get(), Rec.get(), (int)m, (int)nchk, l, (int)m, l, (int)m,
+                        cmk(1.0, 0.0), cmk(0.0, 0.0), 0, 0, 0, 0};
+        run_gemms(cj, s);
+        DevBuf<double> acc(2);
+        HBS_CUDA(cudaMemsetAsync(acc.get(), 0, 2 * sizeof(double), s));
+        {
+          prof::KScope _ks("k_diff_norm2", s);
+          k_diff_norm2<<<grid_1d(m * nchk), 256, 0, s>>>(Rec.get(), m, Ms.get(), m, (int)m, (int)nchk, acc.get());
+        }
+        auto ha = acc.download(s);
+        h.nb_residual = ha[1] > 0 ? std::sqrt(ha[0] / ha[1]) : 0.0;
+      }
     }
     HBS_CUDA(cudaStreamSynchronize(s));
   }
@@ -212,7 +278,17 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   // node, so an ID found on a fine subsample holds on all N nodes; a disjoint second
   // subsample checks that.
   ph.next("build:periodizer_id");
-  const int ns = (int)std::min<int64_t>(N, 8192);
+  // Subsample size: at least 16 points per oscillation of the fastest member along the
+  // boundary (wavenumbers up to the contour's reach cK), never fewer than 2048.  At
+  // 2048 points a family's sampled matrix stays resident in L2 through the ID's steps.
+  double perim = 0.0;
+  for (int64_t i = 0; i < N; ++i) {
+    const int64_t j = (i + 1) % N;
+    perim += std::hypot(h.hx[j] - h.hx[i], h.hy[j] - h.hy[i]);
+  }
+  const double osc = perim * std::max(omega, h.cK) / (2.0 * M_PI);
+  int ns_want = std::max(2048, (int)std::ceil(16.0 * osc / 256.0) * 256);
+  const int ns = (int)std::min<int64_t>(N, std::min(ns_want, 16384));
   std::vector<int64_t> hsub(ns), hsub2(ns);
   for (int i = 0; i < ns; ++i) {
     hsub[i] = (int64_t)((double)i * N / ns);
@@ -643,60 +719,131 @@ __global__ void k_assemble(Dims D, const GroupJob* groups, const cplx* proj, dou
 template <int NT>
 __global__ void __launch_bounds__(NT) k_schur_solve(Dims D, const GroupJob* groups, cplx* Spool, cplx* Rpool,
                                                     int* illcond) {
+  // Right-looking LU with partial pivoting of the augmented system [S | R] (one CTA per
+  // Bloch group), blocked by panels of NB columns: the panel is factored column by
+  // column, U12 = L11^{-1} A12 follows by forward substitution (one thread per column),
+  // and the trailing matrix gets one rank-NB update from shared-memory tiles of L21 and
+  // U12 with 4 x 4 register tiles per thread.
+  constexpr int NB = 16, TM = 64;
+  static_assert(NT == 256, "16 x 16 threads per trailing tile");
   __shared__ double redv[32];
   __shared__ int redi[32];
   __shared__ cplx sh_ip;
+  __shared__ cplx Ls[NB][TM + 1];
+  __shared__ cplx Us[NB][TM + 1];
+  __shared__ cplx L11[NB][NB + 1];
   const GroupJob G = groups[blockIdx.x];
-  const int n = G.nsys, q = G.q;
+  const int n = G.nsys, q = G.q, nc = n + q;
   cplx* A = Spool + G.s_off;
   cplx* B = Rpool + G.r_off;
+  auto col = [&](int j) -> cplx* { return j < n ? A + (int64_t)j * n : B + (int64_t)(j - n) * n; };
   const int tid = threadIdx.x;
   double pmax = 0.0, pmin = 1e300;
-  for (int c = 0; c < n; ++c) {
-    double best = -1.0;
-    int bi = 0x7fffffff;
-    for (int i = c + tid; i < n; i += NT) {
-      double v = cabs2(A[(int64_t)c * n + i]);
-      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
-    }
-    double pv;
-    int p;
-    block_argmax<NT>(best, bi, redv, redi, &pv, &p);
-    pmax = fmax(pmax, pv);
-    pmin = fmin(pmin, pv);
-    if (p != c) {
-      for (int j = tid; j < n; j += NT) {
-        cplx t = A[(int64_t)j * n + c]; A[(int64_t)j * n + c] = A[(int64_t)j * n + p]; A[(int64_t)j * n + p] = t;
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    const int nb = min(NB, n - k0);
+    for (int c = k0; c < k0 + nb; ++c) {
+      cplx* ac = A + (int64_t)c * n;
+      double best = -1.0;
+      int bi = 0x7fffffff;
+      for (int i = c + tid; i < n; i += NT) {
+        const double v = cabs2(ac[i]);
+        if (v > best || (v == best && i < bi)) { best = v; bi = i; }
       }
-      for (int j = tid; j < q; j += NT) {
-        cplx t = B[(int64_t)j * n + c]; B[(int64_t)j * n + c] = B[(int64_t)j * n + p]; B[(int64_t)j * n + p] = t;
+      double pv;
+      int p;
+      block_argmax<NT>(best, bi, redv, redi, &pv, &p);
+      pmax = fmax(pmax, pv);
+      pmin = fmin(pmin, pv);
+      if (p != c) {
+        for (int j = tid; j < nc; j += NT) {
+          cplx* cj = col(j);
+          const cplx t = cj[c];
+          cj[c] = cj[p];
+          cj[p] = t;
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        const cplx dv = ac[c];
+        sh_ip = cabs2(dv) > 0.0 ? cdiv(cmk(1, 0), dv) : cmk(0, 0);
+      }
+      __syncthreads();
+      const cplx ip = sh_ip;
+      for (int i = c + 1 + tid; i < n; i += NT) ac[i] = cmul(ac[i], ip);
+      __syncthreads();
+      for (int j = c + 1; j < k0 + nb; ++j) {
+        cplx* aj = A + (int64_t)j * n;
+        const cplx ucj = aj[c];
+        for (int i = c + 1 + tid; i < n; i += NT) aj[i] = csub(aj[i], cmul(ac[i], ucj));
+      }
+      __syncthreads();
+    }
+    const int j0 = k0 + nb;
+    if (j0 >= nc) break;
+    for (int e = tid; e < NB * NB; e += NT) {
+      const int r = e % NB, cc = e / NB;
+      L11[r][cc] = (r < nb && cc < nb) ? A[(int64_t)(k0 + cc) * n + k0 + r] : cmk(0, 0);
+    }
+    __syncthreads();
+    for (int j = j0 + tid; j < nc; j += NT) {
+      cplx* aj = col(j) + k0;
+      cplx u[NB];
+#pragma unroll
+      for (int r = 0; r < NB; ++r) u[r] = r < nb ? aj[r] : cmk(0, 0);
+#pragma unroll
+      for (int cc = 0; cc < NB; ++cc)
+#pragma unroll
+        for (int r = cc + 1; r < NB; ++r) u[r] = csub(u[r], cmul(L11[r][cc], u[cc]));
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+        if (r < nb) aj[r] = u[r];
+    }
+    __syncthreads();
+    const int rows = n - j0, cols = nc - j0;
+    const int tr = tid & 15, tc = tid >> 4;
+    for (int rt = 0; rt < rows; rt += TM) {
+      for (int ct = 0; ct < cols; ct += TM) {
+        for (int e = tid; e < TM * NB; e += NT) {
+          const int r = e % TM, kk = e / TM;
+          const int i = j0 + rt + r;
+          Ls[kk][r] = (i < n && kk < nb) ? A[(int64_t)(k0 + kk) * n + i] : cmk(0, 0);
+        }
+        for (int e = tid; e < TM * NB; e += NT) {
+          const int kk = e % NB, c = e / NB;
+          const int j = j0 + ct + c;
+          Us[kk][c] = (j < nc && kk < nb) ? col(j)[k0 + kk] : cmk(0, 0);
+        }
+        __syncthreads();
+        cplx acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = cmk(0, 0);
+        for (int kk = 0; kk < nb; ++kk) {
+          cplx la[4], ub[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) la[a] = Ls[kk][tr + 16 * a];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) ub[b] = Us[kk][tc + 16 * b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = cfma(la[a], ub[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int j = j0 + ct + tc + 16 * b;
+          if (j >= nc) continue;
+          cplx* cj = col(j);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int i = j0 + rt + tr + 16 * a;
+            if (i < n) cj[i] = csub(cj[i], acc[a][b]);
+          }
+        }
+        __syncthreads();
       }
     }
-    __syncthreads();
-    if (tid == 0) {
-      cplx dv = A[(int64_t)c * n + c];
-      sh_ip = cabs2(dv) > 0.0 ? cdiv(cmk(1, 0), dv) : cmk(0, 0);
-    }
-    __syncthreads();
-    const cplx ip = sh_ip;
-    // multipliers l_ic = A[i,c]/A[c,c] stored in place
-    for (int i = c + 1 + tid; i < n; i += NT) A[(int64_t)c * n + i] = cmul(A[(int64_t)c * n + i], ip);
-    __syncthreads();
-    const int rows = n - c - 1;
-    const int64_t tot = (int64_t)rows * (n - c - 1 + q);
-    for (int64_t e = tid; e < tot; e += NT) {
-      const int i = c + 1 + (int)(e % rows);
-      const int j = (int)(e / rows);
-      const cplx li = A[(int64_t)c * n + i];
-      if (j < n - c - 1) {
-        const int jj = c + 1 + j;
-        A[(int64_t)jj * n + i] = csub(A[(int64_t)jj * n + i], cmul(li, A[(int64_t)jj * n + c]));
-      } else {
-        const int jj = j - (n - c - 1);
-        B[(int64_t)jj * n + i] = csub(B[(int64_t)jj * n + i], cmul(li, B[(int64_t)jj * n + c]));
-      }
-    }
-    __syncthreads();
   }
   // back substitution, one RHS per warp
   const int lane = tid & 31, warp = tid >> 5;
@@ -1227,6 +1374,7 @@ static zc kn_of(double omega, double kap) {
 
 // Full wall rows C_L^c, C_R^c and Bragg sampling rows E, used only by the plain path.
 static void ensure_full_rows(Handle& h, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(h.lazy_mu);
   const int64_t N = h.N;
   const int M = h.M, S = h.S;
   const DevGeom g = Handle_geom(h);

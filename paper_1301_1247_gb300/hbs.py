@@ -15,13 +15,21 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhbsqp.so")
 
 HBS_OK = 0
+HBS_ERR_INVALID_ARG = 1
+HBS_ERR_OOM = 2
+HBS_ERR_CUDA = 3
+HBS_ERR_RANK = 4
 HBS_WARN_ILLCOND = 5
+HBS_ERR_TIMEOUT = 6
+HBS_ERR_IO = 7
+HBS_ERR_INTERNAL = 8
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "RANK", 5: "WARN_ILLCOND",
                 6: "TIMEOUT", 7: "IO", 8: "INTERNAL"}
 
 # Every entry point declared in include/hbsqp.h.
 EXPORTED = ("hbs_default_options", "hbs_build", "hbs_solve", "hbs_solve_plain", "hbs_bragg_amplitudes",
-            "hbs_result_angle_info", "hbs_info", "hbs_apply_inverse", "hbs_kernel_block", "hbs_row_id",
+            "hbs_result_angle_info", "hbs_info", "hbs_save", "hbs_load", "hbs_apply_inverse",
+            "hbs_kernel_block", "hbs_row_id",
             "hbs_row_id_static",
             "hbs_profile_enable", "hbs_profile_reset", "hbs_profile_get", "hbs_launch_count",
             "hbs_free", "hbs_result_free", "hbs_last_error")
@@ -48,7 +56,8 @@ class Info(ctypes.Structure):
                 ("contour_h", ctypes.c_double), ("contour_c", ctypes.c_double), ("contour_w", ctypes.c_double),
                 ("wood_t0", ctypes.c_double), ("n_bragg_samples", ctypes.c_int), ("y0", ctypes.c_double),
                 ("nb_radius", ctypes.c_double), ("nb_proxies", ctypes.c_int), ("pid_col_rank", ctypes.c_int),
-                ("pid_row_rank", ctypes.c_int), ("pid_residual", ctypes.c_double)]
+                ("pid_row_rank", ctypes.c_int), ("pid_residual", ctypes.c_double),
+                ("nb_residual", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -80,6 +89,10 @@ def lib():
                                        ctypes.POINTER(dbl)]
     L.hbs_result_angle_info.argtypes = [vp, i64, ctypes.POINTER(ci), ctypes.POINTER(dbl)]
     L.hbs_info.argtypes = [vp, ctypes.POINTER(Info)]
+    L.hbs_save.argtypes = [vp, ctypes.c_char_p, vp]
+    L.hbs_save.restype = ctypes.c_int
+    L.hbs_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
+    L.hbs_load.restype = ctypes.c_int
     L.hbs_apply_inverse.argtypes = [vp, vp, vp, i64, vp]
     L.hbs_kernel_block.argtypes = [ctypes.POINTER(Geometry), dbl, ci, dbl, vp, i64, vp, i64, vp, vp]
     L.hbs_row_id.argtypes = [vp, i64, i64, dbl, ctypes.POINTER(ci), vp, vp, vp]
@@ -196,6 +209,21 @@ class Handle:
         _check(st, "hbs_build")
         self._p = out
         self.n = n
+
+    @classmethod
+    def load(cls, path, stream=None) -> "Handle":
+        """A solver written by save() (hbs_load)."""
+        out = ctypes.c_void_p()
+        _check(lib().hbs_load(str(path).encode(), _stream(stream), ctypes.byref(out)), "hbs_load")
+        h = cls.__new__(cls)
+        h._p = out
+        h._keep = []
+        h.n = h.info()["n"]
+        return h
+
+    def save(self, path, stream=None):
+        """Write the built solver to `path` (hbs_save)."""
+        _check(lib().hbs_save(self._p, str(path).encode(), _stream(stream)), "hbs_save")
 
     def __del__(self):
         if getattr(self, "_p", None):

@@ -55,3 +55,13 @@ def test_fullsize_flux_and_fp64_plain_path(full):
         _, c1, d1, _ = fast.bragg(i)
         _, c2, d2, _ = ref.bragg(i)
         assert relerr(np.concatenate([c1, d1]), np.concatenate([c2, d2])) < 1e-10
+
+
+def test_fullsize_compressions_hold_off_sample(full):
+    """The neighbour ID (skeleton chosen among every stride-th node) and the periodizer IDs
+    (found on a point subsample) reconstruct their matrices on nodes they never saw."""
+    hbs, w, geom, h = full
+    info = h.info()
+    assert 0 < info["nb_rank"] < info["nb_proxies"]
+    assert info["nb_residual"] < 1e-10
+    assert info["pid_residual"] < 1e-10

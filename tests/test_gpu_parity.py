@@ -44,18 +44,22 @@ def test_kernel_block_entries(case):
         assert np.max(np.abs(got - refi)) <= 1e-13 * np.abs(refi).max()
 
 
-@pytest.mark.parametrize("shape", [(300, 40), (150, 64), (37, 90)])
+@pytest.mark.parametrize("shape", [(300, 40), (150, 64), (37, 90), (600, 200), (300, 5000), (700, 5000)])
 def test_row_id_matches_oracle(shape):
     """CPQR interpolative decomposition (Def. 3.1): same rank and skeleton as the oracle's
-    LAPACK-pivoted QR on a kernel block, and the same reconstruction accuracy."""
+    LAPACK-pivoted QR on a kernel block, and the same reconstruction accuracy.  The first
+    three shapes run one CTA per matrix; (600, 200) and the 5000-row shapes run the
+    persistent multi-CTA QR (CTA per column for > 320 columns of Mt, warp per column
+    otherwise)."""
     import torch
     hbs = require_lib()
     m_cols, n_rows = shape
     omega = 20.0
-    x, y, dx, dy = inputs.star(0.3, 0.3, 5).sample(600)
+    npts = 600 if n_rows + m_cols < 500 else 8000
+    x, y, dx, dy = inputs.star(0.3, 0.3, 5).sample(npts)
     bd = qd.boundary(x, y, dx, dy)
     rows = np.arange(0, n_rows)
-    cols = np.arange(200, 200 + m_cols)
+    cols = np.arange(200, 200 + m_cols) if npts == 600 else np.arange(npts - m_cols, npts)
     blk = qd.combined(bd.x[rows, None], bd.y[rows, None], bd.x[None, cols], bd.y[None, cols],
                       bd.nx[None, cols], bd.ny[None, cols], omega) * bd.w[None, cols]
     tol = 1e-12
@@ -184,3 +188,30 @@ def test_double_float_products_match_oracle_and_fp64():
         _, c1, d1, _ = a.bragg(i)
         _, c2, d2, _ = b.bragg(i)
         assert relerr(np.concatenate([c1, d1]), np.concatenate([c2, d2])) < 1e-10
+
+
+def test_save_load_round_trip(tmp_path):
+    """A solver written by hbs_save and read by hbs_load solves like the one that was built."""
+    hbs = require_lib()
+    obs = inputs.wiggly(3, 0.35, 20, 0.03)
+    x, y, dx, dy = obs.sample(3000)
+    omega = 25.0
+    h = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12)
+    th = inputs.bloch_grouped_angles(2, omega, 1.0, 2, 3).ravel()
+    a = h.solve(th)
+    path = tmp_path / "solver.hbs"
+    h.save(path)
+    h2 = hbs.Handle.load(path)
+    i1, i2 = h.info(), h2.info()
+    for key in ("n", "levels", "max_rank", "nb_rank", "m", "n_contours", "device_bytes", "pid_col_rank"):
+        assert i1[key] == i2[key], key
+    b = h2.solve(th)
+    c = h2.solve_plain(th[:3])
+    for i in range(len(th)):
+        _, c1, d1, f1 = a.bragg(i)
+        _, c2, d2, f2 = b.bragg(i)
+        assert relerr(np.concatenate([c2, d2]), np.concatenate([c1, d1])) < 1e-14
+    for i in range(3):
+        _, c1, d1, _ = a.bragg(i)
+        _, c3, d3, _ = c.bragg(i)
+        assert relerr(np.concatenate([c3, d3]), np.concatenate([c1, d1])) < 1e-11

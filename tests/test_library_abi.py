@@ -56,3 +56,23 @@ def test_argument_errors_need_no_gpu():
     assert L.hbs_build(ctypes.byref(g), 10.0, 1e-12, None, None, ctypes.byref(out)) == 1
     assert L.hbs_solve(None, None, 0, None, ctypes.byref(out)) == 1
     assert L.hbs_apply_inverse(None, None, None, 1, None) == 1
+
+
+def test_load_rejects_missing_and_foreign_files_without_gpu(tmp_path):
+    """hbs_load checks the file's tag before touching the device: a missing file, a file
+    of random bytes and a truncated tag all give HBS_ERR_IO and no handle."""
+    _ensure_built()
+    from paper_1301_1247_gb300 import hbs
+    L = hbs.lib()
+    out = ctypes.c_void_p(1)
+    assert L.hbs_load(str(tmp_path / "absent.hbs").encode(), None, ctypes.byref(out)) == hbs.HBS_ERR_IO
+    assert not out.value
+    junk = tmp_path / "junk.hbs"
+    junk.write_bytes(bytes(range(256)) * 4)
+    assert L.hbs_load(str(junk).encode(), None, ctypes.byref(out)) == hbs.HBS_ERR_IO
+    short = tmp_path / "short.hbs"
+    short.write_bytes(b"HBSQP\0v1")
+    assert L.hbs_load(str(short).encode(), None, ctypes.byref(out)) == hbs.HBS_ERR_IO
+    assert not out.value
+    assert L.hbs_load(None, None, ctypes.byref(out)) == hbs.HBS_ERR_INVALID_ARG
+    assert L.hbs_save(None, b"x", None) == hbs.HBS_ERR_INVALID_ARG
