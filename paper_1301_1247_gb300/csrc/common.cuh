@@ -26,6 +26,14 @@ __host__ __device__ __forceinline__ cplx cfma(cplx a, cplx b, cplx acc) {
   acc.y = fma(a.y, b.x, acc.y);
   return acc;
 }
+// acc - a * b, four fused multiply-adds
+__host__ __device__ __forceinline__ cplx cfms(cplx a, cplx b, cplx acc) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
 __host__ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
   // Smith's algorithm
   if (fabs(b.x) >= fabs(b.y)) {

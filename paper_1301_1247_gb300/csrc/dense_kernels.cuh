@@ -168,8 +168,8 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, cplx* pool, cp
       }
       w = cfma(cconj(v0), cj[s], w);
       w = cscale(w, tau);
-      if (lane == 0) cj[s] = csub(cj[s], cmul(v0, w));
-      for (int i = s + 1 + lane; i < m; i += 32) cj[i] = csub(cj[i], cmul(cs[i], w));
+      if (lane == 0) cj[s] = cfms(v0, w, cj[s]);
+      for (int i = s + 1 + lane; i < m; i += 32) cj[i] = cfms(cs[i], w, cj[i]);
       __syncwarp();
       // norm downdate, recomputation on cancellation
       if (lane == 0) {
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(NT) k_gj_inverse(const InvJob* jobs, cplx* poo
     for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
       int i = (int)(e % n), j = (int)(e / n);
       if (i == c || j == c) continue;
-      A[(int64_t)j * n + i] = csub(A[(int64_t)j * n + i], cmul(A[(int64_t)c * n + i], A[(int64_t)j * n + c]));
+      A[(int64_t)j * n + i] = cfms(A[(int64_t)c * n + i], A[(int64_t)j * n + c], A[(int64_t)j * n + i]);
     }
     __syncthreads();
     for (int i = tid; i < n; i += NT) {

@@ -345,7 +345,7 @@ static void launch_gemms(std::vector<GemmJob>& jobs_in, cudaStream_t s) {
   for (auto& j : jobs)
     if (j.C == nullptr) j.C = W.get() + j.tile_base;
   for (size_t r = 0; r < reds.size(); ++r) reds[r].W = W.get() + red_ws_off[r];
-  int64_t tiles = gemm_plan(jobs.data(), (int)jobs.size());
+  const int64_t tiles = gemm_plan(jobs.data(), (int)jobs.size());
   if (tiles > 0) {
     DevBuf<GemmJob> dj(jobs.size());
     HBS_CUDA(cudaMemcpyAsync(dj.get(), jobs.data(), jobs.size() * sizeof(GemmJob), cudaMemcpyHostToDevice, s));
@@ -407,13 +407,16 @@ std::vector<int> batched_id(std::vector<CpqrJob>& jobs, cplx* pool, cplx* tpool,
   if (jobs.empty()) return ranks;
   std::vector<CpqrJob> small;
   std::vector<size_t> small_idx, big_idx;
-  // The persistent multi-CTA QR pays off while a level has fewer large nodes than SMs;
-  // with more, one CTA per node keeps every SM busy.
+  // A level with at most 128 nodes runs all of them in one persistent multi-CTA launch
+  // (pqr.cu): one CTA per node would leave SMs idle and serialize on its largest node.
+  // With more nodes, one CTA per node keeps every SM busy, and only the large nodes (if
+  // at most 128 of them) go to the persistent launch.
   size_t nbig = 0;
   for (const auto& j : jobs) nbig += big_cpqr(j) ? 1 : 0;
-  const bool use_big = nbig > 0 && nbig <= 128;
+  const bool all_big = jobs.size() <= 128;
+  const bool use_big = all_big || (nbig > 0 && nbig <= 128);
   for (size_t i = 0; i < jobs.size(); ++i) {
-    if (use_big && big_cpqr(jobs[i])) {
+    if (use_big && (all_big || big_cpqr(jobs[i]))) {
       big_idx.push_back(i);
     } else {
       small_idx.push_back(i);
@@ -459,13 +462,15 @@ std::vector<int> batched_id(std::vector<CpqrJob>& jobs, cplx* pool, cplx* tpool,
 void batched_inverse(std::vector<InvJob>& jobs_in, cplx* pool, cudaStream_t s, const char* what) {
   std::vector<InvJob> jobs;
   std::vector<std::pair<cplx*, int>> big;
-  // The persistent multi-CTA Gauss-Jordan (pgj.cu) pays off while a level has fewer
-  // large blocks than SMs; with more, one CTA per block keeps every SM busy.
+  // Same split as for the IDs: at most 128 blocks all go to the persistent multi-CTA
+  // Gauss-Jordan (pgj.cu); with more, one CTA per block and the large ones (if at most
+  // 128) persistent.
   size_t nbig = 0;
   for (const auto& j : jobs_in) nbig += big_inverse(j.n) ? 1 : 0;
-  const bool use_big = nbig > 0 && nbig <= 128;
+  const bool all_big = jobs_in.size() <= 128;
+  const bool use_big = all_big || (nbig > 0 && nbig <= 128);
   for (auto& j : jobs_in) {
-    if (use_big && big_inverse(j.n)) big.push_back({pool + j.a_off, j.n});
+    if (use_big && (all_big || big_inverse(j.n))) big.push_back({pool + j.a_off, j.n});
     else jobs.push_back(j);
   }
   pgj_run(big, s, what);

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nma
         for (int i = lane; i < n; i += 32) {
           if (i == c) continue;
           const cplx x = (i == p) ? ap : aj[i];
-          aj[i] = csub(x, cmul(u[i], r));
+          aj[i] = cfms(u[i], r, x);
         }
         if (lane == 0) aj[c] = r;
       }

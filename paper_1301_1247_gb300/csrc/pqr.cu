@@ -7,8 +7,8 @@
 //     left by step s-1 and finds the pivot column p (largest remaining norm, lowest index
 //     on ties) - the same reduction in every CTA, so all agree bit for bit;
 //   * every CTA forms the reflector of column p (rows s..m-1) in shared memory;
-//   * each active column j != p is owned by one warp (m <= 320) or one CTA and is
-//     updated in registers, its norm downdated (recomputed on cancellation), and the
+//   * each active column j != p is owned by one warp and is updated (in registers for
+//     its first 320 rows), its norm downdated (recomputed on cancellation), and the
 //     CTA's partial maximum for step s+1 recorded.
 // Columns are never swapped: pivot p of step s stays where it is, its rows < s hold
 // R(:, s) and its rows > s the reflector tail; the diagonal beta_s, the reflector head
@@ -29,9 +29,7 @@ namespace {
 
 constexpr int kNT = 256;
 constexpr int kNW = kNT / 32;
-constexpr int kWarpRows = 320;  // warp-per-column mode up to this many rows
-constexpr int kReg = 10;        // rows per lane held in registers (warp mode)
-constexpr int kRegB = 8;        // rows per thread held in registers (CTA mode)
+constexpr int kReg = 10;        // rows per lane held in registers
 
 struct PqrJob {
   cplx* A;
@@ -88,7 +86,9 @@ __device__ __forceinline__ void tsolve_row_major(const cplx* R, int k, const cpl
   }
 }
 
-// One Householder update of column j at step s (warp mode: 32 lanes own one column).
+// One Householder update of column j at step s: the 32 lanes of a warp own the column,
+// its first 32 kReg rows below s stay in registers between the two passes and the rest
+// (tall matrices) is streamed twice.
 __device__ __forceinline__ double update_col_warp(cplx* aj, const cplx* vt, int64_t m, int64_t s, cplx v0, double tau,
                                                   double nj, double* nref_j, int lane) {
   cplx r[kReg];
@@ -101,71 +101,33 @@ __device__ __forceinline__ double update_col_warp(cplx* aj, const cplx* vt, int6
       w = cfma(cconj(vt[i - s - 1]), r[q], w);
     }
   }
+  for (int64_t i = s + 1 + lane + 32 * kReg; i < m; i += 32) w = cfma(cconj(vt[i - s - 1]), aj[i], w);
   w = warp_sum_c(w);
   const cplx ajs = aj[s];
   w = cscale(cfma(cconj(v0), ajs, w), tau);
-  const cplx top = csub(ajs, cmul(v0, w));
-  double q2 = 0.0;
+  const cplx top = cfms(v0, w, ajs);
 #pragma unroll
   for (int q = 0; q < kReg; ++q) {
     const int64_t i = s + 1 + lane + 32 * q;
     if (i < m) {
-      r[q] = csub(r[q], cmul(vt[i - s - 1], w));
+      r[q] = cfms(vt[i - s - 1], w, r[q]);
       aj[i] = r[q];
-      q2 += cabs2(r[q]);
     }
   }
+  for (int64_t i = s + 1 + lane + 32 * kReg; i < m; i += 32) aj[i] = cfms(vt[i - s - 1], w, aj[i]);
   double t = nj - cabs2(top);
   if (t <= 0.0078125 * *nref_j) {
+    // cancellation: recompute the norm of rows s+1.. from the updated values
+    double q2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < kReg; ++q)
+      if (s + 1 + lane + 32 * q < m) q2 += cabs2(r[q]);
+    for (int64_t i = s + 1 + lane + 32 * kReg; i < m; i += 32) q2 += cabs2(aj[i]);
     t = warp_sum(q2);
     if (lane == 0) *nref_j = t;
   }
   __syncwarp();
   if (lane == 0) aj[s] = top;
-  return t;
-}
-
-// The same update with one CTA per column (rows beyond NT * kRegB are streamed).
-__device__ __forceinline__ double update_col_block(cplx* aj, const cplx* vt, int64_t m, int64_t s, cplx v0, double tau,
-                                                   double nj, double* nref_j, double* red) {
-  const int tid = threadIdx.x;
-  cplx r[kRegB];
-  cplx w = cmk(0.0, 0.0);
-#pragma unroll
-  for (int q = 0; q < kRegB; ++q) {
-    const int64_t i = s + 1 + tid + (int64_t)kNT * q;
-    if (i < m) {
-      r[q] = aj[i];
-      w = cfma(cconj(vt[i - s - 1]), r[q], w);
-    }
-  }
-  for (int64_t i = s + 1 + tid + (int64_t)kNT * kRegB; i < m; i += kNT) w = cfma(cconj(vt[i - s - 1]), aj[i], w);
-  w = block_sum_c<kNT>(w, red);
-  const cplx ajs = aj[s];
-  w = cscale(cfma(cconj(v0), ajs, w), tau);
-  const cplx top = csub(ajs, cmul(v0, w));
-  double q2 = 0.0;
-#pragma unroll
-  for (int q = 0; q < kRegB; ++q) {
-    const int64_t i = s + 1 + tid + (int64_t)kNT * q;
-    if (i < m) {
-      r[q] = csub(r[q], cmul(vt[i - s - 1], w));
-      aj[i] = r[q];
-      q2 += cabs2(r[q]);
-    }
-  }
-  for (int64_t i = s + 1 + tid + (int64_t)kNT * kRegB; i < m; i += kNT) {
-    const cplx x = csub(aj[i], cmul(vt[i - s - 1], w));
-    aj[i] = x;
-    q2 += cabs2(x);
-  }
-  double t = nj - cabs2(top);
-  if (t <= 0.0078125 * *nref_j) {  // uniform over the CTA
-    t = block_sum<kNT>(q2, red);
-    if (tid == 0) *nref_j = t;
-  }
-  __syncthreads();
-  if (tid == 0) aj[s] = top;
   return t;
 }
 
@@ -181,7 +143,6 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
   const int G = gridDim.x;
   const int lb = (int)blockIdx.x - jb.b0;
   const int64_t m = jb.m, n = jb.n;
-  const bool wmode = m <= kWarpRows;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t gw = (int64_t)lb * kNW + warp, nw = (int64_t)jb.nb * kNW;
   cplx* A = jb.A;
@@ -190,22 +151,12 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
   {
     double best = -1.0;
     int bi = 0x7fffffff;
-    if (wmode) {
-      for (int64_t j = gw; j < n; j += nw) {
-        double s2 = 0.0;
-        for (int64_t i = lane; i < m; i += 32) s2 += cabs2(A[j * m + i]);
-        s2 = warp_sum(s2);
-        if (lane == 0) { jb.nrm[j] = s2; jb.nref[j] = s2; }
-        if (better(s2, (int)j, best, bi)) { best = s2; bi = (int)j; }
-      }
-    } else {
-      for (int64_t j = lb; j < n; j += jb.nb) {
-        double s2 = 0.0;
-        for (int64_t i = tid; i < m; i += kNT) s2 += cabs2(A[j * m + i]);
-        s2 = block_sum<kNT>(s2, redv);
-        if (tid == 0) { jb.nrm[j] = s2; jb.nref[j] = s2; }
-        if (better(s2, (int)j, best, bi)) { best = s2; bi = (int)j; }
-      }
+    for (int64_t j = gw; j < n; j += nw) {
+      double s2 = 0.0;
+      for (int64_t i = lane; i < m; i += 32) s2 += cabs2(A[j * m + i]);
+      s2 = warp_sum(s2);
+      if (lane == 0) { jb.nrm[j] = s2; jb.nref[j] = s2; }
+      if (better(s2, (int)j, best, bi)) { best = s2; bi = (int)j; }
     }
     double v;
     int ix;
@@ -267,30 +218,16 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
       const cplx* vt = staged ? sv : ap + s + 1;
       double best = -1.0;
       int bi = 0x7fffffff;
-      if (wmode) {
-        for (int64_t j = gw; j < n; j += nw) {
-          const double nj = jb.nrm[j];
-          if (nj < 0.0) continue;  // an earlier pivot
-          if (j == p) {
-            if (lane == 0) jb.nrm[j] = -1.0;
-            continue;
-          }
-          const double t = update_col_warp(A + j * m, vt, m, s, v0, tau, nj, jb.nref + j, lane);
-          if (lane == 0) jb.nrm[j] = t;
-          if (better(t, (int)j, best, bi)) { best = t; bi = (int)j; }
+      for (int64_t j = gw; j < n; j += nw) {
+        const double nj = jb.nrm[j];
+        if (nj < 0.0) continue;  // an earlier pivot
+        if (j == p) {
+          if (lane == 0) jb.nrm[j] = -1.0;
+          continue;
         }
-      } else {
-        for (int64_t j = lb; j < n; j += jb.nb) {
-          const double nj = jb.nrm[j];
-          if (nj < 0.0) continue;
-          if (j == p) {
-            if (tid == 0) jb.nrm[j] = -1.0;
-            continue;
-          }
-          const double t = update_col_block(A + j * m, vt, m, s, v0, tau, nj, jb.nref + j, redv);
-          if (tid == 0) jb.nrm[j] = t;
-          if (better(t, (int)j, best, bi)) { best = t; bi = (int)j; }
-        }
+        const double t = update_col_warp(A + j * m, vt, m, s, v0, tau, nj, jb.nref + j, lane);
+        if (lane == 0) jb.nrm[j] = t;
+        if (better(t, (int)j, best, bi)) { best = t; bi = (int)j; }
       }
       double v;
       int ix;
@@ -345,7 +282,7 @@ __global__ void __launch_bounds__(kNT) k_pqr_tsolve(const PqrJob* jobs) {
   const PqrJob jb = jobs[blockIdx.y];
   const int k = jb.st->rank;
   const int64_t nc = jb.n - k;
-  if (k <= 0 || nc <= 0) return;
+  if (k <= 0 || nc <= 0 || jb.T == nullptr) return;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)kNT + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kNT) >> 5;
@@ -366,6 +303,105 @@ __global__ void __launch_bounds__(256) k_tsolve_cols(const cplx* R, int k, const
   for (int64_t c = warp; c < ncols; c += nwarps) tsolve_row_major(R, k, B + c * ldb, X + c * ldx, lane);
 }
 
+namespace {
+
+// X(:, c) = R^{-1} B(:, c) for upper-triangular R (k <= 32 KR) stored column-major
+// (Rc[i k + r] = R(r, i)) with its inverse diagonal: one warp per column, the column
+// held in registers (row r in lane r % 32, slot r / 32) and x_i broadcast by shuffle,
+// so the substitution never waits on memory.  X may alias B.
+template <int KR>
+__global__ void __launch_bounds__(256) k_tsolve_cols_reg(const cplx* Rc, const cplx* invd, int k, const cplx* B,
+                                                         int64_t ldb, int64_t ncols, cplx* X, int64_t ldx) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp; c < ncols; c += nwarps) {
+    const cplx* b = B + c * ldb;
+    cplx w[KR];
+#pragma unroll
+    for (int q = 0; q < KR; ++q) {
+      const int r = lane + 32 * q;
+      w[q] = r < k ? b[r] : cmk(0.0, 0.0);
+    }
+#pragma unroll
+    for (int qb = KR - 1; qb >= 0; --qb) {
+      for (int ii = 31; ii >= 0; --ii) {
+        const int i = qb * 32 + ii;
+        if (i >= k) continue;
+        cplx xi = cmk(__shfl_sync(0xffffffffu, w[qb].x, ii), __shfl_sync(0xffffffffu, w[qb].y, ii));
+        xi = cmul(xi, invd[i]);
+        if (lane == ii) w[qb] = xi;
+        const cplx* ri = Rc + (int64_t)i * k;
+#pragma unroll
+        for (int q = 0; q <= qb; ++q) {
+          const int r = lane + 32 * q;
+          if (r < i) w[q] = cfms(ri[r], xi, w[q]);
+        }
+      }
+    }
+    cplx* x = X + c * ldx;
+#pragma unroll
+    for (int q = 0; q < KR; ++q) {
+      const int r = lane + 32 * q;
+      if (r < k) x[r] = w[q];
+    }
+  }
+}
+
+// R11 column-major and 1/R_ii from a factorization.
+__global__ void k_r11_cols(const cplx* A, int64_t m, const int* piv, const cplx* beta, int k, cplx* Rc, cplx* invd) {
+  const int64_t tot = (int64_t)k * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % k), i = (int)(e / k);
+    cplx v = cmk(0.0, 0.0);
+    if (r == i) {
+      v = beta[i];
+      invd[i] = cdiv(cmk(1.0, 0.0), v);
+    } else if (r < i) {
+      v = A[(int64_t)piv[i] * m + r];
+    }
+    Rc[e] = v;
+  }
+}
+
+template <int KR>
+void launch_tsolve_reg(const cplx* Rc, const cplx* invd, int k, cplx* W, int64_t ldw, int64_t ncols, cudaStream_t s) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((ncols + 7) / 8, 152 * 16));
+  k_tsolve_cols_reg<KR><<<grid, 256, 0, s>>>(Rc, invd, k, W, ldw, ncols, W, ldw);
+}
+
+}  // namespace
+
+// W(:, c) <- R11^{-1} W(:, c) for the first k rows, R11 from matrix `job` of a pqr_run.
+void pqr_solve_r11(const cplx* A, int64_t m, const PqrOut& qr, int job, int k, cplx* W, int64_t ldw, int64_t ncols,
+                   cudaStream_t s) {
+  if (k <= 0 || ncols <= 0) return;
+  const int* piv = qr.piv.get() + qr.koff[job];
+  const cplx* beta = qr.beta.get() + qr.koff[job];
+  prof::KScope _ks("k_tsolve_cols", s, 4.0 * k * (double)k * ncols, 0.0);
+  if (k <= 256) {
+    DevBuf<cplx> Rc((size_t)k * k), invd(k);
+    k_r11_cols<<<std::max(1, std::min(4096, (k * k + 255) / 256)), 256, 0, s>>>(A, m, piv, beta, k, Rc.get(),
+                                                                                 invd.get());
+    switch ((k + 31) / 32) {
+      case 1: launch_tsolve_reg<1>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
+      case 2: launch_tsolve_reg<2>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
+      case 3: launch_tsolve_reg<3>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
+      case 4: launch_tsolve_reg<4>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
+      case 5: launch_tsolve_reg<5>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
+      case 6: launch_tsolve_reg<6>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
+      case 7: launch_tsolve_reg<7>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
+      default: launch_tsolve_reg<8>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
+    }
+  } else {
+    DevBuf<cplx> R((size_t)k * k);
+    k_r11_rows<<<std::max(1, std::min(4096, (k * k + 255) / 256)), 256, 0, s>>>(A, m, piv, beta, k, R.get());
+    k_tsolve_cols<<<(int)std::max<int64_t>(1, std::min<int64_t>((ncols + 7) / 8, 4096)), 256, 0, s>>>(
+        R.get(), k, W, ldw, ncols, W, ldw);
+  }
+  HBS_LAUNCH_CHECK("pqr_solve_r11");
+}
+
 // Column j of conj(Q1) (Q1 = first k columns of H_0 ... H_{k-1}):  q = H_0 ... H_j e_j.
 // One CTA per column; q lives in the output column.
 __global__ void __launch_bounds__(kNT) k_form_qc(const cplx* A, int64_t m, const int* piv, const cplx* v0,
@@ -384,8 +420,8 @@ __global__ void __launch_bounds__(kNT) k_form_qc(const cplx* A, int64_t m, const
     for (int64_t i = s + 1 + threadIdx.x; i < m; i += kNT) w = cfma(cconj(ap[i]), q[i], w);
     w = block_sum_c<kNT>(w, red);
     w = cscale(w, tau[s]);
-    if (threadIdx.x == 0) q[s] = csub(q[s], cmul(h0, w));
-    for (int64_t i = s + 1 + threadIdx.x; i < m; i += kNT) q[i] = csub(q[i], cmul(ap[i], w));
+    if (threadIdx.x == 0) q[s] = cfms(h0, w, q[s]);
+    for (int64_t i = s + 1 + threadIdx.x; i < m; i += kNT) q[i] = cfms(ap[i], w, q[i]);
     __syncthreads();
   }
   for (int64_t i = threadIdx.x; i < m; i += kNT) q[i] = cconj(q[i]);

@@ -287,8 +287,8 @@ __global__ void k_bq_update(cplx* A, int64_t m, int64_t n, int64_t s, double* nr
     }
     w = cfma(cconj(v0), cj[s], w);
     w = cscale(w, tau);
-    cplx top = csub(cj[s], cmul(v0, w));
-    for (int64_t i = s + 1 + lane; i < m; i += 32) cj[i] = csub(cj[i], cmul(cs[i], w));
+    cplx top = cfms(v0, w, cj[s]);
+    for (int64_t i = s + 1 + lane; i < m; i += 32) cj[i] = cfms(cs[i], w, cj[i]);
     double t = nrm[j] - cabs2(top);
     if (t <= 0.0078125 * nref[j]) {
       double q = 0.0;

@@ -50,6 +50,9 @@ struct PqrOut {
   DevBuf<double> tau;
 };
 void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrOut& out);
+// W(:, c) <- R11^{-1} W(:, c) (first k rows) with R11 of matrix `job` of a pqr_run on A (m rows).
+void pqr_solve_r11(const cplx* A, int64_t m, const PqrOut& qr, int job, int k, cplx* W, int64_t ldw, int64_t ncols,
+                   cudaStream_t s);
 // pgj.cu: in-place inverses of several large matrices (pointer, n) in one persistent
 // launch; throws HBS_WARN_ILLCOND on a singular block.
 void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, const char* what);

@@ -144,10 +144,9 @@ void build_periodizer(Handle& h, cudaStream_t s) {
                                cudaMemcpyDeviceToDevice, s));
     const int kcap = (int)std::min<int64_t>(std::min<int64_t>(m, nc), 4096);
     DevBuf<int> cperm(nc);
-    DevBuf<cplx> cT((size_t)kcap * nc);
     PqrOut qr;
     {
-      std::vector<PqrSpec> sp{{Mc.get(), m, nc, kcap, cperm.get(), cT.get()}};
+      std::vector<PqrSpec> sp{{Mc.get(), m, nc, kcap, cperm.get(), nullptr}};
       pqr_run(sp, h.tol, s, qr);
     }
     const int l = qr.rank[0];
@@ -166,25 +165,18 @@ void build_periodizer(Handle& h, cudaStream_t s) {
         k_fill_r<<<grid_1d((int64_t)l * N), 256, 0, s>>>(g, h.nb_skel.get(), l, d, h.Rm.get(), h.Rp.get());
       }
       HBS_LAUNCH_CHECK("k_fill_r");
-      DevBuf<cplx> Qc((size_t)m * l), R11((size_t)l * l), Tall((size_t)l * N);
+      DevBuf<cplx> Qc((size_t)m * l), Tall((size_t)l * N);
       {
         prof::KScope _ks("k_form_qc", s);
         k_form_qc<<<l, 256, 0, s>>>(Mc.get(), m, qr.piv.get(), qr.v0.get(), qr.tau.get(), l, Qc.get());
       }
-      {
-        prof::KScope _ks("k_r11_rows", s);
-        k_r11_rows<<<grid_1d((int64_t)l * l), 256, 0, s>>>(Mc.get(), m, qr.piv.get(), qr.beta.get(), l, R11.get());
-      }
-      HBS_LAUNCH_CHECK("neighbour Q1 / R11");
+      HBS_LAUNCH_CHECK("neighbour Q1");
       // Tall = Q1^H Mt (l x N), then R11^{-1} in place; skeleton nodes get unit columns.
       std::vector<GemmJob> gj(1);
       gj[0] = GemmJob{Qc.get(), Mt.get(), Tall.get(), l, (int)N, (int)m, (int)m, (int)m, l,
                       cmk(1.0, 0.0), cmk(0.0, 0.0), 0, 0, 0, 1};
       run_gemms(gj, s);
-      {
-        prof::KScope _ks("k_tsolve_cols", s);
-        k_tsolve_cols<<<grid_1d(N * 32, 256, 4096), 256, 0, s>>>(R11.get(), l, Tall.get(), l, N, Tall.get(), l);
-      }
+      pqr_solve_r11(Mc.get(), m, qr, 0, l, Tall.get(), l, N, s);
       {
         prof::KScope _ks("k_set_unit_cols", s);
         k_set_unit_cols<<<grid_1d((int64_t)l * l), 256, 0, s>>>(Tall.get(), l, h.nb_skel.get());
@@ -300,24 +292,50 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   const double ptol = std::min(0.1 * h.tol, 1e-13);
   const int nce = 12 * S;
   // IDs: returns rank, fills perm (host), T (device), and the check residual on the second subsample.
-  auto subsample_id = [&](int family, int ncols, std::vector<int>& hperm, DevBuf<cplx>& Tout) -> int {
-    DevBuf<cplx> A((size_t)ns * ncols), A2((size_t)ns * ncols);
+  // The three families' IDs run in one persistent QR launch; each is then checked on the
+  // second subsample (members rebuilt from the skeleton members).
+  struct Family {
+    int family, ncols;
+    DevBuf<cplx> A, A2, T;
+    DevBuf<int> perm;
+  };
+  Family fams[3];
+  fams[0].family = 0; fams[0].ncols = ny;
+  fams[1].family = 1; fams[1].ncols = ny;
+  fams[2].family = 2; fams[2].ncols = nce;
+  std::vector<PqrSpec> fspecs;
+  for (Family& f : fams) {
+    const int ncols = f.ncols;
+    f.A.alloc((size_t)ns * ncols);
+    f.A2.alloc((size_t)ns * ncols);
     {
       prof::KScope _ks("k_fill_family_sub", s);
-      k_fill_family_sub<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(g, cp, M, d, S, h.y0, family, dsub.get(), ns,
-                                                                      ncols, A.get(), ns);
-      k_fill_family_sub<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(g, cp, M, d, S, h.y0, family, dsub2.get(), ns,
-                                                                      ncols, A2.get(), ns);
+      k_fill_family_sub<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(g, cp, M, d, S, h.y0, f.family, dsub.get(), ns,
+                                                                      ncols, f.A.get(), ns);
+      k_fill_family_sub<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(g, cp, M, d, S, h.y0, f.family, dsub2.get(), ns,
+                                                                      ncols, f.A2.get(), ns);
     }
     HBS_LAUNCH_CHECK("k_fill_family_sub");
-    DevBuf<int> perm(ncols);
-    DevBuf<cplx> T((size_t)std::min(ns, ncols) * ncols);
-    int r = big_row_id(A.get(), ns, ncols, ptol, perm.get(), T.get(), std::min(ns, ncols), s);
-    hperm = perm.download(s);
+    f.perm.alloc(ncols);
+    f.T.alloc((size_t)std::min(ns, ncols) * ncols);
+    fspecs.push_back({f.A.get(), ns, ncols, std::min(ns, ncols), f.perm.get(), f.T.get()});
+  }
+  PqrOut fqr;
+  pqr_run(fspecs, ptol, s, fqr);
+  h.pid_residual = 0.0;
+  std::vector<int> fperm[3];
+  DevBuf<cplx>* Touts[3] = {&h.TY, &h.TC, &h.TE};
+  int franks[3];
+  for (int fi = 0; fi < 3; ++fi) {
+    Family& f = fams[fi];
+    const int ncols = f.ncols, r = fqr.rank[fi];
+    franks[fi] = r;
+    std::vector<int>& hperm = fperm[fi];
+    hperm = f.perm.download(s);
+    DevBuf<cplx>& Tout = *Touts[fi];
     Tout.alloc(std::max<int64_t>((int64_t)r * (ncols - r), 1));
     if ((int64_t)r * (ncols - r) > 0)
-      HBS_CUDA(cudaMemcpyAsync(Tout.get(), T.get(), sizeof(cplx) * r * (ncols - r), cudaMemcpyDeviceToDevice, s));
-    // check on the second subsample: members rebuilt from the skeleton members
+      HBS_CUDA(cudaMemcpyAsync(Tout.get(), f.T.get(), sizeof(cplx) * r * (ncols - r), cudaMemcpyDeviceToDevice, s));
     std::vector<int2> rec(ncols);
     std::vector<int> inv(ncols);
     for (int p = 0; p < ncols; ++p) inv[hperm[p]] = p;
@@ -329,25 +347,25 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     DevBuf<cplx> B2((size_t)ns * ncols);
     {
       prof::KScope _ks("k_expand_cols", s);
-      k_expand_cols<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(A2.get(), ns, ns, drec.get(), ncols, Tout.get(), r, 0,
-                                                                  dperm.get(), B2.get(), ns);
+      k_expand_cols<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(f.A2.get(), ns, ns, drec.get(), ncols, Tout.get(), r,
+                                                                  0, dperm.get(), B2.get(), ns);
     }
     DevBuf<double> acc(2);
     HBS_CUDA(cudaMemsetAsync(acc.get(), 0, 2 * sizeof(double), s));
     {
       prof::KScope _ks("k_diff_norm2", s);
-      k_diff_norm2<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(B2.get(), ns, A2.get(), ns, ns, ncols, acc.get());
+      k_diff_norm2<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(B2.get(), ns, f.A2.get(), ns, ns, ncols, acc.get());
     }
     auto ha = acc.download(s);
     const double res = ha[1] > 0 ? std::sqrt(ha[0] / ha[1]) : 0.0;
     h.pid_residual = std::max(h.pid_residual, res);
-    return r;
-  };
-  h.pid_residual = 0.0;
-  std::vector<int> permY, permC, permE;
-  h.rB = subsample_id(0, ny, permY, h.TY);
-  h.rC = subsample_id(1, ny, permC, h.TC);
-  h.rE = subsample_id(2, nce, permE, h.TE);
+  }
+  std::vector<int>& permY = fperm[0];
+  std::vector<int>& permC = fperm[1];
+  std::vector<int>& permE = fperm[2];
+  h.rB = franks[0];
+  h.rC = franks[1];
+  h.rE = franks[2];
   HBS_LAUNCH_CHECK("periodizer ids");
 
   // ---- source columns [P | Y(:, JY)] (not applied: Z is formed as V [P | Y_sel])
@@ -774,7 +792,7 @@ __global__ void __launch_bounds__(NT) k_schur_solve(Dims D, const GroupJob* grou
       for (int j = c + 1; j < k0 + nb; ++j) {
         cplx* aj = A + (int64_t)j * n;
         const cplx ucj = aj[c];
-        for (int i = c + 1 + tid; i < n; i += NT) aj[i] = csub(aj[i], cmul(ac[i], ucj));
+        for (int i = c + 1 + tid; i < n; i += NT) aj[i] = cfms(ac[i], ucj, aj[i]);
       }
       __syncthreads();
     }
@@ -793,7 +811,7 @@ __global__ void __launch_bounds__(NT) k_schur_solve(Dims D, const GroupJob* grou
 #pragma unroll
       for (int cc = 0; cc < NB; ++cc)
 #pragma unroll
-        for (int r = cc + 1; r < NB; ++r) u[r] = csub(u[r], cmul(L11[r][cc], u[cc]));
+        for (int r = cc + 1; r < NB; ++r) u[r] = cfms(L11[r][cc], u[cc], u[r]);
 #pragma unroll
       for (int r = 0; r < NB; ++r)
         if (r < nb) aj[r] = u[r];
@@ -1443,7 +1461,9 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
 
   // ---- process groups in batches
   const int nc = (int)h.contours.size();
-  const int64_t max_cols = plain ? 1024 : 512;
+  // Columns per batch of groups: the precomputed path keeps only rsel x cols
+  // projections per batch, so all groups of a typical call share one Schur launch.
+  const int64_t max_cols = plain ? 1024 : 8192;
   size_t gi = 0;
   while (gi < groups.size()) {
     std::vector<GroupJob> gjobs;

@@ -95,15 +95,6 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched(const GemmJob* job
 // double-float product is several times faster than DFMA while keeping relative
 // errors near 2^-48 per operation; results are written back in FP64.
 // ---------------------------------------------------------------------------
-struct df2 {
-  float h, l;
-};
-__device__ __forceinline__ df2 df_split(double x) {
-  df2 r;
-  r.h = __double2float_rn(x);
-  r.l = __double2float_rn(x - (double)r.h);
-  return r;
-}
 // acc += x * y   (double-float, lazy low part; renormalised by df_norm)
 // (explicit _rn intrinsics: the compiler may not contract these into FMAs, which would
 // break the error-free transformations)
@@ -128,6 +119,54 @@ struct dfc {
   float rh, rl, ih, il;
 };
 
+// Split of an FP64 value into a float pair (hi, lo) with integer operations only (the
+// FP64 conversion path shares the scarce FP64 pipe): hi carries the top 24 bits of the
+// significand, lo the remainder rounded to 24 bits, so hi + lo equals x to 2^-48
+// relative.  Values below the float range become 0.
+__device__ __forceinline__ void df_split_bits(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sgn = (unsigned int)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const int fe = e - 1023 + 127;
+  if (e == 0 || fe < 1) {
+    hi = __uint_as_float(sgn);
+    lo = __uint_as_float(sgn);
+    return;
+  }
+  if (fe > 254) {
+    hi = __uint_as_float(sgn | 0x7f800000u);
+    lo = 0.0f;
+    return;
+  }
+  hi = __uint_as_float(sgn | ((unsigned int)fe << 23) | (unsigned int)(m >> 29));
+  const unsigned int r = (unsigned int)(m & 0x1FFFFFFFull);  // remainder, r 2^(e-1075)
+  if (r == 0u) {
+    lo = 0.0f;
+    return;
+  }
+  const int lz = __clz(r) - 3;  // leading zeros within the 29-bit field
+  int fel = fe - 24 - lz;
+  const unsigned int rn = r << lz;  // leading one at bit 28
+  unsigned int q = (rn + 16u) >> 5;  // 24-bit significand, rounded to nearest
+  if (q >> 24) {
+    q >>= 1;
+    ++fel;
+  }
+  if (fel < 1) {
+    lo = 0.0f;
+    return;
+  }
+  lo = __uint_as_float(sgn | ((unsigned int)fel << 23) | (q & 0x7FFFFFu));
+}
+
+__device__ __forceinline__ dfc to_dfc_bits(cplx v) {
+  dfc r;
+  df_split_bits(v.x, r.rh, r.rl);
+  df_split_bits(v.y, r.ih, r.il);
+  return r;
+}
+
 static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* jobs, int njobs) {
   __shared__ dfc As[GBK][GBM + 1];
   __shared__ dfc Bs[GBK][GBN + 1];
@@ -149,12 +188,6 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* 
 #pragma unroll
     for (int b = 0; b < 2; ++b) acc[a][b] = {0.f, 0.f, 0.f, 0.f};
   const int m = jb.m, n = jb.n, K = jb.k;
-  auto to_dfc = [](cplx v) {
-    df2 re = df_split(v.x), im = df_split(v.y);
-    dfc r;
-    r.rh = re.h; r.rl = re.l; r.ih = im.h; r.il = im.l;
-    return r;
-  };
   for (int k0 = 0; k0 < K; k0 += GBK) {
     {
       cplx av;
@@ -168,10 +201,10 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* 
         int gr = row0 + r, gk = k0 + kk;
         av = (gr < m && gk < K) ? jb.A[(int64_t)gk * jb.lda + gr] : cmk(0.0, 0.0);
       }
-      As[kk][r] = to_dfc(av);
+      As[kk][r] = to_dfc_bits(av);
       int c = tid >> 3, kb = tid & 7;
       int gc = col0 + c, gkb = k0 + kb;
-      Bs[kb][c] = to_dfc((gc < n && gkb < K) ? jb.B[(int64_t)gc * jb.ldb + gkb] : cmk(0.0, 0.0));
+      Bs[kb][c] = to_dfc_bits((gc < n && gkb < K) ? jb.B[(int64_t)gc * jb.ldb + gkb] : cmk(0.0, 0.0));
     }
     __syncthreads();
 #pragma unroll
@@ -216,11 +249,11 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* 
 }
 
 // Host helper: fill tile bookkeeping and return the total tile count.
-inline int64_t gemm_plan(GemmJob* jobs, int njobs) {
+inline int64_t gemm_plan(GemmJob* jobs, int njobs, int bm = GBM, int bn = GBN) {
   int64_t tot = 0;
   for (int i = 0; i < njobs; ++i) {
-    jobs[i].tiles_m = (jobs[i].m + GBM - 1) / GBM;
-    jobs[i].tiles_n = (jobs[i].n + GBN - 1) / GBN;
+    jobs[i].tiles_m = (jobs[i].m + bm - 1) / bm;
+    jobs[i].tiles_n = (jobs[i].n + bn - 1) / bn;
     if (jobs[i].m <= 0 || jobs[i].n <= 0) { jobs[i].tiles_m = 0; jobs[i].tiles_n = 0; }
     jobs[i].tile_base = (int)tot;
     tot += (int64_t)jobs[i].tiles_m * jobs[i].tiles_n;
