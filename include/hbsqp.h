@@ -68,7 +68,7 @@ typedef struct hbs_options {
   double nb_radius;     /* neighbour proxy circle radius, Sec. 3.2 (0: automatic) */
   int nb_proxies;       /* neighbour proxy points (0: automatic) */
   int m;                /* Sommerfeld nodes per wall density type (0: automatic) */
-  double contour_h;     /* trapezoid spacing in Re k (0: automatic) */
+  double contour_h;     /* trapezoid spacing in Re k (0: automatic, 0.2) */
   double contour_c;     /* contour height c in k = t - i c tanh((t - t0)/w) (0: 2) */
   double contour_w;     /* contour width w (0: 2) */
   double contour_k;     /* truncation |Re k - t0| <= K (0: automatic) */
@@ -115,6 +115,19 @@ void hbs_default_options(hbs_options* opts);
  */
 hbs_status hbs_build(const hbs_geometry* geom, double omega, double tol, const hbs_options* opts,
                      void* stream, hbs_handle** out);
+
+/*
+ * The pre-computation of hbs_build for `count` independent solvers at once (gratings of
+ * different obstacles, sizes and frequencies; geoms[i] with omegas[i], one tol and one
+ * options struct for all).  The HBS compression and inversion run level-synchronously
+ * from the leaves: at every stage each kernel covers the current level of every solver
+ * in one launch.  Each out[i] is the same solver hbs_build would return for geoms[i]
+ * (up to the rounding of a different batch split) and is freed with hbs_free; its
+ * build_seconds is the time of the whole batch.  `out` has `count` entries.
+ * Errors: as hbs_build, for the first failing solver; on any error every out[i] is NULL.
+ */
+hbs_status hbs_build_batch(const hbs_geometry* geoms, const double* omegas, int64_t count, double tol,
+                           const hbs_options* opts, void* stream, hbs_handle** out);
 
 /*
  * Block solve (Sec. 3 and Sec. 6, second step) for incident angles
@@ -174,6 +187,50 @@ hbs_status hbs_info(const hbs_handle* h, hbs_info_t* info);
  */
 hbs_status hbs_save(const hbs_handle* h, const char* path, void* stream);
 hbs_status hbs_load(const char* path, void* stream, hbs_handle** out);
+
+/*
+ * Serving: built solvers kept resident and solved for a stream of requests.  The block
+ * solve (Sec. 6, second step) of one geometry handles any number of angles at once and
+ * groups them by Bloch phase (Remark 3.1); a server turns a stream of single-angle
+ * requests into such batches.  `slots` worker threads, each on its own CUDA stream of
+ * the device current at creation, take all requests queued for one geometry (up to
+ * `max_batch`) when they become free; requests arriving while other batches run join
+ * the next batch, so batches grow with the load and up to `slots` of them overlap on
+ * the device.  Results are those of hbs_solve for the same angles (to rounding).
+ *
+ * hbs_server_create: `hbm_budget_bytes` (0: no limit) bounds the device bytes of the
+ *   admitted geometries.  Errors: INVALID_ARG (slots outside 1..64, max_batch < 1),
+ *   CUDA (no device), OOM.
+ * hbs_server_add: admits a built handle (borrowed: it must outlive its membership) and
+ *   returns its geometry id; OOM if its hbs_info device_bytes do not fit the budget.
+ * hbs_server_remove: waits until no queued or running request refers to the geometry,
+ *   then releases its share of the budget.
+ * hbs_server_submit: queues one angle theta in (-pi, 0) for a geometry; returns at once
+ *   with a request id.  Thread-safe.
+ * hbs_server_wait: waits up to timeout_s seconds for a request and hands over its result
+ *   (one angle; read it with hbs_bragg_amplitudes(res, 0, ...), free with
+ *   hbs_result_free).  Each request can be waited for once.  Errors: TIMEOUT (not
+ *   finished yet; the request stays pending), or the solve's own status.
+ * hbs_server_stats: counts, per-request latency percentiles (submit to completion) and
+ *   completed requests per second since the first submission.
+ * hbs_server_free: finishes every queued request, stops the workers and frees the server
+ *   (not the admitted handles).
+ */
+typedef struct hbs_server hbs_server;
+typedef struct hbs_server_stats_t {
+  int64_t submitted, completed, batches;
+  double mean_batch;      /* requests per solve call */
+  double p50_latency_s, p99_latency_s, max_latency_s;
+  double solves_per_s;
+  size_t resident_bytes;  /* device bytes of the admitted geometries */
+} hbs_server_stats_t;
+hbs_status hbs_server_create(size_t hbm_budget_bytes, int slots, int max_batch, hbs_server** out);
+hbs_status hbs_server_add(hbs_server* sv, const hbs_handle* h, int64_t* geometry_id);
+hbs_status hbs_server_remove(hbs_server* sv, int64_t geometry_id);
+hbs_status hbs_server_submit(hbs_server* sv, int64_t geometry_id, double theta, int64_t* request_id);
+hbs_status hbs_server_wait(hbs_server* sv, int64_t request_id, double timeout_s, hbs_result** out);
+hbs_status hbs_server_stats(hbs_server* sv, hbs_server_stats_t* st);
+void hbs_server_free(hbs_server* sv);
 
 /*
  * x = A^{-1} b with the compressed inverse (Sec. 4, telescoping apply),

@@ -287,9 +287,15 @@ def kappa_n(omega, d, theta, n):
 
 
 def k_n(omega, kappa):
-    """k_n = +sqrt(omega^2 - kappa_n^2), non-negative real or positive imaginary."""
+    """k_n = +sqrt(omega^2 - kappa_n^2), non-negative real or positive imaginary.  An order
+    within rounding of a Rayleigh-Wood anomaly, |omega^2 - kappa_n^2| <= 1e-12 omega^2, is
+    taken at the anomaly (k_n = 0): an angle given as the anomaly in FP64 is only that close
+    to it, and the amplitudes have a square-root singularity in the angle there (reading of
+    Sec. 2.4 for exact anomalies)."""
     kappa = np.asarray(kappa, dtype=np.complex128)
-    return np.sqrt(omega * omega - kappa * kappa)
+    v = omega * omega - kappa * kappa
+    v = np.where(np.abs(v) <= 1e-12 * omega * omega, 0.0, v)
+    return np.sqrt(v)
 
 
 def mode_range(omega, d, theta, extra: int = 0):

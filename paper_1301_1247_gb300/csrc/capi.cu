@@ -129,10 +129,9 @@ void hbs_default_options(hbs_options* o) {
   o->precision = HBS_PRECISION_FP64;
 }
 
-hbs_status hbs_build(const hbs_geometry* geom, double omega, double tol, const hbs_options* opts, void* stream,
-                     hbs_handle** out) {
-  if (!out) { set_last_error("out is NULL"); return HBS_ERR_INVALID_ARG; }
-  *out = nullptr;
+namespace {
+
+hbs_status check_build_args(const hbs_geometry* geom, double omega, double tol) {
   if (!geom || !geom->x || !geom->y || !geom->dx || !geom->dy) {
     set_last_error("geometry arrays are NULL");
     return HBS_ERR_INVALID_ARG;
@@ -141,6 +140,33 @@ hbs_status hbs_build(const hbs_geometry* geom, double omega, double tol, const h
     set_last_error("need n >= 64, d > 0, omega > 0, 0 < tol < 1");
     return HBS_ERR_INVALID_ARG;
   }
+  return HBS_OK;
+}
+
+// Options, geometry and the wall check of one solver (before its tree is built).
+void prepare_handle(Handle& h, const hbs_geometry* geom, double omega, double tol, const hbs_options* opts,
+                    cudaStream_t s) {
+  hbs_default_options(&h.opts);
+  if (opts) h.opts = *opts;
+  if (h.opts.leaf_size < 8) h.opts.leaf_size = 64;
+  if (h.opts.n_proxy_min < 8) h.opts.n_proxy_min = 64;
+  if (!(h.opts.proxy_rho > 1.0)) h.opts.proxy_rho = 1.5;
+  if (h.opts.precision != HBS_PRECISION_FP64 && h.opts.precision != HBS_PRECISION_DOUBLE_FLOAT)
+    throw Error(HBS_ERR_INVALID_ARG, "unsupported precision mode");
+  h.omega = omega;
+  h.tol = tol;
+  load_geometry(h, geom, s);
+  for (int64_t i = 0; i < h.N; ++i)
+    if (!(std::fabs(h.hx[i]) < 0.5 * h.d)) throw Error(HBS_ERR_INVALID_ARG, "obstacle touches a unit-cell wall");
+}
+
+}  // namespace
+
+hbs_status hbs_build(const hbs_geometry* geom, double omega, double tol, const hbs_options* opts, void* stream,
+                     hbs_handle** out) {
+  if (!out) { set_last_error("out is NULL"); return HBS_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (hbs_status st = check_build_args(geom, omega, tol)) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   StreamScope scope(s);
   hbs_handle* hh = new (std::nothrow) hbs_handle();
@@ -148,19 +174,8 @@ hbs_status hbs_build(const hbs_geometry* geom, double omega, double tol, const h
   hbs_status st = guarded([&] {
     Handle& h = hh->h;
     auto t0 = std::chrono::steady_clock::now();
-    hbs_default_options(&h.opts);
-    if (opts) h.opts = *opts;
-    if (h.opts.leaf_size < 8) h.opts.leaf_size = 64;
-    if (h.opts.n_proxy_min < 8) h.opts.n_proxy_min = 64;
-    if (!(h.opts.proxy_rho > 1.0)) h.opts.proxy_rho = 1.5;
-    if (h.opts.precision != HBS_PRECISION_FP64 && h.opts.precision != HBS_PRECISION_DOUBLE_FLOAT)
-      throw Error(HBS_ERR_INVALID_ARG, "unsupported precision mode");
+    prepare_handle(h, geom, omega, tol, opts, s);
     GemmModeScope gm(h.opts.precision == HBS_PRECISION_DOUBLE_FLOAT);
-    h.omega = omega;
-    h.tol = tol;
-    load_geometry(h, geom, s);
-    for (int64_t i = 0; i < h.N; ++i)
-      if (!(std::fabs(h.hx[i]) < 0.5 * h.d)) throw Error(HBS_ERR_INVALID_ARG, "obstacle touches a unit-cell wall");
     {
       prof::Phase ph("build:hbs_compress_invert", s);
       build_hbs(h, s);
@@ -174,6 +189,51 @@ hbs_status hbs_build(const hbs_geometry* geom, double omega, double tol, const h
     return st;
   }
   *out = hh;
+  return HBS_OK;
+}
+
+hbs_status hbs_build_batch(const hbs_geometry* geoms, const double* omegas, int64_t count, double tol,
+                           const hbs_options* opts, void* stream, hbs_handle** out) {
+  if (!out || !geoms || !omegas || count <= 0) {
+    set_last_error("bad arguments to hbs_build_batch");
+    return HBS_ERR_INVALID_ARG;
+  }
+  for (int64_t i = 0; i < count; ++i) out[i] = nullptr;
+  for (int64_t i = 0; i < count; ++i)
+    if (hbs_status st = check_build_args(geoms + i, omegas[i], tol)) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScope scope(s);
+  std::vector<hbs_handle*> hh(count, nullptr);
+  for (int64_t i = 0; i < count; ++i) {
+    hh[i] = new (std::nothrow) hbs_handle();
+    if (!hh[i]) {
+      for (auto* p : hh) delete p;
+      set_last_error("host allocation failed");
+      return HBS_ERR_OOM;
+    }
+  }
+  hbs_status st = guarded([&] {
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<Handle*> hs(count);
+    for (int64_t i = 0; i < count; ++i) {
+      hs[i] = &hh[i]->h;
+      prepare_handle(*hs[i], geoms + i, omegas[i], tol, opts, s);
+    }
+    GemmModeScope gm(hs[0]->opts.precision == HBS_PRECISION_DOUBLE_FLOAT);
+    {
+      prof::Phase ph("build:hbs_compress_invert", s);
+      build_hbs_multi(hs, s);
+    }
+    for (Handle* h : hs) build_periodizer(*h, s);
+    HBS_CUDA(cudaStreamSynchronize(s));
+    const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (Handle* h : hs) h->build_seconds = sec;
+  });
+  if (st != HBS_OK) {
+    for (auto* p : hh) delete p;
+    return st;
+  }
+  for (int64_t i = 0; i < count; ++i) out[i] = hh[i];
   return HBS_OK;
 }
 
@@ -310,8 +370,8 @@ hbs_status hbs_row_id(void* mt, int64_t m, int64_t n, double tol, int* rank, int
   return guarded([&] {
     if (n <= 4096) {
       std::vector<CpqrJob> jobs(1);
-      jobs[0] = {0, 0, 0, (int)m, (int)n, 0};
-      auto r = batched_id(jobs, static_cast<cplx*>(mt), static_cast<cplx*>(t), perm, tol, s);
+      jobs[0] = {static_cast<cplx*>(mt), static_cast<cplx*>(t), perm, (int)m, (int)n, 0};
+      auto r = batched_id(jobs, tol, s);
       *rank = r[0];
     } else {
       *rank = big_row_id(static_cast<cplx*>(mt), m, n, tol, perm, static_cast<cplx*>(t),

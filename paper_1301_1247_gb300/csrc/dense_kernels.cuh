@@ -8,18 +8,19 @@
 
 namespace hbs {
 
-// Descriptor of one matrix of a batch.
+// Descriptor of one matrix of a batch (pointers into any device buffers, so a batch may
+// span several solvers).
 struct CpqrJob {
-  int64_t mt_off;  // offset (in cplx) of Mt (m x n, ld = m)
-  int64_t t_off;   // offset of T output (k x (n - k), ld = k; capacity min(m,n) * n)
-  int64_t perm_off;  // offset of perm output (n ints)
+  cplx* mt;    // Mt (m x n, ld = m), overwritten
+  cplx* t;     // T output (k x (n - k), ld = k; capacity min(m,n) * n)
+  int* perm;   // perm output (n ints)
   int m, n;
-  int job;         // index into the rank output array
+  int job;     // index into the rank output array
 };
 
 struct InvJob {
-  int64_t a_off;   // matrix (n x n, ld = n), inverted in place
-  int64_t piv_off; // int scratch (n)
+  cplx* a;     // matrix (n x n, ld = n), inverted in place
+  int* piv;    // int scratch (n), set by the launcher
   int n;
   int job;
 };
@@ -82,8 +83,7 @@ __device__ __forceinline__ void block_argmax(double v, int idx, double* redv, in
 // Dynamic shared memory: 2 n doubles + n ints.
 // ---------------------------------------------------------------------------
 template <int NT>
-__global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, cplx* pool, cplx* tpool, int* permpool,
-                                             int* rank_out, double tol, int kmax) {
+__global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, int* rank_out, double tol, int kmax) {
   extern __shared__ double smem[];
   __shared__ double redv[32];
   __shared__ int redi[32];
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, cplx* pool, cp
 
   const CpqrJob jb = jobs[blockIdx.x];
   const int m = jb.m, n = jb.n;
-  cplx* A = pool + jb.mt_off;
+  cplx* A = jb.mt;
   double* nrm = smem;          // current squared norms of the trailing parts
   double* nrm_ref = smem + n;  // reference norms for the cancellation test
   int* perm = reinterpret_cast<int*>(smem + 2 * n);
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, cplx* pool, cp
   }
   // T = R11^{-1} R12, one warp per column of R12
   const int k = rank;
-  cplx* T = tpool + jb.t_off;
+  cplx* T = jb.t;
   for (int c = warp; c < n - k; c += NW) {
     const cplx* r12 = A + (int64_t)(k + c) * m;
     cplx* tc = T + (int64_t)c * k;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, cplx* pool, cp
       __syncwarp();
     }
   }
-  int* po = permpool + jb.perm_off;
+  int* po = jb.perm;
   for (int j = tid; j < n; j += NT) po[j] = perm[j];
   if (tid == 0) rank_out[jb.job] = k;
 }
@@ -215,14 +215,14 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, cplx* pool, cp
 // rank_out[job] receives 0 on success, or 1 if a zero pivot was met.
 // ---------------------------------------------------------------------------
 template <int NT>
-__global__ void __launch_bounds__(NT) k_gj_inverse(const InvJob* jobs, cplx* pool, int* ipool, int* flag_out) {
+__global__ void __launch_bounds__(NT) k_gj_inverse(const InvJob* jobs, int* flag_out) {
   __shared__ double redv[32];
   __shared__ int redi[32];
   __shared__ cplx sh_piv;
   const InvJob jb = jobs[blockIdx.x];
   const int n = jb.n;
-  cplx* A = pool + jb.a_off;
-  int* piv = ipool + jb.piv_off;
+  cplx* A = jb.a;
+  int* piv = jb.piv;
   const int tid = threadIdx.x;
   int bad = 0;
   for (int c = 0; c < n; ++c) {

@@ -46,13 +46,22 @@ __global__ void k_geom(const double* dx, const double* dy, double* nx, double* n
 
 __device__ __forceinline__ int64_t node_lo(int64_t j, int l, int64_t N) { return (j * N) >> l; }
 
-// Enclosing circle of the original points of each node on level l: centre of the
+// One node of one solver's level: its original points [lo, hi) and where its circle goes.
+struct CircleJob {
+  const double* x;
+  const double* y;
+  int64_t lo, hi;
+  double* out;  // cx, cy, radius
+};
+
+// Enclosing circle of the original points of each node (one block per job): centre of the
 // bounding box, radius = largest distance from it.
-__global__ void k_node_circles(const double* x, const double* y, int64_t N, int l, double* cx, double* cy,
-                               double* rad) {
+__global__ void k_node_circles(const CircleJob* jobs) {
   __shared__ double red[32];
-  const int64_t j = blockIdx.x;
-  const int64_t lo = node_lo(j, l, N), hi = node_lo(j + 1, l, N);
+  const CircleJob jb = jobs[blockIdx.x];
+  const double* x = jb.x;
+  const double* y = jb.y;
+  const int64_t lo = jb.lo, hi = jb.hi;
   double mnx = 1e300, mxx = -1e300, mny = 1e300, mxy = -1e300;
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     mnx = fmin(mnx, x[i]); mxx = fmax(mxx, x[i]);
@@ -86,36 +95,43 @@ __global__ void k_node_circles(const double* x, const double* y, int64_t N, int 
   if (threadIdx.x == 0) {
     double r = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red[w]);
-    cx[j] = ccx;
-    cy[j] = ccy;
-    rad[j] = sqrt(r);
+    jb.out[0] = ccx;
+    jb.out[1] = ccy;
+    jb.out[2] = sqrt(r);
   }
 }
 
-// Near lists: active points of other nodes of the level inside node tau's proxy circle.
-// One block per node scans the level's active points in order, so the list order is
-// deterministic.  With `out` == nullptr only the count is produced.
-__global__ void k_near(const double* x, const double* y, const int64_t* idx, int64_t ntot, const int64_t* off,
-                       const int* nn, const double* cx, const double* cy, const double* rad, double rho,
-                       int64_t* count, const int64_t* out_off, int64_t* out) {
+// Near lists: active points of other nodes of the level (same solver) inside a node's
+// proxy circle.  One block per node scans the level's active points in order, so the list
+// order is deterministic.  With `out` == nullptr only the count is produced.
+struct NearJob {
+  const double* x;
+  const double* y;
+  const int64_t* idx;      // the level's active points
+  int64_t ntot;
+  int64_t own_lo, own_hi;  // this node's range in idx
+  double cx, cy, R2;
+  int64_t* count;          // one element
+  int64_t* out;            // the node's near list, or nullptr
+};
+
+__global__ void k_near(const NearJob* jobs) {
   __shared__ int wsum[32];
   __shared__ int64_t base;
-  const int tau = blockIdx.x;
-  const int64_t own_lo = off[tau], own_hi = off[tau] + nn[tau];
-  const double R = rho * rad[tau], R2 = R * R, ccx = cx[tau], ccy = cy[tau];
+  const NearJob jb = jobs[blockIdx.x];
   if (threadIdx.x == 0) base = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t p0 = 0; p0 < ntot; p0 += blockDim.x) {
-    int64_t p = p0 + threadIdx.x;
+  for (int64_t p0 = 0; p0 < jb.ntot; p0 += blockDim.x) {
+    const int64_t p = p0 + threadIdx.x;
     bool f = false;
     int64_t g = 0;
-    if (p < ntot && (p < own_lo || p >= own_hi)) {
-      g = idx[p];
-      double ddx = x[g] - ccx, ddy = y[g] - ccy;
-      f = ddx * ddx + ddy * ddy < R2;
+    if (p < jb.ntot && (p < jb.own_lo || p >= jb.own_hi)) {
+      g = jb.idx[p];
+      const double ddx = jb.x[g] - jb.cx, ddy = jb.y[g] - jb.cy;
+      f = ddx * ddx + ddy * ddy < jb.R2;
     }
-    unsigned b = __ballot_sync(0xffffffffu, f);
+    const unsigned b = __ballot_sync(0xffffffffu, f);
     if (lane == 0) wsum[warp] = __popc(b);
     __syncthreads();
     int before = 0, total = 0;
@@ -123,18 +139,19 @@ __global__ void k_near(const double* x, const double* y, const int64_t* idx, int
       if (w < warp) before += wsum[w];
       total += wsum[w];
     }
-    if (f && out) out[out_off[tau] + base + before + __popc(b & ((1u << lane) - 1u))] = g;
+    if (f && jb.out) jb.out[base + before + __popc(b & ((1u << lane) - 1u))] = g;
     __syncthreads();
     if (threadIdx.x == 0) base += total;
     __syncthreads();
   }
-  if (threadIdx.x == 0) count[tau] = base;
+  if (threadIdx.x == 0) *jb.count = base;
 }
 
 struct YJob {
-  int64_t mt_off;    // into the Y pool
-  int64_t idx_off;   // into level idx
-  int64_t near_off;  // into near list
+  DevGeom g;           // the solver's geometry
+  const int64_t* idx;  // the node's active points (n)
+  const int64_t* near; // the node's near list (nn)
+  cplx* mt;            // output Mt (m x n, m = 2 nn + 2 np)
   int n, nn, np;
   double cx, cy, R, wp;
 };
@@ -147,18 +164,19 @@ struct YJob {
 // Entries come in pairs that share one Hankel evaluation: A(near_r, j) and A(j, near_r)
 // (rows r and nn + r), and the combined-layer proxy row and the field-at-proxy column of
 // proxy p (rows 2nn + p and 2nn + np + p) -- each pair has a single distance |x - y|.
-__global__ void k_fill_y(DevGeom g, const YJob* jobs, const int64_t* idx, const int64_t* near, cplx* pool) {
+__global__ void k_fill_y(const YJob* jobs) {
   const YJob jb = jobs[blockIdx.y];
+  const DevGeom& g = jb.g;
   const int m = 2 * jb.nn + 2 * jb.np;
   const int half = jb.nn + jb.np;
   const int64_t tot = (int64_t)half * jb.n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(e % half), c = (int)(e / half);
-    const int64_t gj = idx[jb.idx_off + c];
-    cplx* col = pool + jb.mt_off + (int64_t)c * m;
+    const int64_t gj = jb.idx[c];
+    cplx* col = jb.mt + (int64_t)c * m;
     const double xj = g.x[gj], yj = g.y[gj];
     if (r < jb.nn) {
-      const int64_t gi = near[jb.near_off + r];
+      const int64_t gi = jb.near[r];
       cplx v1, v2;
       if (gi == gj) {
         v1 = v2 = cmk(0.5, 0.0);
@@ -196,31 +214,34 @@ __global__ void k_fill_y(DevGeom g, const YJob* jobs, const int64_t* idx, const 
 }
 
 struct DJob {
-  int64_t d_off;      // into D pool (n x n)
-  int64_t idx_off;    // level idx offset of the node
-  int n, k0;          // node size; first child's skeleton size (0 for leaves)
+  DevGeom g;           // the solver's geometry
+  const int64_t* idx;  // the node's active points (n)
+  cplx* d;             // output (n x n)
+  int n, k0;           // node size; first child's skeleton size (0 for leaves)
   int leaf;
-  const cplx* dh0;    // children's Dhat (k0 x k0, k1 x k1)
+  const cplx* dh0;     // children's Dhat (k0 x k0, k1 x k1)
   const cplx* dh1;
 };
 
-__global__ void k_fill_d(DevGeom g, const DJob* jobs, const int64_t* idx, cplx* pool) {
+__global__ void k_fill_d(const DJob* jobs) {
   const DJob jb = jobs[blockIdx.y];
+  const DevGeom& g = jb.g;
+  const int64_t* idx = jb.idx;
   const int n = jb.n;
   const int64_t tot = (int64_t)n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(e % n), c = (int)(e / n);
     cplx v;
     if (jb.leaf) {
-      v = a_entry(g, idx[jb.idx_off + r], idx[jb.idx_off + c]);
+      v = a_entry(g, idx[r], idx[c]);
     } else {
       const int k0 = jb.k0, k1 = n - k0;
       const bool r0 = r < k0, c0 = c < k0;
       if (r0 && c0) v = jb.dh0[(int64_t)c * k0 + r];
       else if (!r0 && !c0) v = jb.dh1[(int64_t)(c - k0) * k1 + (r - k0)];
-      else v = a_entry(g, idx[jb.idx_off + r], idx[jb.idx_off + c]);
+      else v = a_entry(g, idx[r], idx[c]);
     }
-    pool[jb.d_off + e] = v;
+    jb.d[e] = v;
   }
 }
 
@@ -262,13 +283,14 @@ __global__ void k_left_pt(const PJob* jobs) {
 
 // Parent index sets from the children's skeletons: idx_p = [idx_a(perm_a[0..k_a)), idx_b(perm_b[0..k_b))].
 struct GatherJob {
-  int64_t src_off, dst_off;
+  const int64_t* src_idx;  // the child's active points
+  const int* src_perm;     // the child's pivot order
+  int64_t* dst;
   int k;
 };
-__global__ void k_gather_skel(const GatherJob* jobs, const int64_t* src_idx, const int* src_perm, int64_t* dst_idx) {
+__global__ void k_gather_skel(const GatherJob* jobs) {
   const GatherJob jb = jobs[blockIdx.y];
-  for (int i = threadIdx.x; i < jb.k; i += blockDim.x)
-    dst_idx[jb.dst_off + i] = src_idx[jb.src_off + src_perm[jb.src_off + i]];
+  for (int i = threadIdx.x; i < jb.k; i += blockDim.x) jb.dst[i] = jb.src_idx[jb.src_perm[i]];
 }
 
 // ---------------------------------------------------------------------------
@@ -398,11 +420,10 @@ DevGeom Handle_geom(const Handle& h) {
 static bool big_cpqr(const CpqrJob& j) { return (double)j.m * j.n * std::min(j.m, j.n) > 4e6; }
 static bool big_inverse(int n) { return n > 128; }
 
-// Batched CPQR-ID of the matrices described by `jobs` (in `pool`).  Returns ranks.
+// Batched CPQR-ID of the matrices described by `jobs`.  Returns ranks.
 // Small matrices go to one launch with one CTA each; large ones (the top tree levels,
 // where a level has few nodes) share one persistent launch on all SMs (pqr.cu).
-std::vector<int> batched_id(std::vector<CpqrJob>& jobs, cplx* pool, cplx* tpool, int* permpool, double tol,
-                            cudaStream_t s) {
+std::vector<int> batched_id(std::vector<CpqrJob>& jobs, double tol, cudaStream_t s) {
   std::vector<int> ranks(jobs.size(), 0);
   if (jobs.empty()) return ranks;
   std::vector<CpqrJob> small;
@@ -434,7 +455,7 @@ std::vector<int> batched_id(std::vector<CpqrJob>& jobs, cplx* pool, cplx* tpool,
       HBS_CUDA(cudaFuncSetAttribute(k_cpqr<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     {
       prof::KScope _ks("k_cpqr", s);
-      k_cpqr<256><<<(unsigned)small.size(), 256, sm, s>>>(dj.get(), pool, tpool, permpool, dr.get(), tol, 1 << 30);
+      k_cpqr<256><<<(unsigned)small.size(), 256, sm, s>>>(dj.get(), dr.get(), tol, 1 << 30);
     }
     HBS_LAUNCH_CHECK("k_cpqr");
     auto r = dr.download(s);
@@ -444,7 +465,7 @@ std::vector<int> batched_id(std::vector<CpqrJob>& jobs, cplx* pool, cplx* tpool,
     std::vector<BigQrJobSpec> specs;
     for (size_t i : big_idx) {
       const CpqrJob& j = jobs[i];
-      specs.push_back({pool + j.mt_off, j.m, j.n, permpool + j.perm_off, tpool + j.t_off});
+      specs.push_back({j.mt, j.m, j.n, j.perm, j.t});
     }
     auto r = big_row_id_batched(specs, tol, s);
     for (size_t t = 0; t < big_idx.size(); ++t) ranks[big_idx[t]] = r[t];
@@ -459,7 +480,7 @@ std::vector<int> batched_id(std::vector<CpqrJob>& jobs, cplx* pool, cplx* tpool,
 }
 
 // Batched in-place inverses; throws on a singular block.
-void batched_inverse(std::vector<InvJob>& jobs_in, cplx* pool, cudaStream_t s, const char* what) {
+void batched_inverse(std::vector<InvJob>& jobs_in, cudaStream_t s, const char* what) {
   std::vector<InvJob> jobs;
   std::vector<std::pair<cplx*, int>> big;
   // Same split as for the IDs: at most 128 blocks all go to the persistent multi-CTA
@@ -470,22 +491,24 @@ void batched_inverse(std::vector<InvJob>& jobs_in, cplx* pool, cudaStream_t s, c
   const bool all_big = jobs_in.size() <= 128;
   const bool use_big = all_big || (nbig > 0 && nbig <= 128);
   for (auto& j : jobs_in) {
-    if (use_big && (all_big || big_inverse(j.n))) big.push_back({pool + j.a_off, j.n});
+    if (use_big && (all_big || big_inverse(j.n))) big.push_back({j.a, j.n});
     else jobs.push_back(j);
   }
   pgj_run(big, s, what);
   if (jobs.empty()) return;
   for (size_t i = 0; i < jobs.size(); ++i) jobs[i].job = (int)i;
   int64_t piv = 0;
-  for (auto& j : jobs) { j.piv_off = piv; piv += j.n; }
+  for (auto& j : jobs) piv += j.n;
   DevBuf<int> dpiv(std::max<int64_t>(piv, 1));
+  piv = 0;
+  for (auto& j : jobs) { j.piv = dpiv.get() + piv; piv += j.n; }
   DevBuf<InvJob> dj = upload_jobs(jobs, s);
   DevBuf<int> flags(jobs.size());
   double fl = 0.0;
   for (auto& j : jobs) fl += 8.0 * (double)j.n * j.n * j.n;
   {
     prof::KScope _ks("k_gj_inverse", s, fl, 0.0);
-    k_gj_inverse<256><<<(unsigned)jobs.size(), 256, 0, s>>>(dj.get(), pool, dpiv.get(), flags.get());
+    k_gj_inverse<256><<<(unsigned)jobs.size(), 256, 0, s>>>(dj.get(), flags.get());
   }
   HBS_LAUNCH_CHECK("k_gj_inverse");
   auto f = flags.download(s);
@@ -493,227 +516,337 @@ void batched_inverse(std::vector<InvJob>& jobs_in, cplx* pool, cudaStream_t s, c
     if (v) throw Error(HBS_WARN_ILLCOND, std::string("singular block in ") + what);
 }
 
-void build_hbs(Handle& h, cudaStream_t s) {
-  const int64_t N = h.N;
-  const DevGeom g = Handle_geom(h);
-  const double rho = h.opts.proxy_rho;
-  int L = 0;
-  while ((N >> L) > h.opts.leaf_size || ((N + (1LL << L) - 1) >> L) > h.opts.leaf_size) ++L;
-  if (L < 1) L = 1;
-  h.L = L;
-  h.levels.clear();
-  h.levels.resize(L + 1);
-  h.max_rank = 0;
-  h.factor_bytes = 0.0;
-  h.apply_flops = 0.0;
+// Launches a per-job kernel whose job index is blockIdx.y, in chunks that respect the
+// 65535 limit of gridDim.y.
+template <typename J, typename F>
+static void launch_jobs_y(const DevBuf<J>& dj, size_t njobs, F&& launch) {
+  for (size_t j0 = 0; j0 < njobs; j0 += 65535)
+    launch(dj.get() + j0, (unsigned)std::min<size_t>(65535, njobs - j0));
+}
 
+// One level of one solver processed in a stage of the (multi-solver) build.
+struct LevelTask {
+  Handle* h;
+  int l;
+  DevGeom g;
+};
+
+// HBS compression and inversion of several solvers at once.  Stage t processes level
+// L_i - t of every solver i (leaves first, each tree's root last), and every kernel of a
+// stage covers all nodes of all its solvers' levels: one launch per kernel and stage,
+// whatever the number of solvers.
+void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s) {
+  int Lmax = 0;
+  for (Handle* hp : hs) {
+    Handle& h = *hp;
+    int L = 0;
+    while ((h.N >> L) > h.opts.leaf_size || ((h.N + (1LL << L) - 1) >> L) > h.opts.leaf_size) ++L;
+    if (L < 1) L = 1;
+    h.L = L;
+    h.levels.clear();
+    h.levels.resize(L + 1);
+    h.max_rank = 0;
+    h.factor_bytes = 0.0;
+    h.apply_flops = 0.0;
+    Lmax = std::max(Lmax, L);
+  }
   static const char* kLevelNames[] = {
       "build:level_00", "build:level_01", "build:level_02", "build:level_03", "build:level_04", "build:level_05",
       "build:level_06", "build:level_07", "build:level_08", "build:level_09", "build:level_10", "build:level_11",
       "build:level_12", "build:level_13", "build:level_14", "build:level_15", "build:level_16", "build:level_17",
       "build:level_18", "build:level_19", "build:level_20", "build:level_21", "build:level_22", "build:level_23"};
-  for (int l = L; l >= 0; --l) {
-    prof::Phase ph_level(kLevelNames[std::min(l, 23)], s);
-    Level& lv = h.levels[l];
-    lv.l = l;
-    lv.count = 1 << l;
-    lv.first = (1 << l) - 1;
-    lv.n.assign(lv.count, 0);
-    lv.off.assign(lv.count, 0);
-    // ---- index sets
-    if (l == L) {
-      for (int j = 0; j < lv.count; ++j) {
-        int64_t lo = ((int64_t)j * N) >> l, hi = ((int64_t)(j + 1) * N) >> l;
-        lv.n[j] = (int)(hi - lo);
-        lv.off[j] = lo;
-      }
-      lv.ntot = N;
-      std::vector<int64_t> hidx(N);
-      std::iota(hidx.begin(), hidx.end(), 0);
-      lv.idx.upload(hidx, s);
-    } else {
-      Level& ch = h.levels[l + 1];
-      int64_t o = 0;
-      std::vector<GatherJob> gj;
-      for (int j = 0; j < lv.count; ++j) {
-        int a = 2 * j, b = 2 * j + 1;
-        lv.off[j] = o;
-        lv.n[j] = ch.k[a] + ch.k[b];
-        gj.push_back({ch.off[a], o, ch.k[a]});
-        gj.push_back({ch.off[b], o + ch.k[a], ch.k[b]});
-        o += lv.n[j];
-      }
-      lv.ntot = o;
-      lv.idx.alloc(std::max<int64_t>(o, 1));
-      DevBuf<GatherJob> dg = upload_jobs(gj, s);
-      {
-        prof::KScope _ks("k_gather_skel", s);
-        k_gather_skel<<<dim3(1, (unsigned)gj.size()), 128, 0, s>>>(dg.get(), ch.idx.get(), ch.perm.get(), lv.idx.get());
-      }
-      HBS_LAUNCH_CHECK("k_gather_skel");
-      HBS_CUDA(cudaStreamSynchronize(s));
+  for (int t = 0; t <= Lmax; ++t) {
+    prof::Phase ph_level(kLevelNames[std::min(Lmax - t, 23)], s);
+    std::vector<LevelTask> tasks, roots;
+    for (Handle* hp : hs) {
+      const int l = hp->L - t;
+      if (l < 0) continue;
+      (l == 0 ? roots : tasks).push_back({hp, l, Handle_geom(*hp)});
     }
-    DevBuf<int> dn;
-    DevBuf<int64_t> doff;
+    // ---- index sets
     {
-      std::vector<int> nn(lv.n.begin(), lv.n.end());
-      dn.upload(nn, s);
-      doff.upload(lv.off, s);
+      std::vector<GatherJob> gj;
+      auto index_sets = [&](LevelTask& tk) {
+        Handle& h = *tk.h;
+        const int l = tk.l;
+        Level& lv = h.levels[l];
+        lv.l = l;
+        lv.count = 1 << l;
+        lv.first = (1 << l) - 1;
+        lv.n.assign(lv.count, 0);
+        lv.off.assign(lv.count, 0);
+        if (l == h.L) {
+          for (int j = 0; j < lv.count; ++j) {
+            const int64_t lo = ((int64_t)j * h.N) >> l, hi = ((int64_t)(j + 1) * h.N) >> l;
+            lv.n[j] = (int)(hi - lo);
+            lv.off[j] = lo;
+          }
+          lv.ntot = h.N;
+          std::vector<int64_t> hidx(h.N);
+          std::iota(hidx.begin(), hidx.end(), 0);
+          lv.idx.upload(hidx, s);
+        } else {
+          Level& ch = h.levels[l + 1];
+          int64_t o = 0;
+          for (int j = 0; j < lv.count; ++j) {
+            lv.off[j] = o;
+            lv.n[j] = ch.k[2 * j] + ch.k[2 * j + 1];
+            o += lv.n[j];
+          }
+          lv.ntot = o;
+          lv.idx.alloc(std::max<int64_t>(o, 1));
+          for (int j = 0; j < lv.count; ++j) {
+            const int a = 2 * j, b = 2 * j + 1;
+            gj.push_back({ch.idx.get() + ch.off[a], ch.perm.get() + ch.off[a], lv.idx.get() + lv.off[j], ch.k[a]});
+            gj.push_back({ch.idx.get() + ch.off[b], ch.perm.get() + ch.off[b], lv.idx.get() + lv.off[j] + ch.k[a],
+                          ch.k[b]});
+          }
+        }
+      };
+      for (auto& tk : tasks) index_sets(tk);
+      for (auto& tk : roots) index_sets(tk);
+      if (!gj.empty()) {
+        DevBuf<GatherJob> dg = upload_jobs(gj, s);
+        prof::KScope _ks("k_gather_skel", s);
+        launch_jobs_y(dg, gj.size(), [&](const GatherJob* p, unsigned ny) { k_gather_skel<<<dim3(1, ny), 128, 0, s>>>(p); });
+        HBS_LAUNCH_CHECK("k_gather_skel");
+      }
     }
 
-    if (l == 0) {
-      // ---- root: dense inverse of [[Dhat_a, A(J_a,J_b)], [A(J_b,J_a), Dhat_b]]
-      Level& ch = h.levels[1];
-      h.nroot = lv.n[0];
-      h.Groot.alloc((size_t)h.nroot * h.nroot);
-      std::vector<DJob> dj(1);
-      dj[0] = {0, 0, h.nroot, ch.k[0], 0, ch.Dhat.get() + ch.dh_off[0], ch.Dhat.get() + ch.dh_off[1]};
+    // ---- roots: dense inverse of [[Dhat_a, A(J_a,J_b)], [A(J_b,J_a), Dhat_b]]
+    if (!roots.empty()) {
+      std::vector<DJob> dj;
+      std::vector<InvJob> ij;
+      for (auto& tk : roots) {
+        Handle& h = *tk.h;
+        Level& lv = h.levels[0];
+        Level& ch = h.levels[1];
+        h.nroot = lv.n[0];
+        h.Groot.alloc(std::max<int64_t>((int64_t)h.nroot * h.nroot, 1));
+        dj.push_back({tk.g, lv.idx.get(), h.Groot.get(), h.nroot, ch.k[0], 0, ch.Dhat.get() + ch.dh_off[0],
+                      ch.Dhat.get() + ch.dh_off[1]});
+        if (h.nroot > 0) ij.push_back({h.Groot.get(), nullptr, h.nroot, (int)ij.size()});
+        h.factor_bytes += 16.0 * h.nroot * h.nroot;
+        h.apply_flops += 8.0 * h.nroot * h.nroot;
+        lv.k.assign(1, 0);
+      }
       DevBuf<DJob> ddj = upload_jobs(dj, s);
       {
         prof::KScope _ks("k_fill_d", s);
-        k_fill_d<<<dim3(grid_for((int64_t)h.nroot * h.nroot, 256), 1), 256, 0, s>>>(g, ddj.get(), lv.idx.get(), h.Groot.get());
+        launch_jobs_y(ddj, dj.size(), [&](const DJob* p, unsigned ny) { k_fill_d<<<dim3(64, ny), 256, 0, s>>>(p); });
       }
       HBS_LAUNCH_CHECK("k_fill_d root");
-      std::vector<InvJob> ij(1);
-      ij[0] = {0, 0, h.nroot, 0};
-      batched_inverse(ij, h.Groot.get(), s, "root block");
-      h.factor_bytes += 16.0 * h.nroot * h.nroot;
-      h.apply_flops += 8.0 * h.nroot * h.nroot;
-      lv.k.assign(1, 0);
-      break;
+      batched_inverse(ij, s, "root block");
+    }
+    if (tasks.empty()) continue;
+
+    // ---- node circles (one stage buffer, one read-back)
+    int64_t nodes = 0;
+    std::vector<int64_t> node0(tasks.size());
+    for (size_t i = 0; i < tasks.size(); ++i) {
+      node0[i] = nodes;
+      nodes += tasks[i].h->levels[tasks[i].l].count;
+    }
+    std::vector<double> hcirc;
+    {
+      DevBuf<double> circ(3 * nodes);
+      std::vector<CircleJob> cj;
+      for (size_t i = 0; i < tasks.size(); ++i) {
+        Handle& h = *tasks[i].h;
+        const int l = tasks[i].l;
+        const int cnt = 1 << l;
+        for (int j = 0; j < cnt; ++j)
+          cj.push_back({h.x.get(), h.y.get(), ((int64_t)j * h.N) >> l, ((int64_t)(j + 1) * h.N) >> l,
+                        circ.get() + 3 * (node0[i] + j)});
+      }
+      DevBuf<CircleJob> dcj = upload_jobs(cj, s);
+      {
+        prof::KScope _ks("k_node_circles", s);
+        k_node_circles<<<(unsigned)cj.size(), 128, 0, s>>>(dcj.get());
+      }
+      HBS_LAUNCH_CHECK("k_node_circles");
+      hcirc = circ.download(s);
+    }
+    for (size_t i = 0; i < tasks.size(); ++i) {
+      Level& lv = tasks[i].h->levels[tasks[i].l];
+      std::vector<double> cx(lv.count), cy(lv.count);
+      lv.h_rad.assign(lv.count, 0.0);
+      for (int j = 0; j < lv.count; ++j) {
+        cx[j] = hcirc[3 * (node0[i] + j)];
+        cy[j] = hcirc[3 * (node0[i] + j) + 1];
+        lv.h_rad[j] = hcirc[3 * (node0[i] + j) + 2];
+      }
+      lv.cx.upload(cx, s);
+      lv.cy.upload(cy, s);
+      lv.rad.upload(lv.h_rad, s);
     }
 
-    // ---- node circles
-    lv.cx.alloc(lv.count); lv.cy.alloc(lv.count); lv.rad.alloc(lv.count);
+    // ---- near lists (count pass, offsets, fill pass)
+    std::vector<int64_t> hcnt;
+    std::vector<int64_t> noff(nodes, 0);
+    DevBuf<int64_t> near;
     {
-      prof::KScope _ks("k_node_circles", s);
-      k_node_circles<<<lv.count, 128, 0, s>>>(h.x.get(), h.y.get(), N, l, lv.cx.get(), lv.cy.get(), lv.rad.get());
+      DevBuf<int64_t> cnt(nodes);
+      std::vector<NearJob> nj;
+      for (size_t i = 0; i < tasks.size(); ++i) {
+        Handle& h = *tasks[i].h;
+        Level& lv = h.levels[tasks[i].l];
+        const double rho = h.opts.proxy_rho;
+        for (int j = 0; j < lv.count; ++j) {
+          const double R = rho * lv.h_rad[j];
+          nj.push_back({h.x.get(), h.y.get(), lv.idx.get(), lv.ntot, lv.off[j], lv.off[j] + lv.n[j],
+                        hcirc[3 * (node0[i] + j)], hcirc[3 * (node0[i] + j) + 1], R * R, cnt.get() + node0[i] + j,
+                        nullptr});
+        }
+      }
+      DevBuf<NearJob> dnj = upload_jobs(nj, s);
+      {
+        prof::KScope _ks("k_near", s);
+        k_near<<<(unsigned)nj.size(), 256, 0, s>>>(dnj.get());
+      }
+      HBS_LAUNCH_CHECK("k_near count");
+      hcnt = cnt.download(s);
+      int64_t tot = 0;
+      for (int64_t q = 0; q < nodes; ++q) { noff[q] = tot; tot += hcnt[q]; }
+      near.alloc(std::max<int64_t>(tot, 1));
+      for (int64_t q = 0; q < nodes; ++q) nj[q].out = near.get() + noff[q];
+      DevBuf<NearJob> dnj2 = upload_jobs(nj, s);
+      {
+        prof::KScope _ks("k_near", s);
+        k_near<<<(unsigned)nj.size(), 256, 0, s>>>(dnj2.get());
+      }
+      HBS_LAUNCH_CHECK("k_near fill");
     }
-    HBS_LAUNCH_CHECK("k_node_circles");
-    lv.h_rad = lv.rad.download(s);
-    std::vector<double> hcx = lv.cx.download(s), hcy = lv.cy.download(s);
 
-    // ---- near lists
-    DevBuf<int64_t> cnt(lv.count);
+    // ---- ID matrices and the joint IDs (Def. 3.1)
     {
-      prof::KScope _ks("k_near", s);
-      k_near<<<lv.count, 256, 0, s>>>(h.x.get(), h.y.get(), lv.idx.get(), lv.ntot, doff.get(), dn.get(), lv.cx.get(),
-                                      lv.cy.get(), lv.rad.get(), rho, cnt.get(), nullptr, nullptr);
-    }
-    HBS_LAUNCH_CHECK("k_near count");
-    std::vector<int64_t> hc = cnt.download(s);
-    std::vector<int64_t> noff(lv.count, 0);
-    int64_t ntot_near = 0;
-    for (int j = 0; j < lv.count; ++j) { noff[j] = ntot_near; ntot_near += hc[j]; }
-    DevBuf<int64_t> dnoff;
-    dnoff.upload(noff, s);
-    DevBuf<int64_t> near(std::max<int64_t>(ntot_near, 1));
-    {
-      prof::KScope _ks("k_near", s);
-      k_near<<<lv.count, 256, 0, s>>>(h.x.get(), h.y.get(), lv.idx.get(), lv.ntot, doff.get(), dn.get(), lv.cx.get(),
-                                      lv.cy.get(), lv.rad.get(), rho, cnt.get(), dnoff.get(), near.get());
-    }
-    HBS_LAUNCH_CHECK("k_near fill");
-
-    // ---- ID matrices
-    std::vector<YJob> yj(lv.count);
-    int64_t ypool = 0;
-    for (int j = 0; j < lv.count; ++j) {
-      double R = rho * lv.h_rad[j];
-      int np = (int)(2.0 * std::ceil(h.omega * R) + 40.0);
-      np = std::max(np, h.opts.n_proxy_min);
-      np = (np + 7) / 8 * 8;
-      yj[j] = {ypool, lv.off[j], noff[j], lv.n[j], (int)hc[j], np, hcx[j], hcy[j], R, 2.0 * HBS_PI * R / np};
-      ypool += (int64_t)(2 * hc[j] + 2 * np) * lv.n[j];
-    }
-    DevBuf<cplx> Y(std::max<int64_t>(ypool, 1));
-    {
+      std::vector<YJob> yj;
+      std::vector<int64_t> ymt;
+      int64_t ypool = 0;
+      for (size_t i = 0; i < tasks.size(); ++i) {
+        Handle& h = *tasks[i].h;
+        Level& lv = h.levels[tasks[i].l];
+        for (int j = 0; j < lv.count; ++j) {
+          const double R = h.opts.proxy_rho * lv.h_rad[j];
+          int np = (int)(2.0 * std::ceil(h.omega * R) + 40.0);
+          np = std::max(np, h.opts.n_proxy_min);
+          np = (np + 7) / 8 * 8;
+          const int nn = (int)hcnt[node0[i] + j];
+          yj.push_back({tasks[i].g, lv.idx.get() + lv.off[j], near.get() + noff[node0[i] + j], nullptr, lv.n[j], nn,
+                        np, hcirc[3 * (node0[i] + j)], hcirc[3 * (node0[i] + j) + 1], R, 2.0 * HBS_PI * R / np});
+          ymt.push_back(ypool);
+          ypool += (int64_t)(2 * nn + 2 * np) * lv.n[j];
+        }
+      }
+      DevBuf<cplx> Y(std::max<int64_t>(ypool, 1));
+      for (size_t q = 0; q < yj.size(); ++q) yj[q].mt = Y.get() + ymt[q];
       DevBuf<YJob> dyj = upload_jobs(yj, s);
       {
         prof::KScope _ks("k_fill_y", s);
-        k_fill_y<<<dim3(64, lv.count), 256, 0, s>>>(g, dyj.get(), lv.idx.get(), near.get(), Y.get());
+        launch_jobs_y(dyj, yj.size(), [&](const YJob* p, unsigned ny) { k_fill_y<<<dim3(64, ny), 256, 0, s>>>(p); });
       }
       HBS_LAUNCH_CHECK("k_fill_y");
-      std::vector<CpqrJob> cj(lv.count);
-      lv.t_off.assign(lv.count, 0);
-      int64_t tpool = 0;
-      for (int j = 0; j < lv.count; ++j) {
-        int m = 2 * (int)hc[j] + 2 * yj[j].np;
-        cj[j] = {yj[j].mt_off, tpool, lv.off[j], m, lv.n[j], j};
-        lv.t_off[j] = tpool;
-        tpool += (int64_t)std::min(m, lv.n[j]) * lv.n[j];
+      std::vector<CpqrJob> cj;
+      for (size_t i = 0; i < tasks.size(); ++i) {
+        Level& lv = tasks[i].h->levels[tasks[i].l];
+        lv.t_off.assign(lv.count, 0);
+        int64_t tpool = 0;
+        for (int j = 0; j < lv.count; ++j) {
+          const YJob& y = yj[node0[i] + j];
+          const int m = 2 * y.nn + 2 * y.np;
+          lv.t_off[j] = tpool;
+          tpool += (int64_t)std::min(m, lv.n[j]) * lv.n[j];
+        }
+        lv.T.alloc(std::max<int64_t>(tpool, 1));
+        lv.perm.alloc(std::max<int64_t>(lv.ntot, 1));
+        for (int j = 0; j < lv.count; ++j) {
+          const YJob& y = yj[node0[i] + j];
+          cj.push_back({y.mt, lv.T.get() + lv.t_off[j], lv.perm.get() + lv.off[j], 2 * y.nn + 2 * y.np, lv.n[j],
+                        (int)cj.size()});
+        }
       }
-      lv.T.alloc(std::max<int64_t>(tpool, 1));
-      lv.perm.alloc(std::max<int64_t>(lv.ntot, 1));
-      lv.k = batched_id(cj, Y.get(), lv.T.get(), lv.perm.get(), h.tol, s);
+      std::vector<int> ranks = batched_id(cj, tasks[0].h->tol, s);
+      for (size_t i = 0; i < tasks.size(); ++i) {
+        Handle& h = *tasks[i].h;
+        Level& lv = h.levels[tasks[i].l];
+        lv.k.assign(ranks.begin() + node0[i], ranks.begin() + node0[i] + lv.count);
+        for (int j = 0; j < lv.count; ++j) h.max_rank = std::max(h.max_rank, lv.k[j]);
+      }
     }
-    Y.release();
-    for (int j = 0; j < lv.count; ++j) h.max_rank = std::max(h.max_rank, lv.k[j]);
+    near.release();
 
-    // ---- D blocks and their inverses
-    std::vector<int64_t> d_off(lv.count);
-    int64_t dpool = 0;
-    for (int j = 0; j < lv.count; ++j) { d_off[j] = dpool; dpool += (int64_t)lv.n[j] * lv.n[j]; }
-    DevBuf<cplx> Dinv(std::max<int64_t>(dpool, 1));
+    // ---- D blocks and their inverses (Dinv becomes G below)
+    std::vector<DevBuf<cplx>> Dinv(tasks.size()), X(tasks.size()), Yp(tasks.size()), S(tasks.size());
+    std::vector<std::vector<int64_t>> d_off(tasks.size());
     {
-      std::vector<DJob> dj(lv.count);
-      for (int j = 0; j < lv.count; ++j) {
-        if (l == L) {
-          dj[j] = {d_off[j], lv.off[j], lv.n[j], 0, 1, nullptr, nullptr};
-        } else {
-          Level& ch = h.levels[l + 1];
-          dj[j] = {d_off[j], lv.off[j], lv.n[j], ch.k[2 * j], 0, ch.Dhat.get() + ch.dh_off[2 * j],
-                   ch.Dhat.get() + ch.dh_off[2 * j + 1]};
+      std::vector<DJob> dj;
+      std::vector<InvJob> ij;
+      for (size_t i = 0; i < tasks.size(); ++i) {
+        Handle& h = *tasks[i].h;
+        const int l = tasks[i].l;
+        Level& lv = h.levels[l];
+        d_off[i].assign(lv.count, 0);
+        int64_t dpool = 0;
+        for (int j = 0; j < lv.count; ++j) { d_off[i][j] = dpool; dpool += (int64_t)lv.n[j] * lv.n[j]; }
+        Dinv[i].alloc(std::max<int64_t>(dpool, 1));
+        for (int j = 0; j < lv.count; ++j) {
+          cplx* d = Dinv[i].get() + d_off[i][j];
+          if (l == h.L) {
+            dj.push_back({tasks[i].g, lv.idx.get() + lv.off[j], d, lv.n[j], 0, 1, nullptr, nullptr});
+          } else {
+            Level& ch = h.levels[l + 1];
+            dj.push_back({tasks[i].g, lv.idx.get() + lv.off[j], d, lv.n[j], ch.k[2 * j], 0,
+                          ch.Dhat.get() + ch.dh_off[2 * j], ch.Dhat.get() + ch.dh_off[2 * j + 1]});
+          }
+          ij.push_back({d, nullptr, lv.n[j], (int)ij.size()});
         }
       }
       DevBuf<DJob> ddj = upload_jobs(dj, s);
       {
         prof::KScope _ks("k_fill_d", s);
-        k_fill_d<<<dim3(64, lv.count), 256, 0, s>>>(g, ddj.get(), lv.idx.get(), Dinv.get());
+        launch_jobs_y(ddj, dj.size(), [&](const DJob* p, unsigned ny) { k_fill_d<<<dim3(64, ny), 256, 0, s>>>(p); });
       }
       HBS_LAUNCH_CHECK("k_fill_d");
-      std::vector<InvJob> ij(lv.count);
-      for (int j = 0; j < lv.count; ++j) ij[j] = {d_off[j], 0, lv.n[j], j};
-      batched_inverse(ij, Dinv.get(), s, "leaf/level block");
+      batched_inverse(ij, s, "leaf/level block");
     }
     // X = D^{-1} P (n x k), Yt = P^T D^{-1} (k x n), S = P^T X (k x k)
-    lv.e_off.assign(lv.count, 0); lv.f_off.assign(lv.count, 0); lv.g_off.assign(lv.count, 0); lv.dh_off.assign(lv.count, 0);
-    int64_t eo = 0, go = 0, dho = 0;
-    for (int j = 0; j < lv.count; ++j) {
-      lv.e_off[j] = eo; lv.f_off[j] = eo; eo += (int64_t)lv.n[j] * lv.k[j];
-      lv.g_off[j] = go; go += (int64_t)lv.n[j] * lv.n[j];
-      lv.dh_off[j] = dho; dho += (int64_t)lv.k[j] * lv.k[j];
-    }
-    DevBuf<cplx> X(std::max<int64_t>(eo, 1)), Yp(std::max<int64_t>(eo, 1)), S(std::max<int64_t>(dho, 1));
     {
-      std::vector<PJob> rp(lv.count), lp(lv.count);
-      for (int j = 0; j < lv.count; ++j) {
-        const int n = lv.n[j], k = lv.k[j];
-        const int* pm = lv.perm.get() + lv.off[j];
-        const cplx* T = lv.T.get() + lv.t_off[j];
-        rp[j] = {Dinv.get() + d_off[j], X.get() + lv.e_off[j], pm, T, n, k, n, n, n};
-        lp[j] = {Dinv.get() + d_off[j], Yp.get() + lv.f_off[j], pm, T, n, k, n, n, k};
+      std::vector<PJob> rp, lp, lp2;
+      for (size_t i = 0; i < tasks.size(); ++i) {
+        Level& lv = tasks[i].h->levels[tasks[i].l];
+        lv.e_off.assign(lv.count, 0); lv.f_off.assign(lv.count, 0); lv.dh_off.assign(lv.count, 0);
+        int64_t eo = 0, dho = 0;
+        for (int j = 0; j < lv.count; ++j) {
+          lv.e_off[j] = eo; lv.f_off[j] = eo; eo += (int64_t)lv.n[j] * lv.k[j];
+          lv.dh_off[j] = dho; dho += (int64_t)lv.k[j] * lv.k[j];
+        }
+        X[i].alloc(std::max<int64_t>(eo, 1));
+        Yp[i].alloc(std::max<int64_t>(eo, 1));
+        S[i].alloc(std::max<int64_t>(dho, 1));
+        for (int j = 0; j < lv.count; ++j) {
+          const int n = lv.n[j], k = lv.k[j];
+          const int* pm = lv.perm.get() + lv.off[j];
+          const cplx* T = lv.T.get() + lv.t_off[j];
+          cplx* d = Dinv[i].get() + d_off[i][j];
+          rp.push_back({d, X[i].get() + lv.e_off[j], pm, T, n, k, n, n, n});
+          lp.push_back({d, Yp[i].get() + lv.f_off[j], pm, T, n, k, n, n, k});
+          lp2.push_back({X[i].get() + lv.e_off[j], S[i].get() + lv.dh_off[j], pm, T, n, k, k, n, k});
+        }
       }
-      DevBuf<PJob> drp = upload_jobs(rp, s), dlp = upload_jobs(lp, s);
+      DevBuf<PJob> drp = upload_jobs(rp, s), dlp = upload_jobs(lp, s), dlp2 = upload_jobs(lp2, s);
       {
         prof::KScope _ks("k_right_p", s);
-        k_right_p<<<dim3(32, lv.count), 256, 0, s>>>(drp.get());
+        launch_jobs_y(drp, rp.size(), [&](const PJob* p, unsigned ny) { k_right_p<<<dim3(32, ny), 256, 0, s>>>(p); });
       }
       HBS_LAUNCH_CHECK("k_right_p");
       {
         prof::KScope _ks("k_left_pt", s);
-        k_left_pt<<<dim3(32, lv.count), 256, 0, s>>>(dlp.get());
+        launch_jobs_y(dlp, lp.size(), [&](const PJob* p, unsigned ny) { k_left_pt<<<dim3(32, ny), 256, 0, s>>>(p); });
       }
       HBS_LAUNCH_CHECK("k_left_pt");
-      for (int j = 0; j < lv.count; ++j) {
-        const int n = lv.n[j], k = lv.k[j];
-        lp[j] = {X.get() + lv.e_off[j], S.get() + lv.dh_off[j], lv.perm.get() + lv.off[j], lv.T.get() + lv.t_off[j],
-                 n, k, k, n, k};
-      }
-      DevBuf<PJob> dlp2 = upload_jobs(lp, s);
       {
         prof::KScope _ks("k_left_pt", s);
-        k_left_pt<<<dim3(32, lv.count), 256, 0, s>>>(dlp2.get());
+        launch_jobs_y(dlp2, lp2.size(), [&](const PJob* p, unsigned ny) { k_left_pt<<<dim3(32, ny), 256, 0, s>>>(p); });
       }
       HBS_LAUNCH_CHECK("k_left_pt S");
       HBS_CUDA(cudaStreamSynchronize(s));
@@ -721,44 +854,51 @@ void build_hbs(Handle& h, cudaStream_t s) {
     // Dhat = S^{-1}
     {
       std::vector<InvJob> ij;
-      for (int j = 0; j < lv.count; ++j)
-        if (lv.k[j] > 0) ij.push_back({lv.dh_off[j], 0, lv.k[j], j});
-      batched_inverse(ij, S.get(), s, "skeleton block P^T D^-1 P");
+      for (size_t i = 0; i < tasks.size(); ++i) {
+        Level& lv = tasks[i].h->levels[tasks[i].l];
+        for (int j = 0; j < lv.count; ++j)
+          if (lv.k[j] > 0) ij.push_back({S[i].get() + lv.dh_off[j], nullptr, lv.k[j], (int)ij.size()});
+      }
+      batched_inverse(ij, s, "skeleton block P^T D^-1 P");
     }
-    lv.Dhat = std::move(S);
-    lv.E.alloc(std::max<int64_t>(eo, 1));
-    lv.F.alloc(std::max<int64_t>(eo, 1));
-    lv.G = std::move(Dinv);
-    lv.g_off = d_off;
+    // E = X Dhat, F* = Dhat Yt, G = D^{-1} - E Yt
     {
-      std::vector<GemmJob> gj;
-      for (int j = 0; j < lv.count; ++j) {
-        const int n = lv.n[j], k = lv.k[j];
-        if (k == 0) continue;
-        // E = X Dhat  (n x k)
-        gj.push_back({X.get() + lv.e_off[j], lv.Dhat.get() + lv.dh_off[j], lv.E.get() + lv.e_off[j], n, k, k, n, k, n,
-                      cmk(1, 0), cmk(0, 0), 0, 0, 0});
-        // F* = Dhat Yt  (k x n)
-        gj.push_back({lv.Dhat.get() + lv.dh_off[j], Yp.get() + lv.f_off[j], lv.F.get() + lv.f_off[j], k, n, k, k, k, k,
-                      cmk(1, 0), cmk(0, 0), 0, 0, 0});
+      std::vector<GemmJob> g1, g2;
+      for (size_t i = 0; i < tasks.size(); ++i) {
+        Handle& h = *tasks[i].h;
+        Level& lv = h.levels[tasks[i].l];
+        int64_t eo = 0;
+        for (int j = 0; j < lv.count; ++j) eo += (int64_t)lv.n[j] * lv.k[j];
+        lv.Dhat = std::move(S[i]);
+        lv.E.alloc(std::max<int64_t>(eo, 1));
+        lv.F.alloc(std::max<int64_t>(eo, 1));
+        lv.G = std::move(Dinv[i]);
+        lv.g_off = d_off[i];
+        for (int j = 0; j < lv.count; ++j) {
+          const int n = lv.n[j], k = lv.k[j];
+          if (k == 0) continue;
+          g1.push_back({X[i].get() + lv.e_off[j], lv.Dhat.get() + lv.dh_off[j], lv.E.get() + lv.e_off[j], n, k, k, n,
+                        k, n, cmk(1, 0), cmk(0, 0), 0, 0, 0});
+          g1.push_back({lv.Dhat.get() + lv.dh_off[j], Yp[i].get() + lv.f_off[j], lv.F.get() + lv.f_off[j], k, n, k, k,
+                        k, k, cmk(1, 0), cmk(0, 0), 0, 0, 0});
+          g2.push_back({lv.E.get() + lv.e_off[j], Yp[i].get() + lv.f_off[j], lv.G.get() + lv.g_off[j], n, n, k, n, k,
+                        n, cmk(-1, 0), cmk(1, 0), 0, 0, 0});
+        }
+        for (int j = 0; j < lv.count; ++j) {
+          const double n = lv.n[j], k = lv.k[j];
+          h.factor_bytes += 16.0 * (2 * n * k + n * n);
+          h.apply_flops += 8.0 * (2 * n * k + n * n);
+        }
       }
-      launch_gemms(gj, s);
-      gj.clear();
-      for (int j = 0; j < lv.count; ++j) {
-        const int n = lv.n[j], k = lv.k[j];
-        if (k == 0) continue;
-        // G = D^{-1} - E Yt
-        gj.push_back({lv.E.get() + lv.e_off[j], Yp.get() + lv.f_off[j], lv.G.get() + lv.g_off[j], n, n, k, n, k, n,
-                      cmk(-1, 0), cmk(1, 0), 0, 0, 0});
-      }
-      launch_gemms(gj, s);
-    }
-    for (int j = 0; j < lv.count; ++j) {
-      const double n = lv.n[j], k = lv.k[j];
-      h.factor_bytes += 16.0 * (2 * n * k + n * n);
-      h.apply_flops += 8.0 * (2 * n * k + n * n);
+      launch_gemms(g1, s);
+      launch_gemms(g2, s);
     }
   }
+}
+
+void build_hbs(Handle& h, cudaStream_t s) {
+  std::vector<Handle*> one{&h};
+  build_hbs_multi(one, s);
 }
 
 // x = A^{-1} b through the telescoping factorization (Sec. 4): upward b^_tau = F*_tau b_tau,

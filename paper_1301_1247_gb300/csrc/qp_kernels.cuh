@@ -72,10 +72,11 @@ void load_handle(Handle& h, const char* path, cudaStream_t s);
 
 // hbs_build.cu
 void build_hbs(Handle& h, cudaStream_t s);
+// Several solvers at once, level by level from the leaves, one launch per kernel and stage.
+void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s);
 DevGeom Handle_geom(const Handle& h);
 void run_gemms(std::vector<GemmJob>& jobs, cudaStream_t s);
-std::vector<int> batched_id(std::vector<CpqrJob>& jobs, cplx* pool, cplx* tpool, int* permpool, double tol,
-                            cudaStream_t s);
+std::vector<int> batched_id(std::vector<CpqrJob>& jobs, double tol, cudaStream_t s);
 __global__ void k_geom(const double* dx, const double* dy, double* nx, double* ny, double* w, int64_t n);
 
 // qp_kernels.cu

@@ -65,6 +65,26 @@ static double auto_wood_shift(double omega, double d) {
   return 0.5 * best;
 }
 
+// Distance, in the contour variable t, from a pole p of the wall integrands to the
+// Sommerfeld contour k(t) = t - i c tanh((t - t0)/w): min |k(t) - p| / |k'(t)| over a fine
+// sampling of t around the contour's bend (far from it the contour runs at |Im k| = c and
+// only nearby poles can come close).
+static double contour_distance(const Handle& h, int c, std::complex<double> p) {
+  const double t0 = h.contours[c].t0, cc = h.cc, cw = h.cw;
+  if (std::fabs(p.imag()) > cc + 3.0) return 1e300;
+  double best = 1e300;
+  // k(t) = t + O(c), so the nearest contour point lies within a few units of Re p in t
+  const double lo = p.real() - 4.0, hi = p.real() + 4.0;
+  for (double t = lo; t <= hi; t += 0.02) {
+    const double u = (t - t0) / cw;
+    const double th = std::tanh(u), sech2 = 1.0 - th * th;
+    const std::complex<double> k(t, -cc * th);
+    const double dk = std::hypot(1.0, cc / cw * sech2);
+    best = std::min(best, std::abs(k - p) / dk);
+  }
+  return best;
+}
+
 void build_periodizer(Handle& h, cudaStream_t s) {
   const int64_t N = h.N;
   const DevGeom g = Handle_geom(h);
@@ -222,7 +242,10 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   // ---- Sommerfeld contours (Sec. 2.3)
   h.cc = h.opts.contour_c > 0 ? h.opts.contour_c : 2.0;
   h.cw = h.opts.contour_w > 0 ? h.opts.contour_w : 2.0;
-  h.ch = h.opts.contour_h > 0 ? h.opts.contour_h : 0.4;
+  // Trapezoid spacing: a pole of the wall integrands at distance delta (in t) from the
+  // contour costs about exp(-2 pi delta / h); over all incidence angles the nearer of the
+  // two contours keeps delta >= ~0.75, so h = 0.2 holds the quadrature error near 1e-10.
+  h.ch = h.opts.contour_h > 0 ? h.opts.contour_h : 0.2;
   double shift = h.opts.wood_shift;
   if (shift == 0.0) shift = auto_wood_shift(omega, d);
   {
@@ -1385,8 +1408,14 @@ static void reduced_batch(Handle& h, std::vector<GroupJob>& gjobs, std::vector<s
   }
 }
 
+// k_n = sqrt(w^2 - kappa_n^2) (non-negative real or positive imaginary).  An order within
+// rounding of a Rayleigh-Wood anomaly (|w^2 - kappa_n^2| <= 1e-12 w^2; an angle given as the
+// anomaly in FP64 lands there) is taken at the anomaly, k_n = 0: the amplitudes have a
+// square-root singularity in the angle there, so the few-ulp differences between ways of
+// forming kappa_n would otherwise show up at the 1e-8 level.
 static zc kn_of(double omega, double kap) {
   double v = omega * omega - kap * kap;
+  if (std::fabs(v) <= 1e-12 * omega * omega) return zc(0.0, 0.0);
   return v >= 0 ? zc(std::sqrt(v), 0.0) : zc(0.0, std::sqrt(-v));
 }
 
@@ -1476,19 +1505,23 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
       const int q = (int)mem.size();
       const double th0 = theta[mem[0]];
       const double kap_i = omega * std::cos(th0);
-      // poles +-k_n: choose the contour whose crossing is farther from them
+      // poles +-k_n of the integrand: choose the contour that stays farther from all of
+      // them (distance in the trapezoid variable t), since the trapezoid rule loses
+      // accuracy like exp(-2 pi dist / h) as a pole approaches the contour.
       std::vector<std::pair<int, zc>> modes;
       const int nlo = (int)std::floor((-omega - kap_i) * d / (2 * M_PI)) - 4;
       const int nhi = (int)std::ceil((omega - kap_i) * d / (2 * M_PI)) + 4;
-      double dist0 = 1e300, dist1 = 1e300;
       const double t1 = nc > 1 ? h.contours[1].t0 : 0.0;
+      double dist[2] = {1e300, 1e300};
       for (int n = nlo; n <= nhi; ++n) {
         zc kn = kn_of(omega, kap_i + 2 * M_PI * n / d);
         modes.push_back({n, kn});
-        dist0 = std::min(dist0, std::abs(kn));
-        dist1 = std::min(dist1, std::min(std::abs(kn - t1), std::abs(-kn - t1)));
+        // only poles near a crossing point (0 or t1) can come close to either contour
+        if (std::fabs(kn.real()) > std::max(t1, 0.0) + 6.0) continue;
+        for (int cc = 0; cc < nc; ++cc)
+          dist[cc] = std::min(dist[cc], std::min(contour_distance(h, cc, kn), contour_distance(h, cc, -kn)));
       }
-      const int c = (nc > 1 && dist1 > dist0) ? 1 : 0;
+      const int c = (nc > 1 && dist[1] > dist[0]) ? 1 : 0;
       GroupJob G{};
       std::vector<std::pair<double, zc>> wood;
       if (c == 1) {

@@ -27,11 +27,13 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "RANK", 5: "W
                 6: "TIMEOUT", 7: "IO", 8: "INTERNAL"}
 
 # Every entry point declared in include/hbsqp.h.
-EXPORTED = ("hbs_default_options", "hbs_build", "hbs_solve", "hbs_solve_plain", "hbs_bragg_amplitudes",
+EXPORTED = ("hbs_default_options", "hbs_build", "hbs_build_batch", "hbs_solve", "hbs_solve_plain", "hbs_bragg_amplitudes",
             "hbs_result_angle_info", "hbs_info", "hbs_save", "hbs_load", "hbs_apply_inverse",
             "hbs_kernel_block", "hbs_row_id",
             "hbs_row_id_static",
             "hbs_profile_enable", "hbs_profile_reset", "hbs_profile_get", "hbs_launch_count",
+            "hbs_server_create", "hbs_server_add", "hbs_server_remove", "hbs_server_submit", "hbs_server_wait",
+            "hbs_server_stats", "hbs_server_free",
             "hbs_free", "hbs_result_free", "hbs_last_error")
 
 
@@ -63,6 +65,16 @@ class Info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("mean_batch", ctypes.c_double), ("p50_latency_s", ctypes.c_double),
+                ("p99_latency_s", ctypes.c_double), ("max_latency_s", ctypes.c_double),
+                ("solves_per_s", ctypes.c_double), ("resident_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
@@ -83,6 +95,23 @@ def lib():
     L.hbs_default_options.argtypes = [ctypes.POINTER(Options)]
     L.hbs_default_options.restype = None
     L.hbs_build.argtypes = [ctypes.POINTER(Geometry), dbl, dbl, ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]
+    L.hbs_server_create.argtypes = [ctypes.c_size_t, ci, ci, ctypes.POINTER(vp)]
+    L.hbs_server_create.restype = ctypes.c_int
+    L.hbs_server_add.argtypes = [vp, vp, ctypes.POINTER(i64)]
+    L.hbs_server_add.restype = ctypes.c_int
+    L.hbs_server_remove.argtypes = [vp, i64]
+    L.hbs_server_remove.restype = ctypes.c_int
+    L.hbs_server_submit.argtypes = [vp, i64, dbl, ctypes.POINTER(i64)]
+    L.hbs_server_submit.restype = ctypes.c_int
+    L.hbs_server_wait.argtypes = [vp, i64, dbl, ctypes.POINTER(vp)]
+    L.hbs_server_wait.restype = ctypes.c_int
+    L.hbs_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    L.hbs_server_stats.restype = ctypes.c_int
+    L.hbs_server_free.argtypes = [vp]
+    L.hbs_server_free.restype = None
+    L.hbs_build_batch.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(dbl), i64, dbl, ctypes.POINTER(Options),
+                                  vp, ctypes.POINTER(vp)]
+    L.hbs_build_batch.restype = ctypes.c_int
     L.hbs_solve.argtypes = [vp, ctypes.POINTER(dbl), i64, vp, ctypes.POINTER(vp)]
     L.hbs_solve_plain.argtypes = [vp, ctypes.POINTER(dbl), i64, vp, ctypes.POINTER(vp)]
     L.hbs_bragg_amplitudes.argtypes = [vp, i64, ctypes.POINTER(ci), ctypes.POINTER(ci), vp, vp,
@@ -254,6 +283,80 @@ class Handle:
     def apply_inverse(self, b, x, nrhs, stream=None):
         """x = A^{-1} b for device complex128 tensors (N x nrhs, column-major, i.e. torch shape (nrhs, N))."""
         _check(lib().hbs_apply_inverse(self._p, _ptr(b), _ptr(x), int(nrhs), _stream(stream)), "hbs_apply_inverse")
+
+
+class Server:
+    """Request loop over resident solvers (hbs_server_*): submit single angles from any
+    thread, wait for their Bragg amplitudes."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, slots: int = 2, max_batch: int = 256):
+        out = ctypes.c_void_p()
+        _check(lib().hbs_server_create(int(hbm_budget_bytes), int(slots), int(max_batch), ctypes.byref(out)),
+               "hbs_server_create")
+        self._p = out
+        self._handles = {}
+
+    def add(self, handle: "Handle") -> int:
+        gid = ctypes.c_int64()
+        _check(lib().hbs_server_add(self._p, handle._p, ctypes.byref(gid)), "hbs_server_add")
+        self._handles[gid.value] = handle
+        return gid.value
+
+    def remove(self, gid: int):
+        _check(lib().hbs_server_remove(self._p, int(gid)), "hbs_server_remove")
+        self._handles.pop(gid, None)
+
+    def submit(self, gid: int, theta: float) -> int:
+        rid = ctypes.c_int64()
+        _check(lib().hbs_server_submit(self._p, int(gid), float(theta), ctypes.byref(rid)), "hbs_server_submit")
+        return rid.value
+
+    def wait(self, rid: int, timeout_s: float = 60.0):
+        """(orders, c, d, flux_error) of one request."""
+        out = ctypes.c_void_p()
+        st = lib().hbs_server_wait(self._p, int(rid), float(timeout_s), ctypes.byref(out))
+        _check(st, "hbs_server_wait", allow_warn=True)
+        r = Result(out, 1)
+        r.status = st
+        return r.bragg(0)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().hbs_server_stats(self._p, ctypes.byref(s)), "hbs_server_stats")
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "_p", None):
+            lib().hbs_server_free(self._p)
+            self._p = None
+
+    def __del__(self):
+        self.close()
+
+
+def build_batch(geometries, omegas, d, tol, opts: Options | None = None, stream=None) -> list:
+    """Several solvers built level-synchronously (hbs_build_batch).  `geometries` is a list
+    of host (x, y, dx, dy) tuples; returns one Handle per geometry."""
+    cnt = len(geometries)
+    keep = []
+    garr = (Geometry * cnt)()
+    for i, (x, y, dx, dy) in enumerate(geometries):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, dx, dy)]
+        keep.append(arrs)
+        garr[i] = Geometry(len(arrs[0]), float(d), *[a.ctypes.data for a in arrs], 0)
+    om = np.ascontiguousarray(np.asarray(omegas, dtype=np.float64))
+    outs = (ctypes.c_void_p * cnt)()
+    _check(lib().hbs_build_batch(garr, om.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), cnt, float(tol),
+                                 ctypes.byref(opts) if opts is not None else None, _stream(stream), outs),
+           "hbs_build_batch")
+    res = []
+    for i in range(cnt):
+        h = Handle.__new__(Handle)
+        h._p = ctypes.c_void_p(outs[i])
+        h._keep = keep[i]
+        h.n = len(keep[i][0])
+        res.append(h)
+    return res
 
 
 def kernel_block(x, y, dx, dy, omega, kind, shift_x, rows, cols, out, stream=None):

@@ -135,3 +135,23 @@ def workload_complicated_n100k(seed: int = 0, n_groups: int = 100, q: int = 10):
     N = 100 000, 1000 angles in 100 groups of 10 sharing a Bloch phase."""
     return dict(obstacle=wiggly(seed, 0.3, 60, 0.05), omega=60.0, d=1.0, N=100000,
                 thetas=bloch_grouped_angles(seed + 1, 60.0, 1.0, n_groups, q))
+
+
+def workload_batch(seed: int = 0, count: int = 256, n_lo: int = 400, n_hi: int = 20000, w_lo: float = 5.0,
+                   w_hi: float = 40.0, n_angles: int = 8):
+    """Many independent gratings: alternating star and wiggly obstacles with N log-uniform in
+    [n_lo, n_hi] (rounded to a multiple of 8), omega uniform in [w_lo, w_hi] and n_angles
+    incident angles uniform in (-pi/2 + 0.02, -0.1) each (away from grazing incidence).  Returns a list of dicts (obstacle, N, omega,
+    d, thetas)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi))) / 8.0)) * 8
+        omega = float(rng.uniform(w_lo, w_hi))
+        if i % 2 == 0:
+            obs = star(float(rng.uniform(0.2, 0.3)), float(rng.uniform(0.1, 0.3)), int(rng.integers(3, 7)))
+        else:
+            obs = wiggly(int(rng.integers(0, 1 << 30)), 0.3, 20, 0.03)
+        th = rng.uniform(-math.pi / 2 + 0.02, -0.1, n_angles)
+        out.append(dict(obstacle=obs, N=n, omega=omega, d=1.0, thetas=th))
+    return out

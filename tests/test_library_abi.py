@@ -56,6 +56,12 @@ def test_argument_errors_need_no_gpu():
     assert L.hbs_build(ctypes.byref(g), 10.0, 1e-12, None, None, ctypes.byref(out)) == 1
     assert L.hbs_solve(None, None, 0, None, ctypes.byref(out)) == 1
     assert L.hbs_apply_inverse(None, None, None, 1, None) == 1
+    srv = ctypes.c_void_p()
+    assert L.hbs_server_create(0, 0, 1, ctypes.byref(srv)) == 1
+    rid = ctypes.c_int64()
+    assert L.hbs_server_submit(None, 1, -0.5, ctypes.byref(rid)) == 1
+    outs = (ctypes.c_void_p * 2)()
+    assert L.hbs_build_batch(None, None, 2, 1e-12, None, None, outs) == 1
 
 
 def test_load_rejects_missing_and_foreign_files_without_gpu(tmp_path):

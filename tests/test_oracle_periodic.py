@@ -87,7 +87,9 @@ def test_woods_anomaly_shifted_contour():
     standard contour the flux balance fails; moving the crossing point and adding the one
     Rayleigh-Bloch unknown and row restores it (Sec. 2.4)."""
     th = -math.acos(1.0 - 2.0 * math.pi / OMEGA)
-    assert abs(qd.k_n(OMEGA, qd.kappa_n(OMEGA, D, th, 1))) < 1e-6
+    # the anomaly given in FP64 is taken at the anomaly: k_1 is exactly 0
+    assert qd.k_n(OMEGA, qd.kappa_n(OMEGA, D, th, 1)) == 0.0
+    assert abs(qd.k_n(OMEGA, qd.kappa_n(OMEGA, D, th + 1e-6, 1))) > 1e-4
     x, y, dx, dy = _star(600)
     bad = qd.dense_solve(x, y, dx, dy, OMEGA, D, th, qd.Options(**OPTS))
     good = qd.dense_solve(x, y, dx, dy, OMEGA, D, th, qd.Options(**OPTS, t0=2.3))
@@ -119,3 +121,27 @@ def test_bloch_sharing_count():
         step = 2 * math.pi / (omega * D)
         q = int(math.floor(2.0 / step))  # values c + m step inside (-1, 1)
         assert abs(q - omega * D / math.pi) <= 1.0
+
+
+def test_contour_choice_keeps_poles_away():
+    """An evanescent pole k_n = i*2.0 lies next to where the shifted contour (crossing the
+    real axis at T) crosses the imaginary axis, i*c*tanh(T/w) = i*1.94: that contour loses
+    the quadrature (flux error > 1e-4) while the standard one, about 1 away in t, keeps it;
+    halving h then gains the exp(-2 pi delta / h) factor.  This is why the solver picks the
+    contour by the poles' distance to the whole contour (and uses h = 0.2)."""
+    obs = inputs.star(0.25, 0.2, 3)
+    x, y, dx, dy = obs.sample(600)
+    omega, th = 9.164, -1.2158
+    kap = omega * math.cos(th)
+    kn = np.sqrt((omega ** 2 - (kap + 2 * math.pi * np.arange(-3, 4)) ** 2).astype(complex))
+    assert abs(np.min(np.abs(kn)) - 2.0) < 0.02
+    T = 4.254
+    K = math.sqrt(omega ** 2 + (37 / 1.16) ** 2) + 4.0
+
+    def flux(h, t0):
+        m = int(math.ceil(2 * (K + t0) / h))
+        return qd.dense_solve(x, y, dx, dy, omega, 1.0, th, qd.Options(m=m, h=h, c=2.0, w=2.0, t0=t0)).flux_error
+
+    f_std, f_shift = flux(0.4, 0.0), flux(0.4, T)
+    assert f_shift > 1e-4 and f_std < 1e-6
+    assert flux(0.2, 0.0) < 0.2 * f_std
