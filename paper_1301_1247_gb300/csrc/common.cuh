@@ -6,6 +6,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "hankel_table.h"
+
 typedef double2 cplx;
 
 __host__ __device__ __forceinline__ cplx cmk(double re, double im) { return make_double2(re, im); }
@@ -68,58 +70,37 @@ __device__ __forceinline__ cplx csqrt_principal(cplx z) {
 // ---------------------------------------------------------------------------
 // Hankel functions of the first kind, orders 0 and 1, real argument z > 0.
 //
-// z < 17.5: Miller's backward recurrence J_{n-1} = (2n/z) J_n - J_{n+1} from a
-//   fixed start index n0 = 44 (at least z + 26 for every z < 17.5) with the
-//   normalisation J_0 + 2 sum J_{2k} = 1,
-//   then Neumann's series
-//     Y_0 = (2/pi) [ (ln(z/2) + gamma) J_0 - 2 sum_{k>=1} (-1)^k J_{2k} / k ],
-//   and Y_1 = -Y_0' from differentiating it term by term with
-//   J_{2k}' = (J_{2k-1} - J_{2k+1}) / 2:
-//     Y_1 = (2/pi) [ -J_0 / z + (ln(z/2) + gamma) J_1 - J_1
-//                    + sum_{m odd >= 3} (-1)^{(m+1)/2} 4m / (m^2 - 1) J_m ].
-// z >= 17.5: Hankel's asymptotic expansion
+// z < 40: piecewise Chebyshev expansions (hankel_table.h, unit intervals, 18 terms) of
+//   J0, J1 and of the regular parts of Neumann's expansions,
+//     R0 = Y0 - (2/pi)(ln(z/2) + gamma) J0,   R1 = Y1 - (2/pi)(ln(z/2) + gamma) J1 + 2/(pi z),
+//   so that Y0 and Y1 take one logarithm; the four series are summed together by
+//   Clenshaw's recurrence.
+// z >= 40: Hankel's asymptotic expansion
 //     H_nu(z) ~ sqrt(2/(pi z)) e^{i(z - nu pi/2 - pi/4)} sum_k i^k a_k(nu) / z^k,
 //     a_k(nu) = a_{k-1}(nu) (4 nu^2 - (2k-1)^2) / (8k),
-//   summed until the term falls below 1e-17 of the sum (at most 48 terms).
+//   summed until the term falls below 1e-17 (at most 48 terms).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void hankel01(double z, cplx* h0, cplx* h1) {
-  if (z < 17.5) {
-    // The loop is unrolled, so the coefficients 1/k and 4n/(n^2-1) are literals and all
-    // lanes of a warp step through the same n.
-    constexpr int n0 = 44;
-    double jp1 = 0.0, jn = 1e-30;  // J_{n+1}, J_n at n = n0
-    const double tz = 2.0 / z;
-    double norm = 0.0, sy0 = 0.0, sy1 = 0.0, j1 = 0.0;
+  if (z < (double)kHankelIntervals) {
+    const int iv = (int)z;
+    const double t = 2.0 * (z - (double)iv) - 1.0, t2 = 2.0 * t;
+    const double* c = kHankelCheb + (size_t)iv * 4 * kHankelDegree;
+    double b1[4] = {0.0, 0.0, 0.0, 0.0}, b2[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-    for (int n = n0; n >= 1; --n) {
-      if ((n & 1) == 0) {
-        const int k = n >> 1;
-        norm += 2.0 * jn;
-        sy0 += ((k & 1) ? -jn : jn) * (1.0 / (double)k);
-      } else if (n >= 3) {
-        const int e = (n + 1) >> 1;
-        const double cm = 4.0 * (double)n / ((double)n * n - 1.0);
-        sy1 += (e & 1) ? -cm * jn : cm * jn;
-      } else {
-        j1 = jn;
-      }
-      const double jm1 = (double)n * tz * jn - jp1;
-      jp1 = jn;
-      jn = jm1;
-      if (fabs(jn) > 1e200) {
-        const double sc = 1e-200;
-        jn *= sc; jp1 *= sc; norm *= sc; sy0 *= sc; sy1 *= sc; j1 *= sc;
+    for (int k = kHankelDegree - 1; k >= 1; --k) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const double b0 = fma(t2, b1[f], __ldg(c + f * kHankelDegree + k) - b2[f]);
+        b2[f] = b1[f];
+        b1[f] = b0;
       }
     }
-    double j0 = jn;
-    norm += j0;
-    double inv = 1.0 / norm;
-    j0 *= inv; j1 *= inv; sy0 *= inv; sy1 *= inv;
-    double lg = log(0.5 * z) + HBS_EULER_GAMMA;
-    double y0 = (2.0 / HBS_PI) * (lg * j0 - 2.0 * sy0);
-    double y1 = (2.0 / HBS_PI) * (-j0 / z + lg * j1 - j1 + sy1);
-    *h0 = cmk(j0, y0);
-    *h1 = cmk(j1, y1);
+    double v[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) v[f] = fma(t, b1[f], __ldg(c + f * kHankelDegree) - b2[f]);
+    const double lg = (2.0 / HBS_PI) * (log(0.5 * z) + HBS_EULER_GAMMA);
+    *h0 = cmk(v[0], fma(lg, v[0], v[2]));
+    *h1 = cmk(v[1], fma(lg, v[1], v[3]) - 2.0 / (HBS_PI * z));
   } else {
     // unrolled: the ratios (4 nu^2 - (2k-1)^2) / (8k) are literals
     const double iz = 1.0 / z;

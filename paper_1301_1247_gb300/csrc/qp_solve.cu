@@ -304,11 +304,11 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   const double osc = perim * std::max(omega, h.cK) / (2.0 * M_PI);
   int ns_want = std::max(2048, (int)std::ceil(16.0 * osc / 256.0) * 256);
   const int ns = (int)std::min<int64_t>(N, std::min(ns_want, 16384));
-  std::vector<int64_t> hsub(ns), hsub2(ns);
-  for (int i = 0; i < ns; ++i) {
-    hsub[i] = (int64_t)((double)i * N / ns);
-    hsub2[i] = std::min<int64_t>(N - 1, (int64_t)(((double)i + 0.5) * N / ns));
-  }
+  // check sample: half as many nodes, each half-way between two nodes of the subsample
+  const int ns2 = std::max(1, ns / 2);
+  std::vector<int64_t> hsub(ns), hsub2(ns2);
+  for (int i = 0; i < ns; ++i) hsub[i] = (int64_t)((double)i * N / ns);
+  for (int i = 0; i < ns2; ++i) hsub2[i] = std::min<int64_t>(N - 1, (int64_t)(((double)(2 * i) + 0.5) * N / ns));
   DevBuf<int64_t> dsub, dsub2;
   dsub.upload(hsub, s);
   dsub2.upload(hsub2, s);
@@ -330,13 +330,13 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   for (Family& f : fams) {
     const int ncols = f.ncols;
     f.A.alloc((size_t)ns * ncols);
-    f.A2.alloc((size_t)ns * ncols);
+    f.A2.alloc((size_t)ns2 * ncols);
     {
       prof::KScope _ks("k_fill_family_sub", s);
       k_fill_family_sub<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(g, cp, M, d, S, h.y0, f.family, dsub.get(), ns,
                                                                       ncols, f.A.get(), ns);
-      k_fill_family_sub<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(g, cp, M, d, S, h.y0, f.family, dsub2.get(), ns,
-                                                                      ncols, f.A2.get(), ns);
+      k_fill_family_sub<<<grid_1d((int64_t)ns2 * ncols), 256, 0, s>>>(g, cp, M, d, S, h.y0, f.family, dsub2.get(),
+                                                                       ns2, ncols, f.A2.get(), ns2);
     }
     HBS_LAUNCH_CHECK("k_fill_family_sub");
     f.perm.alloc(ncols);
@@ -367,17 +367,17 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     drec.upload(rec, s);
     DevBuf<int> dperm;
     dperm.upload(hperm, s);
-    DevBuf<cplx> B2((size_t)ns * ncols);
+    DevBuf<cplx> B2((size_t)ns2 * ncols);
     {
       prof::KScope _ks("k_expand_cols", s);
-      k_expand_cols<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(f.A2.get(), ns, ns, drec.get(), ncols, Tout.get(), r,
-                                                                  0, dperm.get(), B2.get(), ns);
+      k_expand_cols<<<grid_1d((int64_t)ns2 * ncols), 256, 0, s>>>(f.A2.get(), ns2, ns2, drec.get(), ncols, Tout.get(),
+                                                                   r, 0, dperm.get(), B2.get(), ns2);
     }
     DevBuf<double> acc(2);
     HBS_CUDA(cudaMemsetAsync(acc.get(), 0, 2 * sizeof(double), s));
     {
       prof::KScope _ks("k_diff_norm2", s);
-      k_diff_norm2<<<grid_1d((int64_t)ns * ncols), 256, 0, s>>>(B2.get(), ns, f.A2.get(), ns, ns, ncols, acc.get());
+      k_diff_norm2<<<grid_1d((int64_t)ns2 * ncols), 256, 0, s>>>(B2.get(), ns2, f.A2.get(), ns2, ns2, ncols, acc.get());
     }
     auto ha = acc.download(s);
     const double res = ha[1] > 0 ? std::sqrt(ha[0] / ha[1]) : 0.0;

@@ -160,6 +160,17 @@ __device__ __forceinline__ void df_split_bits(double x, float& hi, float& lo) {
   lo = __uint_as_float(sgn | ((unsigned int)fel << 23) | (q & 0x7FFFFFu));
 }
 
+// float -> double with integer operations only (exact for normal floats; subnormal floats,
+// below 1.2e-38, become 0).
+__device__ __forceinline__ double f2d_bits(float x) {
+  const unsigned int u = __float_as_uint(x);
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned int e = (u >> 23) & 0xFFu;
+  if (e == 0u) return __longlong_as_double((long long)sgn);
+  const unsigned long long de = e == 0xFFu ? 0x7FFull : (unsigned long long)(e - 127u + 1023u);
+  return __longlong_as_double((long long)(sgn | (de << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
 __device__ __forceinline__ dfc to_dfc_bits(cplx v) {
   dfc r;
   df_split_bits(v.x, r.rh, r.rl);
@@ -232,6 +243,10 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* 
       }
     __syncthreads();
   }
+  const bool unit_alpha = jb.alpha.x == 1.0 && jb.alpha.y == 0.0;
+  const bool minus_alpha = jb.alpha.x == -1.0 && jb.alpha.y == 0.0;
+  const bool zero_beta = jb.beta.x == 0.0 && jb.beta.y == 0.0;
+  const bool unit_beta = jb.beta.x == 1.0 && jb.beta.y == 0.0;
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
 #pragma unroll
@@ -240,8 +255,17 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* 
       if (gr < m && gc < n) {
         cplx* c = jb.C + (int64_t)gc * jb.ldc + gr;
         const dfc& q = acc[a][b];
-        cplx v = cmul(jb.alpha, cmk((double)q.rh + (double)q.rl, (double)q.ih + (double)q.il));
-        if (jb.beta.x != 0.0 || jb.beta.y != 0.0) v = cfma(jb.beta, *c, v);
+        // the common (alpha, beta) = (1, 0) and (-1, 1) take two or four FP64 adds only
+        const cplx sum = cmk(f2d_bits(q.rh) + f2d_bits(q.rl), f2d_bits(q.ih) + f2d_bits(q.il));
+        cplx v;
+        if (unit_alpha && zero_beta) {
+          v = sum;
+        } else if (minus_alpha && unit_beta) {
+          v = csub(*c, sum);
+        } else {
+          v = cmul(jb.alpha, sum);
+          if (!zero_beta) v = cfma(jb.beta, *c, v);
+        }
         *c = v;
       }
     }
