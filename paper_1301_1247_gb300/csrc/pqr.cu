@@ -46,6 +46,8 @@ struct PqrJob {
   int* perm;
   cplx* T;
   cplx* r11r;  // k x k row-major copy of R11 (scratch for the triangular solves)
+  cplx* r11c;  // k x k column-major copy of R11
+  cplx* invd;  // 1 / R_ii (k)
   int* pos;    // n: position of each column in perm (scratch)
 };
 
@@ -273,7 +275,68 @@ __global__ void __launch_bounds__(kNT) k_pqr_finish(const PqrJob* jobs) {
     if (l == i) v = jb.beta[i];
     else if (l > i) v = jb.A[(int64_t)jb.piv[l] * m + i];
     jb.r11r[e] = v;
+    jb.r11c[(int64_t)l * k + i] = v;
+    if (l == i) jb.invd[i] = cdiv(cmk(1.0, 0.0), v);
   }
+}
+
+// x = R^{-1} b for upper-triangular R (k <= 32 KR) stored column-major (Rc[i k + r] =
+// R(r, i)) with its inverse diagonal, one warp: the column is held in registers (row r in
+// lane r % 32, slot r / 32) and x_i is broadcast by shuffle, so the substitution never
+// waits on memory.  x is written at the end (it may alias b).
+template <int KR>
+__device__ __forceinline__ void tsolve_reg_col(const cplx* Rc, const cplx* invd, int k, const cplx* b, cplx* x,
+                                               int lane) {
+  cplx w[KR];
+#pragma unroll
+  for (int q = 0; q < KR; ++q) {
+    const int r = lane + 32 * q;
+    w[q] = r < k ? b[r] : cmk(0.0, 0.0);
+  }
+#pragma unroll
+  for (int qb = KR - 1; qb >= 0; --qb) {
+    for (int ii = 31; ii >= 0; --ii) {
+      const int i = qb * 32 + ii;
+      if (i >= k) continue;
+      cplx xi = cmk(__shfl_sync(0xffffffffu, w[qb].x, ii), __shfl_sync(0xffffffffu, w[qb].y, ii));
+      xi = cmul(xi, invd[i]);
+      if (lane == ii) w[qb] = xi;
+      const cplx* ri = Rc + (int64_t)i * k;
+#pragma unroll
+      for (int q = 0; q <= qb; ++q) {
+        const int r = lane + 32 * q;
+        if (r < i) w[q] = cfms(ri[r], xi, w[q]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < KR; ++q) {
+    const int r = lane + 32 * q;
+    if (r < k) x[r] = w[q];
+  }
+}
+
+template <int KR>
+__global__ void __launch_bounds__(256) k_tsolve_cols_reg(const cplx* Rc, const cplx* invd, int k, const cplx* B,
+                                                         int64_t ldb, int64_t ncols, cplx* X, int64_t ldx) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp; c < ncols; c += nwarps) tsolve_reg_col<KR>(Rc, invd, k, B + c * ldb, X + c * ldx, lane);
+}
+
+// The pqr T solves with register-resident columns (every matrix of the batch with k <= 32 KR).
+template <int KR>
+__global__ void __launch_bounds__(256) k_pqr_tsolve_reg(const PqrJob* jobs) {
+  const PqrJob jb = jobs[blockIdx.y];
+  const int k = jb.st->rank;
+  const int64_t nc = jb.n - k;
+  if (k <= 0 || nc <= 0 || jb.T == nullptr) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp; c < nc; c += nwarps)
+    tsolve_reg_col<KR>(jb.r11c, jb.invd, k, jb.A + (int64_t)jb.perm[k + c] * jb.m, jb.T + c * (int64_t)k, lane);
 }
 
 // Per matrix: T(:, c) = R11^{-1} R12(:, c), R12(:, c) = rows 0..k-1 of physical column
@@ -304,49 +367,6 @@ __global__ void __launch_bounds__(256) k_tsolve_cols(const cplx* R, int k, const
 }
 
 namespace {
-
-// X(:, c) = R^{-1} B(:, c) for upper-triangular R (k <= 32 KR) stored column-major
-// (Rc[i k + r] = R(r, i)) with its inverse diagonal: one warp per column, the column
-// held in registers (row r in lane r % 32, slot r / 32) and x_i broadcast by shuffle,
-// so the substitution never waits on memory.  X may alias B.
-template <int KR>
-__global__ void __launch_bounds__(256) k_tsolve_cols_reg(const cplx* Rc, const cplx* invd, int k, const cplx* B,
-                                                         int64_t ldb, int64_t ncols, cplx* X, int64_t ldx) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = warp; c < ncols; c += nwarps) {
-    const cplx* b = B + c * ldb;
-    cplx w[KR];
-#pragma unroll
-    for (int q = 0; q < KR; ++q) {
-      const int r = lane + 32 * q;
-      w[q] = r < k ? b[r] : cmk(0.0, 0.0);
-    }
-#pragma unroll
-    for (int qb = KR - 1; qb >= 0; --qb) {
-      for (int ii = 31; ii >= 0; --ii) {
-        const int i = qb * 32 + ii;
-        if (i >= k) continue;
-        cplx xi = cmk(__shfl_sync(0xffffffffu, w[qb].x, ii), __shfl_sync(0xffffffffu, w[qb].y, ii));
-        xi = cmul(xi, invd[i]);
-        if (lane == ii) w[qb] = xi;
-        const cplx* ri = Rc + (int64_t)i * k;
-#pragma unroll
-        for (int q = 0; q <= qb; ++q) {
-          const int r = lane + 32 * q;
-          if (r < i) w[q] = cfms(ri[r], xi, w[q]);
-        }
-      }
-    }
-    cplx* x = X + c * ldx;
-#pragma unroll
-    for (int q = 0; q < KR; ++q) {
-      const int r = lane + 32 * q;
-      if (r < k) x[r] = w[q];
-    }
-  }
-}
 
 // R11 column-major and 1/R_ii from a factorization.
 __global__ void k_r11_cols(const cplx* A, int64_t m, const int* piv, const cplx* beta, int k, cplx* Rc, cplx* invd) {
@@ -517,7 +537,7 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
   out.tau.alloc(ktot);
   DevBuf<PqrState> st(nj);
   DevBuf<GridSync> gs(1);
-  DevBuf<cplx> r11(std::max<int64_t>(r11tot, 1));
+  DevBuf<cplx> r11(std::max<int64_t>(r11tot, 1)), r11c(std::max<int64_t>(r11tot, 1)), invd(std::max<int64_t>(ktot, 1));
   HBS_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(PqrState) * nj, s));
   HBS_CUDA(cudaMemsetAsync(gs.get(), 0, sizeof(GridSync), s));
   std::vector<PqrJob> jobs(nj);
@@ -527,7 +547,8 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
     const auto& sp = specs[j];
     jobs[j] = {sp.A, sp.m, sp.n, sp.kcap, b0, nb[j], nrm.get() + o, nref.get() + o,
                out.piv.get() + out.koff[j], out.beta.get() + out.koff[j], out.v0.get() + out.koff[j],
-               out.tau.get() + out.koff[j], st.get() + j, sp.perm, sp.T, r11.get() + r11off[j], pos.get() + o};
+               out.tau.get() + out.koff[j], st.get() + j, sp.perm, sp.T, r11.get() + r11off[j],
+               r11c.get() + r11off[j], invd.get() + out.koff[j], pos.get() + o};
     o += sp.n;
     b0 += nb[j];
   }
@@ -546,8 +567,20 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
     HBS_CUDA(cudaLaunchCooperativeKernel((const void*)k_pqr, dim3(G), dim3(kNT), args, smem, s));
   }
   HBS_LAUNCH_CHECK("k_pqr");
+  std::vector<PqrState> hs(nj);
+  GridSync hg{};
+  HBS_CUDA(cudaMemcpyAsync(hs.data(), st.get(), sizeof(PqrState) * nj, cudaMemcpyDeviceToHost, s));
+  HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+  HBS_CUDA(cudaStreamSynchronize(s));
+  if (hg.timed_out) throw Error(HBS_ERR_TIMEOUT, "persistent QR: a grid barrier wait gave up");
+  int kmax = 0;
   int64_t nmax = 0;
-  for (const auto& sp : specs) nmax = std::max(nmax, sp.n);
+  for (int j = 0; j < nj; ++j) {
+    out.rank[j] = hs[j].rank;
+    if (hs[j].capped) throw Error(HBS_ERR_RANK, "interpolative decomposition rank exceeds the supported maximum");
+    kmax = std::max(kmax, hs[j].rank);
+    nmax = std::max(nmax, specs[j].n);
+  }
   {
     prof::KScope _ks("k_pqr_finish", s);
     k_pqr_finish<<<dim3(8, nj), kNT, 0, s>>>(dj.get());
@@ -555,19 +588,21 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
   {
     prof::KScope _ks("k_pqr_tsolve", s);
     const int bx = (int)std::max<int64_t>(1, std::min<int64_t>(1216 / nj + 1, (nmax + kNW - 1) / kNW));
-    k_pqr_tsolve<<<dim3(bx, nj), kNT, 0, s>>>(dj.get());
+    const dim3 grid(bx, nj);
+    switch ((kmax + 31) / 32) {
+      case 0:
+      case 1: k_pqr_tsolve_reg<1><<<grid, 256, 0, s>>>(dj.get()); break;
+      case 2: k_pqr_tsolve_reg<2><<<grid, 256, 0, s>>>(dj.get()); break;
+      case 3: k_pqr_tsolve_reg<3><<<grid, 256, 0, s>>>(dj.get()); break;
+      case 4: k_pqr_tsolve_reg<4><<<grid, 256, 0, s>>>(dj.get()); break;
+      case 5: k_pqr_tsolve_reg<5><<<grid, 256, 0, s>>>(dj.get()); break;
+      case 6: k_pqr_tsolve_reg<6><<<grid, 256, 0, s>>>(dj.get()); break;
+      case 7: k_pqr_tsolve_reg<7><<<grid, 256, 0, s>>>(dj.get()); break;
+      case 8: k_pqr_tsolve_reg<8><<<grid, 256, 0, s>>>(dj.get()); break;
+      default: k_pqr_tsolve<<<grid, kNT, 0, s>>>(dj.get()); break;
+    }
   }
   HBS_LAUNCH_CHECK("k_pqr_finish");
-  std::vector<PqrState> hs(nj);
-  GridSync hg{};
-  HBS_CUDA(cudaMemcpyAsync(hs.data(), st.get(), sizeof(PqrState) * nj, cudaMemcpyDeviceToHost, s));
-  HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));
-  HBS_CUDA(cudaStreamSynchronize(s));
-  if (hg.timed_out) throw Error(HBS_ERR_TIMEOUT, "persistent QR: a grid barrier wait gave up");
-  for (int j = 0; j < nj; ++j) {
-    out.rank[j] = hs[j].rank;
-    if (hs[j].capped) throw Error(HBS_ERR_RANK, "interpolative decomposition rank exceeds the supported maximum");
-  }
   // account the factorization's flops (16 m n per step on the active columns)
   double fl = 0.0;
   for (int j = 0; j < nj; ++j) {
