@@ -20,6 +20,11 @@ bool& gemm_double_float() {
   return df;
 }
 
+std::mutex& coop_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
 cudaStream_t& current_stream() {
   static thread_local cudaStream_t s = nullptr;
   return s;

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -94,6 +95,11 @@ void init_memory_pool();
 // Arithmetic of the library's batched GEMMs on this thread: FP64 (false) or double-float
 // (true), set for the duration of a call from the handle's precision option.
 bool& gemm_double_float();
+
+// Held from the launch of a cooperative (grid-barrier) kernel until the host has seen it
+// finish: at most one such kernel is in flight on the device, whatever the number of
+// threads and streams using the library.
+std::mutex& coop_mutex();
 struct GemmModeScope {
   bool prev;
   explicit GemmModeScope(bool df) : prev(gemm_double_float()) { gemm_double_float() = df; }

@@ -160,12 +160,12 @@ __global__ void k_pgj_copy(const PgjJob* jobs) {
 }  // namespace
 
 static int pgj_grid(size_t smem) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  static const int sms = [] {
+    int dev = 0, sm = 0;
     HBS_CUDA(cudaGetDevice(&dev));
-    HBS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
+    HBS_CUDA(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
+    return sm;
+  }();
   if (smem > 48 * 1024)
     HBS_CUDA(cudaFuncSetAttribute(k_pgj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -215,15 +215,23 @@ void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, con
   }
   DevBuf<PgjJob> dj;
   dj.upload(jobs, s);
+  std::vector<int> hs(nj);
+  GridSync hg{};
   {
     const PgjJob* a0 = dj.get();
     int a1 = nj, a2 = nmax;
     GridSync* a3 = gs.get();
     void* args[] = {&a0, &a1, &a2, &a3};
-    prof::KScope _ks("k_pgj", s, fl, 0.0);
-    HBS_CUDA(cudaLaunchCooperativeKernel((const void*)k_pgj, dim3(G), dim3(kNT), args, smem, s));
+    std::lock_guard<std::mutex> lock(coop_mutex());
+    {
+      prof::KScope _ks("k_pgj", s, fl, 0.0);
+      HBS_CUDA(cudaLaunchCooperativeKernel((const void*)k_pgj, dim3(G), dim3(kNT), args, smem, s));
+    }
+    HBS_LAUNCH_CHECK("k_pgj");
+    HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+    HBS_CUDA(cudaStreamSynchronize(s));
   }
-  HBS_LAUNCH_CHECK("k_pgj");
+  if (hg.timed_out) throw Error(HBS_ERR_TIMEOUT, "persistent Gauss-Jordan: a grid barrier wait gave up");
   {
     prof::KScope _ks("k_pgj_unpivot", s);
     const size_t sm = (size_t)nmax * sizeof(int);
@@ -233,12 +241,8 @@ void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, con
     k_pgj_copy<<<dim3(std::max(1, 1216 / nj), nj), 256, 0, s>>>(dj.get());
   }
   HBS_LAUNCH_CHECK("k_pgj_unpivot");
-  std::vector<int> hs(nj);
-  GridSync hg{};
   HBS_CUDA(cudaMemcpyAsync(hs.data(), sing.get(), sizeof(int) * nj, cudaMemcpyDeviceToHost, s));
-  HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));
   HBS_CUDA(cudaStreamSynchronize(s));
-  if (hg.timed_out) throw Error(HBS_ERR_TIMEOUT, "persistent Gauss-Jordan: a grid barrier wait gave up");
   for (int j = 0; j < nj; ++j)
     if (hs[j]) throw Error(HBS_WARN_ILLCOND, std::string("singular block in ") + what);
 }

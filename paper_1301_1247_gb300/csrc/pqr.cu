@@ -479,12 +479,12 @@ __global__ void k_set_unit_cols(cplx* X, int k, const int64_t* idx) {
 }
 
 static int pqr_grid(size_t smem) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  static const int sms = [] {
+    int dev = 0, sm = 0;
     HBS_CUDA(cudaGetDevice(&dev));
-    HBS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
+    HBS_CUDA(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
+    return sm;
+  }();
   if (smem > 48 * 1024)
     HBS_CUDA(cudaFuncSetAttribute(k_pqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -554,24 +554,27 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
   }
   DevBuf<PqrJob> dj;
   dj.upload(jobs, s);
-  {
-    const PqrJob* a0 = dj.get();
-    int a1 = nj;
-    double* a2 = pv.get();
-    int* a3 = pi.get();
-    GridSync* a4 = gs.get();
-    double a5 = tol;
-    int a6 = vcap;
-    void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};
-    prof::KScope _ks("k_pqr", s);
-    HBS_CUDA(cudaLaunchCooperativeKernel((const void*)k_pqr, dim3(G), dim3(kNT), args, smem, s));
-  }
-  HBS_LAUNCH_CHECK("k_pqr");
+  const PqrJob* a0 = dj.get();
+  int a1 = nj;
+  double* a2 = pv.get();
+  int* a3 = pi.get();
+  GridSync* a4 = gs.get();
+  double a5 = tol;
+  int a6 = vcap;
+  void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};
   std::vector<PqrState> hs(nj);
   GridSync hg{};
-  HBS_CUDA(cudaMemcpyAsync(hs.data(), st.get(), sizeof(PqrState) * nj, cudaMemcpyDeviceToHost, s));
-  HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));
-  HBS_CUDA(cudaStreamSynchronize(s));
+  {
+    std::lock_guard<std::mutex> lock(coop_mutex());
+    {
+      prof::KScope _ks("k_pqr", s);
+      HBS_CUDA(cudaLaunchCooperativeKernel((const void*)k_pqr, dim3(G), dim3(kNT), args, smem, s));
+    }
+    HBS_LAUNCH_CHECK("k_pqr");
+    HBS_CUDA(cudaMemcpyAsync(hs.data(), st.get(), sizeof(PqrState) * nj, cudaMemcpyDeviceToHost, s));
+    HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+    HBS_CUDA(cudaStreamSynchronize(s));
+  }
   if (hg.timed_out) throw Error(HBS_ERR_TIMEOUT, "persistent QR: a grid barrier wait gave up");
   int kmax = 0;
   int64_t nmax = 0;

@@ -21,6 +21,7 @@
 
 #include "dense_kernels.cuh"
 #include "profile.hpp"
+#include "gridsync.cuh"
 #include "qp_kernels.cuh"
 
 namespace hbs {
@@ -905,6 +906,214 @@ __global__ void __launch_bounds__(NT) k_schur_solve(Dims D, const GroupJob* grou
   if (tid == 0) illcond[blockIdx.x] = (pmin <= 1e-28 * pmax) ? 1 : 0;
 }
 
+// The same blocked LU on CL CTAs per Bloch group (a cooperative launch over all groups):
+// CTA 0 of the group factors each panel while the others wait at a grid barrier, then all
+// CL CTAs share the U12 columns and the trailing-update tiles, and the back substitution's
+// right-hand sides.  Three bounded grid barriers per panel (all groups advance together;
+// `npan` is the largest panel count).  Used when the groups are fewer than the SMs, so
+// that every SM takes part.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* groups, int ng, int CL, int npan,
+                                                   cplx* Spool, cplx* Rpool, int* illcond, GridSync* gs) {
+  constexpr int NB = 16, TM = 64;
+  static_assert(NT == 256, "16 x 16 threads per trailing tile");
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  __shared__ cplx sh_ip;
+  __shared__ cplx Ls[NB][TM + 1];
+  __shared__ cplx Us[NB][TM + 1];
+  __shared__ cplx L11[NB][NB + 1];
+  const int g = blockIdx.x / CL, rank = blockIdx.x % CL;
+  const bool act = g < ng;
+  int n = 0, q = 0;
+  cplx* A = nullptr;
+  cplx* B = nullptr;
+  if (act) {
+    const GroupJob G = groups[g];
+    n = G.nsys;
+    q = G.q;
+    A = Spool + G.s_off;
+    B = Rpool + G.r_off;
+  }
+  const int nc = n + q;
+  auto col = [&](int j) -> cplx* { return j < n ? A + (int64_t)j * n : B + (int64_t)(j - n) * n; };
+  const int tid = threadIdx.x;
+  double pmax = 0.0, pmin = 1e300;
+  for (int pn = 0; pn < npan; ++pn) {
+    const int k0 = pn * NB;
+    const bool live = act && k0 < n;
+    const int nb = live ? min(NB, n - k0) : 0;
+    if (live && rank == 0) {
+      for (int c = k0; c < k0 + nb; ++c) {
+        cplx* ac = A + (int64_t)c * n;
+        double best = -1.0;
+        int bi = 0x7fffffff;
+        for (int i = c + tid; i < n; i += NT) {
+          const double v = cabs2(ac[i]);
+          if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+        }
+        double pv;
+        int p;
+        block_argmax<NT>(best, bi, redv, redi, &pv, &p);
+        pmax = fmax(pmax, pv);
+        pmin = fmin(pmin, pv);
+        if (p != c) {
+          for (int j = tid; j < nc; j += NT) {
+            cplx* cj = col(j);
+            const cplx t = cj[c];
+            cj[c] = cj[p];
+            cj[p] = t;
+          }
+        }
+        __syncthreads();
+        if (tid == 0) {
+          const cplx dv = ac[c];
+          sh_ip = cabs2(dv) > 0.0 ? cdiv(cmk(1, 0), dv) : cmk(0, 0);
+        }
+        __syncthreads();
+        const cplx ip = sh_ip;
+        for (int i = c + 1 + tid; i < n; i += NT) ac[i] = cmul(ac[i], ip);
+        __syncthreads();
+        for (int j = c + 1; j < k0 + nb; ++j) {
+          cplx* aj = A + (int64_t)j * n;
+          const cplx ucj = aj[c];
+          for (int i = c + 1 + tid; i < n; i += NT) aj[i] = cfms(ac[i], ucj, aj[i]);
+        }
+        __syncthreads();
+      }
+    }
+    if (grid_sync_sum(gs, 0) < 0) return;
+    const int j0 = k0 + nb;
+    const bool upd = live && j0 < nc;
+    if (upd) {
+      for (int e = tid; e < NB * NB; e += NT) {
+        const int r = e % NB, cc = e / NB;
+        L11[r][cc] = (r < nb && cc < nb) ? A[(int64_t)(k0 + cc) * n + k0 + r] : cmk(0, 0);
+      }
+      __syncthreads();
+      for (int j = j0 + rank * NT + tid; j < nc; j += CL * NT) {
+        cplx* aj = col(j) + k0;
+        cplx u[NB];
+#pragma unroll
+        for (int r = 0; r < NB; ++r) u[r] = r < nb ? aj[r] : cmk(0, 0);
+#pragma unroll
+        for (int cc = 0; cc < NB; ++cc)
+#pragma unroll
+          for (int r = cc + 1; r < NB; ++r) u[r] = cfms(L11[r][cc], u[cc], u[r]);
+#pragma unroll
+        for (int r = 0; r < NB; ++r)
+          if (r < nb) aj[r] = u[r];
+      }
+    }
+    if (grid_sync_sum(gs, 0) < 0) return;
+    if (upd) {
+      const int rows = n - j0, cols = nc - j0;
+      const int nrt = (rows + TM - 1) / TM, nct = (cols + TM - 1) / TM;
+      const int tr = tid & 15, tc = tid >> 4;
+      for (int tt = rank; tt < nrt * nct; tt += CL) {
+        const int rt = (tt % nrt) * TM, ct = (tt / nrt) * TM;
+        for (int e = tid; e < TM * NB; e += NT) {
+          const int r = e % TM, kk = e / TM;
+          const int i = j0 + rt + r;
+          Ls[kk][r] = (i < n && kk < nb) ? A[(int64_t)(k0 + kk) * n + i] : cmk(0, 0);
+        }
+        for (int e = tid; e < TM * NB; e += NT) {
+          const int kk = e % NB, c = e / NB;
+          const int j = j0 + ct + c;
+          Us[kk][c] = (j < nc && kk < nb) ? col(j)[k0 + kk] : cmk(0, 0);
+        }
+        __syncthreads();
+        cplx acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = cmk(0, 0);
+        for (int kk = 0; kk < nb; ++kk) {
+          cplx la[4], ub[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) la[a] = Ls[kk][tr + 16 * a];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) ub[b] = Us[kk][tc + 16 * b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = cfma(la[a], ub[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int j = j0 + ct + tc + 16 * b;
+          if (j >= nc) continue;
+          cplx* cj = col(j);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int i = j0 + rt + tr + 16 * a;
+            if (i < n) cj[i] = csub(cj[i], acc[a][b]);
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (grid_sync_sum(gs, 0) < 0) return;
+  }
+  if (!act) return;
+  // back substitution, one right-hand side per warp of the group's CTAs
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int j = rank * (NT / 32) + warp; j < q; j += CL * (NT / 32)) {
+    cplx* b = B + (int64_t)j * n;
+    for (int i = n - 1; i >= 0; --i) {
+      cplx acc = cmk(0, 0);
+      for (int t = i + 1 + lane; t < n; t += 32) acc = cfma(A[(int64_t)t * n + i], b[t], acc);
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (lane == 0) b[i] = cdiv(csub(b[i], acc), A[(int64_t)i * n + i]);
+      __syncwarp();
+    }
+  }
+  if (rank == 0 && tid == 0) illcond[g] = (pmin <= 1e-28 * pmax) ? 1 : 0;
+}
+
+// Factor and solve every group's Schur system: CL CTAs per group in one cooperative launch
+// when the groups leave SMs idle, else one CTA per group.
+static void schur_solve(const Dims& D, const std::vector<GroupJob>& gjobs, const GroupJob* dg, cplx* Sp, cplx* Rp,
+                        int* ill, cudaStream_t s) {
+  const int ng = (int)gjobs.size();
+  // SM count and residency (thread-safe one-time initialization: solves may run concurrently)
+  static const std::pair<int, int> occ = [] {
+    int dev = 0, sm = 0, per = 0;
+    HBS_CUDA(cudaGetDevice(&dev));
+    HBS_CUDA(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
+    HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_schur_coop<256>, 256, 0));
+    return std::make_pair(sm, per);
+  }();
+  const int sms = occ.first, per_sm = occ.second;
+  const int CL = std::min(4, (sms * std::min(per_sm, 2)) / std::max(ng, 1));
+  if (CL < 2) {
+    k_schur_solve<256><<<ng, 256, 0, s>>>(D, dg, Sp, Rp, ill);
+    return;
+  }
+  int nmax = 0;
+  for (const auto& G : gjobs) nmax = std::max(nmax, G.nsys);
+  const int npan = (nmax + 15) / 16;
+  DevBuf<GridSync> gs(1);
+  HBS_CUDA(cudaMemsetAsync(gs.get(), 0, sizeof(GridSync), s));
+  Dims a0 = D;
+  const GroupJob* a1 = dg;
+  int a2 = ng, a3 = CL, a4 = npan;
+  cplx* a5 = Sp;
+  cplx* a6 = Rp;
+  int* a7 = ill;
+  GridSync* a8 = gs.get();
+  void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8};
+  std::lock_guard<std::mutex> lock(coop_mutex());
+  HBS_CUDA(cudaLaunchCooperativeKernel((const void*)k_schur_coop<256>, dim3(ng * CL), dim3(256), args, 0, s));
+  GridSync hg{};
+  HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+  HBS_CUDA(cudaStreamSynchronize(s));
+  if (hg.timed_out) throw Error(HBS_ERR_TIMEOUT, "Schur factorization: a grid barrier wait gave up");
+}
+
 struct AngleJob {
   int group;
   int col;            // index of this angle within its group
@@ -1361,7 +1570,7 @@ static void reduced_batch(Handle& h, std::vector<GroupJob>& gjobs, std::vector<s
       sfl += 8.0 / 3.0 * n * n * n + 8.0 * n * n * G.q;
     }
     prof::KScope _ks("k_schur_solve", s, sfl, 0.0);
-    k_schur_solve<256><<<ng, 256, 0, s>>>(DD, dg.get(), Sp.get(), Rp.get(), ill.get());
+    schur_solve(DD, gjobs, dg.get(), Sp.get(), Rp.get(), ill.get(), s);
   }
   HBS_LAUNCH_CHECK("k_schur_solve");
   ph.next("solve:bragg");
@@ -1734,7 +1943,7 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
     }
     {
       prof::KScope _ks("k_schur_solve", s, sfl, 0.0);
-      k_schur_solve<256><<<ng, 256, 0, s>>>(D, dg.get(), Sp.get(), Rp.get(), ill.get());
+      schur_solve(D, gjobs, dg.get(), Sp.get(), Rp.get(), ill.get(), s);
     }
     HBS_LAUNCH_CHECK("k_schur_solve");
     // ---- Bragg amplitudes
