@@ -36,6 +36,7 @@ struct PqrJob {
   int64_t m, n;
   int kcap;
   int b0, nb;  // CTA range of this matrix
+  int gw;      // warps per column (1, 2, 4, 8)
   double* nrm;
   double* nref;
   int* piv;
@@ -133,12 +134,72 @@ __device__ __forceinline__ double update_col_warp(cplx* aj, const cplx* vt, int6
   return t;
 }
 
+__device__ __forceinline__ void group_barrier(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// The same update by a group of GW warps (rows split over the group's 32 GW lanes): for the
+// top tree levels, whose few columns would otherwise leave most warps idle.  The group's
+// partial sums meet in shared memory (slot alternates per column) behind a named barrier.
+__device__ double update_col_group(cplx* aj, const cplx* vt, int64_t m, int64_t s, cplx v0, double tau, double nj,
+                                   double* nref_j, int gl, int GW, int grp, int wg, int lane, int slot, cplx* redc,
+                                   double* redn) {
+  const int64_t stride = 32 * GW;
+  const int base = slot * kNW + grp * GW;
+  const cplx ajs = aj[s];  // read by every warp before the group's first barrier
+  cplx r[kReg];
+  cplx w = cmk(0.0, 0.0);
+#pragma unroll
+  for (int q = 0; q < kReg; ++q) {
+    const int64_t i = s + 1 + gl + stride * q;
+    if (i < m) {
+      r[q] = aj[i];
+      w = cfma(cconj(vt[i - s - 1]), r[q], w);
+    }
+  }
+  for (int64_t i = s + 1 + gl + stride * kReg; i < m; i += stride) w = cfma(cconj(vt[i - s - 1]), aj[i], w);
+  w = warp_sum_c(w);
+  if (lane == 0) redc[base + wg] = w;
+  group_barrier(1 + grp, 32 * GW);
+  cplx tot = cmk(0.0, 0.0);
+  for (int k = 0; k < GW; ++k) tot = cadd(tot, redc[base + k]);
+  w = cscale(cfma(cconj(v0), ajs, tot), tau);
+  const cplx top = cfms(v0, w, ajs);
+#pragma unroll
+  for (int q = 0; q < kReg; ++q) {
+    const int64_t i = s + 1 + gl + stride * q;
+    if (i < m) {
+      r[q] = cfms(vt[i - s - 1], w, r[q]);
+      aj[i] = r[q];
+    }
+  }
+  for (int64_t i = s + 1 + gl + stride * kReg; i < m; i += stride) aj[i] = cfms(vt[i - s - 1], w, aj[i]);
+  double t = nj - cabs2(top);
+  if (t <= 0.0078125 * *nref_j) {  // uniform over the group
+    double q2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < kReg; ++q)
+      if (s + 1 + gl + stride * q < m) q2 += cabs2(r[q]);
+    for (int64_t i = s + 1 + gl + stride * kReg; i < m; i += stride) q2 += cabs2(aj[i]);
+    q2 = warp_sum(q2);
+    if (lane == 0) redn[base + wg] = q2;
+    group_barrier(1 + grp, 32 * GW);
+    t = 0.0;
+    for (int k = 0; k < GW; ++k) t += redn[base + k];
+    if (gl == 0) *nref_j = t;
+  }
+  if (gl == 0) aj[s] = top;
+  return t;
+}
+
 // pv / pi: 2 x gridDim.x partial maxima (parity of the step).
 __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, double* pv, int* pi, GridSync* gs, double tol,
                                              int vcap) {
   extern __shared__ cplx sv[];
   __shared__ double redv[32];
   __shared__ int redi[32];
+  __shared__ cplx redc[2 * kNW];
+  __shared__ double redn[2 * kNW];
   int jid = 0;
   while (jid + 1 < nj && jobs[jid + 1].b0 <= (int)blockIdx.x) ++jid;
   const PqrJob jb = jobs[jid];
@@ -147,6 +208,9 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
   const int64_t m = jb.m, n = jb.n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t gw = (int64_t)lb * kNW + warp, nw = (int64_t)jb.nb * kNW;
+  // column groups of GW warps (GW = 1: one warp per column)
+  const int GW = jb.gw, grp = warp / GW, wg = warp % GW, gl = wg * 32 + lane;
+  const int64_t gg = (int64_t)lb * (kNW / GW) + grp, ngrp = (int64_t)jb.nb * (kNW / GW);
   cplx* A = jb.A;
 
   // column norms and the first partial maxima (parity 0)
@@ -220,16 +284,33 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
       const cplx* vt = staged ? sv : ap + s + 1;
       double best = -1.0;
       int bi = 0x7fffffff;
-      for (int64_t j = gw; j < n; j += nw) {
-        const double nj = jb.nrm[j];
-        if (nj < 0.0) continue;  // an earlier pivot
-        if (j == p) {
-          if (lane == 0) jb.nrm[j] = -1.0;
-          continue;
+      if (GW == 1) {
+        for (int64_t j = gw; j < n; j += nw) {
+          const double nj = jb.nrm[j];
+          if (nj < 0.0) continue;  // an earlier pivot
+          if (j == p) {
+            if (lane == 0) jb.nrm[j] = -1.0;
+            continue;
+          }
+          const double t = update_col_warp(A + j * m, vt, m, s, v0, tau, nj, jb.nref + j, lane);
+          if (lane == 0) jb.nrm[j] = t;
+          if (better(t, (int)j, best, bi)) { best = t; bi = (int)j; }
         }
-        const double t = update_col_warp(A + j * m, vt, m, s, v0, tau, nj, jb.nref + j, lane);
-        if (lane == 0) jb.nrm[j] = t;
-        if (better(t, (int)j, best, bi)) { best = t; bi = (int)j; }
+      } else {
+        int slot = 0;
+        for (int64_t j = gg; j < n; j += ngrp) {
+          const double nj = jb.nrm[j];
+          if (nj < 0.0) continue;
+          if (j == p) {
+            if (gl == 0) jb.nrm[j] = -1.0;
+            continue;
+          }
+          const double t = update_col_group(A + j * m, vt, m, s, v0, tau, nj, jb.nref + j, gl, GW, grp, wg, lane,
+                                            slot, redc, redn);
+          slot ^= 1;
+          if (gl == 0) jb.nrm[j] = t;
+          if (better(t, (int)j, best, bi)) { best = t; bi = (int)j; }
+        }
       }
       double v;
       int ix;
@@ -545,7 +626,11 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
   int b0 = 0;
   for (int j = 0; j < nj; ++j) {
     const auto& sp = specs[j];
-    jobs[j] = {sp.A, sp.m, sp.n, sp.kcap, b0, nb[j], nrm.get() + o, nref.get() + o,
+    // warps per column: double while the column groups still cover every column and each
+    // lane keeps at least four rows
+    int gwv = 1;
+    while (gwv < 8 && (int64_t)nb[j] * (kNW / (2 * gwv)) >= sp.n && sp.m >= (int64_t)32 * (2 * gwv) * 4) gwv *= 2;
+    jobs[j] = {sp.A, sp.m, sp.n, sp.kcap, b0, nb[j], gwv, nrm.get() + o, nref.get() + o,
                out.piv.get() + out.koff[j], out.beta.get() + out.koff[j], out.v0.get() + out.koff[j],
                out.tau.get() + out.koff[j], st.get() + j, sp.perm, sp.T, r11.get() + r11off[j],
                r11c.get() + r11off[j], invd.get() + out.koff[j], pos.get() + o};
