@@ -70,7 +70,7 @@ __device__ __forceinline__ cplx csqrt_principal(cplx z) {
 // ---------------------------------------------------------------------------
 // Hankel functions of the first kind, orders 0 and 1, real argument z > 0.
 //
-// z < 40: piecewise Chebyshev expansions (hankel_table.h, unit intervals, 18 terms) of
+// z < 40: piecewise Chebyshev expansions (hankel_table.h, intervals of width 1/2, 11 terms) of
 //   J0, J1 and of the regular parts of Neumann's expansions,
 //     R0 = Y0 - (2/pi)(ln(z/2) + gamma) J0,   R1 = Y1 - (2/pi)(ln(z/2) + gamma) J1 + 2/(pi z),
 //   so that Y0 and Y1 take one logarithm; the four series are summed together by
@@ -81,9 +81,10 @@ __device__ __forceinline__ cplx csqrt_principal(cplx z) {
 //   summed until the term falls below 1e-17 (at most 48 terms).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void hankel01(double z, cplx* h0, cplx* h1) {
-  if (z < (double)kHankelIntervals) {
-    const int iv = (int)z;
-    const double t = 2.0 * (z - (double)iv) - 1.0, t2 = 2.0 * t;
+  if (z < (double)(kHankelIntervals / kHankelPerUnit)) {
+    const double zp = (double)kHankelPerUnit * z;  // exact (power of two)
+    const int iv = (int)zp;
+    const double t = 2.0 * (zp - (double)iv) - 1.0, t2 = 2.0 * t;
     const double* c = kHankelCheb + (size_t)iv * 4 * kHankelDegree;
     double b1[4] = {0.0, 0.0, 0.0, 0.0}, b2[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll

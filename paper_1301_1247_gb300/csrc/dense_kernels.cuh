@@ -45,6 +45,78 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
+// Sum over the block formed in warp 0 alone, so that the other warps issue no FP64
+// instructions for it: the values meet in shared memory (red: NT doubles), lane l of
+// warp 0 adds those of threads l, l + 32, ... and a butterfly finishes.  The sum is
+// returned in every lane of warp 0 (other threads get an unspecified value).  Contains
+// one __syncthreads; red may be reused after the caller's next barrier.
+template <int NT>
+__device__ __forceinline__ double block_sum_warp0(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) t += red[threadIdx.x + 32 * k];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
+// Householder reflector H = I - tau v v^H with v = (v0, x_1, x_2, ...) mapping
+// x = (x0, x_1, ...) to (beta, 0, ...), beta = -(x0/|x0|) ||x|| (sig = sum_{i>0} |x_i|^2).
+__device__ __forceinline__ void householder_scalars(cplx x0, double sig, cplx* v0, cplx* beta, double* tau) {
+  const double ax0 = cabs1(x0);
+  const double xn = sqrt(ax0 * ax0 + sig);
+  const cplx ph = ax0 > 0.0 ? cmk(x0.x / ax0, x0.y / ax0) : cmk(1.0, 0.0);
+  *beta = cmk(-ph.x * xn, -ph.y * xn);
+  *v0 = csub(x0, *beta);
+  const double vv = cabs2(*v0) + sig;
+  *tau = vv > 0.0 ? 2.0 / vv : 0.0;
+}
+
+// Pivot searches compare squared moduli as IEEE-754 bit patterns read as signed 64-bit
+// integers: for non-negative doubles the order is the same, and a -1 marker (an
+// eliminated column) sorts below all of them, so the search takes exactly the decisions
+// of a floating-point search while leaving the FP64 pipe (1/64 of the FP32 rate on
+// GB300; its instructions cost the same with one active lane as with 32) to the updates.
+__device__ __forceinline__ long long nkey(double v) { return __double_as_longlong(v); }
+
+__device__ __forceinline__ bool better(long long v, int i, long long bv, int bi) {
+  return v > bv || (v == bv && i < bi);
+}
+
+constexpr long long kNoKey = (long long)0xBFF0000000000000ull;  // bits of -1.0
+
+// Block-wide (key, index) maximum, lowest index on ties, in every thread.
+template <int NT>
+__device__ __forceinline__ void block_argmax_key(long long v, int idx, long long* redv, int* redi, long long* outv,
+                                                 int* outi) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (better(v2, i2, v, idx)) { v = v2; idx = i2; }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) { redv[warp] = v; redi[warp] = idx; }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    long long t = threadIdx.x < NT / 32 ? redv[threadIdx.x] : kNoKey;
+    int ti = threadIdx.x < NT / 32 ? redi[threadIdx.x] : 0x7fffffff;
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long t2 = __shfl_xor_sync(0xffffffffu, t, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, ti, o);
+      if (better(t2, i2, t, ti)) { t = t2; ti = i2; }
+    }
+    if (threadIdx.x == 0) { redv[0] = t; redi[0] = ti; }
+  }
+  __syncthreads();
+  *outv = redv[0];
+  *outi = redi[0];
+  __syncthreads();
+}
+
 // Returns (max value, lowest index attaining it) over the block.
 template <int NT>
 __device__ __forceinline__ void block_argmax(double v, int idx, double* redv, int* redi, double* outv,
@@ -85,8 +157,9 @@ __device__ __forceinline__ void block_argmax(double v, int idx, double* redv, in
 template <int NT>
 __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, int* rank_out, double tol, int kmax) {
   extern __shared__ double smem[];
-  __shared__ double redv[32];
+  __shared__ long long redv[32];
   __shared__ int redi[32];
+  __shared__ double redsig[NT];
   __shared__ cplx sh_v0;
   __shared__ double sh_tau;
 
@@ -111,20 +184,25 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, int* rank_out,
   __syncthreads();
 
   const int kcap = min(min(m, n), kmax);
-  double r00 = 0.0;
+  double r00 = 0.0, thr2 = 0.0;
   int rank = 0;
   for (int s = 0; s < kcap; ++s) {
-    double best = -1.0;
+    long long best = kNoKey;
     int bi = 0x7fffffff;
     for (int j = s + tid; j < n; j += NT) {
-      double v = nrm[j];
-      if (v > best || (v == best && j < bi)) { best = v; bi = j; }
+      const long long v = nkey(nrm[j]);
+      if (better(v, j, best, bi)) { best = v; bi = j; }
     }
-    double pv;
+    long long kv;
     int p;
-    block_argmax<NT>(best, bi, redv, redi, &pv, &p);
-    if (s == 0) r00 = sqrt(pv);
-    if (!(r00 > 0.0) || sqrt(pv) <= tol * r00) break;
+    block_argmax_key<NT>(best, bi, redv, redi, &kv, &p);
+    const double pv = __longlong_as_double(kv);
+    if (s == 0) {
+      r00 = sqrt(pv);
+      thr2 = (tol * r00) * (tol * r00);
+    }
+    // |R_ss| <= tol |R_00|, compared squared
+    if (!(r00 > 0.0) || !(pv >= 0.0) || pv <= thr2) break;
     // swap columns s and p
     if (p != s) {
       cplx* cs = A + (int64_t)s * m;
@@ -141,17 +219,13 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, int* rank_out,
     cplx* cs = A + (int64_t)s * m;
     double sig = 0.0;
     for (int i = s + 1 + tid; i < m; i += NT) sig += cabs2(cs[i]);
-    sig = block_sum<NT>(sig, redv);
+    sig = block_sum_warp0<NT>(sig, redsig);
     if (tid == 0) {
-      cplx x0 = cs[s];
-      double ax0 = cabs1(x0);
-      double xn = sqrt(ax0 * ax0 + sig);
-      cplx ph = ax0 > 0.0 ? cmk(x0.x / ax0, x0.y / ax0) : cmk(1.0, 0.0);
-      cplx beta = cmk(-ph.x * xn, -ph.y * xn);
-      cplx v0 = csub(x0, beta);
-      double vv = cabs2(v0) + sig;
+      cplx v0, beta;
+      double tau;
+      householder_scalars(cs[s], sig, &v0, &beta, &tau);
       sh_v0 = v0;
-      sh_tau = vv > 0.0 ? 2.0 / vv : 0.0;
+      sh_tau = tau;
       cs[s] = beta;  // R_ss
     }
     __syncthreads();
@@ -216,7 +290,7 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, int* rank_out,
 // ---------------------------------------------------------------------------
 template <int NT>
 __global__ void __launch_bounds__(NT) k_gj_inverse(const InvJob* jobs, int* flag_out) {
-  __shared__ double redv[32];
+  __shared__ long long redv[32];
   __shared__ int redi[32];
   __shared__ cplx sh_piv;
   const InvJob jb = jobs[blockIdx.x];
@@ -226,15 +300,16 @@ __global__ void __launch_bounds__(NT) k_gj_inverse(const InvJob* jobs, int* flag
   const int tid = threadIdx.x;
   int bad = 0;
   for (int c = 0; c < n; ++c) {
-    double best = -1.0;
+    long long best = kNoKey;
     int bi = 0x7fffffff;
     for (int i = c + tid; i < n; i += NT) {
-      double v = cabs2(A[(int64_t)c * n + i]);
-      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+      const long long v = nkey(cabs2(A[(int64_t)c * n + i]));
+      if (better(v, i, best, bi)) { best = v; bi = i; }
     }
-    double pv;
+    long long kv;
     int p;
-    block_argmax<NT>(best, bi, redv, redi, &pv, &p);
+    block_argmax_key<NT>(best, bi, redv, redi, &kv, &p);
+    const double pv = __longlong_as_double(kv);
     if (tid == 0) piv[c] = p;
     if (!(pv > 0.0)) { bad = 1; p = c; }
     if (p != c) {

@@ -44,7 +44,7 @@ __device__ __forceinline__ cplx final_pivot_col(const cplx* u, int i, int c, cpl
 // smem: 2 x nmax pivot columns (ping-pong over the step parity), rows already swapped.
 __global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nmax, GridSync* gs) {
   extern __shared__ cplx su[];
-  __shared__ double redv[32];
+  __shared__ long long redv[32];
   __shared__ int redi[32];
   __shared__ cplx s_ip[2];
   int jid = 0;
@@ -63,19 +63,20 @@ __global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nma
       cplx* u = su + (size_t)par * nmax;
       const cplx* up = su + (size_t)(1 - par) * nmax;
       const cplx* colc = A + (int64_t)c * n;
-      double best = -1.0;
+      long long best = kNoKey;
       int bi = 0x7fffffff;
       for (int i = tid; i < n; i += kNT) {
         const cplx v = colc[i];
         u[i] = v;
         if (i >= c) {
-          const double a = cabs2(v);
-          if (a > best || (a == best && i < bi)) { best = a; bi = i; }
+          const long long a = nkey(cabs2(v));
+          if (better(a, i, best, bi)) { best = a; bi = i; }
         }
       }
-      double pmax;
+      long long kmax;
       int p;
-      block_argmax<kNT>(best, bi, redv, redi, &pmax, &p);  // also publishes u to the CTA
+      block_argmax_key<kNT>(best, bi, redv, redi, &kmax, &p);  // also publishes u to the CTA
+      const double pmax = __longlong_as_double(kmax);
       if (!(pmax > 0.0)) p = c;
       if (tid == 0) {
         if (p != c) {

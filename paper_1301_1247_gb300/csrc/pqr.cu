@@ -52,10 +52,6 @@ struct PqrJob {
   int* pos;    // n: position of each column in perm (scratch)
 };
 
-__device__ __forceinline__ bool better(double v, int i, double bv, int bi) {
-  return v > bv || (v == bv && i < bi);
-}
-
 template <int NT>
 __device__ __forceinline__ cplx block_sum_c(cplx v, double* red) {
   double a = block_sum<NT>(v.x, red);
@@ -63,12 +59,15 @@ __device__ __forceinline__ cplx block_sum_c(cplx v, double* red) {
   return cmk(a, b);
 }
 
+// Warp sum of a complex value with five FP64 additions instead of ten: after the first
+// exchange the lower half-warp carries real parts and the upper half imaginary parts.
+// The pairs added are those of the plain butterfly, so the sum is bitwise the same.
 __device__ __forceinline__ cplx warp_sum_c(cplx w) {
-  for (int o = 16; o > 0; o >>= 1) {
-    w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
-    w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
-  }
-  return w;
+  const bool lo = (threadIdx.x & 31) < 16;
+  double keep = lo ? w.x : w.y;
+  keep += __shfl_xor_sync(0xffffffffu, lo ? w.y : w.x, 16);
+  for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+  return cmk(__shfl_sync(0xffffffffu, keep, 0), __shfl_sync(0xffffffffu, keep, 16));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -196,10 +195,13 @@ __device__ double update_col_group(cplx* aj, const cplx* vt, int64_t m, int64_t 
 __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, double* pv, int* pi, GridSync* gs, double tol,
                                              int vcap) {
   extern __shared__ cplx sv[];
-  __shared__ double redv[32];
+  __shared__ long long redv[32];
   __shared__ int redi[32];
+  __shared__ double redsig[kNT];
   __shared__ cplx redc[2 * kNW];
   __shared__ double redn[2 * kNW];
+  __shared__ cplx s_v0;
+  __shared__ double s_tau;
   int jid = 0;
   while (jid + 1 < nj && jobs[jid + 1].b0 <= (int)blockIdx.x) ++jid;
   const PqrJob jb = jobs[jid];
@@ -215,39 +217,44 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
 
   // column norms and the first partial maxima (parity 0)
   {
-    double best = -1.0;
+    long long best = kNoKey;
     int bi = 0x7fffffff;
     for (int64_t j = gw; j < n; j += nw) {
       double s2 = 0.0;
       for (int64_t i = lane; i < m; i += 32) s2 += cabs2(A[j * m + i]);
       s2 = warp_sum(s2);
       if (lane == 0) { jb.nrm[j] = s2; jb.nref[j] = s2; }
-      if (better(s2, (int)j, best, bi)) { best = s2; bi = (int)j; }
+      if (better(nkey(s2), (int)j, best, bi)) { best = nkey(s2); bi = (int)j; }
     }
-    double v;
+    long long v;
     int ix;
-    block_argmax<kNT>(best, bi, redv, redi, &v, &ix);
-    if (tid == 0) { pv[blockIdx.x] = v; pi[blockIdx.x] = ix; }
+    block_argmax_key<kNT>(best, bi, redv, redi, &v, &ix);
+    if (tid == 0) { pv[blockIdx.x] = __longlong_as_double(v); pi[blockIdx.x] = ix; }
   }
   if (grid_sync_sum(gs, 0) < 0) return;
 
-  double r00 = 0.0;
+  double r00 = 0.0, thr2 = 0.0;
   bool done = false;
   for (int64_t s = 0;; ++s) {
     const int par = (int)(s & 1);
     int p = -1;
-    double pvmax = -1.0;
     if (!done) {
-      double best = -1.0;
+      long long best = kNoKey;
       int bi = 0x7fffffff;
       for (int q = tid; q < jb.nb; q += kNT) {
-        const double v = pv[par * G + jb.b0 + q];
+        const long long v = nkey(pv[par * G + jb.b0 + q]);
         const int ix = pi[par * G + jb.b0 + q];
         if (better(v, ix, best, bi)) { best = v; bi = ix; }
       }
-      block_argmax<kNT>(best, bi, redv, redi, &pvmax, &p);
-      if (s == 0) r00 = sqrt(fmax(pvmax, 0.0));
-      const bool tol_met = !(r00 > 0.0) || !(pvmax >= 0.0) || sqrt(pvmax) <= tol * r00;
+      long long kmax;
+      block_argmax_key<kNT>(best, bi, redv, redi, &kmax, &p);
+      const double pvmax = __longlong_as_double(kmax);
+      if (s == 0) {
+        r00 = sqrt(fmax(pvmax, 0.0));
+        thr2 = (tol * r00) * (tol * r00);
+      }
+      // |R_ss| <= tol |R_00|, compared squared
+      const bool tol_met = !(r00 > 0.0) || !(pvmax >= 0.0) || pvmax <= thr2;
       if (tol_met || s >= jb.kcap || s >= m || s >= n || p < 0 || p >= n) {
         done = true;
         if (lb == 0 && tid == 0) {
@@ -259,7 +266,6 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
     }
     if (!done) {
       const cplx* ap = A + (int64_t)p * m;
-      const cplx x0 = ap[s];
       const bool staged = (m - s - 1) <= vcap;
       double sig = 0.0;
       for (int64_t i = s + 1 + tid; i < m; i += kNT) {
@@ -267,40 +273,45 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
         sig += cabs2(x);
         if (staged) sv[i - s - 1] = x;
       }
-      sig = block_sum<kNT>(sig, redv);  // also publishes sv to the CTA
-      const double ax0 = cabs1(x0);
-      const double xn = sqrt(ax0 * ax0 + sig);
-      const cplx ph = ax0 > 0.0 ? cmk(x0.x / ax0, x0.y / ax0) : cmk(1.0, 0.0);
-      const cplx beta = cmk(-ph.x * xn, -ph.y * xn);
-      const cplx v0 = csub(x0, beta);
-      const double vv = cabs2(v0) + sig;
-      const double tau = vv > 0.0 ? 2.0 / vv : 0.0;
-      if (lb == 0 && tid == 0) {
-        jb.piv[s] = p;
-        jb.beta[s] = beta;
-        jb.v0[s] = v0;
-        jb.tau[s] = tau;
+      // The reflector's scalars are formed once per CTA, by lane 0 of warp 0.
+      sig = block_sum_warp0<kNT>(sig, redsig);  // also publishes sv to the CTA
+      if (tid == 0) {
+        const cplx x0 = ap[s];
+        cplx v0, beta;
+        double tau;
+        householder_scalars(x0, sig, &v0, &beta, &tau);
+        s_v0 = v0;
+        s_tau = tau;
+        if (lb == 0) {
+          jb.piv[s] = p;
+          jb.beta[s] = beta;
+          jb.v0[s] = v0;
+          jb.tau[s] = tau;
+        }
       }
+      __syncthreads();
+      const cplx v0 = s_v0;
+      const double tau = s_tau;
       const cplx* vt = staged ? sv : ap + s + 1;
-      double best = -1.0;
+      long long best = kNoKey;
       int bi = 0x7fffffff;
       if (GW == 1) {
         for (int64_t j = gw; j < n; j += nw) {
           const double nj = jb.nrm[j];
-          if (nj < 0.0) continue;  // an earlier pivot
+          if (nkey(nj) < 0) continue;  // an earlier pivot (marked -1)
           if (j == p) {
             if (lane == 0) jb.nrm[j] = -1.0;
             continue;
           }
           const double t = update_col_warp(A + j * m, vt, m, s, v0, tau, nj, jb.nref + j, lane);
           if (lane == 0) jb.nrm[j] = t;
-          if (better(t, (int)j, best, bi)) { best = t; bi = (int)j; }
+          if (better(nkey(t), (int)j, best, bi)) { best = nkey(t); bi = (int)j; }
         }
       } else {
         int slot = 0;
         for (int64_t j = gg; j < n; j += ngrp) {
           const double nj = jb.nrm[j];
-          if (nj < 0.0) continue;
+          if (nkey(nj) < 0) continue;
           if (j == p) {
             if (gl == 0) jb.nrm[j] = -1.0;
             continue;
@@ -309,13 +320,13 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
                                             slot, redc, redn);
           slot ^= 1;
           if (gl == 0) jb.nrm[j] = t;
-          if (better(t, (int)j, best, bi)) { best = t; bi = (int)j; }
+          if (better(nkey(t), (int)j, best, bi)) { best = nkey(t); bi = (int)j; }
         }
       }
-      double v;
+      long long v;
       int ix;
-      block_argmax<kNT>(best, bi, redv, redi, &v, &ix);
-      if (tid == 0) { pv[(1 - par) * G + blockIdx.x] = v; pi[(1 - par) * G + blockIdx.x] = ix; }
+      block_argmax_key<kNT>(best, bi, redv, redi, &v, &ix);
+      if (tid == 0) { pv[(1 - par) * G + blockIdx.x] = __longlong_as_double(v); pi[(1 - par) * G + blockIdx.x] = ix; }
     }
     const long long act = grid_sync_sum(gs, (lb == 0 && !done) ? 1 : 0);
     if (act <= 0) break;  // all matrices finished (0) or a wait gave up (-1)

@@ -223,6 +223,7 @@ __global__ void k_bq_pivot(cplx* A, int64_t m, int64_t s, double* nrm, double* n
                            const int* pi, int nparts, BigQrState* st, double tol) {
   __shared__ double redv[32];
   __shared__ int redi[32];
+  __shared__ double redsig[256];
   if (st->done) return;
   double best = -1.0;
   int bi = 0x7fffffff;
@@ -235,7 +236,8 @@ __global__ void k_bq_pivot(cplx* A, int64_t m, int64_t s, double* nrm, double* n
   if (s == 0 && threadIdx.x == 0) st->r00 = sqrt(v);
   __syncthreads();
   const double r00 = st->r00;
-  if (!(r00 > 0.0) || sqrt(v) <= tol * r00 || s >= m) {
+  // |R_ss| <= tol |R_00|, compared squared (as the persistent QR does)
+  if (!(r00 > 0.0) || !(v >= 0.0) || v <= (tol * r00) * (tol * r00) || s >= m) {
     if (threadIdx.x == 0) { st->done = 1; st->rank = (int)s; }
     return;
   }
@@ -253,17 +255,13 @@ __global__ void k_bq_pivot(cplx* A, int64_t m, int64_t s, double* nrm, double* n
   cplx* cs = A + s * m;
   double sig = 0.0;
   for (int64_t i = s + 1 + threadIdx.x; i < m; i += blockDim.x) sig += cabs2(cs[i]);
-  sig = block_sum<256>(sig, redv);
+  sig = block_sum_warp0<256>(sig, redsig);
   if (threadIdx.x == 0) {
-    cplx x0 = cs[s];
-    double ax0 = cabs1(x0);
-    double xn = sqrt(ax0 * ax0 + sig);
-    cplx ph = ax0 > 0.0 ? cmk(x0.x / ax0, x0.y / ax0) : cmk(1.0, 0.0);
-    cplx beta = cmk(-ph.x * xn, -ph.y * xn);
-    cplx v0 = csub(x0, beta);
-    double vv = cabs2(v0) + sig;
+    cplx v0, beta;
+    double tau;
+    householder_scalars(cs[s], sig, &v0, &beta, &tau);
     st->v0 = v0;
-    st->tau = vv > 0.0 ? 2.0 / vv : 0.0;
+    st->tau = tau;
     cs[s] = beta;
     st->rank = (int)(s + 1);
   }

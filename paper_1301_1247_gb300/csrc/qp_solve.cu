@@ -769,7 +769,7 @@ __global__ void __launch_bounds__(NT) k_schur_solve(Dims D, const GroupJob* grou
   // U12 with 4 x 4 register tiles per thread.
   constexpr int NB = 16, TM = 64;
   static_assert(NT == 256, "16 x 16 threads per trailing tile");
-  __shared__ double redv[32];
+  __shared__ long long redv[32];
   __shared__ int redi[32];
   __shared__ cplx sh_ip;
   __shared__ cplx Ls[NB][TM + 1];
@@ -786,17 +786,20 @@ __global__ void __launch_bounds__(NT) k_schur_solve(Dims D, const GroupJob* grou
     const int nb = min(NB, n - k0);
     for (int c = k0; c < k0 + nb; ++c) {
       cplx* ac = A + (int64_t)c * n;
-      double best = -1.0;
+      long long best = kNoKey;
       int bi = 0x7fffffff;
       for (int i = c + tid; i < n; i += NT) {
-        const double v = cabs2(ac[i]);
-        if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+        const long long v = nkey(cabs2(ac[i]));
+        if (better(v, i, best, bi)) { best = v; bi = i; }
       }
-      double pv;
+      long long kv;
       int p;
-      block_argmax<NT>(best, bi, redv, redi, &pv, &p);
-      pmax = fmax(pmax, pv);
-      pmin = fmin(pmin, pv);
+      block_argmax_key<NT>(best, bi, redv, redi, &kv, &p);
+      if (tid == 0) {  // pivot range for the conditioning flag (read by thread 0)
+        const double pv = __longlong_as_double(kv);
+        pmax = fmax(pmax, pv);
+        pmin = fmin(pmin, pv);
+      }
       if (p != c) {
         for (int j = tid; j < nc; j += NT) {
           cplx* cj = col(j);
@@ -917,7 +920,7 @@ __global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* group
                                                    cplx* Spool, cplx* Rpool, int* illcond, GridSync* gs) {
   constexpr int NB = 16, TM = 64;
   static_assert(NT == 256, "16 x 16 threads per trailing tile");
-  __shared__ double redv[32];
+  __shared__ long long redv[32];
   __shared__ int redi[32];
   __shared__ cplx sh_ip;
   __shared__ cplx Ls[NB][TM + 1];
@@ -946,17 +949,20 @@ __global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* group
     if (live && rank == 0) {
       for (int c = k0; c < k0 + nb; ++c) {
         cplx* ac = A + (int64_t)c * n;
-        double best = -1.0;
+        long long best = kNoKey;
         int bi = 0x7fffffff;
         for (int i = c + tid; i < n; i += NT) {
-          const double v = cabs2(ac[i]);
-          if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+          const long long v = nkey(cabs2(ac[i]));
+          if (better(v, i, best, bi)) { best = v; bi = i; }
         }
-        double pv;
+        long long kv;
         int p;
-        block_argmax<NT>(best, bi, redv, redi, &pv, &p);
-        pmax = fmax(pmax, pv);
-        pmin = fmin(pmin, pv);
+        block_argmax_key<NT>(best, bi, redv, redi, &kv, &p);
+        if (tid == 0) {  // pivot range for the conditioning flag (read by thread 0)
+          const double pv = __longlong_as_double(kv);
+          pmax = fmax(pmax, pv);
+          pmin = fmin(pmin, pv);
+        }
         if (p != c) {
           for (int j = tid; j < nc; j += NT) {
             cplx* cj = col(j);

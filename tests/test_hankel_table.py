@@ -1,5 +1,5 @@
 """The library's Chebyshev table for H0, H1 (csrc/hankel_table.h), evaluated on the CPU the
-way the device does (Clenshaw on unit intervals, Y0 and Y1 rebuilt with one logarithm),
+way the device does (Clenshaw on intervals of width 1/kHankelPerUnit, Y0 and Y1 rebuilt with one logarithm),
 against SciPy's Bessel functions on 20 000 points in (1e-4, 40)."""
 import math
 import os
@@ -15,15 +15,16 @@ def _table():
     txt = open(os.path.join(ROOT, "paper_1301_1247_gb300", "csrc", "hankel_table.h")).read()
     ni = int(re.search(r"kHankelIntervals = (\d+)", txt).group(1))
     nd = int(re.search(r"kHankelDegree = (\d+)", txt).group(1))
+    pu = int(re.search(r"kHankelPerUnit = (\d+)", txt).group(1))
     body = txt.split("= {", 1)[1].split("};", 1)[0]
     vals = np.array([float(v) for v in body.replace("\n", " ").split(",") if v.strip()])
     assert vals.size == ni * 4 * nd
-    return ni, nd, vals.reshape(ni, 4, nd)
+    return ni // pu, nd, pu, vals.reshape(ni, 4, nd)
 
 
-def _eval(tab, nd, z):
-    i = int(z)
-    t = 2.0 * (z - i) - 1.0
+def _eval(tab, nd, pu, z):
+    i = int(pu * z)
+    t = 2.0 * (pu * z - i) - 1.0
     out = []
     for f in range(4):
         c = tab[i, f]
@@ -37,12 +38,12 @@ def _eval(tab, nd, z):
 
 
 def test_hankel_table_matches_scipy():
-    ni, nd, tab = _table()
+    zmax, nd, pu, tab = _table()
     rng = np.random.default_rng(0)
-    zs = np.concatenate([10.0 ** rng.uniform(-4, math.log10(ni - 1e-9), 20000), [1e-4, 0.5, 1.0, 17.5, 39.99]])
+    zs = np.concatenate([10.0 ** rng.uniform(-4, math.log10(zmax - 1e-9), 20000), [1e-4, 0.5, 1.0, 17.5, 39.99]])
     worst = 0.0
     for z in zs:
-        j0, j1, y0, y1 = _eval(tab, nd, z)
+        j0, j1, y0, y1 = _eval(tab, nd, pu, z)
         h0 = complex(special.j0(z), special.y0(z))
         h1 = complex(special.j1(z), special.y1(z))
         worst = max(worst, abs(complex(j0, y0) - h0) / abs(h0), abs(complex(j1, y1) - h1) / abs(h1))
