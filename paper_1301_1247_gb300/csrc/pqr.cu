@@ -19,6 +19,7 @@
 #include <cstdio>
 
 #include "dense_kernels.cuh"
+#include "dfloat.cuh"
 #include "gridsync.cuh"
 #include "profile.hpp"
 #include "qp_kernels.cuh"
@@ -191,7 +192,139 @@ __device__ double update_col_group(cplx* aj, const cplx* vt, int64_t m, int64_t 
   return t;
 }
 
-// pv / pi: 2 x gridDim.x partial maxima (parity of the step).
+// ---- double-float updates (handles built with double-float precision) ----
+// From the norm pass to the end of the launch the matrix is held in place as complex
+// double-float (dfc, 16 bytes like the complex double it replaces), and the rank-one
+// updates, which carry almost all of the work, run on the FP32 pipes.  Column norms,
+// pivot choices and the reflector scalars stay FP64.
+
+// w = tau (conj(v0) a_s + tot) and the new row-s entry top = a_s - v0 w.
+__device__ __forceinline__ void df_col_scalars(const dfc& ajs, const dfc& tot, const dfc& v0, float th, float tl,
+                                               dfc* w, dfc* top) {
+  dfc u = tot;
+  dfc_cdot_acc(v0, ajs, u);
+  dfc_norm(u);
+  *w = dfc_scale(th, tl, u);
+  dfc t = ajs;
+  dfc_sub_mul(v0, *w, t);
+  *top = t;
+}
+
+// Downdated squared norm nj - |top|^2 (FP64).
+__device__ __forceinline__ double df_downdate(double nj, const dfc& top) {
+  float qh = 0.f, ql = 0.f;
+  df_abs2_acc(top, qh, ql);
+  return (nj - f2d_bits(qh)) - f2d_bits(ql);
+}
+
+__device__ __forceinline__ double update_col_warp_df(dfc* aj, const dfc* vt, int64_t m, int64_t s, const dfc& v0,
+                                                     float th, float tl, double nj, double* nref_j, int lane) {
+  dfc r[kReg];
+  dfc w = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int q = 0; q < kReg; ++q) {
+    const int64_t i = s + 1 + lane + 32 * q;
+    if (i < m) {
+      r[q] = aj[i];
+      dfc_cdot_acc(vt[i - s - 1], r[q], w);
+    }
+  }
+  for (int64_t i = s + 1 + lane + 32 * kReg; i < m; i += 32) dfc_cdot_acc(vt[i - s - 1], aj[i], w);
+  w = dfc_warp_sum(w);
+  const dfc ajs = aj[s];
+  dfc wv, top;
+  df_col_scalars(ajs, w, v0, th, tl, &wv, &top);
+#pragma unroll
+  for (int q = 0; q < kReg; ++q) {
+    const int64_t i = s + 1 + lane + 32 * q;
+    if (i < m) {
+      dfc_sub_mul(vt[i - s - 1], wv, r[q]);
+      aj[i] = r[q];
+    }
+  }
+  for (int64_t i = s + 1 + lane + 32 * kReg; i < m; i += 32) {
+    dfc a = aj[i];
+    dfc_sub_mul(vt[i - s - 1], wv, a);
+    aj[i] = a;
+  }
+  double t = df_downdate(nj, top);
+  if (t <= 0.0078125 * *nref_j) {
+    float qh = 0.f, ql = 0.f;
+#pragma unroll
+    for (int q = 0; q < kReg; ++q)
+      if (s + 1 + lane + 32 * q < m) df_abs2_acc(r[q], qh, ql);
+    for (int64_t i = s + 1 + lane + 32 * kReg; i < m; i += 32) df_abs2_acc(aj[i], qh, ql);
+    t = warp_sum(f2d_bits(qh) + f2d_bits(ql));
+    if (lane == 0) *nref_j = t;
+  }
+  __syncwarp();
+  if (lane == 0) aj[s] = top;
+  return t;
+}
+
+__device__ double update_col_group_df(dfc* aj, const dfc* vt, int64_t m, int64_t s, const dfc& v0, float th, float tl,
+                                      double nj, double* nref_j, int gl, int GW, int grp, int wg, int lane, int slot,
+                                      dfc* redc, double* redn) {
+  const int64_t stride = 32 * GW;
+  const int base = slot * kNW + grp * GW;
+  const dfc ajs = aj[s];  // read by every warp before the group's first barrier
+  dfc r[kReg];
+  dfc w = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int q = 0; q < kReg; ++q) {
+    const int64_t i = s + 1 + gl + stride * q;
+    if (i < m) {
+      r[q] = aj[i];
+      dfc_cdot_acc(vt[i - s - 1], r[q], w);
+    }
+  }
+  for (int64_t i = s + 1 + gl + stride * kReg; i < m; i += stride) dfc_cdot_acc(vt[i - s - 1], aj[i], w);
+  w = dfc_warp_sum(w);
+  if (lane == 0) redc[base + wg] = w;
+  group_barrier(1 + grp, 32 * GW);
+  dfc tot = {0.f, 0.f, 0.f, 0.f};
+  for (int k = 0; k < GW; ++k) {
+    const dfc p = redc[base + k];
+    df_add_to(p.rh, p.rl, tot.rh, tot.rl);
+    df_add_to(p.ih, p.il, tot.ih, tot.il);
+  }
+  dfc_norm(tot);
+  dfc wv, top;
+  df_col_scalars(ajs, tot, v0, th, tl, &wv, &top);
+#pragma unroll
+  for (int q = 0; q < kReg; ++q) {
+    const int64_t i = s + 1 + gl + stride * q;
+    if (i < m) {
+      dfc_sub_mul(vt[i - s - 1], wv, r[q]);
+      aj[i] = r[q];
+    }
+  }
+  for (int64_t i = s + 1 + gl + stride * kReg; i < m; i += stride) {
+    dfc a = aj[i];
+    dfc_sub_mul(vt[i - s - 1], wv, a);
+    aj[i] = a;
+  }
+  double t = df_downdate(nj, top);
+  if (t <= 0.0078125 * *nref_j) {  // uniform over the group
+    float qh = 0.f, ql = 0.f;
+#pragma unroll
+    for (int q = 0; q < kReg; ++q)
+      if (s + 1 + gl + stride * q < m) df_abs2_acc(r[q], qh, ql);
+    for (int64_t i = s + 1 + gl + stride * kReg; i < m; i += stride) df_abs2_acc(aj[i], qh, ql);
+    const double q2 = warp_sum(f2d_bits(qh) + f2d_bits(ql));
+    if (lane == 0) redn[base + wg] = q2;
+    group_barrier(1 + grp, 32 * GW);
+    t = 0.0;
+    for (int k = 0; k < GW; ++k) t += redn[base + k];
+    if (gl == 0) *nref_j = t;
+  }
+  if (gl == 0) aj[s] = top;
+  return t;
+}
+
+// pv / pi: 2 x gridDim.x partial maxima (parity of the step).  DF: double-float updates
+// (the matrix is converted in place after the norm pass and back before the kernel ends).
+template <bool DF>
 __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, double* pv, int* pi, GridSync* gs, double tol,
                                              int vcap) {
   extern __shared__ cplx sv[];
@@ -202,6 +335,8 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
   __shared__ double redn[2 * kNW];
   __shared__ cplx s_v0;
   __shared__ double s_tau;
+  __shared__ dfc s_v0d;
+  __shared__ float s_th, s_tl;
   int jid = 0;
   while (jid + 1 < nj && jobs[jid + 1].b0 <= (int)blockIdx.x) ++jid;
   const PqrJob jb = jobs[jid];
@@ -214,14 +349,19 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
   const int GW = jb.gw, grp = warp / GW, wg = warp % GW, gl = wg * 32 + lane;
   const int64_t gg = (int64_t)lb * (kNW / GW) + grp, ngrp = (int64_t)jb.nb * (kNW / GW);
   cplx* A = jb.A;
+  dfc* D = reinterpret_cast<dfc*>(jb.A);
 
-  // column norms and the first partial maxima (parity 0)
+  // column norms (FP64) and the first partial maxima (parity 0)
   {
     long long best = kNoKey;
     int bi = 0x7fffffff;
     for (int64_t j = gw; j < n; j += nw) {
       double s2 = 0.0;
-      for (int64_t i = lane; i < m; i += 32) s2 += cabs2(A[j * m + i]);
+      for (int64_t i = lane; i < m; i += 32) {
+        const cplx x = A[j * m + i];
+        s2 += cabs2(x);
+        if constexpr (DF) D[j * m + i] = to_dfc_bits(x);
+      }
       s2 = warp_sum(s2);
       if (lane == 0) { jb.nrm[j] = s2; jb.nref[j] = s2; }
       if (better(nkey(s2), (int)j, best, bi)) { best = nkey(s2); bi = (int)j; }
@@ -265,23 +405,44 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
       }
     }
     if (!done) {
-      const cplx* ap = A + (int64_t)p * m;
       const bool staged = (m - s - 1) <= vcap;
       double sig = 0.0;
-      for (int64_t i = s + 1 + tid; i < m; i += kNT) {
-        const cplx x = ap[i];
-        sig += cabs2(x);
-        if (staged) sv[i - s - 1] = x;
+      if constexpr (DF) {
+        const dfc* ap = D + (int64_t)p * m;
+        dfc* svd = reinterpret_cast<dfc*>(sv);
+        float qh = 0.f, ql = 0.f;
+        for (int64_t i = s + 1 + tid; i < m; i += kNT) {
+          const dfc x = ap[i];
+          df_abs2_acc(x, qh, ql);
+          if (staged) svd[i - s - 1] = x;
+        }
+        sig = f2d_bits(qh) + f2d_bits(ql);
+      } else {
+        const cplx* ap = A + (int64_t)p * m;
+        for (int64_t i = s + 1 + tid; i < m; i += kNT) {
+          const cplx x = ap[i];
+          sig += cabs2(x);
+          if (staged) sv[i - s - 1] = x;
+        }
       }
       // The reflector's scalars are formed once per CTA, by lane 0 of warp 0.
       sig = block_sum_warp0<kNT>(sig, redsig);  // also publishes sv to the CTA
       if (tid == 0) {
-        const cplx x0 = ap[s];
+        cplx x0;
+        if constexpr (DF) x0 = from_dfc_bits(D[(int64_t)p * m + s]);
+        else x0 = A[(int64_t)p * m + s];
         cplx v0, beta;
         double tau;
         householder_scalars(x0, sig, &v0, &beta, &tau);
         s_v0 = v0;
         s_tau = tau;
+        if constexpr (DF) {
+          s_v0d = to_dfc_bits(v0);
+          float th, tl;
+          df_split_bits(tau, th, tl);
+          s_th = th;
+          s_tl = tl;
+        }
         if (lb == 0) {
           jb.piv[s] = p;
           jb.beta[s] = beta;
@@ -290,37 +451,71 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
         }
       }
       __syncthreads();
-      const cplx v0 = s_v0;
-      const double tau = s_tau;
-      const cplx* vt = staged ? sv : ap + s + 1;
       long long best = kNoKey;
       int bi = 0x7fffffff;
-      if (GW == 1) {
-        for (int64_t j = gw; j < n; j += nw) {
-          const double nj = jb.nrm[j];
-          if (nkey(nj) < 0) continue;  // an earlier pivot (marked -1)
-          if (j == p) {
-            if (lane == 0) jb.nrm[j] = -1.0;
-            continue;
+      if constexpr (DF) {
+        const dfc v0 = s_v0d;
+        const float th = s_th, tl = s_tl;
+        const dfc* vt = staged ? reinterpret_cast<const dfc*>(sv) : D + (int64_t)p * m + s + 1;
+        if (GW == 1) {
+          for (int64_t j = gw; j < n; j += nw) {
+            const double nj = jb.nrm[j];
+            if (nkey(nj) < 0) continue;  // an earlier pivot (marked -1)
+            if (j == p) {
+              if (lane == 0) jb.nrm[j] = -1.0;
+              continue;
+            }
+            const double t = update_col_warp_df(D + j * m, vt, m, s, v0, th, tl, nj, jb.nref + j, lane);
+            if (lane == 0) jb.nrm[j] = t;
+            if (better(nkey(t), (int)j, best, bi)) { best = nkey(t); bi = (int)j; }
           }
-          const double t = update_col_warp(A + j * m, vt, m, s, v0, tau, nj, jb.nref + j, lane);
-          if (lane == 0) jb.nrm[j] = t;
-          if (better(nkey(t), (int)j, best, bi)) { best = nkey(t); bi = (int)j; }
+        } else {
+          int slot = 0;
+          for (int64_t j = gg; j < n; j += ngrp) {
+            const double nj = jb.nrm[j];
+            if (nkey(nj) < 0) continue;
+            if (j == p) {
+              if (gl == 0) jb.nrm[j] = -1.0;
+              continue;
+            }
+            const double t = update_col_group_df(D + j * m, vt, m, s, v0, th, tl, nj, jb.nref + j, gl, GW, grp, wg,
+                                                 lane, slot, reinterpret_cast<dfc*>(redc), redn);
+            slot ^= 1;
+            if (gl == 0) jb.nrm[j] = t;
+            if (better(nkey(t), (int)j, best, bi)) { best = nkey(t); bi = (int)j; }
+          }
         }
       } else {
-        int slot = 0;
-        for (int64_t j = gg; j < n; j += ngrp) {
-          const double nj = jb.nrm[j];
-          if (nkey(nj) < 0) continue;
-          if (j == p) {
-            if (gl == 0) jb.nrm[j] = -1.0;
-            continue;
+        const cplx v0 = s_v0;
+        const double tau = s_tau;
+        const cplx* vt = staged ? sv : A + (int64_t)p * m + s + 1;
+        if (GW == 1) {
+          for (int64_t j = gw; j < n; j += nw) {
+            const double nj = jb.nrm[j];
+            if (nkey(nj) < 0) continue;  // an earlier pivot (marked -1)
+            if (j == p) {
+              if (lane == 0) jb.nrm[j] = -1.0;
+              continue;
+            }
+            const double t = update_col_warp(A + j * m, vt, m, s, v0, tau, nj, jb.nref + j, lane);
+            if (lane == 0) jb.nrm[j] = t;
+            if (better(nkey(t), (int)j, best, bi)) { best = nkey(t); bi = (int)j; }
           }
-          const double t = update_col_group(A + j * m, vt, m, s, v0, tau, nj, jb.nref + j, gl, GW, grp, wg, lane,
-                                            slot, redc, redn);
-          slot ^= 1;
-          if (gl == 0) jb.nrm[j] = t;
-          if (better(nkey(t), (int)j, best, bi)) { best = nkey(t); bi = (int)j; }
+        } else {
+          int slot = 0;
+          for (int64_t j = gg; j < n; j += ngrp) {
+            const double nj = jb.nrm[j];
+            if (nkey(nj) < 0) continue;
+            if (j == p) {
+              if (gl == 0) jb.nrm[j] = -1.0;
+              continue;
+            }
+            const double t = update_col_group(A + j * m, vt, m, s, v0, tau, nj, jb.nref + j, gl, GW, grp, wg, lane,
+                                              slot, redc, redn);
+            slot ^= 1;
+            if (gl == 0) jb.nrm[j] = t;
+            if (better(nkey(t), (int)j, best, bi)) { best = nkey(t); bi = (int)j; }
+          }
         }
       }
       long long v;
@@ -330,6 +525,11 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
     }
     const long long act = grid_sync_sum(gs, (lb == 0 && !done) ? 1 : 0);
     if (act <= 0) break;  // all matrices finished (0) or a wait gave up (-1)
+  }
+  if constexpr (DF) {
+    // Every CTA has left the step loop at the same barrier: no update is in flight.
+    for (int64_t j = gw; j < n; j += nw)
+      for (int64_t i = lane; i < m; i += 32) A[j * m + i] = from_dfc_bits(D[j * m + i]);
   }
 }
 
@@ -570,6 +770,7 @@ __global__ void k_set_unit_cols(cplx* X, int k, const int64_t* idx) {
   }
 }
 
+template <bool DF>
 static int pqr_grid(size_t smem) {
   static const int sms = [] {
     int dev = 0, sm = 0;
@@ -578,9 +779,9 @@ static int pqr_grid(size_t smem) {
     return sm;
   }();
   if (smem > 48 * 1024)
-    HBS_CUDA(cudaFuncSetAttribute(k_pqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HBS_CUDA(cudaFuncSetAttribute(k_pqr<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pqr, kNT, smem));
+  HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pqr<DF>, kNT, smem));
   if (per_sm < 1) throw Error(HBS_ERR_CUDA, "persistent QR kernel does not fit on an SM");
   return sms * std::min(per_sm, 2);
 }
@@ -601,7 +802,10 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
   }
   const int vcap = (int)std::min<int64_t>(mmax, 6144);
   const size_t smem = (size_t)vcap * sizeof(cplx);
-  const int G = pqr_grid(smem);
+  // Double-float updates on handles built with double-float precision; the public row ID
+  // entry points keep FP64 throughout.
+  const bool df = gemm_double_float();
+  const int G = df ? pqr_grid<true>(smem) : pqr_grid<false>(smem);
   if (nj > G) throw Error(HBS_ERR_INTERNAL, "persistent QR batch larger than the grid");
   // CTAs per matrix in proportion to its size, at least one each.
   std::vector<int> nb(nj, 1);
@@ -664,7 +868,8 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
     std::lock_guard<std::mutex> lock(coop_mutex());
     {
       prof::KScope _ks("k_pqr", s);
-      HBS_CUDA(cudaLaunchCooperativeKernel((const void*)k_pqr, dim3(G), dim3(kNT), args, smem, s));
+      const void* fn = df ? (const void*)k_pqr<true> : (const void*)k_pqr<false>;
+      HBS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kNT), args, smem, s));
     }
     HBS_LAUNCH_CHECK("k_pqr");
     HBS_CUDA(cudaMemcpyAsync(hs.data(), st.get(), sizeof(PqrState) * nj, cudaMemcpyDeviceToHost, s));

@@ -5,6 +5,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace hbs {
 
@@ -95,89 +96,6 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched(const GemmJob* job
 // double-float product is several times faster than DFMA while keeping relative
 // errors near 2^-48 per operation; results are written back in FP64.
 // ---------------------------------------------------------------------------
-// acc += x * y   (double-float, lazy low part; renormalised by df_norm)
-// (explicit _rn intrinsics: the compiler may not contract these into FMAs, which would
-// break the error-free transformations)
-__device__ __forceinline__ void df_mac(float xh, float xl, float yh, float yl, float& ah, float& al) {
-  const float p = __fmul_rn(xh, yh);
-  float e = fmaf(xh, yh, -p);
-  e = fmaf(xh, yl, e);
-  e = fmaf(xl, yh, e);
-  const float sum = __fadd_rn(ah, p);
-  const float v = __fsub_rn(sum, ah);
-  const float t = __fadd_rn(__fsub_rn(ah, __fsub_rn(sum, v)), __fsub_rn(p, v));
-  al = __fadd_rn(al, __fadd_rn(t, e));
-  ah = sum;
-}
-__device__ __forceinline__ void df_norm(float& ah, float& al) {
-  const float sum = __fadd_rn(ah, al);
-  al = __fsub_rn(al, __fsub_rn(sum, ah));
-  ah = sum;
-}
-
-struct dfc {
-  float rh, rl, ih, il;
-};
-
-// Split of an FP64 value into a float pair (hi, lo) with integer operations only (the
-// FP64 conversion path shares the scarce FP64 pipe): hi carries the top 24 bits of the
-// significand, lo the remainder rounded to 24 bits, so hi + lo equals x to 2^-48
-// relative.  Values below the float range become 0.
-__device__ __forceinline__ void df_split_bits(double x, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int sgn = (unsigned int)(b >> 32) & 0x80000000u;
-  const int e = (int)((b >> 52) & 0x7ff);
-  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  const int fe = e - 1023 + 127;
-  if (e == 0 || fe < 1) {
-    hi = __uint_as_float(sgn);
-    lo = __uint_as_float(sgn);
-    return;
-  }
-  if (fe > 254) {
-    hi = __uint_as_float(sgn | 0x7f800000u);
-    lo = 0.0f;
-    return;
-  }
-  hi = __uint_as_float(sgn | ((unsigned int)fe << 23) | (unsigned int)(m >> 29));
-  const unsigned int r = (unsigned int)(m & 0x1FFFFFFFull);  // remainder, r 2^(e-1075)
-  if (r == 0u) {
-    lo = 0.0f;
-    return;
-  }
-  const int lz = __clz(r) - 3;  // leading zeros within the 29-bit field
-  int fel = fe - 24 - lz;
-  const unsigned int rn = r << lz;  // leading one at bit 28
-  unsigned int q = (rn + 16u) >> 5;  // 24-bit significand, rounded to nearest
-  if (q >> 24) {
-    q >>= 1;
-    ++fel;
-  }
-  if (fel < 1) {
-    lo = 0.0f;
-    return;
-  }
-  lo = __uint_as_float(sgn | ((unsigned int)fel << 23) | (q & 0x7FFFFFu));
-}
-
-// float -> double with integer operations only (exact for normal floats; subnormal floats,
-// below 1.2e-38, become 0).
-__device__ __forceinline__ double f2d_bits(float x) {
-  const unsigned int u = __float_as_uint(x);
-  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
-  const unsigned int e = (u >> 23) & 0xFFu;
-  if (e == 0u) return __longlong_as_double((long long)sgn);
-  const unsigned long long de = e == 0xFFu ? 0x7FFull : (unsigned long long)(e - 127u + 1023u);
-  return __longlong_as_double((long long)(sgn | (de << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
-}
-
-__device__ __forceinline__ dfc to_dfc_bits(cplx v) {
-  dfc r;
-  df_split_bits(v.x, r.rh, r.rl);
-  df_split_bits(v.y, r.ih, r.il);
-  return r;
-}
-
 static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* jobs, int njobs) {
   __shared__ dfc As[GBK][GBM + 1];
   __shared__ dfc Bs[GBK][GBN + 1];
