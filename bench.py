@@ -287,6 +287,7 @@ def run_ours(args, ws, rank, local):
                    "build_s": round(info["build_seconds"], 3), "max_rank": info["max_rank"],
                    "nb_rank": info["nb_rank"], "M": info["m"], "levels": info["levels"],
                    "nb_id_residual": info["nb_residual"], "periodizer_id_residual": info["pid_residual"],
+                   "periodizer_ranks": [info["pid_col_rank"], info["pid_row_rank"]],
                    "phases_ms_per_step": phases, "max_flux_error": float(max(flux)),
                    "solve_angles_per_s": round(n_ang / (phases.get("solve:projections", 0) / 1e3 +
                                                        phases.get("solve:schur", 0) / 1e3 +

@@ -116,6 +116,7 @@ static DevGeom geom_view(const hbs_geometry* geom, double omega, DevBuf<double>&
   HBS_LAUNCH_CHECK("k_geom");
   DevGeom g;
   g.x = geom->x; g.y = geom->y; g.nx = nx.get(); g.ny = ny.get(); g.w = w.get(); g.n = N; g.omega = omega;
+  g.df = false;
   return g;
 }
 

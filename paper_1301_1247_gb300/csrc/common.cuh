@@ -6,6 +6,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "dfcore.cuh"
 #include "hankel_table.h"
 
 typedef double2 cplx;
@@ -71,37 +72,75 @@ __device__ __forceinline__ cplx csqrt_principal(cplx z) {
 // Hankel functions of the first kind, orders 0 and 1, real argument z > 0.
 //
 // z < 40: piecewise Chebyshev expansions (hankel_table.h, intervals of width 1/2, 11 terms) of
-//   J0, J1 and of the regular parts of Neumann's expansions,
+//   J0, J1 and, below z = 4, of the regular parts of Neumann's expansions,
 //     R0 = Y0 - (2/pi)(ln(z/2) + gamma) J0,   R1 = Y1 - (2/pi)(ln(z/2) + gamma) J1 + 2/(pi z),
-//   so that Y0 and Y1 take one logarithm; the four series are summed together by
-//   Clenshaw's recurrence.
+//   so that Y0 and Y1 take one logarithm; from z = 4 on, of Y0 and Y1 themselves.  The four
+//   series are summed together by Clenshaw's recurrence, in FP64 or (df) in double-float
+//   arithmetic on the FP32 pipes.
 // z >= 40: Hankel's asymptotic expansion
 //     H_nu(z) ~ sqrt(2/(pi z)) e^{i(z - nu pi/2 - pi/4)} sum_k i^k a_k(nu) / z^k,
 //     a_k(nu) = a_{k-1}(nu) (4 nu^2 - (2k-1)^2) / (8k),
 //   summed until the term falls below 1e-17 (at most 48 terms).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void hankel01(double z, cplx* h0, cplx* h1) {
+__device__ __forceinline__ void hankel01(double z, cplx* h0, cplx* h1, bool df = false) {
   if (z < (double)(kHankelIntervals / kHankelPerUnit)) {
     const double zp = (double)kHankelPerUnit * z;  // exact (power of two)
     const int iv = (int)zp;
-    const double t = 2.0 * (zp - (double)iv) - 1.0, t2 = 2.0 * t;
-    const double* c = kHankelCheb + (size_t)iv * 4 * kHankelDegree;
-    double b1[4] = {0.0, 0.0, 0.0, 0.0}, b2[4] = {0.0, 0.0, 0.0, 0.0};
+    const double t = 2.0 * (zp - (double)iv) - 1.0;
+    double v[4];
+    if (df) {
+      // Clenshaw in double-float arithmetic (FP32 pipes, about 2^-48 per operation)
+      float th, tl;
+      hbs::df_split_bits(t, th, tl);
+      const float t2h = 2.0f * th, t2l = 2.0f * tl;
+      const float* c = kHankelChebDF + (size_t)iv * 8 * kHankelDegree;
+      float b1h[4] = {0.f, 0.f, 0.f, 0.f}, b1l[4] = {0.f, 0.f, 0.f, 0.f};
+      float b2h[4] = {0.f, 0.f, 0.f, 0.f}, b2l[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int k = kHankelDegree - 1; k >= 1; --k) {
+      for (int k = kHankelDegree - 1; k >= 1; --k) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          float bh = __ldg(c + 2 * (f * kHankelDegree + k)), bl = __ldg(c + 2 * (f * kHankelDegree + k) + 1);
+          hbs::df_add_to(-b2h[f], -b2l[f], bh, bl);
+          hbs::df_mac(t2h, t2l, b1h[f], b1l[f], bh, bl);
+          hbs::df_norm(bh, bl);
+          b2h[f] = b1h[f];
+          b2l[f] = b1l[f];
+          b1h[f] = bh;
+          b1l[f] = bl;
+        }
+      }
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
-        const double b0 = fma(t2, b1[f], __ldg(c + f * kHankelDegree + k) - b2[f]);
-        b2[f] = b1[f];
-        b1[f] = b0;
+        float bh = __ldg(c + 2 * f * kHankelDegree), bl = __ldg(c + 2 * f * kHankelDegree + 1);
+        hbs::df_add_to(-b2h[f], -b2l[f], bh, bl);
+        hbs::df_mac(th, tl, b1h[f], b1l[f], bh, bl);
+        v[f] = hbs::f2d_bits(bh) + hbs::f2d_bits(bl);
       }
-    }
-    double v[4];
+    } else {
+      const double t2 = 2.0 * t;
+      const double* c = kHankelCheb + (size_t)iv * 4 * kHankelDegree;
+      double b1[4] = {0.0, 0.0, 0.0, 0.0}, b2[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-    for (int f = 0; f < 4; ++f) v[f] = fma(t, b1[f], __ldg(c + f * kHankelDegree) - b2[f]);
-    const double lg = (2.0 / HBS_PI) * (log(0.5 * z) + HBS_EULER_GAMMA);
-    *h0 = cmk(v[0], fma(lg, v[0], v[2]));
-    *h1 = cmk(v[1], fma(lg, v[1], v[3]) - 2.0 / (HBS_PI * z));
+      for (int k = kHankelDegree - 1; k >= 1; --k) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const double b0 = fma(t2, b1[f], __ldg(c + f * kHankelDegree + k) - b2[f]);
+          b2[f] = b1[f];
+          b1[f] = b0;
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) v[f] = fma(t, b1[f], __ldg(c + f * kHankelDegree) - b2[f]);
+    }
+    if (iv >= kHankelDirect) {  // Y0, Y1 tabulated directly
+      *h0 = cmk(v[0], v[2]);
+      *h1 = cmk(v[1], v[3]);
+    } else {
+      const double lg = (2.0 / HBS_PI) * (log(0.5 * z) + HBS_EULER_GAMMA);
+      *h0 = cmk(v[0], fma(lg, v[0], v[2]));
+      *h1 = cmk(v[1], fma(lg, v[1], v[3]) - 2.0 / (HBS_PI * z));
+    }
   } else {
     // unrolled: the ratios (4 nu^2 - (2k-1)^2) / (8k) are literals
     const double iz = 1.0 / z;
@@ -142,11 +181,11 @@ __device__ __forceinline__ cplx combined_from(double c, cplx h0, cplx h1, double
 // Combined-field kernel dG/dn_y - i w G at target (tx, ty), source (sx, sy) with unit
 // normal (nx, ny), G = (i/4) H0(w r):  (i w / 4) H1(w r) ((x - y).n_y) / r + (w / 4) H0(w r).
 __device__ __forceinline__ cplx combined_kernel(double tx, double ty, double sx, double sy,
-                                                double nx, double ny, double omega) {
+                                                double nx, double ny, double omega, bool df = false) {
   double dx = tx - sx, dy = ty - sy;
   double r = sqrt(dx * dx + dy * dy);
   cplx h0, h1;
-  hankel01(omega * r, &h0, &h1);
+  hankel01(omega * r, &h0, &h1, df);
   double c = 0.25 * omega * (dx * nx + dy * ny) / r;
   // i c H1 + (w/4) H0
   return cmk(-c * h1.y + 0.25 * omega * h0.x, c * h1.x + 0.25 * omega * h0.y);
@@ -155,11 +194,11 @@ __device__ __forceinline__ cplx combined_kernel(double tx, double ty, double sx,
 // Single-layer and double-layer kernels used by proxy sources:
 // G = (i/4) H0(w r), dG/dn_p = (i w / 4) H1(w r) ((x - p).n_p) / r.
 __device__ __forceinline__ void proxy_kernels(double tx, double ty, double px, double py, double nx,
-                                              double ny, double omega, cplx* g, cplx* dg) {
+                                              double ny, double omega, cplx* g, cplx* dg, bool df = false) {
   double dx = tx - px, dy = ty - py;
   double r = sqrt(dx * dx + dy * dy);
   cplx h0, h1;
-  hankel01(omega * r, &h0, &h1);
+  hankel01(omega * r, &h0, &h1, df);
   *g = cmk(-0.25 * h0.y, 0.25 * h0.x);
   double c = 0.25 * omega * (dx * nx + dy * ny) / r;
   *dg = cmk(-c * h1.y, c * h1.x);
@@ -191,17 +230,18 @@ struct DevGeom {
   const double* w;  // (2 pi / N) |z'(t_j)|
   int64_t n;
   double omega;
+  bool df;  // Hankel series in double-float arithmetic (the thread's double-float mode)
 };
 
 // Entry A_ij of the Nystrom matrix (Sec. 2.3), including delta_ij / 2.
 __device__ __forceinline__ cplx a_entry(const DevGeom& g, int64_t i, int64_t j) {
   if (i == j) return cmk(0.5, 0.0);
-  cplx k = combined_kernel(g.x[i], g.y[i], g.x[j], g.y[j], g.nx[j], g.ny[j], g.omega);
+  cplx k = combined_kernel(g.x[i], g.y[i], g.x[j], g.y[j], g.nx[j], g.ny[j], g.omega, g.df);
   return cscale(k, kr6_weight(i, j, g.n) * g.w[j]);
 }
 
 // Entry of the image block A_s (source obstacle shifted by shift_x): plain trapezoid weights.
 __device__ __forceinline__ cplx a_image_entry(const DevGeom& g, int64_t i, int64_t j, double shift_x) {
-  cplx k = combined_kernel(g.x[i], g.y[i], g.x[j] + shift_x, g.y[j], g.nx[j], g.ny[j], g.omega);
+  cplx k = combined_kernel(g.x[i], g.y[i], g.x[j] + shift_x, g.y[j], g.nx[j], g.ny[j], g.omega, g.df);
   return cscale(k, g.w[j]);
 }

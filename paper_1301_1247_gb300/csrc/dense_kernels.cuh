@@ -5,6 +5,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace hbs {
 
@@ -154,7 +155,10 @@ __device__ __forceinline__ void block_argmax(double v, int idx, double* redv, in
 // (relative to the norm at the last recomputation).
 // Dynamic shared memory: 2 n doubles + n ints.
 // ---------------------------------------------------------------------------
-template <int NT>
+// DF: the matrix is held in place as complex double-float (dfc) between the norm pass
+// and the triangular solve, and the rank-one updates run in double-float arithmetic on
+// the FP32 pipes; norms, pivots and the reflector scalars stay FP64.
+template <int NT, bool DF>
 __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, int* rank_out, double tol, int kmax) {
   extern __shared__ double smem[];
   __shared__ long long redv[32];
@@ -162,6 +166,8 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, int* rank_out,
   __shared__ double redsig[NT];
   __shared__ cplx sh_v0;
   __shared__ double sh_tau;
+  __shared__ dfc sh_v0d;
+  __shared__ float sh_th, sh_tl;
 
   const CpqrJob jb = jobs[blockIdx.x];
   const int m = jb.m, n = jb.n;
@@ -172,11 +178,16 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, int* rank_out,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = NT / 32;
 
+  dfc* D = reinterpret_cast<dfc*>(A);
   // initial column norms (one warp per column)
   for (int j = warp; j < n; j += NW) {
     double s = 0.0;
-    const cplx* col = A + (int64_t)j * m;
-    for (int i = lane; i < m; i += 32) s += cabs2(col[i]);
+    cplx* col = A + (int64_t)j * m;
+    for (int i = lane; i < m; i += 32) {
+      const cplx x = col[i];
+      s += cabs2(x);
+      if constexpr (DF) reinterpret_cast<dfc*>(col)[i] = to_dfc_bits(x);
+    }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) { nrm[j] = s; nrm_ref[j] = s; }
   }
@@ -215,6 +226,65 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, int* rank_out,
       }
     }
     __syncthreads();
+    if constexpr (DF) {
+      // Householder reflector for x = A[s:m, s]
+      dfc* cs = D + (int64_t)s * m;
+      float qh = 0.f, ql = 0.f;
+      for (int i = s + 1 + tid; i < m; i += NT) df_abs2_acc(cs[i], qh, ql);
+      const double sig = block_sum_warp0<NT>(f2d_bits(qh) + f2d_bits(ql), redsig);
+      if (tid == 0) {
+        cplx v0, beta;
+        double tau;
+        householder_scalars(from_dfc_bits(cs[s]), sig, &v0, &beta, &tau);
+        sh_v0d = to_dfc_bits(v0);
+        float th, tl;
+        df_split_bits(tau, th, tl);
+        sh_th = th;
+        sh_tl = tl;
+        cs[s] = to_dfc_bits(beta);  // R_ss
+      }
+      __syncthreads();
+      const dfc v0 = sh_v0d;
+      const float th = sh_th, tl = sh_tl;
+      for (int j = s + 1 + warp; j < n; j += NW) {
+        dfc* cj = D + (int64_t)j * m;
+        dfc w = {0.f, 0.f, 0.f, 0.f};
+        for (int i = s + 1 + lane; i < m; i += 32) dfc_cdot_acc(cs[i], cj[i], w);
+        w = dfc_warp_sum(w);
+        const dfc ajs = cj[s];
+        dfc_cdot_acc(v0, ajs, w);
+        dfc_norm(w);
+        const dfc wv = dfc_scale(th, tl, w);
+        for (int i = s + 1 + lane; i < m; i += 32) {
+          dfc a = cj[i];
+          dfc_sub_mul(cs[i], wv, a);
+          cj[i] = a;
+        }
+        dfc top = ajs;
+        dfc_sub_mul(v0, wv, top);
+        __syncwarp();
+        // norm downdate, recomputation on cancellation (uniform over the warp)
+        float ph = 0.f, pl = 0.f;
+        df_abs2_acc(top, ph, pl);
+        double t = (nrm[j] - f2d_bits(ph)) - f2d_bits(pl);
+        if (t <= 0.0078125 * nrm_ref[j]) {
+          float rh = 0.f, rl = 0.f;
+          for (int i = s + 1 + lane; i < m; i += 32) df_abs2_acc(cj[i], rh, rl);
+          double q = f2d_bits(rh) + f2d_bits(rl);
+          for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+          t = q;
+          if (lane == 0) nrm_ref[j] = t;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          cj[s] = top;
+          nrm[j] = t;
+        }
+      }
+      __syncthreads();
+      rank = s + 1;
+      continue;
+    }
     // Householder reflector for x = A[s:m, s]
     cplx* cs = A + (int64_t)s * m;
     double sig = 0.0;
@@ -263,6 +333,13 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, int* rank_out,
   }
   // T = R11^{-1} R12, one warp per column of R12
   const int k = rank;
+  if constexpr (DF) {
+    // back to FP64: rows < k of every column (R11, R12; the rest is scratch)
+    __syncthreads();
+    for (int j = warp; j < n; j += NW)
+      for (int i = lane; i < min(k, m); i += 32) A[(int64_t)j * m + i] = from_dfc_bits(D[(int64_t)j * m + i]);
+    __syncthreads();
+  }
   cplx* T = jb.t;
   for (int c = warp; c < n - k; c += NW) {
     const cplx* r12 = A + (int64_t)(k + c) * m;

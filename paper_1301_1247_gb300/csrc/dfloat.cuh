@@ -6,86 +6,15 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfcore.cuh"
 
 namespace hbs {
-
-// acc += x * y   (double-float, lazy low part; renormalised by df_norm)
-// (explicit _rn intrinsics: the compiler may not contract these into FMAs, which would
-// break the error-free transformations)
-__device__ __forceinline__ void df_mac(float xh, float xl, float yh, float yl, float& ah, float& al) {
-  const float p = __fmul_rn(xh, yh);
-  float e = fmaf(xh, yh, -p);
-  e = fmaf(xh, yl, e);
-  e = fmaf(xl, yh, e);
-  const float sum = __fadd_rn(ah, p);
-  const float v = __fsub_rn(sum, ah);
-  const float t = __fadd_rn(__fsub_rn(ah, __fsub_rn(sum, v)), __fsub_rn(p, v));
-  al = __fadd_rn(al, __fadd_rn(t, e));
-  ah = sum;
-}
-__device__ __forceinline__ void df_norm(float& ah, float& al) {
-  const float sum = __fadd_rn(ah, al);
-  al = __fsub_rn(al, __fsub_rn(sum, ah));
-  ah = sum;
-}
 
 // Complex double-float (16 bytes, the size of a complex double, so a complex128 array
 // can hold it in place).
 struct __align__(16) dfc {
   float rh, rl, ih, il;
 };
-
-// Split of an FP64 value into a float pair (hi, lo) with integer operations only (the
-// FP64 conversion path shares the scarce FP64 pipe): hi carries the top 24 bits of the
-// significand, lo the remainder rounded to 24 bits, so hi + lo equals x to 2^-48
-// relative.  Values below the float range become 0.
-__device__ __forceinline__ void df_split_bits(double x, float& hi, float& lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int sgn = (unsigned int)(b >> 32) & 0x80000000u;
-  const int e = (int)((b >> 52) & 0x7ff);
-  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  const int fe = e - 1023 + 127;
-  if (e == 0 || fe < 1) {
-    hi = __uint_as_float(sgn);
-    lo = __uint_as_float(sgn);
-    return;
-  }
-  if (fe > 254) {
-    hi = __uint_as_float(sgn | 0x7f800000u);
-    lo = 0.0f;
-    return;
-  }
-  hi = __uint_as_float(sgn | ((unsigned int)fe << 23) | (unsigned int)(m >> 29));
-  const unsigned int r = (unsigned int)(m & 0x1FFFFFFFull);  // remainder, r 2^(e-1075)
-  if (r == 0u) {
-    lo = 0.0f;
-    return;
-  }
-  const int lz = __clz(r) - 3;  // leading zeros within the 29-bit field
-  int fel = fe - 24 - lz;
-  const unsigned int rn = r << lz;  // leading one at bit 28
-  unsigned int q = (rn + 16u) >> 5;  // 24-bit significand, rounded to nearest
-  if (q >> 24) {
-    q >>= 1;
-    ++fel;
-  }
-  if (fel < 1) {
-    lo = 0.0f;
-    return;
-  }
-  lo = __uint_as_float(sgn | ((unsigned int)fel << 23) | (q & 0x7FFFFFu));
-}
-
-// float -> double with integer operations only (exact for normal floats; subnormal floats,
-// below 1.2e-38, become 0).
-__device__ __forceinline__ double f2d_bits(float x) {
-  const unsigned int u = __float_as_uint(x);
-  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
-  const unsigned int e = (u >> 23) & 0xFFu;
-  if (e == 0u) return __longlong_as_double((long long)sgn);
-  const unsigned long long de = e == 0xFFu ? 0x7FFull : (unsigned long long)(e - 127u + 1023u);
-  return __longlong_as_double((long long)(sgn | (de << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
-}
 
 __device__ __forceinline__ dfc to_dfc_bits(cplx v) {
   dfc r;
@@ -94,15 +23,6 @@ __device__ __forceinline__ dfc to_dfc_bits(cplx v) {
   return r;
 }
 
-
-// (ah, al) += (bh, bl), lazy low part.
-__device__ __forceinline__ void df_add_to(float bh, float bl, float& ah, float& al) {
-  const float sum = __fadd_rn(ah, bh);
-  const float v = __fsub_rn(sum, ah);
-  const float t = __fadd_rn(__fsub_rn(ah, __fsub_rn(sum, v)), __fsub_rn(bh, v));
-  al = __fadd_rn(al, __fadd_rn(t, bl));
-  ah = sum;
-}
 
 __device__ __forceinline__ cplx from_dfc_bits(const dfc& v) {
   return cmk(f2d_bits(v.rh) + f2d_bits(v.rl), f2d_bits(v.ih) + f2d_bits(v.il));
@@ -153,6 +73,70 @@ __device__ __forceinline__ dfc dfc_shfl_xor(const dfc& a, int o) {
 __device__ __forceinline__ dfc dfc_shfl(const dfc& a, int l) {
   return {__shfl_sync(0xffffffffu, a.rh, l), __shfl_sync(0xffffffffu, a.rl, l), __shfl_sync(0xffffffffu, a.ih, l),
           __shfl_sync(0xffffffffu, a.il, l)};
+}
+
+// The Householder reflector of x = (x0, x_1, ...) in double-float arithmetic (the FP64
+// formulas of householder_scalars, with ||x_1..||^2 = sig): beta = -(x0/|x0|) ||x||,
+// v0 = x0 - beta, tau = 2 / (|v0|^2 + sig).  One thread, FP32 pipes only.
+__device__ __forceinline__ void df_householder(const dfc& x0, float sh, float sl, dfc* v0, dfc* beta, float* th,
+                                               float* tl) {
+  float a2h = 0.f, a2l = 0.f;
+  df_abs2_acc(x0, a2h, a2l);
+  df_norm(a2h, a2l);
+  float axh, axl;
+  df_sqrt(a2h, a2l, axh, axl);
+  float t2h = a2h, t2l = a2l;
+  df_add_to(sh, sl, t2h, t2l);
+  df_norm(t2h, t2l);
+  float xnh, xnl;
+  df_sqrt(t2h, t2l, xnh, xnl);
+  dfc v, b;
+  if (axh > 0.f) {
+    float fh, fl;  // ||x|| / |x0|
+    df_div(xnh, xnl, axh, axl, fh, fl);
+    b = dfc_scale(-fh, -fl, x0);
+    v = x0;  // x0 (1 + f)
+    df_mac(x0.rh, x0.rl, fh, fl, v.rh, v.rl);
+    df_mac(x0.ih, x0.il, fh, fl, v.ih, v.il);
+    dfc_norm(v);
+  } else {
+    b = {-xnh, -xnl, 0.f, 0.f};
+    v = {xnh, xnl, 0.f, 0.f};
+  }
+  float vvh = 0.f, vvl = 0.f;
+  df_abs2_acc(v, vvh, vvl);
+  df_add_to(sh, sl, vvh, vvl);
+  df_norm(vvh, vvl);
+  if (vvh > 0.f) {
+    df_div(2.f, 0.f, vvh, vvl, *th, *tl);
+  } else {
+    *th = 0.f;
+    *tl = 0.f;
+  }
+  *v0 = v;
+  *beta = b;
+}
+
+// Block-wide double-float sum formed in warp 0 (red: 2 NT floats).  The result is valid
+// in every lane of warp 0.  Contains one __syncthreads.
+template <int NT>
+__device__ __forceinline__ void block_sum_df_warp0(float& h, float& l, float* red) {
+  red[threadIdx.x] = h;
+  red[NT + threadIdx.x] = l;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float sh = 0.f, sl = 0.f;
+#pragma unroll
+    for (int k = 0; k < NT / 32; ++k) df_add_to(red[threadIdx.x + 32 * k], red[NT + threadIdx.x + 32 * k], sh, sl);
+    df_norm(sh, sl);
+    for (int o = 16; o > 0; o >>= 1) {
+      const float bh = __shfl_xor_sync(0xffffffffu, sh, o), bl = __shfl_xor_sync(0xffffffffu, sl, o);
+      df_add_to(bh, bl, sh, sl);
+    }
+    df_norm(sh, sl);
+    h = sh;
+    l = sl;
+  }
 }
 
 // Warp sum of a complex double-float value; every lane receives lane 0's result.

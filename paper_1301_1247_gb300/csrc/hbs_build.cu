@@ -164,9 +164,26 @@ struct YJob {
 // Entries come in pairs that share one Hankel evaluation: A(near_r, j) and A(j, near_r)
 // (rows r and nn + r), and the combined-layer proxy row and the field-at-proxy column of
 // proxy p (rows 2nn + p and 2nn + np + p) -- each pair has a single distance |x - y|.
+// Dynamic shared memory: 4 np doubles (the node's proxy points and their directions,
+// formed once per block instead of once per entry).
 __global__ void k_fill_y(const YJob* jobs) {
+  extern __shared__ double sprox[];
   const YJob jb = jobs[blockIdx.y];
   const DevGeom& g = jb.g;
+  double* pxs = sprox;
+  double* pys = sprox + jb.np;
+  double* pcs = sprox + 2 * jb.np;
+  double* psn = sprox + 3 * jb.np;
+  for (int p = threadIdx.x; p < jb.np; p += blockDim.x) {
+    const double th = 2.0 * HBS_PI * (double)p / (double)jb.np;
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    pxs[p] = jb.cx + jb.R * cs;
+    pys[p] = jb.cy + jb.R * sn;
+    pcs[p] = cs;
+    psn[p] = sn;
+  }
+  __syncthreads();
   const int m = 2 * jb.nn + 2 * jb.np;
   const int half = jb.nn + jb.np;
   const int64_t tot = (int64_t)half * jb.n;
@@ -184,7 +201,7 @@ __global__ void k_fill_y(const YJob* jobs) {
         const double dx = g.x[gi] - xj, dy = g.y[gi] - yj;
         const double rr = sqrt(dx * dx + dy * dy);
         cplx h0, h1;
-        hankel01(g.omega * rr, &h0, &h1);
+        hankel01(g.omega * rr, &h0, &h1, g.df);
         const double q = 0.25 * g.omega / rr;
         const double kw = kr6_weight(gi, gj, g.n);
         // A(gi, gj): target gi, source gj;  A(gj, gi): target gj, source gi
@@ -195,14 +212,12 @@ __global__ void k_fill_y(const YJob* jobs) {
       col[jb.nn + r] = v2;
     } else {
       const int p = r - jb.nn;
-      const double th = 2.0 * HBS_PI * (double)p / (double)jb.np;
-      double sn, cs;
-      sincos(th, &sn, &cs);
-      const double px = jb.cx + jb.R * cs, py = jb.cy + jb.R * sn;
+      const double cs = pcs[p], sn = psn[p];
+      const double px = pxs[p], py = pys[p];
       const double dx = xj - px, dy = yj - py;
       const double rr = sqrt(dx * dx + dy * dy);
       cplx h0, h1;
-      hankel01(g.omega * rr, &h0, &h1);
+      hankel01(g.omega * rr, &h0, &h1, g.df);
       const double q = 0.25 * g.omega / rr;
       // combined-layer source at the proxy (normal = radial direction), target node j
       col[2 * jb.nn + p] = cscale(combined_from(q * (dx * cs + dy * sn), h0, h1, g.omega), jb.wp);
@@ -413,6 +428,7 @@ DevGeom Handle_geom(const Handle& h) {
   DevGeom g;
   g.x = h.x.get(); g.y = h.y.get(); g.nx = h.nx.get(); g.ny = h.ny.get(); g.w = h.w.get();
   g.n = h.N; g.omega = h.omega;
+  g.df = gemm_double_float();  // double-float Hankel series in the thread's double-float mode
   return g;
 }
 
@@ -451,11 +467,16 @@ std::vector<int> batched_id(std::vector<CpqrJob>& jobs, double tol, cudaStream_t
     DevBuf<CpqrJob> dj = upload_jobs(small, s);
     DevBuf<int> dr(small.size());
     size_t sm = (size_t)maxn * (2 * sizeof(double) + sizeof(int));
-    if (sm > 48 * 1024)
-      HBS_CUDA(cudaFuncSetAttribute(k_cpqr<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    // double-float updates on handles built with double-float precision
+    const bool df = gemm_double_float();
+    if (sm > 48 * 1024) {
+      if (df) HBS_CUDA(cudaFuncSetAttribute(k_cpqr<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      else HBS_CUDA(cudaFuncSetAttribute(k_cpqr<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    }
     {
       prof::KScope _ks("k_cpqr", s);
-      k_cpqr<256><<<(unsigned)small.size(), 256, sm, s>>>(dj.get(), dr.get(), tol, 1 << 30);
+      if (df) k_cpqr<256, true><<<(unsigned)small.size(), 256, sm, s>>>(dj.get(), dr.get(), tol, 1 << 30);
+      else k_cpqr<256, false><<<(unsigned)small.size(), 256, sm, s>>>(dj.get(), dr.get(), tol, 1 << 30);
     }
     HBS_LAUNCH_CHECK("k_cpqr");
     auto r = dr.download(s);
@@ -743,7 +764,12 @@ void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s) {
       DevBuf<YJob> dyj = upload_jobs(yj, s);
       {
         prof::KScope _ks("k_fill_y", s);
-        launch_jobs_y(dyj, yj.size(), [&](const YJob* p, unsigned ny) { k_fill_y<<<dim3(64, ny), 256, 0, s>>>(p); });
+        int npmax = 0;
+        for (const auto& y : yj) npmax = std::max(npmax, y.np);
+        const size_t psm = 4 * (size_t)npmax * sizeof(double);
+        if (psm > 48 * 1024)
+          HBS_CUDA(cudaFuncSetAttribute(k_fill_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+        launch_jobs_y(dyj, yj.size(), [&](const YJob* p, unsigned ny) { k_fill_y<<<dim3(64, ny), 256, psm, s>>>(p); });
       }
       HBS_LAUNCH_CHECK("k_fill_y");
       std::vector<CpqrJob> cj;

@@ -51,6 +51,7 @@ struct PqrJob {
   cplx* r11c;  // k x k column-major copy of R11
   cplx* invd;  // 1 / R_ii (k)
   int* pos;    // n: position of each column in perm (scratch)
+  GridSync* gs;  // barrier of this matrix's CTAs
 };
 
 template <int NT>
@@ -325,8 +326,7 @@ __device__ double update_col_group_df(dfc* aj, const dfc* vt, int64_t m, int64_t
 // pv / pi: 2 x gridDim.x partial maxima (parity of the step).  DF: double-float updates
 // (the matrix is converted in place after the norm pass and back before the kernel ends).
 template <bool DF>
-__global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, double* pv, int* pi, GridSync* gs, double tol,
-                                             int vcap) {
+__global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, double* pv, int* pi, double tol, int vcap) {
   extern __shared__ cplx sv[];
   __shared__ long long redv[32];
   __shared__ int redi[32];
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
   __shared__ double redn[2 * kNW];
   __shared__ cplx s_v0;
   __shared__ double s_tau;
-  __shared__ dfc s_v0d;
+  __shared__ dfc s_v0d, s_betad;
   __shared__ float s_th, s_tl;
   int jid = 0;
   while (jid + 1 < nj && jobs[jid + 1].b0 <= (int)blockIdx.x) ++jid;
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
     block_argmax_key<kNT>(best, bi, redv, redi, &v, &ix);
     if (tid == 0) { pv[blockIdx.x] = __longlong_as_double(v); pi[blockIdx.x] = ix; }
   }
-  if (grid_sync_sum(gs, 0) < 0) return;
+  if (group_sync_sum(jb.gs, 0, (unsigned)jb.nb) < 0) return;
 
   double r00 = 0.0, thr2 = 0.0;
   bool done = false;
@@ -406,7 +406,6 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
     }
     if (!done) {
       const bool staged = (m - s - 1) <= vcap;
-      double sig = 0.0;
       if constexpr (DF) {
         const dfc* ap = D + (int64_t)p * m;
         dfc* svd = reinterpret_cast<dfc*>(sv);
@@ -416,41 +415,50 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
           df_abs2_acc(x, qh, ql);
           if (staged) svd[i - s - 1] = x;
         }
-        sig = f2d_bits(qh) + f2d_bits(ql);
+        // ||x_{s+1..}||^2 in warp 0, then the reflector by one thread, all in double-float
+        // on the FP32 pipes (an FP64 chain costs 64 cycles per instruction here)
+        block_sum_df_warp0<kNT>(qh, ql, reinterpret_cast<float*>(redsig));  // also publishes sv
+        if (tid == 0) {
+          dfc v0, beta;
+          float th, tl;
+          df_householder(ap[s], qh, ql, &v0, &beta, &th, &tl);
+          s_v0d = v0;
+          s_betad = beta;
+          s_th = th;
+          s_tl = tl;
+        }
+        __syncthreads();
+        if (lb == 0 && tid == 32) {  // FP64 copies for the finishing kernels, off the critical path
+          jb.piv[s] = p;
+          jb.beta[s] = from_dfc_bits(s_betad);
+          jb.v0[s] = from_dfc_bits(s_v0d);
+          jb.tau[s] = f2d_bits(s_th) + f2d_bits(s_tl);
+        }
       } else {
         const cplx* ap = A + (int64_t)p * m;
+        double sig = 0.0;
         for (int64_t i = s + 1 + tid; i < m; i += kNT) {
           const cplx x = ap[i];
           sig += cabs2(x);
           if (staged) sv[i - s - 1] = x;
         }
-      }
-      // The reflector's scalars are formed once per CTA, by lane 0 of warp 0.
-      sig = block_sum_warp0<kNT>(sig, redsig);  // also publishes sv to the CTA
-      if (tid == 0) {
-        cplx x0;
-        if constexpr (DF) x0 = from_dfc_bits(D[(int64_t)p * m + s]);
-        else x0 = A[(int64_t)p * m + s];
-        cplx v0, beta;
-        double tau;
-        householder_scalars(x0, sig, &v0, &beta, &tau);
-        s_v0 = v0;
-        s_tau = tau;
-        if constexpr (DF) {
-          s_v0d = to_dfc_bits(v0);
-          float th, tl;
-          df_split_bits(tau, th, tl);
-          s_th = th;
-          s_tl = tl;
+        // The reflector's scalars are formed once per CTA, by lane 0 of warp 0.
+        sig = block_sum_warp0<kNT>(sig, redsig);  // also publishes sv to the CTA
+        if (tid == 0) {
+          cplx v0, beta;
+          double tau;
+          householder_scalars(ap[s], sig, &v0, &beta, &tau);
+          s_v0 = v0;
+          s_tau = tau;
+          if (lb == 0) {
+            jb.piv[s] = p;
+            jb.beta[s] = beta;
+            jb.v0[s] = v0;
+            jb.tau[s] = tau;
+          }
         }
-        if (lb == 0) {
-          jb.piv[s] = p;
-          jb.beta[s] = beta;
-          jb.v0[s] = v0;
-          jb.tau[s] = tau;
-        }
+        __syncthreads();
       }
-      __syncthreads();
       long long best = kNoKey;
       int bi = 0x7fffffff;
       if constexpr (DF) {
@@ -523,11 +531,12 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
       block_argmax_key<kNT>(best, bi, redv, redi, &v, &ix);
       if (tid == 0) { pv[(1 - par) * G + blockIdx.x] = __longlong_as_double(v); pi[(1 - par) * G + blockIdx.x] = ix; }
     }
-    const long long act = grid_sync_sum(gs, (lb == 0 && !done) ? 1 : 0);
-    if (act <= 0) break;  // all matrices finished (0) or a wait gave up (-1)
+    const long long act = group_sync_sum(jb.gs, (lb == 0 && !done) ? 1 : 0, (unsigned)jb.nb);
+    if (act <= 0) break;  // this matrix is finished (0) or a wait gave up (-1)
   }
   if constexpr (DF) {
-    // Every CTA has left the step loop at the same barrier: no update is in flight.
+    // Every CTA of this matrix has left the step loop at the same barrier: no update of
+    // its columns is in flight.
     for (int64_t j = gw; j < n; j += nw)
       for (int64_t i = lane; i < m; i += 32) A[j * m + i] = from_dfc_bits(D[j * m + i]);
   }
@@ -832,10 +841,10 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
   out.v0.alloc(ktot);
   out.tau.alloc(ktot);
   DevBuf<PqrState> st(nj);
-  DevBuf<GridSync> gs(1);
+  DevBuf<GridSync> gs(nj);
   DevBuf<cplx> r11(std::max<int64_t>(r11tot, 1)), r11c(std::max<int64_t>(r11tot, 1)), invd(std::max<int64_t>(ktot, 1));
   HBS_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(PqrState) * nj, s));
-  HBS_CUDA(cudaMemsetAsync(gs.get(), 0, sizeof(GridSync), s));
+  HBS_CUDA(cudaMemsetAsync(gs.get(), 0, sizeof(GridSync) * nj, s));
   std::vector<PqrJob> jobs(nj);
   int64_t o = 0;
   int b0 = 0;
@@ -848,7 +857,7 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
     jobs[j] = {sp.A, sp.m, sp.n, sp.kcap, b0, nb[j], gwv, nrm.get() + o, nref.get() + o,
                out.piv.get() + out.koff[j], out.beta.get() + out.koff[j], out.v0.get() + out.koff[j],
                out.tau.get() + out.koff[j], st.get() + j, sp.perm, sp.T, r11.get() + r11off[j],
-               r11c.get() + r11off[j], invd.get() + out.koff[j], pos.get() + o};
+               r11c.get() + r11off[j], invd.get() + out.koff[j], pos.get() + o, gs.get() + j};
     o += sp.n;
     b0 += nb[j];
   }
@@ -858,12 +867,11 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
   int a1 = nj;
   double* a2 = pv.get();
   int* a3 = pi.get();
-  GridSync* a4 = gs.get();
   double a5 = tol;
   int a6 = vcap;
-  void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};
+  void* args[] = {&a0, &a1, &a2, &a3, &a5, &a6};
   std::vector<PqrState> hs(nj);
-  GridSync hg{};
+  std::vector<GridSync> hg(nj);
   {
     std::lock_guard<std::mutex> lock(coop_mutex());
     {
@@ -873,10 +881,11 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
     }
     HBS_LAUNCH_CHECK("k_pqr");
     HBS_CUDA(cudaMemcpyAsync(hs.data(), st.get(), sizeof(PqrState) * nj, cudaMemcpyDeviceToHost, s));
-    HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+    HBS_CUDA(cudaMemcpyAsync(hg.data(), gs.get(), sizeof(GridSync) * nj, cudaMemcpyDeviceToHost, s));
     HBS_CUDA(cudaStreamSynchronize(s));
   }
-  if (hg.timed_out) throw Error(HBS_ERR_TIMEOUT, "persistent QR: a grid barrier wait gave up");
+  for (const auto& g : hg)
+    if (g.timed_out) throw Error(HBS_ERR_TIMEOUT, "persistent QR: a barrier wait gave up");
   int kmax = 0;
   int64_t nmax = 0;
   for (int j = 0; j < nj; ++j) {

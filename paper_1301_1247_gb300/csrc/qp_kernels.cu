@@ -90,7 +90,7 @@ __global__ void k_fill_samples(DevGeom g, int S, double d, double y0, double shi
     const double sx = g.x[j] + shift_x, sy = g.y[j], nx = g.nx[j], ny = g.ny[j];
     cplx v;
     if (kind < 2) {
-      v = combined_kernel(tx, ty, sx, sy, nx, ny, omega);
+      v = combined_kernel(tx, ty, sx, sy, nx, ny, omega, g.df);
     } else {
       // target y-derivative of dG/dn_y - i w G (see the oracle's derivation):
       // f' = -(i w/4) H1, f'' = -(i w^2/4)(H0 - H1/(w r)), g = f'/r, g' = (f'' - f'/r)/r
@@ -98,7 +98,7 @@ __global__ void k_fill_samples(DevGeom g, int S, double d, double y0, double shi
       double r = sqrt(ddx * ddx + ddy * ddy);
       double z = omega * r;
       cplx h0, h1;
-      hankel01(z, &h0, &h1);
+      hankel01(z, &h0, &h1, g.df);
       cplx f1 = cmul(cmk(0.0, -0.25 * omega), h1);
       cplx f2 = cmul(cmk(0.0, -0.25 * omega * omega), csub(h0, cscale(h1, 1.0 / z)));
       cplx gg = cscale(f1, 1.0 / r);
@@ -150,6 +150,9 @@ __global__ void k_fill_wall_samples(const cplx* k, const cplx* wk, int M, int S,
 // proxy sources on the neighbour circle (centre cx, cy; radius R; np points; weight wp).
 __global__ void k_fill_nb(DevGeom g, const int64_t* near_m, int nm, const int64_t* near_p, int npn, double d, double cx,
                           double cy, double R, int np, double wp, cplx* Mt) {
+  extern __shared__ double sdir[];  // 2 np doubles: proxy directions, once per block
+  for (int p = threadIdx.x; p < np; p += blockDim.x) sincos(2.0 * HBS_PI * (double)p / (double)np, &sdir[np + p], &sdir[p]);
+  __syncthreads();
   const int m = nm + npn + np;
   const int64_t tot = (int64_t)m * g.n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
@@ -162,10 +165,9 @@ __global__ void k_fill_nb(DevGeom g, const int64_t* near_m, int nm, const int64_
       v = a_image_entry(g, i, near_p[r - nm], d);
     } else {
       const int p = r - nm - npn;
-      double sn, cs;
-      sincos(2.0 * HBS_PI * (double)p / (double)np, &sn, &cs);
+      const double cs = sdir[p], sn = sdir[np + p];
       cplx gg, dg;
-      proxy_kernels(g.x[i], g.y[i], cx + R * cs, cy + R * sn, cs, sn, g.omega, &gg, &dg);
+      proxy_kernels(g.x[i], g.y[i], cx + R * cs, cy + R * sn, cs, sn, g.omega, &gg, &dg, g.df);
       v = cscale(cadd(dg, cmul(cmk(0.0, -g.omega), gg)), wp);
     }
     Mt[i * (int64_t)m + r] = v;
@@ -515,13 +517,13 @@ __device__ __forceinline__ cplx e_entry(const DevGeom& g, int S, double d, doubl
   const double omega = g.omega;
   cplx v;
   if (kind < 2) {
-    v = combined_kernel(tx, ty, sx, sy, nx, ny, omega);
+    v = combined_kernel(tx, ty, sx, sy, nx, ny, omega, g.df);
   } else {
     double ddx = tx - sx, ddy = ty - sy;
     double rr2 = sqrt(ddx * ddx + ddy * ddy);
     double z = omega * rr2;
     cplx h0, h1;
-    hankel01(z, &h0, &h1);
+    hankel01(z, &h0, &h1, g.df);
     cplx f1 = cmul(cmk(0.0, -0.25 * omega), h1);
     cplx f2 = cmul(cmk(0.0, -0.25 * omega * omega), csub(h0, cscale(h1, 1.0 / z)));
     cplx gg = cscale(f1, 1.0 / rr2);

@@ -149,7 +149,10 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     DevBuf<cplx> Mt(m * N);
     {
       prof::KScope _ks("k_fill_nb", s);
-      k_fill_nb<<<grid_1d(m * N), 256, 0, s>>>(g, dnm.get(), nm, dnp.get(), npn, d, cx, cy, R, np, wp, Mt.get());
+      const size_t dsm = 2 * (size_t)np * sizeof(double);
+      if (dsm > 48 * 1024)
+        HBS_CUDA(cudaFuncSetAttribute(k_fill_nb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+      k_fill_nb<<<grid_1d(m * N), 256, dsm, s>>>(g, dnm.get(), nm, dnp.get(), npn, d, cx, cy, R, np, wp, Mt.get());
     }
     HBS_LAUNCH_CHECK("k_fill_nb");
     // Row ID of the neighbour interactions (Def. 3.1).  The skeleton is chosen by a
