@@ -39,6 +39,36 @@ UNIT = "angles/s"
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {"bf16_tflops": 1900.0}  # fallback: one earlier GB300 measurement
+
+
+MEASURED_PEAKS = _measured_peaks()
+# FP32-pipe instruction issue: 152 SM x 128 lanes x 2.07 GHz (instructions / s)
+FP32_INSTR_PEAK = 152 * 128 * 2.07e9
+
+
+def kernel_peak(name, prec):
+    """(bound, peak TFLOP/s, note) for a kernel's algorithmic FP64-equivalent rate, by the unit
+    that executes its arithmetic in this precision mode."""
+    if name == "k_oz_mma":
+        return ("tensor", MEASURED_PEAKS["bf16_tflops"],
+                "executed bf16 tensor flops (28 digit pairs x 4 real products x 2 m n k, padded tiles) "
+                "against the measured cuBLAS bf16 burst rate in MEASURED_PEAKS.json")
+    if name == "k_zgemm_batched_df" or (prec >= 1 and name in ("k_pqr", "k_cpqr")):
+        per = {"k_zgemm_batched_df": 48.0 / 8.0, "k_pqr": 102.0 / 16.0, "k_cpqr": 102.0 / 16.0}[name]
+        return ("alu", FP32_INSTR_PEAK / per / 1e12,
+                "double-float arithmetic on the FP32 pipes: %.2f FP32-pipe instructions per FP64-equivalent flop "
+                "(complex multiply-add = 4 error-free multiply-adds of 12 instructions) at 152 SM x 128 lanes x "
+                "2.07 GHz" % per)
+    return ("alu", FP64_PEAK_TFLOPS, "FP64 from unit counts x clock (152 SM x 2 DFMA/clk x 2.07 GHz); "
+                                      "no FP64 figure in MEASURED_PEAKS.json")
+
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
 # kernel's launches in one step of this bench's default workload) from one ncu capture,
 # with the digest of the sources the kernel is built from at capture time.  The figure
@@ -183,7 +213,7 @@ def run_ours(args, ws, rank, local):
     stream = torch.cuda.current_stream()
     tol = 1e-12
 
-    prec = 1 if args.precision == "df" else 0
+    prec = {"fp64": 0, "df": 1, "tc": 2}[args.precision]
     opts = hbs.default_options(precision=prec)
 
     def step(device_inputs: bool):
@@ -266,6 +296,7 @@ def run_ours(args, ws, rank, local):
     top = max(kern.items(), key=lambda kv: kv[1]["ms"])
     tname, tv = top
     achieved = tv["flops"] / (tv["ms"] / 1e3) / 1e12 if tv["ms"] > 0 else 0.0
+    kbound, kpeak, knote = kernel_peak(tname, prec)
     shares = {k: round(v["ms"] / sum(x["ms"] for x in kern.values()), 4) for k, v in
               sorted(kern.items(), key=lambda kv: -kv[1]["ms"])[:8]}
     # algorithmic FP64(-equivalent) rate of the top kernels that record flops
@@ -278,7 +309,10 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 (complex128); dense products in double-float (2xFP32)" if prec else "f64 (complex128)",
+        "dtype": {0: "f64 (complex128)",
+                  1: "f64 (complex128); dense products in double-float (2xFP32)",
+                  2: "f64 (complex128); dense products in double-float (2xFP32), K >= 4096 products on tcgen05 "
+                     "tensor cores from exact bf16 digit planes"}[prec],
         "data": "synthetic", "err_vs_fp64_plain_path": err,
         "config": {"workload": w["name"], "N": n, "omega": omega, "d": d, "angles": n_ang,
                    "bloch_groups": int(np.asarray(w["thetas"]).shape[0]) if np.asarray(w["thetas"]).ndim == 2 else None,
@@ -295,12 +329,12 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": round(ws * n_ang * args.steps / (e2e_ms / 1e3), 3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "alu", "kernel": tname, "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                     "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+        "roofline": {"bound": kbound, "kernel": tname, "achieved": round(achieved, 4), "peak": round(kpeak, 4),
+                     "unit": "TFLOP/s", "frac": round(achieved / kpeak, 4),
                      "traffic": measured_traffic(tname),
-                     "peak_note": "FP64 from unit counts x clock (152 SM x 2 DFMA/clk x 2.07 GHz); "
-                                  "no FP64 figure in MEASURED_PEAKS.json",
-                     "kernel_time_shares": shares, "kernel_tflops": rates},
+                     "peak_note": knote + " (of measured)" if kbound == "tensor" else knote,
+                     "kernel_time_shares": shares, "kernel_tflops": rates,
+                     "kernel_frac": {k: round(r / kernel_peak(k, prec)[1], 4) for k, r in rates.items()}},
         "clocks": clocks,
     }
     return out
@@ -361,7 +395,7 @@ def main():
     ap.add_argument("--cpu-sample-n", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 plain-path accuracy check")
-    ap.add_argument("--precision", choices=["fp64", "df"], default="df")
+    ap.add_argument("--precision", choices=["fp64", "df", "tc"], default="tc")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":

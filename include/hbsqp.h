@@ -60,6 +60,13 @@ typedef struct hbs_geometry {
  * significant bits, relative error near 1e-14 per product).  Kernel evaluations, the
  * interpolative decompositions, the inversions and the Schur solves stay in FP64. */
 #define HBS_PRECISION_DOUBLE_FLOAT 1
+/* As HBS_PRECISION_DOUBLE_FLOAT, and the large dense products (inner dimension >= 4096,
+ * at least 64 rows) run on the tcgen05 tensor cores: every FP64 row of op(A) and column
+ * of B is scaled by a power of two and cut into seven 7-bit integer digits held exactly
+ * in bf16; the digit products are accumulated exactly in FP32 tensor memory over 64
+ * values of k and recombined in double-float arithmetic (relative error about 2^-46 of
+ * max|a_ik| max|b_kj| per product term). */
+#define HBS_PRECISION_TENSOR 2
 
 typedef struct hbs_options {
   int leaf_size;        /* maximum points per leaf of the binary tree (default 64) */
@@ -75,7 +82,7 @@ typedef struct hbs_options {
   double wood_shift;    /* crossing point t0 of the second contour (0: automatic, < 0: none) */
   int n_bragg_samples;  /* samples per line for the Bragg DFT (0: automatic) */
   double y0;            /* Bragg sampling height (0: max |y| + d/4) */
-  int precision;        /* HBS_PRECISION_FP64 (default) or HBS_PRECISION_DOUBLE_FLOAT */
+  int precision;        /* HBS_PRECISION_FP64 (default), _DOUBLE_FLOAT or _TENSOR */
 } hbs_options;
 
 typedef struct hbs_info_t {
@@ -261,6 +268,21 @@ hbs_status hbs_kernel_block(const hbs_geometry* geom, double omega, int kind, do
  */
 hbs_status hbs_row_id(void* mt, int64_t m, int64_t n, double tol, int* rank, int* perm, void* t,
                       void* stream);
+
+/*
+ * Complex GEMM on device arrays (complex128, column-major):
+ *   C = alpha op(A) B + beta C,
+ * op(A) = A (m x k, lda >= m) or, with trans_a = 1, A^T (A stored k x m, lda >= k);
+ * B is k x n (ldb >= k) and C m x n (ldc >= m); alpha and beta point to two host doubles
+ * (re, im).  precision selects the arithmetic of the library's dense products:
+ * HBS_PRECISION_FP64, _DOUBLE_FLOAT or _TENSOR (see above; products below the tensor
+ * size limits use double-float).  Returns HBS_ERR_INVALID_ARG for negative sizes, short
+ * leading dimensions, null pointers with nonzero sizes or an unknown precision, and
+ * HBS_ERR_TIMEOUT if a tensor-core completion wait gave up.  Synchronizes the stream.
+ */
+hbs_status hbs_zgemm(int64_t m, int64_t n, int64_t k, const double* alpha, const void* a, int64_t lda, int trans_a,
+                     const void* b, int64_t ldb, const double* beta, void* c, int64_t ldc, int precision,
+                     void* stream);
 
 /*
  * Profiling.  hbs_launch_count() is the number of kernels this library has

@@ -20,6 +20,11 @@ bool& gemm_double_float() {
   return df;
 }
 
+bool& gemm_tensor() {
+  static thread_local bool tc = false;
+  return tc;
+}
+
 std::mutex& coop_mutex() {
   static std::mutex mu;
   return mu;
@@ -157,7 +162,8 @@ void prepare_handle(Handle& h, const hbs_geometry* geom, double omega, double to
   if (h.opts.leaf_size < 8) h.opts.leaf_size = 64;
   if (h.opts.n_proxy_min < 8) h.opts.n_proxy_min = 64;
   if (!(h.opts.proxy_rho > 1.0)) h.opts.proxy_rho = 1.5;
-  if (h.opts.precision != HBS_PRECISION_FP64 && h.opts.precision != HBS_PRECISION_DOUBLE_FLOAT)
+  if (h.opts.precision != HBS_PRECISION_FP64 && h.opts.precision != HBS_PRECISION_DOUBLE_FLOAT &&
+      h.opts.precision != HBS_PRECISION_TENSOR)
     throw Error(HBS_ERR_INVALID_ARG, "unsupported precision mode");
   h.omega = omega;
   h.tol = tol;
@@ -181,7 +187,7 @@ hbs_status hbs_build(const hbs_geometry* geom, double omega, double tol, const h
     Handle& h = hh->h;
     auto t0 = std::chrono::steady_clock::now();
     prepare_handle(h, geom, omega, tol, opts, s);
-    GemmModeScope gm(h.opts.precision == HBS_PRECISION_DOUBLE_FLOAT);
+    GemmModeScope gm(h.opts.precision);
     {
       prof::Phase ph("build:hbs_compress_invert", s);
       build_hbs(h, s);
@@ -225,7 +231,7 @@ hbs_status hbs_build_batch(const hbs_geometry* geoms, const double* omegas, int6
       hs[i] = &hh[i]->h;
       prepare_handle(*hs[i], geoms + i, omegas[i], tol, opts, s);
     }
-    GemmModeScope gm(hs[0]->opts.precision == HBS_PRECISION_DOUBLE_FLOAT);
+    GemmModeScope gm(hs[0]->opts.precision);
     {
       prof::Phase ph("build:hbs_compress_invert", s);
       build_hbs_multi(hs, s);
@@ -255,7 +261,7 @@ static hbs_status solve_common(hbs_handle* h, const double* theta, int64_t n_the
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   StreamScope scope(s);
   hbs_status st = guarded([&] {
-    GemmModeScope gm(h->h.opts.precision == HBS_PRECISION_DOUBLE_FLOAT && !plain);
+    GemmModeScope gm(plain ? HBS_PRECISION_FP64 : h->h.opts.precision);
     solve_angles(h->h, theta, n_theta, plain, r->r, s);
     HBS_CUDA(cudaStreamSynchronize(s));
   });
@@ -337,7 +343,7 @@ hbs_status hbs_apply_inverse(const hbs_handle* hh, const void* b, void* x, int64
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   StreamScope scope(s);
   return guarded([&] {
-    GemmModeScope gm(hh->h.opts.precision == HBS_PRECISION_DOUBLE_FLOAT);
+    GemmModeScope gm(hh->h.opts.precision);
     hh->h.apply_inverse(static_cast<const cplx*>(b), static_cast<cplx*>(x), nrhs, s);
     HBS_CUDA(cudaStreamSynchronize(s));
   });
@@ -362,6 +368,41 @@ hbs_status hbs_kernel_block(const hbs_geometry* geom, double omega, int kind, do
       }
       HBS_LAUNCH_CHECK("k_kernel_block");
     }
+    HBS_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+hbs_status hbs_zgemm(int64_t m, int64_t n, int64_t k, const double* alpha, const void* a, int64_t lda, int trans_a,
+                     const void* b, int64_t ldb, const double* beta, void* c, int64_t ldc, int precision,
+                     void* stream) {
+  const bool sizes_ok = m >= 0 && n >= 0 && k >= 0 && m <= INT32_MAX && n <= INT32_MAX && k <= INT32_MAX;
+  if (!sizes_ok || !alpha || !beta || (precision < HBS_PRECISION_FP64 || precision > HBS_PRECISION_TENSOR) ||
+      ldc < std::max<int64_t>(1, m) || ldb < std::max<int64_t>(1, k) ||
+      lda < std::max<int64_t>(1, trans_a ? k : m) || lda > INT32_MAX || ldb > INT32_MAX || ldc > INT32_MAX ||
+      (m > 0 && n > 0 && (!c || (k > 0 && (!a || !b))))) {
+    set_last_error("bad arguments to hbs_zgemm");
+    return HBS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScope scope(s);
+  return guarded([&] {
+    if (m == 0 || n == 0) return;
+    GemmModeScope gm(precision);
+    GemmJob j{};
+    j.A = static_cast<const cplx*>(a);
+    j.B = static_cast<const cplx*>(b);
+    j.C = static_cast<cplx*>(c);
+    j.m = (int)m;
+    j.n = (int)n;
+    j.k = (int)k;
+    j.lda = (int)lda;
+    j.ldb = (int)ldb;
+    j.ldc = (int)ldc;
+    j.alpha = cmk(alpha[0], alpha[1]);
+    j.beta = cmk(beta[0], beta[1]);
+    j.transA = trans_a ? 1 : 0;
+    std::vector<GemmJob> jobs{j};
+    run_gemms(jobs, s);
     HBS_CUDA(cudaStreamSynchronize(s));
   });
 }

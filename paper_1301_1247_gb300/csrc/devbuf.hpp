@@ -100,10 +100,20 @@ bool& gemm_double_float();
 // finish: at most one such kernel is in flight on the device, whatever the number of
 // threads and streams using the library.
 std::mutex& coop_mutex();
+// Large products on the tensor cores (digit-plane splitting) on this thread.
+bool& gemm_tensor();
+
+// Sets the thread's arithmetic modes from an HBS_PRECISION_* value for a call's duration.
 struct GemmModeScope {
-  bool prev;
-  explicit GemmModeScope(bool df) : prev(gemm_double_float()) { gemm_double_float() = df; }
-  ~GemmModeScope() { gemm_double_float() = prev; }
+  bool prev, prev_tc;
+  explicit GemmModeScope(int precision) : prev(gemm_double_float()), prev_tc(gemm_tensor()) {
+    gemm_double_float() = precision == HBS_PRECISION_DOUBLE_FLOAT || precision == HBS_PRECISION_TENSOR;
+    gemm_tensor() = precision == HBS_PRECISION_TENSOR;
+  }
+  ~GemmModeScope() {
+    gemm_double_float() = prev;
+    gemm_tensor() = prev_tc;
+  }
 };
 
 struct StreamScope {

@@ -336,7 +336,14 @@ __global__ void k_splitk_reduce(const SplitRed* reds, int nred) {
 // Batched GEMMs.  Jobs with a long inner dimension and few output tiles (tall-skinny
 // products over all N boundary nodes) are split along K so that every SM gets work; the
 // partial products are summed in a fixed order by k_splitk_reduce.
-static void launch_gemms(std::vector<GemmJob>& jobs_in, cudaStream_t s) {
+static void launch_gemms(std::vector<GemmJob>& jobs_all, cudaStream_t s) {
+  if (jobs_all.empty()) return;
+  // large products on the tensor cores when the thread's mode asks for it
+  std::vector<GemmJob> jobs_in;
+  for (const auto& j : jobs_all) {
+    if (gemm_tensor() && ozaki_eligible(j)) ozaki_gemm(j, s);
+    else jobs_in.push_back(j);
+  }
   if (jobs_in.empty()) return;
   double fl = 0.0, by = 0.0;
   for (const auto& j : jobs_in) {

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "RANK", 5: "W
 # Every entry point declared in include/hbsqp.h.
 EXPORTED = ("hbs_default_options", "hbs_build", "hbs_build_batch", "hbs_solve", "hbs_solve_plain", "hbs_bragg_amplitudes",
             "hbs_result_angle_info", "hbs_info", "hbs_save", "hbs_load", "hbs_apply_inverse",
-            "hbs_kernel_block", "hbs_row_id",
+            "hbs_kernel_block", "hbs_row_id", "hbs_zgemm",
             "hbs_row_id_static",
             "hbs_profile_enable", "hbs_profile_reset", "hbs_profile_get", "hbs_launch_count",
             "hbs_server_create", "hbs_server_add", "hbs_server_remove", "hbs_server_submit", "hbs_server_wait",
@@ -126,6 +126,9 @@ def lib():
     L.hbs_kernel_block.argtypes = [ctypes.POINTER(Geometry), dbl, ci, dbl, vp, i64, vp, i64, vp, vp]
     L.hbs_row_id.argtypes = [vp, i64, i64, dbl, ctypes.POINTER(ci), vp, vp, vp]
     L.hbs_row_id_static.argtypes = [vp, i64, i64, dbl, ctypes.POINTER(ci), vp, vp, vp]
+    L.hbs_zgemm.argtypes = [i64, i64, i64, ctypes.POINTER(dbl), vp, i64, ci, vp, i64, ctypes.POINTER(dbl), vp, i64,
+                            ci, vp]
+    L.hbs_zgemm.restype = ci
     L.hbs_profile_enable.argtypes = [ci]
     L.hbs_profile_enable.restype = None
     L.hbs_profile_reset.argtypes = []
@@ -373,6 +376,17 @@ def row_id(mt, m, n, tol, perm, t, stream=None) -> int:
     _check(lib().hbs_row_id(_ptr(mt), int(m), int(n), float(tol), ctypes.byref(rank), _ptr(perm), _ptr(t),
                             _stream(stream)), "hbs_row_id")
     return rank.value
+
+
+PRECISION_FP64, PRECISION_DOUBLE_FLOAT, PRECISION_TENSOR = 0, 1, 2
+
+
+def zgemm(m, n, k, alpha, a, lda, trans_a, b, ldb, beta, c, ldc, precision=PRECISION_FP64, stream=None):
+    """hbs_zgemm: C = alpha op(A) B + beta C on device complex128 arrays (column-major)."""
+    al = (ctypes.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+    be = (ctypes.c_double * 2)(complex(beta).real, complex(beta).imag)
+    _check(lib().hbs_zgemm(int(m), int(n), int(k), al, _ptr(a), int(lda), int(trans_a), _ptr(b), int(ldb), be, _ptr(c),
+                           int(ldc), int(precision), _stream(stream)), "hbs_zgemm")
 
 
 ROW_ID_STATIC_MAX_N = 262144
