@@ -339,11 +339,12 @@ __global__ void k_splitk_reduce(const SplitRed* reds, int nred) {
 static void launch_gemms(std::vector<GemmJob>& jobs_all, cudaStream_t s) {
   if (jobs_all.empty()) return;
   // large products on the tensor cores when the thread's mode asks for it
-  std::vector<GemmJob> jobs_in;
+  std::vector<GemmJob> jobs_in, jobs_tc;
   for (const auto& j : jobs_all) {
-    if (gemm_tensor() && ozaki_eligible(j)) ozaki_gemm(j, s);
+    if (gemm_tensor() && ozaki_eligible(j)) jobs_tc.push_back(j);
     else jobs_in.push_back(j);
   }
+  ozaki_gemm_batched(jobs_tc, s);
   if (jobs_in.empty()) return;
   double fl = 0.0, by = 0.0;
   for (const auto& j : jobs_in) {

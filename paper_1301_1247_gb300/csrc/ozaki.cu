@@ -13,10 +13,12 @@
 // double-float arithmetic (FP32 pipes) into a running double-float sum per output.
 //
 // Per CTA: 128 x 32 outputs; tensor memory holds 7 levels x (re, im) x 32 columns of FP32
-// accumulators (448 of the 512 columns).  Shared memory is a ring of three stages of 16 k,
-// each with 14 A sub-tiles (7 digits x re/im, 128 x 16 bf16) and 14 B sub-tiles (32 x 16),
-// in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes), filled by cp.async two
-// stages ahead of the MMAs.  One thread issues the 112 MMAs of a stage (M = 128, N = 32,
+// accumulators (level l in columns 32 l and 256 + 32 l).  Shared memory is a ring of three
+// stages of 16 k, each with 14 A sub-tiles (re/im x 7 digits, 128 x 16 bf16) and 14 B
+// sub-tiles (32 x 16), in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes),
+// filled by cp.async two stages ahead of the MMAs.  Since B's digit sub-tiles follow one
+// another, digit i of A meets digits 0..6-i of B in a single MMA of N = 32 (7 - i) columns
+// whose result falls into the levels i..6: one thread issues 28 MMAs per stage (M = 128,
 // K = 16) and commits them to the stage buffer's mbarrier; every wait is bounded (one
 // second) and a timeout is reported through a status word.
 #include <algorithm>
@@ -51,20 +53,36 @@ __device__ __forceinline__ int exp_above(unsigned long long absbits) {
   return e == 0 ? -2000 : e - 1022;
 }
 
-// max(|Re|, |Im|) over one row of op(A) (rows = m, trans: A stored k x m) or one column of
-// B (K x n, column-major): one warp per row, integer compares on the magnitude bits.
-__global__ void k_oz_exponents(const cplx* X, int ld, int strided, int rows, int K, int* E) {
-  const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (warp >= rows) return;
-  unsigned long long mx = 0;
-  for (int k = lane; k < K; k += 32) {
-    const cplx v = strided ? X[(int64_t)k * ld + warp] : X[(int64_t)warp * ld + k];
-    const unsigned long long a = (unsigned long long)__double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFull;
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFull;
-    mx = max(mx, max(a, b));
+// One operand of one product: op(X) is rows x K with element (r, k) at X[r ld + k] (trans)
+// or X[k ld + r]; its exponents and digit planes (14 planes of rows_pad x Kpad bf16) go to
+// E and out.
+struct OzOperand {
+  const cplx* X;
+  int ld, trans;
+  int rows, K, rows_pad, Kpad;
+  int* E;
+  unsigned short* out;
+};
+
+// max(|Re|, |Im|) over each row of operand blockIdx.y: one warp per row, integer compares on
+// the magnitude bits.  Rows past `rows` (padding) get the zero-row exponent.
+__global__ void k_oz_exponents(const OzOperand* ops) {
+  const OzOperand op = ops[blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  for (int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); r < op.rows_pad;
+       r += (int)((gridDim.x * (int64_t)blockDim.x) >> 5)) {
+    unsigned long long mx = 0;
+    if (r < op.rows) {
+      for (int k = lane; k < op.K; k += 32) {
+        const cplx v = op.trans ? op.X[(int64_t)r * op.ld + k] : op.X[(int64_t)k * op.ld + r];
+        const unsigned long long a = (unsigned long long)__double_as_longlong(v.x) & 0x7FFFFFFFFFFFFFFFull;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v.y) & 0x7FFFFFFFFFFFFFFFull;
+        mx = max(mx, max(a, b));
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, (unsigned long long)__shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) op.E[r] = exp_above(mx);
   }
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, (unsigned long long)__shfl_xor_sync(0xffffffffu, mx, o));
-  if (lane == 0) E[warp] = exp_above(mx);
 }
 
 // bf16 bits of the small integer (-1)^sign q (0 <= q <= 128), exact.
@@ -95,18 +113,17 @@ __device__ __forceinline__ void digits_of(double x, int E, unsigned short* out) 
   out[OZ_S - 1] = bf16_of_digit((unsigned int)(r < 0 ? -r : r), sign ^ (r < 0 ? 1u : 0u));
 }
 
-// Digit planes of op(X) (rows x K) into out[(d * 2 + part) * rows_pad * Kpad + r * Kpad + k]
-// (bf16; zero beyond rows and K).  trans = 0: element (r, k) at X[k * ld + r]; 1: X[r * ld + k].
-__global__ void k_oz_digits(const cplx* X, int ld, int trans, int rows, int K, const int* E, int rows_pad, int Kpad,
-                            unsigned short* out) {
-  const int64_t plane = (int64_t)rows_pad * Kpad;
-  const int64_t tot = plane;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e / Kpad), k = (int)(e % Kpad);
+// Digit planes of operand blockIdx.y: out[(part * 7 + d) * rows_pad * Kpad + r * Kpad + k]
+// (bf16; zero beyond rows and K).
+__global__ void k_oz_digits(const OzOperand* ops) {
+  const OzOperand op = ops[blockIdx.y];
+  const int64_t plane = (int64_t)op.rows_pad * op.Kpad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / op.Kpad), k = (int)(e % op.Kpad);
     unsigned short dre[OZ_S], dim[OZ_S];
-    if (r < rows && k < K) {
-      const cplx v = trans ? X[(int64_t)r * ld + k] : X[(int64_t)k * ld + r];
-      const int Er = E[r];
+    if (r < op.rows && k < op.K) {
+      const cplx v = op.trans ? op.X[(int64_t)r * op.ld + k] : op.X[(int64_t)k * op.ld + r];
+      const int Er = op.E[r];
       digits_of(v.x, Er, dre);
       digits_of(v.y, Er, dim);
     } else {
@@ -115,8 +132,8 @@ __global__ void k_oz_digits(const cplx* X, int ld, int trans, int rows, int K, c
     }
 #pragma unroll
     for (int i = 0; i < OZ_S; ++i) {
-      out[(2 * i) * plane + e] = dre[i];
-      out[(2 * i + 1) * plane + e] = dim[i];
+      op.out[i * plane + e] = dre[i];
+      op.out[(OZ_S + i) * plane + e] = dim[i];
     }
   }
 }
@@ -132,9 +149,9 @@ __device__ __forceinline__ uint64_t oz_desc(uint32_t addr) {
          ((uint64_t)1 << 46);
 }
 
-// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major, M = 128, N = 32.
-__host__ __device__ constexpr uint32_t oz_idesc(bool negA) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(OZ_BN >> 3) << 17) |
+// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major, M = 128, N columns.
+__host__ __device__ constexpr uint32_t oz_idesc(bool negA, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(OZ_BM >> 4) << 24);
 }
 
@@ -197,20 +214,30 @@ __device__ __forceinline__ void oz_load_stage(unsigned char* buf, const unsigned
   }
 }
 
-// grid (tiles_m, tiles_n, splits).  Ad: digit planes of op(A) (mpad x Kpad), Bd: of B^T
-// (npad x Kpad).  Split z covers k in [z klen, (z + 1) klen) (klen a multiple of 128).
-// W: m x n (ld m) per split, alpha 2^{E_r + E_c - 14} sum_l 2^{-7 l} S_l in FP64.
-__global__ void __launch_bounds__(128, 1) k_oz_mma(const unsigned short* Ad, const unsigned short* Bd, int mpad,
-                                                    int npad, int Kpad, int klen, const int* Er, const int* Ec,
-                                                    int m, int n, cplx alpha, cplx* W, int* status) {
+// One product of a batch on the tensor cores.  Work items are (tile_m, tile_n, split);
+// item_base is the prefix sum of tiles_m tiles_n splits over the earlier jobs.
+struct OzJob {
+  const unsigned short* Ad;  // digit planes of op(A): 14 x mpad x Kpad
+  const unsigned short* Bd;  // digit planes of B^T: 14 x npad x Kpad
+  const int* Er;
+  const int* Ec;
+  int m, n, mpad, npad, Kpad, klen, splits, tiles_m, tiles_n;
+  int64_t item_base;
+  cplx alpha, beta;
+  cplx* C;  // splits == 1: C = alpha op(A) B + beta C directly
+  int ldc;
+  cplx* W;  // splits > 1: alpha (partial product) per split, splits x (m x n), reduced afterwards
+};
+
+// Persistent: CTA b takes items b, b + gridDim.x, ...; tensor memory, the mbarriers and the
+// shared-memory ring stay with the CTA across items (the stage counter G runs on, so every
+// buffer's barrier phase is known).  Each item runs the pipeline of the head comment over
+// its k range and writes its 128 x 32 outputs.
+__global__ void __launch_bounds__(128, 1) k_oz_mma(const OzJob* jobs, int njobs, int64_t nitems, int* status) {
   extern __shared__ __align__(1024) unsigned char oz_smem[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bar[OZ_RING];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int row0 = blockIdx.x * OZ_BM, col0 = blockIdx.y * OZ_BN;
-  const int k0 = blockIdx.z * klen, k1 = min(Kpad, k0 + klen);
-  const int nst = (k1 - k0) / OZ_BK;
-  const int64_t aplane = (int64_t)mpad * Kpad, bplane = (int64_t)npad * Kpad;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&s_tmem)));
@@ -222,114 +249,148 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const unsigned short* Ad, con
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
-
-  float Rh[2][OZ_BN], Rl[2][OZ_BN];  // running double-float sums (re, im) of this thread's row
-#pragma unroll
-  for (int p = 0; p < 2; ++p)
-#pragma unroll
-    for (int c = 0; c < OZ_BN; ++c) Rh[p][c] = Rl[p][c] = 0.f;
-
-  // prologue: stages 0 and 1 in flight
-  oz_load_stage(oz_smem, Ad, Bd, aplane, bplane, Kpad, row0, col0, k0, tid);
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  if (nst > 1) oz_load_stage(oz_smem + OZ_STAGE, Ad, Bd, aplane, bplane, Kpad, row0, col0, k0 + OZ_BK, tid);
-  asm volatile("cp.async.commit_group;" ::: "memory");
-
-  bool ok = true;
   const int per_flush = OZ_FLUSH / OZ_BK;
-  for (int st = 0; st < nst && ok; ++st) {
-    const int buf = st % OZ_RING;
-    unsigned char* sbuf = oz_smem + buf * OZ_STAGE;
-    asm volatile("cp.async.wait_group 1;" ::: "memory");  // stage st has landed (st + 1 may be in flight)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t ip = oz_idesc(false), in = oz_idesc(true);
-      const uint64_t dA = oz_desc(smem_u32(sbuf)), dB = oz_desc(smem_u32(sbuf + OZ_NSUB * OZ_A_SUB));
-      const bool fresh = (st % per_flush) == 0;
+  bool ok = true;
+  uint32_t G = 0;  // stages issued by this CTA so far
+
+  for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].item_base <= item) lo = mid; else hi = mid - 1;
+    }
+    const OzJob& jb = jobs[lo];
+    const int64_t local = item - jb.item_base;
+    const int per = jb.tiles_m * jb.tiles_n;
+    const int z = (int)(local / per), t2 = (int)(local % per);
+    const int row0 = (t2 % jb.tiles_m) * OZ_BM, col0 = (t2 / jb.tiles_m) * OZ_BN;
+    const int k0 = z * jb.klen, k1 = min(jb.Kpad, k0 + jb.klen);
+    const int nst = (k1 - k0) / OZ_BK;
+    const int Kpad = jb.Kpad;
+    const int64_t aplane = (int64_t)jb.mpad * Kpad, bplane = (int64_t)jb.npad * Kpad;
+    const unsigned short* Ad = jb.Ad;
+    const unsigned short* Bd = jb.Bd;
+
+    float Rh[2][OZ_BN], Rl[2][OZ_BN];  // running double-float sums (re, im) of this thread's row
 #pragma unroll
-      for (int l = 0; l < OZ_S; ++l) {
-        const uint32_t dre = tmem + 64 * l, dim = dre + 32;
+    for (int p = 0; p < 2; ++p)
 #pragma unroll
-        for (int i = 0; i <= l; ++i) {
-          const int j = l - i;
-          const uint64_t ar = dA + (uint64_t)((2 * i) * (OZ_A_SUB >> 4)), ai = ar + (OZ_A_SUB >> 4);
-          const uint64_t br = dB + (uint64_t)((2 * j) * (OZ_B_SUB >> 4)), bi = br + (OZ_B_SUB >> 4);
+      for (int c = 0; c < OZ_BN; ++c) Rh[p][c] = Rl[p][c] = 0.f;
+
+    // every earlier MMA has completed (the last flush waited for it): all buffers are free
+    oz_load_stage(oz_smem + (G % OZ_RING) * OZ_STAGE, Ad, Bd, aplane, bplane, Kpad, row0, col0, k0, tid);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    if (nst > 1)
+      oz_load_stage(oz_smem + ((G + 1) % OZ_RING) * OZ_STAGE, Ad, Bd, aplane, bplane, Kpad, row0, col0, k0 + OZ_BK,
+                    tid);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+
+    for (int st = 0; st < nst && ok; ++st) {
+      const uint32_t gs = G + (uint32_t)st;
+      const int buf = (int)(gs % OZ_RING);
+      unsigned char* sbuf = oz_smem + buf * OZ_STAGE;
+      asm volatile("cp.async.wait_group 1;" ::: "memory");  // stage st has landed (st + 1 may be in flight)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t dA = oz_desc(smem_u32(sbuf)), dB = oz_desc(smem_u32(sbuf + OZ_NSUB * OZ_A_SUB));
+        const bool fresh = (st % per_flush) == 0;
+        // digit i of A against digits 0..6-i of B in one MMA: B's digit sub-tiles lie one
+        // after another (32 rows each), and level l = i + j sits in columns 32 l (re) and
+        // 256 + 32 l (im), so the product lands in the levels i..6 at once.
+#pragma unroll
+        for (int i = 0; i < OZ_S; ++i) {
+          const int N = OZ_BN * (OZ_S - i);
+          const uint32_t ip = oz_idesc(false, N), in = oz_idesc(true, N);
+          const uint64_t ar = dA + (uint64_t)(i * (OZ_A_SUB >> 4)), ai = dA + (uint64_t)((OZ_S + i) * (OZ_A_SUB >> 4));
+          const uint64_t br = dB, bi = dB + (uint64_t)(OZ_S * (OZ_B_SUB >> 4));
+          const uint32_t dre = tmem + OZ_BN * i, dim = tmem + 256 + OZ_BN * i;
           const uint32_t first = (fresh && i == 0) ? 0u : 1u;
           oz_mma(dre, ar, br, ip, first);  // re += Ar Br
           oz_mma(dre, ai, bi, in, 1u);     // re -= Ai Bi
           oz_mma(dim, ar, bi, ip, first);  // im += Ar Bi
           oz_mma(dim, ai, br, ip, 1u);     // im += Ai Br
         }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&s_bar[buf]))
+                     : "memory");
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&s_bar[buf]))
-                   : "memory");
-    }
-    __syncwarp();
-    // refill the buffer of stage st - 1 with stage st + 2 once its MMAs are done
-    if (st + 2 < nst) {
-      if (st >= 1) {
-        const int pb = (st - 1) % OZ_RING;
-        if (!oz_wait(smem_u32(&s_bar[pb]), (uint32_t)(((st - 1) / OZ_RING) & 1))) ok = false;
+      __syncwarp();
+      // refill the buffer of stage st - 1 with stage st + 2 once its MMAs are done
+      if (st + 2 < nst) {
+        if (st >= 1) {
+          const uint32_t pg = gs - 1;
+          if (!oz_wait(smem_u32(&s_bar[pg % OZ_RING]), (pg / OZ_RING) & 1u)) ok = false;
+        }
+        oz_load_stage(oz_smem + ((gs + 2) % OZ_RING) * OZ_STAGE, Ad, Bd, aplane, bplane, Kpad, row0, col0,
+                      k0 + (st + 2) * OZ_BK, tid);
       }
-      oz_load_stage(oz_smem + ((st + 2) % OZ_RING) * OZ_STAGE, Ad, Bd, aplane, bplane, Kpad, row0, col0,
-                    k0 + (st + 2) * OZ_BK, tid);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");  // possibly empty: keeps the group count uniform
-    if ((st % per_flush) == per_flush - 1 || st == nst - 1) {
-      if (!oz_wait(smem_u32(&s_bar[buf]), (uint32_t)((st / OZ_RING) & 1))) ok = false;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (ok) {
-        // T = sum_l 2^{-7 l} S_l (Horner from l = 6), R += T, in double-float
-        const uint32_t lanebase = tmem + ((uint32_t)(warp * 32) << 16);
+      asm volatile("cp.async.commit_group;" ::: "memory");  // possibly empty: keeps the group count uniform
+      if ((st % per_flush) == per_flush - 1 || st == nst - 1) {
+        if (!oz_wait(smem_u32(&s_bar[buf]), (gs / OZ_RING) & 1u)) ok = false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) {
+          // T = sum_l 2^{-7 l} S_l (Horner from l = 6), R += T, in double-float
+          const uint32_t lanebase = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
+          for (int p = 0; p < 2; ++p) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float th[16], tl[16], sv[16];
+            for (int h = 0; h < 2; ++h) {
+              float th[16], tl[16], sv[16];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) th[c] = tl[c] = 0.f;
+              for (int c = 0; c < 16; ++c) th[c] = tl[c] = 0.f;
 #pragma unroll 1
-            for (int l = OZ_S - 1; l >= 0; --l) {
-              tmem_ld16(lanebase + 64 * l + 32 * p + 16 * h, sv);
+              for (int l = OZ_S - 1; l >= 0; --l) {
+                tmem_ld16(lanebase + 256 * p + OZ_BN * l + 16 * h, sv);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                  th[c] *= 0.0078125f;  // 2^-7, exact
+                  tl[c] *= 0.0078125f;
+                  df_add_to(sv[c], 0.f, th[c], tl[c]);
+                  df_norm(th[c], tl[c]);
+                }
+              }
 #pragma unroll
               for (int c = 0; c < 16; ++c) {
-                th[c] *= 0.0078125f;  // 2^-7, exact
-                tl[c] *= 0.0078125f;
-                df_add_to(sv[c], 0.f, th[c], tl[c]);
-                df_norm(th[c], tl[c]);
+                df_add_to(th[c], tl[c], Rh[p][16 * h + c], Rl[p][16 * h + c]);
+                df_norm(Rh[p][16 * h + c], Rl[p][16 * h + c]);
               }
-            }
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              df_add_to(th[c], tl[c], Rh[p][16 * h + c], Rl[p][16 * h + c]);
-              df_norm(Rh[p][16 * h + c], Rl[p][16 * h + c]);
             }
           }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // tensor memory may be overwritten by the next period's MMAs
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();  // tensor memory may be overwritten by the next period's MMAs
     }
-  }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  // ---- epilogue: scale and store this split's partial result
-  const int row = row0 + warp * 32 + lane;
-  if (row < m && ok) {
-    const int er = Er[row];
+    G += (uint32_t)nst;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // ---- epilogue: this item's 128 x 32 outputs (row of this thread)
+    const int row = row0 + warp * 32 + lane;
+    if (row < jb.m && ok) {
+      const int er = jb.Er[row];
+      const cplx al = jb.alpha, be = jb.beta;
+      const bool with_beta = jb.splits == 1 && (be.x != 0.0 || be.y != 0.0);
 #pragma unroll
-    for (int c = 0; c < OZ_BN; ++c) {
-      const int col = col0 + c;
-      if (col >= n) break;
-      const int sc = er + Ec[col] - 14;
-      const double re = ldexp(f2d_bits(Rh[0][c]) + f2d_bits(Rl[0][c]), sc);
-      const double im = ldexp(f2d_bits(Rh[1][c]) + f2d_bits(Rl[1][c]), sc);
-      W[((int64_t)blockIdx.z * n + col) * m + row] = cmk(alpha.x * re - alpha.y * im, alpha.x * im + alpha.y * re);
+      for (int c = 0; c < OZ_BN; ++c) {
+        const int col = col0 + c;
+        if (col >= jb.n) break;
+        const int sc = er + jb.Ec[col] - 14;
+        const double re = ldexp(f2d_bits(Rh[0][c]) + f2d_bits(Rl[0][c]), sc);
+        const double im = ldexp(f2d_bits(Rh[1][c]) + f2d_bits(Rl[1][c]), sc);
+        cplx v = cmk(al.x * re - al.y * im, al.x * im + al.y * re);
+        if (jb.splits == 1) {
+          cplx* cp = jb.C + (int64_t)col * jb.ldc + row;
+          if (with_beta) v = cfma(be, *cp, v);
+          *cp = v;
+        } else {
+          jb.W[((int64_t)z * jb.n + col) * jb.m + row] = v;
+        }
+      }
     }
   }
   if (!ok) {  // a wait gave up: let the MMAs in flight drain (bounded) before freeing tensor memory
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     for (int b = 0; b < OZ_RING; ++b) {
       oz_wait(smem_u32(&s_bar[b]), 0u);
       oz_wait(smem_u32(&s_bar[b]), 1u);
@@ -357,10 +418,15 @@ __global__ void k_oz_reduce(const cplx* W, int m, int n, int splits, cplx beta, 
 
 }  // namespace
 
-bool ozaki_eligible(const GemmJob& j) { return j.k >= 4096 && j.m >= 64 && j.n >= 16; }
+// Products worth the tensor cores: enough k for the digit planes to pay (bands of 128 k)
+// and enough rows for the 128-row tiles.
+bool ozaki_eligible(const GemmJob& j) { return j.k >= 96 && j.m >= 48 && j.n >= 8; }
 
-// One GEMM job on the tensor cores (see the head of this file).
-void ozaki_gemm(const GemmJob& j, cudaStream_t s) {
+// A batch of products on the tensor cores (see the head of this file): exponents and digit
+// planes of every operand (two launches), one persistent MMA launch over all tiles, and a
+// fixed-order reduction for the products split along k.
+void ozaki_gemm_batched(const std::vector<GemmJob>& js, cudaStream_t s) {
+  if (js.empty()) return;
   static const int sms = [] {
     int dev = 0, sm = 0;
     HBS_CUDA(cudaGetDevice(&dev));
@@ -372,38 +438,103 @@ void ozaki_gemm(const GemmJob& j, cudaStream_t s) {
     return true;
   }();
   (void)attr;
-  const int m = j.m, n = j.n, K = j.k;
-  const int tm = (m + OZ_BM - 1) / OZ_BM, tn = (n + OZ_BN - 1) / OZ_BN;
-  const int mpad = tm * OZ_BM, npad = tn * OZ_BN;
-  const int Kpad = (K + OZ_FLUSH - 1) / OZ_FLUSH * OZ_FLUSH;
-  // one wave: at most one CTA per SM (each holds all of tensor memory)
-  int splits = std::max(1, std::min(Kpad / OZ_FLUSH, sms / (tm * tn)));
-  int klen = (Kpad / OZ_FLUSH + splits - 1) / splits * OZ_FLUSH;
-  splits = (Kpad + klen - 1) / klen;
-  DevBuf<int> Er(mpad), Ec(npad), st(1);
-  DevBuf<unsigned short> Ad((size_t)OZ_NSUB * mpad * Kpad), Bd((size_t)OZ_NSUB * npad * Kpad);
-  DevBuf<cplx> W((size_t)splits * m * n);
+  const int nj = (int)js.size();
+  std::vector<OzJob> oj(nj);
+  int64_t adig = 0, bdig = 0, eA = 0, eB = 0, wtot = 0, items = 0;
+  double tflops = 0.0;
+  int tiles_all = 0;
+  for (int q = 0; q < nj; ++q) {
+    const GemmJob& j = js[q];
+    OzJob& o = oj[q];
+    o.m = j.m;
+    o.n = j.n;
+    o.tiles_m = (j.m + OZ_BM - 1) / OZ_BM;
+    o.tiles_n = (j.n + OZ_BN - 1) / OZ_BN;
+    o.mpad = o.tiles_m * OZ_BM;
+    o.npad = o.tiles_n * OZ_BN;
+    o.Kpad = (j.k + OZ_FLUSH - 1) / OZ_FLUSH * OZ_FLUSH;
+    tiles_all += o.tiles_m * o.tiles_n;
+  }
+  for (int q = 0; q < nj; ++q) {
+    const GemmJob& j = js[q];
+    OzJob& o = oj[q];
+    // split along k only when the whole batch has too few tiles to fill the SMs
+    o.splits = 1;
+    if (tiles_all < sms && j.k >= 4096)
+      o.splits = std::max(1, std::min(o.Kpad / OZ_FLUSH, sms / std::max(1, tiles_all)));
+    o.klen = (o.Kpad / OZ_FLUSH + o.splits - 1) / o.splits * OZ_FLUSH;
+    o.splits = (o.Kpad + o.klen - 1) / o.klen;
+    o.item_base = items;
+    items += (int64_t)o.tiles_m * o.tiles_n * o.splits;
+    o.alpha = j.alpha;
+    o.beta = j.beta;
+    o.C = j.C;
+    o.ldc = j.ldc;
+    o.Ad = reinterpret_cast<const unsigned short*>(adig);  // offsets for now
+    o.Bd = reinterpret_cast<const unsigned short*>(bdig);
+    o.Er = reinterpret_cast<const int*>(eA);
+    o.Ec = reinterpret_cast<const int*>(eB);
+    o.W = reinterpret_cast<cplx*>(o.splits > 1 ? wtot : 0);
+    adig += (int64_t)OZ_NSUB * o.mpad * o.Kpad;
+    bdig += (int64_t)OZ_NSUB * o.npad * o.Kpad;
+    eA += o.mpad;
+    eB += o.npad;
+    if (o.splits > 1) wtot += (int64_t)o.splits * j.m * j.n;
+    tflops += 224.0 * o.mpad * (double)o.npad * o.Kpad;
+  }
+  DevBuf<unsigned short> Ad(adig), Bd(bdig);
+  DevBuf<int> E(eA + eB), st(1);
+  DevBuf<cplx> W(std::max<int64_t>(wtot, 1));
+  std::vector<OzOperand> ops;
+  ops.reserve(2 * nj);
+  int maxrows = 0;
+  int64_t maxplane = 0;
+  for (int q = 0; q < nj; ++q) {
+    const GemmJob& j = js[q];
+    OzJob& o = oj[q];
+    unsigned short* ad = Ad.get() + reinterpret_cast<int64_t>(o.Ad);
+    unsigned short* bd = Bd.get() + reinterpret_cast<int64_t>(o.Bd);
+    int* er = E.get() + reinterpret_cast<int64_t>(o.Er);
+    int* ec = E.get() + eA + reinterpret_cast<int64_t>(o.Ec);
+    // op(A) row r, k: transA ? A[r lda + k] : A[k lda + r];  B^T row c, k: B[c ldb + k]
+    ops.push_back({j.A, j.lda, j.transA ? 1 : 0, j.m, j.k, o.mpad, o.Kpad, er, ad});
+    ops.push_back({j.B, j.ldb, 1, j.n, j.k, o.npad, o.Kpad, ec, bd});
+    o.Ad = ad;
+    o.Bd = bd;
+    o.Er = er;
+    o.Ec = ec;
+    o.W = o.splits > 1 ? W.get() + reinterpret_cast<int64_t>(o.W) : nullptr;
+    maxrows = std::max(maxrows, std::max(o.mpad, o.npad));
+    maxplane = std::max(maxplane, (int64_t)std::max(o.mpad, o.npad) * o.Kpad);
+  }
   HBS_CUDA(cudaMemsetAsync(st.get(), 0, sizeof(int), s));
+  DevBuf<OzOperand> dops(ops.size());
+  HBS_CUDA(cudaMemcpyAsync(dops.get(), ops.data(), ops.size() * sizeof(OzOperand), cudaMemcpyHostToDevice, s));
   {
     prof::KScope _ks("k_oz_digits", s);
-    // op(A) row r, k: transA ? A[r lda + k] : A[k lda + r];  B^T row c, k: B[c ldb + k]
-    k_oz_exponents<<<(m * 32 + 255) / 256, 256, 0, s>>>(j.A, j.lda, j.transA ? 0 : 1, m, K, Er.get());
-    k_oz_exponents<<<(n * 32 + 255) / 256, 256, 0, s>>>(j.B, j.ldb, 0, n, K, Ec.get());
-    k_oz_digits<<<grid_1d((int64_t)mpad * Kpad), 256, 0, s>>>(j.A, j.lda, j.transA ? 1 : 0, m, K, Er.get(), mpad,
-                                                              Kpad, Ad.get());
-    k_oz_digits<<<grid_1d((int64_t)npad * Kpad), 256, 0, s>>>(j.B, j.ldb, 1, n, K, Ec.get(), npad, Kpad, Bd.get());
+    const unsigned bx_e = (unsigned)std::min<int64_t>(1024, ((int64_t)maxrows * 32 + 255) / 256);
+    const unsigned bx_d = (unsigned)std::min<int64_t>(2048, (maxplane + 255) / 256);
+    for (size_t o0 = 0; o0 < ops.size(); o0 += 65535) {
+      const unsigned ny = (unsigned)std::min<size_t>(65535, ops.size() - o0);
+      k_oz_exponents<<<dim3(bx_e, ny), 256, 0, s>>>(dops.get() + o0);
+      k_oz_digits<<<dim3(bx_d, ny), 256, 0, s>>>(dops.get() + o0);
+    }
   }
   HBS_LAUNCH_CHECK("k_oz_digits");
+  DevBuf<OzJob> dj(nj);
+  HBS_CUDA(cudaMemcpyAsync(dj.get(), oj.data(), nj * sizeof(OzJob), cudaMemcpyHostToDevice, s));
   {
     // executed tensor work: 28 digit pairs x 4 real products x 2 flops per (padded) m n k
-    prof::KScope _ks("k_oz_mma", s, 224.0 * mpad * (double)npad * Kpad, 0.0);
-    k_oz_mma<<<dim3(tm, tn, splits), 128, OZ_SMEM, s>>>(Ad.get(), Bd.get(), mpad, npad, Kpad, klen, Er.get(),
-                                                         Ec.get(), m, n, j.alpha, W.get(), st.get());
+    prof::KScope _ks("k_oz_mma", s, tflops, 0.0);
+    const unsigned grid = (unsigned)std::min<int64_t>(sms, items);
+    k_oz_mma<<<grid, 128, OZ_SMEM, s>>>(dj.get(), nj, items, st.get());
   }
   HBS_LAUNCH_CHECK("k_oz_mma");
-  {
+  for (int q = 0; q < nj; ++q) {
+    const OzJob& o = oj[q];
+    if (o.splits <= 1) continue;
     prof::KScope _ks("k_oz_reduce", s);
-    k_oz_reduce<<<grid_1d((int64_t)m * n), 256, 0, s>>>(W.get(), m, n, splits, j.beta, j.C, j.ldc);
+    k_oz_reduce<<<grid_1d((int64_t)o.m * o.n), 256, 0, s>>>(o.W, o.m, o.n, o.splits, o.beta, o.C, o.ldc);
   }
   HBS_LAUNCH_CHECK("k_oz_reduce");
   int hs = 0;

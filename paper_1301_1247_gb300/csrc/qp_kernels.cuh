@@ -76,9 +76,10 @@ void build_hbs(Handle& h, cudaStream_t s);
 void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s);
 DevGeom Handle_geom(const Handle& h);
 void run_gemms(std::vector<GemmJob>& jobs, cudaStream_t s);
-// Tensor-core (digit-plane) product of one job (ozaki.cu); eligible: large enough to pay.
+// Tensor-core (digit-plane) products of a batch of jobs (ozaki.cu); eligible: large enough
+// to pay.
 bool ozaki_eligible(const GemmJob& j);
-void ozaki_gemm(const GemmJob& j, cudaStream_t s);
+void ozaki_gemm_batched(const std::vector<GemmJob>& jobs, cudaStream_t s);
 std::vector<int> batched_id(std::vector<CpqrJob>& jobs, double tol, cudaStream_t s);
 __global__ void k_geom(const double* dx, const double* dy, double* nx, double* ny, double* w, int64_t n);
 

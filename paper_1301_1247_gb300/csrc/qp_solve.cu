@@ -452,7 +452,9 @@ void build_periodizer(Handle& h, cudaStream_t s) {
       k_transpose<<<grid_1d((int64_t)N * h.rsel), 256, 0, s>>>(h.Rsel.get(), h.rsel, N, RT.get());
     }
     HBS_LAUNCH_CHECK("k_transpose");
-    const int64_t chunk = 256;
+    // all rows in one sweep (the level vectors take about 3 N rsel complex values): one
+    // batch of products per level instead of one per chunk
+    const int64_t chunk = 1024;
     for (int64_t c0 = 0; c0 < h.rsel; c0 += chunk) {
       int64_t nq = std::min<int64_t>(chunk, h.rsel - c0);
       h.apply_inverse_transpose(RT.get() + c0 * N, h.VT.get() + c0 * N, nq, s);

@@ -161,13 +161,15 @@ def test_plain_path_matches_precomputed_path():
         assert relerr(np.concatenate([c1, d1]), np.concatenate([c2, d2])) < 1e-11
 
 
-def test_double_float_products_match_oracle_and_fp64():
-    """HBS_PRECISION_DOUBLE_FLOAT (dense products in double-float arithmetic) stays within the
-    FP64 bar: Bragg amplitudes vs the dense oracle, and vs the all-FP64 plain path."""
+@pytest.mark.parametrize("prec", [1, 2])
+def test_double_float_products_match_oracle_and_fp64(prec):
+    """HBS_PRECISION_DOUBLE_FLOAT (dense products in double-float arithmetic) and
+    HBS_PRECISION_TENSOR (large products on the tensor cores from bf16 digit planes) stay
+    within the FP64 bar: Bragg amplitudes vs the dense oracle, and vs the all-FP64 plain path."""
     hbs = require_lib()
     x, y, dx, dy = inputs.star(0.3, 0.3, 5).sample(400)
     omega = 10.0
-    h = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12, hbs.default_options(precision=1))
+    h = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12, hbs.default_options(precision=prec))
     info = h.info()
     thetas = np.array([-math.pi / 5, -1.0, -2.5])
     res = h.solve(thetas)
@@ -179,7 +181,7 @@ def test_double_float_products_match_oracle_and_fp64():
     obs = inputs.wiggly(0, 0.35, 20, 0.03)
     x, y, dx, dy = obs.sample(3000)
     omega = 30.0
-    hdf = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12, hbs.default_options(precision=1))
+    hdf = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12, hbs.default_options(precision=prec))
     h64 = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12)
     thetas = inputs.bloch_grouped_angles(9, omega, 1.0, 3, 4).ravel()
     a = hdf.solve(thetas)
