@@ -50,6 +50,17 @@ __device__ __forceinline__ void dfc_sub_mul(const dfc& v, const dfc& w, dfc& a) 
   dfc_norm(a);
 }
 
+// a b   (renormalised)
+__device__ __forceinline__ dfc dfc_mul(const dfc& a, const dfc& b) {
+  dfc r{0.f, 0.f, 0.f, 0.f};
+  df_mac(a.rh, a.rl, b.rh, b.rl, r.rh, r.rl);
+  df_mac(-a.ih, -a.il, b.ih, b.il, r.rh, r.rl);
+  df_mac(a.rh, a.rl, b.ih, b.il, r.ih, r.il);
+  df_mac(a.ih, a.il, b.rh, b.rl, r.ih, r.il);
+  dfc_norm(r);
+  return r;
+}
+
 // acc += |a|^2   (lazy low part)
 __device__ __forceinline__ void df_abs2_acc(const dfc& a, float& ah, float& al) {
   df_mac(a.rh, a.rl, a.rh, a.rl, ah, al);
@@ -63,6 +74,18 @@ __device__ __forceinline__ dfc dfc_scale(float sh, float sl, const dfc& a) {
   df_mac(sh, sl, a.ih, a.il, r.ih, r.il);
   dfc_norm(r);
   return r;
+}
+
+// 1 / d = conj(d) / |d|^2 (0 for d = 0)
+__device__ __forceinline__ dfc dfc_recip(const dfc& d) {
+  float nh = 0.f, nl = 0.f;
+  df_abs2_acc(d, nh, nl);
+  df_norm(nh, nl);
+  if (!(nh > 0.f)) return {0.f, 0.f, 0.f, 0.f};
+  float qh, ql;
+  df_div(1.f, 0.f, nh, nl, qh, ql);
+  const dfc c{d.rh, d.rl, -d.ih, -d.il};
+  return dfc_scale(qh, ql, c);
 }
 
 __device__ __forceinline__ dfc dfc_shfl_xor(const dfc& a, int o) {

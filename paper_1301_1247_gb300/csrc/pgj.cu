@@ -14,6 +14,7 @@
 #include <algorithm>
 
 #include "dense_kernels.cuh"
+#include "dfloat.cuh"
 #include "gridsync.cuh"
 #include "profile.hpp"
 #include "qp_kernels.cuh"
@@ -42,11 +43,16 @@ __device__ __forceinline__ cplx final_pivot_col(const cplx* u, int i, int c, cpl
 }
 
 // smem: 2 x nmax pivot columns (ping-pong over the step parity), rows already swapped.
+// DF: the eliminations run in double-float arithmetic on the FP32 pipes; the matrix is held
+// in place as float pairs between a conversion pass at the start and one at the end, and
+// pivots are chosen on |a|^2 to float precision.
+template <bool DF>
 __global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nmax, GridSync* gs) {
   extern __shared__ cplx su[];
   __shared__ long long redv[32];
   __shared__ int redi[32];
   __shared__ cplx s_ip[2];
+  __shared__ dfc s_ipd[2];
   int jid = 0;
   while (jid + 1 < nj && jobs[jid + 1].b0 <= (int)blockIdx.x) ++jid;
   const PgjJob jb = jobs[jid];
@@ -55,62 +61,126 @@ __global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nma
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gw = lb * kNW + warp, nw = jb.nb * kNW;
   cplx* A = jb.A;
+  dfc* D = reinterpret_cast<dfc*>(jb.A);
   int steps = 0;
   for (int q = 0; q < nj; ++q) steps = max(steps, jobs[q].n);
+  if constexpr (DF) {
+    for (int j = gw; j < n; j += nw)
+      for (int i = lane; i < n; i += 32) D[(int64_t)j * n + i] = to_dfc_bits(A[(int64_t)j * n + i]);
+    if (grid_sync_sum(gs, 0) < 0) return;
+  }
   for (int c = 0; c < steps; ++c) {
     if (c < n) {
       const int par = c & 1;
-      cplx* u = su + (size_t)par * nmax;
-      const cplx* up = su + (size_t)(1 - par) * nmax;
-      const cplx* colc = A + (int64_t)c * n;
       long long best = kNoKey;
       int bi = 0x7fffffff;
-      for (int i = tid; i < n; i += kNT) {
-        const cplx v = colc[i];
-        u[i] = v;
-        if (i >= c) {
-          const long long a = nkey(cabs2(v));
-          if (better(a, i, best, bi)) { best = a; bi = i; }
+      if constexpr (DF) {
+        dfc* u = reinterpret_cast<dfc*>(su) + (size_t)par * nmax;
+        const dfc* colc = D + (int64_t)c * n;
+        for (int i = tid; i < n; i += kNT) {
+          const dfc v = colc[i];
+          u[i] = v;
+          if (i >= c) {
+            const long long a = (long long)__float_as_uint(fmaf(v.rh, v.rh, v.ih * v.ih));
+            if (better(a, i, best, bi)) { best = a; bi = i; }
+          }
+        }
+      } else {
+        cplx* u = su + (size_t)par * nmax;
+        const cplx* colc = A + (int64_t)c * n;
+        for (int i = tid; i < n; i += kNT) {
+          const cplx v = colc[i];
+          u[i] = v;
+          if (i >= c) {
+            const long long a = nkey(cabs2(v));
+            if (better(a, i, best, bi)) { best = a; bi = i; }
+          }
         }
       }
       long long kmax;
       int p;
       block_argmax_key<kNT>(best, bi, redv, redi, &kmax, &p);  // also publishes u to the CTA
-      const double pmax = __longlong_as_double(kmax);
-      if (!(pmax > 0.0)) p = c;
+      const bool nonzero = DF ? (__uint_as_float((unsigned int)kmax) > 0.f) : (__longlong_as_double(kmax) > 0.0);
+      if (!nonzero) p = c;
       if (tid == 0) {
-        if (p != c) {
-          const cplx t = u[c];
-          u[c] = u[p];
-          u[p] = t;
+        if constexpr (DF) {
+          dfc* u = reinterpret_cast<dfc*>(su) + (size_t)par * nmax;
+          if (p != c) {
+            const dfc t = u[c];
+            u[c] = u[p];
+            u[p] = t;
+          }
+          s_ipd[par] = dfc_recip(u[c]);
+        } else {
+          cplx* u = su + (size_t)par * nmax;
+          if (p != c) {
+            const cplx t = u[c];
+            u[c] = u[p];
+            u[p] = t;
+          }
+          const cplx d = u[c];
+          s_ip[par] = cabs2(d) > 0.0 ? cdiv(cmk(1.0, 0.0), d) : cmk(0.0, 0.0);
         }
-        const cplx d = u[c];
-        s_ip[par] = cabs2(d) > 0.0 ? cdiv(cmk(1.0, 0.0), d) : cmk(0.0, 0.0);
         if (lb == 0) {
           jb.piv[c] = p;
-          if (!(pmax > 0.0)) *jb.singular = 1;
+          if (!nonzero) *jb.singular = 1;
         }
       }
       __syncthreads();
-      const cplx ip = s_ip[par];
-      for (int j = gw; j < n; j += nw) {
-        cplx* aj = A + (int64_t)j * n;
-        if (j == c) continue;  // finalized at the next step (or after the last one)
-        if (j == c - 1) {
-          // deferred: the final values of column c-1 from step c-1
-          const cplx ipp = s_ip[1 - par];
-          for (int i = lane; i < n; i += 32) aj[i] = final_pivot_col(up, i, c - 1, ipp);
+      if constexpr (DF) {
+        const dfc* u = reinterpret_cast<const dfc*>(su) + (size_t)par * nmax;
+        const dfc* up = reinterpret_cast<const dfc*>(su) + (size_t)(1 - par) * nmax;
+        const dfc ip = s_ipd[par];
+        for (int j = gw; j < n; j += nw) {
+          dfc* aj = D + (int64_t)j * n;
+          if (j == c) continue;  // finalized at the next step (or after the last one)
+          if (j == c - 1) {
+            // deferred: the final values of column c-1 from step c-1 (1/d at row c-1, -u_i/d elsewhere)
+            const dfc ipp = s_ipd[1 - par];
+            for (int i = lane; i < n; i += 32) {
+              if (i == c - 1) {
+                aj[i] = ipp;
+              } else {
+                const dfc t = dfc_mul(up[i], ipp);
+                aj[i] = {-t.rh, -t.rl, -t.ih, -t.il};
+              }
+            }
+            __syncwarp();
+          }
+          const dfc ac = aj[p], ap = aj[c];  // rows c and p after the interchange
+          const dfc r = dfc_mul(ac, ip);
           __syncwarp();
+          for (int i = lane; i < n; i += 32) {
+            if (i == c) continue;
+            dfc x = (i == p) ? ap : aj[i];
+            dfc_sub_mul(u[i], r, x);
+            aj[i] = x;
+          }
+          if (lane == 0) aj[c] = r;
         }
-        const cplx ac = aj[p], ap = aj[c];  // rows c and p after the interchange
-        const cplx r = cmul(ac, ip);
-        __syncwarp();
-        for (int i = lane; i < n; i += 32) {
-          if (i == c) continue;
-          const cplx x = (i == p) ? ap : aj[i];
-          aj[i] = cfms(u[i], r, x);
+      } else {
+        const cplx* u = su + (size_t)par * nmax;
+        const cplx* up = su + (size_t)(1 - par) * nmax;
+        const cplx ip = s_ip[par];
+        for (int j = gw; j < n; j += nw) {
+          cplx* aj = A + (int64_t)j * n;
+          if (j == c) continue;  // finalized at the next step (or after the last one)
+          if (j == c - 1) {
+            // deferred: the final values of column c-1 from step c-1
+            const cplx ipp = s_ip[1 - par];
+            for (int i = lane; i < n; i += 32) aj[i] = final_pivot_col(up, i, c - 1, ipp);
+            __syncwarp();
+          }
+          const cplx ac = aj[p], ap = aj[c];  // rows c and p after the interchange
+          const cplx r = cmul(ac, ip);
+          __syncwarp();
+          for (int i = lane; i < n; i += 32) {
+            if (i == c) continue;
+            const cplx x = (i == p) ? ap : aj[i];
+            aj[i] = cfms(u[i], r, x);
+          }
+          if (lane == 0) aj[c] = r;
         }
-        if (lane == 0) aj[c] = r;
       }
     }
     if (grid_sync_sum(gs, 0) < 0) return;
@@ -120,11 +190,31 @@ __global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nma
     const int c = n - 1;
     const int own = c % nw;
     if (own == gw) {
-      const cplx* u = su + (size_t)(c & 1) * nmax;
-      const cplx ip = s_ip[c & 1];
-      cplx* ac = A + (int64_t)c * n;
-      for (int i = lane; i < n; i += 32) ac[i] = final_pivot_col(u, i, c, ip);
+      if constexpr (DF) {
+        const dfc* u = reinterpret_cast<const dfc*>(su) + (size_t)(c & 1) * nmax;
+        const dfc ip = s_ipd[c & 1];
+        dfc* ac = D + (int64_t)c * n;
+        for (int i = lane; i < n; i += 32) {
+          if (i == c) {
+            ac[i] = ip;
+          } else {
+            const dfc t = dfc_mul(u[i], ip);
+            ac[i] = {-t.rh, -t.rl, -t.ih, -t.il};
+          }
+        }
+      } else {
+        const cplx* u = su + (size_t)(c & 1) * nmax;
+        const cplx ip = s_ip[c & 1];
+        cplx* ac = A + (int64_t)c * n;
+        for (int i = lane; i < n; i += 32) ac[i] = final_pivot_col(u, i, c, ip);
+      }
     }
+  }
+  if constexpr (DF) {
+    __syncwarp();
+    // every column's final values were written by its owning warp: convert them back
+    for (int j = gw; j < n; j += nw)
+      for (int i = lane; i < n; i += 32) A[(int64_t)j * n + i] = from_dfc_bits(D[(int64_t)j * n + i]);
   }
 }
 
@@ -160,6 +250,7 @@ __global__ void k_pgj_copy(const PgjJob* jobs) {
 
 }  // namespace
 
+template <bool DF>
 static int pgj_grid(size_t smem) {
   static const int sms = [] {
     int dev = 0, sm = 0;
@@ -168,9 +259,9 @@ static int pgj_grid(size_t smem) {
     return sm;
   }();
   if (smem > 48 * 1024)
-    HBS_CUDA(cudaFuncSetAttribute(k_pgj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HBS_CUDA(cudaFuncSetAttribute(k_pgj<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pgj, kNT, smem));
+  HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pgj<DF>, kNT, smem));
   if (per_sm < 1) throw Error(HBS_ERR_CUDA, "persistent Gauss-Jordan kernel does not fit on an SM");
   return sms * std::min(per_sm, 2);
 }
@@ -191,7 +282,9 @@ void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, con
     atot += (int64_t)m.second * m.second;
   }
   const size_t smem = 2 * (size_t)nmax * sizeof(cplx);
-  const int G = pgj_grid(smem);
+  // double-float eliminations on handles built with double-float precision
+  const bool df = gemm_double_float();
+  const int G = df ? pgj_grid<true>(smem) : pgj_grid<false>(smem);
   if (nj > G) throw Error(HBS_ERR_INTERNAL, "persistent Gauss-Jordan batch larger than the grid");
   std::vector<int> nb(nj, 1);
   const int left = G - nj;
@@ -226,7 +319,8 @@ void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, con
     std::lock_guard<std::mutex> lock(coop_mutex());
     {
       prof::KScope _ks("k_pgj", s, fl, 0.0);
-      HBS_CUDA(cudaLaunchCooperativeKernel((const void*)k_pgj, dim3(G), dim3(kNT), args, smem, s));
+      const void* fn = df ? (const void*)k_pgj<true> : (const void*)k_pgj<false>;
+      HBS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kNT), args, smem, s));
     }
     HBS_LAUNCH_CHECK("k_pgj");
     HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));

@@ -156,12 +156,12 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     }
     HBS_LAUNCH_CHECK("k_fill_nb");
     // Row ID of the neighbour interactions (Def. 3.1).  The skeleton is chosen by a
-    // column-pivoted QR among at most 8192 candidate boundary nodes (every stride-th): their
+    // column-pivoted QR among at most 4096 candidate boundary nodes (every stride-th): their
     // columns of Mt are smooth functions of the node, so candidates far finer than the
     // wavelength lose nothing.  Every node's interpolation coefficients then follow by
     // least squares against the skeleton columns, t_i = R11^{-1} Q1^H Mt(:, i), which for
     // the candidates is exactly T = R11^{-1} R12 of the QR.
-    const int64_t stride = std::max<int64_t>(1, (N + 8191) / 8192);
+    const int64_t stride = std::max<int64_t>(1, (N + 4095) / 4096);
     const int64_t nc = (N + stride - 1) / stride;
     DevBuf<cplx> Mc((size_t)m * nc);
     HBS_CUDA(cudaMemcpy2DAsync(Mc.get(), sizeof(cplx) * m, Mt.get(), sizeof(cplx) * m * stride, sizeof(cplx) * m, nc,
@@ -297,17 +297,17 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   // node, so an ID found on a fine subsample holds on all N nodes; a disjoint second
   // subsample checks that.
   ph.next("build:periodizer_id");
-  // Subsample size: at least 16 points per oscillation of the fastest member along the
-  // boundary (wavenumbers up to the contour's reach cK), never fewer than 1024 (16 x the
-  // ~40 oscillations at w = 60 is below that floor); a family's sampled matrix then
-  // stays resident in L2 through the ID's steps.
+  // Subsample size: at least 12 points per oscillation of the fastest member along the
+  // boundary (wavenumbers up to the contour's reach cK), never fewer than 512 (at w = 60,
+  // ~40 oscillations: 512 nodes against family ranks of at most ~200); a family's sampled
+  // matrix then stays resident in L2 through the ID's steps.
   double perim = 0.0;
   for (int64_t i = 0; i < N; ++i) {
     const int64_t j = (i + 1) % N;
     perim += std::hypot(h.hx[j] - h.hx[i], h.hy[j] - h.hy[i]);
   }
   const double osc = perim * std::max(omega, h.cK) / (2.0 * M_PI);
-  int ns_want = std::max(1024, (int)std::ceil(16.0 * osc / 256.0) * 256);
+  int ns_want = std::max(512, (int)std::ceil(12.0 * osc / 256.0) * 256);
   const int ns = (int)std::min<int64_t>(N, std::min(ns_want, 16384));
   // check sample: half as many nodes, each half-way between two nodes of the subsample
   const int ns2 = std::max(1, ns / 2);
