@@ -365,60 +365,115 @@ __global__ void __launch_bounds__(NT) k_cpqr(const CpqrJob* jobs, int* rank_out,
 // partial (row) pivoting; column interchanges are undone at the end.
 // rank_out[job] receives 0 on success, or 1 if a zero pivot was met.
 // ---------------------------------------------------------------------------
-template <int NT>
+// DF: the block is held in place as complex double-float between a conversion at the start
+// and one at the end, and the eliminations run in double-float arithmetic on the FP32
+// pipes; pivots are chosen on |a|^2 to float precision.
+template <int NT, bool DF>
 __global__ void __launch_bounds__(NT) k_gj_inverse(const InvJob* jobs, int* flag_out) {
   __shared__ long long redv[32];
   __shared__ int redi[32];
   __shared__ cplx sh_piv;
+  __shared__ dfc sh_pivd;
   const InvJob jb = jobs[blockIdx.x];
   const int n = jb.n;
   cplx* A = jb.a;
+  dfc* D = reinterpret_cast<dfc*>(jb.a);
   int* piv = jb.piv;
   const int tid = threadIdx.x;
   int bad = 0;
+  if constexpr (DF) {
+    for (int64_t e = tid; e < (int64_t)n * n; e += NT) D[e] = to_dfc_bits(A[e]);
+    __syncthreads();
+  }
   for (int c = 0; c < n; ++c) {
     long long best = kNoKey;
     int bi = 0x7fffffff;
     for (int i = c + tid; i < n; i += NT) {
-      const long long v = nkey(cabs2(A[(int64_t)c * n + i]));
+      long long v;
+      if constexpr (DF) {
+        const dfc x = D[(int64_t)c * n + i];
+        v = (long long)__float_as_uint(fmaf(x.rh, x.rh, x.ih * x.ih));
+      } else {
+        v = nkey(cabs2(A[(int64_t)c * n + i]));
+      }
       if (better(v, i, best, bi)) { best = v; bi = i; }
     }
     long long kv;
     int p;
     block_argmax_key<NT>(best, bi, redv, redi, &kv, &p);
-    const double pv = __longlong_as_double(kv);
+    const bool nonzero = DF ? (__uint_as_float((unsigned int)kv) > 0.f) : (__longlong_as_double(kv) > 0.0);
     if (tid == 0) piv[c] = p;
-    if (!(pv > 0.0)) { bad = 1; p = c; }
-    if (p != c) {
-      for (int j = tid; j < n; j += NT) {
-        cplx t = A[(int64_t)j * n + c];
-        A[(int64_t)j * n + c] = A[(int64_t)j * n + p];
-        A[(int64_t)j * n + p] = t;
+    if (!nonzero) { bad = 1; p = c; }
+    if constexpr (DF) {
+      if (p != c) {
+        for (int j = tid; j < n; j += NT) {
+          const dfc t = D[(int64_t)j * n + c];
+          D[(int64_t)j * n + c] = D[(int64_t)j * n + p];
+          D[(int64_t)j * n + p] = t;
+        }
       }
+      __syncthreads();
+      if (tid == 0) sh_pivd = dfc_recip(D[(int64_t)c * n + c]);
+      __syncthreads();
+      const dfc ip = sh_pivd;
+      // scale pivot row: A[c, :] *= 1/d, with A[c,c] := 1/d
+      for (int j = tid; j < n; j += NT) {
+        if (j == c) D[(int64_t)c * n + c] = ip;
+        else D[(int64_t)j * n + c] = dfc_mul(D[(int64_t)j * n + c], ip);
+      }
+      __syncthreads();
+      // eliminate: for rows i != c: A[i, j] -= A[i, c] * A[c, j]  (j != c)
+      for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        if (i == c || j == c) continue;
+        dfc x = D[(int64_t)j * n + i];
+        dfc_sub_mul(D[(int64_t)c * n + i], D[(int64_t)j * n + c], x);
+        D[(int64_t)j * n + i] = x;
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += NT) {
+        if (i != c) {
+          const dfc t = dfc_mul(D[(int64_t)c * n + i], ip);
+          D[(int64_t)c * n + i] = {-t.rh, -t.rl, -t.ih, -t.il};
+        }
+      }
+      __syncthreads();
+    } else {
+      if (p != c) {
+        for (int j = tid; j < n; j += NT) {
+          cplx t = A[(int64_t)j * n + c];
+          A[(int64_t)j * n + c] = A[(int64_t)j * n + p];
+          A[(int64_t)j * n + p] = t;
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        cplx d = A[(int64_t)c * n + c];
+        sh_piv = (cabs2(d) > 0.0) ? cdiv(cmk(1.0, 0.0), d) : cmk(0.0, 0.0);
+      }
+      __syncthreads();
+      const cplx ip = sh_piv;
+      // scale pivot row: A[c, :] *= 1/d, with A[c,c] := 1/d
+      for (int j = tid; j < n; j += NT) {
+        if (j == c) A[(int64_t)c * n + c] = ip;
+        else A[(int64_t)j * n + c] = cmul(A[(int64_t)j * n + c], ip);
+      }
+      __syncthreads();
+      // eliminate: for rows i != c: A[i, j] -= A[i, c] * A[c, j]  (j != c); A[i, c] = -A[i, c] / d
+      for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
+        int i = (int)(e % n), j = (int)(e / n);
+        if (i == c || j == c) continue;
+        A[(int64_t)j * n + i] = cfms(A[(int64_t)c * n + i], A[(int64_t)j * n + c], A[(int64_t)j * n + i]);
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += NT) {
+        if (i != c) A[(int64_t)c * n + i] = cmul(cmk(-A[(int64_t)c * n + i].x, -A[(int64_t)c * n + i].y), ip);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (tid == 0) {
-      cplx d = A[(int64_t)c * n + c];
-      sh_piv = (cabs2(d) > 0.0) ? cdiv(cmk(1.0, 0.0), d) : cmk(0.0, 0.0);
-    }
-    __syncthreads();
-    const cplx ip = sh_piv;
-    // scale pivot row: A[c, :] *= 1/d, with A[c,c] := 1/d
-    for (int j = tid; j < n; j += NT) {
-      if (j == c) A[(int64_t)c * n + c] = ip;
-      else A[(int64_t)j * n + c] = cmul(A[(int64_t)j * n + c], ip);
-    }
-    __syncthreads();
-    // eliminate: for rows i != c: A[i, j] -= A[i, c] * A[c, j]  (j != c); A[i, c] = -A[i, c] / d
-    for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
-      int i = (int)(e % n), j = (int)(e / n);
-      if (i == c || j == c) continue;
-      A[(int64_t)j * n + i] = cfms(A[(int64_t)c * n + i], A[(int64_t)j * n + c], A[(int64_t)j * n + i]);
-    }
-    __syncthreads();
-    for (int i = tid; i < n; i += NT) {
-      if (i != c) A[(int64_t)c * n + i] = cmul(cmk(-A[(int64_t)c * n + i].x, -A[(int64_t)c * n + i].y), ip);
-    }
+  }
+  if constexpr (DF) {
+    for (int64_t e = tid; e < (int64_t)n * n; e += NT) A[e] = from_dfc_bits(D[e]);
     __syncthreads();
   }
   // undo the row interchanges as column interchanges, in reverse order

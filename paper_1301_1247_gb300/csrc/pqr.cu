@@ -685,8 +685,65 @@ __global__ void k_r11_cols(const cplx* A, int64_t m, const int* piv, const cplx*
   }
 }
 
+// Double-float copy of R11 with its rows scaled by 1/R_ii (column-major, entries r < i), and
+// 1/R_ii itself: back substitution then needs no multiply per step,
+//   x_i = w'_i,  w'_r -= (R_ri / R_rr) x_i,  with w'_r = b_r / R_rr.
+__global__ void k_r11_scaled_df(const cplx* Rc, const cplx* invd, int k, dfc* Rs, dfc* invd_d) {
+  const int64_t tot = (int64_t)k * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % k), i = (int)(e / k);
+    Rs[e] = r < i ? to_dfc_bits(cmul(invd[r], Rc[e])) : dfc{0.f, 0.f, 0.f, 0.f};
+    if (i == 0) invd_d[r] = to_dfc_bits(invd[r]);
+  }
+}
+
+// x = R11^{-1} b for one column per warp, register-resident, in double-float arithmetic.
+template <int KR>
+__global__ void __launch_bounds__(256) k_tsolve_cols_reg_df(const dfc* Rs, const dfc* invd_d, int k, const cplx* B,
+                                                            int64_t ldb, int64_t ncols, cplx* X, int64_t ldx) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp; c < ncols; c += nwarps) {
+    const cplx* b = B + c * ldb;
+    dfc w[KR];
+#pragma unroll
+    for (int q = 0; q < KR; ++q) {
+      const int r = lane + 32 * q;
+      w[q] = r < k ? dfc_mul(to_dfc_bits(b[r]), invd_d[r]) : dfc{0.f, 0.f, 0.f, 0.f};
+    }
+#pragma unroll
+    for (int qb = KR - 1; qb >= 0; --qb) {
+      for (int ii = 31; ii >= 0; --ii) {
+        const int i = qb * 32 + ii;
+        if (i >= k) continue;
+        const dfc xi = dfc_shfl(w[qb], ii);
+        const dfc* ri = Rs + (int64_t)i * k;
+#pragma unroll
+        for (int q = 0; q <= qb; ++q) {
+          const int r = lane + 32 * q;
+          if (r < i) dfc_sub_mul(ri[r], xi, w[q]);
+        }
+      }
+    }
+    cplx* x = X + c * ldx;
+#pragma unroll
+    for (int q = 0; q < KR; ++q) {
+      const int r = lane + 32 * q;
+      if (r < k) x[r] = from_dfc_bits(w[q]);
+    }
+  }
+}
+
 template <int KR>
 void launch_tsolve_reg(const cplx* Rc, const cplx* invd, int k, cplx* W, int64_t ldw, int64_t ncols, cudaStream_t s) {
+  if (gemm_double_float()) {
+    DevBuf<dfc> Rs((size_t)k * k), inv(k);
+    k_r11_scaled_df<<<std::max(1, std::min(4096, (k * k + 255) / 256)), 256, 0, s>>>(Rc, invd, k, Rs.get(), inv.get());
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((ncols + 7) / 8, 152 * 16));
+    k_tsolve_cols_reg_df<KR><<<grid, 256, 0, s>>>(Rs.get(), inv.get(), k, W, ldw, ncols, W, ldw);
+    return;
+  }
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((ncols + 7) / 8, 152 * 16));
   k_tsolve_cols_reg<KR><<<grid, 256, 0, s>>>(Rc, invd, k, W, ldw, ncols, W, ldw);
 }
