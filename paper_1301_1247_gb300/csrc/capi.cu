@@ -188,11 +188,7 @@ hbs_status hbs_build(const hbs_geometry* geom, double omega, double tol, const h
     auto t0 = std::chrono::steady_clock::now();
     prepare_handle(h, geom, omega, tol, opts, s);
     GemmModeScope gm(h.opts.precision);
-    {
-      prof::Phase ph("build:hbs_compress_invert", s);
-      build_hbs(h, s);
-    }
-    build_periodizer(h, s);
+    build_periodizer(h, s, /*with_hbs=*/true);  // runs the HBS compression alongside
     HBS_CUDA(cudaStreamSynchronize(s));
     h.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   });

@@ -129,7 +129,11 @@ __global__ void k_transpose(const cplx* in, int64_t rows, int64_t cols, cplx* ou
 __global__ void k_diff_norm2(const cplx* a, int64_t lda, const cplx* b, int64_t ldb, int nrow, int ncol, double* acc);
 
 // qp_solve.cu
-void build_periodizer(Handle& h, cudaStream_t s);
+// The periodizer and the angle-independent precompute.  With with_hbs, the HBS compression
+// and inversion (build_hbs) runs meanwhile on a second stream from a worker thread: the
+// neighbour and periodizer IDs and the selected rows depend on the geometry only, and the
+// two share the device until the transposed sweep, which needs both.
+void build_periodizer(Handle& h, cudaStream_t s, bool with_hbs = false);
 void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, Result& out, cudaStream_t s);
 
 inline int grid_1d(int64_t tot, int nt = 256, int cap = 8192) {

@@ -17,7 +17,9 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <exception>
 #include <map>
+#include <thread>
 
 #include "dense_kernels.cuh"
 #include "profile.hpp"
@@ -86,7 +88,57 @@ static double contour_distance(const Handle& h, int c, std::complex<double> p) {
   return best;
 }
 
-void build_periodizer(Handle& h, cudaStream_t s) {
+namespace {
+// Runs build_hbs on its own stream from a worker thread (same device and arithmetic modes
+// as the caller); join() waits for it and rethrows its error.  The destructor joins too,
+// so an error on the calling thread never leaves the worker running.
+struct HbsWorker {
+  std::thread t;
+  cudaStream_t s2 = nullptr;
+  std::exception_ptr err;
+  void start(Handle& h) {
+    int dev = 0;
+    HBS_CUDA(cudaGetDevice(&dev));
+    HBS_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    const bool df = gemm_double_float(), tc = gemm_tensor();
+    t = std::thread([this, &h, dev, df, tc] {
+      try {
+        HBS_CUDA(cudaSetDevice(dev));
+        gemm_double_float() = df;
+        gemm_tensor() = tc;
+        StreamScope scope(s2);
+        {
+          prof::Phase ph("build:hbs_compress_invert", s2);
+          build_hbs(h, s2);
+        }
+        HBS_CUDA(cudaStreamSynchronize(s2));
+      } catch (...) {
+        err = std::current_exception();
+      }
+    });
+  }
+  void join() {
+    if (t.joinable()) t.join();
+    if (s2) {
+      cudaStreamDestroy(s2);
+      s2 = nullptr;
+    }
+    if (err) {
+      std::exception_ptr e = err;
+      err = nullptr;
+      std::rethrow_exception(e);
+    }
+  }
+  ~HbsWorker() {
+    if (t.joinable()) t.join();
+    if (s2) cudaStreamDestroy(s2);
+  }
+};
+}  // namespace
+
+void build_periodizer(Handle& h, cudaStream_t s, bool with_hbs) {
+  HbsWorker hbs_worker;
+  if (with_hbs) hbs_worker.start(h);
   const int64_t N = h.N;
   const DevGeom g = Handle_geom(h);
   const double d = h.d, omega = h.omega;
@@ -320,8 +372,9 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   const double ptol = std::min(0.1 * h.tol, 1e-13);
   const int nce = 12 * S;
   // IDs: returns rank, fills perm (host), T (device), and the check residual on the second subsample.
-  // The three families' IDs run in one persistent QR launch; each is then checked on the
-  // second subsample (members rebuilt from the skeleton members).
+  // The three families' IDs run in one persistent QR launch (one after another they took
+  // longer: their pivot steps then add up); each is then checked on the second subsample
+  // (members rebuilt from the skeleton members).
   struct Family {
     int family, ncols;
     DevBuf<cplx> A, A2, T;
@@ -350,13 +403,15 @@ void build_periodizer(Handle& h, cudaStream_t s) {
   }
   PqrOut fqr;
   pqr_run(fspecs, ptol, s, fqr);
+  int fqr_rank[3];
+  for (int fi = 0; fi < 3; ++fi) fqr_rank[fi] = fqr.rank[fi];
   h.pid_residual = 0.0;
   std::vector<int> fperm[3];
   DevBuf<cplx>* Touts[3] = {&h.TY, &h.TC, &h.TE};
   int franks[3];
   for (int fi = 0; fi < 3; ++fi) {
     Family& f = fams[fi];
-    const int ncols = f.ncols, r = fqr.rank[fi];
+    const int ncols = f.ncols, r = fqr_rank[fi];
     franks[fi] = r;
     std::vector<int>& hperm = fperm[fi];
     hperm = f.perm.download(s);
@@ -443,6 +498,10 @@ void build_periodizer(Handle& h, cudaStream_t s) {
     HBS_CUDA(cudaStreamSynchronize(s));
   }
   // ---- V^T = A^{-T} Rsel^T (one transposed apply of the compressed inverse)
+  if (with_hbs) {
+    ph.next("build:wait_hbs");
+    hbs_worker.join();  // the compressed inverse is complete
+  }
   ph.next("build:V_apply");
   h.VT.alloc((size_t)N * h.rsel);
   {
