@@ -20,8 +20,10 @@
 #include <exception>
 #include <map>
 #include <thread>
+#include <type_traits>
 
 #include "dense_kernels.cuh"
+#include "dfloat.cuh"
 #include "profile.hpp"
 #include "gridsync.cuh"
 #include "qp_kernels.cuh"
@@ -979,32 +981,106 @@ __global__ void __launch_bounds__(NT) k_schur_solve(Dims D, const GroupJob* grou
 // right-hand sides.  Three bounded grid barriers per panel (all groups advance together;
 // `npan` is the largest panel count).  Used when the groups are fewer than the SMs, so
 // that every SM takes part.
-template <int NT>
+// Element arithmetic of the Schur LU for complex FP64 (cplx) and complex double-float (dfc).
+__device__ __forceinline__ long long lu_key(const cplx& v) { return nkey(cabs2(v)); }
+__device__ __forceinline__ long long lu_key(const dfc& v) {
+  return (long long)__float_as_uint(fmaf(v.rh, v.rh, v.ih * v.ih));  // |v|^2 to float precision
+}
+__device__ __forceinline__ bool lu_key_nonzero(long long k, const cplx*) { return __longlong_as_double(k) > 0.0; }
+__device__ __forceinline__ bool lu_key_nonzero(long long k, const dfc*) { return __uint_as_float((unsigned)k) > 0.f; }
+__device__ __forceinline__ double lu_key_value(long long k, const cplx*) { return __longlong_as_double(k); }
+__device__ __forceinline__ double lu_key_value(long long k, const dfc*) { return (double)__uint_as_float((unsigned)k); }
+__device__ __forceinline__ cplx lu_recip(const cplx& d) { return cabs2(d) > 0.0 ? cdiv(cmk(1, 0), d) : cmk(0, 0); }
+__device__ __forceinline__ dfc lu_recip(const dfc& d) { return dfc_recip(d); }
+__device__ __forceinline__ cplx lu_mul(const cplx& a, const cplx& b) { return cmul(a, b); }
+__device__ __forceinline__ dfc lu_mul(const dfc& a, const dfc& b) { return dfc_mul(a, b); }
+// c - a b
+__device__ __forceinline__ cplx lu_fms(const cplx& a, const cplx& b, const cplx& c) { return cfms(a, b, c); }
+__device__ __forceinline__ dfc lu_fms(const dfc& a, const dfc& b, const dfc& c) {
+  dfc r = c;
+  dfc_sub_mul(a, b, r);
+  return r;
+}
+// acc += a b (lazy for dfc; lu_norm finishes it)
+__device__ __forceinline__ void lu_acc(const cplx& a, const cplx& b, cplx& acc) { acc = cfma(a, b, acc); }
+__device__ __forceinline__ void lu_acc(const dfc& a, const dfc& b, dfc& acc) {
+  df_mac(a.rh, a.rl, b.rh, b.rl, acc.rh, acc.rl);
+  df_mac(-a.ih, -a.il, b.ih, b.il, acc.rh, acc.rl);
+  df_mac(a.rh, a.rl, b.ih, b.il, acc.ih, acc.il);
+  df_mac(a.ih, a.il, b.rh, b.rl, acc.ih, acc.il);
+}
+__device__ __forceinline__ void lu_norm(cplx&) {}
+__device__ __forceinline__ void lu_norm(dfc& a) { dfc_norm(a); }
+__device__ __forceinline__ cplx lu_sub(const cplx& c, const cplx& a) { return csub(c, a); }
+__device__ __forceinline__ dfc lu_sub(const dfc& c, const dfc& a) {
+  dfc r = c;
+  df_add_to(-a.rh, -a.rl, r.rh, r.rl);
+  df_add_to(-a.ih, -a.il, r.ih, r.il);
+  dfc_norm(r);
+  return r;
+}
+template <typename T> __device__ __forceinline__ T lu_zero();
+template <> __device__ __forceinline__ cplx lu_zero<cplx>() { return cmk(0, 0); }
+template <> __device__ __forceinline__ dfc lu_zero<dfc>() { return {0.f, 0.f, 0.f, 0.f}; }
+// warp sum (result in every lane)
+__device__ __forceinline__ cplx lu_warp_sum(cplx a) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+    a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+  }
+  return a;
+}
+__device__ __forceinline__ dfc lu_warp_sum(dfc a) { return dfc_warp_sum(a); }
+
+// CL CTAs per Bloch group factor [S | R] with the panel-blocked LU of k_schur_solve: the
+// panel by CTA 0 of the group, U12 and the trailing update split over the group's CTAs,
+// three grid barriers per panel (every wait bounded).  The row interchanges are recorded
+// in pivpool (pstride per group) for a later refinement.  DF: the arithmetic is double-float on
+// the FP32 pipes, with [S | R] held in place as float pairs between a conversion pass at
+// the start and one at the end (pivots chosen on |a|^2 to float precision); the caller
+// then refines the solution once against the FP64 system.
+template <int NT, bool DF>
 __global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* groups, int ng, int CL, int npan,
-                                                   cplx* Spool, cplx* Rpool, int* illcond, GridSync* gs) {
+                                                   cplx* Spool, cplx* Rpool, int* illcond, int* pivpool,
+                                                   int pstride, GridSync* gs) {
+  using T = typename std::conditional<DF, dfc, cplx>::type;
   constexpr int NB = 16, TM = 64;
   static_assert(NT == 256, "16 x 16 threads per trailing tile");
   __shared__ long long redv[32];
   __shared__ int redi[32];
-  __shared__ cplx sh_ip;
-  __shared__ cplx Ls[NB][TM + 1];
-  __shared__ cplx Us[NB][TM + 1];
-  __shared__ cplx L11[NB][NB + 1];
+  __shared__ T sh_ip;
+  __shared__ T Ls[NB][TM + 1];
+  __shared__ T Us[NB][TM + 1];
+  __shared__ T L11[NB][NB + 1];
   const int g = blockIdx.x / CL, rank = blockIdx.x % CL;
   const bool act = g < ng;
   int n = 0, q = 0;
-  cplx* A = nullptr;
-  cplx* B = nullptr;
+  cplx* A64 = nullptr;
+  cplx* B64 = nullptr;
+  int* piv = nullptr;
   if (act) {
     const GroupJob G = groups[g];
     n = G.nsys;
     q = G.q;
-    A = Spool + G.s_off;
-    B = Rpool + G.r_off;
+    A64 = Spool + G.s_off;
+    B64 = Rpool + G.r_off;
+    piv = pivpool + (int64_t)g * pstride;
   }
+  T* A = reinterpret_cast<T*>(A64);
+  T* B = reinterpret_cast<T*>(B64);
   const int nc = n + q;
-  auto col = [&](int j) -> cplx* { return j < n ? A + (int64_t)j * n : B + (int64_t)(j - n) * n; };
+  auto col = [&](int j) -> T* { return j < n ? A + (int64_t)j * n : B + (int64_t)(j - n) * n; };
+  auto col64 = [&](int j) -> cplx* { return j < n ? A64 + (int64_t)j * n : B64 + (int64_t)(j - n) * n; };
   const int tid = threadIdx.x;
+  if constexpr (DF) {
+    if (act)
+      for (int j = rank; j < nc; j += CL) {
+        cplx* c64 = col64(j);
+        dfc* cd = reinterpret_cast<dfc*>(c64);
+        for (int i = tid; i < n; i += NT) cd[i] = to_dfc_bits(c64[i]);
+      }
+    if (grid_sync_sum(gs, 0) < 0) return;
+  }
   double pmax = 0.0, pmin = 1e300;
   for (int pn = 0; pn < npan; ++pn) {
     const int k0 = pn * NB;
@@ -1012,42 +1088,40 @@ __global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* group
     const int nb = live ? min(NB, n - k0) : 0;
     if (live && rank == 0) {
       for (int c = k0; c < k0 + nb; ++c) {
-        cplx* ac = A + (int64_t)c * n;
+        T* ac = A + (int64_t)c * n;
         long long best = kNoKey;
         int bi = 0x7fffffff;
         for (int i = c + tid; i < n; i += NT) {
-          const long long v = nkey(cabs2(ac[i]));
+          const long long v = lu_key(ac[i]);
           if (better(v, i, best, bi)) { best = v; bi = i; }
         }
         long long kv;
         int p;
         block_argmax_key<NT>(best, bi, redv, redi, &kv, &p);
         if (tid == 0) {  // pivot range for the conditioning flag (read by thread 0)
-          const double pv = __longlong_as_double(kv);
+          const double pv = lu_key_value(kv, A);
           pmax = fmax(pmax, pv);
           pmin = fmin(pmin, pv);
+          piv[c] = p;
         }
         if (p != c) {
           for (int j = tid; j < nc; j += NT) {
-            cplx* cj = col(j);
-            const cplx t = cj[c];
+            T* cj = col(j);
+            const T t = cj[c];
             cj[c] = cj[p];
             cj[p] = t;
           }
         }
         __syncthreads();
-        if (tid == 0) {
-          const cplx dv = ac[c];
-          sh_ip = cabs2(dv) > 0.0 ? cdiv(cmk(1, 0), dv) : cmk(0, 0);
-        }
+        if (tid == 0) sh_ip = lu_recip(ac[c]);
         __syncthreads();
-        const cplx ip = sh_ip;
-        for (int i = c + 1 + tid; i < n; i += NT) ac[i] = cmul(ac[i], ip);
+        const T ip = sh_ip;
+        for (int i = c + 1 + tid; i < n; i += NT) ac[i] = lu_mul(ac[i], ip);
         __syncthreads();
         for (int j = c + 1; j < k0 + nb; ++j) {
-          cplx* aj = A + (int64_t)j * n;
-          const cplx ucj = aj[c];
-          for (int i = c + 1 + tid; i < n; i += NT) aj[i] = cfms(ac[i], ucj, aj[i]);
+          T* aj = A + (int64_t)j * n;
+          const T ucj = aj[c];
+          for (int i = c + 1 + tid; i < n; i += NT) aj[i] = lu_fms(ac[i], ucj, aj[i]);
         }
         __syncthreads();
       }
@@ -1058,18 +1132,18 @@ __global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* group
     if (upd) {
       for (int e = tid; e < NB * NB; e += NT) {
         const int r = e % NB, cc = e / NB;
-        L11[r][cc] = (r < nb && cc < nb) ? A[(int64_t)(k0 + cc) * n + k0 + r] : cmk(0, 0);
+        L11[r][cc] = (r < nb && cc < nb) ? A[(int64_t)(k0 + cc) * n + k0 + r] : lu_zero<T>();
       }
       __syncthreads();
       for (int j = j0 + rank * NT + tid; j < nc; j += CL * NT) {
-        cplx* aj = col(j) + k0;
-        cplx u[NB];
+        T* aj = col(j) + k0;
+        T u[NB];
 #pragma unroll
-        for (int r = 0; r < NB; ++r) u[r] = r < nb ? aj[r] : cmk(0, 0);
+        for (int r = 0; r < NB; ++r) u[r] = r < nb ? aj[r] : lu_zero<T>();
 #pragma unroll
         for (int cc = 0; cc < NB; ++cc)
 #pragma unroll
-          for (int r = cc + 1; r < NB; ++r) u[r] = cfms(L11[r][cc], u[cc], u[r]);
+          for (int r = cc + 1; r < NB; ++r) u[r] = lu_fms(L11[r][cc], u[cc], u[r]);
 #pragma unroll
         for (int r = 0; r < NB; ++r)
           if (r < nb) aj[r] = u[r];
@@ -1085,21 +1159,21 @@ __global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* group
         for (int e = tid; e < TM * NB; e += NT) {
           const int r = e % TM, kk = e / TM;
           const int i = j0 + rt + r;
-          Ls[kk][r] = (i < n && kk < nb) ? A[(int64_t)(k0 + kk) * n + i] : cmk(0, 0);
+          Ls[kk][r] = (i < n && kk < nb) ? A[(int64_t)(k0 + kk) * n + i] : lu_zero<T>();
         }
         for (int e = tid; e < TM * NB; e += NT) {
           const int kk = e % NB, c = e / NB;
           const int j = j0 + ct + c;
-          Us[kk][c] = (j < nc && kk < nb) ? col(j)[k0 + kk] : cmk(0, 0);
+          Us[kk][c] = (j < nc && kk < nb) ? col(j)[k0 + kk] : lu_zero<T>();
         }
         __syncthreads();
-        cplx acc[4][4];
+        T acc[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = cmk(0, 0);
+          for (int b = 0; b < 4; ++b) acc[a][b] = lu_zero<T>();
         for (int kk = 0; kk < nb; ++kk) {
-          cplx la[4], ub[4];
+          T la[4], ub[4];
 #pragma unroll
           for (int a = 0; a < 4; ++a) la[a] = Ls[kk][tr + 16 * a];
 #pragma unroll
@@ -1107,17 +1181,20 @@ __global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* group
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = cfma(la[a], ub[b], acc[a][b]);
+            for (int b = 0; b < 4; ++b) lu_acc(la[a], ub[b], acc[a][b]);
         }
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const int j = j0 + ct + tc + 16 * b;
           if (j >= nc) continue;
-          cplx* cj = col(j);
+          T* cj = col(j);
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
             const int i = j0 + rt + tr + 16 * a;
-            if (i < n) cj[i] = csub(cj[i], acc[a][b]);
+            if (i < n) {
+              lu_norm(acc[a][b]);
+              cj[i] = lu_sub(cj[i], acc[a][b]);
+            }
           }
         }
         __syncthreads();
@@ -1125,27 +1202,85 @@ __global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* group
     }
     if (grid_sync_sum(gs, 0) < 0) return;
   }
-  if (!act) return;
-  // back substitution, one right-hand side per warp of the group's CTAs
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int j = rank * (NT / 32) + warp; j < q; j += CL * (NT / 32)) {
-    cplx* b = B + (int64_t)j * n;
-    for (int i = n - 1; i >= 0; --i) {
-      cplx acc = cmk(0, 0);
-      for (int t = i + 1 + lane; t < n; t += 32) acc = cfma(A[(int64_t)t * n + i], b[t], acc);
-      for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  if (act) {
+    // back substitution, one right-hand side per warp of the group's CTAs
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int j = rank * (NT / 32) + warp; j < q; j += CL * (NT / 32)) {
+      T* b = B + (int64_t)j * n;
+      for (int i = n - 1; i >= 0; --i) {
+        T acc = lu_zero<T>();
+        for (int t = i + 1 + lane; t < n; t += 32) lu_acc(A[(int64_t)t * n + i], b[t], acc);
+        acc = lu_warp_sum(acc);
+        if (lane == 0) b[i] = lu_mul(lu_sub(b[i], acc), lu_recip(A[(int64_t)i * n + i]));
+        __syncwarp();
       }
-      if (lane == 0) b[i] = cdiv(csub(b[i], acc), A[(int64_t)i * n + i]);
+    }
+    if (rank == 0 && tid == 0) illcond[g] = (pmin <= 1e-28 * pmax) ? 1 : 0;
+  }
+  if constexpr (DF) {
+    if (grid_sync_sum(gs, 0) < 0) return;  // every CTA of the group is done with [S | R]
+    if (act)
+      for (int j = rank; j < nc; j += CL) {
+        cplx* c64 = col64(j);
+        const dfc* cd = reinterpret_cast<const dfc*>(c64);
+        for (int i = tid; i < n; i += NT) c64[i] = from_dfc_bits(cd[i]);  // same 16-byte slot
+      }
+  }
+}
+
+// One step of iterative refinement per group against the FP64 system (after a factorization
+// in double-float): Rres holds R - S X (computed in FP64); solve (LU) d = P Rres with the
+// stored factors and pivots, and X += d.  One CTA per group, one right-hand side per warp,
+// in shared memory; 1/U_ii is formed once per group.
+__global__ void __launch_bounds__(256) k_schur_refine(const GroupJob* groups, const cplx* Spool, cplx* Rpool,
+                                                      const cplx* Rres, const int* pivpool, int pstride) {
+  extern __shared__ cplx sref[];  // n (1/U_ii) + 8 n (one column per warp)
+  const GroupJob G = groups[blockIdx.x];
+  const int n = G.nsys, q = G.q;
+  const cplx* A = Spool + G.s_off;
+  const int* piv = pivpool + (int64_t)blockIdx.x * pstride;
+  cplx* inv = sref;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) inv[i] = cdiv(cmk(1, 0), A[(int64_t)i * n + i]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  cplx* r = sref + n + (int64_t)warp * n;
+  for (int j = warp; j < q; j += 8) {
+    const cplx* rr = Rres + G.r_off + (int64_t)j * n;
+    for (int i = lane; i < n; i += 32) r[i] = rr[i];
+    __syncwarp();
+    if (lane == 0)
+      for (int c = 0; c < n; ++c) {
+        const int p = piv[c];
+        if (p != c) {
+          const cplx t = r[c];
+          r[c] = r[p];
+          r[p] = t;
+        }
+      }
+    __syncwarp();
+    for (int t = 0; t < n; ++t) {  // unit lower L
+      const cplx rt = r[t];
+      __syncwarp();
+      for (int i = t + 1 + lane; i < n; i += 32) r[i] = cfms(A[(int64_t)t * n + i], rt, r[i]);
       __syncwarp();
     }
+    for (int t = n - 1; t >= 0; --t) {  // upper U
+      if (lane == 0) r[t] = cmul(r[t], inv[t]);
+      __syncwarp();
+      const cplx rt = r[t];
+      for (int i = lane; i < t; i += 32) r[i] = cfms(A[(int64_t)t * n + i], rt, r[i]);
+      __syncwarp();
+    }
+    cplx* x = Rpool + G.r_off + (int64_t)j * n;
+    for (int i = lane; i < n; i += 32) x[i] = cadd(x[i], r[i]);
+    __syncwarp();
   }
-  if (rank == 0 && tid == 0) illcond[g] = (pmin <= 1e-28 * pmax) ? 1 : 0;
 }
 
 // Factor and solve every group's Schur system: CL CTAs per group in one cooperative launch
-// when the groups leave SMs idle, else one CTA per group.
+// when the groups leave SMs idle, else one CTA per group.  In the thread's double-float
+// mode the cooperative factorization runs in double-float and the solution is refined once
+// against the FP64 system (residual by an FP64 product, correction with the same factors).
 static void schur_solve(const Dims& D, const std::vector<GroupJob>& gjobs, const GroupJob* dg, cplx* Sp, cplx* Rp,
                         int* ill, cudaStream_t s) {
   const int ng = (int)gjobs.size();
@@ -1154,7 +1289,7 @@ static void schur_solve(const Dims& D, const std::vector<GroupJob>& gjobs, const
     int dev = 0, sm = 0, per = 0;
     HBS_CUDA(cudaGetDevice(&dev));
     HBS_CUDA(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
-    HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_schur_coop<256>, 256, 0));
+    HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_schur_coop<256, false>, 256, 0));
     return std::make_pair(sm, per);
   }();
   const int sms = occ.first, per_sm = occ.second;
@@ -1164,9 +1299,23 @@ static void schur_solve(const Dims& D, const std::vector<GroupJob>& gjobs, const
     return;
   }
   int nmax = 0;
-  for (const auto& G : gjobs) nmax = std::max(nmax, G.nsys);
+  int64_t send = 0, rend = 0;
+  for (const auto& G : gjobs) {
+    nmax = std::max(nmax, G.nsys);
+    send = std::max<int64_t>(send, G.s_off + (int64_t)G.nsys * G.nsys);
+    rend = std::max<int64_t>(rend, G.r_off + (int64_t)G.nsys * G.q);
+  }
+  const bool df = gemm_double_float();
   const int npan = (nmax + 15) / 16;
   DevBuf<GridSync> gs(1);
+  DevBuf<int> piv((size_t)ng * std::max(nmax, 1));
+  DevBuf<cplx> S0, R0;
+  if (df) {  // the FP64 system, for the refinement
+    S0.alloc(std::max<int64_t>(send, 1));
+    R0.alloc(std::max<int64_t>(rend, 1));
+    HBS_CUDA(cudaMemcpyAsync(S0.get(), Sp, sizeof(cplx) * send, cudaMemcpyDeviceToDevice, s));
+    HBS_CUDA(cudaMemcpyAsync(R0.get(), Rp, sizeof(cplx) * rend, cudaMemcpyDeviceToDevice, s));
+  }
   HBS_CUDA(cudaMemsetAsync(gs.get(), 0, sizeof(GridSync), s));
   Dims a0 = D;
   const GroupJob* a1 = dg;
@@ -1174,14 +1323,37 @@ static void schur_solve(const Dims& D, const std::vector<GroupJob>& gjobs, const
   cplx* a5 = Sp;
   cplx* a6 = Rp;
   int* a7 = ill;
-  GridSync* a8 = gs.get();
-  void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8};
-  std::lock_guard<std::mutex> lock(coop_mutex());
-  HBS_CUDA(cudaLaunchCooperativeKernel((const void*)k_schur_coop<256>, dim3(ng * CL), dim3(256), args, 0, s));
-  GridSync hg{};
-  HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));
-  HBS_CUDA(cudaStreamSynchronize(s));
-  if (hg.timed_out) throw Error(HBS_ERR_TIMEOUT, "Schur factorization: a grid barrier wait gave up");
+  int* a8 = piv.get();
+  int a9 = nmax;
+  GridSync* a10 = gs.get();
+  void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9, &a10};
+  {
+    std::lock_guard<std::mutex> lock(coop_mutex());
+    const void* fn = df ? (const void*)k_schur_coop<256, true> : (const void*)k_schur_coop<256, false>;
+    HBS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(ng * CL), dim3(256), args, 0, s));
+    GridSync hg{};
+    HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+    HBS_CUDA(cudaStreamSynchronize(s));
+    if (hg.timed_out) throw Error(HBS_ERR_TIMEOUT, "Schur factorization: a grid barrier wait gave up");
+  }
+  if (!df) return;
+  // R0 <- R0 - S0 X (FP64), then X += (LU)^{-1} P R0
+  {
+    GemmModeScope fp64(HBS_PRECISION_FP64);
+    std::vector<GemmJob> gj;
+    for (const auto& G : gjobs)
+      gj.push_back({S0.get() + G.s_off, Rp + G.r_off, R0.get() + G.r_off, G.nsys, G.q, G.nsys, G.nsys, G.nsys,
+                    G.nsys, cmk(-1, 0), cmk(1, 0), 0, 0, 0});
+    run_gemms(gj, s);
+  }
+  {
+    prof::KScope _ks("k_schur_refine", s);
+    const size_t shm = (size_t)9 * nmax * sizeof(cplx);
+    if (shm > 48 * 1024)
+      HBS_CUDA(cudaFuncSetAttribute(k_schur_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    k_schur_refine<<<ng, 256, shm, s>>>(dg, Sp, Rp, R0.get(), piv.get(), nmax);
+  }
+  HBS_LAUNCH_CHECK("k_schur_refine");
 }
 
 struct AngleJob {
