@@ -311,8 +311,9 @@ def run_ours(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None,
         "dtype": {0: "f64 (complex128)",
                   1: "f64 (complex128); dense products in double-float (2xFP32)",
-                  2: "f64 (complex128); dense products in double-float (2xFP32), K >= 4096 products on tcgen05 "
-                     "tensor cores from exact bf16 digit planes"}[prec],
+                  2: "f64 (complex128) data; double-float (2xFP32) arithmetic for the dense products, the QR and "
+                     "Gauss-Jordan updates, the Hankel series and the Schur LU (refined once in FP64); products with "
+                     "k >= 96 on tcgen05 tensor cores from exact bf16 digit planes"}[prec],
         "data": "synthetic", "err_vs_fp64_plain_path": err,
         "config": {"workload": w["name"], "N": n, "omega": omega, "d": d, "angles": n_ang,
                    "bloch_groups": int(np.asarray(w["thetas"]).shape[0]) if np.asarray(w["thetas"]).ndim == 2 else None,
