@@ -310,7 +310,8 @@ def run_ours(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {0: "f64 (complex128)",
-                  1: "f64 (complex128); dense products in double-float (2xFP32)",
+                  1: "f64 (complex128) data; double-float (2xFP32) arithmetic for the dense products, the QR and "
+                     "Gauss-Jordan updates, the Hankel series and the Schur LU (refined once in FP64)",
                   2: "f64 (complex128) data; double-float (2xFP32) arithmetic for the dense products, the QR and "
                      "Gauss-Jordan updates, the Hankel series and the Schur LU (refined once in FP64); products with "
                      "k >= 96 on tcgen05 tensor cores from exact bf16 digit planes"}[prec],

@@ -217,3 +217,27 @@ def test_save_load_round_trip(tmp_path):
         _, c1, d1, _ = a.bragg(i)
         _, c3, d3, _ = c.bragg(i)
         assert relerr(np.concatenate([c3, d3]), np.concatenate([c1, d1])) < 1e-11
+
+
+def test_tensor_precision_large_tree_matches_fp64():
+    """At N = 20 000 the tree has levels with more than 128 nodes, so the double-float
+    one-CTA-per-node QR and per-block Gauss-Jordan run as well as the persistent ones; the
+    tensor-precision build still matches the all-FP64 plain path to 1e-10, and its
+    interpolative decompositions keep their residuals."""
+    hbs = require_lib()
+    obs = inputs.wiggly(5, 0.35, 20, 0.03)
+    x, y, dx, dy = obs.sample(20000)
+    omega = 40.0
+    htc = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12, hbs.default_options(precision=2))
+    h64 = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12)
+    thetas = inputs.bloch_grouped_angles(4, omega, 1.0, 4, 3).ravel()
+    a = htc.solve(thetas)
+    b = h64.solve_plain(thetas)
+    for i in range(len(thetas)):
+        _, c1, d1, f1 = a.bragg(i)
+        _, c2, d2, _ = b.bragg(i)
+        assert relerr(np.concatenate([c1, d1]), np.concatenate([c2, d2])) < 1e-10
+        assert f1 < 1e-8
+    info = htc.info()
+    assert info["levels"] >= 8
+    assert info["nb_residual"] < 1e-10 and info["pid_residual"] < 1e-10
