@@ -3,14 +3,16 @@
 // One cooperative launch runs every column step of every matrix in a batch, with one
 // grid barrier per step.
 //
-// Step c of a matrix: every CTA of the matrix copies column c into shared memory, finds
-// the pivot row p (largest modulus among rows >= c, lowest index on ties; the same in
-// every CTA) and 1/pivot.  Each warp owns a fixed set of columns j != c and applies the
-// row interchange (c, p), the scaling of row c and the elimination to them.  Column c
-// itself must stay untouched until every CTA has read it, so its owner writes its final
-// values (1/pivot in row c, -A(i,c)/pivot elsewhere) at the start of step c+1, from the
-// copy kept in shared memory, before applying step c+1 to it.  The row interchanges
-// are undone at the end as one column permutation (k_pgj_unpivot).
+// Step c of a matrix: every CTA of the matrix copies column c into shared memory and takes
+// the pivot row p (largest modulus among rows >= c, lowest index on ties) and 1/pivot from
+// the slot that the owner of column c filled right after updating it in step c - 1 (so no
+// CTA searches or divides on the critical path between two barriers).  Each warp owns a
+// fixed set of columns j != c and applies the row interchange (c, p), the scaling of row c
+// and the elimination to them.  Column c itself must stay untouched until every CTA has
+// read it, so its owner writes its final values (1/pivot in row c, -A(i,c)/pivot
+// elsewhere) at the start of step c+1, from the copy kept in shared memory, before
+// applying step c+1 to it.  The row interchanges are undone at the end as one column
+// permutation (k_pgj_unpivot).
 #include <algorithm>
 
 #include "dense_kernels.cuh"
@@ -33,7 +35,50 @@ struct PgjJob {
   int* piv;  // n
   int* singular;
   cplx* tmp;  // n x n scratch for the final column permutation
+  // pivot of the next step (parity slots), found by the owner of that column right after
+  // updating it: row, nonzero flag, and the reciprocal of the pivot (dfc bits in DF mode)
+  int* la_p;
+  int* la_nz;
+  cplx* la_ip;
 };
+
+// The next pivot of column `col` (rows >= c) by its owning warp, from its current values:
+// lowest row of largest modulus (keys as in the block search), written to slot c & 1.
+template <bool DF>
+__device__ __forceinline__ void pgj_lookahead(const PgjJob& jb, const cplx* colp, int c, int lane) {
+  const int n = jb.n;
+  long long best = kNoKey;
+  int bi = 0x7fffffff;
+  for (int i = c + lane; i < n; i += 32) {
+    long long a;
+    if constexpr (DF) {
+      const dfc v = reinterpret_cast<const dfc*>(colp)[i];
+      a = (long long)__float_as_uint(fmaf(v.rh, v.rh, v.ih * v.ih));
+    } else {
+      a = nkey(cabs2(colp[i]));
+    }
+    if (better(a, i, best, bi)) { best = a; bi = i; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long v2 = __shfl_xor_sync(0xffffffffu, best, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (better(v2, i2, best, bi)) { best = v2; bi = i2; }
+  }
+  if (lane == 0) {
+    const bool nonzero = DF ? (__uint_as_float((unsigned int)best) > 0.f) : (__longlong_as_double(best) > 0.0);
+    const int p = nonzero ? bi : c;
+    const int slot = c & 1;
+    jb.la_p[slot] = p;
+    jb.la_nz[slot] = nonzero ? 1 : 0;
+    if constexpr (DF) {
+      const dfc r = dfc_recip(reinterpret_cast<const dfc*>(colp)[p]);
+      reinterpret_cast<dfc*>(jb.la_ip)[slot] = r;
+    } else {
+      const cplx d = colp[p];
+      jb.la_ip[slot] = cabs2(d) > 0.0 ? cdiv(cmk(1.0, 0.0), d) : cmk(0.0, 0.0);
+    }
+  }
+}
 
 // Column c after step c (rows swapped): 1/d at row c, -u_i/d elsewhere.
 __device__ __forceinline__ cplx final_pivot_col(const cplx* u, int i, int c, cplx ip) {
@@ -49,8 +94,6 @@ __device__ __forceinline__ cplx final_pivot_col(const cplx* u, int i, int c, cpl
 template <bool DF>
 __global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nmax, GridSync* gs) {
   extern __shared__ cplx su[];
-  __shared__ long long redv[32];
-  __shared__ int redi[32];
   __shared__ cplx s_ip[2];
   __shared__ dfc s_ipd[2];
   int jid = 0;
@@ -67,64 +110,49 @@ __global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nma
   if constexpr (DF) {
     for (int j = gw; j < n; j += nw)
       for (int i = lane; i < n; i += 32) D[(int64_t)j * n + i] = to_dfc_bits(A[(int64_t)j * n + i]);
-    if (grid_sync_sum(gs, 0) < 0) return;
   }
+  // the first pivot, by the owner of column 0 (the same warp converted that column)
+  if (n > 0 && gw == 0) {
+    __syncwarp();
+    pgj_lookahead<DF>(jb, A, 0, lane);
+  }
+  if (grid_sync_sum(gs, 0) < 0) return;
   for (int c = 0; c < steps; ++c) {
     if (c < n) {
       const int par = c & 1;
-      long long best = kNoKey;
-      int bi = 0x7fffffff;
+      // pivot row and 1/pivot found at the end of the previous step (lookahead)
+      const int p = jb.la_p[par];
+      const bool nonzero = jb.la_nz[par] != 0;
       if constexpr (DF) {
         dfc* u = reinterpret_cast<dfc*>(su) + (size_t)par * nmax;
         const dfc* colc = D + (int64_t)c * n;
-        for (int i = tid; i < n; i += kNT) {
-          const dfc v = colc[i];
-          u[i] = v;
-          if (i >= c) {
-            const long long a = (long long)__float_as_uint(fmaf(v.rh, v.rh, v.ih * v.ih));
-            if (better(a, i, best, bi)) { best = a; bi = i; }
-          }
-        }
-      } else {
-        cplx* u = su + (size_t)par * nmax;
-        const cplx* colc = A + (int64_t)c * n;
-        for (int i = tid; i < n; i += kNT) {
-          const cplx v = colc[i];
-          u[i] = v;
-          if (i >= c) {
-            const long long a = nkey(cabs2(v));
-            if (better(a, i, best, bi)) { best = a; bi = i; }
-          }
-        }
-      }
-      long long kmax;
-      int p;
-      block_argmax_key<kNT>(best, bi, redv, redi, &kmax, &p);  // also publishes u to the CTA
-      const bool nonzero = DF ? (__uint_as_float((unsigned int)kmax) > 0.f) : (__longlong_as_double(kmax) > 0.0);
-      if (!nonzero) p = c;
-      if (tid == 0) {
-        if constexpr (DF) {
-          dfc* u = reinterpret_cast<dfc*>(su) + (size_t)par * nmax;
+        for (int i = tid; i < n; i += kNT) u[i] = colc[i];
+        __syncthreads();
+        if (tid == 0) {
           if (p != c) {
             const dfc t = u[c];
             u[c] = u[p];
             u[p] = t;
           }
-          s_ipd[par] = dfc_recip(u[c]);
-        } else {
-          cplx* u = su + (size_t)par * nmax;
+          s_ipd[par] = reinterpret_cast<const dfc*>(jb.la_ip)[par];
+        }
+      } else {
+        cplx* u = su + (size_t)par * nmax;
+        const cplx* colc = A + (int64_t)c * n;
+        for (int i = tid; i < n; i += kNT) u[i] = colc[i];
+        __syncthreads();
+        if (tid == 0) {
           if (p != c) {
             const cplx t = u[c];
             u[c] = u[p];
             u[p] = t;
           }
-          const cplx d = u[c];
-          s_ip[par] = cabs2(d) > 0.0 ? cdiv(cmk(1.0, 0.0), d) : cmk(0.0, 0.0);
+          s_ip[par] = jb.la_ip[par];
         }
-        if (lb == 0) {
-          jb.piv[c] = p;
-          if (!nonzero) *jb.singular = 1;
-        }
+      }
+      if (tid == 0 && lb == 0) {
+        jb.piv[c] = p;
+        if (!nonzero) *jb.singular = 1;
       }
       __syncthreads();
       if constexpr (DF) {
@@ -157,6 +185,10 @@ __global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nma
             aj[i] = x;
           }
           if (lane == 0) aj[c] = r;
+          if (j == c + 1) {  // the next pivot column is final for step c + 1
+            __syncwarp();
+            pgj_lookahead<true>(jb, reinterpret_cast<const cplx*>(aj), c + 1, lane);
+          }
         }
       } else {
         const cplx* u = su + (size_t)par * nmax;
@@ -180,6 +212,10 @@ __global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nma
             aj[i] = cfms(u[i], r, x);
           }
           if (lane == 0) aj[c] = r;
+          if (j == c + 1) {  // the next pivot column is final for step c + 1
+            __syncwarp();
+            pgj_lookahead<false>(jb, aj, c + 1, lane);
+          }
         }
       }
     }
@@ -293,7 +329,8 @@ void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, con
   int used = 0;
   for (int v : nb) used += v;
   for (int j = 0; used < G; j = (j + 1) % nj, ++used) ++nb[j];
-  DevBuf<int> piv(ptot), sing(nj);
+  DevBuf<int> piv(ptot), sing(nj), la_p(2 * nj), la_nz(2 * nj);
+  DevBuf<cplx> la_ip(2 * nj);
   DevBuf<cplx> tmp(atot);
   DevBuf<GridSync> gs(1);
   HBS_CUDA(cudaMemsetAsync(sing.get(), 0, sizeof(int) * nj, s));
@@ -302,7 +339,8 @@ void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, con
   int64_t po = 0, ao = 0;
   int b0 = 0;
   for (int j = 0; j < nj; ++j) {
-    jobs[j] = {mats[j].first, mats[j].second, b0, nb[j], piv.get() + po, sing.get() + j, tmp.get() + ao};
+    jobs[j] = {mats[j].first, mats[j].second, b0,  nb[j], piv.get() + po, sing.get() + j, tmp.get() + ao,
+               la_p.get() + 2 * j, la_nz.get() + 2 * j, la_ip.get() + 2 * j};
     po += mats[j].second;
     ao += (int64_t)mats[j].second * mats[j].second;
     b0 += nb[j];
