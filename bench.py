@@ -387,6 +387,34 @@ def run_reference(args, ws, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_gemm(args):
+    """Kernel benchmark of hbs_zgemm (C = A B, device complex128, m x n x k) in the chosen
+    arithmetic; one JSON line with the FP64-equivalent rate (8 m n k flops per product).  The
+    dense products of the precompute (Z = V [P | Y_sel]: 690 x 180 x N at the bench workload)
+    have this shape."""
+    import torch
+    from paper_1301_1247_gb300 import hbs
+    m, n, k = args.gemm
+    prec = {"fp64": 0, "df": 1, "tc": 2}[args.precision]
+    torch.manual_seed(0)
+    a = torch.randn(m * k, dtype=torch.complex128, device="cuda")
+    b = torch.randn(k * n, dtype=torch.complex128, device="cuda")
+    c = torch.zeros(m * n, dtype=torch.complex128, device="cuda")
+    for _ in range(max(args.warmup, 1)):
+        hbs.zgemm(m, n, k, 1.0, a, m, 0, b, k, 0.0, c, m, prec)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        hbs.zgemm(m, n, k, 1.0, a, m, 0, b, k, 0.0, c, m, prec)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    return {"metric": "complex GEMM FP64-equivalent rate (hbs_zgemm)", "value": round(8.0 * m * n * k / (ms / 1e3) / 1e12, 3),
+            "unit": "TFLOP/s", "ms_per_call": round(ms, 3), "steps": args.steps, "warmup": args.warmup,
+            "config": {"m": m, "n": n, "k": k, "precision": args.precision}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -398,7 +426,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 plain-path accuracy check")
     ap.add_argument("--precision", choices=["fp64", "df", "tc"], default="tc")
+    ap.add_argument("--gemm", type=int, nargs=3, metavar=("M", "N", "K"),
+                    help="time hbs_zgemm alone at this shape instead of the solver step")
     args = ap.parse_args()
+    if args.gemm:
+        print(json.dumps(run_gemm(args)))
+        return
     ws, rank, local = dist_init()
     if args.impl == "reference":
         out = run_reference(args, ws, rank)

@@ -260,39 +260,43 @@ __global__ void k_fill_d(const DJob* jobs) {
   }
 }
 
-struct PJob {
-  const cplx* in;   // input matrix
+// Permuted copies for the products with P = Pi [I; T^T] (Pi: the ID's column order):
+//   cols: out(:, c) = in(:, perm[c]) (rows x n), first = out(:, 0..k)   (ld rows)
+//   rows: out(r, :) = in(perm[r], :) (n x cols), first = out(0..k, :)   (ld k)
+// and Tt = T^T ((n - k) x k).  The rest of each product is then a GEMM with T or T^T.
+struct PermJob {
+  const cplx* in;
   cplx* out;
-  const int* perm;  // n entries
-  const cplx* T;    // k x (n - k), ld = k
-  int n, k;
-  int other;        // the other dimension (rows of In for right-P, columns for left-P^T)
-  int ld_in, ld_out;
+  cplx* first;
+  const int* perm;
+  const cplx* T;
+  cplx* Tt;
+  int n, k, other, ld_in;
+  int by_rows;
 };
-
-// out = In * P  (In: other x n, out: other x k):  out[:, i] = In[:, perm[i]] + sum_j T[i, j] In[:, perm[k + j]]
-__global__ void k_right_p(const PJob* jobs) {
-  const PJob jb = jobs[blockIdx.y];
-  const int64_t tot = (int64_t)jb.other * jb.k;
+__global__ void k_perm_copy(const PermJob* jobs) {
+  const PermJob jb = jobs[blockIdx.y];
+  const int64_t tot = (int64_t)jb.n * jb.other;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e % jb.other), i = (int)(e / jb.other);
-    cplx acc = jb.in[(int64_t)jb.perm[i] * jb.ld_in + r];
-    for (int j = 0; j < jb.n - jb.k; ++j)
-      acc = cfma(jb.T[(int64_t)j * jb.k + i], jb.in[(int64_t)jb.perm[jb.k + j] * jb.ld_in + r], acc);
-    jb.out[(int64_t)i * jb.ld_out + r] = acc;
+    if (jb.by_rows) {  // out is n x other
+      const int r = (int)(e % jb.n), c = (int)(e / jb.n);
+      const cplx v = jb.in[(int64_t)c * jb.ld_in + jb.perm[r]];
+      jb.out[e] = v;
+      if (r < jb.k) jb.first[(int64_t)c * jb.k + r] = v;
+    } else {  // out is other x n
+      const int r = (int)(e % jb.other), c = (int)(e / jb.other);
+      const cplx v = jb.in[(int64_t)jb.perm[c] * jb.ld_in + r];
+      jb.out[e] = v;
+      if (c < jb.k) jb.first[e] = v;
+    }
   }
-}
-
-// out = P^T * In  (In: n x other, out: k x other): out[i, :] = In[perm[i], :] + sum_j T[i, j] In[perm[k+j], :]
-__global__ void k_left_pt(const PJob* jobs) {
-  const PJob jb = jobs[blockIdx.y];
-  const int64_t tot = (int64_t)jb.other * jb.k;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % jb.k), c = (int)(e / jb.k);
-    const cplx* col = jb.in + (int64_t)c * jb.ld_in;
-    cplx acc = col[jb.perm[i]];
-    for (int j = 0; j < jb.n - jb.k; ++j) acc = cfma(jb.T[(int64_t)j * jb.k + i], col[jb.perm[jb.k + j]], acc);
-    jb.out[(int64_t)c * jb.ld_out + i] = acc;
+  if (jb.Tt != nullptr) {
+    const int nk = jb.n - jb.k;
+    const int64_t tt = (int64_t)nk * jb.k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tt; e += (int64_t)gridDim.x * blockDim.x) {
+      const int j = (int)(e % nk), i = (int)(e / nk);
+      jb.Tt[e] = jb.T[(int64_t)j * jb.k + i];  // Tt(j, i) = T(i, j)
+    }
   }
 }
 
@@ -425,12 +429,6 @@ static DevBuf<J> upload_jobs(const std::vector<J>& v, cudaStream_t s) {
   return d;
 }
 
-static inline int grid_for(int64_t tot, int nt, int cap = 4096) {
-  int64_t b = (tot + nt - 1) / nt;
-  if (b < 1) b = 1;
-  if (b > cap) b = cap;
-  return (int)b;
-}
 
 DevGeom Handle_geom(const Handle& h) {
   DevGeom g;
@@ -846,46 +844,71 @@ void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s) {
       HBS_LAUNCH_CHECK("k_fill_d");
       batched_inverse(ij, s, "leaf/level block");
     }
-    // X = D^{-1} P (n x k), Yt = P^T D^{-1} (k x n), S = P^T X (k x k)
+    // X = D^{-1} P (n x k), Yt = P^T D^{-1} (k x n), S = P^T X (k x k).  With Dp = D^{-1}(:, perm),
+    // Dr = D^{-1}(perm, :) and Xr = X(perm, :):
+    //   X = Dp(:, :k) + Dp(:, k:) T^T,   Yt = Dr(:k, :) + T Dr(k:, :),   S = Xr(:k, :) + T Xr(k:, :),
+    // permuted copies followed by batched GEMMs (double-float or tensor cores).
     {
-      std::vector<PJob> rp, lp, lp2;
+      std::vector<PermJob> pj1, pj2;
+      std::vector<GemmJob> g1, g2;
+      std::vector<DevBuf<cplx>> Dp(tasks.size()), Dr(tasks.size()), Xr(tasks.size()), Tt(tasks.size());
       for (size_t i = 0; i < tasks.size(); ++i) {
         Level& lv = tasks[i].h->levels[tasks[i].l];
         lv.e_off.assign(lv.count, 0); lv.f_off.assign(lv.count, 0); lv.dh_off.assign(lv.count, 0);
-        int64_t eo = 0, dho = 0;
+        int64_t eo = 0, dho = 0, nno = 0, tto = 0;
+        std::vector<int64_t> nn_off(lv.count), tt_off(lv.count);
         for (int j = 0; j < lv.count; ++j) {
           lv.e_off[j] = eo; lv.f_off[j] = eo; eo += (int64_t)lv.n[j] * lv.k[j];
           lv.dh_off[j] = dho; dho += (int64_t)lv.k[j] * lv.k[j];
+          nn_off[j] = nno; nno += (int64_t)lv.n[j] * lv.n[j];
+          tt_off[j] = tto; tto += (int64_t)(lv.n[j] - lv.k[j]) * lv.k[j];
         }
         X[i].alloc(std::max<int64_t>(eo, 1));
         Yp[i].alloc(std::max<int64_t>(eo, 1));
         S[i].alloc(std::max<int64_t>(dho, 1));
+        Dp[i].alloc(std::max<int64_t>(nno, 1));
+        Dr[i].alloc(std::max<int64_t>(nno, 1));
+        Xr[i].alloc(std::max<int64_t>(eo, 1));
+        Tt[i].alloc(std::max<int64_t>(tto, 1));
         for (int j = 0; j < lv.count; ++j) {
-          const int n = lv.n[j], k = lv.k[j];
+          const int n = lv.n[j], k = lv.k[j], nk = n - k;
+          if (k == 0) continue;
           const int* pm = lv.perm.get() + lv.off[j];
           const cplx* T = lv.T.get() + lv.t_off[j];
-          cplx* d = Dinv[i].get() + d_off[i][j];
-          rp.push_back({d, X[i].get() + lv.e_off[j], pm, T, n, k, n, n, n});
-          lp.push_back({d, Yp[i].get() + lv.f_off[j], pm, T, n, k, n, n, k});
-          lp2.push_back({X[i].get() + lv.e_off[j], S[i].get() + lv.dh_off[j], pm, T, n, k, k, n, k});
+          const cplx* d = Dinv[i].get() + d_off[i][j];
+          cplx* dp = Dp[i].get() + nn_off[j];
+          cplx* dr = Dr[i].get() + nn_off[j];
+          cplx* x = X[i].get() + lv.e_off[j];
+          cplx* yt = Yp[i].get() + lv.f_off[j];
+          cplx* xr = Xr[i].get() + lv.e_off[j];
+          cplx* tt = Tt[i].get() + tt_off[j];
+          pj1.push_back({d, dp, x, pm, T, nk > 0 ? tt : nullptr, n, k, n, n, 0});
+          pj1.push_back({d, dr, yt, pm, nullptr, nullptr, n, k, n, n, 1});
+          pj2.push_back({x, xr, S[i].get() + lv.dh_off[j], pm, nullptr, nullptr, n, k, k, n, 1});
+          if (nk > 0) {
+            // X += Dp(:, k:) Tt   (n x nk) (nk x k)
+            g1.push_back({dp + (int64_t)k * n, tt, x, n, k, nk, n, nk, n, cmk(1, 0), cmk(1, 0), 0, 0, 0});
+            // Yt += T Dr(k:, :)    (k x nk) (nk x n)
+            g1.push_back({T, dr + k, yt, k, n, nk, k, n, k, cmk(1, 0), cmk(1, 0), 0, 0, 0});
+            // S += T Xr(k:, :)     (k x nk) (nk x k)
+            g2.push_back({T, xr + k, S[i].get() + lv.dh_off[j], k, k, nk, k, n, k, cmk(1, 0), cmk(1, 0), 0, 0, 0});
+          }
         }
       }
-      DevBuf<PJob> drp = upload_jobs(rp, s), dlp = upload_jobs(lp, s), dlp2 = upload_jobs(lp2, s);
       {
-        prof::KScope _ks("k_right_p", s);
-        launch_jobs_y(drp, rp.size(), [&](const PJob* p, unsigned ny) { k_right_p<<<dim3(32, ny), 256, 0, s>>>(p); });
+        DevBuf<PermJob> dp1 = upload_jobs(pj1, s);
+        prof::KScope _ks("k_perm_copy", s);
+        launch_jobs_y(dp1, pj1.size(), [&](const PermJob* p, unsigned ny) { k_perm_copy<<<dim3(32, ny), 256, 0, s>>>(p); });
       }
-      HBS_LAUNCH_CHECK("k_right_p");
+      HBS_LAUNCH_CHECK("k_perm_copy");
+      launch_gemms(g1, s);
       {
-        prof::KScope _ks("k_left_pt", s);
-        launch_jobs_y(dlp, lp.size(), [&](const PJob* p, unsigned ny) { k_left_pt<<<dim3(32, ny), 256, 0, s>>>(p); });
+        DevBuf<PermJob> dp2 = upload_jobs(pj2, s);
+        prof::KScope _ks("k_perm_copy", s);
+        launch_jobs_y(dp2, pj2.size(), [&](const PermJob* p, unsigned ny) { k_perm_copy<<<dim3(32, ny), 256, 0, s>>>(p); });
       }
-      HBS_LAUNCH_CHECK("k_left_pt");
-      {
-        prof::KScope _ks("k_left_pt", s);
-        launch_jobs_y(dlp2, lp2.size(), [&](const PJob* p, unsigned ny) { k_left_pt<<<dim3(32, ny), 256, 0, s>>>(p); });
-      }
-      HBS_LAUNCH_CHECK("k_left_pt S");
+      HBS_LAUNCH_CHECK("k_perm_copy X");
+      launch_gemms(g2, s);
       HBS_CUDA(cudaStreamSynchronize(s));
     }
     // Dhat = S^{-1}
