@@ -471,16 +471,28 @@ namespace hbs {
 // rows / columns it keeps.
 // ---------------------------------------------------------------------------
 
-// Column `col` of Y = [B_L^0 | B_R^0 | B_L^1 | B_R^1] at boundary node i (each block [mu | nu]).
+__global__ void k_contour_s(const cplx* k, int M, double omega, cplx* s, cplx* si) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+    const cplx v = sqrt_branch(omega, k[m]);
+    s[m] = v;
+    si[m] = cdiv(cmk(1.0, 0.0), v);
+  }
+}
+
+// Column `col` of Y = [B_L^0 | B_R^0 | B_L^1 | B_R^1] at boundary node i (each block [mu | nu]):
+// e^{i k_m y} e^{i s a} as one exponential, with s and 1/s from the per-node tables.
 __device__ __forceinline__ cplx b_entry(const DevGeom& g, const ContourPtrs& cp, int M, double d, int64_t i, int col) {
   const int c = col / (4 * M), rem = col % (4 * M);
   const int side = rem / (2 * M), kind = (rem % (2 * M)) / M, m = rem % M;
   const cplx km = cp.k[c][m], w = cp.wk[c][m];
-  const cplx s = sqrt_branch(g.omega, km);
+  const cplx s = cp.s[c][m];
   const double xi = g.x[i], yi = g.y[i];
   const double a = side == 0 ? xi + 0.5 * d : 0.5 * d - xi;
-  cplx e = cmul(cexp(cmk(-km.y * yi, km.x * yi)), cexp(cmk(-s.y * a, s.x * a)));
-  if (kind == 0) return cmul(cmul(e, cdiv(cmk(0.0, 0.5), s)), w);
+  const cplx e = cexp(cmk(-km.y * yi - s.y * a, km.x * yi + s.x * a));
+  if (kind == 0) {
+    const cplx si = cp.si[c][m];  // (i / 2) / s
+    return cmul(cmul(e, cmk(-0.5 * si.y, 0.5 * si.x)), w);
+  }
   return cmul(cscale(e, side == 0 ? 0.5 : -0.5), w);
 }
 
@@ -490,16 +502,16 @@ __device__ __forceinline__ cplx c_entry(const DevGeom& g, const ContourPtrs& cp,
   const int side = rem / (2 * M), kind = (rem % (2 * M)) / M, m = rem % M;
   const double shift_x = side == 0 ? d : -d, x0 = side == 0 ? -0.5 * d : 0.5 * d;
   const cplx km = cp.k[c][m];
-  const cplx s = sqrt_branch(g.omega, km);
+  const cplx s = cp.s[c][m], si = cp.si[c][m];
   const double sx = g.x[j] + shift_x, sy = g.y[j], nx = g.nx[j], ny = g.ny[j];
   const double sg = sx - x0 > 0.0 ? 1.0 : -1.0;
   const double ax = fabs(sx - x0);
-  cplx base = cmul(cexp(cmk(km.y * sy, -km.x * sy)), cexp(cmk(-s.y * ax, s.x * ax)));
+  cplx base = cexp(cmk(km.y * sy - s.y * ax, -km.x * sy + s.x * ax));  // e^{-i k_m y} e^{i s |x - x0|}
   base = cscale(base, g.w[j] / (4.0 * HBS_PI));
   const cplx iw = cmk(0.0, g.omega);
   if (kind == 0) {
-    cplx s_hat = cdiv(cmul(cmk(0.0, 1.0), base), s);
-    cplx d_hat = cmul(base, cadd(cmk(-sg * nx, 0.0), cscale(cdiv(km, s), ny)));
+    cplx s_hat = cmul(cmul(cmk(0.0, 1.0), base), si);
+    cplx d_hat = cmul(base, cadd(cmk(-sg * nx, 0.0), cscale(cmul(km, si), ny)));
     return csub(d_hat, cmul(iw, s_hat));
   }
   cplx dstar_hat = cscale(base, sg);

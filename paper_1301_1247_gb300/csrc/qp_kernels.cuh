@@ -105,7 +105,11 @@ __global__ void k_bq_tsolve(const cplx* A, int64_t m, int64_t n, int k, cplx* T)
 struct ContourPtrs {
   const cplx* k[2];   // contour nodes of contour 0 and (if present) 1
   const cplx* wk[2];  // their weights
+  const cplx* s[2];   // sqrt(w - k) sqrt(w + k) at the nodes (principal roots)
+  const cplx* si[2];  // 1 / s
 };
+// s and 1/s at M contour nodes (the wall entries' per-node factors, formed once).
+__global__ void k_contour_s(const cplx* k, int M, double omega, cplx* s, cplx* si);
 __global__ void k_fill_family_sub(DevGeom g, ContourPtrs cp, int M, double d, int S, double y0, int family,
                                   const int64_t* pts, int np, int nfam, cplx* out, int64_t ld);
 __global__ void k_fill_family_sel(DevGeom g, ContourPtrs cp, int M, double d, int S, double y0, int family,

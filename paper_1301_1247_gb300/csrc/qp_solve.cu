@@ -330,11 +330,17 @@ void build_periodizer(Handle& h, cudaStream_t s, bool with_hbs) {
   // ---- contours' wall-sample rows (small: 4S x 2M each)
   const int ny = 4 * M * nc;
   ContourPtrs cp{};
+  DevBuf<cplx> cs_tab[2], csi_tab[2];
   for (int c = 0; c < nc; ++c) {
     ContourData& cd = h.contours[c];
     cd.col_off = (int64_t)4 * M * c;
     cp.k[c] = cd.dk.get();
     cp.wk[c] = cd.dwk.get();
+    cs_tab[c].alloc(M);
+    csi_tab[c].alloc(M);
+    k_contour_s<<<(M + 255) / 256, 256, 0, s>>>(cd.dk.get(), M, omega, cs_tab[c].get(), csi_tab[c].get());
+    cp.s[c] = cs_tab[c].get();
+    cp.si[c] = csi_tab[c].get();
     cd.SL.alloc((size_t)4 * S * 2 * M);
     cd.SR.alloc((size_t)4 * S * 2 * M);
     {
