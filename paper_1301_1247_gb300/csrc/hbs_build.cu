@@ -322,6 +322,7 @@ struct SplitRed {
   const cplx* W;
   int m, n, ldc, splits;
   cplx beta;
+  int transC;
 };
 __global__ void k_splitk_reduce(const SplitRed* reds, int nred) {
   const SplitRed r = reds[blockIdx.y];
@@ -331,7 +332,7 @@ __global__ void k_splitk_reduce(const SplitRed* reds, int nred) {
     const int64_t j = e / r.m;
     cplx acc = cmk(0.0, 0.0);
     for (int sidx = 0; sidx < r.splits; ++sidx) acc = cadd(acc, r.W[sidx * mn + e]);
-    cplx* c = r.C + j * r.ldc + i;
+    cplx* c = r.transC ? r.C + (int64_t)i * r.ldc + j : r.C + j * r.ldc + i;
     if (r.beta.x != 0.0 || r.beta.y != 0.0) acc = cfma(r.beta, *c, acc);
     *c = acc;
   }
@@ -373,7 +374,7 @@ static void launch_gemms(std::vector<GemmJob>& jobs_all, cudaStream_t s) {
     int chunk = (j.k + splits - 1) / splits;
     chunk = (chunk + GBK - 1) / GBK * GBK;
     splits = (j.k + chunk - 1) / chunk;
-    SplitRed r{j.C, nullptr, j.m, j.n, j.ldc, splits, j.beta};
+    SplitRed r{j.C, nullptr, j.m, j.n, j.ldc, splits, j.beta, j.transC};
     reds.push_back(r);
     red_ws_off.push_back((size_t)ws);
     for (int sidx = 0; sidx < splits; ++sidx) {
@@ -384,6 +385,7 @@ static void launch_gemms(std::vector<GemmJob>& jobs_all, cudaStream_t s) {
       sj.k = kl;
       sj.C = nullptr;  // set below (workspace)
       sj.ldc = j.m;
+      sj.transC = 0;  // partial products in the column-major workspace
       sj.beta = cmk(0.0, 0.0);
       sj.tile_base = (int)(ws + (int64_t)sidx * j.m * j.n);  // temporary: workspace offset
       jobs.push_back(sj);
@@ -976,7 +978,27 @@ static void apply_impl(const Handle& H, const cplx* b, cplx* xout, int64_t nrhs,
     dn[l].alloc(std::max<int64_t>(levels[l].ntot * nrhs, 1));
   }
   auto upptr = [&](int l) -> const cplx* { return l == Lv ? b : up[l].get(); };
-  const int ta = trans ? 1 : 0;
+  // Y = Op^T X for a factor Op (stored rows x cols, ld) and a level vector X (rows x nrhs):
+  // formed as Y^T = X^T Op (nrhs x cols, Y written row-major), so that the many right-hand
+  // sides fill the 128-row tiles of the tensor-core products even at the leaves.
+  auto tprod = [&](std::vector<GemmJob>& gj, const cplx* Op, int rows, int cols, int ld, const cplx* X, int64_t ldx,
+                   cplx* Y, int64_t ldy, cplx beta) {
+    GemmJob j{};
+    j.A = X;
+    j.lda = (int)ldx;
+    j.transA = 1;
+    j.B = Op;
+    j.ldb = ld;
+    j.C = Y;
+    j.ldc = (int)ldy;
+    j.transC = 1;
+    j.m = (int)nrhs;
+    j.n = cols;
+    j.k = rows;
+    j.alpha = cmk(1, 0);
+    j.beta = beta;
+    gj.push_back(j);
+  };
   for (int l = Lv; l >= 1; --l) {
     const Level& lv = levels[l];
     const Level& pa = levels[l - 1];
@@ -986,18 +1008,25 @@ static void apply_impl(const Handle& H, const cplx* b, cplx* xout, int64_t nrhs,
       if (k == 0) continue;
       const int parent = j >> 1;
       const int64_t prow = pa.off[parent] + ((j & 1) ? levels[l].k[j - 1] : 0);
-      // upward: F* (k x n), or E^T with E stored n x k
-      const cplx* Aop = trans ? lv.E.get() + lv.e_off[j] : lv.F.get() + lv.f_off[j];
-      const int lda = trans ? n : k;
-      gj.push_back({Aop, upptr(l) + lv.off[j], up[l - 1].get() + prow, k, (int)nrhs, n, lda, (int)lv.ntot,
-                    (int)pa.ntot, cmk(1, 0), cmk(0, 0), 0, 0, 0, ta});
+      if (trans) {
+        // upward: E^T b (E stored n x k)
+        tprod(gj, lv.E.get() + lv.e_off[j], n, k, n, upptr(l) + lv.off[j], lv.ntot, up[l - 1].get() + prow, pa.ntot,
+              cmk(0, 0));
+      } else {
+        // upward: F* b (F* stored k x n)
+        gj.push_back({lv.F.get() + lv.f_off[j], upptr(l) + lv.off[j], up[l - 1].get() + prow, k, (int)nrhs, n, k,
+                      (int)lv.ntot, (int)pa.ntot, cmk(1, 0), cmk(0, 0), 0, 0, 0, 0, 0});
+      }
     }
     run_gemms(gj, s);
   }
   {
-    std::vector<GemmJob> gj(1);
-    gj[0] = {H.Groot.get(), up[0].get(), dn[0].get(), H.nroot, (int)nrhs, H.nroot, H.nroot, H.nroot, H.nroot,
-             cmk(1, 0), cmk(0, 0), 0, 0, 0, ta};
+    std::vector<GemmJob> gj;
+    if (trans)
+      tprod(gj, H.Groot.get(), H.nroot, H.nroot, H.nroot, up[0].get(), H.nroot, dn[0].get(), H.nroot, cmk(0, 0));
+    else
+      gj.push_back({H.Groot.get(), up[0].get(), dn[0].get(), H.nroot, (int)nrhs, H.nroot, H.nroot, H.nroot, H.nroot,
+                    cmk(1, 0), cmk(0, 0), 0, 0, 0, 0, 0});
     run_gemms(gj, s);
   }
   for (int l = 1; l <= Lv; ++l) {
@@ -1008,8 +1037,12 @@ static void apply_impl(const Handle& H, const cplx* b, cplx* xout, int64_t nrhs,
     for (int j = 0; j < lv.count; ++j) {
       const int n = lv.n[j];
       // x_tau = G b_tau  (or G^T b_tau)
-      gj.push_back({lv.G.get() + lv.g_off[j], upptr(l) + lv.off[j], outp + lv.off[j], n, (int)nrhs, n, n,
-                    (int)lv.ntot, (int)lv.ntot, cmk(1, 0), cmk(0, 0), 0, 0, 0, ta});
+      if (trans)
+        tprod(gj, lv.G.get() + lv.g_off[j], n, n, n, upptr(l) + lv.off[j], lv.ntot, outp + lv.off[j], lv.ntot,
+              cmk(0, 0));
+      else
+        gj.push_back({lv.G.get() + lv.g_off[j], upptr(l) + lv.off[j], outp + lv.off[j], n, (int)nrhs, n, n,
+                      (int)lv.ntot, (int)lv.ntot, cmk(1, 0), cmk(0, 0), 0, 0, 0, 0, 0});
     }
     run_gemms(gj, s);
     gj.clear();
@@ -1018,11 +1051,15 @@ static void apply_impl(const Handle& H, const cplx* b, cplx* xout, int64_t nrhs,
       if (k == 0) continue;
       const int parent = j >> 1;
       const int64_t prow = pa.off[parent] + ((j & 1) ? levels[l].k[j - 1] : 0);
-      // x_tau += E x^_tau  (or F*^T x^_tau with F* stored k x n)
-      const cplx* Aop = trans ? lv.F.get() + lv.f_off[j] : lv.E.get() + lv.e_off[j];
-      const int lda = trans ? k : n;
-      gj.push_back({Aop, dn[l - 1].get() + prow, outp + lv.off[j], n, (int)nrhs, k, lda, (int)pa.ntot, (int)lv.ntot,
-                    cmk(1, 0), cmk(1, 0), 0, 0, 0, ta});
+      if (trans) {
+        // x_tau += F*^T x^_tau  (F* stored k x n)
+        tprod(gj, lv.F.get() + lv.f_off[j], k, n, k, dn[l - 1].get() + prow, pa.ntot, outp + lv.off[j], lv.ntot,
+              cmk(1, 0));
+      } else {
+        // x_tau += E x^_tau  (E stored n x k)
+        gj.push_back({lv.E.get() + lv.e_off[j], dn[l - 1].get() + prow, outp + lv.off[j], n, (int)nrhs, k, n,
+                      (int)pa.ntot, (int)lv.ntot, cmk(1, 0), cmk(1, 0), 0, 0, 0, 0, 0});
+      }
     }
     run_gemms(gj, s);
   }

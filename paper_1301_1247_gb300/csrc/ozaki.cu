@@ -226,6 +226,7 @@ struct OzJob {
   cplx alpha, beta;
   cplx* C;  // splits == 1: C = alpha op(A) B + beta C directly
   int ldc;
+  int transC;  // C row-major
   cplx* W;  // splits > 1: alpha (partial product) per split, splits x (m x n), reduced afterwards
 };
 
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const OzJob* jobs, int njobs,
         const double im = ldexp(f2d_bits(Rh[1][c]) + f2d_bits(Rl[1][c]), sc);
         cplx v = cmk(al.x * re - al.y * im, al.x * im + al.y * re);
         if (jb.splits == 1) {
-          cplx* cp = jb.C + (int64_t)col * jb.ldc + row;
+          cplx* cp = jb.transC ? jb.C + (int64_t)row * jb.ldc + col : jb.C + (int64_t)col * jb.ldc + row;
           if (with_beta) v = cfma(be, *cp, v);
           *cp = v;
         } else {
@@ -403,14 +404,14 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const OzJob* jobs, int njobs,
 }
 
 // C = beta C + sum_s W_s (fixed order).
-__global__ void k_oz_reduce(const cplx* W, int m, int n, int splits, cplx beta, cplx* C, int ldc) {
+__global__ void k_oz_reduce(const cplx* W, int m, int n, int splits, cplx beta, cplx* C, int ldc, int transC) {
   const int64_t tot = (int64_t)m * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % m);
     const int64_t j = e / m;
     cplx acc = cmk(0.0, 0.0);
     for (int s = 0; s < splits; ++s) acc = cadd(acc, W[s * tot + e]);
-    cplx* c = C + j * ldc + i;
+    cplx* c = transC ? C + (int64_t)i * ldc + j : C + j * ldc + i;
     if (beta.x != 0.0 || beta.y != 0.0) acc = cfma(beta, *c, acc);
     *c = acc;
   }
@@ -418,8 +419,9 @@ __global__ void k_oz_reduce(const cplx* W, int m, int n, int splits, cplx beta, 
 
 }  // namespace
 
-// Products worth the tensor cores: enough k for the digit planes to pay (bands of 128 k)
-// and enough rows for the 128-row tiles.
+// Products worth the tensor cores: enough k for the digit planes to pay and enough rows for
+// the 128-row tiles.  (Routing the leaf products of the sweeps, k ~ 50, here as well was
+// measured slower: their digit planes cost as much as the double-float product.)
 bool ozaki_eligible(const GemmJob& j) { return j.k >= 96 && j.m >= 48 && j.n >= 8; }
 
 // A batch of products on the tensor cores (see the head of this file): exponents and digit
@@ -452,7 +454,7 @@ void ozaki_gemm_batched(const std::vector<GemmJob>& js, cudaStream_t s) {
     o.tiles_n = (j.n + OZ_BN - 1) / OZ_BN;
     o.mpad = o.tiles_m * OZ_BM;
     o.npad = o.tiles_n * OZ_BN;
-    o.Kpad = (j.k + OZ_FLUSH - 1) / OZ_FLUSH * OZ_FLUSH;
+    o.Kpad = (j.k + OZ_BK - 1) / OZ_BK * OZ_BK;  // stages of 16; the last period may be short
     tiles_all += o.tiles_m * o.tiles_n;
   }
   for (int q = 0; q < nj; ++q) {
@@ -462,7 +464,7 @@ void ozaki_gemm_batched(const std::vector<GemmJob>& js, cudaStream_t s) {
     o.splits = 1;
     if (tiles_all < sms && j.k >= 4096)
       o.splits = std::max(1, std::min(o.Kpad / OZ_FLUSH, sms / std::max(1, tiles_all)));
-    o.klen = (o.Kpad / OZ_FLUSH + o.splits - 1) / o.splits * OZ_FLUSH;
+    o.klen = ((o.Kpad + OZ_FLUSH - 1) / OZ_FLUSH + o.splits - 1) / o.splits * OZ_FLUSH;
     o.splits = (o.Kpad + o.klen - 1) / o.klen;
     o.item_base = items;
     items += (int64_t)o.tiles_m * o.tiles_n * o.splits;
@@ -470,6 +472,7 @@ void ozaki_gemm_batched(const std::vector<GemmJob>& js, cudaStream_t s) {
     o.beta = j.beta;
     o.C = j.C;
     o.ldc = j.ldc;
+    o.transC = j.transC;
     o.Ad = reinterpret_cast<const unsigned short*>(adig);  // offsets for now
     o.Bd = reinterpret_cast<const unsigned short*>(bdig);
     o.Er = reinterpret_cast<const int*>(eA);
@@ -534,7 +537,7 @@ void ozaki_gemm_batched(const std::vector<GemmJob>& js, cudaStream_t s) {
     const OzJob& o = oj[q];
     if (o.splits <= 1) continue;
     prof::KScope _ks("k_oz_reduce", s);
-    k_oz_reduce<<<grid_1d((int64_t)o.m * o.n), 256, 0, s>>>(o.W, o.m, o.n, o.splits, o.beta, o.C, o.ldc);
+    k_oz_reduce<<<grid_1d((int64_t)o.m * o.n), 256, 0, s>>>(o.W, o.m, o.n, o.splits, o.beta, o.C, o.ldc, o.transC);
   }
   HBS_LAUNCH_CHECK("k_oz_reduce");
   int hs = 0;

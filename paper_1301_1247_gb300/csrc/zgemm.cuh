@@ -19,6 +19,7 @@ struct GemmJob {
   int tiles_m, tiles_n;  // ceil(m / BM), ceil(n / BN)
   int tile_base;         // prefix sum of tiles over earlier jobs
   int transA;            // 1: op(A) = A^T (A stored k x m, column-major, leading dimension lda)
+  int transC;            // 1: C stored row-major, C(i, j) at C[i ldc + j]
 };
 
 constexpr int GBM = 32, GBN = 32, GBK = 8;
@@ -79,7 +80,7 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched(const GemmJob* job
     for (int b = 0; b < 2; ++b) {
       int gr = row0 + tr + 16 * a, gc = col0 + tc + 16 * b;
       if (gr < m && gc < n) {
-        cplx* c = jb.C + (int64_t)gc * jb.ldc + gr;
+        cplx* c = jb.transC ? jb.C + (int64_t)gr * jb.ldc + gc : jb.C + (int64_t)gc * jb.ldc + gr;
         cplx v = cmul(jb.alpha, acc[a][b]);
         if (jb.beta.x != 0.0 || jb.beta.y != 0.0) v = cfma(jb.beta, *c, v);
         *c = v;
@@ -171,7 +172,7 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* 
     for (int b = 0; b < 2; ++b) {
       int gr = row0 + tr + 16 * a, gc = col0 + tc + 16 * b;
       if (gr < m && gc < n) {
-        cplx* c = jb.C + (int64_t)gc * jb.ldc + gr;
+        cplx* c = jb.transC ? jb.C + (int64_t)gr * jb.ldc + gc : jb.C + (int64_t)gc * jb.ldc + gr;
         const dfc& q = acc[a][b];
         // the common (alpha, beta) = (1, 0) and (-1, 1) take two or four FP64 adds only
         const cplx sum = cmk(f2d_bits(q.rh) + f2d_bits(q.rl), f2d_bits(q.ih) + f2d_bits(q.il));
