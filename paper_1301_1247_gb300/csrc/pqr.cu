@@ -8,7 +8,7 @@
 //     on ties) - the same reduction in every CTA, so all agree bit for bit;
 //   * every CTA forms the reflector of column p (rows s..m-1) in shared memory;
 //   * each active column j != p is owned by one warp and is updated (in registers for
-//     its first 320 rows), its norm downdated (recomputed on cancellation), and the
+//     its first 64 rows, the rest streamed 4 rows per lane at a time), its norm downdated (recomputed on cancellation), and the
 //     CTA's partial maximum for step s+1 recorded.
 // Columns are never swapped: pivot p of step s stays where it is, its rows < s hold
 // R(:, s) and its rows > s the reflector tail; the diagonal beta_s, the reflector head
@@ -30,7 +30,19 @@ namespace {
 
 constexpr int kNT = 256;
 constexpr int kNW = kNT / 32;
-constexpr int kReg = 10;        // rows per lane held in registers
+constexpr int kReg = 2;   // rows per lane held in registers between the two passes of an update
+constexpr int kU = 4;     // rows per lane loaded together in the streamed part (loads in flight)
+
+// L1 prefetch of the lane's next kU rows (in-bounds rows only): another chunk in flight
+// without holding registers for it.
+template <typename T>
+__device__ __forceinline__ void prefetch_next(const T* aj, int64_t i0, int64_t stride, int64_t m) {
+#pragma unroll
+  for (int u = 0; u < kU; ++u) {
+    const int64_t ip = i0 + stride * (kU + u);
+    if (ip < m) asm volatile("prefetch.L1 [%0];" ::"l"(aj + ip));
+  }
+}
 
 struct PqrJob {
   cplx* A;
@@ -92,7 +104,9 @@ __device__ __forceinline__ void tsolve_row_major(const cplx* R, int k, const cpl
 
 // One Householder update of column j at step s: the 32 lanes of a warp own the column,
 // its first 32 kReg rows below s stay in registers between the two passes and the rest
-// (tall matrices) is streamed twice.
+// (tall matrices) is streamed twice, kU rows per lane loaded together so that the loads
+// overlap instead of each waiting on the accumulation chain.  Each lane still adds its rows
+// in increasing order, so the sums do not depend on kU.
 __device__ __forceinline__ double update_col_warp(cplx* aj, const cplx* vt, int64_t m, int64_t s, cplx v0, double tau,
                                                   double nj, double* nref_j, int lane) {
   cplx r[kReg];
@@ -105,7 +119,16 @@ __device__ __forceinline__ double update_col_warp(cplx* aj, const cplx* vt, int6
       w = cfma(cconj(vt[i - s - 1]), r[q], w);
     }
   }
-  for (int64_t i = s + 1 + lane + 32 * kReg; i < m; i += 32) w = cfma(cconj(vt[i - s - 1]), aj[i], w);
+  for (int64_t i0 = s + 1 + lane + 32 * kReg; i0 < m; i0 += 32 * kU) {
+    prefetch_next(aj, i0, 32, m);
+    cplx a[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + 32 * u < m) a[u] = aj[i0 + 32 * u];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + 32 * u < m) w = cfma(cconj(vt[i0 + 32 * u - s - 1]), a[u], w);
+  }
   w = warp_sum_c(w);
   const cplx ajs = aj[s];
   w = cscale(cfma(cconj(v0), ajs, w), tau);
@@ -118,7 +141,16 @@ __device__ __forceinline__ double update_col_warp(cplx* aj, const cplx* vt, int6
       aj[i] = r[q];
     }
   }
-  for (int64_t i = s + 1 + lane + 32 * kReg; i < m; i += 32) aj[i] = cfms(vt[i - s - 1], w, aj[i]);
+  for (int64_t i0 = s + 1 + lane + 32 * kReg; i0 < m; i0 += 32 * kU) {
+    prefetch_next(aj, i0, 32, m);
+    cplx a[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + 32 * u < m) a[u] = aj[i0 + 32 * u];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + 32 * u < m) aj[i0 + 32 * u] = cfms(vt[i0 + 32 * u - s - 1], w, a[u]);
+  }
   double t = nj - cabs2(top);
   if (t <= 0.0078125 * *nref_j) {
     // cancellation: recompute the norm of rows s+1.. from the updated values
@@ -158,7 +190,16 @@ __device__ double update_col_group(cplx* aj, const cplx* vt, int64_t m, int64_t 
       w = cfma(cconj(vt[i - s - 1]), r[q], w);
     }
   }
-  for (int64_t i = s + 1 + gl + stride * kReg; i < m; i += stride) w = cfma(cconj(vt[i - s - 1]), aj[i], w);
+  for (int64_t i0 = s + 1 + gl + stride * kReg; i0 < m; i0 += stride * kU) {
+    prefetch_next(aj, i0, stride, m);
+    cplx a[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + stride * u < m) a[u] = aj[i0 + stride * u];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + stride * u < m) w = cfma(cconj(vt[i0 + stride * u - s - 1]), a[u], w);
+  }
   w = warp_sum_c(w);
   if (lane == 0) redc[base + wg] = w;
   group_barrier(1 + grp, 32 * GW);
@@ -174,7 +215,16 @@ __device__ double update_col_group(cplx* aj, const cplx* vt, int64_t m, int64_t 
       aj[i] = r[q];
     }
   }
-  for (int64_t i = s + 1 + gl + stride * kReg; i < m; i += stride) aj[i] = cfms(vt[i - s - 1], w, aj[i]);
+  for (int64_t i0 = s + 1 + gl + stride * kReg; i0 < m; i0 += stride * kU) {
+    prefetch_next(aj, i0, stride, m);
+    cplx a[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + stride * u < m) a[u] = aj[i0 + stride * u];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + stride * u < m) aj[i0 + stride * u] = cfms(vt[i0 + stride * u - s - 1], w, a[u]);
+  }
   double t = nj - cabs2(top);
   if (t <= 0.0078125 * *nref_j) {  // uniform over the group
     double q2 = 0.0;
@@ -230,7 +280,16 @@ __device__ __forceinline__ double update_col_warp_df(dfc* aj, const dfc* vt, int
       dfc_cdot_acc(vt[i - s - 1], r[q], w);
     }
   }
-  for (int64_t i = s + 1 + lane + 32 * kReg; i < m; i += 32) dfc_cdot_acc(vt[i - s - 1], aj[i], w);
+  for (int64_t i0 = s + 1 + lane + 32 * kReg; i0 < m; i0 += 32 * kU) {
+    prefetch_next(aj, i0, 32, m);
+    dfc a[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + 32 * u < m) a[u] = aj[i0 + 32 * u];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + 32 * u < m) dfc_cdot_acc(vt[i0 + 32 * u - s - 1], a[u], w);
+  }
   w = dfc_warp_sum(w);
   const dfc ajs = aj[s];
   dfc wv, top;
@@ -243,10 +302,18 @@ __device__ __forceinline__ double update_col_warp_df(dfc* aj, const dfc* vt, int
       aj[i] = r[q];
     }
   }
-  for (int64_t i = s + 1 + lane + 32 * kReg; i < m; i += 32) {
-    dfc a = aj[i];
-    dfc_sub_mul(vt[i - s - 1], wv, a);
-    aj[i] = a;
+  for (int64_t i0 = s + 1 + lane + 32 * kReg; i0 < m; i0 += 32 * kU) {
+    prefetch_next(aj, i0, 32, m);
+    dfc a[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + 32 * u < m) a[u] = aj[i0 + 32 * u];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + 32 * u < m) {
+        dfc_sub_mul(vt[i0 + 32 * u - s - 1], wv, a[u]);
+        aj[i0 + 32 * u] = a[u];
+      }
   }
   double t = df_downdate(nj, top);
   if (t <= 0.0078125 * *nref_j) {
@@ -279,7 +346,16 @@ __device__ double update_col_group_df(dfc* aj, const dfc* vt, int64_t m, int64_t
       dfc_cdot_acc(vt[i - s - 1], r[q], w);
     }
   }
-  for (int64_t i = s + 1 + gl + stride * kReg; i < m; i += stride) dfc_cdot_acc(vt[i - s - 1], aj[i], w);
+  for (int64_t i0 = s + 1 + gl + stride * kReg; i0 < m; i0 += stride * kU) {
+    prefetch_next(aj, i0, stride, m);
+    dfc a[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + stride * u < m) a[u] = aj[i0 + stride * u];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + stride * u < m) dfc_cdot_acc(vt[i0 + stride * u - s - 1], a[u], w);
+  }
   w = dfc_warp_sum(w);
   if (lane == 0) redc[base + wg] = w;
   group_barrier(1 + grp, 32 * GW);
@@ -300,10 +376,18 @@ __device__ double update_col_group_df(dfc* aj, const dfc* vt, int64_t m, int64_t
       aj[i] = r[q];
     }
   }
-  for (int64_t i = s + 1 + gl + stride * kReg; i < m; i += stride) {
-    dfc a = aj[i];
-    dfc_sub_mul(vt[i - s - 1], wv, a);
-    aj[i] = a;
+  for (int64_t i0 = s + 1 + gl + stride * kReg; i0 < m; i0 += stride * kU) {
+    prefetch_next(aj, i0, stride, m);
+    dfc a[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + stride * u < m) a[u] = aj[i0 + stride * u];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i0 + stride * u < m) {
+        dfc_sub_mul(vt[i0 + stride * u - s - 1], wv, a[u]);
+        aj[i0 + stride * u] = a[u];
+      }
   }
   double t = df_downdate(nj, top);
   if (t <= 0.0078125 * *nref_j) {  // uniform over the group
