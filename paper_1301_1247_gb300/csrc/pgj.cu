@@ -1,7 +1,7 @@
 // Persistent Gauss-Jordan inversion with partial pivoting for the large per-node blocks
 // of the HBS inversion (the D_tau of Eqs. def_muhD..def_muG at the top tree levels).
 // One cooperative launch runs every column step of every matrix in a batch, with one
-// grid barrier per step.
+// barrier per step among the CTAs of each matrix.
 //
 // Step c of a matrix: every CTA of the matrix copies column c into shared memory and takes
 // the pivot row p (largest modulus among rows >= c, lowest index on ties) and 1/pivot from
@@ -40,6 +40,7 @@ struct PgjJob {
   int* la_p;
   int* la_nz;
   cplx* la_ip;
+  GridSync* gs;  // barrier of this matrix's CTAs
 };
 
 // The next pivot of column `col` (rows >= c) by its owning warp, from its current values:
@@ -92,7 +93,7 @@ __device__ __forceinline__ cplx final_pivot_col(const cplx* u, int i, int c, cpl
 // in place as float pairs between a conversion pass at the start and one at the end, and
 // pivots are chosen on |a|^2 to float precision.
 template <bool DF>
-__global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nmax, GridSync* gs) {
+__global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nmax) {
   extern __shared__ cplx su[];
   __shared__ cplx s_ip[2];
   __shared__ dfc s_ipd[2];
@@ -105,8 +106,6 @@ __global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nma
   const int gw = lb * kNW + warp, nw = jb.nb * kNW;
   cplx* A = jb.A;
   dfc* D = reinterpret_cast<dfc*>(jb.A);
-  int steps = 0;
-  for (int q = 0; q < nj; ++q) steps = max(steps, jobs[q].n);
   if constexpr (DF) {
     for (int j = gw; j < n; j += nw)
       for (int i = lane; i < n; i += 32) D[(int64_t)j * n + i] = to_dfc_bits(A[(int64_t)j * n + i]);
@@ -116,9 +115,9 @@ __global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nma
     __syncwarp();
     pgj_lookahead<DF>(jb, A, 0, lane);
   }
-  if (grid_sync_sum(gs, 0) < 0) return;
-  for (int c = 0; c < steps; ++c) {
-    if (c < n) {
+  if (group_sync(jb.gs, (unsigned)jb.nb) < 0) return;
+  for (int c = 0; c < n; ++c) {
+    {
       const int par = c & 1;
       // pivot row and 1/pivot found at the end of the previous step (lookahead)
       const int p = jb.la_p[par];
@@ -219,7 +218,7 @@ __global__ void __launch_bounds__(kNT) k_pgj(const PgjJob* jobs, int nj, int nma
         }
       }
     }
-    if (grid_sync_sum(gs, 0) < 0) return;
+    if (group_sync(jb.gs, (unsigned)jb.nb) < 0) return;
   }
   // the last pivot column of this matrix
   if (n > 0) {
@@ -332,15 +331,15 @@ void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, con
   DevBuf<int> piv(ptot), sing(nj), la_p(2 * nj), la_nz(2 * nj);
   DevBuf<cplx> la_ip(2 * nj);
   DevBuf<cplx> tmp(atot);
-  DevBuf<GridSync> gs(1);
+  DevBuf<GridSync> gs(nj);
   HBS_CUDA(cudaMemsetAsync(sing.get(), 0, sizeof(int) * nj, s));
-  HBS_CUDA(cudaMemsetAsync(gs.get(), 0, sizeof(GridSync), s));
+  HBS_CUDA(cudaMemsetAsync(gs.get(), 0, sizeof(GridSync) * nj, s));
   std::vector<PgjJob> jobs(nj);
   int64_t po = 0, ao = 0;
   int b0 = 0;
   for (int j = 0; j < nj; ++j) {
     jobs[j] = {mats[j].first, mats[j].second, b0,  nb[j], piv.get() + po, sing.get() + j, tmp.get() + ao,
-               la_p.get() + 2 * j, la_nz.get() + 2 * j, la_ip.get() + 2 * j};
+               la_p.get() + 2 * j, la_nz.get() + 2 * j, la_ip.get() + 2 * j, gs.get() + j};
     po += mats[j].second;
     ao += (int64_t)mats[j].second * mats[j].second;
     b0 += nb[j];
@@ -348,12 +347,11 @@ void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, con
   DevBuf<PgjJob> dj;
   dj.upload(jobs, s);
   std::vector<int> hs(nj);
-  GridSync hg{};
+  std::vector<GridSync> hg(nj);
   {
     const PgjJob* a0 = dj.get();
     int a1 = nj, a2 = nmax;
-    GridSync* a3 = gs.get();
-    void* args[] = {&a0, &a1, &a2, &a3};
+    void* args[] = {&a0, &a1, &a2};
     std::lock_guard<std::mutex> lock(coop_mutex());
     {
       prof::KScope _ks("k_pgj", s, fl, 0.0);
@@ -361,10 +359,11 @@ void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, con
       HBS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kNT), args, smem, s));
     }
     HBS_LAUNCH_CHECK("k_pgj");
-    HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+    HBS_CUDA(cudaMemcpyAsync(hg.data(), gs.get(), sizeof(GridSync) * nj, cudaMemcpyDeviceToHost, s));
     HBS_CUDA(cudaStreamSynchronize(s));
   }
-  if (hg.timed_out) throw Error(HBS_ERR_TIMEOUT, "persistent Gauss-Jordan: a grid barrier wait gave up");
+  for (const auto& g : hg)
+    if (g.timed_out) throw Error(HBS_ERR_TIMEOUT, "persistent Gauss-Jordan: a barrier wait gave up");
   {
     prof::KScope _ks("k_pgj_unpivot", s);
     const size_t sm = (size_t)nmax * sizeof(int);

@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
     block_argmax_key<kNT>(best, bi, redv, redi, &v, &ix);
     if (tid == 0) { pv[blockIdx.x] = __longlong_as_double(v); pi[blockIdx.x] = ix; }
   }
-  if (group_sync_sum(jb.gs, 0, (unsigned)jb.nb) < 0) return;
+  if (group_sync(jb.gs, (unsigned)jb.nb) < 0) return;
 
   double r00 = 0.0, thr2 = 0.0;
   bool done = false;
@@ -615,8 +615,9 @@ __global__ void __launch_bounds__(kNT, 2) k_pqr(const PqrJob* jobs, int nj, doub
       block_argmax_key<kNT>(best, bi, redv, redi, &v, &ix);
       if (tid == 0) { pv[(1 - par) * G + blockIdx.x] = __longlong_as_double(v); pi[(1 - par) * G + blockIdx.x] = ix; }
     }
-    const long long act = group_sync_sum(jb.gs, (lb == 0 && !done) ? 1 : 0, (unsigned)jb.nb);
-    if (act <= 0) break;  // this matrix is finished (0) or a wait gave up (-1)
+    // Every CTA of the matrix takes the same stop decision (the same reduction of the same
+    // partial maxima), so all of them leave the loop after the same barrier.
+    if (group_sync(jb.gs, (unsigned)jb.nb) < 0 || done) break;
   }
   if constexpr (DF) {
     // Every CTA of this matrix has left the step loop at the same barrier: no update of

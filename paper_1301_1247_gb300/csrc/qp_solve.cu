@@ -101,7 +101,11 @@ struct HbsWorker {
   void start(Handle& h) {
     int dev = 0;
     HBS_CUDA(cudaGetDevice(&dev));
-    HBS_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    // The compression and inversion are the longer of the two concurrent chains: their
+    // CTAs are scheduled ahead of the periodizer's whenever both are waiting.
+    int least = 0, greatest = 0;
+    HBS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    HBS_CUDA(cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, greatest));
     const bool df = gemm_double_float(), tc = gemm_tensor();
     t = std::thread([this, &h, dev, df, tc] {
       try {
@@ -1085,7 +1089,7 @@ __global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* group
         dfc* cd = reinterpret_cast<dfc*>(c64);
         for (int i = tid; i < n; i += NT) cd[i] = to_dfc_bits(c64[i]);
       }
-    if (grid_sync_sum(gs, 0) < 0) return;
+    if (grid_sync(gs) < 0) return;
   }
   double pmax = 0.0, pmin = 1e300;
   for (int pn = 0; pn < npan; ++pn) {
@@ -1132,7 +1136,7 @@ __global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* group
         __syncthreads();
       }
     }
-    if (grid_sync_sum(gs, 0) < 0) return;
+    if (grid_sync(gs) < 0) return;
     const int j0 = k0 + nb;
     const bool upd = live && j0 < nc;
     if (upd) {
@@ -1155,7 +1159,7 @@ __global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* group
           if (r < nb) aj[r] = u[r];
       }
     }
-    if (grid_sync_sum(gs, 0) < 0) return;
+    if (grid_sync(gs) < 0) return;
     if (upd) {
       const int rows = n - j0, cols = nc - j0;
       const int nrt = (rows + TM - 1) / TM, nct = (cols + TM - 1) / TM;
@@ -1206,7 +1210,7 @@ __global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* group
         __syncthreads();
       }
     }
-    if (grid_sync_sum(gs, 0) < 0) return;
+    if (grid_sync(gs) < 0) return;
   }
   if (act) {
     // back substitution, one right-hand side per warp of the group's CTAs
@@ -1224,7 +1228,7 @@ __global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* group
     if (rank == 0 && tid == 0) illcond[g] = (pmin <= 1e-28 * pmax) ? 1 : 0;
   }
   if constexpr (DF) {
-    if (grid_sync_sum(gs, 0) < 0) return;  // every CTA of the group is done with [S | R]
+    if (grid_sync(gs) < 0) return;  // every CTA of the group is done with [S | R]
     if (act)
       for (int j = rank; j < nc; j += CL) {
         cplx* c64 = col64(j);
