@@ -321,6 +321,7 @@ void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, con
   const bool df = gemm_double_float();
   const int G = df ? pgj_grid<true>(smem) : pgj_grid<false>(smem);
   if (nj > G) throw Error(HBS_ERR_INTERNAL, "persistent Gauss-Jordan batch larger than the grid");
+  // CTAs per matrix in proportion to its size, at least one each.
   std::vector<int> nb(nj, 1);
   const int left = G - nj;
   for (int j = 0; j < nj; ++j)

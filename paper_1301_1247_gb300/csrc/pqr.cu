@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cstdio>
 
+#include "balance.hpp"
 #include "dense_kernels.cuh"
 #include "dfloat.cuh"
 #include "gridsync.cuh"
@@ -921,6 +922,14 @@ __global__ void k_set_unit_cols(cplx* X, int k, const int64_t* idx) {
   }
 }
 
+// Warps per column group for a matrix on b CTAs: doubled while the groups still cover
+// every column and each lane keeps at least four rows.
+static int col_group_warps(int b, int64_t m, int64_t n) {
+  int g = 1;
+  while (g < 8 && (int64_t)b * (kNW / (2 * g)) >= n && m >= (int64_t)32 * (2 * g) * 4) g *= 2;
+  return g;
+}
+
 template <bool DF>
 static int pqr_grid(size_t smem) {
   static const int sms = [] {
@@ -937,19 +946,17 @@ static int pqr_grid(size_t smem) {
   return sms * std::min(per_sm, 2);
 }
 
-void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrOut& out) {
+void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrOut& out, bool equal_steps) {
   const int nj = (int)specs.size();
   out.rank.assign(nj, 0);
   out.koff.assign(nj + 1, 0);
   if (nj == 0) return;
   int64_t mmax = 0, ntot = 0;
-  double work = 0.0;
   for (int j = 0; j < nj; ++j) {
     const auto& sp = specs[j];
     mmax = std::max(mmax, sp.m);
     ntot += sp.n;
     out.koff[j + 1] = out.koff[j] + std::max(1, sp.kcap);
-    work += (double)sp.m * sp.n;
   }
   const int vcap = (int)std::min<int64_t>(mmax, 6144);
   const size_t smem = (size_t)vcap * sizeof(cplx);
@@ -958,16 +965,20 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
   const bool df = gemm_double_float();
   const int G = df ? pqr_grid<true>(smem) : pqr_grid<false>(smem);
   if (nj > G) throw Error(HBS_ERR_INTERNAL, "persistent QR batch larger than the grid");
-  // CTAs per matrix in proportion to its size, at least one each.
-  std::vector<int> nb(nj, 1);
-  int left = G - nj;
-  for (int j = 0; j < nj; ++j) {
-    const int extra = (int)std::floor((double)left * specs[j].m * specs[j].n / work);
-    nb[j] += extra;
-  }
-  int used = 0;
-  for (int v : nb) used += v;
-  for (int j = 0; used < G; j = (j + 1) % nj, ++used) ++nb[j];
+  // CTAs per matrix: a step of matrix j on b CTAs takes about as long as its busiest
+  // column group's work (columns per group x rows per lane, the groups' width GW as chosen
+  // below) plus a fixed cost of the pivot choice, the reflector and the barrier (about 24
+  // such units, measured), for up to min(m, n, kcap) steps (or the same number for all).
+  const std::vector<int> nb = balance_ctas(G, nj, [&](int j, int b) {
+    const auto& sp = specs[j];
+    const int g = col_group_warps(b, sp.m, sp.n);
+    const int64_t groups = (int64_t)b * (kNW / g);
+    const double cols = (double)((sp.n + groups - 1) / groups);
+    const double rows = (double)((sp.m + 32 * g - 1) / (32 * g));
+    const double steps =
+        equal_steps ? 1.0 : (double)std::max<int64_t>(1, std::min<int64_t>(sp.kcap, std::min(sp.m, sp.n)));
+    return steps * (cols * rows + 24.0);
+  });
   const int64_t ktot = out.koff[nj];
   int64_t r11tot = 0;
   std::vector<int64_t> r11off(nj);
@@ -992,10 +1003,7 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
   int b0 = 0;
   for (int j = 0; j < nj; ++j) {
     const auto& sp = specs[j];
-    // warps per column: double while the column groups still cover every column and each
-    // lane keeps at least four rows
-    int gwv = 1;
-    while (gwv < 8 && (int64_t)nb[j] * (kNW / (2 * gwv)) >= sp.n && sp.m >= (int64_t)32 * (2 * gwv) * 4) gwv *= 2;
+    const int gwv = col_group_warps(nb[j], sp.m, sp.n);
     jobs[j] = {sp.A, sp.m, sp.n, sp.kcap, b0, nb[j], gwv, nrm.get() + o, nref.get() + o,
                out.piv.get() + out.koff[j], out.beta.get() + out.koff[j], out.v0.get() + out.koff[j],
                out.tau.get() + out.koff[j], st.get() + j, sp.perm, sp.T, r11.get() + r11off[j],

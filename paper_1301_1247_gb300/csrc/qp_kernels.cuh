@@ -49,7 +49,9 @@ struct PqrOut {
   DevBuf<cplx> beta, v0;
   DevBuf<double> tau;
 };
-void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrOut& out);
+// equal_steps: the matrices are expected to reach similar ranks (the CTAs are then divided
+// by the work of one step); otherwise each is expected to run min(m, n, kcap) steps.
+void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrOut& out, bool equal_steps = false);
 // W(:, c) <- R11^{-1} W(:, c) (first k rows) with R11 of matrix `job` of a pqr_run on A (m rows).
 void pqr_solve_r11(const cplx* A, int64_t m, const PqrOut& qr, int job, int k, cplx* W, int64_t ldw, int64_t ncols,
                    cudaStream_t s);

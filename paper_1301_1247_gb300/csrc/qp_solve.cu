@@ -414,7 +414,7 @@ void build_periodizer(Handle& h, cudaStream_t s, bool with_hbs) {
     fspecs.push_back({f.A.get(), ns, ncols, std::min(ns, ncols), f.perm.get(), f.T.get()});
   }
   PqrOut fqr;
-  pqr_run(fspecs, ptol, s, fqr);
+  pqr_run(fspecs, ptol, s, fqr, /*equal_steps=*/true);  // family ranks are alike (~100-200 at w = 60)
   int fqr_rank[3];
   for (int fi = 0; fi < 3; ++fi) fqr_rank[fi] = fqr.rank[fi];
   h.pid_residual = 0.0;
