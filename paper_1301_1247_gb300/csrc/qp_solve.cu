@@ -1240,51 +1240,53 @@ __global__ void __launch_bounds__(NT) k_schur_coop(Dims D, const GroupJob* group
 
 // One step of iterative refinement per group against the FP64 system (after a factorization
 // in double-float): Rres holds R - S X (computed in FP64); solve (LU) d = P Rres with the
-// stored factors and pivots, and X += d.  One CTA per group, one right-hand side per warp,
-// in shared memory; 1/U_ii is formed once per group.
-__global__ void __launch_bounds__(256) k_schur_refine(const GroupJob* groups, const cplx* Spool, cplx* Rpool,
-                                                      const cplx* Rres, const int* pivpool, int pstride) {
-  extern __shared__ cplx sref[];  // n (1/U_ii) + 8 n (one column per warp)
-  const GroupJob G = groups[blockIdx.x];
-  const int n = G.nsys, q = G.q;
+// stored factors and pivots, and X += d.  One single-warp CTA per group and right-hand side
+// (CTA g qmax + j: right-hand side j of group g), in shared memory: the triangular solves are
+// sequential in the row index, so the parallelism is across the right-hand sides of all
+// groups.
+__global__ void __launch_bounds__(32) k_schur_refine(const GroupJob* groups, const cplx* Spool, cplx* Rpool,
+                                                     const cplx* Rres, const int* pivpool, int pstride, int qmax) {
+  extern __shared__ cplx sref[];  // n (1/U_ii) + n (the right-hand side)
+  const int g = (int)(blockIdx.x / (unsigned)qmax), j = (int)(blockIdx.x % (unsigned)qmax);
+  const GroupJob G = groups[g];
+  const int n = G.nsys;
+  if (j >= G.q) return;
   const cplx* A = Spool + G.s_off;
-  const int* piv = pivpool + (int64_t)blockIdx.x * pstride;
+  const int* piv = pivpool + (int64_t)g * pstride;
+  const int lane = threadIdx.x;
   cplx* inv = sref;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) inv[i] = cdiv(cmk(1, 0), A[(int64_t)i * n + i]);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  cplx* r = sref + n + (int64_t)warp * n;
-  for (int j = warp; j < q; j += 8) {
-    const cplx* rr = Rres + G.r_off + (int64_t)j * n;
-    for (int i = lane; i < n; i += 32) r[i] = rr[i];
-    __syncwarp();
-    if (lane == 0)
-      for (int c = 0; c < n; ++c) {
-        const int p = piv[c];
-        if (p != c) {
-          const cplx t = r[c];
-          r[c] = r[p];
-          r[p] = t;
-        }
+  cplx* r = sref + n;
+  const cplx* rr = Rres + G.r_off + (int64_t)j * n;
+  for (int i = lane; i < n; i += 32) {
+    inv[i] = cdiv(cmk(1, 0), A[(int64_t)i * n + i]);
+    r[i] = rr[i];
+  }
+  __syncwarp();
+  if (lane == 0)
+    for (int c = 0; c < n; ++c) {
+      const int p = piv[c];
+      if (p != c) {
+        const cplx t = r[c];
+        r[c] = r[p];
+        r[p] = t;
       }
+    }
+  __syncwarp();
+  for (int t = 0; t < n; ++t) {  // unit lower L
+    const cplx rt = r[t];
     __syncwarp();
-    for (int t = 0; t < n; ++t) {  // unit lower L
-      const cplx rt = r[t];
-      __syncwarp();
-      for (int i = t + 1 + lane; i < n; i += 32) r[i] = cfms(A[(int64_t)t * n + i], rt, r[i]);
-      __syncwarp();
-    }
-    for (int t = n - 1; t >= 0; --t) {  // upper U
-      if (lane == 0) r[t] = cmul(r[t], inv[t]);
-      __syncwarp();
-      const cplx rt = r[t];
-      for (int i = lane; i < t; i += 32) r[i] = cfms(A[(int64_t)t * n + i], rt, r[i]);
-      __syncwarp();
-    }
-    cplx* x = Rpool + G.r_off + (int64_t)j * n;
-    for (int i = lane; i < n; i += 32) x[i] = cadd(x[i], r[i]);
+    for (int i = t + 1 + lane; i < n; i += 32) r[i] = cfms(A[(int64_t)t * n + i], rt, r[i]);
     __syncwarp();
   }
+  for (int t = n - 1; t >= 0; --t) {  // upper U
+    if (lane == 0) r[t] = cmul(r[t], inv[t]);
+    __syncwarp();
+    const cplx rt = r[t];
+    for (int i = lane; i < t; i += 32) r[i] = cfms(A[(int64_t)t * n + i], rt, r[i]);
+    __syncwarp();
+  }
+  cplx* x = Rpool + G.r_off + (int64_t)j * n;
+  for (int i = lane; i < n; i += 32) x[i] = cadd(x[i], r[i]);
 }
 
 // Factor and solve every group's Schur system: CL CTAs per group in one cooperative launch
@@ -1358,10 +1360,12 @@ static void schur_solve(const Dims& D, const std::vector<GroupJob>& gjobs, const
   }
   {
     prof::KScope _ks("k_schur_refine", s);
-    const size_t shm = (size_t)9 * nmax * sizeof(cplx);
+    const size_t shm = (size_t)2 * nmax * sizeof(cplx);
     if (shm > 48 * 1024)
       HBS_CUDA(cudaFuncSetAttribute(k_schur_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    k_schur_refine<<<ng, 256, shm, s>>>(dg, Sp, Rp, R0.get(), piv.get(), nmax);
+    int qmax = 1;
+    for (const auto& G : gjobs) qmax = std::max(qmax, G.q);
+    k_schur_refine<<<(unsigned)(ng * qmax), 32, shm, s>>>(dg, Sp, Rp, R0.get(), piv.get(), nmax, qmax);
   }
   HBS_LAUNCH_CHECK("k_schur_refine");
 }

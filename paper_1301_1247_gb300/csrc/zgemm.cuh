@@ -24,6 +24,24 @@ struct GemmJob {
 
 constexpr int GBM = 32, GBN = 32, GBK = 8;
 
+// The multiply-adds of one GBK slice for one thread's outputs (rows tr, tr + 16; columns tc,
+// tc + 16), leaving out the second row (R1 false) or column (C1 false).
+template <bool R1, bool C1>
+__device__ __forceinline__ void tile_fma(const cplx (*As)[GBM + 1], const cplx (*Bs)[GBN + 1], int tr, int tc,
+                                         cplx (&acc)[2][2]) {
+#pragma unroll
+  for (int kk = 0; kk < GBK; ++kk) {
+    const cplx a0 = As[kk][tr], b0 = Bs[kk][tc];
+    acc[0][0] = cfma(a0, b0, acc[0][0]);
+    if (C1) {
+      const cplx b1 = Bs[kk][tc + 16];
+      acc[0][1] = cfma(a0, b1, acc[0][1]);
+      if (R1) acc[1][1] = cfma(As[kk][tr + 16], b1, acc[1][1]);
+    }
+    if (R1) acc[1][0] = cfma(As[kk][tr + 16], b0, acc[1][0]);
+  }
+}
+
 // grid.x = total tiles over all jobs; each CTA finds its job by binary search on tile_base.
 static __global__ void __launch_bounds__(256) k_zgemm_batched(const GemmJob* jobs, int njobs) {
   __shared__ cplx As[GBK][GBM + 1];
@@ -46,6 +64,11 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched(const GemmJob* job
 #pragma unroll
     for (int b = 0; b < 2; ++b) acc[a][b] = cmk(0.0, 0.0);
   const int m = jb.m, n = jb.n, K = jb.k;
+  // Output columns tc and tc + 16, rows tr and tr + 16 of the tile: a warp holds two values
+  // of tc and all 16 of tr, so for narrow products whole warps skip the multiply-adds of
+  // columns past n, and every warp those of rows past m when the tile has at most 16 (a warp
+  // instruction costs the same however many of its lanes are active).
+  const bool c0 = col0 + tc < n, c1 = col0 + tc + 16 < n, r1 = row0 + 16 < m;
   for (int k0 = 0; k0 < K; k0 += GBK) {
     // load A tile (GBM x GBK): 256 threads, one element each
     {
@@ -63,14 +86,14 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched(const GemmJob* job
       Bs[kb][c] = (gc < n && gkb < K) ? jb.B[(int64_t)gc * jb.ldb + gkb] : cmk(0.0, 0.0);
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GBK; ++kk) {
-      cplx a0 = As[kk][tr], a1 = As[kk][tr + 16];
-      cplx b0 = Bs[kk][tc], b1 = Bs[kk][tc + 16];
-      acc[0][0] = cfma(a0, b0, acc[0][0]);
-      acc[0][1] = cfma(a0, b1, acc[0][1]);
-      acc[1][0] = cfma(a1, b0, acc[1][0]);
-      acc[1][1] = cfma(a1, b1, acc[1][1]);
+    if (c0) {
+      if (c1) {
+        if (r1) tile_fma<true, true>(As, Bs, tr, tc, acc);
+        else tile_fma<false, true>(As, Bs, tr, tc, acc);
+      } else {
+        if (r1) tile_fma<true, false>(As, Bs, tr, tc, acc);
+        else tile_fma<false, false>(As, Bs, tr, tc, acc);
+      }
     }
     __syncthreads();
   }
@@ -97,6 +120,32 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched(const GemmJob* job
 // double-float product is several times faster than DFMA while keeping relative
 // errors near 2^-48 per operation; results are written back in FP64.
 // ---------------------------------------------------------------------------
+// acc += a b in double-float (re += ar br - ai bi; im += ar bi + ai br), lazy low parts.
+__device__ __forceinline__ void dfc_mac_tile(const dfc& a, const dfc& b, dfc& c) {
+  df_mac(a.rh, a.rl, b.rh, b.rl, c.rh, c.rl);
+  df_mac(-a.ih, -a.il, b.ih, b.il, c.rh, c.rl);
+  df_mac(a.rh, a.rl, b.ih, b.il, c.ih, c.il);
+  df_mac(a.ih, a.il, b.rh, b.rl, c.ih, c.il);
+}
+
+// The double-float multiply-adds of one GBK slice for one thread's outputs, leaving out the
+// second row (R1 false) or column (C1 false).
+template <bool R1, bool C1>
+__device__ __forceinline__ void tile_mac_df(const dfc (*As)[GBM + 1], const dfc (*Bs)[GBN + 1], int tr, int tc,
+                                            dfc (&acc)[2][2]) {
+#pragma unroll
+  for (int kk = 0; kk < GBK; ++kk) {
+    const dfc a0 = As[kk][tr], b0 = Bs[kk][tc];
+    dfc_mac_tile(a0, b0, acc[0][0]);
+    if (C1) {
+      const dfc b1 = Bs[kk][tc + 16];
+      dfc_mac_tile(a0, b1, acc[0][1]);
+      if (R1) dfc_mac_tile(As[kk][tr + 16], b1, acc[1][1]);
+    }
+    if (R1) dfc_mac_tile(As[kk][tr + 16], b0, acc[1][0]);
+  }
+}
+
 static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* jobs, int njobs) {
   __shared__ dfc As[GBK][GBM + 1];
   __shared__ dfc Bs[GBK][GBN + 1];
@@ -118,6 +167,8 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* 
 #pragma unroll
     for (int b = 0; b < 2; ++b) acc[a][b] = {0.f, 0.f, 0.f, 0.f};
   const int m = jb.m, n = jb.n, K = jb.k;
+  // the same skipping of padded rows and columns as in k_zgemm_batched
+  const bool c0 = col0 + tc < n, c1 = col0 + tc + 16 < n, r1 = row0 + 16 < m;
   for (int k0 = 0; k0 < K; k0 += GBK) {
     {
       cplx av;
@@ -137,21 +188,14 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* 
       Bs[kb][c] = to_dfc_bits((gc < n && gkb < K) ? jb.B[(int64_t)gc * jb.ldb + gkb] : cmk(0.0, 0.0));
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GBK; ++kk) {
-      const dfc a[2] = {As[kk][tr], As[kk][tr + 16]};
-      const dfc b[2] = {Bs[kk][tc], Bs[kk][tc + 16]};
-#pragma unroll
-      for (int x = 0; x < 2; ++x)
-#pragma unroll
-        for (int y = 0; y < 2; ++y) {
-          dfc& c = acc[x][y];
-          // re += ar br - ai bi ; im += ar bi + ai br
-          df_mac(a[x].rh, a[x].rl, b[y].rh, b[y].rl, c.rh, c.rl);
-          df_mac(-a[x].ih, -a[x].il, b[y].ih, b[y].il, c.rh, c.rl);
-          df_mac(a[x].rh, a[x].rl, b[y].ih, b[y].il, c.ih, c.il);
-          df_mac(a[x].ih, a[x].il, b[y].rh, b[y].rl, c.ih, c.il);
-        }
+    if (c0) {
+      if (c1) {
+        if (r1) tile_mac_df<true, true>(As, Bs, tr, tc, acc);
+        else tile_mac_df<false, true>(As, Bs, tr, tc, acc);
+      } else {
+        if (r1) tile_mac_df<true, false>(As, Bs, tr, tc, acc);
+        else tile_mac_df<false, false>(As, Bs, tr, tc, acc);
+      }
     }
 #pragma unroll
     for (int x = 0; x < 2; ++x)
