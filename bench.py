@@ -138,6 +138,12 @@ def barrier(ws):
         dist.barrier()
 
 
+def whole_job_rate(ws, units_per_step, steps, ms_max):
+    """Units per second of the whole job: every rank processes units_per_step units per
+    step (weak scaling), and the slowest rank's time (ms_max, max over ranks) counts."""
+    return ws * units_per_step * steps / (ms_max / 1e3)
+
+
 def max_over_ranks(v, ws):
     if ws == 1:
         return v
@@ -290,7 +296,7 @@ def run_ours(args, ws, rank, local):
         del h64, ref
 
     n_ang = len(thetas)
-    value = ws * n_ang * args.steps / (ms_max / 1e3)
+    value = whole_job_rate(ws, n_ang, args.steps, ms_max)
     kern = {k: v for k, v in prof.items() if not k.startswith("phase:")}
     phases = {k[6:]: round(v["ms"] / args.steps, 2) for k, v in prof.items() if k.startswith("phase:")}
     top = max(kern.items(), key=lambda kv: kv[1]["ms"])
@@ -328,7 +334,7 @@ def run_ours(args, ws, rank, local):
                    "solve_angles_per_s": round(n_ang / (phases.get("solve:projections", 0) / 1e3 +
                                                        phases.get("solve:schur", 0) / 1e3 +
                                                        phases.get("solve:bragg", 0) / 1e3 + 1e-9), 1)},
-        "e2e": {"value": round(ws * n_ang * args.steps / (e2e_ms / 1e3), 3), "unit": UNIT,
+        "e2e": {"value": round(whole_job_rate(ws, n_ang, args.steps, e2e_ms), 3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": {"bound": kbound, "kernel": tname, "achieved": round(achieved, 4), "peak": round(kpeak, 4),
