@@ -397,19 +397,30 @@ def dft_rows(xs, kappa):
     return np.exp(-1j * np.outer(kappa, xs)) / len(xs)
 
 
-def dense_solve(x, y, dx, dy, omega: float, d: float, theta: float, opts: Options) -> Solution:
+def obstacle_blocks(x, y, dx, dy, omega: float, d: float, p: int = 1):
+    """The angle-independent N x N blocks: A and the neighbour images A_j, 0 < |j| <= P.
+    Passing them to dense_solve for several angles of one obstacle saves refilling them."""
+    bd = boundary(x, y, dx, dy)
+    imgs = {j: matrix_a_image(bd, omega, d, j) for j in range(-p, p + 1) if j != 0}
+    return matrix_a(bd, omega), imgs
+
+
+def dense_solve(x, y, dx, dy, omega: float, d: float, theta: float, opts: Options,
+                blocks=None) -> Solution:
     """Fill and solve Eq. (block2) (plus Wood's rows) densely, then extract Bragg
-    amplitudes and the flux error.  This is the oracle's answer for one angle."""
+    amplitudes and the flux error.  This is the oracle's answer for one angle.
+    `blocks` = obstacle_blocks(...) of the same obstacle, omega, d and P, or None."""
     bd = boundary(x, y, dx, dy)
     alpha = np.exp(1j * omega * d * math.cos(theta))
     ct = contour(opts.m, opts.h, opts.c, opts.w, opts.t0)
     y0 = opts.y0 if opts.y0 is not None else default_y0(bd, d)
     p = opts.p
 
-    a = matrix_a(bd, omega)
+    a0, imgs = blocks if blocks is not None else obstacle_blocks(x, y, dx, dy, omega, d, p)
+    a = a0.copy()
     for j in range(-p, p + 1):
         if j != 0:
-            a = a + (alpha ** j) * matrix_a_image(bd, omega, d, j)
+            a += (alpha ** j) * imgs[j]
     bl, br = matrix_b_parts(bd, ct, omega, d)
     b = bl + alpha * br
     cl, cr = matrix_c_parts(bd, ct, omega, d, p)

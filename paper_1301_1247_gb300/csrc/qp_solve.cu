@@ -19,6 +19,7 @@
 #include <complex>
 #include <exception>
 #include <map>
+#include <mutex>
 #include <thread>
 #include <type_traits>
 
@@ -1296,15 +1297,28 @@ __global__ void __launch_bounds__(32) k_schur_refine(const GroupJob* groups, con
 static void schur_solve(const Dims& D, const std::vector<GroupJob>& gjobs, const GroupJob* dg, cplx* Sp, cplx* Rp,
                         int* ill, cudaStream_t s) {
   const int ng = (int)gjobs.size();
-  // SM count and residency (thread-safe one-time initialization: solves may run concurrently)
-  static const std::pair<int, int> occ = [] {
-    int dev = 0, sm = 0, per = 0;
+  const bool df = gemm_double_float();
+  // SM count and residency of the variant this call launches, per device (looked up once
+  // per device and variant under a lock: solves may run concurrently)
+  int sms = 0, per_sm = 0;
+  {
+    static std::mutex mu;
+    static std::map<std::pair<int, bool>, std::pair<int, int>> occ;
+    int dev = 0;
     HBS_CUDA(cudaGetDevice(&dev));
-    HBS_CUDA(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
-    HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_schur_coop<256, false>, 256, 0));
-    return std::make_pair(sm, per);
-  }();
-  const int sms = occ.first, per_sm = occ.second;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = occ.find({dev, df});
+    if (it == occ.end()) {
+      int sm = 0, per = 0;
+      HBS_CUDA(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
+      if (df) HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_schur_coop<256, true>, 256, 0));
+      else HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_schur_coop<256, false>, 256, 0));
+      it = occ.emplace(std::make_pair(dev, df), std::make_pair(sm, per)).first;
+    }
+    sms = it->second.first;
+    per_sm = it->second.second;
+  }
+  // every CTA of the cooperative launch must be co-resident: ng * CL <= sms * per_sm
   const int CL = std::min(4, (sms * std::min(per_sm, 2)) / std::max(ng, 1));
   if (CL < 2) {
     k_schur_solve<256><<<ng, 256, 0, s>>>(D, dg, Sp, Rp, ill);
@@ -1317,7 +1331,6 @@ static void schur_solve(const Dims& D, const std::vector<GroupJob>& gjobs, const
     send = std::max<int64_t>(send, G.s_off + (int64_t)G.nsys * G.nsys);
     rend = std::max<int64_t>(rend, G.r_off + (int64_t)G.nsys * G.q);
   }
-  const bool df = gemm_double_float();
   const int npan = (nmax + 15) / 16;
   DevBuf<GridSync> gs(1);
   DevBuf<int> piv((size_t)ng * std::max(nmax, 1));
@@ -1973,12 +1986,14 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
       const double kap_i = omega * std::cos(th0);
       // poles +-k_n of the integrand: choose the contour that stays farther from all of
       // them (distance in the trapezoid variable t), since the trapezoid rule loses
-      // accuracy like exp(-2 pi dist / h) as a pole approaches the contour.
+      // accuracy like exp(-2 pi dist / h) as a pole approaches the contour.  Distances
+      // beyond 3 count as 3 (both contours are then exact to rounding); on a tie the
+      // standard contour is kept.
       std::vector<std::pair<int, zc>> modes;
       const int nlo = (int)std::floor((-omega - kap_i) * d / (2 * M_PI)) - 4;
       const int nhi = (int)std::ceil((omega - kap_i) * d / (2 * M_PI)) + 4;
       const double t1 = nc > 1 ? h.contours[1].t0 : 0.0;
-      double dist[2] = {1e300, 1e300};
+      double dist[2] = {3.0, 3.0};
       for (int n = nlo; n <= nhi; ++n) {
         zc kn = kn_of(omega, kap_i + 2 * M_PI * n / d);
         modes.push_back({n, kn});

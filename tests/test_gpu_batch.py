@@ -9,14 +9,9 @@ import pytest
 from oracle import qp_dense as qd
 from paper_1301_1247_gb300 import inputs
 
-from gpu_util import relerr, require_lib
+from gpu_util import assert_library_readings, oracle_options_checked, relerr, require_lib
 
 pytestmark = pytest.mark.gpu
-
-
-def _oracle_opts(info):
-    return dict(m=info["m"], h=info["contour_h"], c=info["contour_c"], w=info["contour_w"],
-                n_samples=info["n_bragg_samples"], y0=info["y0"])
 
 
 def test_batch_build_matches_individual_builds():
@@ -40,11 +35,11 @@ def test_batch_build_matches_individual_builds():
             assert relerr(np.concatenate([c1, d1]), np.concatenate([c2, d2])) < 1e-11, (i, a)
     # the N = 400 star against the dense oracle
     x, y, dx, dy = geoms[0]
-    info = batch[0].info()
+    assert_library_readings(batch[0].info(), x, y, omegas[0])
     res = batch[0].solve(th[:2])
     for a in range(2):
-        _, t0 = res.angle_info(a)
-        sol = qd.dense_solve(x, y, dx, dy, omegas[0], 1.0, th[a], qd.Options(**_oracle_opts(info), t0=t0))
+        opts = oracle_options_checked(res, a, x, y, omegas[0], th[a])
+        sol = qd.dense_solve(x, y, dx, dy, omegas[0], 1.0, th[a], opts)
         _, c, d, _ = res.bragg(a)
         assert relerr(np.concatenate([c, d]), qd.bragg_vector(sol)) < 1e-10
 

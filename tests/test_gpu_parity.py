@@ -7,7 +7,7 @@ import pytest
 from oracle import interp, qp_dense as qd
 from paper_1301_1247_gb300 import inputs
 
-from gpu_util import dev, relerr, require_lib
+from gpu_util import assert_library_readings, dev, oracle_options_checked, relerr, require_lib
 
 pytestmark = pytest.mark.gpu
 
@@ -101,23 +101,18 @@ def test_apply_inverse_matches_dense_inverse(case):
     assert relerr(got, ref) < 1e-10
 
 
-def _oracle_opts(info):
-    return dict(m=info["m"], h=info["contour_h"], c=info["contour_c"], w=info["contour_w"],
-                n_samples=info["n_bragg_samples"], y0=info["y0"])
-
-
 def test_solve_matches_oracle_star():
     """Bragg amplitudes of the full block solve (Secs. 2-4) vs the dense oracle, several angles."""
     hbs = require_lib()
     x, y, dx, dy = inputs.star(0.3, 0.3, 5).sample(400)
     omega = 10.0
     h = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12)
-    info = h.info()
+    assert_library_readings(h.info(), x, y, omega)
     thetas = np.array([-math.pi / 5, -0.4, -1.0, -2.5, -math.pi / 2])
     res = h.solve(thetas)
     for i, th in enumerate(thetas):
-        nw, t0 = res.angle_info(i)
-        sol = qd.dense_solve(x, y, dx, dy, omega, 1.0, th, qd.Options(**_oracle_opts(info), t0=t0))
+        nw, _ = res.angle_info(i)
+        sol = qd.dense_solve(x, y, dx, dy, omega, 1.0, th, oracle_options_checked(res, i, x, y, omega, th))
         orders, c, d, fe = res.bragg(i)
         assert list(orders) == list(sol.orders)
         assert nw == len(sol.wood_modes)
@@ -132,12 +127,13 @@ def test_woods_anomaly_matches_oracle():
     x, y, dx, dy = inputs.star(0.3, 0.3, 5).sample(400)
     omega = 10.0
     h = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12)
-    info = h.info()
+    assert_library_readings(h.info(), x, y, omega)
     th = -math.acos(1.0 - 2.0 * math.pi / omega)
     res = h.solve([th])
     nw, t0 = res.angle_info(0)
     assert nw == 1 and t0 > 0
-    sol = qd.dense_solve(x, y, dx, dy, omega, 1.0, th, qd.Options(**_oracle_opts(info), t0=t0))
+    sol = qd.dense_solve(x, y, dx, dy, omega, 1.0, th, oracle_options_checked(res, 0, x, y, omega, th))
+    assert len(sol.wood_modes) == 1
     orders, c, d, fe = res.bragg(0)
     assert relerr(np.concatenate([c, d]), qd.bragg_vector(sol)) < 1e-10
     assert fe < 1e-5
@@ -170,12 +166,11 @@ def test_double_float_products_match_oracle_and_fp64(prec):
     x, y, dx, dy = inputs.star(0.3, 0.3, 5).sample(400)
     omega = 10.0
     h = hbs.Handle(x, y, dx, dy, 1.0, omega, 1e-12, hbs.default_options(precision=prec))
-    info = h.info()
+    assert_library_readings(h.info(), x, y, omega)
     thetas = np.array([-math.pi / 5, -1.0, -2.5])
     res = h.solve(thetas)
     for i, th in enumerate(thetas):
-        nw, t0 = res.angle_info(i)
-        sol = qd.dense_solve(x, y, dx, dy, omega, 1.0, th, qd.Options(**_oracle_opts(info), t0=t0))
+        sol = qd.dense_solve(x, y, dx, dy, omega, 1.0, th, oracle_options_checked(res, i, x, y, omega, th))
         _, c, d, _ = res.bragg(i)
         assert relerr(np.concatenate([c, d]), qd.bragg_vector(sol)) < 1e-10
     obs = inputs.wiggly(0, 0.35, 20, 0.03)
