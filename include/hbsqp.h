@@ -270,6 +270,19 @@ hbs_status hbs_row_id(void* mt, int64_t m, int64_t n, double tol, int* rank, int
                       void* stream);
 
 /*
+ * Batched in-place inverse of `count` complex128 blocks of size n x n (column-major,
+ * back to back in device memory `a`), the per-node inversion step of Sec. 4 (D_tau^{-1}
+ * in Eqs. def_muhD..def_muG): Gauss-Jordan elimination with partial pivoting, all
+ * blocks in one launch (a persistent multi-CTA kernel for up to 128 blocks, one CTA per
+ * block otherwise).  precision as for hbs_zgemm: _DOUBLE_FLOAT and _TENSOR run the
+ * eliminations in double-float arithmetic.  1 <= n <= 4096, 1 <= count <= 2^20, else
+ * HBS_ERR_INVALID_ARG.  Returns HBS_WARN_ILLCOND when a pivot is exactly zero (the
+ * blocks' contents are then undefined) and HBS_ERR_TIMEOUT if a bounded barrier wait
+ * of the persistent kernel gave up.  Synchronizes the stream.
+ */
+hbs_status hbs_batched_inverse(void* a, int64_t n, int64_t count, int precision, void* stream);
+
+/*
  * Complex GEMM on device arrays (complex128, column-major):
  *   C = alpha op(A) B + beta C,
  * op(A) = A (m x k, lda >= m) or, with trans_a = 1, A^T (A stored k x m, lda >= k);
@@ -318,6 +331,8 @@ int64_t hbs_launch_count(void);
  *    HBS_ERR_INVALID_ARG.
  *  - The first call on a device looks up the array's device address (with that
  *    device current); make that first call before any CUDA graph capture.
+ *  - Every call waits for `stream` before it returns: it steps the pivot search
+ *    from the host and reads the rank back.
  *  - All calls share the one array and it keeps the last call's contents: two
  *    calls that overlap on the GPU (different streams, or different host threads)
  *    race and give wrong results.  Serialise them.
@@ -325,6 +340,35 @@ int64_t hbs_launch_count(void);
 #define HBS_ROW_ID_STATIC_MAX_N 262144
 hbs_status hbs_row_id_static(void* mt, int64_t m, int64_t n, double tol, int* rank, int* perm,
                              void* t, void* stream);
+
+/*
+ * Error-path testing (the paper has no counterpart).  Nothing here makes a GPU fault,
+ * trap or hang.
+ *
+ * hbs_fault_inject(kind, value) arms a host-side fault for the library's later calls
+ * (process-wide, all threads):
+ *  - HBS_INJECT_CLEAR: disarm everything (value ignored);
+ *  - HBS_INJECT_ALLOC_FAILURE: the device allocation `value` allocations from now
+ *    (0 = the next one) fails before cudaMallocAsync is called; the call that made
+ *    it returns HBS_ERR_OOM and frees what it had allocated.  One failure per arming;
+ *  - HBS_INJECT_RANK_CAP: interpolative decompositions of the persistent QR (tree
+ *    levels of at most 128 nodes, the neighbour and periodizer IDs, hbs_row_id with
+ *    n > 4096) may reach rank `value` at most (0 = no cap); one that needs more
+ *    returns HBS_ERR_RANK, as an overflow of the supported maximum would.
+ * Returns HBS_ERR_INVALID_ARG for an unknown kind or a negative value.
+ *
+ * hbs_barrier_selftest runs the library's bounded grid barrier (the one the
+ * persistent QR, Gauss-Jordan and Schur kernels use) in a cooperative launch of
+ * `ctas` CTAs (1..64) passing three barriers; CTA `absent_cta` (if in [0, ctas))
+ * leaves before the second, so the others give up after `limit_s` seconds (0 < limit_s
+ * <= 10) and return.  *passed (host int) = CTAs that passed all three.  Returns
+ * HBS_ERR_TIMEOUT when a wait gave up, HBS_OK otherwise.  Synchronizes the stream.
+ */
+#define HBS_INJECT_CLEAR 0
+#define HBS_INJECT_ALLOC_FAILURE 1
+#define HBS_INJECT_RANK_CAP 2
+hbs_status hbs_fault_inject(int kind, int64_t value);
+hbs_status hbs_barrier_selftest(int ctas, int absent_cta, double limit_s, int* passed, void* stream);
 
 void hbs_free(hbs_handle* h);
 void hbs_result_free(hbs_result* r);

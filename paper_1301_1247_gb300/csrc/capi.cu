@@ -7,7 +7,6 @@
 
 #include "dense_kernels.cuh"
 #include "profile.hpp"
-#include "profile.hpp"
 #include "qp_kernels.cuh"
 
 namespace hbs {
@@ -420,6 +419,23 @@ hbs_status hbs_row_id(void* mt, int64_t m, int64_t n, double tol, int* rank, int
       *rank = big_row_id(static_cast<cplx*>(mt), m, n, tol, perm, static_cast<cplx*>(t),
                          (int)std::min<int64_t>(m, n), s);
     }
+    HBS_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+hbs_status hbs_batched_inverse(void* a, int64_t n, int64_t count, int precision, void* stream) {
+  if (!a || n < 1 || n > 4096 || count < 1 || count > (1 << 20) || precision < HBS_PRECISION_FP64 ||
+      precision > HBS_PRECISION_TENSOR) {
+    set_last_error("bad arguments to hbs_batched_inverse");
+    return HBS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScope scope(s);
+  GemmModeScope mode(precision);
+  return guarded([&] {
+    std::vector<InvJob> jobs((size_t)count);
+    for (int64_t i = 0; i < count; ++i) jobs[i] = {static_cast<cplx*>(a) + i * n * n, nullptr, (int)n, (int)i};
+    batched_inverse(jobs, s, "hbs_batched_inverse");
     HBS_CUDA(cudaStreamSynchronize(s));
   });
 }

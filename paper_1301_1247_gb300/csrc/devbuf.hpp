@@ -32,6 +32,11 @@ inline void cuda_check(cudaError_t e, const char* what) {
 
 cudaStream_t& current_stream();
 
+// Fault injection for tests of the error paths (hbs_fault_inject): true when the caller's
+// device allocation is the one chosen to fail; the largest rank an ID may reach (0 = none).
+bool injected_alloc_failure();
+int injected_rank_cap();
+
 // Owning device allocation (stream-ordered cudaMallocAsync / cudaFreeAsync on the
 // library's current stream).
 template <typename T>
@@ -51,6 +56,8 @@ class DevBuf {
     release();
     if (n == 0) return;
     void* p = nullptr;
+    if (injected_alloc_failure())
+      throw Error(HBS_ERR_OOM, "device allocation failed (injected by hbs_fault_inject)");
     HBS_CUDA(cudaMallocAsync(&p, n * sizeof(T), current_stream()));
     p_ = static_cast<T*>(p);
     n_ = n;

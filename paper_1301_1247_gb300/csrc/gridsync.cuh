@@ -39,8 +39,9 @@ __device__ __forceinline__ uint64_t global_ns() {
 // batch; *gs zeroed before the launch).  The arrival counter only grows: the b-th barrier
 // is complete once it reaches (b + 1) count, and each CTA learns b from the value its own
 // arrival returns, so nothing is reset between barriers.  Returns 0, or -1 if a wait gave
-// up.  Every one of the `count` CTAs must call it the same number of times.
-__device__ __forceinline__ int group_sync(GridSync* gs, unsigned int count) {
+// up (after limit_ns, or at once if another CTA already gave up).  Every one of the
+// `count` CTAs must call it the same number of times.
+__device__ __forceinline__ int group_sync(GridSync* gs, unsigned int count, uint64_t limit_ns = kGridWaitNs) {
   __shared__ int s_res;
   __syncthreads();  // the CTA's writes happen before thread 0's release below
   if (threadIdx.x == 0) {
@@ -54,7 +55,7 @@ __device__ __forceinline__ int group_sync(GridSync* gs, unsigned int count) {
       while ((int)(ld_acquire_u32(&gs->arrive) - target) < 0) {
         if ((++it & 15u) == 0) {
           if (*(volatile int*)&gs->timed_out) { ok = -1; break; }
-          if (global_ns() - t0 > kGridWaitNs) {
+          if (global_ns() - t0 > limit_ns) {
             atomicExch(&gs->timed_out, 1);
             ok = -1;
             break;

@@ -946,7 +946,11 @@ static int pqr_grid(size_t smem) {
   return sms * std::min(per_sm, 2);
 }
 
-void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrOut& out, bool equal_steps) {
+void pqr_run(const std::vector<PqrSpec>& specs_in, double tol, cudaStream_t s, PqrOut& out, bool equal_steps) {
+  // a rank cap set by hbs_fault_inject (tests of the HBS_ERR_RANK path) lowers every kcap
+  std::vector<PqrSpec> specs(specs_in);
+  if (const int cap = injected_rank_cap(); cap > 0)
+    for (auto& sp : specs) sp.kcap = std::min(sp.kcap, cap);
   const int nj = (int)specs.size();
   out.rank.assign(nj, 0);
   out.koff.assign(nj + 1, 0);
@@ -1066,13 +1070,16 @@ void pqr_run(const std::vector<PqrSpec>& specs, double tol, cudaStream_t s, PqrO
     }
   }
   HBS_LAUNCH_CHECK("k_pqr_finish");
-  // account the factorization's flops (16 m n per step on the active columns)
-  double fl = 0.0;
+  // algorithmic work of an interpolative decomposition of an m x n block of rank k: 8 m n k
+  // flops (the Householder factorization executes about twice that), and the block read
+  // once plus the interpolation matrix and the order written once
+  double fl = 0.0, by = 0.0;
   for (int j = 0; j < nj; ++j) {
     const double m = (double)specs[j].m, n = (double)specs[j].n, k = out.rank[j];
-    fl += 16.0 * k * (m * n - 0.5 * (m + n) * k + k * k / 3.0);
+    fl += 8.0 * m * n * k;
+    by += 16.0 * m * n + 16.0 * k * (n - k) + 4.0 * n;
   }
-  prof::add_work("k_pqr", fl, 0.0);
+  prof::add_work("k_pqr", fl, by);
 }
 
 }  // namespace hbs

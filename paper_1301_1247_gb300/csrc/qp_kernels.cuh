@@ -58,6 +58,10 @@ void pqr_solve_r11(const cplx* A, int64_t m, const PqrOut& qr, int job, int k, c
 // pgj.cu: in-place inverses of several large matrices (pointer, n) in one persistent
 // launch; throws HBS_WARN_ILLCOND on a singular block.
 void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, const char* what);
+struct InvJob;
+// In-place inverses of a batch of blocks (persistent Gauss-Jordan for few or large blocks,
+// one CTA per block otherwise); throws HBS_WARN_ILLCOND when a pivot is exactly zero.
+void batched_inverse(std::vector<InvJob>& jobs, cudaStream_t s, const char* what);
 // X(:, c) = R^{-1} B(:, c) for upper-triangular R (k x k, row-major); X may alias B.
 __global__ void k_tsolve_cols(const cplx* R, int k, const cplx* B, int64_t ldb, int64_t ncols, cplx* X, int64_t ldx);
 // Columns of conj(Q1), Q1 = the first k columns of the factorization's Q (m x k, ld m).

@@ -29,11 +29,11 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "RANK", 5: "W
 # Every entry point declared in include/hbsqp.h.
 EXPORTED = ("hbs_default_options", "hbs_build", "hbs_build_batch", "hbs_solve", "hbs_solve_plain", "hbs_bragg_amplitudes",
             "hbs_result_angle_info", "hbs_info", "hbs_save", "hbs_load", "hbs_apply_inverse",
-            "hbs_kernel_block", "hbs_row_id", "hbs_zgemm",
+            "hbs_kernel_block", "hbs_row_id", "hbs_batched_inverse", "hbs_zgemm",
             "hbs_row_id_static",
             "hbs_profile_enable", "hbs_profile_reset", "hbs_profile_get", "hbs_launch_count",
             "hbs_server_create", "hbs_server_add", "hbs_server_remove", "hbs_server_submit", "hbs_server_wait",
-            "hbs_server_stats", "hbs_server_free",
+            "hbs_server_stats", "hbs_server_free", "hbs_fault_inject", "hbs_barrier_selftest",
             "hbs_free", "hbs_result_free", "hbs_last_error")
 
 
@@ -129,6 +129,12 @@ def lib():
     L.hbs_zgemm.argtypes = [i64, i64, i64, ctypes.POINTER(dbl), vp, i64, ci, vp, i64, ctypes.POINTER(dbl), vp, i64,
                             ci, vp]
     L.hbs_zgemm.restype = ci
+    L.hbs_batched_inverse.argtypes = [vp, i64, i64, ci, vp]
+    L.hbs_batched_inverse.restype = ci
+    L.hbs_fault_inject.argtypes = [ci, i64]
+    L.hbs_fault_inject.restype = ci
+    L.hbs_barrier_selftest.argtypes = [ci, ci, dbl, ctypes.POINTER(ci), vp]
+    L.hbs_barrier_selftest.restype = ci
     L.hbs_profile_enable.argtypes = [ci]
     L.hbs_profile_enable.restype = None
     L.hbs_profile_reset.argtypes = []
@@ -387,6 +393,30 @@ def zgemm(m, n, k, alpha, a, lda, trans_a, b, ldb, beta, c, ldc, precision=PRECI
     be = (ctypes.c_double * 2)(complex(beta).real, complex(beta).imag)
     _check(lib().hbs_zgemm(int(m), int(n), int(k), al, _ptr(a), int(lda), int(trans_a), _ptr(b), int(ldb), be, _ptr(c),
                            int(ldc), int(precision), _stream(stream)), "hbs_zgemm")
+
+
+def batched_inverse(a, n, count, precision=0, stream=None):
+    """hbs_batched_inverse: `count` device n x n complex128 blocks (column-major, back to
+    back) inverted in place.  Returns the status (HBS_OK or HBS_WARN_ILLCOND); raises on errors."""
+    st = lib().hbs_batched_inverse(_ptr(a), int(n), int(count), int(precision), _stream(stream))
+    _check(st, "hbs_batched_inverse", allow_warn=True)
+    return st
+
+
+INJECT_CLEAR, INJECT_ALLOC_FAILURE, INJECT_RANK_CAP = 0, 1, 2
+
+
+def fault_inject(kind, value=0):
+    """hbs_fault_inject: arm a host-side fault (allocation failure, rank cap) or clear them."""
+    _check(lib().hbs_fault_inject(int(kind), int(value)), "hbs_fault_inject")
+
+
+def barrier_selftest(ctas, absent_cta, limit_s, stream=None):
+    """hbs_barrier_selftest: (status, CTAs that passed all barriers)."""
+    passed = ctypes.c_int()
+    st = lib().hbs_barrier_selftest(int(ctas), int(absent_cta), float(limit_s), ctypes.byref(passed),
+                                    _stream(stream))
+    return st, passed.value
 
 
 ROW_ID_STATIC_MAX_N = 262144

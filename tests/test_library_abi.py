@@ -62,6 +62,25 @@ def test_argument_errors_need_no_gpu():
     assert L.hbs_server_submit(None, 1, -0.5, ctypes.byref(rid)) == 1
     outs = (ctypes.c_void_p * 2)()
     assert L.hbs_build_batch(None, None, 2, 1e-12, None, None, outs) == 1
+    fake = ctypes.c_void_p(256)
+    assert L.hbs_batched_inverse(None, 8, 1, 0, None) == 1
+    assert L.hbs_batched_inverse(fake, 5000, 1, 0, None) == 1
+    assert L.hbs_batched_inverse(fake, 8, 1, 7, None) == 1
+    passed = ctypes.c_int()
+    assert L.hbs_barrier_selftest(0, 0, 0.1, ctypes.byref(passed), None) == 1
+    assert L.hbs_barrier_selftest(4, 0, 0.0, ctypes.byref(passed), None) == 1
+
+
+def test_fault_injection_arms_and_clears_without_gpu():
+    """The host-side fault switches accept their kinds, reject bad ones, and clear."""
+    _ensure_built()
+    from paper_1301_1247_gb300 import hbs
+    L = hbs.lib()
+    assert L.hbs_fault_inject(hbs.INJECT_RANK_CAP, 5) == 0
+    assert L.hbs_fault_inject(hbs.INJECT_ALLOC_FAILURE, 3) == 0
+    assert L.hbs_fault_inject(hbs.INJECT_ALLOC_FAILURE, -2) == hbs.HBS_ERR_INVALID_ARG
+    assert L.hbs_fault_inject(99, 0) == hbs.HBS_ERR_INVALID_ARG
+    assert L.hbs_fault_inject(hbs.INJECT_CLEAR, 0) == 0
 
 
 def test_load_rejects_missing_and_foreign_files_without_gpu(tmp_path):
