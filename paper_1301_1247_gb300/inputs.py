@@ -155,3 +155,39 @@ def workload_batch(seed: int = 0, count: int = 256, n_lo: int = 400, n_hi: int =
         th = rng.uniform(-math.pi / 2 + 0.02, -0.1, n_angles)
         out.append(dict(obstacle=obs, N=n, omega=omega, d=1.0, thetas=th))
     return out
+
+
+def workload_serving(seed: int = 0, count: int = 32, n_lo: int = 2000, n_hi: int = 100000, w_lo: float = 10.0,
+                     w_hi: float = 60.0):
+    """Resident geometries for the request loop: alternating wiggly and star obstacles with N
+    log-uniform in [n_lo, n_hi] (rounded to a multiple of 8) and omega uniform in [w_lo, w_hi].
+    Returns a list of dicts (obstacle, N, omega, d)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi))) / 8.0)) * 8
+        omega = float(rng.uniform(w_lo, w_hi))
+        if i % 2 == 0:
+            obs = wiggly(int(rng.integers(0, 1 << 30)), 0.3, 40, 0.04)
+        else:
+            obs = star(float(rng.uniform(0.2, 0.3)), float(rng.uniform(0.1, 0.3)), int(rng.integers(3, 7)))
+        out.append(dict(obstacle=obs, N=n, omega=omega, d=1.0))
+    return out
+
+
+def request_stream(seed: int, count: int, rate_per_s: float, omegas, d: float = 1.0, wood_frac: float = 0.1):
+    """A Poisson stream of single-angle requests over the geometries with wavenumbers `omegas`:
+    arrival times (s, exponential gaps of mean 1/rate), geometry index (uniform), and angle:
+    uniform in (-pi + 0.05, -0.05), except a fraction wood_frac placed exactly at a
+    Rayleigh-Wood anomaly of the geometry, cos(theta) = 1 - 2 pi n / (omega d).  Returns
+    (times, geometry indices, angles) as numpy arrays."""
+    rng = np.random.default_rng(seed)
+    times = np.cumsum(rng.exponential(1.0 / rate_per_s, size=count))
+    gi = rng.integers(0, len(omegas), size=count)
+    th = rng.uniform(-math.pi + 0.05, -0.05, size=count)
+    for i in np.flatnonzero(rng.random(count) < wood_frac):
+        om = float(omegas[gi[i]])
+        orders = [n for n in range(1, 64) if 1.0 - 2.0 * math.pi * n / (om * d) > -1.0]
+        n = int(rng.choice(orders))
+        th[i] = -math.acos(1.0 - 2.0 * math.pi * n / (om * d))
+    return times, gi, th
