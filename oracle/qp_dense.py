@@ -397,11 +397,18 @@ def dft_rows(xs, kappa):
     return np.exp(-1j * np.outer(kappa, xs)) / len(xs)
 
 
-def obstacle_blocks(x, y, dx, dy, omega: float, d: float, p: int = 1):
+def obstacle_blocks(x, y, dx, dy, omega: float, d: float, p: int = 1, quadrature: str = "kr6"):
     """The angle-independent N x N blocks: A and the neighbour images A_j, 0 < |j| <= P.
-    Passing them to dense_solve for several angles of one obstacle saves refilling them."""
+    Passing them to dense_solve for several angles of one obstacle saves refilling them.
+    quadrature "kr6" (Sec. 2.3, the paper's) or "kress" (oracle/kress.py, a second
+    discretization of the same operator, used to pin the first) for the log-singular A."""
     bd = boundary(x, y, dx, dy)
     imgs = {j: matrix_a_image(bd, omega, d, j) for j in range(-p, p + 1) if j != 0}
+    if quadrature == "kress":
+        from . import kress
+        return kress.matrix_a(x, y, dx, dy, omega), imgs
+    if quadrature != "kr6":
+        raise ValueError(quadrature)
     return matrix_a(bd, omega), imgs
 
 

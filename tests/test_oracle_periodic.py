@@ -145,3 +145,48 @@ def test_contour_choice_keeps_poles_away():
     f_std, f_shift = flux(0.4, 0.0), flux(0.4, T)
     assert f_shift > 1e-4 and f_std < 1e-6
     assert flux(0.2, 0.0) < 0.2 * f_std
+
+
+def test_q_by_brute_force_from_the_wall_fields():
+    """Q (Eq. Q, reading R3) against the wall potentials' own fields: a unit density at one
+    contour node k, put into (urep) on both walls (R carrying alpha times L's density), gives a
+    wall discrepancy u_L - u_R / alpha (and its x-derivative) that is a single Fourier mode
+    e^{iky} times the contour weight; its coefficient must be Q's entry."""
+    ct = qd.contour(40, 0.4, 2.0, 2.0, 0.0)
+    m = ct.m
+    y = np.array([0.3, -0.2, 1.1])
+    for th in (-0.7, -2.2):
+        alpha = np.exp(1j * OMEGA * D * math.cos(th))
+        q = qd.matrix_q(ct, OMEGA, D, alpha)
+        for row, der in ((0, None), (m, "x")):
+            sl, sr, dl, dr = qd.wall_field_rows(np.full(3, -0.5 * D), y, ct, OMEGA, D, der)
+            sl2, sr2, dl2, dr2 = qd.wall_field_rows(np.full(3, 0.5 * D), y, ct, OMEGA, D, der)
+            f_mu = (sl + alpha * sr) - (sl2 + alpha * sr2) / alpha
+            f_nu = (dl + alpha * dr) - (dl2 + alpha * dr2) / alpha
+            for j in (0, 7, 19, 33):
+                unit = ct.wk[j] * np.exp(1j * ct.k[j] * y)
+                assert np.allclose(f_mu[:, j] / unit, q[row + j, j], rtol=1e-13, atol=0)
+                assert np.allclose(f_nu[:, j] / unit, q[row + j, m + j], rtol=1e-13, atol=0)
+            # no coupling between different contour nodes
+            assert np.count_nonzero(q[row:row + m, :m] - np.diag(np.diag(q[row:row + m, :m]))) == 0
+
+
+def test_c_tilde_rows_invert_to_the_real_space_kernel():
+    """C~'s rows (Sec. 2.4) are the Fourier transforms, along the walls, of the image sources'
+    combined-field kernel and its x-derivative.  Integrating them back along the Sommerfeld
+    contour, sum_k w_k f^(k) e^{iky}, must give the kernel itself, evaluated directly with
+    SciPy's Hankel functions at points of the wall (both walls, both image sides)."""
+    ct = qd.contour(1200, 0.2, 2.0, 2.0, 0.0)
+    m = ct.m
+    ys = np.array([-0.7, 0.0, 0.4, 1.3])
+    for sx, x0 in ((0.35 + D, -0.5 * D), (-0.3 - D, 0.5 * D), (0.2 + D, -0.5 * D)):
+        sy, snx, sny = 0.12, 0.6, -0.8
+        rows = qd.wall_fourier_rows(np.array([sx]), np.array([sy]), np.array([snx]), np.array([sny]),
+                                    np.ones(1), ct, OMEGA, x0)
+        f, fn = rows[:m, 0], rows[m:, 0]
+        rec = np.array([np.sum(ct.wk * f * np.exp(1j * ct.k * yy)) for yy in ys])
+        recn = np.array([np.sum(ct.wk * fn * np.exp(1j * ct.k * yy)) for yy in ys])
+        g = qd.combined(np.full(4, x0), ys, sx, sy, snx, sny, OMEGA)
+        gx, _ = qd.combined_grad(np.full(4, x0), ys, sx, sy, snx, sny, OMEGA)
+        assert np.max(np.abs(rec - g)) < 1e-13 * np.max(np.abs(g))
+        assert np.max(np.abs(recn - gx)) < 1e-13 * np.max(np.abs(gx))

@@ -108,3 +108,40 @@ def test_a_rows_are_rows_of_a():
     bd = qd.boundary(x, y, dx, dy)
     rows = [0, 1, 7, 100, 199]
     assert np.allclose(qd.a_rows(bd, 10.0, rows), qd.matrix_a(bd, 10.0)[rows], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("m", [0, 3, 11])
+def test_kress_circle_eigenvalues_spectral(m):
+    """The oracle's second quadrature (Kress's, oracle/kress.py) has the same circle
+    eigenvalues to rounding at modest N: it is spectrally accurate for analytic curves."""
+    from oracle import kress
+    a, omega, n = 0.4, 10.0, 96
+    z = omega * a
+    lam = (1j * np.pi * z / 2) * sp.hankel1(m, z) * (sp.jvp(m, z) - 1j * sp.jv(m, z))
+    t = 2 * np.pi * np.arange(n) / n
+    mat = kress.matrix_a(a * np.cos(t), a * np.sin(t), -a * np.sin(t), a * np.cos(t), omega)
+    v = np.exp(1j * m * t)
+    assert np.max(np.abs(mat @ v - lam * v)) < 1e-12
+
+
+def test_kress_and_kr6_give_the_same_bragg_amplitudes():
+    """Two discretizations of one continuum problem (Sec. 2.3's KR6 and Kress's spectral rule)
+    converge to the same Bragg amplitudes: Kress at N = 256 against KR6 at N = 1024 and 2048
+    (same contour, samples and y0); KR6's gap shrinks at its sixth order."""
+    import math
+    from oracle import readings as rd
+    obs = inputs.star(0.3, 0.3, 5)
+    omega, th = 10.0, -math.pi / 5
+
+    def amps(quad, n):
+        x, y, dx, dy = obs.sample(n)
+        o = rd.options(x, y, omega, 1.0, th)
+        o.y0 = 0.7  # one sampling line for all N (y0 = max|y| + d/4 moves with the samples)
+        b = qd.obstacle_blocks(x, y, dx, dy, omega, 1.0, quadrature=quad)
+        return qd.bragg_vector(qd.dense_solve(x, y, dx, dy, omega, 1.0, th, o, b))
+
+    ref = amps("kress", 256)
+    e1 = np.linalg.norm(amps("kr6", 1024) - ref) / np.linalg.norm(ref)
+    e2 = np.linalg.norm(amps("kr6", 2048) - ref) / np.linalg.norm(ref)
+    assert e2 < 1e-10
+    assert e1 / e2 > 40
