@@ -31,6 +31,64 @@ def _run(fn, mt_host, m, n, tol):
     return k, perm.cpu().numpy(), t.cpu().numpy()[: k * (n - k)]
 
 
+def _device_memory_counters():
+    """(free device bytes from cudaMemGetInfo, used bytes of the device's default stream-ordered
+    memory pool, bytes held by torch's caching allocator).  Any device allocation by the call
+    under test moves the first (cudaMalloc reserves at least 2 MiB) or the second (cudaMallocAsync)."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    used = None
+    try:
+        cu = ctypes.CDLL("libcuda.so.1")
+        devh = ctypes.c_int()
+        pool = ctypes.c_void_p()
+        val = ctypes.c_uint64()
+        if (cu.cuDeviceGet(ctypes.byref(devh), torch.cuda.current_device()) == 0
+                and cu.cuDeviceGetDefaultMemPool(ctypes.byref(pool), devh) == 0
+                and cu.cuMemPoolGetAttribute(pool, 7, ctypes.byref(val)) == 0):  # USED_MEM_CURRENT
+            used = int(val.value)
+    except OSError:
+        pass
+    return free, used, torch.cuda.memory_reserved()
+
+
+@pytest.mark.gpu
+def test_static_scratch_id_allocates_nothing():
+    """After a first call (which looks up the fixed array's address), further calls leave the
+    device's free memory, its default memory pool and torch's allocator exactly as they were."""
+    hbs = require_lib()
+    import torch
+    mt_host = _low_rank(96, 6000, 9)
+    mt = dev(np.asfortranarray(mt_host).ravel(order="F"))
+    perm = torch.zeros(6000, dtype=torch.int32, device="cuda")
+    t = torch.zeros(96 * 6000, dtype=torch.complex128, device="cuda")
+    inputs = [mt.clone() for _ in range(4)]  # Mt is overwritten: one copy per call, made up front
+    hbs.row_id_static(inputs[0], 96, 6000, 1e-12, perm, t)
+    torch.cuda.synchronize()
+    before = _device_memory_counters()
+    for a in inputs[1:]:
+        hbs.row_id_static(a, 96, 6000, 1e-12, perm, t)
+    torch.cuda.synchronize()
+    after = _device_memory_counters()
+    assert abs(after[0] - before[0]) < (1 << 20), (before, after)
+    assert after[1] == before[1], (before, after)
+
+
+@pytest.mark.gpu
+def test_static_scratch_id_matches_one_cta_id_small_n():
+    """For n <= 4096 hbs_row_id runs the one-CTA-per-matrix pivoted QR while the static entry
+    point runs the multi-CTA one: the two must still give the same rank, skeleton order and T."""
+    hbs = require_lib()
+    for m, n, seed in ((48, 1000, 11), (90, 4096, 12), (64, 300, 13)):
+        mt = _low_rank(m, n, seed)
+        k0, p0, t0 = _run(hbs.row_id, mt, m, n, 1e-12)
+        for _ in range(2):
+            k, p, t = _run(hbs.row_id_static, mt, m, n, 1e-12)
+            assert k == k0, (m, n, k, k0)
+            assert np.array_equal(p, p0), (m, n)
+            assert np.allclose(t, t0, rtol=1e-11, atol=1e-11 * np.abs(t0).max())
+
+
 @pytest.mark.gpu
 def test_static_scratch_id_matches_allocating_id_twice():
     hbs = require_lib()
