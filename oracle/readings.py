@@ -131,10 +131,11 @@ def contour_distances(omega: float, d: float, theta: float, disc: Discretization
 
 def choose_t0(omega: float, d: float, theta: float, disc: Discretization):
     """Crossing point of the contour used for the Bloch phase of `theta`, and the margin
-    |dist_shifted - dist_standard| of the decision (a near tie means both contours are fine)."""
+    |dist_shifted - dist_standard| of the decision (a near tie means both contours are fine;
+    inf when the choice cannot tie)."""
     dist = contour_distances(omega, d, theta, disc)
-    if len(dist) == 1:
-        return 0.0, math.inf
+    if len(dist) == 1 or min(dist) >= DISTANCE_CAP:
+        return 0.0, math.inf  # one contour, or both at the cap: the standard one, no tie
     t0 = disc.shift if dist[1] > dist[0] else 0.0
     return t0, abs(dist[1] - dist[0])
 
