@@ -51,16 +51,17 @@ def main(path):
     for name, make, omega, seed, wood_order in CASES:
         t_start = time.time()
         x, y, dx, dy = make().sample(N)
-        lines.append(f"case {name} {omega!r} {N} {float(np.sum(x))!r} {float(np.sum(y))!r}")
+        lines.append(f"case {name} {float(omega)!r} {N} {float(np.sum(x))!r} {float(np.sum(y))!r}")
         disc = rd.discretization(x, y, omega, D)
         blocks = qd.obstacle_blocks(x, y, dx, dy, omega, D)
         for i, th in enumerate(case_angles(omega, seed, wood_order)):
             t0, margin = rd.choose_t0(omega, D, th, disc)
             sol = qd.dense_solve(x, y, dx, dy, omega, D, th, rd.options(x, y, omega, D, th, t0), blocks)
-            lines.append(f"angle {name} {i} {th!r} {t0!r} {len(sol.wood_modes)} {sol.flux_error!r} {margin!r}")
+            lines.append(f"angle {name} {i} {float(th)!r} {float(t0)!r} {len(sol.wood_modes)} "
+                         f"{float(sol.flux_error)!r} {float(margin)!r}")
             for kind, vals in (("c", sol.c), ("d", sol.d)):
                 for n, v in zip(sol.orders, vals):
-                    lines.append(f"amp {name} {i} {kind} {int(n)} {v.real!r} {v.imag!r}")
+                    lines.append(f"amp {name} {i} {kind} {int(n)} {float(v.real)!r} {float(v.imag)!r}")
             print(f"{name} angle {i}: theta={th:.6f} t0={t0:.4f} nw={len(sol.wood_modes)} "
                   f"flux={sol.flux_error:.2e} ({time.time() - t_start:.0f} s)", flush=True)
         del blocks
