@@ -248,6 +248,18 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def tuned_shapes():
+    """The autotuner's choices (key -> [variant, ms]) from its file, if any."""
+    path = os.environ.get("HBS_TUNE_FILE")
+    out = {}
+    if path and os.path.exists(path):
+        for line in open(path):
+            f = line.split()
+            if len(f) == 3:
+                out[f[0]] = [int(f[1]), float(f[2])]
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_1301_1247_gb300 import hbs
@@ -301,6 +313,8 @@ def run_ours(args, ws, rank, local):
     l0 = hbs.launch_count()
     with ClockSampler(_gpu_id_for_smi(local)) as clk:
         ms, (h, r, amps) = timed(lambda: step(True), args.steps)
+    if info is None:
+        info = h.info()
     del h, r
     launches = hbs.launch_count() - l0
     clocks = clk.summary()
@@ -423,6 +437,7 @@ def run_ours(args, ws, rank, local):
                    "nb_id_residual": info["nb_residual"], "periodizer_id_residual": info["pid_residual"],
                    "periodizer_ranks": [info["pid_col_rank"], info["pid_row_rank"]],
                    "profiled_pass_ms_per_step": round(prof_ms / args.steps, 2),
+                   "autotuned_shapes": tuned_shapes(),
                    "phases_ms_per_step": phases, "max_flux_error": float(max(flux))},
         "e2e": {"value": round(whole_job_rate(ws, n_ang, args.steps, e2e_ms), 3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -691,7 +706,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="complicated_n100k")
     ap.add_argument("--cpu-sample-n", type=int, nargs="+", default=[400, 1000, 2000])
@@ -706,6 +722,12 @@ def main():
     ap.add_argument("--gemm", type=int, nargs=3, metavar=("M", "N", "K"),
                     help="time hbs_zgemm alone at this shape instead of the solver step")
     args = ap.parse_args()
+    if not args.no_autotune:
+        # the launch-shape autotuner times the candidate shapes during the warm-up steps
+        os.environ["HBS_AUTOTUNE"] = "1"
+        if not os.environ.get("HBS_TUNE_FILE"):
+            os.environ["HBS_TUNE_FILE"] = os.path.join(tempfile.gettempdir(),
+                                                       f"hbsqp_tune_{os.getpid()}_{os.environ.get('RANK', '0')}.txt")
     if args.gemm:
         print(json.dumps(run_gemm(args)))
         return

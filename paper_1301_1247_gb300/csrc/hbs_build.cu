@@ -31,6 +31,7 @@
 #include "profile.hpp"
 #include "handle.hpp"
 #include "qp_kernels.cuh"
+#include "tune.hpp"
 #include "zgemm.cuh"
 
 namespace hbs {
@@ -517,9 +518,8 @@ std::vector<int> batched_id(std::vector<CpqrJob>& jobs, double tol, cudaStream_t
 void batched_inverse(std::vector<InvJob>& jobs_in, cudaStream_t s, const char* what) {
   std::vector<InvJob> jobs;
   std::vector<std::pair<cplx*, int>> big;
-  // Same split as for the IDs: at most 128 blocks all go to the persistent multi-CTA
-  // Gauss-Jordan (pgj.cu); with more, one CTA per block and the large ones (if at most
-  // 128) persistent.
+  // Same split as for the IDs: at most 128 blocks all go to one multi-CTA launch; with
+  // more, one CTA per block and the large ones (if at most 128) multi-CTA.
   size_t nbig = 0;
   for (const auto& j : jobs_in) nbig += big_inverse(j.n) ? 1 : 0;
   const bool all_big = jobs_in.size() <= 128;
@@ -528,7 +528,27 @@ void batched_inverse(std::vector<InvJob>& jobs_in, cudaStream_t s, const char* w
     if (use_big && (all_big || big_inverse(j.n))) big.push_back({j.a, j.n});
     else jobs.push_back(j);
   }
-  pgj_run(big, s, what);
+  if (!big.empty()) {
+    // The multi-CTA inversion: the persistent Gauss-Jordan (pgj.cu, one grid barrier per
+    // column step; the default) or the blocked one (bgj.cu) on clusters of 1, 2, 4 or 8 CTAs
+    // per block; the autotuner measures them per shape class when it is on.
+    int nmax = 0;
+    for (const auto& m : big) nmax = std::max(nmax, m.second);
+    int n_pow = 1, c_pow = 1;
+    while (n_pow < nmax) n_pow *= 2;
+    while (c_pow < (int)big.size()) c_pow *= 2;
+    const std::string tkey = "inverse/n" + std::to_string(n_pow) + "/j" + std::to_string(c_pow) +
+                             (gemm_double_float() ? "/df" : "");
+    static const int kCs[5] = {0, 1, 2, 4, 8};
+    int var = tune::choose(tkey, 5, 0);
+    if (var > 0 && bgj_panel_width(nmax, kCs[var]) == 0) {  // does not fit: not a candidate
+      if (tune::exploring(tkey, 5)) tune::record(tkey, var, 5, 1e30f);
+      var = 0;
+    }
+    tune::Timed timed(tkey, var, 5, s);
+    if (var == 0) pgj_run(big, s, what);
+    else bgj_run(big, kCs[var], s, what);
+  }
   if (jobs.empty()) return;
   for (size_t i = 0; i < jobs.size(); ++i) jobs[i].job = (int)i;
   int64_t piv = 0;

@@ -58,6 +58,11 @@ void pqr_solve_r11(const cplx* A, int64_t m, const PqrOut& qr, int job, int k, c
 // pgj.cu: in-place inverses of several large matrices (pointer, n) in one persistent
 // launch; throws HBS_WARN_ILLCOND on a singular block.
 void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, const char* what);
+// The same by blocked Gauss-Jordan (bgj.cu): panels of columns eliminated by a cluster of
+// cs CTAs per block (1, 2, 4 or 8), the rest of each block updated by the batched GEMM.
+void bgj_run(const std::vector<std::pair<cplx*, int>>& mats, int cs, cudaStream_t s, const char* what);
+// Panel width bgj_run uses for blocks up to nmax on clusters of cs CTAs (0: does not fit).
+int bgj_panel_width(int nmax, int cs);
 struct InvJob;
 // In-place inverses of a batch of blocks (persistent Gauss-Jordan for few or large blocks,
 // one CTA per block otherwise); throws HBS_WARN_ILLCOND when a pivot is exactly zero.

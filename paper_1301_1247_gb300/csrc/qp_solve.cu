@@ -28,6 +28,7 @@
 #include "profile.hpp"
 #include "gridsync.cuh"
 #include "qp_kernels.cuh"
+#include "tune.hpp"
 
 namespace hbs {
 
@@ -1319,8 +1320,8 @@ static void schur_solve(const Dims& D, const std::vector<GroupJob>& gjobs, const
     per_sm = it->second.second;
   }
   // every CTA of the cooperative launch must be co-resident: ng * CL <= sms * per_sm
-  const int CL = std::min(4, (sms * std::min(per_sm, 2)) / std::max(ng, 1));
-  if (CL < 2) {
+  const int cl_max = std::min(4, (sms * std::min(per_sm, 2)) / std::max(ng, 1));
+  if (cl_max < 2) {
     k_schur_solve<256><<<ng, 256, 0, s>>>(D, dg, Sp, Rp, ill);
     return;
   }
@@ -1331,6 +1332,19 @@ static void schur_solve(const Dims& D, const std::vector<GroupJob>& gjobs, const
     send = std::max<int64_t>(send, G.s_off + (int64_t)G.nsys * G.nsys);
     rend = std::max<int64_t>(rend, G.r_off + (int64_t)G.nsys * G.q);
   }
+  // CTAs per group: 2, 3 or 4 (tuned per shape class when autotuning is on; the most that
+  // stay co-resident by default)
+  int n_pow = 1, g_pow = 1;
+  while (n_pow < nmax) n_pow *= 2;
+  while (g_pow < ng) g_pow *= 2;
+  const std::string tkey = "schur/n" + std::to_string(n_pow) + "/g" + std::to_string(g_pow) + (df ? "/df" : "");
+  int var = tune::choose(tkey, 3, cl_max - 2);
+  if (var + 2 > cl_max) {  // more CTAs than stay co-resident: not a candidate
+    if (tune::exploring(tkey, 3)) tune::record(tkey, var, 3, 1e30f);
+    var = cl_max - 2;
+  }
+  const int CL = var + 2;
+  tune::Timed timed(tkey, var, 3, s);
   const int npan = (nmax + 15) / 16;
   DevBuf<GridSync> gs(1);
   DevBuf<int> piv((size_t)ng * std::max(nmax, 1));

@@ -71,24 +71,30 @@ def test_rank_cap_gives_err_rank():
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("count,n", [(3, 150), (200, 40), (5, 512)])
-def test_batched_inverse_matches_numpy_and_flags_singular_blocks(count, n, precision):
-    """The per-node inversion kernels (persistent multi-CTA for few blocks, one CTA per block
-    for many) against numpy's inverse; then one block with a zero column gives
-    HBS_WARN_ILLCOND."""
+@pytest.mark.parametrize("count,n", [(3, 150), (200, 40), (5, 512), (2, 1000)])
+def test_batched_inverse_matches_numpy_and_flags_singular_blocks(count, n, precision, monkeypatch):
+    """The per-node inversion kernels (multi-CTA for few blocks, one CTA per block for many)
+    against numpy's inverse; then one block with a zero column gives HBS_WARN_ILLCOND.  With
+    the autotuner exploring, consecutive calls of one shape run every multi-CTA variant in
+    turn: the persistent Gauss-Jordan and the blocked one on clusters of 1, 2, 4 and 8 CTAs."""
     hbs = require_lib()
+    monkeypatch.setenv("HBS_AUTOTUNE", "1")
+    monkeypatch.setenv("HBS_TUNE_FILE", "")
     rng = np.random.default_rng(count + n)
     a = rng.standard_normal((count, n, n)) + 1j * rng.standard_normal((count, n, n))
     a += 4 * np.sqrt(n) * np.eye(n)[None]  # well conditioned, as the leaf blocks of A are
-    buf = dev(np.ascontiguousarray(np.transpose(a, (0, 2, 1))).ravel())  # column-major blocks
-    assert hbs.batched_inverse(buf, n, count, precision) == hbs.HBS_OK
-    got = np.transpose(buf.cpu().numpy().reshape(count, n, n), (0, 2, 1))
     ref = np.linalg.inv(a)
-    assert relerr(got, ref) < (1e-13 if precision == 0 else 1e-12)
+    for _ in range(5):
+        buf = dev(np.ascontiguousarray(np.transpose(a, (0, 2, 1))).ravel())  # column-major blocks
+        assert hbs.batched_inverse(buf, n, count, precision) == hbs.HBS_OK
+        got = np.transpose(buf.cpu().numpy().reshape(count, n, n), (0, 2, 1))
+        assert relerr(got, ref) < (1e-13 if precision == 0 else 1e-12)
     a[count // 2][:, n // 3] = 0.0
-    buf = dev(np.ascontiguousarray(np.transpose(a, (0, 2, 1))).ravel())
-    assert hbs.batched_inverse(buf, n, count, precision) == hbs.HBS_WARN_ILLCOND
-    assert b"singular" in hbs.lib().hbs_last_error()
+    a2 = np.concatenate([a, a])  # twice the blocks: a shape class of its own, explored afresh
+    for _ in range(5):
+        buf = dev(np.ascontiguousarray(np.transpose(a2, (0, 2, 1))).ravel())
+        assert hbs.batched_inverse(buf, n, 2 * count, precision) == hbs.HBS_WARN_ILLCOND
+        assert b"singular" in hbs.lib().hbs_last_error()
 
 
 def test_injected_allocation_failure_gives_oom_then_normal_service():
