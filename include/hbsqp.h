@@ -158,6 +158,22 @@ hbs_status hbs_solve_plain(hbs_handle* h, const double* theta, int64_t n_theta, 
                            hbs_result** out);
 
 /*
+ * The same Bragg amplitudes with a second periodizer: proxy points and wall discrepancies
+ * instead of the Sommerfeld-contour wall potentials of Secs. 2.2-2.4 (the paper's Sec. 7
+ * points to this family of schemes without defining one).  The handle's compressed
+ * inverse and neighbour factors (Secs. 3.2, 4) are reused; the unit cell is cut to the box
+ * |x| <= d/2, |y| <= h (h = max|y| + d/8), the images beyond the neighbours are represented by
+ * combined-field sources on a circle around it, and the radiation condition by outgoing
+ * Rayleigh-Bloch expansions matched on y = +-h.  Each Bloch phase's rectangular system is
+ * solved in the least-squares sense; every step is FP64.  The amplitudes are referred to
+ * y = +-y0 as hbs_solve's are (n_wood = 0, t0 = 0 in hbs_result_angle_info).  Meant to
+ * cross-check hbs_solve, not tuned for speed.  theta must lie in (-pi, 0), else
+ * HBS_ERR_INVALID_ARG; OOM and CUDA as hbs_solve.  Synchronizes the stream.
+ */
+hbs_status hbs_solve_proxy(hbs_handle* h, const double* theta, int64_t n_theta, void* stream,
+                           hbs_result** out);
+
+/*
  * Bragg amplitudes of angle i of a result (Remarks 2.2, 2.3): propagating
  * orders n_min..n_max (|kappa_n| <= w), upward c_n and downward d_n as in
  * Eqs. (rbu), (rbd), and the flux error |sum_n (k_n/k_0)(|c_n|^2 +

@@ -35,6 +35,7 @@ namespace hbs {
 namespace {
 
 constexpr int kCNT = 256;     // threads per CTA of the panel kernel
+constexpr const char* kBgjUnavailable = "blocked Gauss-Jordan launch shape unavailable";
 constexpr int kMaxPanel = 32;
 // shared memory one CTA may use for its slice of the panel (P, U and V rows, used flags)
 constexpr size_t kSmemBudget = 200 * 1024;
@@ -264,6 +265,8 @@ __global__ void k_bgj_copy(const BgjJob* jobs) {
 static size_t bgj_slice_bytes(int R, int b) { return (size_t)R * b * 3 * sizeof(cplx) + (size_t)R * sizeof(int); }
 
 // Panel width for blocks up to nmax on clusters of cs CTAs (0: does not fit).
+bool bgj_unavailable(const Error& e) { return std::string(e.what()).rfind(kBgjUnavailable, 0) == 0; }
+
 int bgj_panel_width(int nmax, int cs) {
   const int R = (nmax + cs - 1) / cs;
   int b = kMaxPanel;
@@ -276,6 +279,26 @@ static void launch_bgj_panel(const BgjJob* dj, int nj, int c0, int b, size_t sme
   if (smem > 48 * 1024)
     HBS_CUDA(cudaFuncSetAttribute(k_bgj_panel<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_bgj_panel<CS><<<(unsigned)(nj * CS), kCNT, smem, s>>>(dj, c0, b);
+}
+
+// Clusters of this launch shape the device can hold at once (0: it cannot run one).
+template <int CS>
+static int bgj_max_clusters(size_t smem) {
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_bgj_panel<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(CS, 1, 1);
+  cfg.blockDim = dim3(kCNT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_bgj_panel<CS>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 void bgj_run(const std::vector<std::pair<cplx*, int>>& mats, int cs, cudaStream_t s, const char* what) {
@@ -297,6 +320,14 @@ void bgj_run(const std::vector<std::pair<cplx*, int>>& mats, int cs, cudaStream_
   if (b == 0) throw Error(HBS_ERR_INVALID_ARG, "blocked Gauss-Jordan: block too large for the cluster");
   const int R = (nmax + CS - 1) / CS;
   const size_t smem = bgj_slice_bytes(R, b);
+  int fits = 0;
+  switch (CS) {
+    case 8: fits = bgj_max_clusters<8>(smem); break;
+    case 4: fits = bgj_max_clusters<4>(smem); break;
+    case 2: fits = bgj_max_clusters<2>(smem); break;
+    default: fits = bgj_max_clusters<1>(smem); break;
+  }
+  if (fits < 1) throw Error(HBS_ERR_INTERNAL, std::string(kBgjUnavailable) + ": no cluster of this shape fits");
   DevBuf<int> pi(ntot), used(ntot), sing(nj);
   DevBuf<cplx> U(ntot * b), V(ntot * b), Vt(ntot * b), tmp(atot);
   HBS_CUDA(cudaMemsetAsync(used.get(), 0, sizeof(int) * ntot, s));
@@ -329,6 +360,12 @@ void bgj_run(const std::vector<std::pair<cplx*, int>>& mats, int cs, cudaStream_
         case 2: launch_bgj_panel<2>(dj.get(), nj, c0, b, smem, s); break;
         default: launch_bgj_panel<1>(dj.get(), nj, c0, b, smem, s); break;
       }
+    }
+    if (c0 == 0) {
+      // a launch the device rejects never ran: the blocks are untouched, the caller may fall back
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess)
+        throw Error(HBS_ERR_INTERNAL, std::string(kBgjUnavailable) + ": " + cudaGetErrorString(e));
     }
     HBS_LAUNCH_CHECK("k_bgj_panel");
     // A <- A - U V^T on the columns outside the panel (left and right of it)

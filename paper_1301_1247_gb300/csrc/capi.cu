@@ -277,6 +277,31 @@ hbs_status hbs_solve_plain(hbs_handle* h, const double* theta, int64_t n_theta, 
   return solve_common(h, theta, n_theta, stream, out, true);
 }
 
+hbs_status hbs_solve_proxy(hbs_handle* h, const double* theta, int64_t n_theta, void* stream, hbs_result** out) {
+  if (!h || !out || (n_theta > 0 && !theta) || n_theta < 0) {
+    set_last_error("bad arguments to hbs_solve_proxy");
+    return HBS_ERR_INVALID_ARG;
+  }
+  for (int64_t i = 0; i < n_theta; ++i)
+    if (!(theta[i] < 0.0 && theta[i] > -M_PI)) {
+      set_last_error("hbs_solve_proxy: incident angles must lie in (-pi, 0)");
+      return HBS_ERR_INVALID_ARG;
+    }
+  *out = nullptr;
+  hbs_result* r = new (std::nothrow) hbs_result();
+  if (!r) { set_last_error("host allocation failed"); return HBS_ERR_OOM; }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScope scope(s);
+  hbs_status st = guarded([&] {
+    GemmModeScope gm(HBS_PRECISION_FP64);
+    solve_angles_proxy(h->h, theta, n_theta, r->r, s);
+    HBS_CUDA(cudaStreamSynchronize(s));
+  });
+  if (st != HBS_OK) { delete r; return st; }
+  *out = r;
+  return HBS_OK;
+}
+
 hbs_status hbs_bragg_amplitudes(const hbs_result* r, int64_t i, int* n_min, int* n_max, double* c, double* d,
                                 double* flux_err) {
   if (!r || i < 0 || i >= (int64_t)r->r.angles.size()) {

@@ -545,9 +545,21 @@ void batched_inverse(std::vector<InvJob>& jobs_in, cudaStream_t s, const char* w
       if (tune::exploring(tkey, 5)) tune::record(tkey, var, 5, 1e30f);
       var = 0;
     }
-    tune::Timed timed(tkey, var, 5, s);
-    if (var == 0) pgj_run(big, s, what);
-    else bgj_run(big, kCs[var], s, what);
+    bool done = false;
+    if (var > 0) {
+      try {
+        tune::Timed timed(tkey, var, 5, s);
+        bgj_run(big, kCs[var], s, what);
+        done = true;
+      } catch (const Error& e) {
+        if (!bgj_unavailable(e)) throw;
+        tune::record(tkey, var, 5, 1e30f);  // this shape cannot run here: never choose it
+      }
+    }
+    if (!done) {
+      tune::Timed timed(tkey, 0, 5, s);
+      pgj_run(big, s, what);
+    }
   }
   if (jobs.empty()) return;
   for (size_t i = 0; i < jobs.size(); ++i) jobs[i].job = (int)i;

@@ -63,6 +63,10 @@ void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, con
 void bgj_run(const std::vector<std::pair<cplx*, int>>& mats, int cs, cudaStream_t s, const char* what);
 // Panel width bgj_run uses for blocks up to nmax on clusters of cs CTAs (0: does not fit).
 int bgj_panel_width(int nmax, int cs);
+// True for bgj_run's error when the device cannot run the requested cluster shape; the
+// blocks are then untouched.
+struct Error;
+bool bgj_unavailable(const Error& e);
 struct InvJob;
 // In-place inverses of a batch of blocks (persistent Gauss-Jordan for few or large blocks,
 // one CTA per block otherwise); throws HBS_WARN_ILLCOND when a pivot is exactly zero.
@@ -150,6 +154,8 @@ __global__ void k_diff_norm2(const cplx* a, int64_t lda, const cplx* b, int64_t 
 // two share the device until the transposed sweep, which needs both.
 void build_periodizer(Handle& h, cudaStream_t s, bool with_hbs = false);
 void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, Result& out, cudaStream_t s);
+// The same angles with the proxy-point / wall-discrepancy periodizer (proxy.cu).
+void solve_angles_proxy(Handle& h, const double* theta, int64_t n_theta, Result& out, cudaStream_t s);
 
 inline int grid_1d(int64_t tot, int nt = 256, int cap = 8192) {
   int64_t b = (tot + nt - 1) / nt;

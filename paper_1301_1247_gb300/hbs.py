@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "RANK", 5: "W
                 6: "TIMEOUT", 7: "IO", 8: "INTERNAL"}
 
 # Every entry point declared in include/hbsqp.h.
-EXPORTED = ("hbs_default_options", "hbs_build", "hbs_build_batch", "hbs_solve", "hbs_solve_plain", "hbs_bragg_amplitudes",
+EXPORTED = ("hbs_default_options", "hbs_build", "hbs_build_batch", "hbs_solve", "hbs_solve_plain", "hbs_solve_proxy",
+            "hbs_bragg_amplitudes",
             "hbs_result_angle_info", "hbs_info", "hbs_save", "hbs_load", "hbs_apply_inverse",
             "hbs_kernel_block", "hbs_row_id", "hbs_batched_inverse", "hbs_zgemm",
             "hbs_row_id_static",
@@ -114,6 +115,7 @@ def lib():
     L.hbs_build_batch.restype = ctypes.c_int
     L.hbs_solve.argtypes = [vp, ctypes.POINTER(dbl), i64, vp, ctypes.POINTER(vp)]
     L.hbs_solve_plain.argtypes = [vp, ctypes.POINTER(dbl), i64, vp, ctypes.POINTER(vp)]
+    L.hbs_solve_proxy.argtypes = [vp, ctypes.POINTER(dbl), i64, vp, ctypes.POINTER(vp)]
     L.hbs_bragg_amplitudes.argtypes = [vp, i64, ctypes.POINTER(ci), ctypes.POINTER(ci), vp, vp,
                                        ctypes.POINTER(dbl)]
     L.hbs_result_angle_info.argtypes = [vp, i64, ctypes.POINTER(ci), ctypes.POINTER(dbl)]
@@ -149,7 +151,8 @@ def lib():
     L.hbs_result_free.restype = None
     L.hbs_last_error.argtypes = []
     L.hbs_last_error.restype = ctypes.c_char_p
-    for name in ("hbs_build", "hbs_solve", "hbs_solve_plain", "hbs_bragg_amplitudes", "hbs_result_angle_info",
+    for name in ("hbs_build", "hbs_solve", "hbs_solve_plain", "hbs_solve_proxy", "hbs_bragg_amplitudes",
+                 "hbs_result_angle_info",
                  "hbs_info", "hbs_apply_inverse", "hbs_kernel_block", "hbs_row_id", "hbs_row_id_static"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -288,6 +291,10 @@ class Handle:
 
     def solve_plain(self, thetas, stream=None) -> Result:
         return self._solve(lib().hbs_solve_plain, thetas, stream)
+
+    def solve_proxy(self, thetas, stream=None) -> Result:
+        """hbs_solve_proxy: the same amplitudes with the proxy-point / wall-discrepancy periodizer."""
+        return self._solve(lib().hbs_solve_proxy, thetas, stream)
 
     def apply_inverse(self, b, x, nrhs, stream=None):
         """x = A^{-1} b for device complex128 tensors (N x nrhs, column-major, i.e. torch shape (nrhs, N))."""
