@@ -79,16 +79,19 @@ FLOP_COUNT_NOTE = {
     "k_oz_mma": "executed bf16 digit-plane flops on padded tiles",
 }
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
-# kernel's launches in one step of this bench's default workload) from one ncu capture,
-# with the digest of the sources the kernel is built from at capture time.  The figure
-# is reported only while those sources are unchanged.
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum averaged over the
+# kernel's launches in one step) from ncu captures, per workload, with the digest of the
+# sources the kernel is built from at capture time; reported only while they are unchanged.
+# k_pqr's traffic does not grow in proportion to its work (one launch, the periodizer
+# families, dominates it by writing back its trailing matrix when the matrices outgrow L2),
+# so the N = 1e4 capture is not scaled to the N = 1e5 workload.
 NCU_TRAFFIC = {
-    # profiles/launch_list_complicated_n100k.md: mean over the kernel's launches in one run
-    "k_pqr": {"bytes_per_launch": 4.962e+09, "sources": ['paper_1301_1247_gb300/csrc/pqr.cu', 'paper_1301_1247_gb300/csrc/common.cuh', 'paper_1301_1247_gb300/csrc/gridsync.cuh', 'paper_1301_1247_gb300/csrc/dense_kernels.cuh', 'paper_1301_1247_gb300/csrc/dfloat.cuh', 'paper_1301_1247_gb300/csrc/dfcore.cuh', 'paper_1301_1247_gb300/csrc/hankel_table.h', 'paper_1301_1247_gb300/csrc/balance.hpp'],
-              "digest": "a6d5580279ef7a21"},
-    "k_zgemm_batched_df": {"bytes_per_launch": 3.087e+08, "sources": ['paper_1301_1247_gb300/csrc/zgemm.cuh', 'paper_1301_1247_gb300/csrc/common.cuh', 'paper_1301_1247_gb300/csrc/dfcore.cuh', 'paper_1301_1247_gb300/csrc/dfloat.cuh', 'paper_1301_1247_gb300/csrc/hankel_table.h'],
-                           "digest": "982e0a980ec1bb5a"},
+    # profiles/k_pqr_wiggly_n10k.md: all 9 launches of a step at N = 1e4 (27 over 3 steps)
+    ("wiggly_n10k", "k_pqr"): {"bytes_per_launch": 3.598e+08, "sources": ['paper_1301_1247_gb300/csrc/pqr.cu', 'paper_1301_1247_gb300/csrc/common.cuh', 'paper_1301_1247_gb300/csrc/gridsync.cuh', 'paper_1301_1247_gb300/csrc/dense_kernels.cuh', 'paper_1301_1247_gb300/csrc/dfloat.cuh', 'paper_1301_1247_gb300/csrc/dfcore.cuh', 'paper_1301_1247_gb300/csrc/hankel_table.h', 'paper_1301_1247_gb300/csrc/balance.hpp'],
+                                "digest": "f334d8b6ea0d5aff"},
+    # profiles/launch_list_complicated_n100k.md (first capture of this kernel's sources)
+    ("complicated_n100k", "k_zgemm_batched_df"): {"bytes_per_launch": 3.087e+08, "sources": ['paper_1301_1247_gb300/csrc/zgemm.cuh', 'paper_1301_1247_gb300/csrc/common.cuh', 'paper_1301_1247_gb300/csrc/dfcore.cuh', 'paper_1301_1247_gb300/csrc/dfloat.cuh', 'paper_1301_1247_gb300/csrc/hankel_table.h'],
+                                                  "digest": "982e0a980ec1bb5a"},
 }
 
 
@@ -101,8 +104,8 @@ def _sources_digest(paths):
     return hsh.hexdigest()[:16]
 
 
-def measured_traffic(kernel):
-    rec = NCU_TRAFFIC.get(kernel)
+def measured_traffic(workload_name, kernel):
+    rec = NCU_TRAFFIC.get((workload_name, kernel))
     if rec is None:
         return None
     try:
@@ -444,7 +447,10 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": int(launches),
         "roofline": {"bound": kbound, "kernel": tname, "achieved": round(achieved, 4), "peak": round(kpeak, 4),
                      "unit": "TFLOP/s", "frac": round(achieved / kpeak, 4),
-                     "traffic": measured_traffic(tname),
+                     "traffic": measured_traffic(w["name"], tname),
+                     "traffic_note": None if measured_traffic(w["name"], tname) is not None else
+                     "no capture of this kernel's current sources on this workload; k_pqr's DRAM traffic at N = 1e4 "
+                     "is in profiles/k_pqr_wiggly_n10k.md (it does not scale with the work, so it is not scaled here)",
                      "algorithmic_bytes_per_launch": round(tv["bytes"] / max(tv["launches"], 1), 1) or None,
                      "flop_count": FLOP_COUNT_NOTE.get(tname, "as recorded by the library"),
                      "peak_note": knote + " (of measured)" if kbound == "tensor" else knote,
