@@ -1003,63 +1003,72 @@ void build_hbs(Handle& h, cudaStream_t s) {
 // root solve, downward x_tau = E_tau x^_tau + G_tau b_tau.
 // x = A^{-1} b (trans = false) or x = A^{-T} b (trans = true, the factors transposed:
 // A^{-T} = F*^T (M~ + Dhat)^{-T} E^T + G^T, applied with the same telescoping sweep).
-static void apply_impl(const Handle& H, const cplx* b, cplx* xout, int64_t nrhs, cudaStream_t s, bool trans) {
-  if (nrhs <= 0) return;
+// Y = Op^T X for a factor Op (stored rows x cols, ld) and a level vector X (rows x nrhs):
+// formed as Y^T = X^T Op (nrhs x cols, Y written row-major), so that the many right-hand
+// sides fill the 128-row tiles of the tensor-core products even at the leaves.
+static void tprod(std::vector<GemmJob>& gj, int64_t nrhs, const cplx* Op, int rows, int cols, int ld, const cplx* X,
+                  int64_t ldx, cplx* Y, int64_t ldy, cplx beta) {
+  GemmJob j{};
+  j.A = X;
+  j.lda = (int)ldx;
+  j.transA = 1;
+  j.B = Op;
+  j.ldb = ld;
+  j.C = Y;
+  j.ldc = (int)ldy;
+  j.transC = 1;
+  j.m = (int)nrhs;
+  j.n = cols;
+  j.k = rows;
+  j.alpha = cmk(1, 0);
+  j.beta = beta;
+  gj.push_back(j);
+}
+
+// The upward step of level l (1 <= l <= L): up[l - 1] = F* b_tau (or E^T b_tau) for every
+// node, from level l's vector (b itself at the leaves).  The parent level's offsets follow
+// from level l's ranks (a parent's size is the sum of its two children's ranks).
+static void sweep_upward_level(const Handle& H, int l, const cplx* b, int64_t nrhs, bool trans,
+                        std::vector<DevBuf<cplx>>& up, cudaStream_t s) {
+  const Level& lv = H.levels[l];
+  const int np = lv.count / 2;
+  std::vector<int64_t> poff(std::max(np, 1), 0);
+  int64_t pnt = 0;
+  for (int p = 0; p < np; ++p) {
+    poff[p] = pnt;
+    pnt += lv.k[2 * p] + lv.k[2 * p + 1];
+  }
+  if ((int)up.size() < H.L + 1) up.resize(H.L + 1);
+  up[l - 1].alloc(std::max<int64_t>(pnt * nrhs, 1));
+  const cplx* in = l == H.L ? b : up[l].get();
+  std::vector<GemmJob> gj;
+  for (int j = 0; j < lv.count; ++j) {
+    const int n = lv.n[j], k = lv.k[j];
+    if (k == 0) continue;
+    const int64_t prow = poff[j >> 1] + ((j & 1) ? lv.k[j - 1] : 0);
+    if (trans)  // E^T b (E stored n x k)
+      tprod(gj, nrhs, lv.E.get() + lv.e_off[j], n, k, n, in + lv.off[j], lv.ntot, up[l - 1].get() + prow, pnt,
+            cmk(0, 0));
+    else  // F* b (F* stored k x n)
+      gj.push_back({lv.F.get() + lv.f_off[j], in + lv.off[j], up[l - 1].get() + prow, k, (int)nrhs, n, k,
+                    (int)lv.ntot, (int)pnt, cmk(1, 0), cmk(0, 0), 0, 0, 0, 0, 0});
+  }
+  run_gemms(gj, s);
+}
+
+// The rest of the sweep once every upward step is done: the root solve and the downward
+// steps, x_tau = G b_tau + E x^_tau (or G^T b_tau + F*^T x^_tau).
+static void sweep_finish(const Handle& H, const cplx* b, cplx* xout, int64_t nrhs, bool trans,
+                  std::vector<DevBuf<cplx>>& up, cudaStream_t s) {
   const int Lv = H.L;
   const auto& levels = H.levels;
-  // level vectors: up[l] holds b_tau for all nodes of level l (ntot x nrhs, ld = ntot)
-  std::vector<DevBuf<cplx>> up(Lv + 1), dn(Lv + 1);
-  for (int l = 0; l < Lv; ++l) {
-    up[l].alloc(std::max<int64_t>(levels[l].ntot * nrhs, 1));
-    dn[l].alloc(std::max<int64_t>(levels[l].ntot * nrhs, 1));
-  }
+  std::vector<DevBuf<cplx>> dn(Lv + 1);
+  for (int l = 0; l < Lv; ++l) dn[l].alloc(std::max<int64_t>(levels[l].ntot * nrhs, 1));
   auto upptr = [&](int l) -> const cplx* { return l == Lv ? b : up[l].get(); };
-  // Y = Op^T X for a factor Op (stored rows x cols, ld) and a level vector X (rows x nrhs):
-  // formed as Y^T = X^T Op (nrhs x cols, Y written row-major), so that the many right-hand
-  // sides fill the 128-row tiles of the tensor-core products even at the leaves.
-  auto tprod = [&](std::vector<GemmJob>& gj, const cplx* Op, int rows, int cols, int ld, const cplx* X, int64_t ldx,
-                   cplx* Y, int64_t ldy, cplx beta) {
-    GemmJob j{};
-    j.A = X;
-    j.lda = (int)ldx;
-    j.transA = 1;
-    j.B = Op;
-    j.ldb = ld;
-    j.C = Y;
-    j.ldc = (int)ldy;
-    j.transC = 1;
-    j.m = (int)nrhs;
-    j.n = cols;
-    j.k = rows;
-    j.alpha = cmk(1, 0);
-    j.beta = beta;
-    gj.push_back(j);
-  };
-  for (int l = Lv; l >= 1; --l) {
-    const Level& lv = levels[l];
-    const Level& pa = levels[l - 1];
-    std::vector<GemmJob> gj;
-    for (int j = 0; j < lv.count; ++j) {
-      const int n = lv.n[j], k = lv.k[j];
-      if (k == 0) continue;
-      const int parent = j >> 1;
-      const int64_t prow = pa.off[parent] + ((j & 1) ? levels[l].k[j - 1] : 0);
-      if (trans) {
-        // upward: E^T b (E stored n x k)
-        tprod(gj, lv.E.get() + lv.e_off[j], n, k, n, upptr(l) + lv.off[j], lv.ntot, up[l - 1].get() + prow, pa.ntot,
-              cmk(0, 0));
-      } else {
-        // upward: F* b (F* stored k x n)
-        gj.push_back({lv.F.get() + lv.f_off[j], upptr(l) + lv.off[j], up[l - 1].get() + prow, k, (int)nrhs, n, k,
-                      (int)lv.ntot, (int)pa.ntot, cmk(1, 0), cmk(0, 0), 0, 0, 0, 0, 0});
-      }
-    }
-    run_gemms(gj, s);
-  }
   {
     std::vector<GemmJob> gj;
     if (trans)
-      tprod(gj, H.Groot.get(), H.nroot, H.nroot, H.nroot, up[0].get(), H.nroot, dn[0].get(), H.nroot, cmk(0, 0));
+      tprod(gj, nrhs, H.Groot.get(), H.nroot, H.nroot, H.nroot, up[0].get(), H.nroot, dn[0].get(), H.nroot, cmk(0, 0));
     else
       gj.push_back({H.Groot.get(), up[0].get(), dn[0].get(), H.nroot, (int)nrhs, H.nroot, H.nroot, H.nroot, H.nroot,
                     cmk(1, 0), cmk(0, 0), 0, 0, 0, 0, 0});
@@ -1074,7 +1083,7 @@ static void apply_impl(const Handle& H, const cplx* b, cplx* xout, int64_t nrhs,
       const int n = lv.n[j];
       // x_tau = G b_tau  (or G^T b_tau)
       if (trans)
-        tprod(gj, lv.G.get() + lv.g_off[j], n, n, n, upptr(l) + lv.off[j], lv.ntot, outp + lv.off[j], lv.ntot,
+        tprod(gj, nrhs, lv.G.get() + lv.g_off[j], n, n, n, upptr(l) + lv.off[j], lv.ntot, outp + lv.off[j], lv.ntot,
               cmk(0, 0));
       else
         gj.push_back({lv.G.get() + lv.g_off[j], upptr(l) + lv.off[j], outp + lv.off[j], n, (int)nrhs, n, n,
@@ -1089,8 +1098,8 @@ static void apply_impl(const Handle& H, const cplx* b, cplx* xout, int64_t nrhs,
       const int64_t prow = pa.off[parent] + ((j & 1) ? levels[l].k[j - 1] : 0);
       if (trans) {
         // x_tau += F*^T x^_tau  (F* stored k x n)
-        tprod(gj, lv.F.get() + lv.f_off[j], k, n, k, dn[l - 1].get() + prow, pa.ntot, outp + lv.off[j], lv.ntot,
-              cmk(1, 0));
+        tprod(gj, nrhs, lv.F.get() + lv.f_off[j], k, n, k, dn[l - 1].get() + prow, pa.ntot, outp + lv.off[j],
+              lv.ntot, cmk(1, 0));
       } else {
         // x_tau += E x^_tau  (E stored n x k)
         gj.push_back({lv.E.get() + lv.e_off[j], dn[l - 1].get() + prow, outp + lv.off[j], n, (int)nrhs, k, n,
@@ -1099,6 +1108,13 @@ static void apply_impl(const Handle& H, const cplx* b, cplx* xout, int64_t nrhs,
     }
     run_gemms(gj, s);
   }
+}
+
+static void apply_impl(const Handle& H, const cplx* b, cplx* xout, int64_t nrhs, cudaStream_t s, bool trans) {
+  if (nrhs <= 0) return;
+  std::vector<DevBuf<cplx>> up(H.L + 1);
+  for (int l = H.L; l >= 1; --l) sweep_upward_level(H, l, b, nrhs, trans, up, s);
+  sweep_finish(H, b, xout, nrhs, trans, up, s);
 }
 
 void Handle::apply_inverse(const cplx* b, cplx* xout, int64_t nrhs, cudaStream_t s) const {
