@@ -234,13 +234,11 @@ def matrix_b_parts(bd: Boundary, ct: Contour, omega, d):
     return np.hstack([sl, dl]), np.hstack([sr, dr])
 
 
-def wall_fourier_rows(sx, sy, snx, sny, sw, ct: Contour, omega, x0):
-    """Fourier transform at the contour nodes of the wall discrepancy rows produced by
-    combined-field sources (sx, sy) (Sec. 2.2, operators S^, D^, D*^, T^):
-
-    f-row  = D^ - i w S^,   fn-row = T^ - i w D*^,  each 2M x N after stacking [f; fn],
-    multiplied by the source weights sw.
-    """
+def wall_fourier_parts(sx, sy, snx, sny, ct: Contour, omega, x0):
+    """Fourier transforms at the contour nodes (M x sources) of the wall data of a
+    single-layer source (value S^, x-derivative D*^) and of a double-layer source (value
+    D^, x-derivative T^) at (sx, sy) with normal (snx, sny), for the wall at x = x0
+    (Sec. 2.2)."""
     k = ct.k[:, None]
     s = sqrt_branch(omega, k)
     sg = np.sign(sx - x0)[None, :]
@@ -249,6 +247,17 @@ def wall_fourier_rows(sx, sy, snx, sny, sw, ct: Contour, omega, x0):
     d_hat = base * (-sg * snx[None, :] + (k / s) * sny[None, :])
     dstar_hat = base * sg
     t_hat = 1j * base * (s * snx[None, :] - k * sg * sny[None, :])
+    return s_hat, d_hat, dstar_hat, t_hat
+
+
+def wall_fourier_rows(sx, sy, snx, sny, sw, ct: Contour, omega, x0):
+    """Fourier transform at the contour nodes of the wall discrepancy rows produced by
+    combined-field sources (sx, sy) (Sec. 2.2, operators S^, D^, D*^, T^):
+
+    f-row  = D^ - i w S^,   fn-row = T^ - i w D*^,  each 2M x N after stacking [f; fn],
+    multiplied by the source weights sw.
+    """
+    s_hat, d_hat, dstar_hat, t_hat = wall_fourier_parts(sx, sy, snx, sny, ct, omega, x0)
     f = (d_hat - 1j * omega * s_hat) * sw[None, :]
     fn = (t_hat - 1j * omega * dstar_hat) * sw[None, :]
     return np.vstack([f, fn])
