@@ -26,12 +26,19 @@ jump relations of the layer potentials.  The readings:
   Every operator is a difference of two kernels in which the 1/r^2 of T and the log r of S
   cancel to at most a log r singularity: the identity plus a compact operator, as Sec. 5
   says.
+* Scaling.  The sigma rows are divided by w and the single-layer density is carried as
+  s = sigma / w, so that the field is u = w S s + D tau.  This is a diagonal similarity of
+  the system above (the same fields and Bragg amplitudes); it balances the 2 x 2 blocks,
+  whose T difference grows like w^2: on a wiggly obstacle at w = 30 (n = 1.3) the operator's
+  condition number falls from 3557 to 24, at w = 60 from 9.3e4 to 61, the Dirichlet
+  operator's own level.  Interpolative decompositions with a relative tolerance then resolve
+  both kinds of rows alike.
 * Row functionals.  The tau row of node p takes the value of a field at y_p, the sigma row
-  minus its normal derivative.  Every outside contribution (images, wall potentials, Wood's
-  plane waves) enters a row through its functional, and the right-hand side is minus the
-  functional of u_inc.  The tau rows are the Dirichlet problem's rows.
-* Interlacing (Sec. 5): unknowns [sigma_1; tau_1; sigma_2; tau_2; ...], rows in the same
-  order (sigma row of node 1, tau row of node 1, ...).
+  minus its normal derivative divided by w.  Every outside contribution (images, wall
+  potentials, Wood's plane waves) enters a row through its functional, and the right-hand
+  side is minus the functional of u_inc.  The tau rows are the Dirichlet problem's rows.
+* Interlacing (Sec. 5): unknowns [s_1; tau_1; s_2; tau_2; ...], rows in the same order
+  (sigma row of node 1, tau row of node 1, ...).
 * Quadrature: the Kapur-Rokhlin corrections of Sec. 2.3 on every kernel difference (each is
   of the form phi(s) log|s| + psi(s) with phi, psi smooth); the diagonal 2 x 2 blocks are
   the identity (R_0 = 0).  Images take plain trapezoid weights.
@@ -40,8 +47,8 @@ jump relations of the layer potentials.  The readings:
   D*^ to the fn rows, a tau column D^ and T^.  Q is unchanged (Sec. 5).
 * Wood's anomalies, the Bragg extraction and the flux balance are the Dirichlet oracle's.
   For real n the obstacle absorbs nothing, so the flux still balances.
-* Setting sigma = -i w eta, tau = eta turns the pair into the combined layer, so every
-  outside row of this module reduces to the Dirichlet oracle's (a pin).
+* Setting s = -i eta, tau = eta turns the pair into the combined layer (D - i w S) eta, so
+  every outside row of this module reduces to the Dirichlet oracle's (a pin).
 """
 from __future__ import annotations
 
@@ -117,11 +124,11 @@ def interlace_cols(sigma_cols, tau_cols):
     return out
 
 
-def row_functional(bd: qd.Boundary, value, gx, gy):
-    """Rows of a field sampled at the boundary nodes: sigma row = -du/dn, tau row = u."""
+def row_functional(bd: qd.Boundary, omega, value, gx, gy):
+    """Rows of a field sampled at the boundary nodes: sigma row = -(du/dn)/w, tau row = u."""
     nx = bd.nx.reshape((-1,) + (1,) * (np.ndim(value) - 1))
     ny = bd.ny.reshape((-1,) + (1,) * (np.ndim(value) - 1))
-    return interlace_rows(-(nx * gx + ny * gy), value)
+    return interlace_rows(-(nx * gx + ny * gy) / omega, value)
 
 
 # --------------------------------------------------------------------------
@@ -129,8 +136,8 @@ def row_functional(bd: qd.Boundary, value, gx, gy):
 # --------------------------------------------------------------------------
 
 def matrix_a(bd: qd.Boundary, omega: float, index: float) -> np.ndarray:
-    """The Mueller-type operator of the reading above on one obstacle, interlaced, with the
-    Kapur-Rokhlin weights (2 pi/N) R_{|p-q|} |z'(t_q)| on every kernel difference."""
+    """The Mueller-type operator of the reading above on one obstacle, interlaced and scaled,
+    with the Kapur-Rokhlin weights (2 pi/N) R_{|p-q|} |z'(t_q)| on every kernel difference."""
     n = bd.n
     idx = np.arange(n)
     dist = np.abs(idx[:, None] - idx[None, :])
@@ -146,9 +153,9 @@ def matrix_a(bd: qd.Boundary, omega: float, index: float) -> np.ndarray:
         parts.append(v * rw)
     kp, t, s, dd = parts
     a = np.zeros((2 * n, 2 * n), dtype=np.complex128)
-    a[0::2, 0::2] = -kp
-    a[0::2, 1::2] = -t
-    a[1::2, 0::2] = s
+    a[0::2, 0::2] = -kp            # (1/w) row, w column
+    a[0::2, 1::2] = -t / omega
+    a[1::2, 0::2] = s * omega
     a[1::2, 1::2] = dd
     a[np.arange(2 * n), np.arange(2 * n)] += 1.0
     return a
@@ -161,8 +168,8 @@ def matrix_a_image(bd: qd.Boundary, omega: float, d: float, j: int) -> np.ndarra
     w = bd.w[None, :]
     a = np.zeros((2 * bd.n, 2 * bd.n), dtype=np.complex128)
     a[0::2, 0::2] = -kp * w
-    a[0::2, 1::2] = -t * w
-    a[1::2, 0::2] = s * w
+    a[0::2, 1::2] = -t * w / omega
+    a[1::2, 0::2] = s * w * omega
     a[1::2, 1::2] = dd * w
     return a
 
@@ -181,15 +188,16 @@ def matrix_b_parts(bd: qd.Boundary, ct: qd.Contour, omega, d):
     gx = qd.wall_field_rows(bd.x, bd.y, ct, omega, d, "x")
     gy = qd.wall_field_rows(bd.x, bd.y, ct, omega, d, "y")
     # each is (SL, SR, DL, DR)
-    bl = row_functional(bd, np.hstack([v[0], v[2]]), np.hstack([gx[0], gx[2]]), np.hstack([gy[0], gy[2]]))
-    br = row_functional(bd, np.hstack([v[1], v[3]]), np.hstack([gx[1], gx[3]]), np.hstack([gy[1], gy[3]]))
+    bl = row_functional(bd, omega, np.hstack([v[0], v[2]]), np.hstack([gx[0], gx[2]]), np.hstack([gy[0], gy[2]]))
+    br = row_functional(bd, omega, np.hstack([v[1], v[3]]), np.hstack([gx[1], gx[3]]), np.hstack([gy[1], gy[3]]))
     return bl, br
 
 
 def wall_fourier_rows_pair(sx, sy, snx, sny, sw, ct: qd.Contour, omega, x0):
-    """Wall discrepancy rows [f; fn] (2M x 2N) of the pair's sources: sigma columns
-    [S^; D*^], tau columns [D^; T^], times the source weights."""
+    """Wall discrepancy rows [f; fn] (2M x 2N) of the pair's sources: s columns
+    w [S^; D*^], tau columns [D^; T^], times the source weights."""
     s_hat, d_hat, dstar_hat, t_hat = qd.wall_fourier_parts(sx, sy, snx, sny, ct, omega, x0)
+    s_hat, dstar_hat = omega * s_hat, omega * dstar_hat
     w = sw[None, :]
     return np.vstack([interlace_cols(s_hat * w, d_hat * w), interlace_cols(dstar_hat * w, t_hat * w)])
 
@@ -215,7 +223,7 @@ def eval_rows(tx, ty, bd: qd.Boundary, ct: qd.Contour, omega, d, alpha, p: int =
         else:
             gx, gy, dx_, dy_ = layer_gradients(*args)
             gs, gt = (gx, dx_) if deriv == "x" else (gy, dy_)
-        sig += (alpha ** j) * gs * bd.w[None, :]
+        sig += (alpha ** j) * omega * gs * bd.w[None, :]
         tau += (alpha ** j) * gt * bd.w[None, :]
     sl, sr, dl, dr = qd.wall_field_rows(tx[:, 0], ty[:, 0], ct, omega, d, deriv)
     return interlace_cols(sig, tau), np.hstack([sl + alpha * sr, dl + alpha * dr])
@@ -225,7 +233,7 @@ def incident_rhs(bd: qd.Boundary, omega, theta):
     """Minus the row functionals of u_inc = exp(i w (x cos theta + y sin theta))."""
     kx, ky = omega * math.cos(theta), omega * math.sin(theta)
     u = np.exp(1j * (kx * bd.x + ky * bd.y))
-    return -row_functional(bd, u, 1j * kx * u, 1j * ky * u)
+    return -row_functional(bd, omega, u, 1j * kx * u, 1j * ky * u)
 
 
 # --------------------------------------------------------------------------
@@ -268,7 +276,7 @@ def dense_solve(x, y, dx, dy, omega: float, index: float, d: float, theta: float
         uy_eta, uy_xi = eval_rows(xs, ys_lo, bd, ct, omega, d, alpha, p, deriv="y")
         for i, (kap, kn) in enumerate(zip(kap_w, kn_w)):
             pw = qd.plane_wave(bd.x, bd.y, kap, kn)
-            big[:nn, nn + m2 + i] = row_functional(bd, pw, 1j * kap * pw, 1j * kn * pw)
+            big[:nn, nn + m2 + i] = row_functional(bd, omega, pw, 1j * kap * pw, 1j * kn * pw)
             f = qd.dft_rows(xs, np.array([kap]))[0]
             row = nn + m2 + i
             big[row, :nn] = 1j * kn * (f @ u_eta) + f @ uy_eta
@@ -313,10 +321,10 @@ def bragg(bd, ct, omega, d, theta, alpha, eta, xi, wood, wc, y0, n_samples, p=1)
 # --------------------------------------------------------------------------
 
 def free_solve(x, y, dx, dy, omega: float, index: float, theta: float):
-    """The pair's densities (sigma, tau) for an isolated obstacle (no images, no walls)."""
+    """The pair's densities (sigma = w s, tau) for an isolated obstacle (no images, no walls)."""
     bd = qd.boundary(x, y, dx, dy)
     eta = scipy.linalg.solve(matrix_a(bd, omega, index), incident_rhs(bd, omega, theta))
-    return bd, eta[0::2], eta[1::2]
+    return bd, omega * eta[0::2], eta[1::2]
 
 
 def free_field(bd: qd.Boundary, sigma, tau, k, tx, ty):
@@ -386,7 +394,7 @@ def proxy_solve(x, y, dx, dy, omega: float, index: float, d: float, theta: float
         else:
             gx, gy, dx_, dy_ = layer_gradients(*args)
             gs, gt = (gx, dx_) if der == "x" else (gy, dy_)
-        return interlace_cols(gs * bd.w[None, :], gt * bd.w[None, :])
+        return interlace_cols(omega * gs * bd.w[None, :], gt * bd.w[None, :])
 
     def prox(tx, ty, der=None):
         return pp._proxy_field(tx, ty, px, py, pnx, pny, omega, der)
@@ -400,7 +408,7 @@ def proxy_solve(x, y, dx, dy, omega: float, index: float, d: float, theta: float
     rows = []
     r0 = np.zeros((n2, ncol), dtype=np.complex128)
     r0[:, :n2] = at
-    r0[:, n2:n2 + mp] = row_functional(bd, prox(bd.x, bd.y), prox(bd.x, bd.y, "x"), prox(bd.x, bd.y, "y"))
+    r0[:, n2:n2 + mp] = row_functional(bd, omega, prox(bd.x, bd.y), prox(bd.x, bd.y, "x"), prox(bd.x, bd.y, "y"))
     rows.append(r0)
     for der in (None, "x"):
         r = np.zeros((o.m_wall, ncol), dtype=np.complex128)

@@ -68,14 +68,14 @@ def test_index_one_is_the_identity_and_scatters_nothing():
 
 
 def test_pair_with_combined_densities_is_the_combined_layer():
-    """sigma = -i w eta, tau = eta makes S sigma + D tau the Dirichlet combined layer, so the
-    pair's outside rows reduce to the (separately pinned) Dirichlet oracle's."""
+    """s = -i eta (sigma = -i w eta), tau = eta makes w S s + D tau the Dirichlet combined
+    layer, so the pair's outside rows reduce to the (separately pinned) Dirichlet oracle's."""
     om = 10.0
     x, y, dx, dy = inputs.star(0.3, 0.3, 5).sample(200)
     bd = qd.boundary(x, y, dx, dy)
     rng = np.random.default_rng(5)
     eta = rng.standard_normal(bd.n) + 1j * rng.standard_normal(bd.n)
-    pair = tr.interlace_rows(-1j * om * eta, eta)
+    pair = tr.interlace_rows(-1j * eta, eta)
 
     def close(a, b):
         assert np.linalg.norm(a - b) <= 1e-13 * np.linalg.norm(b)
@@ -100,7 +100,7 @@ def test_pair_with_combined_densities_is_the_combined_layer():
 
 def test_sigma_rows_are_minus_normal_derivatives():
     """The sigma rows of the image blocks, of B and of the right-hand side equal minus a
-    centred finite difference of the field along the normal."""
+    centred finite difference of the field along the normal, divided by w."""
     om = 10.0
     x, y, dx, dy = inputs.star(0.3, 0.3, 5).sample(160)
     bd = qd.boundary(x, y, dx, dy)
@@ -119,21 +119,21 @@ def test_sigma_rows_are_minus_normal_derivatives():
         e0, _ = tr.eval_rows(pts[0], pts[1], bd, ct, om, D, alpha, 0)
         return (e - e0) @ eta
 
-    fd = -(img_field(up) - img_field(dn)) / (2 * h)
+    fd = -(img_field(up) - img_field(dn)) / (2 * h) / om
     rows = (alpha * tr.matrix_a_image(bd, om, D, 1) + tr.matrix_a_image(bd, om, D, -1) / alpha) @ eta
     assert np.linalg.norm(rows[0::2] - fd) < 1e-6 * np.linalg.norm(fd)
 
     def wall_field(pts):
         return tr.eval_rows(pts[0], pts[1], bd, ct, om, D, alpha, 0)[1] @ xi
 
-    fd = -(wall_field(up) - wall_field(dn)) / (2 * h)
+    fd = -(wall_field(up) - wall_field(dn)) / (2 * h) / om
     bl, br = tr.matrix_b_parts(bd, ct, om, D)
     assert np.linalg.norm(((bl + alpha * br) @ xi)[0::2] - fd) < 1e-6 * np.linalg.norm(fd)
 
     th = -0.9
     inc = lambda p: np.exp(1j * om * (math.cos(th) * p[0] + math.sin(th) * p[1]))
     rhs = tr.incident_rhs(bd, om, th)
-    assert np.linalg.norm(rhs[0::2] - (inc(up) - inc(dn)) / (2 * h)) < 1e-6 * om
+    assert np.linalg.norm(rhs[0::2] - (inc(up) - inc(dn)) / (2 * h) / om) < 1e-6
     assert np.max(np.abs(rhs[1::2] + inc((bd.x, bd.y)))) < 1e-14
 
 
