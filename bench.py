@@ -123,6 +123,8 @@ def workload(name):
         w = inputs.workload_wiggly_n10k()
     elif name == "star_n400":
         w = inputs.workload_star_n400()
+    elif name == "transmission_n10k":
+        w = inputs.workload_transmission_n10k()
     else:
         raise SystemExit(f"unknown workload {name}")
     w["name"] = name
@@ -132,7 +134,8 @@ def workload(name):
 def workload_config(w, ws):
     """The `config` object of both arms: the workload by name and size."""
     th = np.asarray(w["thetas"])
-    return {"workload": w["name"], "N": w["N"], "omega": w["omega"], "d": w["d"], "angles": int(th.size),
+    extra = {"problem": "transmission", "index": w["index"]} if w.get("index") else {}
+    return {"workload": w["name"], **extra, "N": w["N"], "omega": w["omega"], "d": w["d"], "angles": int(th.size),
             "bloch_groups": int(th.shape[0]) if th.ndim == 2 else None, "tol": 1e-12,
             "parallelism": f"replicas x{ws}",
             "l2": "inputs larger than L2 (the resident factor and precompute are several GB)"}
@@ -279,7 +282,8 @@ def run_ours(args, ws, rank, local):
     tol = 1e-12
 
     prec = {"fp64": 0, "df": 1, "tc": 2}[args.precision]
-    opts = hbs.default_options(precision=prec)
+    index = float(w.get("index", 0.0))  # > 0: the transmission problem (Sec. 5)
+    opts = hbs.default_options(precision=prec, index=index)
 
     def step(device_inputs: bool):
         if device_inputs:
@@ -350,7 +354,8 @@ def run_ours(args, ws, rank, local):
         #  * FP64 precomputed path: the same library path as the headline, every step in FP64.
         torch.cuda.synchronize()
         t_b = time.perf_counter()
-        h64 = hbs.Handle(gx, gy, gdx, gdy, d, omega, tol, hbs.default_options(precision=0), stream=stream)
+        h64 = hbs.Handle(gx, gy, gdx, gdy, d, omega, tol, hbs.default_options(precision=0, index=index),
+                         stream=stream)
         torch.cuda.synchronize()
         build64_s = time.perf_counter() - t_b
         gflux = [max(flux[g * th2.shape[1]:(g + 1) * th2.shape[1]]) for g in range(n_groups)]
@@ -478,12 +483,19 @@ def oracle_sample(w, n_sample):
     th = float(np.asarray(w["thetas"]).ravel()[0])
     x, y, dx, dy = obs.sample(n_sample)
     opts = rd.options(x, y, omega, d, th)
+    index = w.get("index", 0.0)
     t0 = time.perf_counter()
-    blocks = qd.obstacle_blocks(x, y, dx, dy, omega, d)
-    t1 = time.perf_counter()
-    qd.dense_solve(x, y, dx, dy, omega, d, th, opts, blocks)
+    if index:  # the transmission oracle (Sec. 5): 2 N unknowns
+        from oracle import transmission as tr
+        blocks = tr.obstacle_blocks(x, y, dx, dy, omega, index, d)
+        t1 = time.perf_counter()
+        tr.dense_solve(x, y, dx, dy, omega, index, d, th, opts, blocks)
+    else:
+        blocks = qd.obstacle_blocks(x, y, dx, dy, omega, d)
+        t1 = time.perf_counter()
+        qd.dense_solve(x, y, dx, dy, omega, d, th, opts, blocks)
     t2 = time.perf_counter()
-    size = n_sample + 2 * opts.m
+    size = (2 if index else 1) * n_sample + 2 * opts.m
     # the LAPACK factorization inside that solve, timed alone on a matrix of the same size, so
     # that the extrapolation scales it (size^3) apart from the rest of the angle (linear in N)
     import scipy.linalg
@@ -501,9 +513,10 @@ def oracle_step_seconds(w, n_sample, fill_s, solve_s, lu_s, size):
     each angle refills the periodizer blocks and samples (linear in N) and factors the dense
     system (LU, size^3)."""
     n, n_ang = w["N"], int(np.asarray(w["thetas"]).size)
-    m2 = size - n_sample
+    u = 2 if w.get("index") else 1  # unknowns per node
+    m2 = size - u * n_sample
     fill = fill_s * (n / n_sample) ** 2
-    per_angle = (solve_s - lu_s) * (n / n_sample) + lu_s * ((n + m2) / size) ** 3
+    per_angle = (solve_s - lu_s) * (n / n_sample) + lu_s * ((u * n + m2) / size) ** 3
     return fill + n_ang * per_angle, fill, per_angle
 
 
@@ -715,7 +728,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="complicated_n100k")
+    ap.add_argument("--workload", default="complicated_n100k",
+                    help="complicated_n100k (the headline), wiggly_n10k, star_n400, or transmission_n10k "
+                         "(dielectric obstacles, Sec. 6.3)")
     ap.add_argument("--cpu-sample-n", type=int, nargs="+", default=[400, 1000, 2000])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 plain-path accuracy check")

@@ -83,6 +83,14 @@ typedef struct hbs_options {
   int n_bragg_samples;  /* samples per line for the Bragg DFT (0: automatic) */
   double y0;            /* Bragg sampling height (0: max |y| + d/4) */
   int precision;        /* HBS_PRECISION_FP64 (default), _DOUBLE_FLOAT or _TENSOR */
+  double index;         /* refractive index n of the obstacles, Sec. 5 (0, the default:
+                           sound-soft obstacles, Sec. 2).  n > 0 selects the transmission
+                           problem: two unknowns per boundary node, interlaced
+                           [s_1; tau_1; s_2; ...] (s = sigma / omega the single-layer and tau
+                           the double-layer density), rows in the same order (sigma row:
+                           minus the normal derivative of the field over omega, tau row: its
+                           value).  Its kernel functions are evaluated in FP64 in every
+                           precision mode. */
 } hbs_options;
 
 typedef struct hbs_info_t {
@@ -106,6 +114,8 @@ typedef struct hbs_info_t {
   int pid_row_rank;      /* skeleton rows kept of C_L, C_R and of the Bragg sampling rows */
   double pid_residual;   /* relative error of those decompositions on an independent point sample */
   double nb_residual;    /* relative error of the neighbour ID (Sec. 3.2) on nodes between its candidates */
+  int64_t unknowns;      /* n (sound-soft) or 2 n (transmission): the size of A */
+  double index;          /* refractive index (0: sound-soft) */
 } hbs_info_t;
 
 /* Fill `opts` with the defaults listed above. */
@@ -167,8 +177,9 @@ hbs_status hbs_solve_plain(hbs_handle* h, const double* theta, int64_t n_theta, 
  * Rayleigh-Bloch expansions matched on y = +-h.  Each Bloch phase's rectangular system is
  * solved in the least-squares sense; every step is FP64.  The amplitudes are referred to
  * y = +-y0 as hbs_solve's are (n_wood = 0, t0 = 0 in hbs_result_angle_info).  Meant to
- * cross-check hbs_solve, not tuned for speed.  theta must lie in (-pi, 0), else
- * HBS_ERR_INVALID_ARG; OOM and CUDA as hbs_solve.  Synchronizes the stream.
+ * cross-check hbs_solve, not tuned for speed.  Sound-soft solvers only (options.index =
+ * 0).  theta must lie in (-pi, 0); either violation gives HBS_ERR_INVALID_ARG; OOM and
+ * CUDA as hbs_solve.  Synchronizes the stream.
  */
 hbs_status hbs_solve_proxy(hbs_handle* h, const double* theta, int64_t n_theta, void* stream,
                            hbs_result** out);
@@ -258,7 +269,8 @@ void hbs_server_free(hbs_server* sv);
 /*
  * x = A^{-1} b with the compressed inverse (Sec. 4, telescoping apply),
  * for nrhs columns at once.  b and x are device arrays of N x nrhs complex128,
- * column-major with leading dimension N; they may not alias.
+ * column-major with leading dimension N (N = hbs_info_t.unknowns: interlaced
+ * [sigma; tau] per node for the transmission problem); they may not alias.
  */
 hbs_status hbs_apply_inverse(const hbs_handle* h, const void* b, void* x, int64_t nrhs,
                              void* stream);
@@ -274,6 +286,20 @@ hbs_status hbs_apply_inverse(const hbs_handle* h, const void* b, void* x, int64_
 hbs_status hbs_kernel_block(const hbs_geometry* geom, double omega, int kind, double shift_x,
                             const int64_t* rows, int64_t nr, const int64_t* cols, int64_t nc,
                             void* out, void* stream);
+
+/*
+ * The same for the transmission problem (Sec. 5) with refractive index `index` > 0:
+ * rows and cols index the 2 n interlaced unknowns (2p: s_p = sigma_p / omega, single
+ * layer; 2p + 1: tau_p, double layer) and rows (2p: minus the normal derivative of the
+ * outside minus the inside field, over omega; 2p + 1: its value).  kind 0: the operator A
+ * (identity plus kernel differences between wavenumbers omega and index * omega,
+ * Kapur-Rokhlin weights); kind 1: the image block of the pair shifted by shift_x
+ * (outside wavenumber only).
+ * Errors: INVALID_ARG (as hbs_kernel_block, or index <= 0), CUDA.
+ */
+hbs_status hbs_kernel_block_transmission(const hbs_geometry* geom, double omega, double index, int kind,
+                                         double shift_x, const int64_t* rows, int64_t nr,
+                                         const int64_t* cols, int64_t nc, void* out, void* stream);
 
 /*
  * Interpolative decomposition (Def. 3.1) by column-pivoted QR of a device

@@ -88,23 +88,45 @@ __global__ void k_kernel_block(DevGeom g, int kind, double shift_x, const int64_
   }
 }
 
-// Copy the caller's geometry into device SoA arrays and derive normals and weights.
+// Each node's geometry at both of its unknowns (transmission: out[2p] = out[2p + 1] = in[p]).
+__global__ void k_dup2(const double* in, int64_t n, double* out) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const double v = in[p];
+    out[2 * p] = v;
+    out[2 * p + 1] = v;
+  }
+}
+
+// Copy the caller's geometry into device SoA arrays and derive normals and weights; for the
+// transmission problem (comps = 2) the arrays are laid out per unknown.
 static void load_geometry(Handle& h, const hbs_geometry* geom, cudaStream_t s) {
   const int64_t N = geom->n;
-  h.N = N;
+  h.nodes = N;
+  h.N = N * h.comps;
   h.d = geom->d;
-  h.x.alloc(N); h.y.alloc(N); h.nx.alloc(N); h.ny.alloc(N); h.w.alloc(N);
+  DevBuf<double> x(N), y(N), nx(N), ny(N), w(N);
   DevBuf<double> dx(N), dy(N);
   const cudaMemcpyKind kind = geom->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  HBS_CUDA(cudaMemcpyAsync(h.x.get(), geom->x, N * sizeof(double), kind, s));
-  HBS_CUDA(cudaMemcpyAsync(h.y.get(), geom->y, N * sizeof(double), kind, s));
+  HBS_CUDA(cudaMemcpyAsync(x.get(), geom->x, N * sizeof(double), kind, s));
+  HBS_CUDA(cudaMemcpyAsync(y.get(), geom->y, N * sizeof(double), kind, s));
   HBS_CUDA(cudaMemcpyAsync(dx.get(), geom->dx, N * sizeof(double), kind, s));
   HBS_CUDA(cudaMemcpyAsync(dy.get(), geom->dy, N * sizeof(double), kind, s));
   {
     prof::KScope _ks("k_geom", s);
-    k_geom<<<grid_1d(N), 256, 0, s>>>(dx.get(), dy.get(), h.nx.get(), h.ny.get(), h.w.get(), N);
+    k_geom<<<grid_1d(N), 256, 0, s>>>(dx.get(), dy.get(), nx.get(), ny.get(), w.get(), N);
   }
   HBS_LAUNCH_CHECK("k_geom");
+  if (h.comps == 1) {
+    h.x = std::move(x); h.y = std::move(y); h.nx = std::move(nx); h.ny = std::move(ny); h.w = std::move(w);
+  } else {
+    DevBuf<double>* src[5] = {&x, &y, &nx, &ny, &w};
+    DevBuf<double>* dst[5] = {&h.x, &h.y, &h.nx, &h.ny, &h.w};
+    for (int a = 0; a < 5; ++a) {
+      dst[a]->alloc(2 * N);
+      k_dup2<<<grid_1d(N), 256, 0, s>>>(src[a]->get(), N, dst[a]->get());
+    }
+    HBS_LAUNCH_CHECK("k_dup2");
+  }
   h.hx = h.x.download(s);
   h.hy = h.y.download(s);
 }
@@ -121,6 +143,8 @@ static DevGeom geom_view(const hbs_geometry* geom, double omega, DevBuf<double>&
   DevGeom g;
   g.x = geom->x; g.y = geom->y; g.nx = nx.get(); g.ny = ny.get(); g.w = w.get(); g.n = N; g.omega = omega;
   g.df = false;
+  g.comps = 1;
+  g.omega_in = 0.0;
   return g;
 }
 
@@ -164,6 +188,10 @@ void prepare_handle(Handle& h, const hbs_geometry* geom, double omega, double to
   if (h.opts.precision != HBS_PRECISION_FP64 && h.opts.precision != HBS_PRECISION_DOUBLE_FLOAT &&
       h.opts.precision != HBS_PRECISION_TENSOR)
     throw Error(HBS_ERR_INVALID_ARG, "unsupported precision mode");
+  if (!(h.opts.index >= 0.0) || !std::isfinite(h.opts.index))
+    throw Error(HBS_ERR_INVALID_ARG, "refractive index must be 0 (sound-soft) or positive");
+  h.comps = h.opts.index > 0.0 ? 2 : 1;
+  h.index = h.opts.index;
   h.omega = omega;
   h.tol = tol;
   load_geometry(h, geom, s);
@@ -293,6 +321,7 @@ hbs_status hbs_solve_proxy(hbs_handle* h, const double* theta, int64_t n_theta, 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   StreamScope scope(s);
   hbs_status st = guarded([&] {
+    if (h->h.comps != 1) throw Error(HBS_ERR_INVALID_ARG, "hbs_solve_proxy: sound-soft solvers only");
     GemmModeScope gm(HBS_PRECISION_FP64);
     solve_angles_proxy(h->h, theta, n_theta, r->r, s);
     HBS_CUDA(cudaStreamSynchronize(s));
@@ -332,7 +361,9 @@ hbs_status hbs_result_angle_info(const hbs_result* r, int64_t i, int* n_wood, do
 hbs_status hbs_info(const hbs_handle* hh, hbs_info_t* info) {
   if (!hh || !info) { set_last_error("NULL argument"); return HBS_ERR_INVALID_ARG; }
   const Handle& h = hh->h;
-  info->n = h.N;
+  info->n = h.nodes;
+  info->unknowns = h.N;
+  info->index = h.index;
   info->levels = h.L;
   info->max_rank = h.max_rank;
   info->nb_rank = h.nb_rank;
@@ -381,6 +412,43 @@ hbs_status hbs_kernel_block(const hbs_geometry* geom, double omega, int kind, do
   return guarded([&] {
     DevBuf<double> nx, ny, w;
     DevGeom g = geom_view(geom, omega, nx, ny, w, s);
+    if (nr * nc > 0) {
+      {
+        prof::KScope _ks("k_kernel_block", s);
+        k_kernel_block<<<grid_1d(nr * nc), 256, 0, s>>>(g, kind, shift_x, rows, nr, cols, nc, static_cast<cplx*>(out));
+      }
+      HBS_LAUNCH_CHECK("k_kernel_block");
+    }
+    HBS_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+hbs_status hbs_kernel_block_transmission(const hbs_geometry* geom, double omega, double index, int kind,
+                                         double shift_x, const int64_t* rows, int64_t nr, const int64_t* cols,
+                                         int64_t nc, void* out, void* stream) {
+  if (!geom || !geom->on_device || !rows || !cols || !out || nr < 0 || nc < 0 || (kind != 0 && kind != 1) ||
+      geom->n < 13 || !(index > 0.0) || !std::isfinite(index)) {
+    set_last_error("bad arguments to hbs_kernel_block_transmission (geometry on the device, index > 0)");
+    return HBS_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamScope scope(s);
+  return guarded([&] {
+    const int64_t N = geom->n;
+    DevBuf<double> nx, ny, w;
+    DevGeom g1 = geom_view(geom, omega, nx, ny, w, s);
+    DevBuf<double> arr[5];
+    const double* src[5] = {g1.x, g1.y, g1.nx, g1.ny, g1.w};
+    for (int a = 0; a < 5; ++a) {
+      arr[a].alloc(2 * N);
+      k_dup2<<<grid_1d(N), 256, 0, s>>>(src[a], N, arr[a].get());
+    }
+    HBS_LAUNCH_CHECK("k_dup2");
+    DevGeom g = g1;
+    g.x = arr[0].get(); g.y = arr[1].get(); g.nx = arr[2].get(); g.ny = arr[3].get(); g.w = arr[4].get();
+    g.n = 2 * N;
+    g.comps = 2;
+    g.omega_in = index * omega;
     if (nr * nc > 0) {
       {
         prof::KScope _ks("k_kernel_block", s);

@@ -221,20 +221,90 @@ __device__ __forceinline__ double kr6_weight(int64_t i, int64_t j, int64_t n) {
   }
 }
 
-// Boundary geometry, structure-of-arrays on the device.
+// Boundary geometry, structure-of-arrays on the device, indexed by unknown.
+//
+// Sound-soft obstacles (Sec. 2): one unknown per boundary node.  Transmission problem
+// (Sec. 5): two unknowns per node, interlaced: unknown 2p is s_p, the single-layer density
+// sigma_p = w s_p in units of w, unknown 2p + 1 the double-layer density tau_p, and row 2p
+// (2p + 1) the sigma (tau) row of node p.  Carrying w with the single layer and 1/w with
+// the sigma row (a diagonal similarity) balances the 2 x 2 blocks of the operator.  The
+// arrays hold every node twice, at both of its unknowns, so that the tree, the near lists
+// and every index set of the method address unknowns.
 struct DevGeom {
   const double* x;
   const double* y;
   const double* nx;
   const double* ny;
-  const double* w;  // (2 pi / N) |z'(t_j)|
-  int64_t n;
+  const double* w;  // (2 pi / N_nodes) |z'(t_j)|
+  int64_t n;        // unknowns
   double omega;
-  bool df;  // Hankel series in double-float arithmetic (the thread's double-float mode)
+  bool df;          // Hankel series in double-float arithmetic (the thread's double-float mode)
+  int comps;        // unknowns per node: 1 (sound-soft) or 2 (transmission)
+  double omega_in;  // n omega, the wavenumber inside the obstacles (transmission)
 };
+
+// Field of a unit source of the single layer (c = 0: G = (i/4) H0(k r)) or of the double
+// layer (c = 1: dG/dn_y = (i k/4) H1(k r) (d.n_y)/r) at offset d = x - y (|d| = r), with
+// H0, H1 at k r given, and its gradient in the target x:
+//   grad G       = -(i k/4) H1 d / r,
+//   grad dG/dn_y = (i k/4) [k H0 d (d.n_y)/r^2 + (H1/r) (n_y - 2 d (d.n_y)/r^2)]
+// (from H1' = H0 - H1/z).
+__device__ __forceinline__ void layer_field(double ddx, double ddy, double r, cplx h0, cplx h1, double k, double snx,
+                                            double sny, int c, cplx* v, cplx* gx, cplx* gy) {
+  const double ir = 1.0 / r;
+  const cplx ik4h1 = cmk(-0.25 * k * h1.y, 0.25 * k * h1.x);  // (i k / 4) H1
+  if (c == 0) {
+    *v = cmk(-0.25 * h0.y, 0.25 * h0.x);
+    *gx = cscale(ik4h1, -ddx * ir);
+    *gy = cscale(ik4h1, -ddy * ir);
+    return;
+  }
+  const double cy = (ddx * snx + ddy * sny) * ir;
+  *v = cscale(ik4h1, cy);
+  const cplx a = cscale(cmk(-0.25 * k * k * h0.y, 0.25 * k * k * h0.x), cy * ir);  // multiplies d
+  const cplx b = cscale(ik4h1, ir);
+  *gx = cadd(cscale(a, ddx), cscale(b, snx - 2.0 * ddx * cy * ir));
+  *gy = cadd(cscale(a, ddy), cscale(b, sny - 2.0 * ddy * cy * ir));
+}
+
+// Row functional of the transmission rows (Sec. 5): the tau row of a node takes the value
+// of a field, the sigma row minus its normal derivative divided by w.
+__device__ __forceinline__ cplx row_functional(const DevGeom& g, int64_t i, cplx v, cplx gx, cplx gy) {
+  if (i & 1) return v;
+  const double f = -1.0 / g.omega;
+  return cmk(f * (g.nx[i] * gx.x + g.ny[i] * gy.x), f * (g.nx[i] * gx.y + g.ny[i] * gy.y));
+}
+
+// Transmission: the row of unknown i applied to the source of unknown j placed at
+// (sx, sy), wavenumber k, without quadrature weight (single-layer sources carry w).
+__device__ __forceinline__ cplx pair_entry(const DevGeom& g, int64_t i, double sx, double sy, int64_t j, double k) {
+  const double ddx = g.x[i] - sx, ddy = g.y[i] - sy;
+  const double r = sqrt(ddx * ddx + ddy * ddy);
+  cplx h0, h1, v, gx, gy;
+  hankel01(k * r, &h0, &h1, g.df);
+  layer_field(ddx, ddy, r, h0, h1, k, g.nx[j], g.ny[j], (int)(j & 1), &v, &gx, &gy);
+  if (!(j & 1)) {
+    v = cscale(v, g.omega);
+    gx = cscale(gx, g.omega);
+    gy = cscale(gy, g.omega);
+  }
+  return row_functional(g, i, v, gx, gy);
+}
+
+// Transmission entry A_ij (Sec. 5): the identity on the node's own 2 x 2 block, else the
+// row functional of the outside source minus that of the inside source (the jumps of the
+// matching conditions), with the Kapur-Rokhlin weights of the node distance.
+__device__ __forceinline__ cplx tr_a_entry(const DevGeom& g, int64_t i, int64_t j) {
+  const int64_t p = i >> 1, q = j >> 1;
+  if (p == q) return cmk(i == j ? 1.0 : 0.0, 0.0);
+  const cplx vo = pair_entry(g, i, g.x[j], g.y[j], j, g.omega);
+  const cplx vi = pair_entry(g, i, g.x[j], g.y[j], j, g.omega_in);
+  return cscale(csub(vo, vi), kr6_weight(p, q, g.n >> 1) * g.w[j]);
+}
 
 // Entry A_ij of the Nystrom matrix (Sec. 2.3), including delta_ij / 2.
 __device__ __forceinline__ cplx a_entry(const DevGeom& g, int64_t i, int64_t j) {
+  if (g.comps == 2) return tr_a_entry(g, i, j);
   if (i == j) return cmk(0.5, 0.0);
   cplx k = combined_kernel(g.x[i], g.y[i], g.x[j], g.y[j], g.nx[j], g.ny[j], g.omega, g.df);
   return cscale(k, kr6_weight(i, j, g.n) * g.w[j]);
@@ -242,6 +312,46 @@ __device__ __forceinline__ cplx a_entry(const DevGeom& g, int64_t i, int64_t j) 
 
 // Entry of the image block A_s (source obstacle shifted by shift_x): plain trapezoid weights.
 __device__ __forceinline__ cplx a_image_entry(const DevGeom& g, int64_t i, int64_t j, double shift_x) {
+  if (g.comps == 2) return cscale(pair_entry(g, i, g.x[j] + shift_x, g.y[j], j, g.omega), g.w[j]);
   cplx k = combined_kernel(g.x[i], g.y[i], g.x[j] + shift_x, g.y[j], g.nx[j], g.ny[j], g.omega, g.df);
   return cscale(k, g.w[j]);
+}
+
+// Transmission: field (what = 0), x-derivative (1) or y-derivative (2) at a point
+// (tx, ty) off the boundary of the layer of unknown j placed at (sx, sy), outside
+// wavenumber, without weight (single-layer sources carry w).
+__device__ __forceinline__ cplx pair_source_field(const DevGeom& g, double tx, double ty, double sx, double sy,
+                                                  int64_t j, int what) {
+  const double ddx = tx - sx, ddy = ty - sy;
+  const double r = sqrt(ddx * ddx + ddy * ddy);
+  cplx h0, h1, v, gx, gy;
+  hankel01(g.omega * r, &h0, &h1, g.df);
+  layer_field(ddx, ddy, r, h0, h1, g.omega, g.nx[j], g.ny[j], (int)(j & 1), &v, &gx, &gy);
+  const cplx out = what == 0 ? v : (what == 1 ? gx : gy);
+  return (j & 1) ? out : cscale(out, g.omega);
+}
+
+// Transmission: row functional of unknown i applied to a combined-layer proxy source
+// dG/dn_p - i k G at (px, py) with normal (pnx, pny), wavenumber k.
+__device__ __forceinline__ cplx proxy_row_entry(const DevGeom& g, int64_t i, double px, double py, double pnx,
+                                                double pny, double k) {
+  const double ddx = g.x[i] - px, ddy = g.y[i] - py;
+  const double r = sqrt(ddx * ddx + ddy * ddy);
+  cplx h0, h1, v1, gx1, gy1, v0, gx0, gy0;
+  hankel01(k * r, &h0, &h1, g.df);
+  layer_field(ddx, ddy, r, h0, h1, k, pnx, pny, 1, &v1, &gx1, &gy1);
+  layer_field(ddx, ddy, r, h0, h1, k, pnx, pny, 0, &v0, &gx0, &gy0);
+  const cplx mik = cmk(0.0, -k);
+  return row_functional(g, i, cadd(v1, cmul(mik, v0)), cadd(gx1, cmul(mik, gx0)), cadd(gy1, cmul(mik, gy0)));
+}
+
+// Transmission: value at (tx, ty) of the layer of unknown j (at its node), wavenumber k,
+// without weight (single-layer sources carry w).
+__device__ __forceinline__ cplx layer_value_at(const DevGeom& g, double tx, double ty, int64_t j, double k) {
+  const double ddx = tx - g.x[j], ddy = ty - g.y[j];
+  const double r = sqrt(ddx * ddx + ddy * ddy);
+  cplx h0, h1, v, gx, gy;
+  hankel01(k * r, &h0, &h1, g.df);
+  layer_field(ddx, ddy, r, h0, h1, k, g.nx[j], g.ny[j], (int)(j & 1), &v, &gx, &gy);
+  return (j & 1) ? v : cscale(v, g.omega);
 }

@@ -51,11 +51,14 @@ struct ContourData {
 };
 
 struct Handle {
-  int64_t N = 0;
+  int64_t N = 0;       // unknowns: boundary nodes x comps
+  int64_t nodes = 0;   // boundary nodes
+  int comps = 1;       // unknowns per node: 1 (sound-soft) or 2 (transmission, Sec. 5)
+  double index = 0.0;  // refractive index n of the obstacles (transmission)
   double d = 1.0, omega = 0.0, tol = 0.0;
   hbs_options opts{};
   int L = 0;
-  DevBuf<double> x, y, nx, ny, w;
+  DevBuf<double> x, y, nx, ny, w;             // per unknown (each node at both of its unknowns)
   std::vector<double> hx, hy, hnx, hny, hw;  // host copies (for host-side planning only)
   std::vector<Level> levels;                  // index = level (0 = root)
   int nroot = 0;

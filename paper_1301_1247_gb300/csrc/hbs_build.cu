@@ -171,6 +171,7 @@ __global__ void k_fill_y(const YJob* jobs) {
   extern __shared__ double sprox[];
   const YJob jb = jobs[blockIdx.y];
   const DevGeom& g = jb.g;
+  if (g.comps != 1) return;
   double* pxs = sprox;
   double* pys = sprox + jb.np;
   double* pcs = sprox + 2 * jb.np;
@@ -225,6 +226,58 @@ __global__ void k_fill_y(const YJob* jobs) {
       // field at the proxy of the node's source j
       col[2 * jb.nn + jb.np + p] =
           cscale(combined_from(-q * (dx * g.nx[gj] + dy * g.ny[gj]), h0, h1, g.omega), g.w[gj]);
+    }
+  }
+}
+
+// Rows of Mt per node: 2 nn near rows, then np proxy rows per direction and wavenumber
+// (one wavenumber for sound-soft obstacles, the outside and the inside one for the
+// transmission problem).
+__host__ __device__ __forceinline__ int y_rows(const YJob& y) { return 2 * y.nn + 2 * y.np * y.g.comps; }
+
+// The transmission problem's Mt (Sec. 5): columns are the node's unknowns, rows
+// A(near_r, j) and A(j, near_r) (r < nn), then for each wavenumber k of (w, n w) the
+// combined-layer proxy sources at k acting on the row of unknown j (outside -> in), then
+// for each k the field at the proxy points of unknown j's layer at k (in -> out).  Every
+// far interaction of the operator is a sum of fields of the two wavenumbers, each a
+// Helmholtz field in the proxy disk (in) or a radiating one determined by its values on the
+// circle (out), so the proxies of both wavenumbers span it.
+__global__ void k_fill_y_tr(const YJob* jobs) {
+  extern __shared__ double sprox[];
+  const YJob jb = jobs[blockIdx.y];
+  const DevGeom& g = jb.g;
+  if (g.comps != 2) return;
+  double* pxs = sprox;
+  double* pys = sprox + jb.np;
+  double* pcs = sprox + 2 * jb.np;
+  double* psn = sprox + 3 * jb.np;
+  for (int p = threadIdx.x; p < jb.np; p += blockDim.x) {
+    const double th = 2.0 * HBS_PI * (double)p / (double)jb.np;
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    pxs[p] = jb.cx + jb.R * cs;
+    pys[p] = jb.cy + jb.R * sn;
+    pcs[p] = cs;
+    psn[p] = sn;
+  }
+  __syncthreads();
+  const int m = 2 * jb.nn + 4 * jb.np;
+  const int half = jb.nn + 2 * jb.np;
+  const int64_t tot = (int64_t)half * jb.n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % half), c = (int)(e / half);
+    const int64_t gj = jb.idx[c];
+    cplx* col = jb.mt + (int64_t)c * m;
+    if (r < jb.nn) {
+      const int64_t gi = jb.near[r];
+      col[r] = a_entry(g, gi, gj);
+      col[jb.nn + r] = a_entry(g, gj, gi);
+    } else {
+      const int p = r - jb.nn;
+      const int q = p % jb.np;
+      const double k = p < jb.np ? g.omega : g.omega_in;
+      col[2 * jb.nn + p] = cscale(proxy_row_entry(g, gj, pxs[q], pys[q], pcs[q], psn[q], k), jb.wp);
+      col[2 * jb.nn + 2 * jb.np + p] = cscale(layer_value_at(g, pxs[q], pys[q], gj, k), g.w[gj]);
     }
   }
 }
@@ -437,7 +490,12 @@ DevGeom Handle_geom(const Handle& h) {
   DevGeom g;
   g.x = h.x.get(); g.y = h.y.get(); g.nx = h.nx.get(); g.ny = h.ny.get(); g.w = h.w.get();
   g.n = h.N; g.omega = h.omega;
-  g.df = gemm_double_float();  // double-float Hankel series in the thread's double-float mode
+  g.comps = h.comps;
+  g.omega_in = h.index * h.omega;
+  // double-float Hankel series in the thread's double-float mode; the transmission
+  // operator's kernel differences cancel their leading singular terms, so their Hankel
+  // functions stay in FP64
+  g.df = h.comps == 2 ? false : gemm_double_float();
   return g;
 }
 
@@ -796,14 +854,16 @@ void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s) {
         Level& lv = h.levels[tasks[i].l];
         for (int j = 0; j < lv.count; ++j) {
           const double R = h.opts.proxy_rho * lv.h_rad[j];
-          int np = (int)(2.0 * std::ceil(h.omega * R) + 40.0);
+          // the fastest wavenumber of the operator: w, or n w inside transmission obstacles
+          const double kmax = h.comps == 2 ? std::max(h.omega, h.index * h.omega) : h.omega;
+          int np = (int)(2.0 * std::ceil(kmax * R) + 40.0);
           np = std::max(np, h.opts.n_proxy_min);
           np = (np + 7) / 8 * 8;
           const int nn = (int)hcnt[node0[i] + j];
           yj.push_back({tasks[i].g, lv.idx.get() + lv.off[j], near.get() + noff[node0[i] + j], nullptr, lv.n[j], nn,
                         np, hcirc[3 * (node0[i] + j)], hcirc[3 * (node0[i] + j) + 1], R, 2.0 * HBS_PI * R / np});
           ymt.push_back(ypool);
-          ypool += (int64_t)(2 * nn + 2 * np) * lv.n[j];
+          ypool += (int64_t)y_rows(yj.back()) * lv.n[j];
         }
       }
       DevBuf<cplx> Y(std::max<int64_t>(ypool, 1));
@@ -814,9 +874,17 @@ void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s) {
         int npmax = 0;
         for (const auto& y : yj) npmax = std::max(npmax, y.np);
         const size_t psm = 4 * (size_t)npmax * sizeof(double);
-        if (psm > 48 * 1024)
+        bool any1 = false, any2 = false;
+        for (const auto& y : yj) (y.g.comps == 2 ? any2 : any1) = true;
+        if (psm > 48 * 1024) {
           HBS_CUDA(cudaFuncSetAttribute(k_fill_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
-        launch_jobs_y(dyj, yj.size(), [&](const YJob* p, unsigned ny) { k_fill_y<<<dim3(64, ny), 256, psm, s>>>(p); });
+          HBS_CUDA(cudaFuncSetAttribute(k_fill_y_tr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+        }
+        // each kernel skips the jobs of the other problem
+        if (any1)
+          launch_jobs_y(dyj, yj.size(), [&](const YJob* p, unsigned ny) { k_fill_y<<<dim3(64, ny), 256, psm, s>>>(p); });
+        if (any2)
+          launch_jobs_y(dyj, yj.size(), [&](const YJob* p, unsigned ny) { k_fill_y_tr<<<dim3(64, ny), 256, psm, s>>>(p); });
       }
       HBS_LAUNCH_CHECK("k_fill_y");
       std::vector<CpqrJob> cj;
@@ -826,7 +894,7 @@ void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s) {
         int64_t tpool = 0;
         for (int j = 0; j < lv.count; ++j) {
           const YJob& y = yj[node0[i] + j];
-          const int m = 2 * y.nn + 2 * y.np;
+          const int m = y_rows(y);
           lv.t_off[j] = tpool;
           tpool += (int64_t)std::min(m, lv.n[j]) * lv.n[j];
         }
@@ -834,7 +902,7 @@ void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s) {
         lv.perm.alloc(std::max<int64_t>(lv.ntot, 1));
         for (int j = 0; j < lv.count; ++j) {
           const YJob& y = yj[node0[i] + j];
-          cj.push_back({y.mt, lv.T.get() + lv.t_off[j], lv.perm.get() + lv.off[j], 2 * y.nn + 2 * y.np, lv.n[j],
+          cj.push_back({y.mt, lv.T.get() + lv.t_off[j], lv.perm.get() + lv.off[j], y_rows(y), lv.n[j],
                         (int)cj.size()});
         }
       }

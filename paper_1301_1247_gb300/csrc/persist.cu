@@ -102,6 +102,7 @@ struct Reader {
 template <class Ar>
 void visit(Ar& ar, Handle& h) {
   ar.pod(h.N);
+  ar.pod(h.nodes); ar.pod(h.comps); ar.pod(h.index);
   ar.pod(h.d);
   ar.pod(h.omega);
   ar.pod(h.tol);
@@ -148,7 +149,7 @@ Header make_header() {
   hd.opts_bytes = (uint32_t)sizeof(hbs_options);
   hd.cplx_bytes = (uint32_t)sizeof(cplx);
   hd.int2_bytes = (uint32_t)sizeof(int2);
-  hd.handle_fields = 1;  // layout revision of visit()
+  hd.handle_fields = 2;  // layout revision of visit()
   return hd;
 }
 

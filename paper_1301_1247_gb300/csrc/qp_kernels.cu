@@ -15,6 +15,15 @@ __device__ __forceinline__ cplx sqrt_branch(double omega, cplx k) {
   return cmul(csqrt_principal(cmk(omega - k.x, -k.y)), csqrt_principal(cmk(omega + k.x, k.y)));
 }
 
+// Transmission sigma rows of the wall potentials: minus the normal derivative of
+// e^{i k y} e^{i s |x - x0|} over w, i.e. the value times -i (+-s n_x + k n_y) / w (+ for
+// the left wall, x > x0; - for the right wall).
+__device__ __forceinline__ cplx wall_sigma_factor(const DevGeom& g, int64_t i, cplx s, cplx km, bool left) {
+  const double sx = left ? g.nx[i] : -g.nx[i];
+  const cplx a = cscale(cadd(cscale(s, sx), cscale(km, g.ny[i])), 1.0 / g.omega);
+  return cmk(a.y, -a.x);
+}
+
 // B_L and B_R columns (N x 2M each) for one contour, written into W (ld = N) at
 // columns [col_bl, col_bl + 2M) and [col_br, col_br + 2M).  Optionally combined as
 // B_L + alpha B_R into col_bl only (alpha_only != 0).
@@ -35,6 +44,11 @@ __global__ void k_fill_b(DevGeom g, const cplx* k, const cplx* wk, int M, double
     cplx is2 = cdiv(cmk(0.0, 0.5), s);  // i / (2 s)
     cplx sl = cmul(cmul(el, is2), w), dl = cmul(cscale(el, 0.5), w);
     cplx sr = cmul(cmul(er, is2), w), dr = cmul(cscale(er, -0.5), w);
+    if (g.comps == 2 && !(i & 1)) {
+      const cplx fl = wall_sigma_factor(g, i, s, km, true), fr = wall_sigma_factor(g, i, s, km, false);
+      sl = cmul(sl, fl); dl = cmul(dl, fl);
+      sr = cmul(sr, fr); dr = cmul(dr, fr);
+    }
     if (combine) {
       W[(col_bl + m) * ldw + i] = cadd(sl, cmul(alpha, sr));
       W[(col_bl + M + m) * ldw + i] = cadd(dl, cmul(alpha, dr));
@@ -70,6 +84,10 @@ __global__ void k_fill_c(DevGeom g, const cplx* k, int M, double shift_x, double
     const cplx iw = cmk(0.0, g.omega);
     cplx f = csub(d_hat, cmul(iw, s_hat));
     cplx fn = csub(t_hat, cmul(iw, dstar_hat));
+    if (g.comps == 2) {  // the pair: single-layer columns w [S^; D*^], double-layer [D^; T^]
+      f = (j & 1) ? d_hat : cscale(s_hat, g.omega);
+      fn = (j & 1) ? t_hat : cscale(dstar_hat, g.omega);
+    }
     const double w = g.w[j];
     C[j * ldc + m] = cscale(f, w);
     C[j * ldc + M + m] = cscale(fn, w);
@@ -89,7 +107,9 @@ __global__ void k_fill_samples(DevGeom g, int S, double d, double y0, double shi
     const double ty = (kind == 0 || kind == 2) ? y0 : -y0;
     const double sx = g.x[j] + shift_x, sy = g.y[j], nx = g.nx[j], ny = g.ny[j];
     cplx v;
-    if (kind < 2) {
+    if (g.comps == 2) {
+      v = pair_source_field(g, tx, ty, sx, sy, j, kind < 2 ? 0 : 2);
+    } else if (kind < 2) {
       v = combined_kernel(tx, ty, sx, sy, nx, ny, omega, g.df);
     } else {
       // target y-derivative of dG/dn_y - i w G (see the oracle's derivation):
@@ -166,9 +186,13 @@ __global__ void k_fill_nb(DevGeom g, const int64_t* near_m, int nm, const int64_
     } else {
       const int p = r - nm - npn;
       const double cs = sdir[p], sn = sdir[np + p];
-      cplx gg, dg;
-      proxy_kernels(g.x[i], g.y[i], cx + R * cs, cy + R * sn, cs, sn, g.omega, &gg, &dg, g.df);
-      v = cscale(cadd(dg, cmul(cmk(0.0, -g.omega), gg)), wp);
+      if (g.comps == 2) {
+        v = cscale(proxy_row_entry(g, i, cx + R * cs, cy + R * sn, cs, sn, g.omega), wp);
+      } else {
+        cplx gg, dg;
+        proxy_kernels(g.x[i], g.y[i], cx + R * cs, cy + R * sn, cs, sn, g.omega, &gg, &dg, g.df);
+        v = cscale(cadd(dg, cmul(cmk(0.0, -g.omega), gg)), wp);
+      }
     }
     Mt[i * (int64_t)m + r] = v;
   }
@@ -488,7 +512,8 @@ __device__ __forceinline__ cplx b_entry(const DevGeom& g, const ContourPtrs& cp,
   const cplx s = cp.s[c][m];
   const double xi = g.x[i], yi = g.y[i];
   const double a = side == 0 ? xi + 0.5 * d : 0.5 * d - xi;
-  const cplx e = cexp(cmk(-km.y * yi - s.y * a, km.x * yi + s.x * a));
+  cplx e = cexp(cmk(-km.y * yi - s.y * a, km.x * yi + s.x * a));
+  if (g.comps == 2 && !(i & 1)) e = cmul(e, wall_sigma_factor(g, i, s, km, side == 0));
   if (kind == 0) {
     const cplx si = cp.si[c][m];  // (i / 2) / s
     return cmul(cmul(e, cmk(-0.5 * si.y, 0.5 * si.x)), w);
@@ -509,13 +534,17 @@ __device__ __forceinline__ cplx c_entry(const DevGeom& g, const ContourPtrs& cp,
   cplx base = cexp(cmk(km.y * sy - s.y * ax, -km.x * sy + s.x * ax));  // e^{-i k_m y} e^{i s |x - x0|}
   base = cscale(base, g.w[j] / (4.0 * HBS_PI));
   const cplx iw = cmk(0.0, g.omega);
+  // transmission: w S^, w D*^ (single layer) or D^, T^ (double layer)
+  const bool pair = g.comps == 2, tau = (j & 1) != 0;
   if (kind == 0) {
     cplx s_hat = cmul(cmul(cmk(0.0, 1.0), base), si);
     cplx d_hat = cmul(base, cadd(cmk(-sg * nx, 0.0), cscale(cmul(km, si), ny)));
+    if (pair) return tau ? d_hat : cscale(s_hat, g.omega);
     return csub(d_hat, cmul(iw, s_hat));
   }
   cplx dstar_hat = cscale(base, sg);
   cplx t_hat = cmul(cmul(cmk(0.0, 1.0), base), csub(cscale(s, nx), cscale(km, sg * ny)));
+  if (pair) return tau ? t_hat : cscale(dstar_hat, g.omega);
   return csub(t_hat, cmul(iw, dstar_hat));
 }
 
@@ -528,7 +557,9 @@ __device__ __forceinline__ cplx e_entry(const DevGeom& g, int S, double d, doubl
   const double sx = g.x[j] + (jj - 1) * d, sy = g.y[j], nx = g.nx[j], ny = g.ny[j];
   const double omega = g.omega;
   cplx v;
-  if (kind < 2) {
+  if (g.comps == 2) {
+    v = pair_source_field(g, tx, ty, sx, sy, j, kind < 2 ? 0 : 2);
+  } else if (kind < 2) {
     v = combined_kernel(tx, ty, sx, sy, nx, ny, omega, g.df);
   } else {
     double ddx = tx - sx, ddy = ty - sy;
@@ -603,7 +634,12 @@ __global__ void k_fill_dirs(DevGeom g, double cx, double cy, int K, cplx* out) {
     const int k = (int)(e / g.n);
     double sn, cs;
     sincospi(2.0 * (double)k / (double)K, &sn, &cs);
-    out[e] = cexp_i(g.omega * ((g.x[i] - cx) * cs + (g.y[i] - cy) * sn));
+    cplx v = cexp_i(g.omega * ((g.x[i] - cx) * cs + (g.y[i] - cy) * sn));
+    if (g.comps == 2 && !(i & 1)) {  // transmission sigma row: -(d/dn) / w = -i (n . dir)
+      const double f = -(g.nx[i] * cs + g.ny[i] * sn);
+      v = cmk(-f * v.y, f * v.x);
+    }
+    out[e] = v;
   }
 }
 

@@ -221,11 +221,26 @@ void build_periodizer(Handle& h, cudaStream_t s, bool with_hbs) {
     // wavelength lose nothing.  Every node's interpolation coefficients then follow by
     // least squares against the skeleton columns, t_i = R11^{-1} Q1^H Mt(:, i), which for
     // the candidates is exactly T = R11^{-1} R12 of the QR.
+    // Candidates are whole nodes (both unknowns of a transmission node, whose rows differ).
+    const int comps = h.comps;
+    const int64_t nodes = N / comps;
     const int64_t stride = std::max<int64_t>(1, (N + 4095) / 4096);
-    const int64_t nc = (N + stride - 1) / stride;
+    const int64_t ncn = (nodes + stride - 1) / stride;  // candidate nodes
+    const int64_t nc = ncn * comps;
     DevBuf<cplx> Mc((size_t)m * nc);
-    HBS_CUDA(cudaMemcpy2DAsync(Mc.get(), sizeof(cplx) * m, Mt.get(), sizeof(cplx) * m * stride, sizeof(cplx) * m, nc,
-                               cudaMemcpyDeviceToDevice, s));
+    std::vector<int64_t> cand(nc);
+    for (int64_t c = 0; c < ncn; ++c)
+      for (int u = 0; u < comps; ++u) cand[c * comps + u] = c * stride * comps + u;
+    if (comps == 1) {
+      HBS_CUDA(cudaMemcpy2DAsync(Mc.get(), sizeof(cplx) * m, Mt.get(), sizeof(cplx) * m * stride, sizeof(cplx) * m,
+                                 nc, cudaMemcpyDeviceToDevice, s));
+    } else {
+      DevBuf<int64_t> dcand;
+      dcand.upload(cand, s);
+      prof::KScope _ks("k_gather_cols", s);
+      k_gather_cols<<<grid_1d(m * nc), 256, 0, s>>>(Mt.get(), m, m, dcand.get(), nc, Mc.get(), m);
+      HBS_CUDA(cudaStreamSynchronize(s));  // dcand goes out of scope
+    }
     const int kcap = (int)std::min<int64_t>(std::min<int64_t>(m, nc), 4096);
     DevBuf<int> cperm(nc);
     PqrOut qr;
@@ -237,7 +252,7 @@ void build_periodizer(Handle& h, cudaStream_t s, bool with_hbs) {
     h.nb_rank = l;
     std::vector<int> hpiv = qr.piv.download(s, l);
     std::vector<int64_t> J(l);
-    for (int i = 0; i < l; ++i) J[i] = (int64_t)hpiv[i] * stride;
+    for (int i = 0; i < l; ++i) J[i] = cand[hpiv[i]];
     h.nb_skel.upload(J, s);
     h.Rm.alloc(std::max<int64_t>((int64_t)l * N, 1));
     h.Rp.alloc(std::max<int64_t>((int64_t)l * N, 1));
@@ -272,9 +287,13 @@ void build_periodizer(Handle& h, cudaStream_t s, bool with_hbs) {
       HBS_LAUNCH_CHECK("neighbour interpolation");
       // Check on nodes half-way between candidates: |Mt(:, i) - Mt(:, J) t_i| / |Mt(:, i)|.
       if (stride > 1) {
-        const int64_t nchk = std::min<int64_t>(nc - 1, 4096);
+        const int64_t nchk_n = std::min<int64_t>(ncn - 1, 4096 / comps);
+        const int64_t nchk = nchk_n * comps;
         std::vector<int64_t> chk(nchk);
-        for (int64_t c = 0; c < nchk; ++c) chk[c] = std::min<int64_t>(N - 1, ((c * (nc - 1)) / nchk) * stride + stride / 2);
+        for (int64_t c = 0; c < nchk_n; ++c) {
+          const int64_t node = std::min<int64_t>(nodes - 1, ((c * (ncn - 1)) / nchk_n) * stride + stride / 2);
+          for (int u = 0; u < comps; ++u) chk[c * comps + u] = node * comps + u;
+        }
         DevBuf<int64_t> dchk;
         dchk.upload(chk, s);
         DevBuf<cplx> G((size_t)m * l), Ms((size_t)m * nchk), Ts((size_t)l * nchk), Rec((size_t)m * nchk);
@@ -374,12 +393,20 @@ void build_periodizer(Handle& h, cudaStream_t s, bool with_hbs) {
   }
   const double osc = perim * std::max(omega, h.cK) / (2.0 * M_PI);
   int ns_want = std::max(512, (int)std::ceil(12.0 * osc / 256.0) * 256);
-  const int ns = (int)std::min<int64_t>(N, std::min(ns_want, 16384));
+  // subsamples of whole nodes (both unknowns of a transmission node)
+  const int comps = h.comps;
+  const int64_t nodes = N / comps;
+  const int nsn = (int)std::min<int64_t>(nodes, std::min(ns_want, 16384));
   // check sample: half as many nodes, each half-way between two nodes of the subsample
-  const int ns2 = std::max(1, ns / 2);
+  const int ns2n = std::max(1, nsn / 2);
+  const int ns = nsn * comps, ns2 = ns2n * comps;
   std::vector<int64_t> hsub(ns), hsub2(ns2);
-  for (int i = 0; i < ns; ++i) hsub[i] = (int64_t)((double)i * N / ns);
-  for (int i = 0; i < ns2; ++i) hsub2[i] = std::min<int64_t>(N - 1, (int64_t)(((double)(2 * i) + 0.5) * N / ns));
+  for (int i = 0; i < nsn; ++i)
+    for (int u = 0; u < comps; ++u) hsub[i * comps + u] = (int64_t)((double)i * nodes / nsn) * comps + u;
+  for (int i = 0; i < ns2n; ++i)
+    for (int u = 0; u < comps; ++u)
+      hsub2[i * comps + u] =
+          std::min<int64_t>(nodes - 1, (int64_t)(((double)(2 * i) + 0.5) * nodes / nsn)) * comps + u;
   DevBuf<int64_t> dsub, dsub2;
   dsub.upload(hsub, s);
   dsub2.upload(hsub2, s);
@@ -1486,6 +1513,10 @@ __global__ void k_fill_rhs(DevGeom g, const RhsCol* cols, int ncol, cplx* X) {
     const int c = (int)(e / g.n);
     const RhsCol rc = cols[c];
     cplx v = cexp(cmk(-rc.ky.y * g.y[i], rc.kap * g.x[i] + rc.ky.x * g.y[i]));
+    if (g.comps == 2 && !(i & 1)) {  // transmission sigma row: -(d/dn) / w = -i (kappa n_x + k_y n_y) / w
+      const cplx a = cscale(cadd(cmk(rc.kap * g.nx[i], 0.0), cscale(rc.ky, g.ny[i])), 1.0 / g.omega);
+      v = cmul(cmk(a.y, -a.x), v);
+    }
     X[e] = cscale(v, rc.sign);
   }
 }

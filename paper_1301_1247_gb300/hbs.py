@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "RANK", 5: "W
 EXPORTED = ("hbs_default_options", "hbs_build", "hbs_build_batch", "hbs_solve", "hbs_solve_plain", "hbs_solve_proxy",
             "hbs_bragg_amplitudes",
             "hbs_result_angle_info", "hbs_info", "hbs_save", "hbs_load", "hbs_apply_inverse",
-            "hbs_kernel_block", "hbs_row_id", "hbs_batched_inverse", "hbs_zgemm",
+            "hbs_kernel_block", "hbs_kernel_block_transmission", "hbs_row_id", "hbs_batched_inverse", "hbs_zgemm",
             "hbs_row_id_static",
             "hbs_profile_enable", "hbs_profile_reset", "hbs_profile_get", "hbs_launch_count",
             "hbs_server_create", "hbs_server_add", "hbs_server_remove", "hbs_server_submit", "hbs_server_wait",
@@ -48,7 +48,8 @@ class Options(ctypes.Structure):
                 ("nb_radius", ctypes.c_double), ("nb_proxies", ctypes.c_int), ("m", ctypes.c_int),
                 ("contour_h", ctypes.c_double), ("contour_c", ctypes.c_double), ("contour_w", ctypes.c_double),
                 ("contour_k", ctypes.c_double), ("wood_shift", ctypes.c_double),
-                ("n_bragg_samples", ctypes.c_int), ("y0", ctypes.c_double), ("precision", ctypes.c_int)]
+                ("n_bragg_samples", ctypes.c_int), ("y0", ctypes.c_double), ("precision", ctypes.c_int),
+                ("index", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -60,7 +61,7 @@ class Info(ctypes.Structure):
                 ("wood_t0", ctypes.c_double), ("n_bragg_samples", ctypes.c_int), ("y0", ctypes.c_double),
                 ("nb_radius", ctypes.c_double), ("nb_proxies", ctypes.c_int), ("pid_col_rank", ctypes.c_int),
                 ("pid_row_rank", ctypes.c_int), ("pid_residual", ctypes.c_double),
-                ("nb_residual", ctypes.c_double)]
+                ("nb_residual", ctypes.c_double), ("unknowns", ctypes.c_int64), ("index", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -126,6 +127,8 @@ def lib():
     L.hbs_load.restype = ctypes.c_int
     L.hbs_apply_inverse.argtypes = [vp, vp, vp, i64, vp]
     L.hbs_kernel_block.argtypes = [ctypes.POINTER(Geometry), dbl, ci, dbl, vp, i64, vp, i64, vp, vp]
+    L.hbs_kernel_block_transmission.argtypes = [ctypes.POINTER(Geometry), dbl, dbl, ci, dbl, vp, i64, vp, i64, vp,
+                                                vp]
     L.hbs_row_id.argtypes = [vp, i64, i64, dbl, ctypes.POINTER(ci), vp, vp, vp]
     L.hbs_row_id_static.argtypes = [vp, i64, i64, dbl, ctypes.POINTER(ci), vp, vp, vp]
     L.hbs_zgemm.argtypes = [i64, i64, i64, ctypes.POINTER(dbl), vp, i64, ci, vp, i64, ctypes.POINTER(dbl), vp, i64,
@@ -153,7 +156,8 @@ def lib():
     L.hbs_last_error.restype = ctypes.c_char_p
     for name in ("hbs_build", "hbs_solve", "hbs_solve_plain", "hbs_solve_proxy", "hbs_bragg_amplitudes",
                  "hbs_result_angle_info",
-                 "hbs_info", "hbs_apply_inverse", "hbs_kernel_block", "hbs_row_id", "hbs_row_id_static"):
+                 "hbs_info", "hbs_apply_inverse", "hbs_kernel_block", "hbs_kernel_block_transmission", "hbs_row_id",
+                 "hbs_row_id_static"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -250,6 +254,7 @@ class Handle:
         _check(st, "hbs_build")
         self._p = out
         self.n = n
+        self.unknowns = self.info()["unknowns"]  # n, or 2 n for the transmission problem
 
     @classmethod
     def load(cls, path, stream=None) -> "Handle":
@@ -260,6 +265,7 @@ class Handle:
         h._p = out
         h._keep = []
         h.n = h.info()["n"]
+        h.unknowns = h.info()["unknowns"]
         return h
 
     def save(self, path, stream=None):
@@ -371,6 +377,7 @@ def build_batch(geometries, omegas, d, tol, opts: Options | None = None, stream=
         h._p = ctypes.c_void_p(outs[i])
         h._keep = keep[i]
         h.n = len(keep[i][0])
+        h.unknowns = h.info()["unknowns"]
         res.append(h)
     return res
 
@@ -381,6 +388,16 @@ def kernel_block(x, y, dx, dy, omega, kind, shift_x, rows, cols, out, stream=Non
     _check(lib().hbs_kernel_block(ctypes.byref(g), float(omega), int(kind), float(shift_x), _ptr(rows),
                                   int(rows.numel()), _ptr(cols), int(cols.numel()), _ptr(out), _stream(stream)),
            "hbs_kernel_block")
+
+
+def kernel_block_transmission(x, y, dx, dy, omega, index, kind, shift_x, rows, cols, out, stream=None):
+    """Device-side fill of the transmission operator's entries (Sec. 5) on the interlaced
+    unknowns (kind 0: A; kind 1: the pair's image shifted by shift_x)."""
+    g = Geometry(int(x.numel()), 1.0, _ptr(x).value, _ptr(y).value, _ptr(dx).value, _ptr(dy).value, 1)
+    _check(lib().hbs_kernel_block_transmission(ctypes.byref(g), float(omega), float(index), int(kind),
+                                               float(shift_x), _ptr(rows), int(rows.numel()), _ptr(cols),
+                                               int(cols.numel()), _ptr(out), _stream(stream)),
+           "hbs_kernel_block_transmission")
 
 
 def row_id(mt, m, n, tol, perm, t, stream=None) -> int:

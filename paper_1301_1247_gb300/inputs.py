@@ -137,6 +137,15 @@ def workload_complicated_n100k(seed: int = 0, n_groups: int = 100, q: int = 10):
                 thetas=bloch_grouped_angles(seed + 1, 60.0, 1.0, n_groups, q))
 
 
+def workload_transmission_n10k(seed: int = 0, n_groups: int = 100, q: int = 9):
+    """Transmission grating (Sec. 6.3: the complicated obstacle of Sec. 6.2 with dielectric
+    obstacles): r0 = 0.3 with 60 modes of amplitude <= 0.05, omega = 30, refractive index
+    1.5, N = 10 000 nodes (20 000 unknowns), 900 angles in 100 groups of 9 sharing a Bloch
+    phase."""
+    return dict(obstacle=wiggly(seed, 0.3, 60, 0.05), omega=30.0, d=1.0, N=10000, index=1.5,
+                thetas=bloch_grouped_angles(seed + 1, 30.0, 1.0, n_groups, q))
+
+
 def workload_batch(seed: int = 0, count: int = 256, n_lo: int = 400, n_hi: int = 20000, w_lo: float = 5.0,
                    w_hi: float = 40.0, n_angles: int = 8):
     """Many independent gratings: alternating star and wiggly obstacles with N log-uniform in
