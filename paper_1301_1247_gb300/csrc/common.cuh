@@ -302,6 +302,31 @@ __device__ __forceinline__ cplx tr_a_entry(const DevGeom& g, int64_t i, int64_t 
   return cscale(csub(vo, vi), kr6_weight(p, q, g.n >> 1) * g.w[j]);
 }
 
+// Transmission: A_ij and A_ji together (i, j on different nodes): both share the distance,
+// so one Hankel pair per wavenumber serves the two entries.
+__device__ __forceinline__ void tr_a_entry_pair(const DevGeom& g, int64_t i, int64_t j, cplx* aij, cplx* aji) {
+  const double ddx = g.x[i] - g.x[j], ddy = g.y[i] - g.y[j];
+  const double r = sqrt(ddx * ddx + ddy * ddy);
+  cplx e_ij = cmk(0.0, 0.0), e_ji = cmk(0.0, 0.0);
+  for (int side = 0; side < 2; ++side) {  // outside minus inside
+    const double k = side == 0 ? g.omega : g.omega_in;
+    cplx h0, h1, v, gx, gy;
+    hankel01(k * r, &h0, &h1, g.df);
+    // source j seen from i (offset x_i - x_j), source i seen from j (the opposite offset)
+    layer_field(ddx, ddy, r, h0, h1, k, g.nx[j], g.ny[j], (int)(j & 1), &v, &gx, &gy);
+    if (!(j & 1)) { v = cscale(v, g.omega); gx = cscale(gx, g.omega); gy = cscale(gy, g.omega); }
+    const cplx a = row_functional(g, i, v, gx, gy);
+    layer_field(-ddx, -ddy, r, h0, h1, k, g.nx[i], g.ny[i], (int)(i & 1), &v, &gx, &gy);
+    if (!(i & 1)) { v = cscale(v, g.omega); gx = cscale(gx, g.omega); gy = cscale(gy, g.omega); }
+    const cplx b = row_functional(g, j, v, gx, gy);
+    e_ij = side == 0 ? a : csub(e_ij, a);
+    e_ji = side == 0 ? b : csub(e_ji, b);
+  }
+  const double kw = kr6_weight(i >> 1, j >> 1, g.n >> 1);
+  *aij = cscale(e_ij, kw * g.w[j]);
+  *aji = cscale(e_ji, kw * g.w[i]);
+}
+
 // Entry A_ij of the Nystrom matrix (Sec. 2.3), including delta_ij / 2.
 __device__ __forceinline__ cplx a_entry(const DevGeom& g, int64_t i, int64_t j) {
   if (g.comps == 2) return tr_a_entry(g, i, j);
@@ -354,4 +379,22 @@ __device__ __forceinline__ cplx layer_value_at(const DevGeom& g, double tx, doub
   hankel01(k * r, &h0, &h1, g.df);
   layer_field(ddx, ddy, r, h0, h1, k, g.nx[j], g.ny[j], (int)(j & 1), &v, &gx, &gy);
   return (j & 1) ? v : cscale(v, g.omega);
+}
+
+// Transmission: for node unknown j and a proxy point p (normal (pnx, pny)) at wavenumber
+// k, both proxy rows of the node ID from one Hankel pair: the row functional of j applied
+// to the combined-layer proxy source, and the field at p of unknown j's layer.
+__device__ __forceinline__ void proxy_pair_entries(const DevGeom& g, int64_t j, double px, double py, double pnx,
+                                                   double pny, double k, cplx* row, cplx* field) {
+  const double ddx = g.x[j] - px, ddy = g.y[j] - py;
+  const double r = sqrt(ddx * ddx + ddy * ddy);
+  cplx h0, h1, v1, gx1, gy1, v0, gx0, gy0;
+  hankel01(k * r, &h0, &h1, g.df);
+  layer_field(ddx, ddy, r, h0, h1, k, pnx, pny, 1, &v1, &gx1, &gy1);
+  layer_field(ddx, ddy, r, h0, h1, k, pnx, pny, 0, &v0, &gx0, &gy0);
+  const cplx mik = cmk(0.0, -k);
+  *row = row_functional(g, j, cadd(v1, cmul(mik, v0)), cadd(gx1, cmul(mik, gx0)), cadd(gy1, cmul(mik, gy0)));
+  cplx v, gx, gy;
+  layer_field(-ddx, -ddy, r, h0, h1, k, g.nx[j], g.ny[j], (int)(j & 1), &v, &gx, &gy);
+  *field = (j & 1) ? v : cscale(v, g.omega);
 }

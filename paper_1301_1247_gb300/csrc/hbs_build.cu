@@ -270,14 +270,22 @@ __global__ void k_fill_y_tr(const YJob* jobs) {
     cplx* col = jb.mt + (int64_t)c * m;
     if (r < jb.nn) {
       const int64_t gi = jb.near[r];
-      col[r] = a_entry(g, gi, gj);
-      col[jb.nn + r] = a_entry(g, gj, gi);
+      cplx v1, v2;
+      if ((gi >> 1) == (gj >> 1)) {  // the node's own 2 x 2 block: the identity
+        v1 = v2 = cmk(gi == gj ? 1.0 : 0.0, 0.0);
+      } else {
+        tr_a_entry_pair(g, gi, gj, &v1, &v2);
+      }
+      col[r] = v1;
+      col[jb.nn + r] = v2;
     } else {
       const int p = r - jb.nn;
       const int q = p % jb.np;
       const double k = p < jb.np ? g.omega : g.omega_in;
-      col[2 * jb.nn + p] = cscale(proxy_row_entry(g, gj, pxs[q], pys[q], pcs[q], psn[q], k), jb.wp);
-      col[2 * jb.nn + 2 * jb.np + p] = cscale(layer_value_at(g, pxs[q], pys[q], gj, k), g.w[gj]);
+      cplx row, field;
+      proxy_pair_entries(g, gj, pxs[q], pys[q], pcs[q], psn[q], k, &row, &field);
+      col[2 * jb.nn + p] = cscale(row, jb.wp);
+      col[2 * jb.nn + 2 * jb.np + p] = cscale(field, g.w[gj]);
     }
   }
 }
