@@ -15,12 +15,18 @@
 // Per CTA: 128 x 32 outputs; tensor memory holds 7 levels x (re, im) x 32 columns of FP32
 // accumulators (level l in columns 32 l and 256 + 32 l).  Shared memory is a ring of three
 // stages of 16 k, each with 14 A sub-tiles (re/im x 7 digits, 128 x 16 bf16) and 14 B
-// sub-tiles (32 x 16), in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes),
-// filled by cp.async two stages ahead of the MMAs.  Since B's digit sub-tiles follow one
+// sub-tiles (32 x 16) in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes).  The
+// tensor memory accelerator fills a stage with four bulk tensor copies two stages ahead of
+// the MMAs: the digit planes are a 3-D tensor (k, row, plane), and a box of 8 k x all rows of
+// the tile x 14 planes lands as [plane][row][8 k], i.e. one k-group of every sub-tile, core
+// matrices of consecutive row groups 128 bytes apart; the two k-groups of a stage sit one
+// region apart (the descriptors' leading byte offset).  Since B's digit sub-tiles follow one
 // another, digit i of A meets digits 0..6-i of B in a single MMA of N = 32 (7 - i) columns
-// whose result falls into the levels i..6: one thread issues 28 MMAs per stage (M = 128,
-// K = 16) and commits them to the stage buffer's mbarrier; every wait is bounded (one
-// second) and a timeout is reported through a status word.
+// whose result falls into the levels i..6: one thread issues the copies and 28 MMAs per
+// stage (M = 128, K = 16) and commits them to the stage buffer's mbarrier; every wait is
+// bounded (one second) and a timeout is reported through a status word.
+#include <cuda.h>
+
 #include <algorithm>
 #include <cstdint>
 
@@ -41,9 +47,11 @@ constexpr int OZ_BK = 16;      // k per shared-memory stage (one MMA)
 constexpr int OZ_FLUSH = 128;  // k per exact accumulation period
 constexpr int OZ_RING = 3;     // stages in flight
 constexpr int OZ_NSUB = 2 * OZ_S;                         // sub-tiles per operand and stage
-constexpr int OZ_A_SUB = OZ_BM * OZ_BK * 2;               // bytes of one A sub-tile (4 KB)
-constexpr int OZ_B_SUB = OZ_BN * OZ_BK * 2;               // bytes of one B sub-tile (1 KB)
-constexpr int OZ_STAGE = OZ_NSUB * (OZ_A_SUB + OZ_B_SUB);  // 70 KB
+constexpr int OZ_A_PL = OZ_BM * 16;                       // one plane's k-group of A: 128 rows x 16 B
+constexpr int OZ_B_PL = OZ_BN * 16;                       // one plane's k-group of B: 32 rows x 16 B
+constexpr int OZ_A_KG = OZ_NSUB * OZ_A_PL;                // a k-group of all 14 A planes (28 KB)
+constexpr int OZ_B_KG = OZ_NSUB * OZ_B_PL;                // a k-group of all 14 B planes (7 KB)
+constexpr int OZ_STAGE = 2 * (OZ_A_KG + OZ_B_KG);         // 70 KB: [A kg0 | A kg1 | B kg0 | B kg1]
 constexpr int OZ_SMEM = OZ_RING * OZ_STAGE;                // 210 KB
 
 // Exponent E with |x| < 2^E for the largest |x| given as IEEE bits (sign cleared); -2000
@@ -140,12 +148,12 @@ __global__ void k_oz_digits(const OzOperand* ops) {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Shared-memory matrix descriptor: no swizzle, K-major; LBO = 128 B between the two
-// k-adjacent core matrices of a 16-k sub-tile, SBO = 256 B between 8-row groups.  The start
-// address sits in the low 14 bits (address / 16), so the descriptor of a sub-tile at byte
-// offset o from another is that descriptor plus o / 16.
-__device__ __forceinline__ uint64_t oz_desc(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+// Shared-memory matrix descriptor: no swizzle, K-major; LBO = the byte offset between the two
+// k-adjacent core matrices of a 16-k sub-tile (one k-group region), SBO = 128 B between 8-row
+// groups.  The start address sits in the low 14 bits (address / 16), so the descriptor of a
+// sub-tile at byte offset o from another is that descriptor plus o / 16.
+__device__ __forceinline__ uint64_t oz_desc(uint32_t addr, uint32_t lbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(128 >> 4) << 32) |
          ((uint64_t)1 << 46);
 }
 
@@ -192,26 +200,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+// One bulk tensor copy of a box (8 k from x, rows from y, all 14 planes) of a digit-plane
+// tensor into shared memory at dst, completing on the mbarrier bar.  x is a multiple of 8
+// (16 bytes of bf16), as a tensor copy's innermost coordinate must be.
+__device__ __forceinline__ void oz_tma_load(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(0), "r"(bar)
+      : "memory");
 }
 
-// One stage (16 k from kb) of every digit plane into ring buffer `buf`: 16-byte chunks
-// (8 bf16 along k) into the core-matrix layout [row group][k group][8 rows][16 B].
-__device__ __forceinline__ void oz_load_stage(unsigned char* buf, const unsigned short* Ad, const unsigned short* Bd,
-                                              int64_t aplane, int64_t bplane, int Kpad, int row0, int col0, int kb,
-                                              int tid) {
-  for (int q = tid; q < OZ_NSUB * OZ_BM * 2; q += 128) {
-    const int sub = q / (OZ_BM * 2), rem = q % (OZ_BM * 2), r = rem >> 1, c8 = rem & 1;
-    const unsigned short* src = Ad + sub * aplane + (int64_t)(row0 + r) * Kpad + kb + 8 * c8;
-    cp_async16(smem_u32(buf + sub * OZ_A_SUB + ((r >> 3) * 2 + c8) * 128 + (r & 7) * 16), src);
-  }
-  unsigned char* bb = buf + OZ_NSUB * OZ_A_SUB;
-  for (int q = tid; q < OZ_NSUB * OZ_BN * 2; q += 128) {
-    const int sub = q / (OZ_BN * 2), rem = q % (OZ_BN * 2), r = rem >> 1, c8 = rem & 1;
-    const unsigned short* src = Bd + sub * bplane + (int64_t)(col0 + r) * Kpad + kb + 8 * c8;
-    cp_async16(smem_u32(bb + sub * OZ_B_SUB + ((r >> 3) * 2 + c8) * 128 + (r & 7) * 16), src);
-  }
+// One stage (16 k from kb) of every digit plane of A (rows row0..) and B (rows col0..) into the
+// ring buffer at buf: announce the stage's bytes on its full barrier, then four copies (two
+// k-groups of each operand).
+__device__ __forceinline__ void oz_issue_stage(uint32_t buf, const CUtensorMap* tmA, const CUtensorMap* tmB, int row0,
+                                               int col0, int kb, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(OZ_STAGE) : "memory");
+  oz_tma_load(buf, tmA, kb, row0, bar);
+  oz_tma_load(buf + OZ_A_KG, tmA, kb + 8, row0, bar);
+  oz_tma_load(buf + 2 * OZ_A_KG, tmB, kb, col0, bar);
+  oz_tma_load(buf + 2 * OZ_A_KG + OZ_B_KG, tmB, kb + 8, col0, bar);
 }
 
 // One product of a batch on the tensor cores.  Work items are (tile_m, tile_n, split);
@@ -219,6 +228,8 @@ __device__ __forceinline__ void oz_load_stage(unsigned char* buf, const unsigned
 struct OzJob {
   const unsigned short* Ad;  // digit planes of op(A): 14 x mpad x Kpad
   const unsigned short* Bd;  // digit planes of B^T: 14 x npad x Kpad
+  const CUtensorMap* tmA;    // 3-D tensor maps of Ad and Bd (k, row, plane), boxes 8 x 128 x 14 and 8 x 32 x 14
+  const CUtensorMap* tmB;
   const int* Er;
   const int* Ec;
   int m, n, mpad, npad, Kpad, klen, splits, tiles_m, tiles_n;
@@ -232,26 +243,35 @@ struct OzJob {
 
 // Persistent: CTA b takes items b, b + gridDim.x, ...; tensor memory, the mbarriers and the
 // shared-memory ring stay with the CTA across items (the stage counter G runs on, so every
-// buffer's barrier phase is known).  Each item runs the pipeline of the head comment over
-// its k range and writes its 128 x 32 outputs.
+// buffer's barrier phases are known).  Thread 0 issues the copies and the MMAs of every stage
+// (warp 0 follows it stage by stage); at the end of each 128-k period all four warps meet it
+// at a barrier, wait for the period's MMAs and read the accumulators.  A wait that gives up clears the CTA-wide flag s_ok, which every thread
+// reads after the period's barrier, so all of them stop together.
 __global__ void __launch_bounds__(128, 1) k_oz_mma(const OzJob* jobs, int njobs, int64_t nitems, int* status) {
   extern __shared__ __align__(1024) unsigned char oz_smem[];
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_bar[OZ_RING];
+  __shared__ __align__(8) uint64_t s_bar[OZ_RING];   // MMAs of the buffer's stage done
+  __shared__ __align__(8) uint64_t s_full[OZ_RING];  // the buffer's stage has landed
+  __shared__ int s_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&s_tmem)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid < OZ_RING) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[tid])));
+  if (tid < OZ_RING) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar[tid])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_full[tid])));
+  }
+  if (tid == 0) s_ok = 1;
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
+  const uint32_t ring = smem_u32(oz_smem);
   const int per_flush = OZ_FLUSH / OZ_BK;
-  bool ok = true;
+  bool ok = true;  // CTA-uniform: refreshed from s_ok after every period's barrier
   uint32_t G = 0;  // stages issued by this CTA so far
 
   for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
@@ -267,10 +287,8 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const OzJob* jobs, int njobs,
     const int row0 = (t2 % jb.tiles_m) * OZ_BM, col0 = (t2 / jb.tiles_m) * OZ_BN;
     const int k0 = z * jb.klen, k1 = min(jb.Kpad, k0 + jb.klen);
     const int nst = (k1 - k0) / OZ_BK;
-    const int Kpad = jb.Kpad;
-    const int64_t aplane = (int64_t)jb.mpad * Kpad, bplane = (int64_t)jb.npad * Kpad;
-    const unsigned short* Ad = jb.Ad;
-    const unsigned short* Bd = jb.Bd;
+    const CUtensorMap* tmA = jb.tmA;
+    const CUtensorMap* tmB = jb.tmB;
 
     float Rh[2][OZ_BN], Rl[2][OZ_BN];  // running double-float sums (re, im) of this thread's row
 #pragma unroll
@@ -278,60 +296,79 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const OzJob* jobs, int njobs,
 #pragma unroll
       for (int c = 0; c < OZ_BN; ++c) Rh[p][c] = Rl[p][c] = 0.f;
 
-    // every earlier MMA has completed (the last flush waited for it): all buffers are free
-    oz_load_stage(oz_smem + (G % OZ_RING) * OZ_STAGE, Ad, Bd, aplane, bplane, Kpad, row0, col0, k0, tid);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    if (nst > 1)
-      oz_load_stage(oz_smem + ((G + 1) % OZ_RING) * OZ_STAGE, Ad, Bd, aplane, bplane, Kpad, row0, col0, k0 + OZ_BK,
-                    tid);
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    bool ok0 = true;  // thread 0's own waits in this item
+    if (tid == 0) {
+      // the tensor maps were written by the host before the launch; order their reads by the
+      // copy engine after that
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(tmA))
+                   : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(tmB))
+                   : "memory");
+      // every earlier MMA has completed (the last period's wait covered it): all buffers are free
+      oz_issue_stage(ring + (G % OZ_RING) * OZ_STAGE, tmA, tmB, row0, col0, k0, smem_u32(&s_full[G % OZ_RING]));
+      if (nst > 1)
+        oz_issue_stage(ring + ((G + 1) % OZ_RING) * OZ_STAGE, tmA, tmB, row0, col0, k0 + OZ_BK,
+                       smem_u32(&s_full[(G + 1) % OZ_RING]));
+    }
 
-    for (int st = 0; st < nst && ok; ++st) {
+    for (int st = 0; st < nst; ++st) {
       const uint32_t gs = G + (uint32_t)st;
       const int buf = (int)(gs % OZ_RING);
-      unsigned char* sbuf = oz_smem + buf * OZ_STAGE;
-      asm volatile("cp.async.wait_group 1;" ::: "memory");  // stage st has landed (st + 1 may be in flight)
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint64_t dA = oz_desc(smem_u32(sbuf)), dB = oz_desc(smem_u32(sbuf + OZ_NSUB * OZ_A_SUB));
-        const bool fresh = (st % per_flush) == 0;
-        // digit i of A against digits 0..6-i of B in one MMA: B's digit sub-tiles lie one
-        // after another (32 rows each), and level l = i + j sits in columns 32 l (re) and
-        // 256 + 32 l (im), so the product lands in the levels i..6 at once.
+      if (warp == 0) {
+        if (lane == 0 && ok0) {
+          if (!oz_wait(smem_u32(&s_full[buf]), (gs / OZ_RING) & 1u)) {
+            ok0 = false;
+          } else {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = ring + buf * OZ_STAGE, sb = sa + 2 * OZ_A_KG;
+            const uint64_t dA = oz_desc(sa, OZ_A_KG), dB = oz_desc(sb, OZ_B_KG);
+            const bool fresh = (st % per_flush) == 0;
+            // digit i of A against digits 0..6-i of B in one MMA: B's digit planes lie one after
+            // another (32 rows each), and level l = i + j sits in columns 32 l (re) and
+            // 256 + 32 l (im), so the product lands in the levels i..6 at once.
 #pragma unroll
-        for (int i = 0; i < OZ_S; ++i) {
-          const int N = OZ_BN * (OZ_S - i);
-          const uint32_t ip = oz_idesc(false, N), in = oz_idesc(true, N);
-          const uint64_t ar = dA + (uint64_t)(i * (OZ_A_SUB >> 4)), ai = dA + (uint64_t)((OZ_S + i) * (OZ_A_SUB >> 4));
-          const uint64_t br = dB, bi = dB + (uint64_t)(OZ_S * (OZ_B_SUB >> 4));
-          const uint32_t dre = tmem + OZ_BN * i, dim = tmem + 256 + OZ_BN * i;
-          const uint32_t first = (fresh && i == 0) ? 0u : 1u;
-          oz_mma(dre, ar, br, ip, first);  // re += Ar Br
-          oz_mma(dre, ai, bi, in, 1u);     // re -= Ai Bi
-          oz_mma(dim, ar, bi, ip, first);  // im += Ar Bi
-          oz_mma(dim, ai, br, ip, 1u);     // im += Ai Br
+            for (int i = 0; i < OZ_S; ++i) {
+              const int N = OZ_BN * (OZ_S - i);
+              const uint32_t ip = oz_idesc(false, N), in = oz_idesc(true, N);
+              const uint64_t ar = dA + (uint64_t)(i * (OZ_A_PL >> 4)), ai = dA + (uint64_t)((OZ_S + i) * (OZ_A_PL >> 4));
+              const uint64_t br = dB, bi = dB + (uint64_t)(OZ_S * (OZ_B_PL >> 4));
+              const uint32_t dre = tmem + OZ_BN * i, dim = tmem + 256 + OZ_BN * i;
+              const uint32_t first = (fresh && i == 0) ? 0u : 1u;
+              oz_mma(dre, ar, br, ip, first);  // re += Ar Br
+              oz_mma(dre, ai, bi, in, 1u);     // re -= Ai Bi
+              oz_mma(dim, ar, bi, ip, first);  // im += Ar Bi
+              oz_mma(dim, ai, br, ip, 1u);     // im += Ai Br
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&s_bar[buf]))
+                         : "memory");
+            // refill the buffer of stage st - 1 with stage st + 2 once its MMAs are done
+            if (st + 2 < nst) {
+              const uint32_t pg = gs - 1;
+              if (st >= 1 && !oz_wait(smem_u32(&s_bar[pg % OZ_RING]), (pg / OZ_RING) & 1u)) {
+                ok0 = false;
+              } else {
+                const uint32_t nb = (gs + 2) % OZ_RING;
+                oz_issue_stage(ring + nb * OZ_STAGE, tmA, tmB, row0, col0, k0 + (st + 2) * OZ_BK,
+                               smem_u32(&s_full[nb]));
+              }
+            }
+          }
+          if (!ok0) atomicExch(&s_ok, 0);
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&s_bar[buf]))
-                     : "memory");
+        __syncwarp();
       }
-      __syncwarp();
-      // refill the buffer of stage st - 1 with stage st + 2 once its MMAs are done
-      if (st + 2 < nst) {
-        if (st >= 1) {
-          const uint32_t pg = gs - 1;
-          if (!oz_wait(smem_u32(&s_bar[pg % OZ_RING]), (pg / OZ_RING) & 1u)) ok = false;
-        }
-        oz_load_stage(oz_smem + ((gs + 2) % OZ_RING) * OZ_STAGE, Ad, Bd, aplane, bplane, Kpad, row0, col0,
-                      k0 + (st + 2) * OZ_BK, tid);
-      }
-      asm volatile("cp.async.commit_group;" ::: "memory");  // possibly empty: keeps the group count uniform
       if ((st % per_flush) == per_flush - 1 || st == nst - 1) {
-        if (!oz_wait(smem_u32(&s_bar[buf]), (gs / OZ_RING) & 1u)) ok = false;
+        // thread 0 arrives here only after committing this stage's MMAs, so the wait below
+        // is for the buffer's current phase (a parity wait tells only two phases apart: a
+        // warp running ahead of the issuing thread would see an older phase of the same
+        // parity complete)
+        __syncthreads();
+        const bool w = oz_wait(smem_u32(&s_bar[buf]), (gs / OZ_RING) & 1u);
+        if (!w) atomicExch(&s_ok, 0);
+        __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) {
+        if (w) {
           // T = sum_l 2^{-7 l} S_l (Horner from l = 6), R += T, in double-float
           const uint32_t lanebase = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
@@ -362,10 +399,12 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const OzJob* jobs, int njobs,
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();  // tensor memory may be overwritten by the next period's MMAs
+        ok = s_ok != 0;
+        __syncthreads();  // every thread has read the flag before any can clear it again
+        if (!ok) break;
       }
     }
     G += (uint32_t)nst;
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
     // ---- epilogue: this item's 128 x 32 outputs (row of this thread)
     const int row = row0 + warp * 32 + lane;
     if (row < jb.m && ok) {
@@ -390,9 +429,12 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const OzJob* jobs, int njobs,
       }
     }
   }
-  if (!ok) {  // a wait gave up: let the MMAs in flight drain (bounded) before freeing tensor memory
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (!ok && tid == 0) {
+    // a wait gave up: let the copies and MMAs in flight drain (bounded) before freeing
+    // tensor memory and leaving the shared memory they write
     for (int b = 0; b < OZ_RING; ++b) {
+      oz_wait(smem_u32(&s_full[b]), 0u);
+      oz_wait(smem_u32(&s_full[b]), 1u);
       oz_wait(smem_u32(&s_bar[b]), 0u);
       oz_wait(smem_u32(&s_bar[b]), 1u);
     }
@@ -418,6 +460,39 @@ __global__ void k_oz_reduce(const cplx* W, int m, int n, int splits, cplx beta, 
 }
 
 }  // namespace
+
+// cuTensorMapEncodeTiled from the driver (through the runtime's entry-point query, so the
+// library needs no link to the driver library).
+typedef CUresult (*TmapEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static TmapEncodeFn tmap_encoder() {
+  static TmapEncodeFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    HBS_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || p == nullptr)
+      throw Error(HBS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    return reinterpret_cast<TmapEncodeFn>(p);
+  }();
+  return fn;
+}
+
+// Tensor map of one operand's digit planes (14 planes of rows_pad x Kpad bf16, k contiguous)
+// as a 3-D tensor (k, row, plane) with boxes of 8 k x box_rows x 14 planes.  The driver checks
+// the base (16-byte aligned), the strides (multiples of 16 bytes) and the box; a failure is an
+// error here, before any launch.
+static void encode_planes(CUtensorMap* m, const unsigned short* base, int Kpad, int rows_pad, int box_rows) {
+  const cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)rows_pad, (cuuint64_t)OZ_NSUB};
+  const cuuint64_t strides[2] = {(cuuint64_t)Kpad * 2, (cuuint64_t)Kpad * 2 * (cuuint64_t)rows_pad};
+  const cuuint32_t box[3] = {8, (cuuint32_t)box_rows, (cuuint32_t)OZ_NSUB};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = tmap_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<unsigned short*>(base), dims,
+                                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    throw Error(HBS_ERR_CUDA, "cuTensorMapEncodeTiled failed (CUresult " + std::to_string((int)r) + ")");
+}
 
 // Products worth the tensor cores: enough k for the digit planes to pay and enough rows for
 // the 128-row tiles.  (Routing the leaf products of the sweeps, k ~ 50, here as well was
@@ -524,6 +599,20 @@ void ozaki_gemm_batched(const std::vector<GemmJob>& js, cudaStream_t s) {
     }
   }
   HBS_LAUNCH_CHECK("k_oz_digits");
+  // the digit planes' tensor maps, two per product, in device memory (128-byte aligned)
+  std::vector<CUtensorMap> maps(2 * (size_t)nj);
+  for (int q = 0; q < nj; ++q) {
+    const OzJob& o = oj[q];
+    encode_planes(&maps[2 * q], o.Ad, o.Kpad, o.mpad, OZ_BM);
+    encode_planes(&maps[2 * q + 1], o.Bd, o.Kpad, o.npad, OZ_BN);
+  }
+  DevBuf<CUtensorMap> dmaps;
+  dmaps.upload(maps, s);
+  if (reinterpret_cast<uintptr_t>(dmaps.get()) % 128 != 0) throw Error(HBS_ERR_INTERNAL, "tensor maps misaligned");
+  for (int q = 0; q < nj; ++q) {
+    oj[q].tmA = dmaps.get() + 2 * q;
+    oj[q].tmB = dmaps.get() + 2 * q + 1;
+  }
   DevBuf<OzJob> dj(nj);
   HBS_CUDA(cudaMemcpyAsync(dj.get(), oj.data(), nj * sizeof(OzJob), cudaMemcpyHostToDevice, s));
   {

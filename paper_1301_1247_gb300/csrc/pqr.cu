@@ -843,7 +843,7 @@ void pqr_solve_r11(const cplx* A, int64_t m, const PqrOut& qr, int job, int k, c
   const int* piv = qr.piv.get() + qr.koff[job];
   const cplx* beta = qr.beta.get() + qr.koff[job];
   prof::KScope _ks("k_tsolve_cols", s, 4.0 * k * (double)k * ncols, 0.0);
-  if (k <= 256) {
+  if (k <= 512) {
     DevBuf<cplx> Rc((size_t)k * k), invd(k);
     k_r11_cols<<<std::max(1, std::min(4096, (k * k + 255) / 256)), 256, 0, s>>>(A, m, piv, beta, k, Rc.get(),
                                                                                  invd.get());
@@ -855,7 +855,9 @@ void pqr_solve_r11(const cplx* A, int64_t m, const PqrOut& qr, int job, int k, c
       case 5: launch_tsolve_reg<5>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
       case 6: launch_tsolve_reg<6>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
       case 7: launch_tsolve_reg<7>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
-      default: launch_tsolve_reg<8>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
+      case 8: launch_tsolve_reg<8>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
+      case 9: case 10: case 11: case 12: launch_tsolve_reg<12>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
+      default: launch_tsolve_reg<16>(Rc.get(), invd.get(), k, W, ldw, ncols, s); break;
     }
   } else {
     DevBuf<cplx> R((size_t)k * k);
@@ -1066,6 +1068,8 @@ void pqr_run(const std::vector<PqrSpec>& specs_in, double tol, cudaStream_t s, P
       case 6: k_pqr_tsolve_reg<6><<<grid, 256, 0, s>>>(dj.get()); break;
       case 7: k_pqr_tsolve_reg<7><<<grid, 256, 0, s>>>(dj.get()); break;
       case 8: k_pqr_tsolve_reg<8><<<grid, 256, 0, s>>>(dj.get()); break;
+      case 9: case 10: case 11: case 12: k_pqr_tsolve_reg<12><<<grid, 256, 0, s>>>(dj.get()); break;
+      case 13: case 14: case 15: case 16: k_pqr_tsolve_reg<16><<<grid, 256, 0, s>>>(dj.get()); break;
       default: k_pqr_tsolve<<<grid, kNT, 0, s>>>(dj.get()); break;
     }
   }
