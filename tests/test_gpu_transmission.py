@@ -150,3 +150,37 @@ def test_plain_path_and_compressed_inverse():
     rows = np.unique(np.concatenate([rng.integers(0, n2, 200), [0, 1, n2 - 2, n2 - 1]]))
     for k in range(2):
         assert relerr(amat[rows] @ sol[k], rhs[k][rows]) < 1e-10
+
+
+def test_batch_build_and_server():
+    """Transmission solvers built in one batch (every tree level of every grating in the same
+    launches) solve like separate builds, the smallest like the dense oracle, and the request
+    server answers single angles on them with the same amplitudes."""
+    hbs = require_lib()
+    specs = [(inputs.paper_star(), 300, 10.0), (inputs.wiggly(1, 0.35, 20, 0.03), 1200, 25.0),
+             (inputs.star(0.25, 0.2, 3), 600, 8.0)]
+    geoms = [obs.sample(n) for obs, n, _ in specs]
+    omegas = [om for _, _, om in specs]
+    index = 1.4
+    opts = hbs.default_options(index=index)
+    batch = hbs.build_batch(geoms, omegas, D, 1e-12, opts)
+    th = inputs.uniform_angles(5, 6, -math.pi / 2 + 0.05, -0.1)
+    for i, (g, om) in enumerate(zip(geoms, omegas)):
+        assert batch[i].unknowns == 2 * len(g[0])
+        alone = hbs.Handle(*g, D, om, 1e-12, opts)
+        rb, ra = batch[i].solve(th), alone.solve(th)
+        for a in range(len(th)):
+            _, c1, d1, _ = rb.bragg(a)
+            _, c2, d2, _ = ra.bragg(a)
+            assert relerr(np.concatenate([c1, d1]), np.concatenate([c2, d2])) < 1e-11, (i, a)
+    _compare(batch[0].solve(th[:3]), geoms[0], omegas[0], index, th[:3], 1e-10)
+    sv = hbs.Server(hbm_budget_bytes=0, slots=2, max_batch=16)
+    try:
+        gids = [sv.add(h) for h in batch]
+        reqs = [(i, a, sv.submit(gids[i], float(th[a]))) for i in range(len(batch)) for a in range(len(th))]
+        for i, a, rid in reqs:
+            _, c, d, _ = sv.wait(rid, 120.0)
+            _, c2, d2, _ = batch[i].solve([th[a]]).bragg(0)
+            assert relerr(np.concatenate([c, d]), np.concatenate([c2, d2])) < 1e-11, (i, a)
+    finally:
+        sv.close()
