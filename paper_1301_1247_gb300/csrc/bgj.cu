@@ -276,16 +276,14 @@ int bgj_panel_width(int nmax, int cs) {
 
 template <int CS>
 static void launch_bgj_panel(const BgjJob* dj, int nj, int c0, int b, size_t smem, cudaStream_t s) {
-  if (smem > 48 * 1024)
-    HBS_CUDA(cudaFuncSetAttribute(k_bgj_panel<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HBS_CUDA(raise_smem_limit((const void*)k_bgj_panel<CS>, smem));
   k_bgj_panel<CS><<<(unsigned)(nj * CS), kCNT, smem, s>>>(dj, c0, b);
 }
 
 // Clusters of this launch shape the device can hold at once (0: it cannot run one).
 template <int CS>
 static int bgj_max_clusters(size_t smem) {
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(k_bgj_panel<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (raise_smem_limit((const void*)k_bgj_panel<CS>, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -402,8 +400,7 @@ void bgj_run(const std::vector<std::pair<cplx*, int>>& mats, int cs, cudaStream_
     prof::KScope _ks("k_bgj_unpermute", s);
     const unsigned bx = (unsigned)std::max(1, 1216 / nj);
     const size_t sm = (size_t)nmax * sizeof(int);
-    if (sm > 48 * 1024)
-      HBS_CUDA(cudaFuncSetAttribute(k_bgj_unpermute, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HBS_CUDA(raise_smem_limit((const void*)k_bgj_unpermute, sm));
     k_bgj_unpermute<<<dim3(bx, nj), 256, sm, s>>>(dj.get());
     k_bgj_copy<<<dim3(bx, nj), 256, 0, s>>>(dj.get());
   }

@@ -5,9 +5,11 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <mutex>
 #include <stdexcept>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/hbsqp.h"
@@ -35,6 +37,24 @@ cudaStream_t& current_stream();
 // Fault injection for tests of the error paths (hbs_fault_inject): true when the caller's
 // device allocation is the one chosen to fail; the largest rank an ID may reach (0 = none).
 bool injected_alloc_failure();
+
+// Raise a kernel's limit on dynamic shared memory to at least `bytes` (cudaFuncSetAttribute)
+// on the current device.  The limit only ever grows, under a lock: two host threads that
+// launch the same kernel with different sizes (the build's two streams) cannot lower it
+// between another's occupancy query and its launch.  Returns the runtime's status.
+inline cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[{dev, fn}];
+  if (bytes <= 48 * 1024 || bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 int injected_rank_cap();
 
 // Owning device allocation (stream-ordered cudaMallocAsync / cudaFreeAsync on the

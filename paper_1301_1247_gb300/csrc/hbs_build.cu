@@ -103,17 +103,19 @@ __global__ void k_node_circles(const CircleJob* jobs) {
 }
 
 // Near lists: active points of other nodes of the level (same solver) inside a node's
-// proxy circle.  One block per node scans the level's active points in order, so the list
-// order is deterministic.  With `out` == nullptr only the count is produced.
+// proxy circle.  One block per node scans, in increasing position, the ranges of the level's
+// active points that belong to candidate nodes (those whose enclosing circle meets the proxy
+// circle: no point of another node can be near), so the list order is deterministic and the
+// same as a scan of every point.  With `out` == nullptr only the count is produced.
 struct NearJob {
   const double* x;
   const double* y;
-  const int64_t* idx;      // the level's active points
-  int64_t ntot;
-  int64_t own_lo, own_hi;  // this node's range in idx
+  const int64_t* idx;       // the level's active points
+  const longlong2* ranges;  // position ranges [x, y) in idx to scan, increasing, the node's own excluded
+  int nranges;
   double cx, cy, R2;
-  int64_t* count;          // one element
-  int64_t* out;            // the node's near list, or nullptr
+  int64_t* count;           // one element
+  int64_t* out;             // the node's near list, or nullptr
 };
 
 __global__ void k_near(const NearJob* jobs) {
@@ -123,11 +125,12 @@ __global__ void k_near(const NearJob* jobs) {
   if (threadIdx.x == 0) base = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t p0 = 0; p0 < jb.ntot; p0 += blockDim.x) {
+  for (int rg = 0; rg < jb.nranges; ++rg)
+  for (int64_t p0 = jb.ranges[rg].x; p0 < jb.ranges[rg].y; p0 += blockDim.x) {
     const int64_t p = p0 + threadIdx.x;
     bool f = false;
     int64_t g = 0;
-    if (p < jb.ntot && (p < jb.own_lo || p >= jb.own_hi)) {
+    if (p < jb.ranges[rg].y) {
       g = jb.idx[p];
       const double ddx = jb.x[g] - jb.cx, ddy = jb.y[g] - jb.cy;
       f = ddx * ddx + ddy * ddy < jb.R2;
@@ -545,10 +548,7 @@ std::vector<int> batched_id(std::vector<CpqrJob>& jobs, double tol, cudaStream_t
     size_t sm = (size_t)maxn * (2 * sizeof(double) + sizeof(int));
     // double-float updates on handles built with double-float precision
     const bool df = gemm_double_float();
-    if (sm > 48 * 1024) {
-      if (df) HBS_CUDA(cudaFuncSetAttribute(k_cpqr<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      else HBS_CUDA(cudaFuncSetAttribute(k_cpqr<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    }
+    HBS_CUDA(raise_smem_limit(df ? (const void*)k_cpqr<256, true> : (const void*)k_cpqr<256, false>, sm));
     {
       prof::KScope _ks("k_cpqr", s);
       if (df) k_cpqr<256, true><<<(unsigned)small.size(), 256, sm, s>>>(dj.get(), dr.get(), tol, 1 << 30);
@@ -821,6 +821,51 @@ void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s) {
     DevBuf<int64_t> near;
     {
       DevBuf<int64_t> cnt(nodes);
+      // candidate ranges per node: the nodes whose enclosing circle meets its proxy circle,
+      // found by a sweep over the centres sorted in x (window: the proxy radius plus the
+      // level's largest node radius)
+      std::vector<longlong2> hranges;
+      std::vector<int64_t> rbeg(nodes + 1, 0);
+      for (size_t i = 0; i < tasks.size(); ++i) {
+        Level& lv = tasks[i].h->levels[tasks[i].l];
+        const double rho = tasks[i].h->opts.proxy_rho;
+        const double* hc = hcirc.data() + 3 * node0[i];
+        std::vector<int> order(lv.count);
+        std::iota(order.begin(), order.end(), 0);
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return hc[3 * a] < hc[3 * b]; });
+        std::vector<double> xs(lv.count);
+        double rmax = 0.0;
+        for (int q = 0; q < lv.count; ++q) {
+          xs[q] = hc[3 * order[q]];
+          rmax = std::max(rmax, hc[3 * q + 2]);
+        }
+        std::vector<int> cand;
+        for (int j = 0; j < lv.count; ++j) {
+          const double R = rho * lv.h_rad[j];
+          // a point of node c lies within r_c of c's centre; the margin covers the rounding
+          // of the computed radii
+          const double reach = R + rmax * (1.0 + 1e-9) + 1e-12;
+          const double cxj = hc[3 * j], cyj = hc[3 * j + 1];
+          cand.clear();
+          for (auto it = std::lower_bound(xs.begin(), xs.end(), cxj - reach); it != xs.end() && *it <= cxj + reach;
+               ++it) {
+            const int c = order[it - xs.begin()];
+            if (c == j) continue;
+            const double lim = R + hc[3 * c + 2] * (1.0 + 1e-9) + 1e-12;
+            if (std::hypot(hc[3 * c] - cxj, hc[3 * c + 1] - cyj) < lim) cand.push_back(c);
+          }
+          std::sort(cand.begin(), cand.end());
+          for (int c : cand) {
+            const int64_t lo = lv.off[c], hi = lv.off[c] + lv.n[c];
+            if (hi <= lo) continue;
+            if ((int64_t)hranges.size() > rbeg[node0[i] + j] && hranges.back().y == lo) hranges.back().y = hi;
+            else hranges.push_back(make_longlong2(lo, hi));
+          }
+          rbeg[node0[i] + j + 1] = (int64_t)hranges.size();
+        }
+      }
+      DevBuf<longlong2> dranges;
+      dranges.upload(hranges, s);
       std::vector<NearJob> nj;
       for (size_t i = 0; i < tasks.size(); ++i) {
         Handle& h = *tasks[i].h;
@@ -828,9 +873,9 @@ void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s) {
         const double rho = h.opts.proxy_rho;
         for (int j = 0; j < lv.count; ++j) {
           const double R = rho * lv.h_rad[j];
-          nj.push_back({h.x.get(), h.y.get(), lv.idx.get(), lv.ntot, lv.off[j], lv.off[j] + lv.n[j],
-                        hcirc[3 * (node0[i] + j)], hcirc[3 * (node0[i] + j) + 1], R * R, cnt.get() + node0[i] + j,
-                        nullptr});
+          const int64_t q = node0[i] + j;
+          nj.push_back({h.x.get(), h.y.get(), lv.idx.get(), dranges.get() + rbeg[q], (int)(rbeg[q + 1] - rbeg[q]),
+                        hcirc[3 * q], hcirc[3 * q + 1], R * R, cnt.get() + q, nullptr});
         }
       }
       DevBuf<NearJob> dnj = upload_jobs(nj, s);
@@ -885,8 +930,8 @@ void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s) {
         bool any1 = false, any2 = false;
         for (const auto& y : yj) (y.g.comps == 2 ? any2 : any1) = true;
         if (psm > 48 * 1024) {
-          HBS_CUDA(cudaFuncSetAttribute(k_fill_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
-          HBS_CUDA(cudaFuncSetAttribute(k_fill_y_tr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+          HBS_CUDA(raise_smem_limit((const void*)k_fill_y, psm));
+          HBS_CUDA(raise_smem_limit((const void*)k_fill_y_tr, psm));
         }
         // each kernel skips the jobs of the other problem
         if (any1)

@@ -293,8 +293,7 @@ static int pgj_grid(size_t smem) {
     HBS_CUDA(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
     return sm;
   }();
-  if (smem > 48 * 1024)
-    HBS_CUDA(cudaFuncSetAttribute(k_pgj<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HBS_CUDA(raise_smem_limit((const void*)k_pgj<DF>, smem));
   int per_sm = 0;
   HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pgj<DF>, kNT, smem));
   if (per_sm < 1) throw Error(HBS_ERR_CUDA, "persistent Gauss-Jordan kernel does not fit on an SM");
@@ -368,8 +367,7 @@ void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, con
   {
     prof::KScope _ks("k_pgj_unpivot", s);
     const size_t sm = (size_t)nmax * sizeof(int);
-    if (sm > 48 * 1024)
-      HBS_CUDA(cudaFuncSetAttribute(k_pgj_unpivot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HBS_CUDA(raise_smem_limit((const void*)k_pgj_unpivot, sm));
     k_pgj_unpivot<<<dim3(std::max(1, 1216 / nj), nj), kNT, sm, s>>>(dj.get(), nmax);
     k_pgj_copy<<<dim3(std::max(1, 1216 / nj), nj), 256, 0, s>>>(dj.get());
   }

@@ -940,8 +940,7 @@ static int pqr_grid(size_t smem) {
     HBS_CUDA(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
     return sm;
   }();
-  if (smem > 48 * 1024)
-    HBS_CUDA(cudaFuncSetAttribute(k_pqr<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HBS_CUDA(raise_smem_limit((const void*)k_pqr<DF>, smem));
   int per_sm = 0;
   HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pqr<DF>, kNT, smem));
   if (per_sm < 1) throw Error(HBS_ERR_CUDA, "persistent QR kernel does not fit on an SM");

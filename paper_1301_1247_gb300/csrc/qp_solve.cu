@@ -210,8 +210,7 @@ void build_periodizer(Handle& h, cudaStream_t s, bool with_hbs) {
     {
       prof::KScope _ks("k_fill_nb", s);
       const size_t dsm = 2 * (size_t)np * sizeof(double);
-      if (dsm > 48 * 1024)
-        HBS_CUDA(cudaFuncSetAttribute(k_fill_nb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+      HBS_CUDA(raise_smem_limit((const void*)k_fill_nb, dsm));
       k_fill_nb<<<grid_1d(m * N), 256, dsm, s>>>(g, dnm.get(), nm, dnp.get(), npn, d, cx, cy, R, np, wp, Mt.get());
     }
     HBS_LAUNCH_CHECK("k_fill_nb");
@@ -1415,8 +1414,7 @@ static void schur_solve(const Dims& D, const std::vector<GroupJob>& gjobs, const
   {
     prof::KScope _ks("k_schur_refine", s);
     const size_t shm = (size_t)2 * nmax * sizeof(cplx);
-    if (shm > 48 * 1024)
-      HBS_CUDA(cudaFuncSetAttribute(k_schur_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    HBS_CUDA(raise_smem_limit((const void*)k_schur_refine, shm));
     int qmax = 1;
     for (const auto& G : gjobs) qmax = std::max(qmax, G.q);
     k_schur_refine<<<(unsigned)(ng * qmax), 32, shm, s>>>(dg, Sp, Rp, R0.get(), piv.get(), nmax, qmax);
