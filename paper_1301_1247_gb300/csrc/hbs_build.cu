@@ -293,6 +293,23 @@ __global__ void k_fill_y_tr(const YJob* jobs) {
   }
 }
 
+// Rows of a randomized ID sketch beyond the node's size (l = n + kSketchOver).
+constexpr int kSketchOver = 16;
+
+// Omega (l x m, ld = l): independent random signs +-1 from SplitMix64 (Steele, Lea and Flood,
+// 2014) of the entry's position, the same matrix on every call.
+__global__ void k_sketch_signs(cplx* om, int l, int m) {
+  const int64_t tot = (int64_t)l * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = (uint64_t)e + 0x2545F4914F6CDD1Dull;
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    om[e] = cmk((z & 1) ? 1.0 : -1.0, 0.0);
+  }
+}
+
 struct DJob {
   DevGeom g;           // the solver's geometry
   const int64_t* idx;  // the node's active points (n)
@@ -940,22 +957,65 @@ void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s) {
           launch_jobs_y(dyj, yj.size(), [&](const YJob* p, unsigned ny) { k_fill_y_tr<<<dim3(64, ny), 256, psm, s>>>(p); });
       }
       HBS_LAUNCH_CHECK("k_fill_y");
+      // The matrix each ID runs on: Mt itself, or on tensor-core handles its randomized
+      // sketch when Mt is tall (the published randomized ID: the skeleton and T of the
+      // column-pivoted QR of Y = Omega Mt, Omega an l x m matrix of random signs with
+      // l = n + 16 rows, approximate those of Mt, whose columns Y's rows sample).  The sketch
+      // is one batched product on the tensor cores; the QR then runs on l instead of m rows.
+      std::vector<cplx*> idmat(yj.size());
+      std::vector<int> idrows(yj.size());
+      DevBuf<cplx> Ysk, Om;
+      {
+        std::vector<GemmJob> sj;
+        std::vector<size_t> sq;
+        int64_t pool = 0;
+        int lmax = 0, mmax = 0;
+        for (size_t q = 0; q < yj.size(); ++q) {
+          const int m = y_rows(yj[q]), n = yj[q].n;
+          idmat[q] = yj[q].mt;
+          idrows[q] = m;
+          const int l = n + kSketchOver;
+          if (!gemm_tensor() || m < 96 || 4 * m < 5 * l) continue;
+          sq.push_back(q);
+          pool += (int64_t)l * n;
+          lmax = std::max(lmax, l);
+          mmax = std::max(mmax, m);
+        }
+        if (!sq.empty()) {
+          Om.alloc((size_t)lmax * mmax);
+          Ysk.alloc((size_t)pool);
+          {
+            prof::KScope _ks("k_sketch_signs", s);
+            k_sketch_signs<<<grid_1d((int64_t)lmax * mmax), 256, 0, s>>>(Om.get(), lmax, mmax);
+          }
+          HBS_LAUNCH_CHECK("k_sketch_signs");
+          int64_t o = 0;
+          for (size_t q : sq) {
+            const int m = y_rows(yj[q]), n = yj[q].n, l = n + kSketchOver;
+            sj.push_back(GemmJob{Om.get(), yj[q].mt, Ysk.get() + o, l, n, m, lmax, m, l, cmk(1.0, 0.0),
+                                 cmk(0.0, 0.0), 0, 0, 0, 0, 0});
+            idmat[q] = Ysk.get() + o;
+            idrows[q] = l;
+            o += (int64_t)l * n;
+          }
+          run_gemms(sj, s);
+        }
+      }
       std::vector<CpqrJob> cj;
       for (size_t i = 0; i < tasks.size(); ++i) {
         Level& lv = tasks[i].h->levels[tasks[i].l];
         lv.t_off.assign(lv.count, 0);
         int64_t tpool = 0;
         for (int j = 0; j < lv.count; ++j) {
-          const YJob& y = yj[node0[i] + j];
-          const int m = y_rows(y);
+          const int m = idrows[node0[i] + j];
           lv.t_off[j] = tpool;
           tpool += (int64_t)std::min(m, lv.n[j]) * lv.n[j];
         }
         lv.T.alloc(std::max<int64_t>(tpool, 1));
         lv.perm.alloc(std::max<int64_t>(lv.ntot, 1));
         for (int j = 0; j < lv.count; ++j) {
-          const YJob& y = yj[node0[i] + j];
-          cj.push_back({y.mt, lv.T.get() + lv.t_off[j], lv.perm.get() + lv.off[j], y_rows(y), lv.n[j],
+          const size_t q = node0[i] + j;
+          cj.push_back({idmat[q], lv.T.get() + lv.t_off[j], lv.perm.get() + lv.off[j], idrows[q], lv.n[j],
                         (int)cj.size()});
         }
       }
