@@ -82,16 +82,26 @@ FLOP_COUNT_NOTE = {
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum averaged over the
 # kernel's launches in one step) from ncu captures, per workload, with the digest of the
 # sources the kernel is built from at capture time; reported only while they are unchanged.
-# k_pqr's traffic does not grow in proportion to its work (one launch, the periodizer
-# families, dominates it by writing back its trailing matrix when the matrices outgrow L2),
-# so the N = 1e4 capture is not scaled to the N = 1e5 workload.
+# A record is either a capture of that workload ("bytes_per_launch") or a capture of a smaller
+# one scaled to this workload's launches by their algorithmic bytes ("ratio_to_algorithmic",
+# DRAM bytes over algorithmic bytes in the capture), for kernels whose traffic grows with
+# their operands (the batched GEMMs).  k_pqr's traffic does not grow in proportion to its
+# work (one launch, the periodizer families, dominates it by writing back its trailing
+# matrix when the matrices outgrow L2), so its N = 1e4 capture is not scaled.
 NCU_TRAFFIC = {
     # profiles/k_pqr_wiggly_n10k.md: all 9 launches of a step at N = 1e4 (27 over 3 steps)
-    ("wiggly_n10k", "k_pqr"): {"bytes_per_launch": 3.598e+08, "sources": ['paper_1301_1247_gb300/csrc/pqr.cu', 'paper_1301_1247_gb300/csrc/common.cuh', 'paper_1301_1247_gb300/csrc/gridsync.cuh', 'paper_1301_1247_gb300/csrc/dense_kernels.cuh', 'paper_1301_1247_gb300/csrc/dfloat.cuh', 'paper_1301_1247_gb300/csrc/dfcore.cuh', 'paper_1301_1247_gb300/csrc/hankel_table.h', 'paper_1301_1247_gb300/csrc/balance.hpp'],
+    ("wiggly_n10k", "k_pqr"): {"bytes_per_launch": 3.598e+08, "note": "ncu capture of this workload",
+                                "sources": ['paper_1301_1247_gb300/csrc/pqr.cu', 'paper_1301_1247_gb300/csrc/common.cuh', 'paper_1301_1247_gb300/csrc/gridsync.cuh', 'paper_1301_1247_gb300/csrc/dense_kernels.cuh', 'paper_1301_1247_gb300/csrc/dfloat.cuh', 'paper_1301_1247_gb300/csrc/dfcore.cuh', 'paper_1301_1247_gb300/csrc/hankel_table.h', 'paper_1301_1247_gb300/csrc/balance.hpp'],
                                 "digest": "f334d8b6ea0d5aff"},
-    # profiles/launch_list_complicated_n100k.md (first capture of this kernel's sources)
-    ("complicated_n100k", "k_zgemm_batched_df"): {"bytes_per_launch": 3.087e+08, "sources": ['paper_1301_1247_gb300/csrc/zgemm.cuh', 'paper_1301_1247_gb300/csrc/common.cuh', 'paper_1301_1247_gb300/csrc/dfcore.cuh', 'paper_1301_1247_gb300/csrc/dfloat.cuh', 'paper_1301_1247_gb300/csrc/hankel_table.h'],
-                                                  "digest": "982e0a980ec1bb5a"},
+    # profiles/k_zgemm_batched_df_wiggly_n10k.md: all 141 launches of 3 steps at N = 1e4 moved
+    # 25.39 MB of DRAM per launch against 37.38 MB of algorithmic bytes per launch (the same
+    # command's profiled pass); scaled to the N = 1e5 launches by their algorithmic bytes
+    ("complicated_n100k", "k_zgemm_batched_df"): {
+        "ratio_to_algorithmic": 0.6792, "scaled_from": "wiggly_n10k",
+        "note": "scaled: an ncu capture at N = 1e4 (wiggly_n10k) gave 0.6792 DRAM bytes per algorithmic byte; "
+                "times this workload's algorithmic bytes per launch",
+        "sources": ['paper_1301_1247_gb300/csrc/zgemm.cuh', 'paper_1301_1247_gb300/csrc/common.cuh', 'paper_1301_1247_gb300/csrc/dfcore.cuh', 'paper_1301_1247_gb300/csrc/dfloat.cuh', 'paper_1301_1247_gb300/csrc/hankel_table.h'],
+        "digest": "630d3917ea1648e7"},
 }
 
 
@@ -104,16 +114,22 @@ def _sources_digest(paths):
     return hsh.hexdigest()[:16]
 
 
-def measured_traffic(workload_name, kernel):
+def measured_traffic(workload_name, kernel, alg_bytes_per_launch=None):
+    """(DRAM bytes per launch, how they were obtained), or (None, why not)."""
     rec = NCU_TRAFFIC.get((workload_name, kernel))
     if rec is None:
-        return None
+        return None, (f"no ncu capture of {kernel} for this workload (profiles/ holds the kernel captures at "
+                      "N = 1e4)")
     try:
         if _sources_digest(rec["sources"]) != rec["digest"]:
-            return None
+            return None, f"the ncu capture of {kernel} predates its current sources"
     except OSError:
-        return None
-    return rec["bytes_per_launch"]
+        return None, "sources of the capture not found"
+    if "bytes_per_launch" in rec:
+        return rec["bytes_per_launch"], rec["note"]
+    if not alg_bytes_per_launch:
+        return None, "no algorithmic bytes to scale the capture by"
+    return rec["ratio_to_algorithmic"] * alg_bytes_per_launch, rec["note"]
 
 
 def workload(name):
@@ -425,6 +441,10 @@ def run_ours(args, ws, rank, local):
     h2d = 4 * n * 8 + n_ang * 8
     n_orders = sum(len(a[1]) for a in amps)
     d2h = n_orders * 2 * 16 + n_ang * 8
+    alg_b = tv["bytes"] / max(tv["launches"], 1)
+    traffic_b, traffic_note = measured_traffic(w["name"], tname, alg_b)
+    if traffic_b is not None:
+        traffic_b = round(traffic_b, -3)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2), "higher_is_better": True,
@@ -452,16 +472,17 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": int(launches),
         "roofline": {"bound": kbound, "kernel": tname, "achieved": round(achieved, 4), "peak": round(kpeak, 4),
                      "unit": "TFLOP/s", "frac": round(achieved / kpeak, 4),
-                     "traffic": measured_traffic(w["name"], tname),
-                     "traffic_note": None if measured_traffic(w["name"], tname) is not None else
-                     "no capture of this kernel's current sources on this workload; k_pqr's DRAM traffic at N = 1e4 "
-                     "is in profiles/k_pqr_wiggly_n10k.md (it does not scale with the work, so it is not scaled here)",
+                     "traffic": traffic_b,
+                     "traffic_note": traffic_note,
                      "algorithmic_bytes_per_launch": round(tv["bytes"] / max(tv["launches"], 1), 1) or None,
                      "flop_count": FLOP_COUNT_NOTE.get(tname, "as recorded by the library"),
                      "peak_note": knote + " (of measured)" if kbound == "tensor" else knote,
                      "timed_in": "separate profiled pass of the same steps (per-launch CUDA events on the launching "
                                  "stream)",
                      "kernel_time_shares": shares, "kernel_tflops": rates,
+                     "kernel_algorithmic_bytes_per_launch": {
+                         k: round(v["bytes"] / max(v["launches"], 1), 1) for k, v in
+                         sorted(kern.items(), key=lambda kv: -kv[1]["ms"])[:8] if v["bytes"] > 0},
                      "kernel_frac": {k: round(r / kernel_peak(k, prec)[1], 4) for k, r in rates.items()},
                      "hbm": {"bytes_per_step_lower_bound": hbm_bytes, "achieved_gbs": round(hbm_gbs, 2),
                              "peak_gbs": peaks_hbm, "frac": round(hbm_gbs / peaks_hbm, 5),
