@@ -177,9 +177,10 @@ hbs_status hbs_solve_plain(hbs_handle* h, const double* theta, int64_t n_theta, 
  * Rayleigh-Bloch expansions matched on y = +-h.  Each Bloch phase's rectangular system is
  * solved in the least-squares sense; every step is FP64.  The amplitudes are referred to
  * y = +-y0 as hbs_solve's are (n_wood = 0, t0 = 0 in hbs_result_angle_info).  Meant to
- * cross-check hbs_solve, not tuned for speed.  Sound-soft solvers only (options.index =
- * 0).  theta must lie in (-pi, 0); either violation gives HBS_ERR_INVALID_ARG; OOM and
- * CUDA as hbs_solve.  Synchronizes the stream.
+ * cross-check hbs_solve, not tuned for speed.  Transmission solvers (options.index > 0) use
+ * the same scheme with the pair of densities (Sec. 5): their obstacle rows are the interlaced
+ * transmission rows.  theta must lie in (-pi, 0), else HBS_ERR_INVALID_ARG; OOM and CUDA as
+ * hbs_solve.  Synchronizes the stream.
  */
 hbs_status hbs_solve_proxy(hbs_handle* h, const double* theta, int64_t n_theta, void* stream,
                            hbs_result** out);

@@ -321,7 +321,6 @@ hbs_status hbs_solve_proxy(hbs_handle* h, const double* theta, int64_t n_theta, 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   StreamScope scope(s);
   hbs_status st = guarded([&] {
-    if (h->h.comps != 1) throw Error(HBS_ERR_INVALID_ARG, "hbs_solve_proxy: sound-soft solvers only");
     GemmModeScope gm(HBS_PRECISION_FP64);
     solve_angles_proxy(h->h, theta, n_theta, r->r, s);
     HBS_CUDA(cudaStreamSynchronize(s));

@@ -81,7 +81,9 @@ __global__ void k_px_rows(DevGeom g, const PxRow* rows, int nr, int r0, cplx* R,
     const int r = (int)(e % nr);
     const int64_t j = e / nr;
     const PxRow q = rows[r];
-    const cplx k = px_kernel(q.tx, q.ty, g.x[j] + q.shift, g.y[j], g.nx[j], g.ny[j], g.omega, q.kind);
+    // the combined layer (sound-soft), or the layer of unknown j's density (transmission)
+    const cplx k = g.comps == 2 ? pair_source_field(g, q.tx, q.ty, g.x[j] + q.shift, g.y[j], j, q.kind)
+                                : px_kernel(q.tx, q.ty, g.x[j] + q.shift, g.y[j], g.nx[j], g.ny[j], g.omega, q.kind);
     R[(int64_t)(r0 + r) + j * ldr] = cscale(k, g.w[j]);
   }
 }
@@ -96,7 +98,8 @@ __global__ void k_px_proxy_rows(const PxRow* rows, int nr, const double* p4, int
   }
 }
 
-// Right-hand sides X(:, 0:l) = P, X(:, l:l+mp) = phi_p at the nodes, X(:, l+mp+q) = -u_inc(theta_q).
+// Right-hand sides X(:, 0:l) = P, X(:, l:l+mp) = phi_p at the nodes, X(:, l+mp+q) = -u_inc(theta_q)
+// (transmission: the row functionals of phi_p and of -u_inc, Sec. 5).
 __global__ void k_px_rhs(DevGeom g, const cplx* P, int l, const double* p4, int mp, const double* kx,
                          const double* ky, int nq, cplx* X) {
   const int64_t n = g.n;
@@ -109,11 +112,16 @@ __global__ void k_px_rhs(DevGeom g, const cplx* P, int l, const double* p4, int 
       v = P[e];
     } else if (c < l + mp) {
       const int p = c - l;
-      v = px_kernel(g.x[i], g.y[i], p4[4 * p], p4[4 * p + 1], p4[4 * p + 2], p4[4 * p + 3], g.omega, 0);
+      v = g.comps == 2 ? proxy_row_entry(g, i, p4[4 * p], p4[4 * p + 1], p4[4 * p + 2], p4[4 * p + 3], g.omega)
+                       : px_kernel(g.x[i], g.y[i], p4[4 * p], p4[4 * p + 1], p4[4 * p + 2], p4[4 * p + 3], g.omega, 0);
     } else {
       const int q = c - l - mp;
       const cplx u = cexp_i(kx[q] * g.x[i] + ky[q] * g.y[i]);
       v = cmk(-u.x, -u.y);
+      if (g.comps == 2 && !(i & 1)) {  // sigma row: +(du/dn) / w = i (kx n_x + ky n_y) u / w
+        const double f = (kx[q] * g.nx[i] + ky[q] * g.ny[i]) / g.omega;
+        v = cmk(-f * u.y, f * u.x);
+      }
     }
     X[e] = v;
   }

@@ -184,3 +184,32 @@ def test_batch_build_and_server():
             assert relerr(np.concatenate([c, d]), np.concatenate([c2, d2])) < 1e-11, (i, a)
     finally:
         sv.close()
+
+
+def test_proxy_periodizer_matches_its_oracle_and_the_fourier_wall_solve():
+    """The second periodizer (hbs_solve_proxy) on a transmission solver: its amplitudes match
+    the oracle's box scheme for the pair (transmission.proxy_solve), the dense Fourier-wall
+    transmission oracle and the library's Fourier-wall solve, including an exact Wood's
+    anomaly."""
+    from oracle import proxy_periodizer as pp
+    hbs = require_lib()
+    geom = inputs.paper_star().sample(400)
+    x, y, dx, dy = geom
+    omega, index = 10.0, 1.5
+    h = _handle(hbs, geom, omega, index)
+    y0 = h.info()["y0"]
+    thetas = np.array([-math.pi / 5, -1.0, -2.5, -math.acos(1.0 - 2.0 * math.pi / omega)])
+    rp_, rf_ = h.solve_proxy(thetas), h.solve(thetas)
+    blocks = tr.obstacle_blocks(x, y, dx, dy, omega, index, D)
+    for i, th in enumerate(thetas):
+        orders, c, d, flux = rp_.bragg(i)
+        got = np.concatenate([c, d])
+        sp = tr.proxy_solve(x, y, dx, dy, omega, index, D, th, blocks=blocks)
+        cp, dp = pp.bragg_at(sp, omega, D, th, y0)
+        assert list(orders) == list(sp.orders)
+        assert relerr(got, np.concatenate([cp, dp])) < 1e-10, (th, "proxy oracle")
+        sf = tr.dense_solve(x, y, dx, dy, omega, index, D, th, rd.options(x, y, omega, D, th), blocks)
+        assert relerr(got, qd.bragg_vector(sf)) < 1e-10, (th, "Fourier-wall oracle")
+        _, c2, d2, _ = rf_.bragg(i)
+        assert relerr(got, np.concatenate([c2, d2])) < 1e-10, (th, "Fourier-wall solve")
+        assert abs(flux - sf.flux_error) < 1e-8
