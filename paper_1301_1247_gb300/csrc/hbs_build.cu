@@ -992,8 +992,9 @@ void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s) {
           int64_t o = 0;
           for (size_t q : sq) {
             const int m = y_rows(yj[q]), n = yj[q].n, l = n + kSketchOver;
+            // Omega's entries are real signs: one digit plane (the tensor-core product skips the rest)
             sj.push_back(GemmJob{Om.get(), yj[q].mt, Ysk.get() + o, l, n, m, lmax, m, l, cmk(1.0, 0.0),
-                                 cmk(0.0, 0.0), 0, 0, 0, 0, 0});
+                                 cmk(0.0, 0.0), 0, 0, 0, 0, 0, 1});
             idmat[q] = Ysk.get() + o;
             idrows[q] = l;
             o += (int64_t)l * n;

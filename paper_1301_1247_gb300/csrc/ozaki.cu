@@ -70,6 +70,7 @@ struct OzOperand {
   int rows, K, rows_pad, Kpad;
   int* E;
   unsigned short* out;
+  int nplanes;  // leading digit planes written (14; fewer when the rest are known to be zero)
 };
 
 // max(|Re|, |Im|) over each row of operand blockIdx.y: one warp per row, integer compares on
@@ -140,8 +141,8 @@ __global__ void k_oz_digits(const OzOperand* ops) {
     }
 #pragma unroll
     for (int i = 0; i < OZ_S; ++i) {
-      op.out[i * plane + e] = dre[i];
-      op.out[(OZ_S + i) * plane + e] = dim[i];
+      if (i < op.nplanes) op.out[i * plane + e] = dre[i];
+      if (OZ_S + i < op.nplanes) op.out[(OZ_S + i) * plane + e] = dim[i];
     }
   }
 }
@@ -211,12 +212,13 @@ __device__ __forceinline__ void oz_tma_load(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// One stage (16 k from kb) of every digit plane of A (rows row0..) and B (rows col0..) into the
-// ring buffer at buf: announce the stage's bytes on its full barrier, then four copies (two
-// k-groups of each operand).
+// One stage (16 k from kb) of the digit planes of A (rows row0..; the first planes_a of them,
+// as A's tensor map boxes hold) and of B (rows col0..) into the ring buffer at buf: announce
+// the stage's bytes on its full barrier, then four copies (two k-groups of each operand).
 __device__ __forceinline__ void oz_issue_stage(uint32_t buf, const CUtensorMap* tmA, const CUtensorMap* tmB, int row0,
-                                               int col0, int kb, uint32_t bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(OZ_STAGE) : "memory");
+                                               int col0, int kb, uint32_t bar, int planes_a) {
+  const uint32_t bytes = 2u * (uint32_t)(planes_a * OZ_A_PL + OZ_B_KG);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
   oz_tma_load(buf, tmA, kb, row0, bar);
   oz_tma_load(buf + OZ_A_KG, tmA, kb + 8, row0, bar);
   oz_tma_load(buf + 2 * OZ_A_KG, tmB, kb, col0, bar);
@@ -233,6 +235,7 @@ struct OzJob {
   const int* Er;
   const int* Ec;
   int m, n, mpad, npad, Kpad, klen, splits, tiles_m, tiles_n;
+  int nre, nim;  // digit planes of op(A)'s real and imaginary parts that can be nonzero
   int64_t item_base;
   cplx alpha, beta;
   cplx* C;  // splits == 1: C = alpha op(A) B + beta C directly
@@ -289,6 +292,7 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const OzJob* jobs, int njobs,
     const int nst = (k1 - k0) / OZ_BK;
     const CUtensorMap* tmA = jb.tmA;
     const CUtensorMap* tmB = jb.tmB;
+    const int planes_a = jb.nim > 0 ? OZ_NSUB : jb.nre;  // A's planes the copies bring
 
     float Rh[2][OZ_BN], Rl[2][OZ_BN];  // running double-float sums (re, im) of this thread's row
 #pragma unroll
@@ -305,10 +309,11 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const OzJob* jobs, int njobs,
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(tmB))
                    : "memory");
       // every earlier MMA has completed (the last period's wait covered it): all buffers are free
-      oz_issue_stage(ring + (G % OZ_RING) * OZ_STAGE, tmA, tmB, row0, col0, k0, smem_u32(&s_full[G % OZ_RING]));
+      oz_issue_stage(ring + (G % OZ_RING) * OZ_STAGE, tmA, tmB, row0, col0, k0, smem_u32(&s_full[G % OZ_RING]),
+                     planes_a);
       if (nst > 1)
         oz_issue_stage(ring + ((G + 1) % OZ_RING) * OZ_STAGE, tmA, tmB, row0, col0, k0 + OZ_BK,
-                       smem_u32(&s_full[(G + 1) % OZ_RING]));
+                       smem_u32(&s_full[(G + 1) % OZ_RING]), planes_a);
     }
 
     for (int st = 0; st < nst; ++st) {
@@ -327,6 +332,8 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const OzJob* jobs, int njobs,
             // another (32 rows each), and level l = i + j sits in columns 32 l (re) and
             // 256 + 32 l (im), so the product lands in the levels i..6 at once.
 #pragma unroll
+            // digits of A known to be zero (jb.nre, jb.nim) are skipped; digit 0 of the real
+            // part always runs, as it opens each period's accumulators
             for (int i = 0; i < OZ_S; ++i) {
               const int N = OZ_BN * (OZ_S - i);
               const uint32_t ip = oz_idesc(false, N), in = oz_idesc(true, N);
@@ -334,10 +341,14 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const OzJob* jobs, int njobs,
               const uint64_t br = dB, bi = dB + (uint64_t)(OZ_S * (OZ_B_PL >> 4));
               const uint32_t dre = tmem + OZ_BN * i, dim = tmem + 256 + OZ_BN * i;
               const uint32_t first = (fresh && i == 0) ? 0u : 1u;
-              oz_mma(dre, ar, br, ip, first);  // re += Ar Br
-              oz_mma(dre, ai, bi, in, 1u);     // re -= Ai Bi
-              oz_mma(dim, ar, bi, ip, first);  // im += Ar Bi
-              oz_mma(dim, ai, br, ip, 1u);     // im += Ai Br
+              if (i < jb.nre) {
+                oz_mma(dre, ar, br, ip, first);  // re += Ar Br
+                oz_mma(dim, ar, bi, ip, first);  // im += Ar Bi
+              }
+              if (i < jb.nim) {
+                oz_mma(dre, ai, bi, in, 1u);  // re -= Ai Bi
+                oz_mma(dim, ai, br, ip, 1u);  // im += Ai Br
+              }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&s_bar[buf]))
@@ -350,7 +361,7 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const OzJob* jobs, int njobs,
               } else {
                 const uint32_t nb = (gs + 2) % OZ_RING;
                 oz_issue_stage(ring + nb * OZ_STAGE, tmA, tmB, row0, col0, k0 + (st + 2) * OZ_BK,
-                               smem_u32(&s_full[nb]));
+                               smem_u32(&s_full[nb]), planes_a);
               }
             }
           }
@@ -482,10 +493,11 @@ static TmapEncodeFn tmap_encoder() {
 // as a 3-D tensor (k, row, plane) with boxes of 8 k x box_rows x 14 planes.  The driver checks
 // the base (16-byte aligned), the strides (multiples of 16 bytes) and the box; a failure is an
 // error here, before any launch.
-static void encode_planes(CUtensorMap* m, const unsigned short* base, int Kpad, int rows_pad, int box_rows) {
+static void encode_planes(CUtensorMap* m, const unsigned short* base, int Kpad, int rows_pad, int box_rows,
+                          int box_planes = OZ_NSUB) {
   const cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)rows_pad, (cuuint64_t)OZ_NSUB};
   const cuuint64_t strides[2] = {(cuuint64_t)Kpad * 2, (cuuint64_t)Kpad * 2 * (cuuint64_t)rows_pad};
-  const cuuint32_t box[3] = {8, (cuuint32_t)box_rows, (cuuint32_t)OZ_NSUB};
+  const cuuint32_t box[3] = {8, (cuuint32_t)box_rows, (cuuint32_t)box_planes};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = tmap_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<unsigned short*>(base), dims,
                                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -530,6 +542,8 @@ void ozaki_gemm_batched(const std::vector<GemmJob>& js, cudaStream_t s) {
     o.mpad = o.tiles_m * OZ_BM;
     o.npad = o.tiles_n * OZ_BN;
     o.Kpad = (j.k + OZ_BK - 1) / OZ_BK * OZ_BK;  // stages of 16; the last period may be short
+    o.nre = j.a_real_digits > 0 ? std::min(j.a_real_digits, OZ_S) : OZ_S;
+    o.nim = j.a_real_digits > 0 ? 0 : OZ_S;
     tiles_all += o.tiles_m * o.tiles_n;
   }
   for (int q = 0; q < nj; ++q) {
@@ -558,7 +572,11 @@ void ozaki_gemm_batched(const std::vector<GemmJob>& js, cudaStream_t s) {
     eA += o.mpad;
     eB += o.npad;
     if (o.splits > 1) wtot += (int64_t)o.splits * j.m * j.n;
-    tflops += 224.0 * o.mpad * (double)o.npad * o.Kpad;
+    // executed: per digit i of A, 2 (7 - i) MMA units for its real part, 2 (7 - i) for its
+    // imaginary part; 112 units in all for a general A (224 flops per m n k)
+    double units = 0.0;
+    for (int i = 0; i < OZ_S; ++i) units += 2.0 * (OZ_S - i) * ((i < o.nre) + (i < o.nim));
+    tflops += 2.0 * units * o.mpad * (double)o.npad * o.Kpad;
   }
   DevBuf<unsigned short> Ad(adig), Bd(bdig);
   DevBuf<int> E(eA + eB), st(1);
@@ -575,8 +593,8 @@ void ozaki_gemm_batched(const std::vector<GemmJob>& js, cudaStream_t s) {
     int* er = E.get() + reinterpret_cast<int64_t>(o.Er);
     int* ec = E.get() + eA + reinterpret_cast<int64_t>(o.Ec);
     // op(A) row r, k: transA ? A[r lda + k] : A[k lda + r];  B^T row c, k: B[c ldb + k]
-    ops.push_back({j.A, j.lda, j.transA ? 1 : 0, j.m, j.k, o.mpad, o.Kpad, er, ad});
-    ops.push_back({j.B, j.ldb, 1, j.n, j.k, o.npad, o.Kpad, ec, bd});
+    ops.push_back({j.A, j.lda, j.transA ? 1 : 0, j.m, j.k, o.mpad, o.Kpad, er, ad, o.nim > 0 ? OZ_NSUB : o.nre});
+    ops.push_back({j.B, j.ldb, 1, j.n, j.k, o.npad, o.Kpad, ec, bd, OZ_NSUB});
     o.Ad = ad;
     o.Bd = bd;
     o.Er = er;
@@ -603,7 +621,7 @@ void ozaki_gemm_batched(const std::vector<GemmJob>& js, cudaStream_t s) {
   std::vector<CUtensorMap> maps(2 * (size_t)nj);
   for (int q = 0; q < nj; ++q) {
     const OzJob& o = oj[q];
-    encode_planes(&maps[2 * q], o.Ad, o.Kpad, o.mpad, OZ_BM);
+    encode_planes(&maps[2 * q], o.Ad, o.Kpad, o.mpad, OZ_BM, o.nim > 0 ? OZ_NSUB : o.nre);
     encode_planes(&maps[2 * q + 1], o.Bd, o.Kpad, o.npad, OZ_BN);
   }
   DevBuf<CUtensorMap> dmaps;

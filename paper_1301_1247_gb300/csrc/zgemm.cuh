@@ -20,6 +20,8 @@ struct GemmJob {
   int tile_base;         // prefix sum of tiles over earlier jobs
   int transA;            // 1: op(A) = A^T (A stored k x m, column-major, leading dimension lda)
   int transC;            // 1: C stored row-major, C(i, j) at C[i ldc + j]
+  int a_real_digits = 0; // tensor-core products: 0 for a general A; d > 0 when A is real and each
+                         // of its rows needs only its first d digit planes (e.g. 1 for signs)
 };
 
 constexpr int GBM = 32, GBN = 32, GBK = 8;
