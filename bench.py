@@ -422,8 +422,17 @@ def run_ours(args, ws, rank, local):
         del h64, ref, hb, ra, rb
 
     value = whole_job_rate(ws, n_ang, args.steps, ms_max)
-    kern = {k: v for k, v in prof.items() if not k.startswith("phase:")}
+    kern = {k: v for k, v in prof.items() if not k.startswith(("phase:", "in:"))}
     phases = {k[6:]: round(v["ms"] / args.steps, 2) for k, v in prof.items() if k.startswith("phase:")}
+    if args.phase_kernels:
+        by_phase = {}
+        for k, v in prof.items():
+            if k.startswith("in:"):
+                ph, kn = k[3:].rsplit(":", 1)
+                by_phase.setdefault(ph, {})[kn] = {"ms": round(v["ms"] / args.steps, 3),
+                                                  "launches": v["launches"] / args.steps}
+        with open(args.phase_kernels, "w") as f:
+            json.dump({"phases_ms_per_step": phases, "kernels_by_phase": by_phase}, f, indent=1, sort_keys=True)
     top = max(kern.items(), key=lambda kv: kv[1]["ms"])
     tname, tv = top
     achieved = tv["flops"] / (tv["ms"] / 1e3) / 1e12 if tv["ms"] > 0 else 0.0
@@ -755,6 +764,8 @@ def main():
     ap.add_argument("--cpu-sample-n", type=int, nargs="+", default=[400, 1000, 2000])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 plain-path accuracy check")
+    ap.add_argument("--phase-kernels", metavar="PATH",
+                    help="write the profiled pass's device time per phase and kernel (ms per step) as JSON")
     ap.add_argument("--precision", choices=["fp64", "df", "tc"], default="tc")
     ap.add_argument("--mode", choices=["solver", "batch", "serving"], default="solver",
                     help="solver: the headline step; batch: many gratings built at once; serving: request loop")

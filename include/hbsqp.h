@@ -346,10 +346,13 @@ hbs_status hbs_zgemm(int64_t m, int64_t n, int64_t k, const double* alpha, const
  * bracketed by CUDA events on its stream; hbs_profile_get copies up to `max`
  * per-kernel records (launches, summed device milliseconds, summed algorithmic
  * flops and bytes; entries named "phase:..." are host wall time of build and
- * solve phases) and returns the number of records.  hbs_profile_reset clears them.
+ * solve phases; entries named "in:<phase>:<kernel>" are the launches and device
+ * milliseconds of one kernel inside one phase, charged to the innermost phase open on
+ * the launching host thread) and returns the number of records.  hbs_profile_reset
+ * clears them.
  */
 typedef struct hbs_kernel_stat {
-  char name[48];
+  char name[80];
   int64_t launches;
   double ms;
   double flops;

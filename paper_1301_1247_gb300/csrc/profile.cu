@@ -1,4 +1,10 @@
-// Launch accounting and per-kernel CUDA-event timing (see profile.hpp).
+// Launch accounting and per-kernel CUDA-event timing (see profile.hpp).  With the
+// environment variable HBS_PROFILE_TIMELINE naming a file, every profiled launch is also
+// written there as one CSV line (kernel, phase, stream, device start and duration in ms, the
+// start measured from an event recorded when profiling was switched on, and the host time
+// at which the launch was issued, from the same moment on the host clock).
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -17,8 +23,11 @@ std::atomic<int> g_enabled{0};
 namespace {
 struct Pending {
   std::string name;
+  const char* phase;
+  cudaStream_t s;
   cudaEvent_t a, b;
   double flops, bytes;
+  std::chrono::steady_clock::time_point issued;
 };
 struct Stat {
   int64_t launches = 0;
@@ -28,6 +37,9 @@ std::mutex g_mu;
 std::vector<Pending> g_pending;
 std::map<std::string, Stat> g_stats;
 std::vector<cudaEvent_t> g_free;
+FILE* g_timeline = nullptr;
+cudaEvent_t g_origin = nullptr;
+std::chrono::steady_clock::time_point g_origin_host;
 
 void drain_locked() {
   for (auto& p : g_pending) {
@@ -39,6 +51,20 @@ void drain_locked() {
     st.ms += ms;
     st.flops += p.flops;
     st.bytes += p.bytes;
+    if (p.phase) {
+      // the same launch charged to its phase: "in:<phase>:<kernel>", time and launches only
+      Stat& sp = g_stats[std::string("in:") + p.phase + ":" + p.name];
+      sp.launches += 1;
+      sp.ms += ms;
+    }
+    if (g_timeline && g_origin) {
+      float t0 = 0.f;
+      if (cudaEventElapsedTime(&t0, g_origin, p.a) == cudaSuccess)
+        std::fprintf(g_timeline, "%s,%s,%p,%.4f,%.4f,%.4f\n", p.name.c_str(), p.phase ? p.phase : "", (void*)p.s, t0,
+                     ms, 1e3 * std::chrono::duration<double>(p.issued - g_origin_host).count());
+      else
+        cudaGetLastError();
+    }
     g_free.push_back(p.a);
     g_free.push_back(p.b);
   }
@@ -58,9 +84,10 @@ cudaEvent_t new_event() {
   return e;
 }
 
-void record(const char* name, cudaStream_t, cudaEvent_t a, cudaEvent_t b, double flops, double bytes) {
+void record(const char* name, const char* phase, cudaStream_t s, cudaEvent_t a, cudaEvent_t b, double flops,
+            double bytes, std::chrono::steady_clock::time_point issued) {
   std::lock_guard<std::mutex> lk(g_mu);
-  g_pending.push_back({name, a, b, flops, bytes});
+  g_pending.push_back({name, phase, s, a, b, flops, bytes, issued});
   if (g_pending.size() > 4096) drain_locked();
 }
 
@@ -86,7 +113,22 @@ using namespace hbs::prof;
 
 extern "C" {
 
-void hbs_profile_enable(int on) { g_enabled.store(on ? 1 : 0); }
+void hbs_profile_enable(int on) {
+  if (on) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    const char* path = std::getenv("HBS_PROFILE_TIMELINE");
+    if (path && *path && !g_timeline) {
+      g_timeline = std::fopen(path, "w");
+      if (g_timeline) std::fprintf(g_timeline, "kernel,phase,stream,start_ms,ms,issued_ms\n");
+    }
+    if (g_timeline) {
+      if (!g_origin) cudaEventCreate(&g_origin);
+      cudaEventRecord(g_origin, 0);
+      g_origin_host = std::chrono::steady_clock::now();
+    }
+  }
+  g_enabled.store(on ? 1 : 0);
+}
 
 void hbs_profile_reset(void) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -97,6 +139,7 @@ void hbs_profile_reset(void) {
 int hbs_profile_get(hbs_kernel_stat* out, int max) {
   std::lock_guard<std::mutex> lk(g_mu);
   drain_locked();
+  if (g_timeline) std::fflush(g_timeline);
   int i = 0;
   for (auto& kv : g_stats) {
     if (out && i < max) {

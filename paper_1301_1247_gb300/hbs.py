@@ -78,7 +78,7 @@ class ServerStats(ctypes.Structure):
 
 
 class KernelStat(ctypes.Structure):
-    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+    _fields_ = [("name", ctypes.c_char * 80), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
