@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "dense_kernels.cuh"
 #include "profile.hpp"
@@ -34,6 +36,59 @@ cudaStream_t& current_stream() {
   return s;
 }
 
+namespace {
+// Pinned host blocks for read_to_host, kept for the life of the process (never freed:
+// cudaFreeHost would synchronize the device).
+struct PinnedPool {
+  std::mutex mu;
+  std::vector<std::pair<void*, size_t>> free;
+};
+PinnedPool& pinned_pool() {
+  static PinnedPool* p = new PinnedPool;
+  return *p;
+}
+}  // namespace
+
+void read_to_host(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return;
+  PinnedPool& pool = pinned_pool();
+  void* blk = nullptr;
+  size_t cap = 0;
+  {
+    std::lock_guard<std::mutex> lk(pool.mu);
+    size_t best = pool.free.size();
+    for (size_t i = 0; i < pool.free.size(); ++i)
+      if (pool.free[i].second >= bytes && (best == pool.free.size() || pool.free[i].second < pool.free[best].second))
+        best = i;
+    if (best < pool.free.size()) {
+      blk = pool.free[best].first;
+      cap = pool.free[best].second;
+      pool.free.erase(pool.free.begin() + (std::ptrdiff_t)best);
+    }
+  }
+  if (!blk) {
+    cap = 64 * 1024;
+    while (cap < bytes) cap *= 2;
+    if (cudaMallocHost(&blk, cap) != cudaSuccess) {
+      cudaGetLastError();
+      blk = nullptr;
+    }
+  }
+  if (!blk) {  // no pinned memory to be had: copy into the caller's memory directly
+    HBS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+    HBS_CUDA(cudaStreamSynchronize(s));
+    return;
+  }
+  cudaError_t e = cudaMemcpyAsync(blk, src, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) std::memcpy(dst, blk, bytes);
+  {
+    std::lock_guard<std::mutex> lk(pool.mu);
+    pool.free.push_back({blk, cap});
+  }
+  cuda_check(e, "read_to_host");
+}
+
 // Keep freed memory in the device's default pool (the library frees and reallocates
 // work arrays at every level and batch); the pool belongs to this process's context.
 void init_memory_pool() {
@@ -45,6 +100,12 @@ void init_memory_pool() {
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
       uint64_t thr = UINT64_MAX;
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      // A block freed on one stream is reused by another only once the free has completed:
+      // the build's two concurrent chains never wait on each other's kernels through the
+      // allocator (with internal dependencies allowed, an allocation on the compression
+      // chain's stream could be made to wait for the periodizer's queued launches).
+      int no = 0;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
     }
     cudaGetLastError();
   });

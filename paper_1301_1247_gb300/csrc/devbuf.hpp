@@ -57,6 +57,13 @@ inline cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
 }
 int injected_rank_cap();
 
+// Copies `bytes` of device memory at `src` to host memory at `dst` once the stream reaches
+// the copy, and returns then.  The copy lands in a pinned staging block (a process-wide pool,
+// reused) and is then copied out: a device-to-host copy into pageable memory would hold the
+// runtime's pageable-copy path until the stream got there, and a second host thread's
+// uploads (the build runs two) would stall behind it meanwhile.
+void read_to_host(void* dst, const void* src, size_t bytes, cudaStream_t s);
+
 // Owning device allocation (stream-ordered cudaMallocAsync / cudaFreeAsync on the
 // library's current stream).
 template <typename T>
@@ -98,10 +105,7 @@ class DevBuf {
   std::vector<T> download(cudaStream_t s, size_t count = SIZE_MAX) const {
     size_t c = count == SIZE_MAX ? n_ : count;
     std::vector<T> h(c);
-    if (c) {
-      HBS_CUDA(cudaMemcpyAsync(h.data(), p_, c * sizeof(T), cudaMemcpyDeviceToHost, s));
-      HBS_CUDA(cudaStreamSynchronize(s));
-    }
+    if (c) read_to_host(h.data(), p_, c * sizeof(T), s);
     return h;
   }
 

@@ -648,8 +648,7 @@ void ozaki_gemm_batched(const std::vector<GemmJob>& js, cudaStream_t s) {
   }
   HBS_LAUNCH_CHECK("k_oz_reduce");
   int hs = 0;
-  HBS_CUDA(cudaMemcpyAsync(&hs, st.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
-  HBS_CUDA(cudaStreamSynchronize(s));
+  read_to_host(&hs, st.get(), sizeof(int), s);
   if (hs) throw Error(HBS_ERR_TIMEOUT, "tensor-core GEMM: an MMA completion wait gave up");
 }
 

@@ -359,8 +359,7 @@ void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, con
       HBS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kNT), args, smem, s));
     }
     HBS_LAUNCH_CHECK("k_pgj");
-    HBS_CUDA(cudaMemcpyAsync(hg.data(), gs.get(), sizeof(GridSync) * nj, cudaMemcpyDeviceToHost, s));
-    HBS_CUDA(cudaStreamSynchronize(s));
+    read_to_host(hg.data(), gs.get(), sizeof(GridSync) * nj, s);
   }
   for (const auto& g : hg)
     if (g.timed_out) throw Error(HBS_ERR_TIMEOUT, "persistent Gauss-Jordan: a barrier wait gave up");
@@ -372,8 +371,7 @@ void pgj_run(const std::vector<std::pair<cplx*, int>>& mats, cudaStream_t s, con
     k_pgj_copy<<<dim3(std::max(1, 1216 / nj), nj), 256, 0, s>>>(dj.get());
   }
   HBS_LAUNCH_CHECK("k_pgj_unpivot");
-  HBS_CUDA(cudaMemcpyAsync(hs.data(), sing.get(), sizeof(int) * nj, cudaMemcpyDeviceToHost, s));
-  HBS_CUDA(cudaStreamSynchronize(s));
+  read_to_host(hs.data(), sing.get(), sizeof(int) * nj, s);
   for (int j = 0; j < nj; ++j)
     if (hs[j]) throw Error(HBS_WARN_ILLCOND, std::string("singular block in ") + what);
 }

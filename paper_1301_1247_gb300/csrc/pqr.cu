@@ -1035,9 +1035,8 @@ void pqr_run(const std::vector<PqrSpec>& specs_in, double tol, cudaStream_t s, P
       HBS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kNT), args, smem, s));
     }
     HBS_LAUNCH_CHECK("k_pqr");
-    HBS_CUDA(cudaMemcpyAsync(hs.data(), st.get(), sizeof(PqrState) * nj, cudaMemcpyDeviceToHost, s));
-    HBS_CUDA(cudaMemcpyAsync(hg.data(), gs.get(), sizeof(GridSync) * nj, cudaMemcpyDeviceToHost, s));
-    HBS_CUDA(cudaStreamSynchronize(s));
+    read_to_host(hs.data(), st.get(), sizeof(PqrState) * nj, s);
+    read_to_host(hg.data(), gs.get(), sizeof(GridSync) * nj, s);
   }
   for (const auto& g : hg)
     if (g.timed_out) throw Error(HBS_ERR_TIMEOUT, "persistent QR: a barrier wait gave up");

@@ -1397,8 +1397,7 @@ static void schur_solve(const Dims& D, const std::vector<GroupJob>& gjobs, const
     const void* fn = df ? (const void*)k_schur_coop<256, true> : (const void*)k_schur_coop<256, false>;
     HBS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(ng * CL), dim3(256), args, 0, s));
     GridSync hg{};
-    HBS_CUDA(cudaMemcpyAsync(&hg, gs.get(), sizeof(GridSync), cudaMemcpyDeviceToHost, s));
-    HBS_CUDA(cudaStreamSynchronize(s));
+    read_to_host(&hg, gs.get(), sizeof(GridSync), s);
     if (hg.timed_out) throw Error(HBS_ERR_TIMEOUT, "Schur factorization: a grid barrier wait gave up");
   }
   if (!df) return;

@@ -132,10 +132,13 @@ __device__ __forceinline__ void dfc_mac_tile(const dfc& a, const dfc& b, dfc& c)
 
 // The double-float multiply-adds of one GBK slice for one thread's outputs, leaving out the
 // second row (R1 false) or column (C1 false).
+// The slice loop is unrolled by 2: fully unrolled (8), the four variants' code (48 FP32-pipe
+// instructions per complex multiply-add) overflows the instruction cache and the warps stall on
+// instruction fetches; not unrolled at all, the loop overhead shows.
 template <bool R1, bool C1>
 __device__ __forceinline__ void tile_mac_df(const dfc (*As)[GBM + 1], const dfc (*Bs)[GBN + 1], int tr, int tc,
                                             dfc (&acc)[2][2]) {
-#pragma unroll
+#pragma unroll 2
   for (int kk = 0; kk < GBK; ++kk) {
     const dfc a0 = As[kk][tr], b0 = Bs[kk][tc];
     dfc_mac_tile(a0, b0, acc[0][0]);
@@ -148,9 +151,13 @@ __device__ __forceinline__ void tile_mac_df(const dfc (*As)[GBM + 1], const dfc 
   }
 }
 
+// Slices are double-buffered in shared memory: while the CTA multiplies one slice, each thread
+// already holds its elements of the next in registers (loads issued before the multiply-adds),
+// and stores them into the other buffer afterwards, so one barrier per slice suffices and the
+// L2 latency of the loads overlaps the arithmetic.
 static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* jobs, int njobs) {
-  __shared__ dfc As[GBK][GBM + 1];
-  __shared__ dfc Bs[GBK][GBN + 1];
+  __shared__ dfc As[2][GBK][GBM + 1];
+  __shared__ dfc Bs[2][GBK][GBN + 1];
   int t = blockIdx.x;
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {
@@ -171,32 +178,36 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* 
   const int m = jb.m, n = jb.n, K = jb.k;
   // the same skipping of padded rows and columns as in k_zgemm_batched
   const bool c0 = col0 + tc < n, c1 = col0 + tc + 16 < n, r1 = row0 + 16 < m;
+  // this thread's element of each slice: A (row ar, slice column ak), B (slice row bk, column bc)
+  const bool ta = jb.transA != 0;
+  const int ar = ta ? tid >> 3 : tid & 31, ak = ta ? tid & 7 : tid >> 5;
+  const int bc = tid >> 3, bk = tid & 7;
+  const bool a_row = row0 + ar < m, b_col = col0 + bc < n;
+  const cplx* pa = ta ? jb.A + (int64_t)(row0 + ar) * jb.lda + ak : jb.A + (int64_t)ak * jb.lda + row0 + ar;
+  const int64_t a_step = ta ? GBK : (int64_t)GBK * jb.lda;
+  const cplx* pb = jb.B + (int64_t)(col0 + bc) * jb.ldb + bk;
+  cplx av = (a_row && ak < K) ? pa[0] : cmk(0.0, 0.0);
+  cplx bv = (b_col && bk < K) ? pb[0] : cmk(0.0, 0.0);
+  As[0][ak][ar] = to_dfc_bits(av);
+  Bs[0][bk][bc] = to_dfc_bits(bv);
+  __syncthreads();
+  int buf = 0;
   for (int k0 = 0; k0 < K; k0 += GBK) {
-    {
-      cplx av;
-      int r, kk;
-      if (jb.transA) {
-        r = tid >> 3; kk = tid & 7;
-        int gr = row0 + r, gk = k0 + kk;
-        av = (gr < m && gk < K) ? jb.A[(int64_t)gr * jb.lda + gk] : cmk(0.0, 0.0);
-      } else {
-        r = tid & 31; kk = tid >> 5;
-        int gr = row0 + r, gk = k0 + kk;
-        av = (gr < m && gk < K) ? jb.A[(int64_t)gk * jb.lda + gr] : cmk(0.0, 0.0);
-      }
-      As[kk][r] = to_dfc_bits(av);
-      int c = tid >> 3, kb = tid & 7;
-      int gc = col0 + c, gkb = k0 + kb;
-      Bs[kb][c] = to_dfc_bits((gc < n && gkb < K) ? jb.B[(int64_t)gc * jb.ldb + gkb] : cmk(0.0, 0.0));
+    const int k1 = k0 + GBK;
+    const bool more = k1 < K;
+    if (more) {
+      pa += a_step;
+      pb += GBK;
+      av = (a_row && k1 + ak < K) ? pa[0] : cmk(0.0, 0.0);
+      bv = (b_col && k1 + bk < K) ? pb[0] : cmk(0.0, 0.0);
     }
-    __syncthreads();
     if (c0) {
       if (c1) {
-        if (r1) tile_mac_df<true, true>(As, Bs, tr, tc, acc);
-        else tile_mac_df<false, true>(As, Bs, tr, tc, acc);
+        if (r1) tile_mac_df<true, true>(As[buf], Bs[buf], tr, tc, acc);
+        else tile_mac_df<false, true>(As[buf], Bs[buf], tr, tc, acc);
       } else {
-        if (r1) tile_mac_df<true, false>(As, Bs, tr, tc, acc);
-        else tile_mac_df<false, false>(As, Bs, tr, tc, acc);
+        if (r1) tile_mac_df<true, false>(As[buf], Bs[buf], tr, tc, acc);
+        else tile_mac_df<false, false>(As[buf], Bs[buf], tr, tc, acc);
       }
     }
 #pragma unroll
@@ -206,7 +217,12 @@ static __global__ void __launch_bounds__(256) k_zgemm_batched_df(const GemmJob* 
         df_norm(acc[x][y].rh, acc[x][y].rl);
         df_norm(acc[x][y].ih, acc[x][y].il);
       }
+    if (more) {
+      As[buf ^ 1][ak][ar] = to_dfc_bits(av);
+      Bs[buf ^ 1][bk][bc] = to_dfc_bits(bv);
+    }
     __syncthreads();
+    buf ^= 1;
   }
   const bool unit_alpha = jb.alpha.x == 1.0 && jb.alpha.y == 0.0;
   const bool minus_alpha = jb.alpha.x == -1.0 && jb.alpha.y == 0.0;
