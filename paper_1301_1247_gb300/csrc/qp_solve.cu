@@ -1519,6 +1519,27 @@ __global__ void k_fill_rhs(DevGeom g, const RhsCol* cols, int ncol, cplx* X) {
 }
 
 // columns c0.. of X: s * P (P: N x l)
+// Weights of exact trigonometric interpolation in the incidence direction: column c of the
+// K x ncol output holds phase_c D_K(psi_c - 2 pi k / K), k = 0..K-1, with D_K the
+// interpolation kernel of K equispaced points, D_K(t) = (sin((K - 1) t / 2) / sin(t / 2)
+// + cos(K t / 2)) / K (1 at t = 0).  A column with phase 0 (an evanescent plane wave, formed
+// directly) gets zeros.
+__global__ void k_interp_dirs(const double* psi, const cplx* phase, int64_t ncol, int K, cplx* out) {
+  const int64_t tot = ncol * K;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / K;
+    const int k = (int)(e - c * K);
+    const cplx ph = phase[c];
+    double dk = 0.0;
+    if (ph.x != 0.0 || ph.y != 0.0) {
+      const double t = psi[c] - 2.0 * HBS_PI * k / K;
+      const double sh = sin(0.5 * t);
+      dk = fabs(sh) < 1e-12 ? 1.0 : (sin(0.5 * (K - 1) * t) / sh + cos(0.5 * K * t)) / K;
+    }
+    out[e] = cmk(ph.x * dk, ph.y * dk);
+  }
+}
+
 __global__ void k_scaled_copy(const cplx* src, int64_t n, cplx f, cplx* dst) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     dst[e] = cmul(f, src[e]);
@@ -2095,38 +2116,37 @@ void solve_angles(Handle& h, const double* theta, int64_t n_theta, bool plain, R
       for (auto& G : gjobs) { G.rhs_col = (int)pos; pos += G.q + G.nw; }
       const int K = h.Kdir;
       DevBuf<cplx> Psel((size_t)h.rsel * cols);
-      std::vector<cplx> hint((size_t)K * cols, cmk(0, 0));
+      // per column: the direction angle and phase of its plane wave (propagating), or a zero
+      // phase (evanescent: formed directly below); the weights are formed on the device
+      std::vector<double> hpsi((size_t)cols, 0.0);
+      std::vector<cplx> hphase((size_t)cols, cmk(0, 0));
       std::vector<RhsCol> evan;
       std::vector<int64_t> evan_col;
       size_t rc = 0;
-      auto interp_col = [&](int64_t col, double psi, zc phase) {
-        cplx* dst = hint.data() + (size_t)col * K;
-        for (int k = 0; k < K; ++k) {
-          const double t = psi - 2.0 * M_PI * k / K;
-          const double sh = std::sin(0.5 * t);
-          double dk;
-          if (std::fabs(sh) < 1e-12) dk = 1.0;
-          else dk = (std::sin(0.5 * (K - 1) * t) / sh + std::cos(0.5 * K * t)) / K;
-          dst[k] = cmk(phase.real() * dk, phase.imag() * dk);
-        }
-      };
       for (int gg = 0; gg < ng; ++gg) {
         const GroupJob& G = gjobs[gg];
         for (int a2 = 0; a2 < G.q + G.nw; ++a2, ++rc) {
           const RhsCol& r = rcols[rc];
           const int64_t col = G.rhs_col + a2;
           if (r.ky.y == 0.0) {
-            const double psi = std::atan2(r.ky.x, r.kap);
+            hpsi[col] = std::atan2(r.ky.x, r.kap);
             const zc phase = r.sign * std::exp(zc(0.0, r.kap * h.dir_cx + r.ky.x * h.dir_cy));
-            interp_col(col, psi, phase);
+            hphase[col] = to_c(phase);
           } else {
             evan.push_back(r);
             evan_col.push_back(col);
           }
         }
       }
-      DevBuf<cplx> dint;
-      dint.upload(hint, s);
+      DevBuf<double> dpsi;
+      DevBuf<cplx> dphase, dint((size_t)K * cols);
+      dpsi.upload(hpsi, s);
+      dphase.upload(hphase, s);
+      {
+        prof::KScope _ks("k_interp_dirs", s);
+        k_interp_dirs<<<grid_1d((int64_t)K * cols), 256, 0, s>>>(dpsi.get(), dphase.get(), cols, K, dint.get());
+      }
+      HBS_LAUNCH_CHECK("k_interp_dirs");
       std::vector<GemmJob> gj(1);
       gj[0] = {h.Pdir.get(), dint.get(), Psel.get(), h.rsel, (int)cols, K, h.rsel, K, h.rsel, cmk(1, 0), cmk(0, 0), 0,
                0, 0, 0};
