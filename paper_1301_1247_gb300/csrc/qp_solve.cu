@@ -684,6 +684,8 @@ struct GroupJob {
   cplx* hm;                  // H = Vt QU  (rB x rC)
   cplx* hc;                  // H [Zc(C rows) | Psel(C rows)]  (rB x (l + rB + q + nw))
   cplx* wd;                  // Wood's: psi^T Wall(alpha) (2M) then w = that QU (rC), per mode
+  cplx* qcoef;               // per contour node m: Q's entries qff, qfn, qnf, qnn and 1 / det (5 M)
+  cplx* wpsi;                // Wood's sampling weights psi_t(s), s = S..4S-1 (3S per mode)
 };
 
 struct Dims {
@@ -1586,6 +1588,37 @@ __device__ __forceinline__ void q_node(double omega, double d, cplx alpha, cplx 
   *qnn = cscale(cmul(cmul(ee, cmk(0, 1)), cmul(sq, am)), 0.5);
 }
 
+// Per group, the factors the reduced kernels use many times over: Q's 2 x 2 block of each
+// contour node (its four entries and the reciprocal of its determinant) and the Wood's
+// sampling weights psi_t(s) of each Wood's mode.
+__global__ void k_red_tables(RedDims D, Dims DD, const GroupJob* groups) {
+  const GroupJob G = groups[blockIdx.y];
+  const int M = D.M, S3 = 3 * D.S;
+  const int64_t tot = M + (int64_t)G.nw * S3;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < M) {
+      const int m = (int)e;
+      cplx qff, qfn, qnf, qnn;
+      q_node(D.omega, D.d, G.alpha, G.ck[m], &qff, &qfn, &qnf, &qnn);
+      cplx* c = G.qcoef + 5 * (int64_t)m;
+      c[0] = qff;
+      c[1] = qfn;
+      c[2] = qnf;
+      c[3] = qnn;
+      c[4] = cdiv(cmk(1, 0), csub(cmul(qff, qnn), cmul(qfn, qnf)));
+    } else {
+      const int64_t q = e - M;
+      const int t = (int)(q / S3), sidx = (int)(q % S3);
+      G.wpsi[q] = wood_psi(DD, G, t, D.S + sidx);
+    }
+  }
+}
+
+// psi_t(s) for s in [S, 4S) from the group's table.
+__device__ __forceinline__ cplx wood_psi_tab(const GroupJob& G, int S, int t, int sidx) {
+  return G.wpsi[(int64_t)t * 3 * S + (sidx - S)];
+}
+
 // Per group: vt = (V_L + alpha V_R)^T and qu = Q^{-1} (alpha U_L - alpha^{-2} U_R).
 __global__ void k_red_prep(RedDims D, const GroupJob* groups) {
   const GroupJob G = groups[blockIdx.y];
@@ -1599,14 +1632,13 @@ __global__ void k_red_prep(RedDims D, const GroupJob* groups) {
     } else {
       const int64_t q = e - nv;
       const int m = (int)(q % M), c = (int)(q / M);
-      cplx qff, qfn, qnf, qnn;
-      q_node(D.omega, D.d, G.alpha, G.ck[m], &qff, &qfn, &qnf, &qnn);
-      const cplx det = csub(cmul(qff, qnn), cmul(qfn, qnf));
+      const cplx* qc = G.qcoef + 5 * (int64_t)m;
+      const cplx qff = qc[0], qfn = qc[1], qnf = qc[2], qnn = qc[3], idet = qc[4];
       const int64_t o = (int64_t)c * M2;
       cplx uf = csub(cmul(G.alpha, G.ul[m + o]), cmul(ia2, G.ur[m + o]));
       cplx un = csub(cmul(G.alpha, G.ul[M + m + o]), cmul(ia2, G.ur[M + m + o]));
-      G.qu[m + o] = cdiv(csub(cmul(qnn, uf), cmul(qfn, un)), det);
-      G.qu[M + m + o] = cdiv(csub(cmul(qff, un), cmul(qnf, uf)), det);
+      G.qu[m + o] = cmul(csub(cmul(qnn, uf), cmul(qfn, un)), idet);
+      G.qu[M + m + o] = cmul(csub(cmul(qff, un), cmul(qnf, uf)), idet);
     }
   }
 }
@@ -1621,7 +1653,7 @@ __global__ void k_red_wood(RedDims D, const GroupJob* groups, Dims DD) {
     for (int mm = threadIdx.x; mm < M2; mm += blockDim.x) {
       cplx acc = cmk(0, 0);
       for (int sidx = D.S; sidx < S4; ++sidx) {
-        cplx p = wood_psi(DD, G, t, sidx);
+        cplx p = wood_psi_tab(G, D.S, t, sidx);
         if (p.x == 0.0 && p.y == 0.0) continue;
         acc = cfma(p, cfma(G.alpha, G.sr[(int64_t)mm * S4 + sidx], G.sl[(int64_t)mm * S4 + sidx]), acc);
       }
@@ -1645,7 +1677,7 @@ __device__ __forceinline__ cplx wood_phi(const Dims& DD, const GroupJob& G, int 
   for (int jj = 0; jj < 3; ++jj) {
     cplx part = cmk(0, 0);
     for (int sidx = S; sidx < 4 * S; ++sidx) {
-      cplx p = wood_psi(DD, G, t, sidx);
+      cplx p = wood_psi_tab(G, S, t, sidx);
       if (p.x == 0.0 && p.y == 0.0) continue;
       part = cfma(p, X[4 * S * jj + sidx], part);
     }
@@ -1701,7 +1733,7 @@ __global__ void k_red_assemble(RedDims D, Dims DD, const GroupJob* groups, const
       if (kind == 2) {
         cplx acc = cmk(0, 0);
         for (int sidx = D.S; sidx < 4 * D.S; ++sidx) {
-          cplx p = wood_psi(DD, G, tw, sidx);
+          cplx p = wood_psi_tab(G, D.S, tw, sidx);
           if (p.x == 0.0 && p.y == 0.0) continue;
           acc = cfma(p, sample_point_pw(DD, G, idx, sidx, y0), acc);
         }
@@ -1713,7 +1745,54 @@ __global__ void k_red_assemble(RedDims D, Dims DD, const GroupJob* groups, const
   }
 }
 
+// Sum_j A[j ld] x[j] for an FP64 column-strided A and a vector x in shared memory: in FP64,
+// or (DF) in double-float on the FP32 pipes, A split on load and x already held as pairs,
+// renormalised every 8 terms.  Eight loads of A are issued together ahead of their
+// multiply-adds (each thread runs a long dot product alone; one load at a time would wait
+// out the L2 latency at every term).
+template <bool DF>
+__device__ __forceinline__ cplx red_dot(const cplx* A, int64_t ld, const cplx* x, int n) {
+  if constexpr (DF) {
+    const dfc* xd = reinterpret_cast<const dfc*>(x);
+    dfc acc{0.f, 0.f, 0.f, 0.f};
+    int j = 0;
+    for (; j + 8 <= n; j += 8) {
+      cplx a[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[q] = A[(int64_t)(j + q) * ld];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) dfc_mac_tile(to_dfc_bits(a[q]), xd[j + q], acc);
+      dfc_norm(acc);
+    }
+    for (; j < n; ++j) dfc_mac_tile(to_dfc_bits(A[(int64_t)j * ld]), xd[j], acc);
+    dfc_norm(acc);
+    return from_dfc_bits(acc);
+  } else {
+    cplx acc = cmk(0, 0);
+    int j = 0;
+    for (; j + 8 <= n; j += 8) {
+      cplx a[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[q] = A[(int64_t)(j + q) * ld];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc = cfma(a[q], x[j + q], acc);
+    }
+    for (; j < n; ++j) acc = cfma(A[(int64_t)j * ld], x[j], acc);
+    return acc;
+  }
+}
+
+// Entry i of a shared vector read by red_dot: FP64, or (DF) its double-float pair in place.
+template <bool DF>
+__device__ __forceinline__ void red_store(cplx* x, int i, cplx v) {
+  if constexpr (DF) reinterpret_cast<dfc*>(x)[i] = to_dfc_bits(v);
+  else x[i] = v;
+}
+
 // Bragg amplitudes from the reduced solution: gamma, xi = Q^{-1} U gamma, samples, DFT.
+// The image columns of the neighbour unknowns enter as w = [alpha^{-1} u_1 + alpha u_2; u_B]
+// (both images' columns of Z and of the E rows are the same skeleton columns).
+template <bool DF>
 __global__ void k_red_bragg(RedDims D, Dims DD, const GroupJob* groups, const AngleJob* angles, const cplx* Zc,
                             const cplx* Psel, const cplx* EZ, const cplx* EP, const cplx* Rpool, double y0,
                             cplx* cout, cplx* dout, double* flux) {
@@ -1721,50 +1800,39 @@ __global__ void k_red_bragg(RedDims D, Dims DD, const GroupJob* groups, const An
   const AngleJob A = angles[blockIdx.x];
   const GroupJob G = groups[A.group];
   const int l = D.l, rB = D.rB, rC = D.rC, rsel = D.rsel, S = D.S, S4 = 4 * D.S, S12 = 12 * D.S, M2 = 2 * D.M;
-  const int n = G.nsys;
-  cplx* gam = sh;
-  cplx* xi = sh + rC;
-  cplx* samp = sh + rC + M2;
+  const int n = G.nsys, nz = l + rB;
+  cplx* w = sh;
+  cplx* gam = sh + nz;
+  cplx* xi = gam + rC;
+  cplx* samp = xi + M2;
   const cplx* u = Rpool + G.r_off + (int64_t)A.col * n;
   const cplx ia = cdiv(cmk(1, 0), G.alpha);
+  for (int j = threadIdx.x; j < nz; j += blockDim.x)
+    red_store<DF>(w, j, j < l ? cadd(cmul(ia, u[j]), cmul(G.alpha, u[l + j])) : u[2 * l + (j - l)]);
+  __syncthreads();
   for (int c = threadIdx.x; c < rC; c += blockDim.x) {
     const int row = 2 * l + c;
-    cplx acc = cmk(0, 0);
-    for (int j = 0; j < 2 * l; ++j) {
-      const cplx f = j < l ? ia : G.alpha;
-      acc = cfma(cmul(f, Zc[row + (int64_t)(j < l ? j : j - l) * rsel]), u[j], acc);
-    }
-    for (int k = 0; k < rB; ++k) acc = cfma(Zc[row + (int64_t)(l + k) * rsel], u[2 * l + k], acc);
+    cplx acc = red_dot<DF>(Zc + row, rsel, w, nz);
     for (int t = 0; t < G.nw; ++t) acc = cfma(Psel[row + (int64_t)(G.rhs_col + G.q + t) * rsel], u[2 * l + rB + t], acc);
-    gam[c] = csub(acc, Psel[row + (int64_t)(G.rhs_col + A.col) * rsel]);
+    red_store<DF>(gam, c, csub(acc, Psel[row + (int64_t)(G.rhs_col + A.col) * rsel]));
   }
   __syncthreads();
-  for (int mm = threadIdx.x; mm < M2; mm += blockDim.x) {
-    cplx acc = cmk(0, 0);
-    for (int c = 0; c < rC; ++c) acc = cfma(G.qu[mm + (int64_t)c * M2], gam[c], acc);
-    xi[mm] = acc;
-  }
+  for (int mm = threadIdx.x; mm < M2; mm += blockDim.x) red_store<DF>(xi, mm, red_dot<DF>(G.qu + mm, M2, gam, rC));
   __syncthreads();
   for (int r = threadIdx.x; r < 2 * S; r += blockDim.x) {
     cplx acc = cmk(0, 0);
     cplx aj = ia;
     for (int jj = 0; jj < 3; ++jj) {
       const int row = S4 * jj + r;
-      cplx part = EP[row + (int64_t)(G.rhs_col + A.col) * S12];
-      for (int j = 0; j < 2 * l; ++j) {
-        const cplx f = j < l ? ia : G.alpha;
-        part = csub(part, cmul(cmul(f, EZ[row + (int64_t)(j < l ? j : j - l) * S12]), u[j]));
-      }
-      for (int k = 0; k < rB; ++k) part = csub(part, cmul(EZ[row + (int64_t)(l + k) * S12], u[2 * l + k]));
+      cplx part = csub(EP[row + (int64_t)(G.rhs_col + A.col) * S12], red_dot<DF>(EZ + row, S12, w, nz));
       for (int t = 0; t < G.nw; ++t)
         part = csub(part, cmul(EP[row + (int64_t)(G.rhs_col + G.q + t) * S12], u[2 * l + rB + t]));
       acc = cfma(aj, part, acc);
       aj = cmul(aj, G.alpha);
     }
-    for (int mm = 0; mm < M2; ++mm) {
-      cplx wv = cfma(G.alpha, G.sr[(int64_t)mm * S4 + r], G.sl[(int64_t)mm * S4 + r]);
-      acc = cfma(wv, xi[mm], acc);
-    }
+    // the wall samples (SL + alpha SR) xi
+    acc = cadd(acc, red_dot<DF>(G.sl + r, S4, xi, M2));
+    acc = cfma(G.alpha, red_dot<DF>(G.sr + r, S4, xi, M2), acc);
     for (int t = 0; t < G.nw; ++t) acc = cfma(sample_point_pw(DD, G, t, r, y0), u[2 * l + rB + t], acc);
     samp[r] = acc;
   }
@@ -1836,9 +1904,10 @@ static void reduced_batch(Handle& h, std::vector<GroupJob>& gjobs, std::vector<s
     run_gemms(gj, s);
   }
   // per-group work arrays
-  int64_t nvt = 0, nqu = 0, nhm = 0, nhc = 0, nwd = 0, so = 0, ro = 0;
+  int64_t nvt = 0, nqu = 0, nhm = 0, nhc = 0, nwd = 0, nps = 0, so = 0, ro = 0;
   for (auto& G : gjobs) {
     G.nsys = 2 * l + rB + G.nw;
+    nps += (int64_t)G.nw * 3 * S;
     nvt += (int64_t)rB * M2;
     nqu += (int64_t)M2 * rC;
     nhm += (int64_t)rB * rC;
@@ -1849,10 +1918,13 @@ static void reduced_batch(Handle& h, std::vector<GroupJob>& gjobs, std::vector<s
   }
   DevBuf<cplx> vt(std::max<int64_t>(nvt, 1)), qu(std::max<int64_t>(nqu, 1)), hm(std::max<int64_t>(nhm, 1)),
       hc(std::max<int64_t>(nhc, 1)), wd(std::max<int64_t>(nwd, 1)), Sp(std::max<int64_t>(so, 1)),
-      Rp(std::max<int64_t>(ro, 1));
+      Rp(std::max<int64_t>(ro, 1)), qcoef((size_t)ng * 5 * M), wpsi(std::max<int64_t>(nps, 1));
   {
-    int64_t a = 0, b = 0, c = 0, d2 = 0, e = 0;
-    for (auto& G : gjobs) {
+    int64_t a = 0, b = 0, c = 0, d2 = 0, e = 0, f = 0;
+    for (size_t gg = 0; gg < gjobs.size(); ++gg) {
+      GroupJob& G = gjobs[gg];
+      G.qcoef = qcoef.get() + 5 * (int64_t)M * gg;
+      G.wpsi = wpsi.get() + f; f += (int64_t)G.nw * 3 * S;
       const ContourData& cd = h.contours[G.contour];
       G.ul = cd.UL.get(); G.ur = cd.UR.get(); G.vl = cd.VL.get(); G.vr = cd.VR.get();
       G.vt = vt.get() + a; a += (int64_t)rB * M2;
@@ -1866,6 +1938,11 @@ static void reduced_batch(Handle& h, std::vector<GroupJob>& gjobs, std::vector<s
   dg.upload(gjobs, s);
   RedDims R{l, M, S, rB, rC, rsel, h.d, h.omega};
   Dims DD{l, M, S, 0, h.d, h.omega, 0};
+  {
+    prof::KScope _ks("k_red_tables", s);
+    k_red_tables<<<dim3((M + 12 * S + 255) / 256, ng), 256, 0, s>>>(R, DD, dg.get());
+  }
+  HBS_LAUNCH_CHECK("k_red_tables");
   {
     prof::KScope _ks("k_red_prep", s);
     k_red_prep<<<dim3(64, ng), 256, 0, s>>>(R, dg.get());
@@ -1918,9 +1995,19 @@ static void reduced_batch(Handle& h, std::vector<GroupJob>& gjobs, std::vector<s
   DevBuf<double> fbuf(ajobs.size());
   {
     prof::KScope _ks("k_red_bragg", s);
-    const size_t shm = (size_t)(rC + M2 + 2 * S) * sizeof(cplx);
-    k_red_bragg<<<(unsigned)ajobs.size(), 128, shm, s>>>(R, DD, dg.get(), da.get(), h.Zc.get(), Psel, h.EZ.get(),
-                                                         EP.get(), Rp.get(), h.y0, cbuf.get(), dbuf.get(), fbuf.get());
+    const size_t shm = (size_t)(l + rB + rC + M2 + 2 * S) * sizeof(cplx);
+    // double-float products on double-float handles (the FP64 pipe's rate bounds this kernel)
+    const bool df = gemm_double_float();
+    const void* fn = df ? (const void*)k_red_bragg<true> : (const void*)k_red_bragg<false>;
+    HBS_CUDA(raise_smem_limit(fn, shm));
+    if (df)
+      k_red_bragg<true><<<(unsigned)ajobs.size(), 128, shm, s>>>(R, DD, dg.get(), da.get(), h.Zc.get(), Psel,
+                                                                 h.EZ.get(), EP.get(), Rp.get(), h.y0, cbuf.get(),
+                                                                 dbuf.get(), fbuf.get());
+    else
+      k_red_bragg<false><<<(unsigned)ajobs.size(), 128, shm, s>>>(R, DD, dg.get(), da.get(), h.Zc.get(), Psel,
+                                                                  h.EZ.get(), EP.get(), Rp.get(), h.y0, cbuf.get(),
+                                                                  dbuf.get(), fbuf.get());
   }
   HBS_LAUNCH_CHECK("k_red_bragg");
   auto hcv = cbuf.download(s), hdv = dbuf.download(s);
