@@ -27,6 +27,9 @@ struct Level {
   DevBuf<cplx> E, F, G, Dhat;   // E: n x k, F: F* (k x n), G: n x n, Dhat: k x k
   DevBuf<double> cx, cy, rad;   // enclosing circle of the node's original points
   std::vector<double> h_rad;
+  // Not compressed (level 1 when the root stays small): P = I, so Dhat = D, E = F* = I and
+  // G = 0; the telescoping sweeps pass the level's vectors through unchanged.
+  bool passthru = false;
 };
 
 // Periodizer blocks on one Sommerfeld contour (Secs. 2.2-2.4).

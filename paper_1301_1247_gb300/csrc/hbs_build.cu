@@ -531,6 +531,18 @@ DevGeom Handle_geom(const Handle& h) {
 static bool big_cpqr(const CpqrJob& j) { return (double)j.m * j.n * std::min(j.m, j.n) > 4e6; }
 static bool big_inverse(int n) { return n > 128; }
 
+// Largest root (sum of the level-2 skeletons) for which level 1 is left uncompressed.  At the
+// top of the tree the level-1 ID and inversions are latency-bound work on two nodes; without
+// them the root inverts the level-2 skeletons' coupled system directly (the same system,
+// one interpolative decomposition fewer).
+constexpr int kPassThroughRootMax = 1536;
+
+static bool passthrough_level(const Handle& h, int l) {
+  if (l != 1 || h.L < 2) return false;
+  const Level& lv = h.levels[1];
+  return lv.n.size() == 2 && lv.n[0] + lv.n[1] <= kPassThroughRootMax;
+}
+
 // Batched CPQR-ID of the matrices described by `jobs`.  Returns ranks.
 // Small matrices go to one launch with one CTA each; large ones (the top tree levels,
 // where a level has few nodes) share one persistent launch on all SMs (pqr.cu).
@@ -788,6 +800,50 @@ void build_hbs_multi(const std::vector<Handle*>& hs, cudaStream_t s) {
       }
       HBS_LAUNCH_CHECK("k_fill_d root");
       batched_inverse(ij, s, "root block");
+    }
+    // ---- uncompressed levels: D only, which is also Dhat; identity order, no T, E, F*, G
+    {
+      std::vector<LevelTask> rest;
+      std::vector<DJob> dj;
+      std::vector<Level*> plv;
+      for (auto& tk : tasks) {
+        Handle& h = *tk.h;
+        if (!passthrough_level(h, tk.l)) {
+          rest.push_back(tk);
+          continue;
+        }
+        Level& lv = h.levels[tk.l];
+        Level& ch = h.levels[tk.l + 1];
+        lv.passthru = true;
+        lv.k = lv.n;
+        lv.t_off.assign(lv.count, 0);
+        lv.e_off.assign(lv.count, 0);
+        lv.f_off.assign(lv.count, 0);
+        lv.g_off.assign(lv.count, 0);
+        lv.dh_off.assign(lv.count, 0);
+        int64_t dpool = 0;
+        std::vector<int> order(lv.ntot);
+        for (int j = 0; j < lv.count; ++j) {
+          lv.dh_off[j] = dpool;
+          dpool += (int64_t)lv.n[j] * lv.n[j];
+          for (int i = 0; i < lv.n[j]; ++i) order[lv.off[j] + i] = i;
+          h.factor_bytes += 16.0 * lv.n[j] * lv.n[j];
+        }
+        lv.Dhat.alloc(std::max<int64_t>(dpool, 1));
+        lv.perm.upload(order, s);
+        for (int j = 0; j < lv.count; ++j)
+          dj.push_back({tk.g, lv.idx.get() + lv.off[j], lv.Dhat.get() + lv.dh_off[j], lv.n[j], ch.k[2 * j], 0,
+                        ch.Dhat.get() + ch.dh_off[2 * j], ch.Dhat.get() + ch.dh_off[2 * j + 1]});
+      }
+      if (!dj.empty()) {
+        DevBuf<DJob> ddj = upload_jobs(dj, s);
+        {
+          prof::KScope _ks("k_fill_d", s);
+          launch_jobs_y(ddj, dj.size(), [&](const DJob* p, unsigned ny) { k_fill_d<<<dim3(64, ny), 256, 0, s>>>(p); });
+        }
+        HBS_LAUNCH_CHECK("k_fill_d pass-through");
+      }
+      tasks.swap(rest);
     }
     if (tasks.empty()) continue;
 
@@ -1223,6 +1279,11 @@ static void sweep_upward_level(const Handle& H, int l, const cplx* b, int64_t nr
   if ((int)up.size() < H.L + 1) up.resize(H.L + 1);
   up[l - 1].alloc(std::max<int64_t>(pnt * nrhs, 1));
   const cplx* in = l == H.L ? b : up[l].get();
+  if (lv.passthru) {  // F* = E^T = I: the parent's vector is this level's (same layout, pnt = ntot)
+    if (pnt * nrhs > 0)
+      HBS_CUDA(cudaMemcpyAsync(up[l - 1].get(), in, sizeof(cplx) * pnt * nrhs, cudaMemcpyDeviceToDevice, s));
+    return;
+  }
   std::vector<GemmJob> gj;
   for (int j = 0; j < lv.count; ++j) {
     const int n = lv.n[j], k = lv.k[j];
@@ -1260,6 +1321,11 @@ static void sweep_finish(const Handle& H, const cplx* b, cplx* xout, int64_t nrh
     const Level& lv = levels[l];
     const Level& pa = levels[l - 1];
     cplx* outp = l == Lv ? xout : dn[l].get();
+    if (lv.passthru) {  // G = 0, E = F*^T = I: x_tau = x^_tau (same layout)
+      if (lv.ntot * nrhs > 0)
+        HBS_CUDA(cudaMemcpyAsync(outp, dn[l - 1].get(), sizeof(cplx) * lv.ntot * nrhs, cudaMemcpyDeviceToDevice, s));
+      continue;
+    }
     std::vector<GemmJob> gj;
     for (int j = 0; j < lv.count; ++j) {
       const int n = lv.n[j];

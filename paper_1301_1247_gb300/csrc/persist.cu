@@ -118,6 +118,7 @@ void visit(Ar& ar, Handle& h) {
     ar.vec(lv.e_off); ar.vec(lv.f_off); ar.vec(lv.g_off); ar.vec(lv.dh_off);
     ar.dev(lv.E); ar.dev(lv.F); ar.dev(lv.G); ar.dev(lv.Dhat);
     ar.dev(lv.cx); ar.dev(lv.cy); ar.dev(lv.rad); ar.vec(lv.h_rad);
+    ar.pod(lv.passthru);
   }
   ar.pod(h.nroot); ar.dev(h.Groot); ar.pod(h.max_rank);
   ar.pod(h.nb_rank); ar.pod(h.nb_R); ar.pod(h.nb_np);
@@ -149,7 +150,7 @@ Header make_header() {
   hd.opts_bytes = (uint32_t)sizeof(hbs_options);
   hd.cplx_bytes = (uint32_t)sizeof(cplx);
   hd.int2_bytes = (uint32_t)sizeof(int2);
-  hd.handle_fields = 2;  // layout revision of visit()
+  hd.handle_fields = 3;  // layout revision of visit()
   return hd;
 }
 
