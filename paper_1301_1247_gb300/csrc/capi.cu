@@ -26,6 +26,11 @@ bool& gemm_tensor() {
   return tc;
 }
 
+bool& background_chain() {
+  static thread_local bool bg = false;
+  return bg;
+}
+
 std::mutex& coop_mutex() {
   static std::mutex mu;
   return mu;

@@ -133,6 +133,10 @@ bool& gemm_double_float();
 std::mutex& coop_mutex();
 // Large products on the tensor cores (digit-plane splitting) on this thread.
 bool& gemm_tensor();
+// True on the thread that builds the periodizer while another thread runs the compression
+// chain (the build's critical path) on a higher-priority stream: this thread's persistent
+// QRs take one CTA per SM instead of two and leave half of every SM to the compression.
+bool& background_chain();
 
 // Sets the thread's arithmetic modes from an HBS_PRECISION_* value for a call's duration.
 struct GemmModeScope {

@@ -944,7 +944,7 @@ static int pqr_grid(size_t smem) {
   int per_sm = 0;
   HBS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pqr<DF>, kNT, smem));
   if (per_sm < 1) throw Error(HBS_ERR_CUDA, "persistent QR kernel does not fit on an SM");
-  return sms * std::min(per_sm, 2);
+  return sms * std::min(per_sm, background_chain() ? 1 : 2);
 }
 
 void pqr_run(const std::vector<PqrSpec>& specs_in, double tol, cudaStream_t s, PqrOut& out, bool equal_steps) {

@@ -144,9 +144,20 @@ struct HbsWorker {
 };
 }  // namespace
 
+namespace {
+// Marks this thread as the background chain while the compression runs beside it.
+struct BackgroundScope {
+  bool prev;
+  explicit BackgroundScope(bool on) : prev(background_chain()) { background_chain() = on || prev; }
+  void end() { background_chain() = prev; }
+  ~BackgroundScope() { end(); }
+};
+}  // namespace
+
 void build_periodizer(Handle& h, cudaStream_t s, bool with_hbs) {
   HbsWorker hbs_worker;
   if (with_hbs) hbs_worker.start(h);
+  BackgroundScope background(with_hbs);
   const int64_t N = h.N;
   const DevGeom g = Handle_geom(h);
   const double d = h.d, omega = h.omega;
@@ -175,150 +186,6 @@ void build_periodizer(Handle& h, cudaStream_t s, bool with_hbs) {
   }
 
   prof::PhaseSeq ph(s);
-  ph.next("build:neighbour_id");
-  // ---- neighbour proxy circle and near points (Sec. 3.2)
-  double R = h.opts.nb_radius;
-  if (!(R > 0.0)) R = rsrc > 1.05 * rmax ? 0.5 * (rmax + rsrc) : 1.1 * rmax;
-  std::vector<int64_t> near_m, near_p;
-  double rfar = 1e300;
-  for (int64_t i = 0; i < N; ++i) {
-    double dm = std::hypot(h.hx[i] - d - cx, h.hy[i] - cy);
-    double dp = std::hypot(h.hx[i] + d - cx, h.hy[i] - cy);
-    if (dm < R) near_m.push_back(i); else rfar = std::min(rfar, dm);
-    if (dp < R) near_p.push_back(i); else rfar = std::min(rfar, dp);
-  }
-  int np = h.opts.nb_proxies;
-  if (np <= 0) {
-    // The fields of image sources beyond r_far restricted to the obstacle (radius r_max)
-    // have Fourier-Bessel modes decaying like (r_max / r_far)^|m| past |m| ~ w R; the
-    // proxy circle must span modes up to that cut-off (an ID needs the span only).
-    double q = std::min(rmax / rfar, 0.97);
-    np = (int)(2.0 * (std::ceil(omega * R) + std::ceil(std::log(1e-16) / std::log(q)) + 8));
-    np = std::max(64, std::min(np, 2048));
-    np = (np + 7) / 8 * 8;
-  }
-  const double wp = 2.0 * M_PI * R / np;
-  h.nb_R = R;
-  h.nb_np = np;
-  {
-    const int nm = (int)near_m.size(), npn = (int)near_p.size();
-    const int64_t m = nm + npn + np;
-    DevBuf<int64_t> dnm, dnp;
-    dnm.upload(near_m, s);
-    dnp.upload(near_p, s);
-    DevBuf<cplx> Mt(m * N);
-    {
-      prof::KScope _ks("k_fill_nb", s);
-      const size_t dsm = 2 * (size_t)np * sizeof(double);
-      HBS_CUDA(raise_smem_limit((const void*)k_fill_nb, dsm));
-      k_fill_nb<<<grid_1d(m * N), 256, dsm, s>>>(g, dnm.get(), nm, dnp.get(), npn, d, cx, cy, R, np, wp, Mt.get());
-    }
-    HBS_LAUNCH_CHECK("k_fill_nb");
-    // Row ID of the neighbour interactions (Def. 3.1).  The skeleton is chosen by a
-    // column-pivoted QR among at most 4096 candidate boundary nodes (every stride-th): their
-    // columns of Mt are smooth functions of the node, so candidates far finer than the
-    // wavelength lose nothing.  Every node's interpolation coefficients then follow by
-    // least squares against the skeleton columns, t_i = R11^{-1} Q1^H Mt(:, i), which for
-    // the candidates is exactly T = R11^{-1} R12 of the QR.
-    // Candidates are whole nodes (both unknowns of a transmission node, whose rows differ).
-    const int comps = h.comps;
-    const int64_t nodes = N / comps;
-    const int64_t stride = std::max<int64_t>(1, (N + 4095) / 4096);
-    const int64_t ncn = (nodes + stride - 1) / stride;  // candidate nodes
-    const int64_t nc = ncn * comps;
-    DevBuf<cplx> Mc((size_t)m * nc);
-    std::vector<int64_t> cand(nc);
-    for (int64_t c = 0; c < ncn; ++c)
-      for (int u = 0; u < comps; ++u) cand[c * comps + u] = c * stride * comps + u;
-    if (comps == 1) {
-      HBS_CUDA(cudaMemcpy2DAsync(Mc.get(), sizeof(cplx) * m, Mt.get(), sizeof(cplx) * m * stride, sizeof(cplx) * m,
-                                 nc, cudaMemcpyDeviceToDevice, s));
-    } else {
-      DevBuf<int64_t> dcand;
-      dcand.upload(cand, s);
-      prof::KScope _ks("k_gather_cols", s);
-      k_gather_cols<<<grid_1d(m * nc), 256, 0, s>>>(Mt.get(), m, m, dcand.get(), nc, Mc.get(), m);
-      HBS_CUDA(cudaStreamSynchronize(s));  // dcand goes out of scope
-    }
-    const int kcap = (int)std::min<int64_t>(std::min<int64_t>(m, nc), 4096);
-    DevBuf<int> cperm(nc);
-    PqrOut qr;
-    {
-      std::vector<PqrSpec> sp{{Mc.get(), m, nc, kcap, cperm.get(), nullptr}};
-      pqr_run(sp, h.tol, s, qr);
-    }
-    const int l = qr.rank[0];
-    h.nb_rank = l;
-    std::vector<int> hpiv = qr.piv.download(s, l);
-    std::vector<int64_t> J(l);
-    for (int i = 0; i < l; ++i) J[i] = cand[hpiv[i]];
-    h.nb_skel.upload(J, s);
-    h.Rm.alloc(std::max<int64_t>((int64_t)l * N, 1));
-    h.Rp.alloc(std::max<int64_t>((int64_t)l * N, 1));
-    h.Pnb.alloc(std::max<int64_t>((int64_t)l * N, 1));
-    h.nb_residual = 0.0;
-    if (l > 0) {
-      {
-        prof::KScope _ks("k_fill_r", s);
-        k_fill_r<<<grid_1d((int64_t)l * N), 256, 0, s>>>(g, h.nb_skel.get(), l, d, h.Rm.get(), h.Rp.get());
-      }
-      HBS_LAUNCH_CHECK("k_fill_r");
-      DevBuf<cplx> Qc((size_t)m * l), Tall((size_t)l * N);
-      {
-        prof::KScope _ks("k_form_qc", s);
-        k_form_qc<<<l, 256, 0, s>>>(Mc.get(), m, qr.piv.get(), qr.v0.get(), qr.tau.get(), l, Qc.get());
-      }
-      HBS_LAUNCH_CHECK("neighbour Q1");
-      // Tall = Q1^H Mt (l x N), then R11^{-1} in place; skeleton nodes get unit columns.
-      std::vector<GemmJob> gj(1);
-      gj[0] = GemmJob{Qc.get(), Mt.get(), Tall.get(), l, (int)N, (int)m, (int)m, (int)m, l,
-                      cmk(1.0, 0.0), cmk(0.0, 0.0), 0, 0, 0, 1};
-      run_gemms(gj, s);
-      pqr_solve_r11(Mc.get(), m, qr, 0, l, Tall.get(), l, N, s);
-      {
-        prof::KScope _ks("k_set_unit_cols", s);
-        k_set_unit_cols<<<grid_1d((int64_t)l * l), 256, 0, s>>>(Tall.get(), l, h.nb_skel.get());
-      }
-      {
-        prof::KScope _ks("k_transpose", s);
-        k_transpose<<<grid_1d((int64_t)l * N), 256, 0, s>>>(Tall.get(), l, N, h.Pnb.get());
-      }
-      HBS_LAUNCH_CHECK("neighbour interpolation");
-      // Check on nodes half-way between candidates: |Mt(:, i) - Mt(:, J) t_i| / |Mt(:, i)|.
-      if (stride > 1) {
-        const int64_t nchk_n = std::min<int64_t>(ncn - 1, 4096 / comps);
-        const int64_t nchk = nchk_n * comps;
-        std::vector<int64_t> chk(nchk);
-        for (int64_t c = 0; c < nchk_n; ++c) {
-          const int64_t node = std::min<int64_t>(nodes - 1, ((c * (ncn - 1)) / nchk_n) * stride + stride / 2);
-          for (int u = 0; u < comps; ++u) chk[c * comps + u] = node * comps + u;
-        }
-        DevBuf<int64_t> dchk;
-        dchk.upload(chk, s);
-        DevBuf<cplx> G((size_t)m * l), Ms((size_t)m * nchk), Ts((size_t)l * nchk), Rec((size_t)m * nchk);
-        {
-          prof::KScope _ks("k_gather_cols", s);
-          k_gather_cols<<<grid_1d((int64_t)m * l), 256, 0, s>>>(Mt.get(), m, m, h.nb_skel.get(), l, G.get(), m);
-          k_gather_cols<<<grid_1d(m * nchk), 256, 0, s>>>(Mt.get(), m, m, dchk.get(), nchk, Ms.get(), m);
-          k_gather_cols<<<grid_1d((int64_t)l * nchk), 256, 0, s>>>(Tall.get(), l, l, dchk.get(), nchk, Ts.get(), l);
-        }
-        std::vector<GemmJob> cj(1);
-        cj[0] = GemmJob{G.get(), Ts.get(), Rec.get(), (int)m, (int)nchk, l, (int)m, l, (int)m,
-                        cmk(1.0, 0.0), cmk(0.0, 0.0), 0, 0, 0, 0};
-        run_gemms(cj, s);
-        DevBuf<double> acc(2);
-        HBS_CUDA(cudaMemsetAsync(acc.get(), 0, 2 * sizeof(double), s));
-        {
-          prof::KScope _ks("k_diff_norm2", s);
-          k_diff_norm2<<<grid_1d(m * nchk), 256, 0, s>>>(Rec.get(), m, Ms.get(), m, (int)m, (int)nchk, acc.get());
-        }
-        auto ha = acc.download(s);
-        h.nb_residual = ha[1] > 0 ? std::sqrt(ha[0] / ha[1]) : 0.0;
-      }
-    }
-    HBS_CUDA(cudaStreamSynchronize(s));
-  }
-  const int l = h.nb_rank;
   ph.next("build:periodizer_fill");
 
   // ---- Sommerfeld contours (Sec. 2.3)
@@ -491,6 +358,154 @@ void build_periodizer(Handle& h, cudaStream_t s, bool with_hbs) {
   h.rE = franks[2];
   HBS_LAUNCH_CHECK("periodizer ids");
 
+  // ---- neighbour interactions (after the periodizer: with the compression running beside
+  // this thread, the periodizer's large persistent QR then overlaps the leaf levels, whose
+  // kernels are not cooperative, instead of a level that waits for the cooperative-launch lock)
+  ph.next("build:neighbour_id");
+  // ---- neighbour proxy circle and near points (Sec. 3.2)
+  double R = h.opts.nb_radius;
+  if (!(R > 0.0)) R = rsrc > 1.05 * rmax ? 0.5 * (rmax + rsrc) : 1.1 * rmax;
+  std::vector<int64_t> near_m, near_p;
+  double rfar = 1e300;
+  for (int64_t i = 0; i < N; ++i) {
+    double dm = std::hypot(h.hx[i] - d - cx, h.hy[i] - cy);
+    double dp = std::hypot(h.hx[i] + d - cx, h.hy[i] - cy);
+    if (dm < R) near_m.push_back(i); else rfar = std::min(rfar, dm);
+    if (dp < R) near_p.push_back(i); else rfar = std::min(rfar, dp);
+  }
+  int np = h.opts.nb_proxies;
+  if (np <= 0) {
+    // The fields of image sources beyond r_far restricted to the obstacle (radius r_max)
+    // have Fourier-Bessel modes decaying like (r_max / r_far)^|m| past |m| ~ w R; the
+    // proxy circle must span modes up to that cut-off (an ID needs the span only).
+    double q = std::min(rmax / rfar, 0.97);
+    np = (int)(2.0 * (std::ceil(omega * R) + std::ceil(std::log(1e-16) / std::log(q)) + 8));
+    np = std::max(64, std::min(np, 2048));
+    np = (np + 7) / 8 * 8;
+  }
+  const double wp = 2.0 * M_PI * R / np;
+  h.nb_R = R;
+  h.nb_np = np;
+  {
+    const int nm = (int)near_m.size(), npn = (int)near_p.size();
+    const int64_t m = nm + npn + np;
+    DevBuf<int64_t> dnm, dnp;
+    dnm.upload(near_m, s);
+    dnp.upload(near_p, s);
+    DevBuf<cplx> Mt(m * N);
+    {
+      prof::KScope _ks("k_fill_nb", s);
+      const size_t dsm = 2 * (size_t)np * sizeof(double);
+      HBS_CUDA(raise_smem_limit((const void*)k_fill_nb, dsm));
+      k_fill_nb<<<grid_1d(m * N), 256, dsm, s>>>(g, dnm.get(), nm, dnp.get(), npn, d, cx, cy, R, np, wp, Mt.get());
+    }
+    HBS_LAUNCH_CHECK("k_fill_nb");
+    // Row ID of the neighbour interactions (Def. 3.1).  The skeleton is chosen by a
+    // column-pivoted QR among at most 4096 candidate boundary nodes (every stride-th): their
+    // columns of Mt are smooth functions of the node, so candidates far finer than the
+    // wavelength lose nothing.  Every node's interpolation coefficients then follow by
+    // least squares against the skeleton columns, t_i = R11^{-1} Q1^H Mt(:, i), which for
+    // the candidates is exactly T = R11^{-1} R12 of the QR.
+    // Candidates are whole nodes (both unknowns of a transmission node, whose rows differ).
+    const int comps = h.comps;
+    const int64_t nodes = N / comps;
+    const int64_t stride = std::max<int64_t>(1, (N + 4095) / 4096);
+    const int64_t ncn = (nodes + stride - 1) / stride;  // candidate nodes
+    const int64_t nc = ncn * comps;
+    DevBuf<cplx> Mc((size_t)m * nc);
+    std::vector<int64_t> cand(nc);
+    for (int64_t c = 0; c < ncn; ++c)
+      for (int u = 0; u < comps; ++u) cand[c * comps + u] = c * stride * comps + u;
+    if (comps == 1) {
+      HBS_CUDA(cudaMemcpy2DAsync(Mc.get(), sizeof(cplx) * m, Mt.get(), sizeof(cplx) * m * stride, sizeof(cplx) * m,
+                                 nc, cudaMemcpyDeviceToDevice, s));
+    } else {
+      DevBuf<int64_t> dcand;
+      dcand.upload(cand, s);
+      prof::KScope _ks("k_gather_cols", s);
+      k_gather_cols<<<grid_1d(m * nc), 256, 0, s>>>(Mt.get(), m, m, dcand.get(), nc, Mc.get(), m);
+      HBS_CUDA(cudaStreamSynchronize(s));  // dcand goes out of scope
+    }
+    const int kcap = (int)std::min<int64_t>(std::min<int64_t>(m, nc), 4096);
+    DevBuf<int> cperm(nc);
+    PqrOut qr;
+    {
+      std::vector<PqrSpec> sp{{Mc.get(), m, nc, kcap, cperm.get(), nullptr}};
+      pqr_run(sp, h.tol, s, qr);
+    }
+    const int l = qr.rank[0];
+    h.nb_rank = l;
+    std::vector<int> hpiv = qr.piv.download(s, l);
+    std::vector<int64_t> J(l);
+    for (int i = 0; i < l; ++i) J[i] = cand[hpiv[i]];
+    h.nb_skel.upload(J, s);
+    h.Rm.alloc(std::max<int64_t>((int64_t)l * N, 1));
+    h.Rp.alloc(std::max<int64_t>((int64_t)l * N, 1));
+    h.Pnb.alloc(std::max<int64_t>((int64_t)l * N, 1));
+    h.nb_residual = 0.0;
+    if (l > 0) {
+      {
+        prof::KScope _ks("k_fill_r", s);
+        k_fill_r<<<grid_1d((int64_t)l * N), 256, 0, s>>>(g, h.nb_skel.get(), l, d, h.Rm.get(), h.Rp.get());
+      }
+      HBS_LAUNCH_CHECK("k_fill_r");
+      DevBuf<cplx> Qc((size_t)m * l), Tall((size_t)l * N);
+      {
+        prof::KScope _ks("k_form_qc", s);
+        k_form_qc<<<l, 256, 0, s>>>(Mc.get(), m, qr.piv.get(), qr.v0.get(), qr.tau.get(), l, Qc.get());
+      }
+      HBS_LAUNCH_CHECK("neighbour Q1");
+      // Tall = Q1^H Mt (l x N), then R11^{-1} in place; skeleton nodes get unit columns.
+      std::vector<GemmJob> gj(1);
+      gj[0] = GemmJob{Qc.get(), Mt.get(), Tall.get(), l, (int)N, (int)m, (int)m, (int)m, l,
+                      cmk(1.0, 0.0), cmk(0.0, 0.0), 0, 0, 0, 1};
+      run_gemms(gj, s);
+      pqr_solve_r11(Mc.get(), m, qr, 0, l, Tall.get(), l, N, s);
+      {
+        prof::KScope _ks("k_set_unit_cols", s);
+        k_set_unit_cols<<<grid_1d((int64_t)l * l), 256, 0, s>>>(Tall.get(), l, h.nb_skel.get());
+      }
+      {
+        prof::KScope _ks("k_transpose", s);
+        k_transpose<<<grid_1d((int64_t)l * N), 256, 0, s>>>(Tall.get(), l, N, h.Pnb.get());
+      }
+      HBS_LAUNCH_CHECK("neighbour interpolation");
+      // Check on nodes half-way between candidates: |Mt(:, i) - Mt(:, J) t_i| / |Mt(:, i)|.
+      if (stride > 1) {
+        const int64_t nchk_n = std::min<int64_t>(ncn - 1, 4096 / comps);
+        const int64_t nchk = nchk_n * comps;
+        std::vector<int64_t> chk(nchk);
+        for (int64_t c = 0; c < nchk_n; ++c) {
+          const int64_t node = std::min<int64_t>(nodes - 1, ((c * (ncn - 1)) / nchk_n) * stride + stride / 2);
+          for (int u = 0; u < comps; ++u) chk[c * comps + u] = node * comps + u;
+        }
+        DevBuf<int64_t> dchk;
+        dchk.upload(chk, s);
+        DevBuf<cplx> G((size_t)m * l), Ms((size_t)m * nchk), Ts((size_t)l * nchk), Rec((size_t)m * nchk);
+        {
+          prof::KScope _ks("k_gather_cols", s);
+          k_gather_cols<<<grid_1d((int64_t)m * l), 256, 0, s>>>(Mt.get(), m, m, h.nb_skel.get(), l, G.get(), m);
+          k_gather_cols<<<grid_1d(m * nchk), 256, 0, s>>>(Mt.get(), m, m, dchk.get(), nchk, Ms.get(), m);
+          k_gather_cols<<<grid_1d((int64_t)l * nchk), 256, 0, s>>>(Tall.get(), l, l, dchk.get(), nchk, Ts.get(), l);
+        }
+        std::vector<GemmJob> cj(1);
+        cj[0] = GemmJob{G.get(), Ts.get(), Rec.get(), (int)m, (int)nchk, l, (int)m, l, (int)m,
+                        cmk(1.0, 0.0), cmk(0.0, 0.0), 0, 0, 0, 0};
+        run_gemms(cj, s);
+        DevBuf<double> acc(2);
+        HBS_CUDA(cudaMemsetAsync(acc.get(), 0, 2 * sizeof(double), s));
+        {
+          prof::KScope _ks("k_diff_norm2", s);
+          k_diff_norm2<<<grid_1d(m * nchk), 256, 0, s>>>(Rec.get(), m, Ms.get(), m, (int)m, (int)nchk, acc.get());
+        }
+        auto ha = acc.download(s);
+        h.nb_residual = ha[1] > 0 ? std::sqrt(ha[0] / ha[1]) : 0.0;
+      }
+    }
+    HBS_CUDA(cudaStreamSynchronize(s));
+  }
+  const int l = h.nb_rank;
+
   // ---- source columns [P | Y(:, JY)] (not applied: Z is formed as V [P | Y_sel])
   ph.next("build:skeleton_columns");
   const int rB = h.rB, rC = h.rC, rE = h.rE;
@@ -541,6 +556,7 @@ void build_periodizer(Handle& h, cudaStream_t s, bool with_hbs) {
   if (with_hbs) {
     ph.next("build:wait_hbs");
     hbs_worker.join();  // the compressed inverse is complete
+    background.end();
   }
   ph.next("build:V_apply");
   h.VT.alloc((size_t)N * h.rsel);
