@@ -89,10 +89,10 @@ FLOP_COUNT_NOTE = {
 # work (one launch, the periodizer families, dominates it by writing back its trailing
 # matrix when the matrices outgrow L2), so its N = 1e4 capture is not scaled.
 NCU_TRAFFIC = {
-    # profiles/k_pqr_wiggly_n10k.md: all 9 launches of a step at N = 1e4 (27 over 3 steps)
-    ("wiggly_n10k", "k_pqr"): {"bytes_per_launch": 3.635e+08, "note": "ncu capture of this workload",
+    # profiles/k_pqr_wiggly_n10k.md: all 8 launches of a step at N = 1e4 (24 over 3 steps)
+    ("wiggly_n10k", "k_pqr"): {"bytes_per_launch": 4.024e+08, "note": "ncu capture of this workload",
                                 "sources": ['paper_1301_1247_gb300/csrc/pqr.cu', 'paper_1301_1247_gb300/csrc/common.cuh', 'paper_1301_1247_gb300/csrc/gridsync.cuh', 'paper_1301_1247_gb300/csrc/dense_kernels.cuh', 'paper_1301_1247_gb300/csrc/dfloat.cuh', 'paper_1301_1247_gb300/csrc/dfcore.cuh', 'paper_1301_1247_gb300/csrc/hankel_table.h', 'paper_1301_1247_gb300/csrc/balance.hpp', 'paper_1301_1247_gb300/csrc/devbuf.hpp'],
-                                "digest": "6e7a6fff1b5102b1"},
+                                "digest": "d697f4a8d32a5b40"},
     # profiles/k_zgemm_batched_df_wiggly_n10k.md: all 141 launches of 3 steps at N = 1e4 moved
     # 25.40 MB of DRAM per launch against 37.38 MB of algorithmic bytes per launch (the same
     # command's profiled pass); scaled to the N = 1e5 launches by their algorithmic bytes
