@@ -132,6 +132,20 @@ def measured_traffic(workload_name, kernel, alg_bytes_per_launch=None):
     return rec["ratio_to_algorithmic"] * alg_bytes_per_launch, rec["note"]
 
 
+def split_profile(prof, steps):
+    """Split hbs.profile_get() records: the per-kernel records, each phase's host wall time
+    (ms per step; "phase:<name>") and, per phase, each kernel's device time (ms per step) and
+    launches per step ("in:<phase>:<kernel>", phase names themselves hold colons)."""
+    kern = {k: v for k, v in prof.items() if not k.startswith(("phase:", "in:"))}
+    phases = {k[6:]: round(v["ms"] / steps, 2) for k, v in prof.items() if k.startswith("phase:")}
+    by_phase = {}
+    for k, v in prof.items():
+        if k.startswith("in:"):
+            ph, kn = k[3:].rsplit(":", 1)
+            by_phase.setdefault(ph, {})[kn] = {"ms": round(v["ms"] / steps, 3), "launches": v["launches"] / steps}
+    return kern, phases, by_phase
+
+
 def workload(name):
     if name == "complicated_n100k":
         w = inputs.workload_complicated_n100k()
@@ -422,15 +436,8 @@ def run_ours(args, ws, rank, local):
         del h64, ref, hb, ra, rb
 
     value = whole_job_rate(ws, n_ang, args.steps, ms_max)
-    kern = {k: v for k, v in prof.items() if not k.startswith(("phase:", "in:"))}
-    phases = {k[6:]: round(v["ms"] / args.steps, 2) for k, v in prof.items() if k.startswith("phase:")}
+    kern, phases, by_phase = split_profile(prof, args.steps)
     if args.phase_kernels:
-        by_phase = {}
-        for k, v in prof.items():
-            if k.startswith("in:"):
-                ph, kn = k[3:].rsplit(":", 1)
-                by_phase.setdefault(ph, {})[kn] = {"ms": round(v["ms"] / args.steps, 3),
-                                                  "launches": v["launches"] / args.steps}
         with open(args.phase_kernels, "w") as f:
             json.dump({"phases_ms_per_step": phases, "kernels_by_phase": by_phase}, f, indent=1, sort_keys=True)
     top = max(kern.items(), key=lambda kv: kv[1]["ms"])
