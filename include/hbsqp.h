@@ -378,7 +378,8 @@ int64_t hbs_launch_count(void);
  *  - The first call on a device looks up the array's device address (with that
  *    device current); make that first call before any CUDA graph capture.
  *  - Every call waits for `stream` before it returns: it steps the pivot search
- *    from the host and reads the rank back.
+ *    from the host and reads the rank back.  No call may therefore run while the
+ *    stream is being captured into a CUDA graph.
  *  - All calls share the one array and it keeps the last call's contents: two
  *    calls that overlap on the GPU (different streams, or different host threads)
  *    race and give wrong results.  Serialise them.
