@@ -60,8 +60,14 @@ def kernel_peak(name, prec):
         return ("tensor", MEASURED_PEAKS["bf16_tflops"],
                 "executed bf16 tensor flops (28 digit pairs x 4 real products x 2 m n k, padded tiles) "
                 "against the measured cuBLAS bf16 burst rate in MEASURED_PEAKS.json")
-    if name == "k_zgemm_batched_df" or (prec >= 1 and name in ("k_pqr", "k_cpqr")):
-        per = {"k_zgemm_batched_df": 48.0 / 8.0, "k_pqr": 102.0 / 16.0, "k_cpqr": 102.0 / 16.0}[name]
+    # kernels whose updates run in double-float on double-float and tensor-precision handles:
+    # FP32-pipe instructions per FP64-equivalent flop (a complex multiply-add is 4 error-free
+    # multiply-adds of 12 instructions, 48 per 8 flops; the pivoted QR's update, 102 per 16)
+    df_per = {"k_zgemm_batched_df": 48.0 / 8.0, "k_pqr": 102.0 / 16.0, "k_cpqr": 102.0 / 16.0,
+              "k_schur_solve": 48.0 / 8.0, "k_pgj": 48.0 / 8.0, "k_gj_inverse": 48.0 / 8.0,
+              "k_bgj_panel": 48.0 / 8.0}
+    if name == "k_zgemm_batched_df" or (prec >= 1 and name in df_per):
+        per = df_per[name]
         return ("alu", FP32_INSTR_PEAK / per / 1e12,
                 "double-float arithmetic on the FP32 pipes: %.2f FP32-pipe instructions per FP64-equivalent flop "
                 "(complex multiply-add = 4 error-free multiply-adds of 12 instructions) at 152 SM x 128 lanes x "

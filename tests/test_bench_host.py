@@ -62,3 +62,16 @@ def test_committed_traffic_records_name_existing_sources():
         for p in rec["sources"]:
             assert os.path.exists(os.path.join(bench.ROOT, p)), p
         assert len(rec["digest"]) == 16
+
+
+def test_kernel_peaks_follow_the_precision_mode():
+    # FP64 handles: the FP64 unit; double-float and tensor precision: the FP32 pipes for every
+    # kernel whose updates run in double-float, so no kernel's fraction can exceed its unit
+    fp64 = bench.kernel_peak("k_schur_solve", 0)[1]
+    for name in ("k_schur_solve", "k_pgj", "k_gj_inverse", "k_bgj_panel", "k_pqr", "k_cpqr"):
+        assert bench.kernel_peak(name, 0)[1] == fp64
+        for prec in (1, 2):
+            bound, peak, note = bench.kernel_peak(name, prec)
+            assert bound == "alu" and peak > 4.0 * fp64 and "double-float" in note
+    assert bench.kernel_peak("k_zgemm_batched_df", 0)[1] > 4.0 * fp64
+    assert bench.kernel_peak("k_oz_mma", 2)[0] == "tensor"
