@@ -535,7 +535,7 @@ static bool big_inverse(int n) { return n > 128; }
 // top of the tree the level-1 ID and inversions are latency-bound work on two nodes; without
 // them the root inverts the level-2 skeletons' coupled system directly (the same system,
 // one interpolative decomposition fewer).
-constexpr int kPassThroughRootMax = 1536;
+constexpr int kPassThroughRootMax = 2048;
 
 static bool passthrough_level(const Handle& h, int l) {
   if (l != 1 || h.L < 2) return false;
